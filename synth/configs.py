@@ -1,0 +1,147 @@
+"""The five seeded workloads (plus small variants used by tests).
+
+Each builder returns plain NumPy arrays (float64 positions/velocities, box
+edges) and a dict of run parameters.  Nothing here evaluates the method.
+
+Workloads (LJ units, sigma = epsilon = m = 1, density 0.8442 unless stated):
+  lj_small    1000 atoms, sc 10^3, uniform noise +-0.05, T = 1.0, rc = 2.5
+  lj_solid    fcc 63^3 cells = 1,000,188 atoms, Gaussian noise 0.02, T = 0.8,
+              rc = 2.5, list cutoff 2.8, list rebuilt every 10 steps
+  structure   four 512,000-atom periodic boxes (fcc, bcc, hcp, liquid-like)
+              per noise level sigma in {0.02, 0.05, 0.1} x nearest-neighbour distance
+  replicas    256 independent boxes, N log-uniform in [500, 32000],
+              density U[0.7, 1.0], T U[0.7, 1.5], jittered sc
+  classifier  training and inference sets of structure-style boxes
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .lattices import (cell_edges, jittered, make_lattice, maxwell_boltzmann, rng_stream, wrap)
+
+RHO = 0.8442
+RC = 2.5
+R_BOA = 1.5
+# CNA cutoff: midway between the first (a/sqrt2) and second (a) shells of fcc at RHO.
+_A_FCC = (4.0 / RHO) ** (1.0 / 3.0)
+R_CNA = 0.5 * (_A_FCC / math.sqrt(2.0) + _A_FCC)
+DT = 0.005
+
+
+def lj_small(seed: int = 1, n_side: int = 10, temperature: float = 1.0):
+    """Plain method, small, FP64 (1000 atoms on a 10^3 simple-cubic lattice)."""
+    lat = make_lattice("sc", n_side, RHO)
+    pos, box = jittered(lat, rng_stream(seed, 0), "uniform", 0.05, cutoffs=(RC,),
+                        resample_rng=rng_stream(seed, 1))
+    vel = maxwell_boltzmann(rng_stream(seed, 2), len(pos), temperature)
+    return dict(pos=pos, vel=vel, box=box, rc=RC, r_list=RC, rebuild_every=1, dt=DT,
+                steps=100, mass=1.0, name=f"lj_small_sc{n_side}^3")
+
+
+def lj_solid(seed: int = 2, n_cells: int = 63, temperature: float = 0.8, skin: float = 0.3,
+             noise: float = 0.02):
+    """Large LJ solid: fcc n_cells^3 (63^3 -> 1,000,188 atoms)."""
+    lat = make_lattice("fcc", n_cells, RHO)
+    r_list = RC + skin
+    pos, box = jittered(lat, rng_stream(seed, 0), "gauss", noise, cutoffs=(RC, r_list),
+                        resample_rng=rng_stream(seed, 1))
+    vel = maxwell_boltzmann(rng_stream(seed, 2), len(pos), temperature)
+    return dict(pos=pos, vel=vel, box=box, rc=RC, r_list=r_list, rebuild_every=10, dt=DT,
+                steps=1000, mass=1.0, name=f"lj_solid_fcc{n_cells}^3")
+
+
+def nn_distance(kind: str, rho: float = RHO) -> float:
+    e = cell_edges(kind, rho)
+    if kind == "fcc":
+        return e[0] / math.sqrt(2.0)
+    if kind == "bcc":
+        return e[0] * math.sqrt(3.0) / 2.0
+    if kind in ("hcp", "sc"):
+        return e[0]
+    raise ValueError(kind)
+
+
+# Cell counts giving 512,000 atoms for each structure box.
+STRUCTURE_CELLS = {"fcc": (80, 80, 20), "bcc": (80, 80, 40), "hcp": (80, 40, 40), "liquid": (80, 80, 80)}
+# Liquid-like box: a simple-cubic lattice with large Gaussian displacements
+# (0.15 per component).  It stands in for an equilibrated LJ liquid snapshot,
+# which would have to be produced by the method under test.
+LIQUID_NOISE = 0.15
+
+
+def structure_box(kind: str, sigma_frac: float, seed: int, cells=None):
+    """One structure-analysis box.  `kind` in fcc, bcc, hcp, liquid."""
+    cells = cells if cells is not None else STRUCTURE_CELLS[kind]
+    stream0 = {"fcc": 0, "bcc": 2, "hcp": 4, "liquid": 6}[kind]
+    if kind == "liquid":
+        lat = make_lattice("sc", cells, RHO)
+        amp = LIQUID_NOISE
+    else:
+        lat = make_lattice(kind, cells, RHO)
+        amp = sigma_frac * nn_distance(kind)
+    pos, box = jittered(lat, rng_stream(seed, stream0), "gauss", amp, cutoffs=(R_BOA, R_CNA),
+                        resample_rng=rng_stream(seed, stream0 + 1))
+    return dict(pos=pos, box=box, kind=kind, sigma=amp)
+
+
+def structure(sigma_frac: float = 0.02, seed: int = 30, cells=None):
+    """The four boxes of one noise level, in the order fcc, bcc, hcp, liquid."""
+    out = []
+    for kind in ("fcc", "bcc", "hcp", "liquid"):
+        c = None if cells is None else cells[kind]
+        out.append(structure_box(kind, sigma_frac, seed, c))
+    return out
+
+
+def replicas(seed: int = 4, nrep: int = 256, n_min: int = 500, n_max: int = 32000, skin: float = 0.3):
+    """Batched replicas: per replica N, density, temperature, box, positions, velocities.
+
+    N = round(exp(U(ln n_min, ln n_max))); sc lattice with ceil(N^(1/3)) sites per
+    edge scaled to the box L = (N/rho)^(1/3); the first N sites in index order are
+    used; uniform +-0.05 jitter.  The list cutoff is min(rc + skin, L/3) so that
+    every box has at least three cells per edge.
+    """
+    g = rng_stream(seed, 0)
+    ns = np.rint(np.exp(g.uniform(math.log(n_min), math.log(n_max), nrep))).astype(np.int64)
+    rhos = g.uniform(0.7, 1.0, nrep)
+    temps = g.uniform(0.7, 1.5, nrep)
+    reps = []
+    for r in range(nrep):
+        n = int(ns[r])
+        side = int(math.ceil(round(n ** (1.0 / 3.0), 9)))
+        box_l = (n / rhos[r]) ** (1.0 / 3.0)
+        lat = make_lattice("sc", side, 1.0)
+        lat.edges = np.full(3, box_l / side)
+        lat.box = lat.edges * side
+        r_list = min(RC + skin, math.floor(box_l / 3.0 * 1e6) / 1e6)
+        pos, box = jittered(lat, rng_stream(seed, 10 + 3 * r), "uniform", 0.05, cutoffs=(RC, r_list),
+                            n_active=n, resample_rng=rng_stream(seed, 11 + 3 * r))
+        vel = maxwell_boltzmann(rng_stream(seed, 12 + 3 * r), n, float(temps[r]))
+        reps.append(dict(pos=pos, vel=vel, box=box, rho=float(rhos[r]), T=float(temps[r]), r_list=r_list))
+    return reps
+
+
+def random_box(n: int, box, seed: int, cutoffs=(), margin: float = 1e-6, min_dist: float = 0.0):
+    """n atoms uniform in a box (small n: brute-force pair checks).  Atoms closer than
+    min_dist to another atom, or in a pair within `margin` of a cutoff, are redrawn."""
+    box = np.asarray(box, dtype=np.float64)
+    g = rng_stream(seed, 0)
+    pos = g.uniform(0.0, 1.0, (n, 3)) * box
+    for _ in range(200):
+        dr = pos[:, None, :] - pos[None, :, :]
+        dr -= box * np.rint(dr / box)
+        r = np.sqrt((dr ** 2).sum(-1))
+        np.fill_diagonal(r, np.inf)
+        bad = (r < min_dist)
+        for c in cutoffs:
+            bad |= np.abs(r - c) < margin
+        rows = np.nonzero(bad.any(1))[0]
+        if len(rows) == 0:
+            return wrap(pos, box), box
+        # redraw the higher-index atom of each offending pair
+        ii, jj = np.nonzero(np.triu(bad, 1))
+        idx = np.unique(jj)
+        pos[idx] = g.uniform(0.0, 1.0, (len(idx), 3)) * box
+    raise RuntimeError("random_box: could not satisfy constraints")

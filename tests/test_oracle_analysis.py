@@ -1,0 +1,230 @@
+"""Pins of the FP64 oracle's bond order analysis, common neighbour analysis,
+classifier features and MLP reference (no GPU)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from synth import configs, make_lattice
+from synth.configs import R_CNA, random_box
+
+RHO = 0.8442
+LATTICE_CELLS = {"fcc": 4, "hcp": (5, 3, 3), "bcc": 5}
+
+
+def _perfect(kind):
+    lat = make_lattice(kind, LATTICE_CELLS[kind], RHO)
+    return lat.sites(), lat.box
+
+
+@pytest.mark.parametrize("kind", ["fcc", "hcp", "bcc"])
+def test_perfect_lattice_Q_matches_paper_table(kind, golden):
+    pos, box = _perfect(kind)
+    offs, nbr = oracle.neighbours_brute(pos, box, 1.5)
+    ref = golden["Q_table"][kind]
+    for l, key in ((4, "Q4"), (5, "Q5"), (6, "Q6")):
+        Q, nnb = oracle.boa(pos, box, offs, nbr, 1.5, l)
+        assert (nnb == (14 if kind == "bcc" else 12)).all()
+        # the paper prints three digits
+        assert np.abs(Q - ref[key]).max() <= 0.0006, (kind, l, Q[0])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_Q_direct_equals_addition_theorem(seed):
+    """Two independent routes to Q_l: sums of Y_l^m (Eq. (2)) and the Legendre
+    addition theorem."""
+    pos, box = random_box(150, [6.0, 6.0, 6.0], seed, cutoffs=(1.5,), margin=1e-6, min_dist=0.8)
+    offs, nbr = oracle.neighbours_brute(pos, box, 1.5)
+    for l in (2, 3, 4, 6, 8):
+        Qd, nnb = oracle.boa(pos, box, offs, nbr, 1.5, l)
+        Qa = oracle.boa(pos, box, offs, nbr, 1.5, l, method="addition")
+        assert np.abs(Qd - Qa).max() < 1e-12
+        assert (Qd[nnb == 0] == 0).all()
+    # l = 0: Y_0^0 is constant, so Q_0 = 1 for every atom with a neighbour
+    Q0, nnb = oracle.boa(pos, box, offs, nbr, 1.5, 0)
+    assert np.allclose(Q0[nnb > 0], 1.0, atol=1e-14)
+
+
+def _rotation(seed):
+    q = np.random.default_rng(seed).normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                     [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                     [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+def test_Q_rotation_and_translation_invariant():
+    rng = np.random.default_rng(3)
+    cluster = rng.normal(0, 0.7, (40, 3))
+    cluster = cluster[np.linalg.norm(cluster, axis=1) < 2.0]
+    box = np.array([40.0, 40.0, 40.0])
+    base = cluster + 20.0
+    offs, nbr = oracle.neighbours_brute(base, box, 1.5)
+    Q6a, _ = oracle.boa(base, box, offs, nbr, 1.5, 6)
+    rot = cluster @ _rotation(4).T + np.array([13.3, 21.7, 19.1])
+    Q6b, _ = oracle.boa(rot, box, offs, nbr, 1.5, 6)
+    assert np.abs(Q6a - Q6b).max() < 1e-12
+
+
+def _sig(nbond, trip, i):
+    out = {}
+    for t in trip[i, :nbond[i]]:
+        k = f"{t >> 16},{(t >> 8) & 255},{t & 255}"
+        out[k] = out.get(k, 0) + 1
+    return out
+
+
+@pytest.mark.parametrize("kind", ["fcc", "hcp", "bcc"])
+def test_perfect_lattice_cna_signatures(kind, golden):
+    pos, box = _perfect(kind)
+    offs, nbr = oracle.neighbours_brute(pos, box, R_CNA)
+    nbond, trip, partner, numax = oracle.cna(pos, box, offs, nbr, R_CNA)
+    ref = golden["cna_signatures"][kind]
+    for i in range(len(pos)):
+        assert nbond[i] == ref["nbonds"]
+        assert _sig(nbond, trip, i) == ref["triplets"]
+    lab = oracle.cna_label(nbond, trip)
+    assert (lab == {"fcc": 1, "hcp": 2, "bcc": 3}[kind]).all()
+
+
+def _cna_brute(pos, box, rc):
+    """Independent CNA: adjacency sets, common neighbours by intersection,
+    largest component by union-find, counted in edges."""
+    n = len(pos)
+    dr = pos[:, None, :] - pos[None, :, :]
+    dr -= box * np.rint(dr / box)
+    adj = ((dr ** 2).sum(-1) < rc * rc) & ~np.eye(n, dtype=bool)
+    nb = [set(np.nonzero(adj[i])[0].tolist()) for i in range(n)]
+    out = {}
+    for i in range(n):
+        for j in nb[i]:
+            C = nb[i] & nb[j]
+            E = [(v, w) for v, w in itertools.combinations(sorted(C), 2) if w in nb[v]]
+            parent = {v: v for v in C}
+
+            def find(x):
+                while parent[x] != x:
+                    parent[x] = parent[parent[x]]
+                    x = parent[x]
+                return x
+            for v, w in E:
+                parent[find(v)] = find(w)
+            count = {}
+            for v, w in E:
+                r = find(v)
+                count[r] = count.get(r, 0) + 1
+            out[(i, j)] = (len(C), len(E), max(count.values()) if count else 0)
+    return out
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_cna_matches_brute_force(seed):
+    pos, box = random_box(100, [5.2, 5.0, 4.9], seed, cutoffs=(R_CNA,), margin=1e-6, min_dist=0.8)
+    offs, nbr = oracle.neighbours_brute(pos, box, 2.0)
+    nbond, trip, partner, numax = oracle.cna(pos, box, offs, nbr, R_CNA)
+    ref = _cna_brute(pos, box, R_CNA)
+    seen = set()
+    for i in range(len(pos)):
+        for a in range(nbond[i]):
+            j = int(partner[i, a])
+            t = trip[i, a]
+            assert (int(t >> 16), int((t >> 8) & 255), int(t & 255)) == ref[(i, j)]
+            seen.add((i, j))
+    assert seen == set(ref)
+    # the triplet of a bond does not depend on which end computes it
+    tmap = {(i, int(partner[i, a])): trip[i, a] for i in range(len(pos)) for a in range(nbond[i])}
+    assert all(tmap[(j, i)] == t for (i, j), t in tmap.items())
+    # the random boxes exercise split common-neighbour graphs (n_lcb < n_b)
+    assert len(set(ref.values())) >= 5 and any(v[2] < v[1] for v in ref.values())
+
+
+def test_cna_labels_permutation_invariant():
+    c = configs.structure_box("hcp", 0.05, seed=9, cells=(6, 3, 3))
+    pos, box = c["pos"], c["box"]
+    perm = np.random.default_rng(1).permutation(len(pos))
+    offs, nbr = oracle.neighbours_brute(pos, box, R_CNA)
+    lab = oracle.cna_label(*oracle.cna(pos, box, offs, nbr, R_CNA)[:2])
+    o2, n2 = oracle.neighbours_brute(pos[perm], box, R_CNA)
+    lab2 = oracle.cna_label(*oracle.cna(pos[perm], box, o2, n2, R_CNA)[:2])
+    assert np.array_equal(lab[perm], lab2)
+    assert (lab == 2).sum() > 0
+
+
+def test_features_perfect_fcc_closed_form():
+    pos, box = _perfect("fcc")
+    offs, nbr = oracle.neighbours_brute(pos, box, 1.5)
+    f = oracle.features(pos, box, offs, nbr, 1.5)
+    d = (4.0 / RHO) ** (1.0 / 3.0) / np.sqrt(2.0)
+    expect = np.zeros(30)
+    expect[0], expect[1] = 0.19094065395649334, 0.5745242597140697
+    expect[2:14] = d / 1.5
+    expect[14:16] = 1.0
+    # 66 neighbour pairs: cos = 1/2 (24), 0 (12), -1/2 (24), -1 (6); tent bins
+    expect[16 + 10] = 24 / 66
+    expect[16 + 6] = expect[16 + 7] = 6 / 66
+    expect[16 + 3] = 24 / 66
+    expect[16 + 0] = 6 / 66
+    assert np.abs(f - expect).max() < 1e-9
+
+
+def test_features_rotation_invariant_and_normalised():
+    rng = np.random.default_rng(8)
+    cluster = rng.normal(0, 0.6, (30, 3))
+    box = np.array([40.0, 40.0, 40.0])
+    a = cluster + 20.0
+    b = cluster @ _rotation(9).T + 17.5
+    offs, nbr = oracle.neighbours_brute(a, box, 1.5)
+    fa = oracle.features(a, box, offs, nbr)
+    fb = oracle.features(b, box, offs, nbr)
+    assert np.abs(fa - fb).max() < 1e-9
+    nn = np.diff(offs)
+    has2 = nn >= 2
+    assert np.allclose(fa[has2, 16:].sum(1), 1.0)
+    assert (np.diff(fa[:, 2:16], axis=1) >= -1e-15).all()
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    p = mlp.init_params(rng)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.normal(0, 0.1, p[k].shape)
+    x = rng.normal(0, 1, (16, 30))
+    y = rng.integers(0, 4, 16)
+    loss, g = mlp.loss_and_grad(p, x, y)
+    h = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        for idx in rng.choice(flat.size, min(6, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = mlp.loss_and_grad(p, x, y)[0]
+            flat[idx] = old - h
+            lm = mlp.loss_and_grad(p, x, y)[0]
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[k].reshape(-1)[idx]) < 1e-7 * max(1.0, abs(fd)), k
+
+
+def test_adamw_textbook_steps():
+    """Three parameters, two steps, against values worked out by hand from the
+    AdamW update (bias-corrected moments, decoupled decay on weights)."""
+    p = {"W1": np.array([1.0, -2.0, 0.5])}
+    s = mlp.adamw_init(p)
+    g1 = {"W1": np.array([0.1, 0.0, -0.4])}
+    mlp.adamw_step(p, g1, s, lr=0.1, wd=0.5, eps=1e-8)
+    # step 1: m_hat = g, v_hat = g^2 -> update g/(|g| + eps) = sign(g) (or 0)
+    exp1 = np.array([1.0 * (1 - 0.05) - 0.1 * (0.1 / (0.1 + 1e-8)),
+                     -2.0 * (1 - 0.05),
+                     0.5 * (1 - 0.05) + 0.1 * (0.4 / (0.4 + 1e-8))])
+    assert np.allclose(p["W1"], exp1, rtol=0, atol=1e-12)
+    g2 = {"W1": np.array([0.3, 0.2, 0.0])}
+    mlp.adamw_step(p, g2, s, lr=0.1, wd=0.5, eps=1e-8)
+    m = 0.9 * 0.1 * np.array([0.1, 0.0, -0.4]) + 0.1 * np.array([0.3, 0.2, 0.0])
+    v = 0.999 * 0.001 * np.array([0.01, 0.0, 0.16]) + 0.001 * np.array([0.09, 0.04, 0.0])
+    mh, vh = m / (1 - 0.81), v / (1 - 0.999 ** 2)
+    exp2 = exp1 * (1 - 0.05) - 0.1 * mh / (np.sqrt(vh) + 1e-8)
+    assert np.allclose(p["W1"], exp2, rtol=0, atol=1e-12)

@@ -1,0 +1,208 @@
+"""Pins of the FP64 oracle's cell list, neighbour list, LJ pair loop and
+Velocity Verlet against facts fixed by the paper and by mathematics (no GPU)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import configs, make_lattice, maxwell_boltzmann, rng_stream
+from synth.configs import random_box
+
+RHO = 0.8442
+
+
+def _lattice_energy_per_atom(kind, rc, shift=0.0):
+    """Closed-form lattice sum by integer enumeration (independent of the oracle):
+    fcc sites are (i, j, k) a/2 with i + j + k even; sc sites are (i, j, k) a."""
+    if kind == "fcc":
+        a = (4.0 / RHO) ** (1.0 / 3.0)
+        scale, parity = a / 2.0, True
+    else:
+        a = RHO ** (-1.0 / 3.0)
+        scale, parity = a, False
+    R = int(rc / scale) + 1
+    s = 0.0
+    for i, j, k in itertools.product(range(-R, R + 1), repeat=3):
+        if parity and (i + j + k) % 2:
+            continue
+        r = math.sqrt(i * i + j * j + k * k) * scale
+        if 0 < r < rc:
+            s += 2.0 * (r ** -12 - r ** -6 + shift)
+    return s
+
+
+@pytest.mark.parametrize("kind,ncell", [("fcc", 6), ("sc", 8)])
+@pytest.mark.parametrize("shift", [0.0, 0.25])
+def test_lattice_energy_closed_form(kind, ncell, shift):
+    lat = make_lattice(kind, ncell, RHO)
+    pos, box = lat.sites(), lat.box
+    offs, nbr = oracle.neighbours_cells(pos, box, 2.5)
+    F, e, U, W = oracle.lj(pos, box, offs, nbr, shift=shift)
+    ref = _lattice_energy_per_atom(kind, 2.5, shift)
+    assert abs(U / len(pos) - ref) < 1e-11 * abs(ref)
+    assert np.allclose(e, ref, rtol=1e-11, atol=0)
+    assert np.abs(F).max() < 1e-11  # every atom is a centre of inversion
+    # neighbour counts within 2.5: 54 for fcc, 56 for sc; within 2.8 fcc has 78
+    assert (np.diff(offs) == (54 if kind == "fcc" else 56)).all()
+    if kind == "fcc":
+        o28, _ = oracle.neighbours_cells(pos, box, 2.8)
+        assert (np.diff(o28) == 78).all()
+
+
+def test_fcc_closed_form_values():
+    # fixed decimal values of the two lattice sums at rho = 0.8442, rc = 2.5
+    assert abs(_lattice_energy_per_atom("fcc", 2.5) - (-6.773368053253)) < 1e-11
+    assert abs(_lattice_energy_per_atom("fcc", 2.5, 0.25) - 20.226631946747) < 1e-11
+    assert abs(_lattice_energy_per_atom("sc", 2.5) - (-5.220218519441)) < 1e-11
+
+
+def _tiny_box(seed, n=60, L=7.3, margin=1e-3):
+    return random_box(n, [L, L * 1.1, L * 0.95], seed, cutoffs=(2.5, 2.8), margin=margin, min_dist=0.85)
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_neighbour_list_cells_equal_brute_force(seed):
+    pos, box = _tiny_box(seed, n=140, L=9.0)
+    for r in (2.5, 2.8):
+        o1, n1 = oracle.neighbours_brute(pos, box, r)
+        o2, n2 = oracle.neighbours_cells(pos, box, r)
+        assert np.array_equal(o1, o2) and np.array_equal(n1, n2)
+        # symmetric: j in N(i) iff i in N(j)
+        pairs = {(i, int(j)) for i in range(len(pos)) for j in n1[o1[i]:o1[i + 1]]}
+        assert all((j, i) in pairs for (i, j) in pairs)
+
+
+def test_cells_contain_their_atoms():
+    c = configs.lj_solid(n_cells=6)
+    pos, box = c["pos"], c["box"]
+    nc, cell_of, start, atoms = oracle.cells(pos, box, 2.8)
+    assert (nc == np.floor(box / 2.8)).all()
+    w = box / nc
+    cz, rem = np.divmod(cell_of, nc[0] * nc[1])
+    cy, cx = np.divmod(rem, nc[0])
+    cc = np.stack([cx, cy, cz], 1)
+    assert (cc * w <= pos + 1e-12).all() and (pos < (cc + 1) * w + 1e-12).all()
+    assert start[0] == 0 and start[-1] == len(pos) and (np.diff(start) >= 0).all()
+    for c_ in range(len(start) - 1):
+        members = atoms[start[c_]:start[c_ + 1]]
+        assert (cell_of[members] == c_).all() and (np.diff(members) > 0).all()
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_force_is_minus_energy_gradient(seed):
+    """F = -grad U (Eq. (8) from Eq. (7)) by central differences of the total energy;
+    pins the force's sign, exponents and prefactor."""
+    pos, box = _tiny_box(seed)
+    offs, nbr = oracle.neighbours_brute(pos, box, 2.5)
+    F, e, U, W = oracle.lj(pos, box, offs, nbr)
+    h = 1e-6
+    rng = np.random.default_rng(seed)
+    for i in rng.choice(len(pos), 8, replace=False):
+        for d in range(3):
+            pp = pos.copy(); pp[i, d] += h
+            pm = pos.copy(); pm[i, d] -= h
+            Up = oracle.lj(pp, box, offs, nbr)[2]
+            Um = oracle.lj(pm, box, offs, nbr)[2]
+            fd = -(Up - Um) / (2 * h)
+            assert abs(fd - F[i, d]) < 1e-6 * max(1.0, abs(F[i, d]))
+
+
+@pytest.mark.parametrize("seed", [31])
+def test_virial_is_volume_derivative(seed):
+    """W = sum_{i<j} r_ij . f_ij equals -dU/dlambda under uniform scaling r -> lambda r."""
+    pos, box = _tiny_box(seed)
+    offs, nbr = oracle.neighbours_brute(pos, box, 2.5)
+    F, e, U, W = oracle.lj(pos, box, offs, nbr)
+    h = 1e-7
+    Up = oracle.lj(pos * (1 + h), box * (1 + h), offs, nbr)[2]
+    Um = oracle.lj(pos * (1 - h), box * (1 - h), offs, nbr)[2]
+    assert abs(-(Up - Um) / (2 * h) - W) < 1e-5 * max(1.0, abs(W))
+
+
+def test_newton_third_law_and_energy_sum():
+    c = configs.lj_solid(n_cells=6)
+    offs, nbr = oracle.neighbours_cells(c["pos"], c["box"], 2.8)
+    F, e, U, W = oracle.lj(c["pos"], c["box"], offs, nbr)
+    rmsF = np.sqrt((F ** 2).sum(1).mean())
+    assert np.abs(F.sum(0)).max() < 1e-12 * len(F) * rmsF
+    assert abs(e.sum() - U) < 1e-12 * abs(U)
+    # the list at 2.8 gives the same forces as the list at exactly 2.5
+    o2, n2 = oracle.neighbours_cells(c["pos"], c["box"], 2.5)
+    F2 = oracle.lj(c["pos"], c["box"], o2, n2)[0]
+    assert np.abs(F - F2).max() < 1e-12 * rmsF
+
+
+def test_shift_changes_energy_not_force():
+    c = configs.lj_small()
+    offs, nbr = oracle.neighbours_cells(c["pos"], c["box"], 2.5)
+    F0, e0, U0, _ = oracle.lj(c["pos"], c["box"], offs, nbr, shift=0.0)
+    F1, e1, U1, _ = oracle.lj(c["pos"], c["box"], offs, nbr, shift=0.25)
+    assert np.array_equal(F0, F1)
+    # +eps per pair term, half to each atom of the pair: e_i gains nu_i / 2
+    assert np.allclose(e1 - e0, np.diff(offs) * 0.5, rtol=0, atol=1e-12)
+
+
+def test_vv_constant_force_closed_form():
+    """One step of Algorithm 6 under a constant force reproduces the exact
+    kinematics r + v dt + F dt^2 / (2m) and v + F dt / m."""
+    box = np.array([50.0, 50.0, 50.0])
+    pos = np.array([[10.0, 20.0, 30.0]])
+    vel = np.array([[0.3, -0.2, 0.1]])
+    F = np.array([[1.5, 0.5, -2.0]])
+    m, dt = 2.0, 0.01
+    p1, v1 = oracle.vv(1, pos, vel, F, box, m, dt)
+    p2, v2 = oracle.vv(2, p1, v1, F, box, m, dt)
+    assert np.allclose(p2, pos + vel * dt + F * dt * dt / (2 * m), rtol=0, atol=1e-14)
+    assert np.allclose(v2, vel + F * dt / m, rtol=0, atol=1e-14)
+
+
+def test_vv_wraps_into_box():
+    box = np.array([5.0, 5.0, 5.0])
+    pos = np.array([[4.999, 0.0005, 2.0]])
+    vel = np.array([[1.0, -1.0, 0.0]])
+    p1, _ = oracle.vv(1, pos, vel, np.zeros((1, 3)), box, 1.0, 0.005)
+    assert np.allclose(p1, [[0.004, 4.9955, 2.0]], atol=1e-12)
+    assert ((p1 >= 0) & (p1 < box)).all()
+
+
+def _cold_crystal(dt, nsteps):
+    lat = make_lattice("fcc", 4, RHO)
+    pos = lat.sites() + rng_stream(5, 0).normal(0, 0.005, (lat.nsite, 3))
+    vel = maxwell_boltzmann(rng_stream(5, 1), lat.nsite, 0.01)
+    return oracle.md_run(pos, vel, lat.box, nsteps, rc=2.5, r_list=2.5, rebuild_every=1, dt=dt)
+
+
+def test_vv_energy_error_is_second_order():
+    """Velocity Verlet conserves energy up to O(dt^2): halving dt quarters the
+    energy fluctuation (cold fcc crystal: no pair crosses the cutoff)."""
+    _, v_a, _, en_a, _ = _cold_crystal(0.005, 200)
+    _, v_b, _, en_b, _ = _cold_crystal(0.0025, 400)
+    ea = en_a.sum(1)
+    eb = en_b.sum(1)
+    fa = ea.max() - ea.min()
+    fb = eb.max() - eb.min()
+    assert fa / abs(ea.mean()) < 1e-6
+    assert 3.0 < fa / fb < 5.0
+    # total momentum is conserved (it starts at zero)
+    assert np.abs(v_a.sum(0)).max() < 1e-11
+
+
+def test_md_time_reversible():
+    c = configs.lj_small()
+    p1, v1, _, _, _ = oracle.md_run(c["pos"], c["vel"], c["box"], 30)
+    p0, v0, _, _, _ = oracle.md_run(p1, -v1, c["box"], 30)
+    d = p0 - c["pos"]
+    d -= c["box"] * np.rint(d / c["box"])
+    assert np.abs(d).max() < 1e-8 and np.abs(-v0 - c["vel"]).max() < 1e-8
+
+
+def test_md_rebuild_policy_matches_fresh_lists():
+    """With list reuse (r_list = 2.8, rebuild every 10 steps) the trajectory equals
+    the one with a fresh list at rc every step while no pair enters rc unlisted."""
+    c = configs.lj_solid(n_cells=6)
+    a = oracle.md_run(c["pos"], c["vel"], c["box"], 20, r_list=2.8, rebuild_every=10)
+    b = oracle.md_run(c["pos"], c["vel"], c["box"], 20, r_list=2.5, rebuild_every=1)
+    assert 0.0 < a[4] < 0.3  # largest displacement between rebuilds stayed below the skin
+    assert np.abs(a[0] - b[0]).max() < 1e-10
