@@ -1,0 +1,205 @@
+/*
+ * ppmd.h -- C ABI of the B300 (sm_103a) implementation of the data-parallel
+ * hot path of Saunders, Grant & Mueller, "A Domain Specific Language for
+ * Performance Portable Molecular Dynamics Algorithms" (arXiv:1704.03329):
+ * the cell-list / neighbour-list Lennard-Jones pair loop under periodic
+ * boundaries, the Velocity Verlet particle loops that feed it, and the two
+ * per-atom structure analyses (bond order Q4/Q6 and common neighbour
+ * analysis) plus a learned structure classifier that falls back to CNA.
+ *
+ * Conventions (every entry point):
+ *  - Pointers to particle data are DEVICE pointers owned by the caller; the
+ *    library never frees or retains them past the call.  Arrays of 3-vectors
+ *    are row-major [n][3] FP64 (the paper's ParticleDat with ncomp = 3).
+ *    Scalar outputs marked "device" are device pointers too.  Arguments
+ *    marked "host" are ordinary host memory read or written during the call.
+ *  - The library owns its scratch memory (allocated on first use and grown
+ *    as needed, freed by ppmd_destroy) and runs everything on the stream
+ *    bound to the context.  Calls are asynchronous on that stream unless a
+ *    host output is requested.
+ *  - Boxes are orthorhombic [0, L0) x [0, L1) x [0, L2), periodic in x, y, z
+ *    (the paper's BoundaryTypePeriodic domain, Sec. 3.5).  Minimum-image
+ *    separations r_i - r_j are used; every cutoff must be below L/2 and the
+ *    cell grid needs at least three cells per edge (else PPMD_ERR_BOX).
+ *  - Cutoff tests are strict (r < r_cut), as in the paper's kernels.
+ *    Neighbour and cutoff decisions are exact: a single-precision test with
+ *    a double-precision re-test of every pair within a small band of the
+ *    cutoff, the double-precision test computing
+ *        d = r_i - r_j;  d = d - L * rint(d / L);  r^2 = dx*dx + dy*dy + dz*dz
+ *    with IEEE round-to-nearest operations and no fused multiply-add.
+ *  - Return value: 0 = PPMD_OK, < 0 an error, > 0 a warning.  Conditions
+ *    found by a kernel (capacity overflow, non-finite data, a bounded wait
+ *    that ran out) are latched in the context and returned by the next
+ *    synchronising call (ppmd_sync / ppmd_status, or any call with a host
+ *    output).  No C++ exception crosses this interface.
+ */
+#ifndef PPMD_H
+#define PPMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PPMD_OK 0
+#define PPMD_ERR_INVALID (-1)   /* bad argument (null pointer, negative size, ...) */
+#define PPMD_ERR_BOX (-2)       /* fewer than 3 cells per edge, or a cutoff >= L/2 */
+#define PPMD_ERR_CAPACITY (-3)  /* an output array is too small; ppmd_status reports the size needed */
+#define PPMD_ERR_NONFINITE (-4) /* NaN or infinite coordinate met */
+#define PPMD_ERR_CUDA (-5)      /* CUDA runtime error; ppmd_last_error has the text */
+#define PPMD_ERR_TIMEOUT (-6)   /* a bounded device-side wait ran out */
+#define PPMD_ERR_NOMEM (-7)     /* scratch allocation failed */
+#define PPMD_WARN_SKIN 1        /* an atom moved more than half the list skin between rebuilds */
+
+/* Structure codes written by ppmd_cna and ppmd_classify. */
+#define PPMD_OTHER 0
+#define PPMD_FCC 1
+#define PPMD_HCP 2
+#define PPMD_BCC 3
+
+typedef struct ppmd_ctx ppmd_ctx;
+typedef struct ppmd_md ppmd_md;
+
+/* Orthorhombic periodic domain (Sec. 3.5, Listing "state-example"). */
+typedef struct {
+    double L[3];
+} ppmd_box;
+
+/* Arithmetic of the pair loop.  PPMD_FP64: double precision throughout.
+ * PPMD_FP32: single-precision pair arithmetic with compensated (Kahan)
+ * per-atom sums; positions enter as exact 32-bit fixed-point box
+ * coordinates, integration and global reductions stay in double. */
+typedef enum { PPMD_FP64 = 0, PPMD_FP32 = 1 } ppmd_prec;
+
+/* Truncated Lennard-Jones, Eq. (7) and Eq. (8):
+ *   V(r) = 4 eps ((sigma/r)^12 - (sigma/r)^6 + shift)   for r < rc, else 0
+ *   F_i  = sum_j 48 eps / sigma^2 (r_i - r_j) ((sigma/r)^14 - (sigma/r)^8 / 2)
+ * shift = 0 gives the truncated, unshifted potential; shift = 0.25 is the
+ * form printed as Eq. (7).  Forces do not depend on shift. */
+typedef struct {
+    double eps, sigma, rc, shift;
+} ppmd_lj_params;
+
+/* ------------------------------------------------------------------ */
+/* Context                                                            */
+/* ------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`, bound to `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *ctx receives the
+ * handle; free it with ppmd_destroy. */
+int ppmd_create(ppmd_ctx **ctx, int device, void *cuda_stream);
+int ppmd_destroy(ppmd_ctx *ctx);
+/* Rebind the context to another stream of the same device. */
+int ppmd_set_stream(ppmd_ctx *ctx, void *cuda_stream);
+/* Wait for the stream; return (and clear) the latched status. */
+int ppmd_sync(ppmd_ctx *ctx);
+/* As ppmd_sync; *needed (host, may be NULL) receives the capacity that the
+ * last PPMD_ERR_CAPACITY asked for (atoms, cells or neighbours). */
+int ppmd_status(ppmd_ctx *ctx, int64_t *needed);
+/* Text of the last error (static storage owned by the context). */
+const char *ppmd_last_error(const ppmd_ctx *ctx);
+/* Number of kernels this context has launched so far (host counter;
+ * graph replays count every kernel node). */
+int64_t ppmd_kernel_count(const ppmd_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* Cell list, Sec. 3.5 (cell width >= cutoff, every particle in exactly one
+ * cell; the paper's cell-occupancy matrix H in compressed-row form).
+ *   n_d = floor(L_d / min_cell_width), w_d = L_d / n_d (>= min_cell_width),
+ *   x' = x - L floor(x / L) (the wrapped coordinate),
+ *   c_d = min(floor(x'_d / w_d), n_d - 1),  c = (c_z n_y + c_y) n_x + c_x.
+ * Outputs (device): cell_of[n]; cell_start[ncell + 1] (exclusive prefix of
+ * the occupancies); cell_atoms[n] (atom indices grouped by cell, increasing
+ * within a cell).  ncell_out (host, 3 ints) receives n_x, n_y, n_z.
+ * PPMD_ERR_BOX if some n_d < 3; PPMD_ERR_CAPACITY if ncell + 1 >
+ * cell_capacity (ppmd_status then reports ncell + 1). */
+int ppmd_build_cells(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double min_cell_width,
+                     int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms, int32_t ncell_out[3],
+                     int64_t cell_capacity);
+
+/* Neighbour list, Sec. 3.5 and Eq. (6): for every atom i all j != i with
+ * |r_i - r_j| < r_list (minimum image), found through the 27 cells around
+ * the cell of i.  This is the paper's neighbour matrix W (W_{m,i} = m-th
+ * neighbour of i), stored transposed as nbr[i * max_nbr + m] so that the
+ * neighbours of one atom are contiguous; the order within a row is
+ * unspecified.  nbr_count[i] (device) receives the full count even when it
+ * exceeds max_nbr (entries past max_nbr are not written, and the call
+ * latches PPMD_ERR_CAPACITY with the largest count as the needed size).
+ * The cell arrays are those of ppmd_build_cells with min_cell_width >=
+ * r_list.  needed_max_nbr (host, may be NULL): if given, the call
+ * synchronises and stores the largest count. */
+int ppmd_build_neighbours(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list,
+                          const int32_t *cell_start, const int32_t *cell_atoms, const int32_t ncell[3],
+                          int32_t *nbr, int32_t *nbr_count, int32_t max_nbr, int32_t *needed_max_nbr);
+
+/* Lennard-Jones pair loop over a neighbour list (Eqs. (7)-(8), Listing
+ * "LJ-kernel"): every listed ordered pair (i, j) with r < rc adds its force
+ * to i only (Sec. 2, no Newton's-third-law symmetry).  force[n][3] has
+ * INC_ZERO semantics (set, not accumulated).  e_atom[n] (device, may be
+ * NULL) receives 1/2 sum_j V(r_ij), e_total[1] and virial[1] (device, may
+ * be NULL) receive U = sum_i e_atom[i] and W = 1/2 sum_{i != j} r_ij . f_ij.
+ * The list must have been built with r_list >= rc. */
+int ppmd_lj_forces(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, const ppmd_lj_params *lj,
+                   const int32_t *nbr, const int32_t *nbr_count, int32_t max_nbr, ppmd_prec prec, double *force,
+                   double *e_atom, double *e_total, double *virial);
+
+/* Velocity Verlet particle loops, Algorithm 6 and Listings
+ * "position_update" / "velocity_update":
+ *   phase 1 (line 6): v += dt/(2m) F;  r += dt v;  r wrapped into the box
+ *   phase 2 (line 8): v += dt/(2m) F
+ * pos and vel are updated in place (pos is not touched in phase 2). */
+int ppmd_verlet_step(ppmd_ctx *ctx, int phase, double *pos, double *vel, const double *force, int64_t n,
+                     const ppmd_box *box, double mass, double dt);
+
+/* Kinetic energy K = sum_i m |v_i|^2 / 2 (Sec. 2, Example 1) into ke[1] (device). */
+int ppmd_kinetic_energy(ppmd_ctx *ctx, const double *vel, int64_t n, double mass, double *ke);
+
+/* ------------------------------------------------------------------ */
+/* Time stepping (Algorithm 6 driven by the list-reuse policy of Sec. 3.5,
+ * the paper's IntegratorRange), for one box or a batch of independent boxes
+ * (replicas) advanced together.  The integrator keeps its own copy of the
+ * particles, sorted by cell at every list rebuild, in device memory.      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    ppmd_lj_params lj;
+    double r_list;         /* list cutoff r_c + delta (Eq. (6)); per box min(r_list, box_r_list[b]) */
+    double mass, dt;
+    int32_t rebuild_every; /* list rebuilt when step % rebuild_every == 0 (and at set-up) */
+    int32_t max_nbr;       /* row capacity of the neighbour list */
+    int32_t prec;          /* ppmd_prec of the pair loop */
+    int32_t energy_every;  /* potential/kinetic energy recorded every k steps (0 = never) */
+} ppmd_md_params;
+
+/* nbox boxes; atoms of box b are [atom_off[b], atom_off[b+1]) of the arrays
+ * given to ppmd_md_set_state (atom_off, boxes and box_r_list are host
+ * arrays; box_r_list may be NULL: r_list for every box). */
+int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **md, int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes,
+                   const double *box_r_list, const ppmd_md_params *params);
+int ppmd_md_destroy(ppmd_md *md);
+/* Load positions and velocities (device, [n][3], caller order), wrap, sort,
+ * build the list and compute the initial forces F(r_0). */
+int ppmd_md_set_state(ppmd_md *md, const double *pos, const double *vel);
+/* Advance nsteps steps of Algorithm 6.  energies (device, may be NULL):
+ * [nsteps][2] receives (kinetic, potential) energy summed over all boxes
+ * on every step s with s % energy_every == 0 (other rows untouched).
+ * use_graph != 0 replays CUDA graphs of whole rebuild periods. */
+int ppmd_md_run(ppmd_md *md, int32_t nsteps, double *energies, int use_graph);
+/* Copy positions, velocities and forces back in caller order (device,
+ * [n][3] each; any may be NULL). */
+int ppmd_md_get_state(ppmd_md *md, double *pos, double *vel, double *force);
+/* Counters (host, any may be NULL): steps taken, list rebuilds, and the
+ * largest displacement since a rebuild seen so far.  Synchronises; returns
+ * PPMD_WARN_SKIN when that displacement exceeded half the list skin. */
+int ppmd_md_info(ppmd_md *md, int64_t *steps, int64_t *rebuilds, double *max_disp);
+/* Recompute the forces of the current state (the pair loop alone, line 7 of
+ * Algorithm 6), e.g. to time it; the state is otherwise unchanged. */
+int ppmd_md_forces(ppmd_md *md);
+/* Current neighbour list (host outputs, may be NULL): total listed pairs and
+ * the largest row.  Synchronises. */
+int ppmd_md_list_stats(ppmd_md *md, int64_t *pairs, int32_t *max_row);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPMD_H */

@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libppmd.so (include/ppmd.h).
+
+Only argument marshalling lives here: every step of the computation runs in
+the library's CUDA kernels.  Tensors are PyTorch CUDA tensors (device memory
+and streams); there is no CPU fallback -- importing this module fails if the
+compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libppmd.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1704_03329_b300.build` "
+                      "(there is no CPU fallback)")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, ERR_INVALID, ERR_BOX, ERR_CAPACITY, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6, -7
+WARN_SKIN = 1
+FP64, FP32 = 0, 1
+OTHER, FCC, HCP, BCC = 0, 1, 2, 3
+_NAMES = {0: "PPMD_OK", -1: "PPMD_ERR_INVALID", -2: "PPMD_ERR_BOX", -3: "PPMD_ERR_CAPACITY",
+          -4: "PPMD_ERR_NONFINITE", -5: "PPMD_ERR_CUDA", -6: "PPMD_ERR_TIMEOUT", -7: "PPMD_ERR_NOMEM",
+          1: "PPMD_WARN_SKIN"}
+
+
+class Box(C.Structure):
+    _fields_ = [("L", C.c_double * 3)]
+
+
+class LJParams(C.Structure):
+    _fields_ = [("eps", C.c_double), ("sigma", C.c_double), ("rc", C.c_double), ("shift", C.c_double)]
+
+
+class MDParams(C.Structure):
+    _fields_ = [("lj", LJParams), ("r_list", C.c_double), ("mass", C.c_double), ("dt", C.c_double),
+                ("rebuild_every", C.c_int32), ("max_nbr", C.c_int32), ("prec", C.c_int32),
+                ("energy_every", C.c_int32)]
+
+
+class PPMDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_P, _I64, _I32, _D, _I = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_int
+_SIGS = {
+    "ppmd_create": (_I, [C.POINTER(_P), _I, _P]),
+    "ppmd_destroy": (_I, [_P]),
+    "ppmd_set_stream": (_I, [_P, _P]),
+    "ppmd_sync": (_I, [_P]),
+    "ppmd_status": (_I, [_P, C.POINTER(_I64)]),
+    "ppmd_last_error": (C.c_char_p, [_P]),
+    "ppmd_kernel_count": (_I64, [_P]),
+    "ppmd_build_cells": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, _P, C.POINTER(_I32), _I64]),
+    "ppmd_build_neighbours": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, C.POINTER(_I32), _P, _P, _I32,
+                                   C.POINTER(_I32)]),
+    "ppmd_lj_forces": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _P, _P, _I32, _I, _P, _P, _P, _P]),
+    "ppmd_verlet_step": (_I, [_P, _I, _P, _P, _P, _I64, C.POINTER(Box), _D, _D]),
+    "ppmd_kinetic_energy": (_I, [_P, _P, _I64, _D, _P]),
+    "ppmd_md_create": (_I, [_P, C.POINTER(_P), _I64, _P, _P, _P, C.POINTER(MDParams)]),
+    "ppmd_md_destroy": (_I, [_P]),
+    "ppmd_md_set_state": (_I, [_P, _P, _P]),
+    "ppmd_md_run": (_I, [_P, _I32, _P, _I]),
+    "ppmd_md_get_state": (_I, [_P, _P, _P, _P]),
+    "ppmd_md_info": (_I, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
+    "ppmd_md_forces": (_I, [_P]),
+    "ppmd_md_list_stats": (_I, [_P, C.POINTER(_I64), C.POINTER(_I32)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _box(L):
+    b = Box()
+    for d in range(3):
+        b.L[d] = float(L[d])
+    return b
+
+
+class Context:
+    """A library context bound to a CUDA device and stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch.cuda.init()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.device = device
+        h = _P()
+        rc = _lib.ppmd_create(C.byref(h), int(device), C.c_void_p(stream.cuda_stream))
+        if rc != OK:
+            raise PPMDError(rc, "ppmd_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ppmd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc, allow_warn=True):
+        if rc < 0 or (rc > 0 and not allow_warn):
+            raise PPMDError(rc, _lib.ppmd_last_error(self.h).decode(errors="replace"))
+        return rc
+
+    def sync(self):
+        return self.check(_lib.ppmd_sync(self.h))
+
+    def status(self):
+        nd = _I64()
+        rc = _lib.ppmd_status(self.h, C.byref(nd))
+        return rc, nd.value
+
+    def kernel_count(self) -> int:
+        return int(_lib.ppmd_kernel_count(self.h))
+
+    def last_error(self) -> str:
+        return _lib.ppmd_last_error(self.h).decode(errors="replace")
+
+
+def ppmd_build_cells(ctx: Context, pos, box, min_cell_width, cell_capacity=None):
+    """Cell list; returns (ncell[3] list, cell_of, cell_start, cell_atoms) as int32 CUDA tensors."""
+    n = pos.shape[0]
+    dev = pos.device
+    ncell = [max(1, int(float(box[d]) // float(min_cell_width))) for d in range(3)]
+    cap = cell_capacity if cell_capacity is not None else ncell[0] * ncell[1] * ncell[2] + 1
+    cell_of = torch.empty(n, dtype=torch.int32, device=dev)
+    cell_start = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    cell_atoms = torch.empty(n, dtype=torch.int32, device=dev)
+    nc = (_I32 * 3)()
+    b = _box(box)
+    rc = _lib.ppmd_build_cells(ctx.h, _ptr(pos), n, C.byref(b), float(min_cell_width), _ptr(cell_of), _ptr(cell_start),
+                               _ptr(cell_atoms), nc, int(cap))
+    ctx.check(rc)
+    nc = [nc[0], nc[1], nc[2]]
+    return nc, cell_of, cell_start[: nc[0] * nc[1] * nc[2] + 1], cell_atoms
+
+
+def ppmd_build_neighbours(ctx: Context, pos, box, r_list, cell_start, cell_atoms, ncell, max_nbr, want_needed=False):
+    """Neighbour list rows nbr[n, max_nbr] (int32) and counts nbr_count[n]."""
+    n = pos.shape[0]
+    nbr = torch.empty((n, max_nbr), dtype=torch.int32, device=pos.device)
+    cnt = torch.empty(n, dtype=torch.int32, device=pos.device)
+    nc = (_I32 * 3)(*[int(x) for x in ncell])
+    needed = _I32(0)
+    b = _box(box)
+    rc = _lib.ppmd_build_neighbours(ctx.h, _ptr(pos), n, C.byref(b), float(r_list), _ptr(cell_start), _ptr(cell_atoms),
+                                    nc, _ptr(nbr), _ptr(cnt), int(max_nbr),
+                                    C.byref(needed) if want_needed else None)
+    ctx.check(rc)
+    if want_needed:
+        return nbr, cnt, needed.value
+    return nbr, cnt
+
+
+def ppmd_lj_forces(ctx: Context, pos, box, nbr, nbr_count, rc=2.5, eps=1.0, sigma=1.0, shift=0.0, prec=FP32,
+                   want_energy=True):
+    """Forces [n,3] f64, per-atom energies [n] f64, and device scalars (U, W)."""
+    n = pos.shape[0]
+    dev = pos.device
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    e = torch.empty(n, dtype=torch.float64, device=dev) if want_energy else None
+    tot = torch.zeros(2, dtype=torch.float64, device=dev)
+    p = LJParams(eps, sigma, rc, shift)
+    b = _box(box)
+    max_nbr = nbr.shape[1] if nbr.dim() == 2 else 0
+    code = _lib.ppmd_lj_forces(ctx.h, _ptr(pos), n, C.byref(b), C.byref(p), _ptr(nbr), _ptr(nbr_count), int(max_nbr),
+                               int(prec), _ptr(F), _ptr(e) if e is not None else None, _ptr(tot[0:1]),
+                               C.c_void_p(tot.data_ptr() + 8))
+    ctx.check(code)
+    return F, e, tot
+
+
+def ppmd_verlet_step(ctx: Context, phase, pos, vel, force, box, mass=1.0, dt=0.005):
+    b = _box(box)
+    ctx.check(_lib.ppmd_verlet_step(ctx.h, int(phase), _ptr(pos), _ptr(vel), _ptr(force), vel.shape[0], C.byref(b),
+                                    float(mass), float(dt)))
+
+
+def ppmd_kinetic_energy(ctx: Context, vel, mass=1.0):
+    ke = torch.zeros(1, dtype=torch.float64, device=vel.device)
+    ctx.check(_lib.ppmd_kinetic_energy(ctx.h, _ptr(vel), vel.shape[0], float(mass), _ptr(ke)))
+    return ke
+
+
+class MD:
+    """Time stepping of one box or a batch of boxes (ppmd_md_*)."""
+
+    def __init__(self, ctx: Context, atom_off, boxes, r_list=2.8, rc=2.5, eps=1.0, sigma=1.0, shift=0.0, mass=1.0,
+                 dt=0.005, rebuild_every=10, max_nbr=128, prec=FP32, energy_every=0, box_r_list=None):
+        self.ctx = ctx
+        off = (C.c_int64 * len(atom_off))(*[int(x) for x in atom_off])
+        nbox = len(atom_off) - 1
+        bx = (Box * nbox)()
+        for b in range(nbox):
+            for d in range(3):
+                bx[b].L[d] = float(boxes[b][d])
+        brl = None
+        if box_r_list is not None:
+            brl = (C.c_double * nbox)(*[float(x) for x in box_r_list])
+        p = MDParams(LJParams(eps, sigma, rc, shift), r_list, mass, dt, rebuild_every, max_nbr, prec, energy_every)
+        h = _P()
+        code = _lib.ppmd_md_create(ctx.h, C.byref(h), nbox, C.cast(off, _P), C.cast(bx, _P),
+                                   C.cast(brl, _P) if brl is not None else None, C.byref(p))
+        ctx.check(code)
+        self.h = h
+        self.n = int(atom_off[-1])
+        self.params = p
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ppmd_md_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, pos, vel):
+        self.ctx.check(_lib.ppmd_md_set_state(self.h, _ptr(pos), _ptr(vel)))
+
+    def run(self, nsteps, energies=None, use_graph=True):
+        self.ctx.check(_lib.ppmd_md_run(self.h, int(nsteps), _ptr(energies) if energies is not None else None,
+                                        1 if use_graph else 0))
+
+    def get_state(self, pos=None, vel=None, force=None):
+        self.ctx.check(_lib.ppmd_md_get_state(self.h, _ptr(pos) if pos is not None else None,
+                                              _ptr(vel) if vel is not None else None,
+                                              _ptr(force) if force is not None else None))
+
+    def forces(self):
+        self.ctx.check(_lib.ppmd_md_forces(self.h))
+
+    def list_stats(self):
+        pairs, mx = _I64(), _I32()
+        self.ctx.check(_lib.ppmd_md_list_stats(self.h, C.byref(pairs), C.byref(mx)))
+        return pairs.value, mx.value
+
+    def info(self):
+        s, r, d = _I64(), _I64(), _D()
+        code = _lib.ppmd_md_info(self.h, C.byref(s), C.byref(r), C.byref(d))
+        self.ctx.check(code)
+        return dict(steps=s.value, rebuilds=r.value, max_disp=d.value, status=code)

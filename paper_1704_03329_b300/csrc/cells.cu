@@ -1,0 +1,110 @@
+// Cell binning by counting sort (Sec. 3.5): histogram -> exclusive scan ->
+// scatter -> per-cell ordering by atom index.
+#include "cells.cuh"
+
+namespace ppmd {
+
+template <bool EXACT>
+__global__ void k_bin(const double *__restrict__ pos, int64_t n, SegTable st, const int32_t *__restrict__ seg_of,
+                      int32_t *__restrict__ cell_of, int32_t *__restrict__ count, int32_t *status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t sid = seg_of ? seg_of[i] : 0;
+    const Seg &S = seg_ref(st, sid);
+    int32_t c[3];
+    bool bad = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double x = pos[3 * i + d];
+        if (!isfinite(x)) {
+            bad = true;
+            x = 0.0;
+        }
+        int32_t cd;
+        if (EXACT) {
+            double xw = wrap_exact(x, S.L[d]);
+            cd = (int32_t)floor(__ddiv_rn(xw, S.w[d]));
+        } else {
+            cd = (int32_t)floor(x * S.inv_w[d]);
+            if (x < 0.0 || x >= S.L[d]) cd = (int32_t)floor(wrap_exact(x, S.L[d]) * S.inv_w[d]);
+        }
+        cd = cd < 0 ? 0 : (cd > S.nc[d] - 1 ? S.nc[d] - 1 : cd);
+        c[d] = cd;
+    }
+    if (bad) latch_status(status, PPMD_ERR_NONFINITE);
+    int32_t cell = S.cell0 + (c[2] * S.nc[1] + c[1]) * S.nc[0] + c[0];
+    cell_of[i] = cell;
+    atomicAdd(&count[cell], 1);
+}
+
+__global__ void k_scatter(int64_t n, const int32_t *__restrict__ cell_of, const int32_t *__restrict__ cell_start,
+                          int32_t *__restrict__ cursor, int32_t *__restrict__ cell_atoms) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t c = cell_of[i];
+    int32_t slot = atomicAdd(&cursor[c], 1);
+    cell_atoms[cell_start[c] + slot] = (int32_t)i;
+}
+
+// Order every cell's atoms by index (insertion sort; cells are small).
+__global__ void k_sort_cells(int64_t ncell, const int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_atoms) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int32_t a = cell_start[c], b = cell_start[c + 1];
+    for (int32_t k = a + 1; k < b; ++k) {
+        int32_t v = cell_atoms[k];
+        int32_t m = k - 1;
+        while (m >= a && cell_atoms[m] > v) {
+            cell_atoms[m + 1] = cell_atoms[m];
+            --m;
+        }
+        cell_atoms[m + 1] = v;
+    }
+}
+
+int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, const int32_t *seg_of, int64_t ncell,
+              bool exact, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms) {
+    cudaStream_t s = ctx->stream;
+    PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cell_start, 0, sizeof(int32_t) * (size_t)(ncell + 1), s), "memset"));
+    if (n > 0) {
+        if (exact)
+            PPMD_LAUNCH(ctx, k_bin<true>, div_up(n, 256), 256, 0, pos, n, st, seg_of, cell_of, cell_start, ctx->d_status);
+        else
+            PPMD_LAUNCH(ctx, k_bin<false>, div_up(n, 256), 256, 0, pos, n, st, seg_of, cell_of, cell_start, ctx->d_status);
+    }
+    PPMD_TRY(exclusive_scan(ctx, cell_start, cell_start, ncell));
+    if (n > 0) {
+        int32_t *cursor = (int32_t *)scratch(ctx, S_COUNT, sizeof(int32_t) * (size_t)ncell);
+        if (!cursor) return PPMD_ERR_NOMEM;
+        PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)ncell, s), "memset"));
+        PPMD_LAUNCH(ctx, k_scatter, div_up(n, 256), 256, 0, n, cell_of, cell_start, cursor, cell_atoms);
+        PPMD_LAUNCH(ctx, k_sort_cells, div_up(ncell, 128), 128, 0, ncell, cell_start, cell_atoms);
+    }
+    return check_launch(ctx, "bin_atoms");
+}
+
+}  // namespace ppmd
+
+using namespace ppmd;
+
+extern "C" int ppmd_build_cells(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double min_cell_width,
+                                int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms, int32_t ncell_out[3],
+                                int64_t cell_capacity) {
+    if (!ctx || !box || n < 0 || !(min_cell_width > 0)) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_build_cells: bad argument");
+    if (n > 0 && (!pos || !cell_of || !cell_atoms)) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_build_cells: null array");
+    if (!cell_start) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_build_cells: null cell_start");
+    if (n >= (int64_t)1 << 31) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_build_cells: n too large");
+    cudaSetDevice(ctx->device);
+    SegTable st;
+    st.d = nullptr;
+    st.nseg = 1;
+    PPMD_TRY(make_seg(ctx, st.one, box->L, min_cell_width, 0.0));
+    int64_t ncell = (int64_t)st.one.nc[0] * st.one.nc[1] * st.one.nc[2];
+    if (ncell_out)
+        for (int d = 0; d < 3; ++d) ncell_out[d] = st.one.nc[d];
+    if (ncell + 1 > cell_capacity) {
+        ctx->host_needed = ncell + 1;
+        return set_error(ctx, PPMD_ERR_CAPACITY, "cell_start needs %lld entries", (long long)(ncell + 1));
+    }
+    return bin_atoms(ctx, pos, n, st, nullptr, ncell, true, cell_of, cell_start, cell_atoms);
+}

@@ -1,0 +1,15 @@
+// Cell binning shared by the cell-list entry point, the integrator and the
+// analysis pipeline.
+#pragma once
+#include "common.cuh"
+
+namespace ppmd {
+// Bin n atoms into the global cell index space of the segment table (ncell
+// cells in total).  exact = true evaluates the cell coordinate with the
+// same IEEE operations as the documented formula (division by the cell
+// edge); exact = false multiplies by the reciprocal (positions already in
+// the box).  Writes cell_of[n], cell_start[ncell+1], cell_atoms[n] (atoms
+// of a cell in increasing index).
+int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, const int32_t *seg_of, int64_t ncell,
+              bool exact, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms);
+}  // namespace ppmd

@@ -1,0 +1,417 @@
+// Time stepping: Algorithm 6 with the list-reuse policy of Sec. 3.5 and
+// Eq. (6) (the paper's IntegratorRange), for one box or a batch of
+// independent boxes.  Particles are kept in device memory sorted by cell;
+// every list rebuild re-sorts them (the periodic reordering the paper's
+// conclusions call for), and whole rebuild periods are replayed as CUDA
+// graphs.
+#include <algorithm>
+#include <math.h>
+
+#include "cells.cuh"
+#include "lj.cuh"
+#include "neighbours.cuh"
+#include "verlet.cuh"
+
+using namespace ppmd;
+
+struct ppmd_md {
+    ppmd_ctx *ctx = nullptr;
+    int64_t n = 0, nbox = 0, ncell = 0;
+    ppmd_md_params p{};
+    LJConst c{};
+    double h = 0, half_m = 0, skin_half = 0;
+    std::vector<Seg> segs;
+    Seg *d_segs = nullptr;
+    SegTable st{};
+    int64_t *d_atom_off = nullptr;
+    // particle state in cell order
+    double *pos = nullptr, *vel = nullptr, *f64 = nullptr;
+    float4 *f4 = nullptr;
+    int4 *xq = nullptr, *xq_ref = nullptr;
+    int32_t *orig = nullptr, *seg_of = nullptr, *cell_of = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
+    int32_t *nbr = nullptr, *cnt = nullptr;
+    // reorder temporaries
+    double *pos_t = nullptr, *vel_t = nullptr;
+    int4 *xq_t = nullptr;
+    int32_t *orig_t = nullptr, *cell_t = nullptr, *seg_t = nullptr;
+    // reductions
+    double *part_f = nullptr, *part_k = nullptr, *red = nullptr, *ebuf = nullptr;
+    unsigned int *max_disp_bits = nullptr;
+    int64_t step = 0, rebuilds = 0;
+    bool ready = false;
+    // graphs
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t graph_steps = 0;
+    int64_t graph_kernels = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+template <class T>
+int md_alloc(ppmd_md *m, T **p, size_t count) {
+    void *q = nullptr;
+    if (cudaMalloc(&q, sizeof(T) * (count > 0 ? count : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(m->ctx, PPMD_ERR_NOMEM, "integrator allocation of %zu bytes failed", sizeof(T) * count);
+    }
+    m->allocs.push_back(q);
+    *p = (T *)q;
+    return PPMD_OK;
+}
+
+__global__ void k_init_state(int64_t n, double *pos, const int64_t *atom_off, int64_t nbox, SegTable st, int4 *xq,
+                             int32_t *orig, int32_t *seg_of, int32_t *status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // box of atom i: the last b with atom_off[b] <= i
+    int64_t lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (atom_off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const int32_t sid = (int32_t)lo;
+    const Seg &S = seg_ref(st, sid);
+    uint32_t q[3];
+    bool bad = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double x = pos[3 * i + d];
+        if (!isfinite(x)) {
+            bad = true;
+            x = 0.0;
+        }
+        x = wrap_exact(x, S.L[d]);
+        pos[3 * i + d] = x;
+        q[d] = to_fixed(x, S.fxs[d]);
+    }
+    if (bad) latch_status(status, PPMD_ERR_NONFINITE);
+    xq[i] = make_int4((int)q[0], (int)q[1], (int)q[2], sid);
+    orig[i] = (int32_t)i;
+    seg_of[i] = sid;
+}
+
+__global__ void k_gather_i32(int64_t n, const int32_t *perm, const int32_t *in, int32_t *out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = in[perm[k]];
+}
+
+__global__ void k_energy_row(const double *red, double *row) {
+    // red[0] = kinetic, red[1] = potential (U), red[2] = virial
+    row[0] = red[0];
+    row[1] = red[1];
+}
+
+int rebuild(ppmd_md *m) {
+    ppmd_ctx *ctx = m->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = m->n;
+    PPMD_TRY(bin_atoms(ctx, m->pos, n, m->st, m->seg_of, m->ncell, false, m->cell_of, m->cell_start, m->cell_atoms));
+    PPMD_TRY(gather_sorted(ctx, n, m->cell_atoms, m->pos, m->vel, m->xq, m->orig, m->cell_of, m->pos_t, m->vel_t, m->xq_t,
+                           m->orig_t, m->cell_t));
+    if (n > 0) PPMD_LAUNCH(ctx, k_gather_i32, div_up(n, 256), 256, 0, n, m->cell_atoms, m->seg_of, m->seg_t);
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, m->pos_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, m->vel_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq_ref, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->cell_of, m->cell_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    PPMD_TRY(build_list(ctx, n, m->xq, m->pos, m->st, m->cell_of, m->cell_start, nullptr, m->nbr, m->cnt, m->p.max_nbr));
+    return PPMD_OK;
+}
+
+int forces(ppmd_md *m, bool energy) {
+    return lj_launch(m->ctx, m->n, m->xq, m->pos, m->st, m->c, m->nbr, m->cnt, m->p.max_nbr, m->p.prec,
+                     m->p.prec == PPMD_FP32 ? m->f4 : nullptr, m->p.prec == PPMD_FP32 ? nullptr : m->f64, nullptr,
+                     energy ? m->part_f : nullptr);
+}
+
+// One step of Algorithm 6.  erow: device row receiving (KE, PE) on energy steps.
+int one_step(ppmd_md *m, int64_t s, double *erow) {
+    ppmd_ctx *ctx = m->ctx;
+    const bool f32 = m->p.prec == PPMD_FP32;
+    const bool energy = m->p.energy_every > 0 && (s % m->p.energy_every) == 0 && erow;
+    PPMD_TRY(md_kick_drift(ctx, m->n, m->pos, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->xq, m->xq_ref, m->st,
+                           m->h, m->p.dt, m->max_disp_bits));
+    if (m->p.rebuild_every > 0 && s % m->p.rebuild_every == 0) {
+        PPMD_TRY(rebuild(m));
+    }
+    PPMD_TRY(forces(m, energy));
+    PPMD_TRY(md_kick(ctx, m->n, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->h, m->half_m,
+                     energy ? m->part_k : nullptr));
+    if (energy) {
+        PPMD_TRY(reduce_partials(ctx, m->part_k, kick_blocks(m->n), 1, m->red));
+        PPMD_TRY(reduce_partials(ctx, m->part_f, lj_blocks(m->n), 2, m->red + 1));
+        PPMD_LAUNCH(ctx, k_energy_row, 1, 1, 0, m->red, erow);
+    }
+    return check_launch(ctx, "one_step");
+}
+
+}  // namespace
+
+extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes,
+                              const double *box_r_list, const ppmd_md_params *params) {
+    if (!ctx || !out || nbox < 1 || !atom_off || !boxes || !params) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_create: bad argument");
+    *out = nullptr;
+    const ppmd_md_params &p = *params;
+    if (!(p.r_list >= p.lj.rc) || !(p.lj.rc > 0) || !(p.mass > 0) || !(p.dt > 0) || p.max_nbr < 1 || p.rebuild_every < 1 ||
+        (p.prec != PPMD_FP32 && p.prec != PPMD_FP64) || p.energy_every < 0)
+        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_create: bad parameters");
+    if (atom_off[0] != 0) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_create: atom_off[0] must be 0");
+    for (int64_t b = 0; b < nbox; ++b)
+        if (atom_off[b + 1] < atom_off[b]) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_create: atom_off not increasing");
+    if (atom_off[nbox] >= ((int64_t)1 << 31)) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_create: too many atoms");
+    cudaSetDevice(ctx->device);
+    ppmd_md *m = new ppmd_md();
+    m->ctx = ctx;
+    m->n = atom_off[nbox];
+    m->nbox = nbox;
+    m->p = p;
+    m->h = p.dt / (2.0 * p.mass);
+    m->half_m = 0.5 * p.mass;
+    m->segs.resize(nbox);
+    double Lmax = 0;
+    int64_t cell0 = 0;
+    double min_skin = 1e300;
+    for (int64_t b = 0; b < nbox; ++b) {
+        double rl = p.r_list;
+        if (box_r_list && box_r_list[b] < rl) rl = box_r_list[b];
+        if (!(rl >= p.lj.rc)) {
+            ppmd_md_destroy(m);
+            return set_error(ctx, PPMD_ERR_INVALID, "box %lld: list cutoff %g below rc", (long long)b, rl);
+        }
+        int rc = make_seg(ctx, m->segs[b], boxes[b].L, rl, rl);
+        if (rc != PPMD_OK) {
+            ppmd_md_destroy(m);
+            return rc;
+        }
+        Seg &S = m->segs[b];
+        S.cell0 = (int32_t)cell0;
+        S.atom0 = atom_off[b];
+        S.atom1 = atom_off[b + 1];
+        cell0 += (int64_t)S.nc[0] * S.nc[1] * S.nc[2];
+        for (int d = 0; d < 3; ++d) Lmax = fmax(Lmax, boxes[b].L[d]);
+        min_skin = fmin(min_skin, rl - p.lj.rc);
+        if (cell0 >= ((int64_t)1 << 31)) {
+            ppmd_md_destroy(m);
+            return set_error(ctx, PPMD_ERR_BOX, "too many cells");
+        }
+    }
+    m->ncell = cell0;
+    m->skin_half = 0.5 * min_skin;
+    m->c = make_ljconst(p.lj, Lmax);
+    const int64_t n = m->n;
+    int rc = PPMD_OK;
+    if (nbox > 1) {
+        rc = md_alloc(m, &m->d_segs, nbox);
+        if (rc == PPMD_OK) rc = cuda_check(ctx, cudaMemcpy(m->d_segs, m->segs.data(), sizeof(Seg) * nbox, cudaMemcpyHostToDevice), "copy");
+        m->st.d = m->d_segs;
+        m->st.nseg = (int32_t)nbox;
+    } else {
+        m->st.d = nullptr;
+        m->st.one = m->segs[0];
+        m->st.nseg = 1;
+    }
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->d_atom_off, nbox + 1);
+    if (rc == PPMD_OK)
+        rc = cuda_check(ctx, cudaMemcpy(m->d_atom_off, atom_off, sizeof(int64_t) * (nbox + 1), cudaMemcpyHostToDevice), "copy");
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->pos, 3 * n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->vel, 3 * n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->pos_t, 3 * n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->vel_t, 3 * n);
+    if (rc == PPMD_OK) {
+        if (p.prec == PPMD_FP32) rc = md_alloc(m, &m->f4, n);
+        else rc = md_alloc(m, &m->f64, 3 * n);
+    }
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->xq, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->xq_ref, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->xq_t, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->orig, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->orig_t, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->seg_of, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->seg_t, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_of, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_t, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_atoms, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_start, m->ncell + 1);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->nbr, (size_t)n * p.max_nbr);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->part_f, 2 * lj_blocks(n) + 2);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->red, 4);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->ebuf, 2 * 1024);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->max_disp_bits, 1);
+    if (rc == PPMD_OK) rc = cuda_check(ctx, cudaMemset(m->max_disp_bits, 0, sizeof(unsigned int)), "memset");
+    if (rc != PPMD_OK) {
+        ppmd_md_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_destroy(ppmd_md *m) {
+    if (!m) return PPMD_OK;
+    if (m->ctx) {
+        cudaSetDevice(m->ctx->device);
+        cudaStreamSynchronize(m->ctx->stream);
+    }
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    for (void *q : m->allocs) cudaFree(q);
+    delete m;
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_set_state(ppmd_md *m, const double *pos, const double *vel) {
+    if (!m || (m->n > 0 && (!pos || !vel))) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    const int64_t n = m->n;
+    cudaStream_t s = ctx->stream;
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    if (n > 0)
+        PPMD_LAUNCH(ctx, k_init_state, div_up(n, 256), 256, 0, n, m->pos, m->d_atom_off, m->nbox, m->st, m->xq, m->orig,
+                    m->seg_of, ctx->d_status);
+    PPMD_TRY(rebuild(m));
+    PPMD_TRY(forces(m, false));
+    m->step = 0;
+    m->rebuilds = 1;
+    m->ready = true;
+    return check_launch(ctx, "ppmd_md_set_state");
+}
+
+extern "C" int ppmd_md_run(ppmd_md *m, int32_t nsteps, double *energies, int use_graph) {
+    if (!m || nsteps < 0) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    if (!m->ready) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_run: state not set");
+    cudaSetDevice(ctx->device);
+    const int32_t P = m->p.rebuild_every;
+    const int32_t E = m->p.energy_every;
+    int32_t unit = P * std::max(1, 10 / P);
+    const bool graph_ok = use_graph && unit <= 1024 && (E == 0 || unit % E == 0);
+    int32_t done = 0;
+    while (done < nsteps) {
+        const int64_t s0 = m->step;
+        if (graph_ok && s0 % unit == 0 && nsteps - done >= unit) {
+            if (!m->exec) {
+                // capture one unit of whole rebuild periods on a private stream
+                if (!m->cap_stream)
+                    PPMD_TRY(cuda_check(ctx, cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking), "stream"));
+                PPMD_TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
+                cudaStream_t user = ctx->stream;
+                ctx->stream = m->cap_stream;
+                int64_t k0 = ctx->launches;
+                cudaGraph_t g = nullptr;
+                int rc = cuda_check(ctx, cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
+                for (int32_t k = 1; rc == PPMD_OK && k <= unit; ++k) rc = one_step(m, k, m->ebuf + 2 * (k - 1));
+                cudaError_t e = cudaStreamEndCapture(m->cap_stream, &g);
+                ctx->stream = user;
+                if (rc != PPMD_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return rc;
+                }
+                PPMD_TRY(cuda_check(ctx, e, "end capture"));
+                e = cudaGraphInstantiate(&m->exec, g, 0);
+                cudaGraphDestroy(g);
+                PPMD_TRY(cuda_check(ctx, e, "graph instantiate"));
+                m->graph_steps = unit;
+                m->graph_kernels = ctx->launches - k0;
+                ctx->launches = k0;
+            }
+            PPMD_TRY(cuda_check(ctx, cudaGraphLaunch(m->exec, ctx->stream), "graph launch"));
+            ctx->launches += m->graph_kernels;
+            if (energies && E > 0) {
+                for (int32_t k = 1; k <= unit; ++k)
+                    if ((k % E) == 0)
+                        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(energies + 2 * (done + k - 1), m->ebuf + 2 * (k - 1),
+                                                                 2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
+                                            "copy"));
+            }
+            m->rebuilds += unit / P;
+            m->step += unit;
+            done += unit;
+        } else {
+            const int64_t s = s0 + 1;
+            PPMD_TRY(one_step(m, s, energies ? energies + 2 * done : nullptr));
+            if (s % P == 0) m->rebuilds += 1;
+            m->step = s;
+            done += 1;
+        }
+    }
+    return check_launch(ctx, "ppmd_md_run");
+}
+
+extern "C" int ppmd_md_get_state(ppmd_md *m, double *pos, double *vel, double *force) {
+    if (!m) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    if (pos) PPMD_TRY(scatter_vec3(ctx, m->n, m->orig, m->pos, pos));
+    if (vel) PPMD_TRY(scatter_vec3(ctx, m->n, m->orig, m->vel, vel));
+    if (force) {
+        if (m->p.prec == PPMD_FP32) PPMD_TRY(scatter_f4(ctx, m->n, m->orig, m->f4, force));
+        else PPMD_TRY(scatter_vec3(ctx, m->n, m->orig, m->f64, force));
+    }
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_info(ppmd_md *m, int64_t *steps, int64_t *rebuilds, double *max_disp) {
+    if (!m) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    unsigned int bits = 0;
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(&bits, m->max_disp_bits, 4, cudaMemcpyDeviceToHost, ctx->stream), "copy"));
+    int rc = ppmd_sync(ctx);
+    float d2;
+    memcpy(&d2, &bits, 4);
+    double md = sqrt((double)d2);
+    if (steps) *steps = m->step;
+    if (rebuilds) *rebuilds = m->rebuilds;
+    if (max_disp) *max_disp = md;
+    if (rc == PPMD_OK && md > m->skin_half) rc = PPMD_WARN_SKIN;
+    return rc;
+}
+
+namespace {
+__global__ void k_list_stats(const int32_t *cnt, int64_t n, unsigned long long *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t v = i < n ? cnt[i] : 0;
+    unsigned long long s = (unsigned long long)v;
+    int32_t mx = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], s);
+        atomicMax(&out[1], (unsigned long long)mx);
+    }
+}
+}  // namespace
+
+extern "C" int ppmd_md_forces(ppmd_md *m) {
+    if (!m || !m->ready) return PPMD_ERR_INVALID;
+    cudaSetDevice(m->ctx->device);
+    return forces(m, false);
+}
+
+extern "C" int ppmd_md_list_stats(ppmd_md *m, int64_t *pairs, int32_t *max_row) {
+    if (!m || !m->ready) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    unsigned long long *d = (unsigned long long *)scratch(ctx, S_TMP1, 16);
+    if (!d) return PPMD_ERR_NOMEM;
+    PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(d, 0, 16, ctx->stream), "memset"));
+    if (m->n > 0) PPMD_LAUNCH(ctx, k_list_stats, div_up(m->n, 256), 256, 0, m->cnt, m->n, d);
+    unsigned long long h[2] = {0, 0};
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, ctx->stream), "copy"));
+    int rc = ppmd_sync(ctx);
+    if (pairs) *pairs = (int64_t)h[0];
+    if (max_row) *max_row = (int32_t)h[1];
+    return rc;
+}

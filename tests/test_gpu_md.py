@@ -1,0 +1,253 @@
+"""GPU parity of the cell list, neighbour list, Lennard-Jones pair loop,
+Velocity Verlet and the time-stepping driver against the FP64 oracle.
+
+Tolerances (floating point, relative to the oracle):
+  FP64 forces   max_i |dF_i| / rms|F| <= 1e-12, |dU| / |U| <= 1e-12
+  FP32 forces   max_i |dF_i| / rms|F| <= 1e-5,  max_i |de_i| <= 1e-6 mean|e_i|
+Integer results (cells, neighbour sets) are compared bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import configs
+from synth.configs import random_box
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1704_03329_b300 import lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    return L.Context(0)
+
+
+def cu(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def rows_as_sets(nbr, cnt):
+    nbr = nbr.cpu().numpy()
+    cnt = cnt.cpu().numpy()
+    return [np.sort(nbr[i, :cnt[i]]) for i in range(len(cnt))]
+
+
+def force_err(F, Fo):
+    rms = np.sqrt((Fo ** 2).sum(1).mean())
+    return np.sqrt(((F - Fo) ** 2).sum(1)).max() / rms
+
+
+CASES = {
+    "fcc10_r2.8": lambda: (configs.lj_solid(n_cells=10), 2.8),
+    "sc10_r2.5": lambda: (configs.lj_small(), 2.5),
+    "random_ragged": lambda: (dict(zip(("pos", "box"), random_box(997, [12.1, 11.3, 13.7], 3, cutoffs=(2.5, 2.8),
+                                                                   margin=1e-6, min_dist=0.7))), 2.8),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_cells_bit_exact(L, ctx, case):
+    c, r = CASES[case]()
+    pos, box = c["pos"], c["box"]
+    nc_o, cell_of_o, start_o, atoms_o = oracle.cells(pos, box, r)
+    nc, cell_of, start, atoms = L.ppmd_build_cells(ctx, cu(pos), box, r)
+    ctx.sync()
+    assert list(nc) == list(nc_o)
+    assert np.array_equal(cell_of.cpu().numpy(), cell_of_o)
+    assert np.array_equal(start.cpu().numpy(), start_o)
+    assert np.array_equal(atoms.cpu().numpy(), atoms_o)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_neighbour_sets_bit_exact(L, ctx, case):
+    c, r = CASES[case]()
+    pos, box = c["pos"], c["box"]
+    offs, nbr_o = oracle.neighbours_cells(pos, box, r)
+    p = cu(pos)
+    nc, cell_of, start, atoms = L.ppmd_build_cells(ctx, p, box, r)
+    nbr, cnt, needed = L.ppmd_build_neighbours(ctx, p, box, r, start, atoms, nc, 128, want_needed=True)
+    assert needed == int(np.diff(offs).max())
+    assert np.array_equal(cnt.cpu().numpy(), np.diff(offs))
+    got = rows_as_sets(nbr, cnt)
+    for i in range(len(pos)):
+        assert np.array_equal(got[i], nbr_o[offs[i]:offs[i + 1]])
+
+
+def test_neighbour_capacity_overflow_reports_needed(L, ctx):
+    c = configs.lj_solid(n_cells=6)
+    p = cu(c["pos"])
+    nc, cell_of, start, atoms = L.ppmd_build_cells(ctx, p, c["box"], 2.8)
+    with pytest.raises(L.PPMDError) as ei:
+        L.ppmd_build_neighbours(ctx, p, c["box"], 2.8, start, atoms, nc, 40, want_needed=True)
+    assert ei.value.code == L.ERR_CAPACITY
+    rc, needed = ctx.status()
+    assert rc == 0  # the status was consumed by the failing call
+    nbr, cnt, needed = L.ppmd_build_neighbours(ctx, p, c["box"], 2.8, start, atoms, nc, 128, want_needed=True)
+    assert needed == 78 or needed > 40
+
+
+def test_box_too_small_is_rejected(L, ctx):
+    pos = cu(np.zeros((4, 3)))
+    with pytest.raises(L.PPMDError) as ei:
+        L.ppmd_build_cells(ctx, pos, [7.0, 9.0, 9.0], 2.8)
+    assert ei.value.code == L.ERR_BOX
+
+
+def test_nonfinite_position_is_reported(L, ctx):
+    c = configs.lj_small()
+    pos = c["pos"].copy()
+    pos[17, 1] = np.nan
+    nc, cell_of, start, atoms = L.ppmd_build_cells(ctx, cu(pos), c["box"], 2.5)
+    rc, _ = ctx.status()
+    assert rc == L.ERR_NONFINITE
+
+
+def _lists(L, ctx, pos, box, r, max_nbr=128):
+    p = cu(pos)
+    nc, cell_of, start, atoms = L.ppmd_build_cells(ctx, p, box, r)
+    nbr, cnt = L.ppmd_build_neighbours(ctx, p, box, r, start, atoms, nc, max_nbr)
+    return p, nbr, cnt
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("shift", [0.0, 0.25])
+def test_lj_fp64_parity(L, ctx, case, shift):
+    c, r = CASES[case]()
+    pos, box = c["pos"], c["box"]
+    offs, nbr_o = oracle.neighbours_cells(pos, box, r)
+    Fo, eo, Uo, Wo = oracle.lj(pos, box, offs, nbr_o, shift=shift)
+    p, nbr, cnt = _lists(L, ctx, pos, box, r)
+    F, e, tot = L.ppmd_lj_forces(ctx, p, box, nbr, cnt, shift=shift, prec=L.FP64)
+    F, e, tot = F.cpu().numpy(), e.cpu().numpy(), tot.cpu().numpy()
+    assert force_err(F, Fo) <= 1e-12
+    assert np.abs(e - eo).max() <= 1e-12 * np.abs(eo).mean()
+    assert abs(tot[0] - Uo) <= 1e-12 * abs(Uo)
+    assert abs(tot[1] - Wo) <= 1e-12 * max(abs(Wo), 1.0)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_lj_fp32_parity(L, ctx, case):
+    c, r = CASES[case]()
+    pos, box = c["pos"], c["box"]
+    offs, nbr_o = oracle.neighbours_cells(pos, box, r)
+    Fo, eo, Uo, Wo = oracle.lj(pos, box, offs, nbr_o)
+    p, nbr, cnt = _lists(L, ctx, pos, box, r)
+    F, e, tot = L.ppmd_lj_forces(ctx, p, box, nbr, cnt, prec=L.FP32)
+    F, e, tot = F.cpu().numpy(), e.cpu().numpy(), tot.cpu().numpy()
+    assert force_err(F, Fo) <= 1e-5
+    assert np.abs(e - eo).max() <= 1e-6 * np.abs(eo).mean()
+    assert abs(tot[0] - Uo) / len(pos) <= 1e-6 * abs(Uo) / len(pos)
+
+
+def test_lj_empty_and_single_atom(L, ctx):
+    box = [9.0, 9.0, 9.0]
+    for n in (0, 1):
+        pos = cu(np.full((n, 3), 1.0))
+        nc, cell_of, start, atoms = L.ppmd_build_cells(ctx, pos, box, 2.5)
+        nbr, cnt = L.ppmd_build_neighbours(ctx, pos, box, 2.5, start, atoms, nc, 8)
+        F, e, tot = L.ppmd_lj_forces(ctx, pos, box, nbr, cnt, prec=L.FP32)
+        ctx.sync()
+        assert F.shape == (n, 3) and (F.cpu() == 0).all() and float(tot[0]) == 0.0
+
+
+@pytest.mark.parametrize("phase", [1, 2])
+def test_verlet_step_bit_exact(L, ctx, phase):
+    c = configs.lj_small()
+    rng = np.random.default_rng(4)
+    F = rng.normal(0, 3, c["pos"].shape)
+    po, vo = oracle.vv(phase, c["pos"], c["vel"], F, c["box"], 1.0, 0.005)
+    p, v = cu(c["pos"]), cu(c["vel"])
+    L.ppmd_verlet_step(ctx, phase, p, v, cu(F), c["box"], 1.0, 0.005)
+    assert np.array_equal(p.cpu().numpy(), po)
+    assert np.array_equal(v.cpu().numpy(), vo)
+
+
+def test_kinetic_energy(L, ctx):
+    c = configs.lj_small()
+    ke = L.ppmd_kinetic_energy(ctx, cu(c["vel"]), 1.0)
+    assert abs(float(ke[0]) - oracle.kinetic(c["vel"])) <= 1e-13 * oracle.kinetic(c["vel"])
+
+
+def _md(L, ctx, c, prec, nsteps, use_graph, energy_every=0, max_nbr=128):
+    n = len(c["pos"])
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=c["r_list"], rebuild_every=c["rebuild_every"], max_nbr=max_nbr,
+              prec=prec, energy_every=energy_every)
+    md.set_state(cu(c["pos"]), cu(c["vel"]))
+    en = torch.zeros((max(nsteps, 1), 2), dtype=torch.float64, device="cuda")
+    md.run(nsteps, en if energy_every else None, use_graph=use_graph)
+    pos = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    vel = torch.empty_like(pos)
+    F = torch.empty_like(pos)
+    md.get_state(pos, vel, F)
+    info = md.info()
+    return pos.cpu().numpy(), vel.cpu().numpy(), F.cpu().numpy(), en.cpu().numpy(), info
+
+
+def _pos_err(p, po, box):
+    d = p - po
+    d -= box * np.rint(d / box)
+    return np.abs(d).max()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_md_fp64_small_100_steps(L, ctx, use_graph):
+    """Plain method, small, FP64: 1000 atoms, rebuild every step, 100 steps."""
+    c = configs.lj_small()
+    po, vo, Fo, eno, _ = oracle.md_run(c["pos"], c["vel"], c["box"], 100, r_list=2.5, rebuild_every=1)
+    p, v, F, en, info = _md(L, ctx, c, L.FP64, 100, use_graph, energy_every=1)
+    assert info["steps"] == 100 and info["rebuilds"] == 101
+    assert _pos_err(p, po, c["box"]) <= 1e-10
+    assert np.abs(v - vo).max() <= 1e-9
+    assert force_err(F, Fo) <= 1e-9
+    assert np.abs(en - eno).max() <= 1e-10 * np.abs(eno).max()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_md_fp32_solid_10_steps(L, ctx, use_graph):
+    """FP32 pair forces with FP64 integration against the FP64 oracle over 10
+    steps (one rebuild at step 10), fcc solid with skin 0.3."""
+    c = configs.lj_solid(n_cells=10)
+    po, vo, Fo, eno, _ = oracle.md_run(c["pos"], c["vel"], c["box"], 10, r_list=2.8, rebuild_every=10)
+    p, v, F, en, info = _md(L, ctx, c, L.FP32, 10, use_graph, energy_every=10)
+    assert force_err(F, Fo) <= 1e-5
+    assert _pos_err(p, po, c["box"]) / c["box"][0] <= 1e-8
+    assert abs(en[9, 1] - eno[9, 1]) <= 1e-6 * abs(eno[9, 1])
+    assert abs(en[9, 0] - eno[9, 0]) <= 1e-6 * abs(eno[9, 0])
+
+
+def test_md_fp64_solid_10_steps_is_exact(L, ctx):
+    c = configs.lj_solid(n_cells=8)
+    po, vo, Fo, eno, _ = oracle.md_run(c["pos"], c["vel"], c["box"], 10, r_list=2.8, rebuild_every=10)
+    p, v, F, en, info = _md(L, ctx, c, L.FP64, 10, True, energy_every=10)
+    assert force_err(F, Fo) <= 1e-11
+    assert _pos_err(p, po, c["box"]) <= 1e-12 * c["box"][0]
+
+
+def test_md_momentum_conserved(L, ctx):
+    c = configs.lj_solid(n_cells=8)
+    p, v, F, en, info = _md(L, ctx, c, L.FP32, 50, True)
+    assert np.abs(v.sum(0)).max() <= 1e-9 * np.abs(v).sum()
+
+
+def test_md_batched_boxes_equal_single_runs(L, ctx):
+    """Several independent boxes advanced together give the single-box results."""
+    reps = configs.replicas(seed=4, nrep=3, n_min=600, n_max=3000)
+    pos = np.concatenate([r["pos"] for r in reps])
+    vel = np.concatenate([r["vel"] for r in reps])
+    off = np.cumsum([0] + [len(r["pos"]) for r in reps])
+    md = L.MD(ctx, off, [r["box"] for r in reps], r_list=2.8, rebuild_every=10, max_nbr=128, prec=L.FP32,
+              box_r_list=[r["r_list"] for r in reps])
+    md.set_state(cu(pos), cu(vel))
+    md.run(20)
+    P = torch.empty((off[-1], 3), dtype=torch.float64, device="cuda")
+    md.get_state(P)
+    P = P.cpu().numpy()
+    for k, r in enumerate(reps):
+        po, _, _, _, _ = oracle.md_run(r["pos"], r["vel"], r["box"], 20, r_list=r["r_list"], rebuild_every=10)
+        assert _pos_err(P[off[k]:off[k + 1]], po, r["box"]) / r["box"][0] <= 1e-8
