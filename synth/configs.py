@@ -124,24 +124,26 @@ def replicas(seed: int = 4, nrep: int = 256, n_min: int = 500, n_max: int = 3200
 
 
 def random_box(n: int, box, seed: int, cutoffs=(), margin: float = 1e-6, min_dist: float = 0.0):
-    """n atoms uniform in a box (small n: brute-force pair checks).  Atoms closer than
-    min_dist to another atom, or in a pair within `margin` of a cutoff, are redrawn."""
+    """n atoms placed one after another uniformly in a box (random sequential
+    addition; small n).  A candidate closer than min_dist to a placed atom, or
+    at a distance within `margin` of a cutoff, is drawn again."""
     box = np.asarray(box, dtype=np.float64)
     g = rng_stream(seed, 0)
-    pos = g.uniform(0.0, 1.0, (n, 3)) * box
-    for _ in range(200):
-        dr = pos[:, None, :] - pos[None, :, :]
-        dr -= box * np.rint(dr / box)
-        r = np.sqrt((dr ** 2).sum(-1))
-        np.fill_diagonal(r, np.inf)
-        bad = (r < min_dist)
-        for c in cutoffs:
-            bad |= np.abs(r - c) < margin
-        rows = np.nonzero(bad.any(1))[0]
-        if len(rows) == 0:
-            return wrap(pos, box), box
-        # redraw the higher-index atom of each offending pair
-        ii, jj = np.nonzero(np.triu(bad, 1))
-        idx = np.unique(jj)
-        pos[idx] = g.uniform(0.0, 1.0, (len(idx), 3)) * box
-    raise RuntimeError("random_box: could not satisfy constraints")
+    pos = np.zeros((n, 3))
+    for k in range(n):
+        for _ in range(100000):
+            x = g.uniform(0.0, 1.0, 3) * box
+            if k == 0:
+                break
+            dr = pos[:k] - x
+            dr -= box * np.rint(dr / box)
+            r = np.sqrt((dr ** 2).sum(-1))
+            ok = (r >= min_dist).all()
+            for c in cutoffs:
+                ok = ok and not (np.abs(r - c) < margin).any()
+            if ok:
+                break
+        else:
+            raise RuntimeError("random_box: could not place an atom")
+        pos[k] = x
+    return wrap(pos, box), box

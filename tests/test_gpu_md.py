@@ -4,6 +4,10 @@ Velocity Verlet and the time-stepping driver against the FP64 oracle.
 Tolerances (floating point, relative to the oracle):
   FP64 forces   max_i |dF_i| / rms|F| <= 1e-12, |dU| / |U| <= 1e-12
   FP32 forces   max_i |dF_i| / rms|F| <= 1e-5,  max_i |de_i| <= 1e-6 mean|e_i|
+                (the energy bound assumes no pair closer than sigma: single-precision
+                pair energies carry ~2^-19 V(r) error, which grows fast below sigma)
+  FP32 trajectories: positions within the displacement a 1e-5 rms|F| force error
+                gives over the run, (k dt)^2 1e-5 rms|F|.
 Integer results (cells, neighbour sets) are compared bit for bit.
 """
 import numpy as np
@@ -47,7 +51,7 @@ CASES = {
     "fcc10_r2.8": lambda: (configs.lj_solid(n_cells=10), 2.8),
     "sc10_r2.5": lambda: (configs.lj_small(), 2.5),
     "random_ragged": lambda: (dict(zip(("pos", "box"), random_box(997, [12.1, 11.3, 13.7], 3, cutoffs=(2.5, 2.8),
-                                                                   margin=1e-6, min_dist=0.7))), 2.8),
+                                                                   margin=1e-6, min_dist=1.0))), 2.8),
 }
 
 
@@ -249,5 +253,7 @@ def test_md_batched_boxes_equal_single_runs(L, ctx):
     md.get_state(P)
     P = P.cpu().numpy()
     for k, r in enumerate(reps):
-        po, _, _, _, _ = oracle.md_run(r["pos"], r["vel"], r["box"], 20, r_list=r["r_list"], rebuild_every=10)
-        assert _pos_err(P[off[k]:off[k + 1]], po, r["box"]) / r["box"][0] <= 1e-8
+        po, _, Fo, _, _ = oracle.md_run(r["pos"], r["vel"], r["box"], 20, r_list=r["r_list"], rebuild_every=10)
+        # displacement that a force error of 1e-5 rms|F| produces over 20 steps
+        bound = (20 * 0.005) ** 2 * 1e-5 * np.sqrt((Fo ** 2).sum(1).mean())
+        assert _pos_err(P[off[k]:off[k + 1]], po, r["box"]) <= bound
