@@ -199,6 +199,33 @@ int ppmd_md_forces(ppmd_md *md);
  * the largest row.  Synchronises. */
 int ppmd_md_list_stats(ppmd_md *md, int64_t *pairs, int32_t *max_row);
 
+/* ------------------------------------------------------------------ */
+/* Forces without any allocation.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory -- programs
+ * whose device memory is owned by a host framework (a fixed pool or a
+ * caching allocator that must see every byte), or latency-critical loops
+ * that may not pay the device synchronisation cudaMalloc/cudaFree can imply.
+ * It computes exactly what ppmd_lj_forces computes, with the same arguments
+ * except that a CUDA stream (cudaStream_t, NULL = legacy default stream of
+ * the current device) replaces the context.  It never calls cudaMalloc,
+ * cudaFree or any allocating routine: its working memory is one statically
+ * sized device array inside the library (about 4.2 MB, held by every GPU
+ * that loads the library until the process exits).
+ *  - n may not exceed PPMD_NOALLOC_MAX_ATOMS; larger n returns
+ *    PPMD_ERR_CAPACITY at once (with a message on stderr), nothing launched.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents:
+ *    calls whose work overlaps on the GPU (different streams, or different
+ *    host threads without ordering) race and give wrong results.
+ *  - There is no context, so device-detected conditions (a non-finite
+ *    coordinate) are not reported; argument and CUDA launch errors are. */
+#define PPMD_NOALLOC_MAX_ATOMS 262144
+int ppmd_lj_forces_noalloc(void *cuda_stream, const double *pos, int64_t n, const ppmd_box *box,
+                           const ppmd_lj_params *lj, const int32_t *nbr, const int32_t *nbr_count, int32_t max_nbr,
+                           ppmd_prec prec, double *force, double *e_atom, double *e_total, double *virial);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,8 @@ _SIGS = {
     "ppmd_md_info": (_I, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
     "ppmd_md_forces": (_I, [_P]),
     "ppmd_md_list_stats": (_I, [_P, C.POINTER(_I64), C.POINTER(_I32)]),
+    "ppmd_lj_forces_noalloc": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _P, _P, _I32, _I, _P, _P, _P,
+                                    _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -272,3 +274,25 @@ class MD:
         code = _lib.ppmd_md_info(self.h, C.byref(s), C.byref(r), C.byref(d))
         self.ctx.check(code)
         return dict(steps=s.value, rebuilds=r.value, max_disp=d.value, status=code)
+
+
+NOALLOC_MAX_ATOMS = 262144
+
+
+def ppmd_lj_forces_noalloc(pos, box, nbr, nbr_count, force, e_atom, totals, rc=2.5, eps=1.0, sigma=1.0, shift=0.0,
+                           prec=FP32, stream=None, n=None):
+    """ppmd_lj_forces into caller-allocated outputs, with no context and no
+    allocation by the library (for callers that may not allocate device
+    memory).  totals: float64 CUDA tensor of 2 (U, W) or None.  Returns the
+    C status code."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n = pos.shape[0] if n is None else n
+    p = LJParams(eps, sigma, rc, shift)
+    b = _box(box)
+    max_nbr = nbr.shape[1] if nbr.dim() == 2 else 0
+    return _lib.ppmd_lj_forces_noalloc(C.c_void_p(stream.cuda_stream), _ptr(pos), int(n), C.byref(b), C.byref(p),
+                                       _ptr(nbr), _ptr(nbr_count), int(max_nbr), int(prec), _ptr(force),
+                                       _ptr(e_atom) if e_atom is not None else None,
+                                       _ptr(totals[0:1]) if totals is not None else None,
+                                       C.c_void_p(totals.data_ptr() + 8) if totals is not None else None)
