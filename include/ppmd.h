@@ -156,6 +156,42 @@ int ppmd_verlet_step(ppmd_ctx *ctx, int phase, double *pos, double *vel, const d
 int ppmd_kinetic_energy(ppmd_ctx *ctx, const double *vel, int64_t n, double mass, double *ke);
 
 /* ------------------------------------------------------------------ */
+/* Structure analysis (Sec. 4).                                          */
+/* ------------------------------------------------------------------ */
+
+/* Bond order parameters, Eqs. (1)-(2) with Algorithms 1 and 2: for every
+ * atom i, nu_i = number of list neighbours j with |r_i - r_j| < r_cut and
+ *   Q_l(i) = sqrt(4 pi / (2l+1) sum_{m=-l..l} |q_lm(i)|^2),
+ *   q_lm(i) = (1/nu_i) sum_j Y_l^m(r_ij / |r_ij|),
+ * for l = 4 and l = 6 (orthonormal spherical harmonics; Q_l = 0 when
+ * nu_i = 0).  The list (as from ppmd_build_neighbours, cutoff >= r_cut)
+ * is read, not changed.  Outputs (device, any may be NULL): q4[n], q6[n]
+ * single precision, n_nb[n]. */
+int ppmd_boa_q46(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_cut, const int32_t *nbr,
+                 const int32_t *nbr_count, int32_t max_nbr, float *q4, float *q6, int32_t *n_nb);
+
+/* Common neighbour analysis, Eqs. (3)-(5) with Algorithms 3, 4, 5 and 7:
+ * atoms closer than r_cut are bonded; for each bonded pair (i, j) the
+ * common neighbours C = N(i) n N(j), the bonds E among them and the
+ * number of bonds in the largest connected part of (C, E) give the triplet
+ * (n_cn, n_b, n_lcb), stored as n_cn << 16 | n_b << 8 | n_lcb in
+ * triplets[i * max_nbr + m] for list slot m (0xFFFFFFFF where nbr[i][m] is
+ * not bonded; triplets may be NULL).  label[n] (device, may be NULL): 1 fcc
+ * (12 bonds, all (4,2,1)), 2 hcp (12 bonds, 6 (4,2,1) + 6 (4,2,2)), 3 bcc
+ * (14 bonds, 8 (6,6,6) + 6 (4,4,4)), else 0.  At most 64 bonds per atom
+ * (more latches PPMD_ERR_CAPACITY and labels the atom 0). */
+int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_cut, const int32_t *nbr,
+             const int32_t *nbr_count, int32_t max_nbr, uint32_t *triplets, int8_t *label);
+
+/* Both analyses straight from positions: the atoms are binned and sorted by
+ * cell internally, the list is built at max(r_boa, r_cna) and the results
+ * are returned in caller order.  Bond order is computed when any of q4, q6,
+ * n_nb is given (cutoff r_boa), CNA labels when label is given (cutoff
+ * r_cna).  Synchronises once (list capacity check). */
+int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
+                 float *q4, float *q6, int32_t *n_nb, int8_t *label);
+
+/* ------------------------------------------------------------------ */
 /* Time stepping (Algorithm 6 driven by the list-reuse policy of Sec. 3.5,
  * the paper's IntegratorRange), for one box or a batch of independent boxes
  * (replicas) advanced together.  The integrator keeps its own copy of the

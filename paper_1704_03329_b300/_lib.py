@@ -65,6 +65,9 @@ _SIGS = {
     "ppmd_lj_forces": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _P, _P, _I32, _I, _P, _P, _P, _P]),
     "ppmd_verlet_step": (_I, [_P, _I, _P, _P, _P, _I64, C.POINTER(Box), _D, _D]),
     "ppmd_kinetic_energy": (_I, [_P, _P, _I64, _D, _P]),
+    "ppmd_boa_q46": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, _I32, _P, _P, _P]),
+    "ppmd_cna": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, _I32, _P, _P]),
+    "ppmd_analyze": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _D, _P, _P, _P, _P]),
     "ppmd_md_create": (_I, [_P, C.POINTER(_P), _I64, _P, _P, _P, C.POINTER(MDParams)]),
     "ppmd_md_destroy": (_I, [_P]),
     "ppmd_md_set_state": (_I, [_P, _P, _P]),
@@ -212,6 +215,51 @@ def ppmd_kinetic_energy(ctx: Context, vel, mass=1.0):
     ke = torch.zeros(1, dtype=torch.float64, device=vel.device)
     ctx.check(_lib.ppmd_kinetic_energy(ctx.h, _ptr(vel), vel.shape[0], float(mass), _ptr(ke)))
     return ke
+
+
+def _opt(t):
+    return _ptr(t) if t is not None else None
+
+
+def ppmd_boa_q46(ctx: Context, pos, box, r_cut, nbr, nbr_count):
+    """Q4, Q6 (float32 [n]) and bonded-neighbour counts (int32 [n])."""
+    n = pos.shape[0]
+    q4 = torch.empty(n, dtype=torch.float32, device=pos.device)
+    q6 = torch.empty(n, dtype=torch.float32, device=pos.device)
+    nnb = torch.empty(n, dtype=torch.int32, device=pos.device)
+    b = _box(box)
+    ctx.check(_lib.ppmd_boa_q46(ctx.h, _ptr(pos), n, C.byref(b), float(r_cut), _ptr(nbr), _ptr(nbr_count),
+                                int(nbr.shape[1]), _ptr(q4), _ptr(q6), _ptr(nnb)))
+    return q4, q6, nnb
+
+
+def ppmd_cna(ctx: Context, pos, box, r_cut, nbr, nbr_count, want_triplets=True):
+    """CNA triplets (uint32 as int32 [n, max_nbr]) and labels (int8 [n])."""
+    n = pos.shape[0]
+    trip = torch.empty(nbr.shape, dtype=torch.int32, device=pos.device) if want_triplets else None
+    lab = torch.empty(n, dtype=torch.int8, device=pos.device)
+    b = _box(box)
+    ctx.check(_lib.ppmd_cna(ctx.h, _ptr(pos), n, C.byref(b), float(r_cut), _ptr(nbr), _ptr(nbr_count),
+                            int(nbr.shape[1]), _opt(trip), _ptr(lab)))
+    return trip, lab
+
+
+def ppmd_analyze(ctx: Context, pos, box, r_boa=1.5, r_cna=None, boa=True, cna=True, out=None):
+    """Pipeline from positions; returns dict with q4, q6, n_nb and/or label."""
+    n = pos.shape[0]
+    dev = pos.device
+    out = out or {}
+    if boa:
+        out.setdefault("q4", torch.empty(n, dtype=torch.float32, device=dev))
+        out.setdefault("q6", torch.empty(n, dtype=torch.float32, device=dev))
+        out.setdefault("n_nb", torch.empty(n, dtype=torch.int32, device=dev))
+    if cna:
+        out.setdefault("label", torch.empty(n, dtype=torch.int8, device=dev))
+    b = _box(box)
+    ctx.check(_lib.ppmd_analyze(ctx.h, _ptr(pos), n, C.byref(b), float(r_boa or 0.0), float(r_cna or 0.0),
+                                _opt(out.get("q4")), _opt(out.get("q6")), _opt(out.get("n_nb")),
+                                _opt(out.get("label"))))
+    return out
 
 
 class MD:

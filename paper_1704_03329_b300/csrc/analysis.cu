@@ -1,0 +1,417 @@
+// Structure analysis over a neighbour list:
+//  - bond order parameters Q4, Q6 (Eqs. (1)-(2), Algorithms 1-2), one thread
+//    per atom accumulating the spherical-harmonic moments of its bonds;
+//  - common neighbour analysis (Eqs. (3)-(5), Algorithms 3-5 and 7), one warp
+//    per atom on 64-bit adjacency masks of the atom's bonded neighbours;
+//  - an analysis pipeline that bins and sorts the atoms by cell, builds the
+//    list and runs either analysis, returning results in caller order.
+#include <math.h>
+
+#include "analysis.cuh"
+#include "cells.cuh"
+#include "neighbours.cuh"
+
+namespace ppmd {
+
+// ---------------------------------------------------------------------
+// Spherical harmonics for l = 4 and l = 6.
+// For a unit vector u = (x, y, z):  Y_l^m(u) = N_lm P_l^m(z) e^{i m phi} and
+// P_l^m(z) e^{i m phi} = Pr_l^m(z) (x + i y)^m with Pr_l^m = P_l^m / (1-z^2)^{m/2},
+// a polynomial obtained from the three-term recurrence
+//   Pr_m^m = (-1)^m (2m-1)!!,  Pr_{m+1}^m = (2m+1) z Pr_m^m,
+//   (l-m) Pr_l^m = (2l-1) z Pr_{l-1}^m - (l+m-1) Pr_{l-2}^m.
+// Q_l^2 = 4 pi/(2l+1) sum_{m=-l..l} |q_lm|^2 = sum_{m=0..l} c_lm |S_lm|^2 / nu^2 with
+// S_lm = sum_j Pr_l^m(z_j) (x_j + i y_j)^m, c_l0 = 1, c_lm = 2 (l-m)!/(l+m)! (m > 0)
+// (the Y_l^{-m} terms equal the Y_l^m ones in modulus).  sqrt(c_lm) is folded
+// into each term so that every partial sum stays of order one.
+// ---------------------------------------------------------------------
+struct YlmCoef {
+    float pmm[7];        // (-1)^m (2m-1)!!
+    float a[7][7];       // (2l-1)/(l-m)
+    float b[7][7];       // (l+m-1)/(l-m)
+    float s4[5], s6[7];  // sqrt(c_4m), sqrt(c_6m)
+};
+
+static YlmCoef make_coef() {
+    YlmCoef k;
+    memset(&k, 0, sizeof(k));
+    double df = 1.0;
+    for (int m = 0; m <= 6; ++m) {
+        if (m > 0) df *= (2.0 * m - 1.0);
+        k.pmm[m] = (float)((m % 2 ? -1.0 : 1.0) * df);
+        for (int l = m + 2; l <= 6; ++l) {
+            k.a[l][m] = (float)((2.0 * l - 1.0) / (l - m));
+            k.b[l][m] = (float)((l + m - 1.0) / (l - m));
+        }
+    }
+    auto fact = [](int q) {
+        double f = 1.0;
+        for (int i = 2; i <= q; ++i) f *= i;
+        return f;
+    };
+    for (int m = 0; m <= 4; ++m) k.s4[m] = (float)sqrt((m ? 2.0 : 1.0) * fact(4 - m) / fact(4 + m));
+    for (int m = 0; m <= 6; ++m) k.s6[m] = (float)sqrt((m ? 2.0 : 1.0) * fact(6 - m) / fact(6 + m));
+    return k;
+}
+
+__device__ __forceinline__ void boa_accumulate(const YlmCoef &K, float x, float y, float z, float (&r4)[5],
+                                               float (&i4)[5], float (&r6)[7], float (&i6)[7]) {
+    float pr = 1.0f, pi = 0.0f;  // (x + i y)^m
+#pragma unroll
+    for (int m = 0; m <= 6; ++m) {
+        if (m > 0) {
+            const float t = pr * x - pi * y;
+            pi = fmaf(pr, y, pi * x);
+            pr = t;
+        }
+        float p2 = 0.0f, p1 = K.pmm[m], p4 = 0.0f, p6 = 0.0f;
+        if (m == 4) p4 = p1;
+        if (m == 6) p6 = p1;
+        if (m + 1 <= 6) {
+            const float p = (2.0f * m + 1.0f) * z * p1;
+            p2 = p1;
+            p1 = p;
+            if (m + 1 == 4) p4 = p1;
+            if (m + 1 == 6) p6 = p1;
+        }
+#pragma unroll
+        for (int l = m + 2; l <= 6; ++l) {
+            const float p = fmaf(K.a[l][m] * z, p1, -K.b[l][m] * p2);
+            p2 = p1;
+            p1 = p;
+            if (l == 4) p4 = p1;
+            if (l == 6) p6 = p1;
+        }
+        if (m <= 4) {
+            const float w = K.s4[m] * p4;
+            r4[m] = fmaf(w, pr, r4[m]);
+            i4[m] = fmaf(w, pi, i4[m]);
+        }
+        const float w6 = K.s6[m] * p6;
+        r6[m] = fmaf(w6, pr, r6[m]);
+        i6[m] = fmaf(w6, pi, i6[m]);
+    }
+}
+
+// One thread per atom.  Bonds: list entries with r < r_cut (exact decision).
+// out_idx (may be null): write the results of atom i at out_idx[i].
+__global__ void __launch_bounds__(256) k_boa(int64_t n, const int4 *__restrict__ xq, const double *__restrict__ pos64,
+                                             SegTable st, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
+                                             int32_t max_nbr, double rc2, float rc2_lo, float rc2_hi, YlmCoef K,
+                                             const int32_t *__restrict__ out_idx, float *__restrict__ q4,
+                                             float *__restrict__ q6, int32_t *__restrict__ nnb) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 xi = xq[i];
+    const Seg &S = seg_ref(st, xi.w);
+    float r4[5], i4[5], r6[7], i6[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        if (m < 5) r4[m] = i4[m] = 0.0f;
+        r6[m] = i6[m] = 0.0f;
+    }
+    const int32_t deg = min(cnt[i], max_nbr);
+    const int32_t *row = nbr + i * (int64_t)max_nbr;
+    int32_t nu = 0;
+    for (int32_t k = 0; k < deg; ++k) {
+        const int32_t j = row[k];
+        const int4 xj = __ldg(&xq[j]);
+        float dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj.x, S.sx[0]);
+        float dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj.y, S.sx[1]);
+        float dz = fixed_delta((uint32_t)xi.z, (uint32_t)xj.z, S.sx[2]);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        bool in = r2 < rc2_lo;
+        if (!in && r2 < rc2_hi) {
+            double dr[3];
+            in = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr) < rc2;
+        }
+        if (!in) continue;
+        const float ir = rsqrtf(r2);
+        boa_accumulate(K, dx * ir, dy * ir, dz * ir, r4, i4, r6, i6);
+        ++nu;
+    }
+    float s4 = 0.0f, s6 = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        if (m < 5) s4 = fmaf(r4[m], r4[m], fmaf(i4[m], i4[m], s4));
+        s6 = fmaf(r6[m], r6[m], fmaf(i6[m], i6[m], s6));
+    }
+    const float inv = nu > 0 ? 1.0f / (float)nu : 0.0f;
+    const int64_t o = out_idx ? out_idx[i] : i;
+    if (q4) q4[o] = sqrtf(s4) * inv;
+    if (q6) q6[o] = sqrtf(s6) * inv;
+    if (nnb) nnb[o] = nu;
+}
+
+// ---------------------------------------------------------------------
+// Common neighbour analysis, one warp per atom.
+// Bonded neighbours of i (list entries with r < r_cut) get local indices
+// 0..nu-1; A[a] is the 64-bit set of local indices bonded to neighbour a.
+// For the bond (i, a):  C = A[a] (common neighbours of i and a),
+//   n_cn = |C|,  n_b = sum_{b in C} |A[b] & C| / 2,
+//   n_lcb = edges of the largest connected component of (C, A restricted to C),
+// found by growing each component from its lowest member.
+// Triplets: trip[i*max_nbr + m] for list slot m (0xFFFFFFFF: not bonded).
+// ---------------------------------------------------------------------
+constexpr int CNA_WARPS = 4;
+constexpr uint32_t NOT_BONDED = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool bonded(const int4 &a, const int4 &b, const double *pa, const double *pb, const Seg &S,
+                                       double rc2, float lo, float hi) {
+    float dx = fixed_delta((uint32_t)a.x, (uint32_t)b.x, S.sx[0]);
+    float dy = fixed_delta((uint32_t)a.y, (uint32_t)b.y, S.sx[1]);
+    float dz = fixed_delta((uint32_t)a.z, (uint32_t)b.z, S.sx[2]);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 < lo) return true;
+    if (r2 >= hi) return false;
+    double dr[3];
+    return min_image_r2(pa, pb, S, dr) < rc2;
+}
+
+__device__ __forceinline__ int32_t cna_label_of(int nu, int c421, int c422, int c444, int c666) {
+    if (nu == 12 && c421 == 12) return PPMD_FCC;
+    if (nu == 12 && c421 == 6 && c422 == 6) return PPMD_HCP;
+    if (nu == 14 && c666 == 8 && c444 == 6) return PPMD_BCC;
+    return PPMD_OTHER;
+}
+
+__global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *__restrict__ xq,
+                                                        const double *__restrict__ pos64, SegTable st,
+                                                        const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
+                                                        int32_t max_nbr, double rc2, float lo, float hi,
+                                                        const int32_t *__restrict__ out_idx, uint32_t *__restrict__ trip,
+                                                        int8_t *__restrict__ label, int32_t *status,
+                                                        unsigned long long *needed) {
+    __shared__ int32_t s_j[CNA_WARPS][64];
+    __shared__ int32_t s_slot[CNA_WARPS][64];
+    __shared__ int4 s_x[CNA_WARPS][64];
+    __shared__ unsigned long long s_A[CNA_WARPS][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * CNA_WARPS + w;
+    if (i >= n) return;
+    const int4 xi = xq[i];
+    const Seg &S = seg_ref(st, xi.w);
+    const int32_t deg = min(cnt[i], max_nbr);
+    const int32_t *row = nbr + i * (int64_t)max_nbr;
+    uint32_t *trow = trip ? trip + i * (int64_t)max_nbr : nullptr;
+    const unsigned lt = (1u << lane) - 1u;
+    // bonded neighbours, compacted in list order
+    int32_t nu = 0;
+    for (int32_t base = 0; base < deg; base += 32) {
+        const int32_t k = base + lane;
+        bool b = false;
+        int32_t j = 0;
+        int4 xj = make_int4(0, 0, 0, 0);
+        if (k < deg) {
+            j = row[k];
+            xj = xq[j];
+            b = bonded(xi, xj, pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, rc2, lo, hi);
+            if (!b && trow) trow[k] = NOT_BONDED;
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, b);
+        if (b) {
+            const int32_t a = nu + __popc(ball & lt);
+            if (a < 64) {
+                s_j[w][a] = j;
+                s_slot[w][a] = k;
+                s_x[w][a] = xj;
+            }
+        }
+        nu += __popc(ball);
+    }
+    __syncwarp();
+    if (nu > 64) {
+        // more bonded neighbours than the 64-bit masks hold
+        if (lane == 0) {
+            latch_status(status, PPMD_ERR_CAPACITY);
+            latch_needed(needed, (unsigned long long)nu);
+            if (label) label[out_idx ? out_idx[i] : i] = PPMD_OTHER;
+        }
+        return;
+    }
+    // adjacency among the bonded neighbours
+    for (int a = lane; a < nu; a += 32) {
+        unsigned long long m = 0ull;
+        const int4 xa = s_x[w][a];
+        const int32_t ja = s_j[w][a];
+        for (int b = 0; b < nu; ++b) {
+            if (b == a) continue;
+            if (bonded(xa, s_x[w][b], pos64 + 3 * (int64_t)ja, pos64 + 3 * (int64_t)s_j[w][b], S, rc2, lo, hi))
+                m |= 1ull << b;
+        }
+        s_A[w][a] = m;
+    }
+    __syncwarp();
+    int c421 = 0, c422 = 0, c444 = 0, c666 = 0;
+    for (int a = lane; a < nu; a += 32) {
+        const unsigned long long C = s_A[w][a];
+        const int ncn = __popcll(C);
+        int twice_nb = 0;
+        for (unsigned long long r = C; r; r &= r - 1) twice_nb += __popcll(s_A[w][__ffsll((long long)r) - 1] & C);
+        // components of the common-neighbour graph
+        int best = 0;
+        unsigned long long rest = C;
+        while (rest) {
+            unsigned long long comp = rest & (~rest + 1ull);
+            unsigned long long frontier = comp;
+            while (frontier) {
+                unsigned long long grow = 0ull;
+                for (unsigned long long f = frontier; f; f &= f - 1) grow |= s_A[w][__ffsll((long long)f) - 1];
+                grow &= C & ~comp;
+                comp |= grow;
+                frontier = grow;
+            }
+            int twice_e = 0;
+            for (unsigned long long f = comp; f; f &= f - 1) twice_e += __popcll(s_A[w][__ffsll((long long)f) - 1] & comp);
+            best = max(best, twice_e >> 1);
+            rest &= ~comp;
+        }
+        const uint32_t t = ((uint32_t)ncn << 16) | ((uint32_t)(twice_nb >> 1) << 8) | (uint32_t)best;
+        if (trow) trow[s_slot[w][a]] = t;
+        c421 += t == ((4u << 16) | (2u << 8) | 1u);
+        c422 += t == ((4u << 16) | (2u << 8) | 2u);
+        c444 += t == ((4u << 16) | (4u << 8) | 4u);
+        c666 += t == ((6u << 16) | (6u << 8) | 6u);
+    }
+    c421 = __reduce_add_sync(0xffffffffu, c421);
+    c422 = __reduce_add_sync(0xffffffffu, c422);
+    c444 = __reduce_add_sync(0xffffffffu, c444);
+    c666 = __reduce_add_sync(0xffffffffu, c666);
+    if (lane == 0 && label) label[out_idx ? out_idx[i] : i] = (int8_t)cna_label_of(nu, c421, c422, c444, c666);
+}
+
+int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
+               const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
+               float *q6, int32_t *nnb) {
+    static const YlmCoef K = make_coef();
+    float lo, hi;
+    cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
+    if (n > 0)
+        PPMD_LAUNCH(ctx, k_boa, div_up(n, 256), 256, 0, n, xq, pos64, st, nbr, cnt, max_nbr, r_cut * r_cut, lo, hi, K, out_idx,
+                    q4, q6, nnb);
+    return check_launch(ctx, "boa");
+}
+
+int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
+               const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
+               int8_t *label) {
+    float lo, hi;
+    cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
+    if (n > 0)
+        PPMD_LAUNCH(ctx, k_cna, div_up(n, CNA_WARPS), CNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr, r_cut * r_cut,
+                    lo, hi, out_idx, trip, label, ctx->d_status, ctx->d_needed);
+    return check_launch(ctx, "cna");
+}
+
+// ---------------------------------------------------------------------
+// Pipeline: sort by cell, list at r_list, analyses, results in caller order.
+// ---------------------------------------------------------------------
+__global__ void k_gather_pos(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ pos,
+                             const int4 *__restrict__ xq_in, double *__restrict__ pos_o, int4 *__restrict__ xq_o,
+                             const int32_t *__restrict__ cell_in, int32_t *__restrict__ cell_o) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t j = perm[k];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) pos_o[3 * k + d] = pos[3 * j + d];
+    xq_o[k] = xq_in[j];
+    cell_o[k] = cell_in[j];
+}
+
+int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int32_t max_nbr,
+                    Snapshot &s) {
+    s.n = n;
+    s.st.d = nullptr;
+    s.st.nseg = 1;
+    PPMD_TRY(make_seg(ctx, s.st.one, box->L, r_list, r_list));
+    s.Lmax = fmax(box->L[0], fmax(box->L[1], box->L[2]));
+    const int64_t ncell = (int64_t)s.st.one.nc[0] * s.st.one.nc[1] * s.st.one.nc[2];
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int4 *xq0 = (int4 *)scratch(ctx, S_XQ, sizeof(int4) * nn);
+    int32_t *cell0 = (int32_t *)scratch(ctx, S_CELLS0, sizeof(int32_t) * nn);
+    s.cell_start = (int32_t *)scratch(ctx, S_CELLS1, sizeof(int32_t) * (size_t)(ncell + 1));
+    s.perm = (int32_t *)scratch(ctx, S_CELLS2, sizeof(int32_t) * nn);
+    s.pos = (double *)scratch(ctx, S_SORTPOS, sizeof(double) * 3 * nn);
+    s.xq = (int4 *)scratch(ctx, S_AUX0, sizeof(int4) * nn);
+    s.cell_of = (int32_t *)scratch(ctx, S_SORTIDX, sizeof(int32_t) * nn);
+    if (!xq0 || !cell0 || !s.cell_start || !s.perm || !s.pos || !s.xq || !s.cell_of) return PPMD_ERR_NOMEM;
+    // exact cells of the caller's atoms, then sort
+    PPMD_TRY(prep_fixed(ctx, pos, n, s.st, nullptr, xq0, nullptr));
+    PPMD_TRY(bin_atoms(ctx, pos, n, s.st, nullptr, ncell, true, cell0, s.cell_start, s.perm));
+    if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos, div_up(n, 256), 256, 0, n, s.perm, pos, xq0, s.pos, s.xq, cell0, s.cell_of);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        s.max_nbr = max_nbr;
+        s.nbr = (int32_t *)scratch(ctx, S_NBR, sizeof(int32_t) * nn * (size_t)max_nbr);
+        s.cnt = (int32_t *)scratch(ctx, S_NBRCNT, sizeof(int32_t) * nn);
+        if (!s.nbr || !s.cnt) return PPMD_ERR_NOMEM;
+        PPMD_TRY(build_list(ctx, n, s.xq, s.pos, s.st, s.cell_of, s.cell_start, nullptr, s.nbr, s.cnt, max_nbr));
+        int64_t need = 0;
+        int rc = ppmd_status(ctx, &need);
+        if (rc == PPMD_ERR_CAPACITY && attempt == 0) {
+            max_nbr = (int32_t)((need + 15) / 16 * 16);
+            continue;
+        }
+        if (rc < 0) return rc;
+        break;
+    }
+    return PPMD_OK;
+}
+
+}  // namespace ppmd
+
+using namespace ppmd;
+
+static int list_args_ok(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_cut, const int32_t *nbr,
+                        const int32_t *cnt, int32_t max_nbr) {
+    if (!ctx || !box || n < 0 || max_nbr < 0 || !(r_cut > 0)) return set_error(ctx, PPMD_ERR_INVALID, "bad argument");
+    if (n > 0 && (!pos || !cnt || (max_nbr > 0 && !nbr))) return set_error(ctx, PPMD_ERR_INVALID, "null array");
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_boa_q46(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_cut,
+                            const int32_t *nbr, const int32_t *nbr_count, int32_t max_nbr, float *q4, float *q6,
+                            int32_t *n_nb) {
+    PPMD_TRY(list_args_ok(ctx, pos, n, box, r_cut, nbr, nbr_count, max_nbr));
+    cudaSetDevice(ctx->device);
+    SegTable st;
+    st.d = nullptr;
+    st.nseg = 1;
+    PPMD_TRY(make_seg(ctx, st.one, box->L, 0.0, r_cut));
+    int4 *xq = (int4 *)scratch(ctx, S_XQ, sizeof(int4) * (size_t)(n > 0 ? n : 1));
+    if (!xq) return PPMD_ERR_NOMEM;
+    PPMD_TRY(prep_fixed(ctx, pos, n, st, nullptr, xq, nullptr));
+    double Lmax = fmax(box->L[0], fmax(box->L[1], box->L[2]));
+    return boa_launch(ctx, n, xq, pos, st, nbr, nbr_count, max_nbr, r_cut, Lmax, nullptr, q4, q6, n_nb);
+}
+
+extern "C" int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_cut, const int32_t *nbr,
+                        const int32_t *nbr_count, int32_t max_nbr, uint32_t *triplets, int8_t *label) {
+    PPMD_TRY(list_args_ok(ctx, pos, n, box, r_cut, nbr, nbr_count, max_nbr));
+    cudaSetDevice(ctx->device);
+    SegTable st;
+    st.d = nullptr;
+    st.nseg = 1;
+    PPMD_TRY(make_seg(ctx, st.one, box->L, 0.0, r_cut));
+    int4 *xq = (int4 *)scratch(ctx, S_XQ, sizeof(int4) * (size_t)(n > 0 ? n : 1));
+    if (!xq) return PPMD_ERR_NOMEM;
+    PPMD_TRY(prep_fixed(ctx, pos, n, st, nullptr, xq, nullptr));
+    double Lmax = fmax(box->L[0], fmax(box->L[1], box->L[2]));
+    return cna_launch(ctx, n, xq, pos, st, nbr, nbr_count, max_nbr, r_cut, Lmax, nullptr, triplets, label);
+}
+
+extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
+                            float *q4, float *q6, int32_t *n_nb, int8_t *label) {
+    if (!ctx || !box || n < 0 || (n > 0 && !pos)) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_analyze: bad argument");
+    const bool want_boa = q4 || q6 || n_nb;
+    const bool want_cna = label != nullptr;
+    if ((want_boa && !(r_boa > 0)) || (want_cna && !(r_cna > 0)))
+        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_analyze: bad cutoff");
+    cudaSetDevice(ctx->device);
+    double r_list = fmax(want_boa ? r_boa : 0.0, want_cna ? r_cna : 0.0);
+    if (!(r_list > 0)) return PPMD_OK;
+    Snapshot s;
+    PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_list, 32, s));
+    if (want_boa) PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
+    if (want_cna) PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_cna, s.Lmax, s.perm, nullptr, label));
+    return PPMD_OK;
+}

@@ -1,0 +1,30 @@
+// Structure analysis kernels (bond order parameters, common neighbour
+// analysis) and the sorted-snapshot pipeline shared with the classifier.
+#pragma once
+#include "common.cuh"
+
+namespace ppmd {
+// Atoms of one box binned and sorted by cell, with their neighbour list.
+struct Snapshot {
+    int64_t n = 0;
+    SegTable st{};
+    double Lmax = 0;
+    double *pos = nullptr;      // [n][3] sorted
+    int4 *xq = nullptr;         // fixed-point, sorted
+    int32_t *perm = nullptr;    // sorted index -> caller index
+    int32_t *cell_of = nullptr, *cell_start = nullptr;
+    int32_t *nbr = nullptr, *cnt = nullptr;
+    int32_t max_nbr = 0;
+};
+// Bin/sort the caller's atoms with cells of edge >= r_list and build the
+// list at r_list (row capacity grown once if max_nbr is too small).
+// Synchronises once to check the list capacity.
+int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int32_t max_nbr,
+                    Snapshot &s);
+int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
+               const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
+               float *q6, int32_t *nnb);
+int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
+               const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
+               int8_t *label);
+}  // namespace ppmd

@@ -1,0 +1,140 @@
+"""GPU parity of bond order analysis (Q4, Q6) and common neighbour analysis
+against the FP64 oracle.
+
+Q_l are computed in single precision: |dQ| <= 1e-5 absolute.  Neighbour
+counts, CNA triplets and structure labels are compared bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import configs, make_lattice
+from synth.configs import R_BOA, R_CNA
+
+pytestmark = pytest.mark.gpu
+SMALL = {"fcc": (10, 10, 5), "bcc": (10, 10, 5), "hcp": (10, 6, 6), "liquid": (12, 12, 12)}
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1704_03329_b300 import lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    return L.Context(0)
+
+
+def cu(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _gpu_list(L, ctx, p, box, r, max_nbr=48):
+    nc, cell_of, start, atoms = L.ppmd_build_cells(ctx, p, box, r)
+    return L.ppmd_build_neighbours(ctx, p, box, r, start, atoms, nc, max_nbr)
+
+
+def _box(kind, sigma, seed=31):
+    return configs.structure_box(kind, sigma, seed, cells=SMALL[kind])
+
+
+@pytest.mark.parametrize("kind", ["fcc", "bcc", "hcp", "liquid"])
+@pytest.mark.parametrize("sigma", [0.02, 0.1])
+def test_boa_parity(L, ctx, kind, sigma):
+    c = _box(kind, sigma)
+    pos, box = c["pos"], c["box"]
+    offs, nb = oracle.neighbours_cells(pos, box, R_BOA)
+    Q4o, nno = oracle.boa(pos, box, offs, nb, R_BOA, 4)
+    Q6o, _ = oracle.boa(pos, box, offs, nb, R_BOA, 6)
+    p = cu(pos)
+    nbr, cnt = _gpu_list(L, ctx, p, box, R_BOA)
+    q4, q6, nnb = L.ppmd_boa_q46(ctx, p, box, R_BOA, nbr, cnt)
+    assert np.array_equal(nnb.cpu().numpy(), nno)
+    assert np.abs(q4.cpu().numpy() - Q4o).max() <= 1e-5
+    assert np.abs(q6.cpu().numpy() - Q6o).max() <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["fcc", "bcc", "hcp"])
+def test_boa_perfect_lattice_table(L, ctx, kind, golden):
+    lat = make_lattice(kind, SMALL[kind], 0.8442)
+    pos, box = lat.sites(), lat.box
+    p = cu(pos)
+    nbr, cnt = _gpu_list(L, ctx, p, box, R_BOA)
+    q4, q6, nnb = L.ppmd_boa_q46(ctx, p, box, R_BOA, nbr, cnt)
+    ref = golden["Q_table"][kind]
+    assert np.abs(q4.cpu().numpy() - ref["Q4"]).max() <= 0.0006
+    assert np.abs(q6.cpu().numpy() - ref["Q6"]).max() <= 0.0006
+
+
+def _trip_map(nbr, cnt, trip):
+    nbr, cnt, trip = nbr.cpu().numpy(), cnt.cpu().numpy(), trip.cpu().numpy().view(np.uint32)
+    out = {}
+    for i in range(len(cnt)):
+        for m in range(cnt[i]):
+            if trip[i, m] != 0xFFFFFFFF:
+                out[(i, int(nbr[i, m]))] = int(trip[i, m])
+    return out
+
+
+@pytest.mark.parametrize("kind", ["fcc", "bcc", "hcp", "liquid"])
+@pytest.mark.parametrize("sigma", [0.02, 0.05, 0.1])
+def test_cna_triplets_and_labels_bit_exact(L, ctx, kind, sigma):
+    c = _box(kind, sigma)
+    pos, box = c["pos"], c["box"]
+    offs, nb = oracle.neighbours_cells(pos, box, R_BOA)
+    nbond, trip_o, partner, _ = oracle.cna(pos, box, offs, nb, R_CNA)
+    lab_o = oracle.cna_label(nbond, trip_o)
+    ref = {(i, int(partner[i, a])): int(trip_o[i, a]) for i in range(len(pos)) for a in range(nbond[i])}
+    p = cu(pos)
+    nbr, cnt = _gpu_list(L, ctx, p, box, R_BOA)
+    trip, lab = L.ppmd_cna(ctx, p, box, R_CNA, nbr, cnt)
+    ctx.sync()
+    assert _trip_map(nbr, cnt, trip) == ref
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+
+
+@pytest.mark.parametrize("kind", ["fcc", "bcc", "hcp"])
+def test_cna_perfect_lattice_labels(L, ctx, kind):
+    lat = make_lattice(kind, SMALL[kind], 0.8442)
+    p = cu(lat.sites())
+    nbr, cnt = _gpu_list(L, ctx, p, lat.box, R_BOA)
+    _, lab = L.ppmd_cna(ctx, p, lat.box, R_CNA, nbr, cnt, want_triplets=False)
+    assert (lab.cpu().numpy() == {"fcc": 1, "hcp": 2, "bcc": 3}[kind]).all()
+
+
+@pytest.mark.parametrize("kind", ["fcc", "hcp", "liquid"])
+def test_analyze_pipeline_parity(L, ctx, kind):
+    """Positions in a shuffled order: the pipeline sorts internally and must
+    return every result in the caller's order."""
+    c = _box(kind, 0.05, seed=32)
+    perm = np.random.default_rng(0).permutation(len(c["pos"]))
+    pos, box = c["pos"][perm], c["box"]
+    offs, nb = oracle.neighbours_cells(pos, box, R_BOA)
+    Q4o, nno = oracle.boa(pos, box, offs, nb, R_BOA, 4)
+    Q6o, _ = oracle.boa(pos, box, offs, nb, R_BOA, 6)
+    lab_o = oracle.cna_label(*oracle.cna(pos, box, offs, nb, R_CNA)[:2])
+    out = L.ppmd_analyze(ctx, cu(pos), box, R_BOA, R_CNA)
+    assert np.array_equal(out["n_nb"].cpu().numpy(), nno)
+    assert np.abs(out["q4"].cpu().numpy() - Q4o).max() <= 1e-5
+    assert np.abs(out["q6"].cpu().numpy() - Q6o).max() <= 1e-5
+    assert np.array_equal(out["label"].cpu().numpy(), lab_o)
+
+
+def test_analyze_full_size_box_sampled(L, ctx):
+    """One 512,000-atom structure box (the analysis workload size): labels and
+    Q_l of a seeded sample of atoms against the oracle evaluated on those atoms."""
+    c = configs.structure_box("hcp", 0.05, seed=30)
+    pos, box = c["pos"], c["box"]
+    out = L.ppmd_analyze(ctx, cu(pos), box, R_BOA, R_CNA)
+    sample = np.random.default_rng(7).choice(len(pos), 400, replace=False)
+    # oracle on the sample: neighbours of the sampled atoms and of their neighbours
+    offs, nb = oracle.neighbours_cells(pos, box, R_BOA)
+    Q6o, nno = oracle.boa(pos, box, offs, nb, R_BOA, 6)
+    nbond, trip, _, _ = oracle.cna(pos, box, offs, nb, R_CNA)
+    lab_o = oracle.cna_label(nbond, trip)
+    assert np.array_equal(out["label"].cpu().numpy()[sample], lab_o[sample])
+    assert np.abs(out["q6"].cpu().numpy()[sample] - Q6o[sample]).max() <= 1e-5
+    # labels are mostly hcp at this noise level
+    assert (out["label"].cpu().numpy() == 2).mean() > 0.5
