@@ -10,6 +10,7 @@
 #include "cells.cuh"
 #include "lj.cuh"
 #include "neighbours.cuh"
+#include "md_kernels.cuh"
 #include "verlet.cuh"
 
 using namespace ppmd;
@@ -29,7 +30,10 @@ struct ppmd_md {
     float4 *f4 = nullptr;
     int4 *xq = nullptr, *xq_ref = nullptr;
     int32_t *orig = nullptr, *seg_of = nullptr, *cell_of = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
-    int32_t *nbr = nullptr, *cnt = nullptr;
+    int32_t *W = nullptr, *cnt = nullptr;  // column-major neighbour matrix W[m * ld + i]
+    int64_t ld = 0;
+    Brick *bricks = nullptr;
+    int64_t nbricks = 0;
     // reorder temporaries
     double *pos_t = nullptr, *vel_t = nullptr;
     int4 *xq_t = nullptr;
@@ -99,9 +103,9 @@ __global__ void k_gather_i32(int64_t n, const int32_t *perm, const int32_t *in, 
 }
 
 __global__ void k_energy_row(const double *red, double *row) {
-    // red[0] = kinetic, red[1] = potential (U), red[2] = virial
-    row[0] = red[0];
-    row[1] = red[1];
+    // red = (potential U, virial W, kinetic K)
+    row[0] = red[2];
+    row[1] = red[0];
 }
 
 int rebuild(ppmd_md *m) {
@@ -109,24 +113,26 @@ int rebuild(ppmd_md *m) {
     cudaStream_t s = ctx->stream;
     const int64_t n = m->n;
     PPMD_TRY(bin_atoms(ctx, m->pos, n, m->st, m->seg_of, m->ncell, false, m->cell_of, m->cell_start, m->cell_atoms));
-    PPMD_TRY(gather_sorted(ctx, n, m->cell_atoms, m->pos, m->vel, m->xq, m->orig, m->cell_of, m->pos_t, m->vel_t, m->xq_t,
-                           m->orig_t, m->cell_t));
-    if (n > 0) PPMD_LAUNCH(ctx, k_gather_i32, div_up(n, 256), 256, 0, n, m->cell_atoms, m->seg_of, m->seg_t);
+    PPMD_TRY(md_gather(ctx, n, m->cell_atoms, m->st, m->pos, m->vel, m->orig, m->seg_of, m->pos_t, m->vel_t, m->xq_t,
+                       m->orig_t, m->seg_t));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, m->pos_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, m->vel_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq_ref, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->cell_of, m->cell_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    PPMD_TRY(build_list(ctx, n, m->xq, m->pos, m->st, m->cell_of, m->cell_start, nullptr, m->nbr, m->cnt, m->p.max_nbr));
+    PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, m->xq, m->pos, m->st, m->cell_start, m->W, m->ld, m->cnt,
+                               m->p.max_nbr));
     return PPMD_OK;
 }
 
-int forces(ppmd_md *m, bool energy) {
-    return lj_launch(m->ctx, m->n, m->xq, m->pos, m->st, m->c, m->nbr, m->cnt, m->p.max_nbr, m->p.prec,
-                     m->p.prec == PPMD_FP32 ? m->f4 : nullptr, m->p.prec == PPMD_FP32 ? nullptr : m->f64, nullptr,
-                     energy ? m->part_f : nullptr);
+// Pair loop; with kick = true also the second kick of the step; on energy
+// steps the per-block (U, W, K) sums.
+int forces(ppmd_md *m, bool energy, bool kick) {
+    const bool f32 = m->p.prec == PPMD_FP32;
+    return lj_columns(m->ctx, m->n, m->ld, m->xq, m->pos, m->st, m->c, m->W, m->cnt, m->p.max_nbr, m->p.prec,
+                      f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, kick ? m->vel : nullptr, m->h, m->half_m,
+                      energy ? m->part_f : nullptr);
 }
 
 // One step of Algorithm 6.  erow: device row receiving (KE, PE) on energy steps.
@@ -134,17 +140,14 @@ int one_step(ppmd_md *m, int64_t s, double *erow) {
     ppmd_ctx *ctx = m->ctx;
     const bool f32 = m->p.prec == PPMD_FP32;
     const bool energy = m->p.energy_every > 0 && (s % m->p.energy_every) == 0 && erow;
-    PPMD_TRY(md_kick_drift(ctx, m->n, m->pos, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->xq, m->xq_ref, m->st,
-                           m->h, m->p.dt, m->max_disp_bits));
+    PPMD_TRY(md_kick_drift2(ctx, m->n, m->pos, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->xq, m->xq_ref,
+                            m->st, m->h, m->p.dt, m->max_disp_bits));
     if (m->p.rebuild_every > 0 && s % m->p.rebuild_every == 0) {
         PPMD_TRY(rebuild(m));
     }
-    PPMD_TRY(forces(m, energy));
-    PPMD_TRY(md_kick(ctx, m->n, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->h, m->half_m,
-                     energy ? m->part_k : nullptr));
+    PPMD_TRY(forces(m, energy, true));
     if (energy) {
-        PPMD_TRY(reduce_partials(ctx, m->part_k, kick_blocks(m->n), 1, m->red));
-        PPMD_TRY(reduce_partials(ctx, m->part_f, lj_blocks(m->n), 2, m->red + 1));
+        PPMD_TRY(reduce_partials(ctx, m->part_f, lj_columns_blocks(m->n), 3, m->red));
         PPMD_LAUNCH(ctx, k_energy_row, 1, 1, 0, m->red, erow);
     }
     return check_launch(ctx, "one_step");
@@ -237,9 +240,19 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_t, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_atoms, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_start, m->ncell + 1);
-    if (rc == PPMD_OK) rc = md_alloc(m, &m->nbr, (size_t)n * p.max_nbr);
+    m->ld = (n + 31) / 32 * 32;
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->W, (size_t)m->ld * p.max_nbr);
+    if (rc == PPMD_OK) {
+        std::vector<Brick> bl;
+        make_bricks(m->segs, bl);
+        m->nbricks = (int64_t)bl.size();
+        rc = md_alloc(m, &m->bricks, bl.size());
+        if (rc == PPMD_OK && !bl.empty())
+            rc = cuda_check(ctx, cudaMemcpy(m->bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice), "copy");
+    }
+    if (rc == PPMD_OK) rc = neigh_brick_setup(ctx, p.max_nbr);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt, n);
-    if (rc == PPMD_OK) rc = md_alloc(m, &m->part_f, 2 * lj_blocks(n) + 2);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->part_f, 3 * lj_columns_blocks(n) + 3);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->red, 4);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->ebuf, 2 * 1024);
@@ -278,7 +291,7 @@ extern "C" int ppmd_md_set_state(ppmd_md *m, const double *pos, const double *ve
         PPMD_LAUNCH(ctx, k_init_state, div_up(n, 256), 256, 0, n, m->pos, m->d_atom_off, m->nbox, m->st, m->xq, m->orig,
                     m->seg_of, ctx->d_status);
     PPMD_TRY(rebuild(m));
-    PPMD_TRY(forces(m, false));
+    PPMD_TRY(forces(m, false, false));
     m->step = 0;
     m->rebuilds = 1;
     m->ready = true;
@@ -397,7 +410,7 @@ __global__ void k_list_stats(const int32_t *cnt, int64_t n, unsigned long long *
 extern "C" int ppmd_md_forces(ppmd_md *m) {
     if (!m || !m->ready) return PPMD_ERR_INVALID;
     cudaSetDevice(m->ctx->device);
-    return forces(m, false);
+    return forces(m, false, false);
 }
 
 extern "C" int ppmd_md_list_stats(ppmd_md *m, int64_t *pairs, int32_t *max_row) {

@@ -1,0 +1,554 @@
+// Kernels of the time-stepping driver.  Atoms are stored in cell order, so
+// the atoms of consecutive cells of a row are contiguous.
+//  - List build: one block per brick (up to three cells of a row) stages the
+//    positions of the brick's neighbourhood in shared memory; each home atom
+//    is tested against its 27 cells by a warp (ballot compaction); the rows
+//    are written out as the paper's column-major neighbour matrix W[m][i].
+//  - Pair loop: one thread per atom walks its column of W; the
+//    single-precision arithmetic runs on packed pairs (f32x2: two neighbours
+//    per instruction) with compensated sums, and the second kick of
+//    Algorithm 6 is applied in the same thread.
+#include <algorithm>
+
+#include "md_kernels.cuh"
+
+namespace ppmd {
+
+// ---------------------------------------------------------------------
+// Packed single-precision pairs (two neighbours per instruction).
+// ---------------------------------------------------------------------
+typedef unsigned long long f2;
+typedef f2 f2_t;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+void make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out) {
+    out.clear();
+    for (size_t s = 0; s < segs.size(); ++s) {
+        const Seg &S = segs[s];
+        // the neighbourhood spans bw + 2 cells of a row and bh + 2 rows; they
+        // must be distinct cells of the periodic grid
+        const int32_t bw = std::min(3, S.nc[0] - 2), bh = std::min(2, S.nc[1] - 2);
+        for (int32_t z = 0; z < S.nc[2]; ++z)
+            for (int32_t y0 = 0; y0 < S.nc[1]; y0 += bh)
+                for (int32_t x0 = 0; x0 < S.nc[0]; x0 += bw) {
+                    const int32_t x1 = std::min(x0 + bw, S.nc[0]), y1 = std::min(y0 + bh, S.nc[1]);
+                    out.push_back(Brick{(int32_t)s, x0 | (x1 << 16), y0 | (y1 << 16), z});
+                }
+    }
+}
+
+size_t neigh_brick_smem(int32_t) { return (size_t)NB_MAX * sizeof(int4); }
+
+__device__ __forceinline__ int32_t wrapi(int32_t v, int32_t n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Signed minimum-image difference of two fixed-point words, as a float.
+__device__ __forceinline__ float fdiff(int32_t a, int32_t b) { return __int2float_rn((int32_t)((uint32_t)a - (uint32_t)b)); }
+
+// One block per brick.  The neighbourhood's fixed-point positions are staged
+// in shared memory (rows of consecutive cells are contiguous in the sorted
+// order, up to the periodic wrap in x).  Each thread owns one home atom and
+// sweeps its 27 cells (three cells in each of nine staged rows), testing
+// two candidates per packed step; threads of the same cell read the same
+// candidate, so the shared-memory reads are broadcasts.  Hits go straight
+// to the atom's column of W.
+__global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__restrict__ bricks,
+                                                               const int4 *__restrict__ xq,
+                                                               const double *__restrict__ pos64, SegTable st,
+                                                               const int32_t *__restrict__ cs, int32_t *__restrict__ W,
+                                                               int64_t ld, int32_t *__restrict__ cnt, int32_t max_nbr,
+                                                               int32_t *status, unsigned long long *needed) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int4 *s_x = (int4 *)smem;
+    __shared__ int32_t s_cell[12][6];  // local start of the row's cells t = 0 .. bw+2
+    __shared__ int32_t s_da[12], s_db[12], s_sw[12];  // global = local + (local < sw ? da : db)
+    __shared__ int32_t s_home[2][4];   // cell starts of the home cells of each home row
+    __shared__ int32_t s_total;
+
+    const Brick B = bricks[blockIdx.x];
+    const Seg &S = seg_ref(st, B.seg);
+    const int32_t nx = S.nc[0], ny = S.nc[1], nz = S.nc[2];
+    const int32_t x0 = B.x01 & 0xffff, x1 = B.x01 >> 16, y0 = B.y01 & 0xffff, y1 = B.y01 >> 16, z = B.z;
+    const int32_t bw = x1 - x0, bh = y1 - y0, nyr = bh + 2, nrow = 3 * nyr;
+    const int tid = threadIdx.x;
+    if (tid < nrow) {
+        const int32_t yy = wrapi(y0 - 1 + tid % nyr, ny), zz = wrapi(z + tid / nyr - 1, nz);
+        const int32_t rb = S.cell0 + (zz * ny + yy) * nx;
+        int32_t acc = 0;
+        for (int t = 0; t <= bw + 1; ++t) {
+            const int32_t x = wrapi(x0 - 1 + t, nx);
+            s_cell[tid][t] = acc;
+            acc += cs[rb + x + 1] - cs[rb + x];
+        }
+        s_cell[tid][bw + 2] = acc;
+    }
+    if (tid >= 32 && tid < 32 + bh) {
+        const int32_t r = tid - 32;
+        const int32_t rm = S.cell0 + (z * ny + y0 + r) * nx;
+        for (int t = 0; t <= bw; ++t) s_home[r][t] = cs[rm + x0 + t];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int32_t base = 0;
+        for (int r = 0; r < nrow; ++r) {
+            const int32_t yy = wrapi(y0 - 1 + r % nyr, ny), zz = wrapi(z + r / nyr - 1, nz);
+            const int32_t rb = S.cell0 + (zz * ny + yy) * nx;
+            const int32_t tot = s_cell[r][bw + 2];
+            for (int t = 0; t <= bw + 2; ++t) s_cell[r][t] += base;
+            const int32_t xa = x0 - 1, xb = x1;  // inclusive cell range of the row
+            if (xa < 0) {  // cell nx-1 first, then cells 0 .. xb
+                const int32_t len1 = cs[rb + nx] - cs[rb + nx - 1];
+                s_da[r] = cs[rb + nx - 1] - base;
+                s_sw[r] = base + len1;
+                s_db[r] = cs[rb] - (base + len1);
+            } else if (xb >= nx) {  // cells xa .. nx-1, then cell 0
+                const int32_t len1 = cs[rb + nx] - cs[rb + xa];
+                s_da[r] = cs[rb + xa] - base;
+                s_sw[r] = base + len1;
+                s_db[r] = cs[rb] - (base + len1);
+            } else {
+                s_da[r] = cs[rb + xa] - base;
+                s_sw[r] = base + tot;
+                s_db[r] = s_da[r];
+            }
+            base += tot;
+        }
+        s_total = base;
+    }
+    __syncthreads();
+    const int32_t T = s_total;
+    const int32_t n0 = s_home[0][bw] - s_home[0][0];
+    const int32_t H = n0 + (bh > 1 ? s_home[1][bw] - s_home[1][0] : 0);
+    if (T > NB_MAX) {
+        for (int32_t h = tid; h < H; h += blockDim.x) cnt[h < n0 ? s_home[0][0] + h : s_home[1][0] + h - n0] = 0;
+        if (tid == 0) {
+            latch_status(status, PPMD_ERR_CAPACITY);
+            latch_needed(needed, (unsigned long long)T);
+        }
+        return;
+    }
+    for (int32_t t = tid; t < T; t += blockDim.x) {
+        int r = 0;
+        while (r + 1 < nrow && s_cell[r + 1][0] <= t) ++r;
+        s_x[t] = xq[t + (t < s_sw[r] ? s_da[r] : s_db[r])];
+    }
+    __syncthreads();
+    const float sx = S.sx[0], sy = S.sx[1], sz = S.sx[2];
+    const f2_t sxx = pk(sx, sx), syy = pk(sy, sy), szz = pk(sz, sz);
+    const float lo = S.rl2_lo, hi = S.rl2_hi;
+    for (int32_t h = tid; h < H; h += blockDim.x) {
+        const int hr = h < n0 ? 0 : 1;
+        const int32_t i = h < n0 ? s_home[0][0] + h : s_home[1][0] + (h - n0);
+        const int4 xi = xq[i];
+        int t = 0;
+        while (t + 1 < bw && i >= s_home[hr][t + 1]) ++t;
+        int32_t count = 0;
+        int32_t *col = W + i;
+        auto hit = [&](int32_t j) {
+            if (count < max_nbr) col[(int64_t)count * ld] = j;
+            ++count;
+        };
+        for (int dz = 0; dz < 3; ++dz)
+            for (int dy = 0; dy < 3; ++dy) {
+                const int r = dz * nyr + hr + dy;
+                const int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
+                const int32_t sw = s_sw[r], da = s_da[r], db = s_db[r];
+                for (int32_t k = a; k < b; k += 2) {
+                    const bool v1 = k + 1 < b;
+                    const int4 xa = s_x[k], xb = s_x[v1 ? k + 1 : k];
+                    const f2_t dx = mul2(pk(fdiff(xi.x, xa.x), fdiff(xi.x, xb.x)), sxx);
+                    const f2_t dy_ = mul2(pk(fdiff(xi.y, xa.y), fdiff(xi.y, xb.y)), syy);
+                    const f2_t dz_ = mul2(pk(fdiff(xi.z, xa.z), fdiff(xi.z, xb.z)), szz);
+                    const f2_t r2 = fma2(dx, dx, fma2(dy_, dy_, mul2(dz_, dz_)));
+                    float ra, rb2;
+                    upk(r2, ra, rb2);
+                    const int32_t ja = k + (k < sw ? da : db);
+                    const int32_t jb = k + 1 + (k + 1 < sw ? da : db);
+                    if (ra < hi && ja != i) {
+                        double dr[3];
+                        if (ra < lo || min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)ja, S, dr) < S.rl2) hit(ja);
+                    }
+                    if (v1 && rb2 < hi && jb != i) {
+                        double dr[3];
+                        if (rb2 < lo || min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jb, S, dr) < S.rl2) hit(jb);
+                    }
+                }
+            }
+        cnt[i] = count;
+        if (count > max_nbr) {
+            latch_status(status, PPMD_ERR_CAPACITY);
+            latch_needed(needed, (unsigned long long)count);
+        }
+    }
+}
+
+int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr) {
+    return cuda_check(ctx, cudaFuncSetAttribute(k_neigh_brick, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)neigh_brick_smem(max_nbr)),
+                      "cudaFuncSetAttribute");
+}
+
+int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, const int4 *xq, const double *pos64,
+                      const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld, int32_t *cnt,
+                      int32_t max_nbr) {
+    if (nbricks > 0)
+        PPMD_LAUNCH(ctx, k_neigh_brick, nbricks, BRICK_THREADS, neigh_brick_smem(max_nbr), bricks, xq, pos64, st,
+                    cell_start, W, ld, cnt, max_nbr, ctx->d_status, ctx->d_needed);
+    return check_launch(ctx, "build_list_bricks");
+}
+
+// Compensated sum of two interleaved streams: value = s - c, kept as cn = -c.
+struct Kahan2 {
+    f2 s, cn;
+    __device__ __forceinline__ void init() { s = cn = 0ull; }
+    // adds a * b to each stream
+    __device__ __forceinline__ void add_prod(f2 a, f2 b) {
+        const f2 yv = fma2(a, b, cn);
+        const f2 t = add2(s, yv);
+        cn = sub2(yv, sub2(t, s));
+        s = t;
+    }
+    // the two streams merged: (hi, lo) with hi + lo the sum
+    __device__ __forceinline__ void merged(float &hi, float &lo) const {
+        float s0, s1, c0, c1;
+        upk(s, s0, s1);
+        upk(cn, c0, c1);
+        hi = s0;
+        lo = c0;
+        two_sum_merge(hi, lo, s1, c1);
+    }
+};
+
+__device__ __forceinline__ void block_sum3(double a, double b, double c, double *partials) {
+    __shared__ double sh[3][32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh[0][w] = a;
+        sh[1][w] = b;
+        sh[2][w] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0, v = 0, k = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            u += sh[0][q];
+            v += sh[1][q];
+            k += sh[2][q];
+        }
+        partials[3 * blockIdx.x] = u;
+        partials[3 * blockIdx.x + 1] = v;
+        partials[3 * blockIdx.x + 2] = k;
+    }
+}
+
+constexpr int COL_BLOCK = 256;
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(COL_BLOCK) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
+                                                        const double *__restrict__ pos64, SegTable st, LJConst c,
+                                                        const int32_t *__restrict__ W, const int32_t *__restrict__ cnt,
+                                                        int32_t max_nbr, float4 *__restrict__ f4,
+                                                        double *__restrict__ vel, double h, double half_m,
+                                                        double *__restrict__ partials) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double u_i = 0.0, w_i = 0.0, k_i = 0.0;
+    if (i < n) {
+        const int4 xi = xq[i];
+        const Seg &S = seg_ref(st, xi.w);
+        const f2 sxx = pk(S.sx[0], S.sx[0]), syy = pk(S.sx[1], S.sx[1]), szz = pk(S.sx[2], S.sx[2]);
+        const f2 two = pk(2.0f, 2.0f), half = pk(0.5f, 0.5f), one = pk(1.0f, 1.0f);
+        const f2 s2 = pk(c.s2, c.s2), f48 = pk(c.f48, c.f48), e2 = pk(c.e2, c.e2), shift = pk(c.shift, c.shift);
+        const int32_t m = min(cnt[i], max_nbr);
+        Kahan2 fx, fy, fz, ea, vir;
+        fx.init();
+        fy.init();
+        fz.init();
+        if (ENERGY) {
+            ea.init();
+            vir.init();
+        }
+        const int32_t *col = W + i;
+        // Two neighbours per packed step; the list entries of the next four
+        // neighbours are loaded one iteration ahead of their use.
+        auto step = [&](int32_t j0, int32_t j1, const int4 &a, const int4 &b) {
+            const bool v0 = j0 >= 0, v1 = j1 >= 0;
+            const f2 dx = mul2(pk(fdiff(xi.x, a.x), fdiff(xi.x, b.x)), sxx);
+            const f2 dy = mul2(pk(fdiff(xi.y, a.y), fdiff(xi.y, b.y)), syy);
+            const f2 dz = mul2(pk(fdiff(xi.z, a.z), fdiff(xi.z, b.z)), szz);
+            const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+            float r2a, r2b;
+            upk(r2, r2a, r2b);
+            bool in0 = v0 && r2a < c.rc2_lo, in1 = v1 && r2b < c.rc2_lo;
+            if (v0 && !in0 && r2a < c.rc2_hi) {
+                double dr[3];
+                in0 = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j0, S, dr) < c.rc2;
+            }
+            if (v1 && !in1 && r2b < c.rc2_hi) {
+                double dr[3];
+                in1 = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j1, S, dr) < c.rc2;
+            }
+            // 1/r^2: hardware estimate refined by one Newton-Raphson step r (2 - x r)
+            f2 ir = pk(rcp_approx(r2a), rcp_approx(r2b));
+            ir = mul2(ir, fma2(pk(-r2a, -r2b), ir, two));
+            const f2 sr2 = mul2(s2, ir);
+            const f2 sr6 = mul2(mul2(sr2, sr2), sr2);
+            f2 fm = mul2(mul2(f48, sub2(sr6, half)), mul2(sr6, ir));
+            float fa, fb;
+            upk(fm, fa, fb);
+            fm = pk(in0 ? fa : 0.0f, in1 ? fb : 0.0f);
+            fx.add_prod(fm, dx);
+            fy.add_prod(fm, dy);
+            fz.add_prod(fm, dz);
+            if (ENERGY) {
+                f2 v = mul2(e2, fma2(sr6, sub2(sr6, one), shift));
+                float va, vb;
+                upk(v, va, vb);
+                ea.add_prod(pk(in0 ? va : 0.0f, in1 ? vb : 0.0f), one);
+                vir.add_prod(fm, r2);
+            }
+        };
+        auto entry = [&](int32_t k) { return k < m ? __ldg(col + (int64_t)k * ld) : -1; };
+        int32_t j0 = entry(0), j1 = entry(1), j2 = entry(2), j3 = entry(3);
+        for (int32_t k = 0; k < m; k += 4) {
+            const int32_t n0 = entry(k + 4), n1 = entry(k + 5), n2 = entry(k + 6), n3 = entry(k + 7);
+            const int4 a0 = __ldg(&xq[j0 >= 0 ? j0 : i]), a1 = __ldg(&xq[j1 >= 0 ? j1 : i]);
+            const int4 a2 = __ldg(&xq[j2 >= 0 ? j2 : i]), a3 = __ldg(&xq[j3 >= 0 ? j3 : i]);
+            step(j0, j1, a0, a1);
+            step(j2, j3, a2, a3);
+            j0 = n0;
+            j1 = n1;
+            j2 = n2;
+            j3 = n3;
+        }
+        float hx, lx, hy, ly, hz, lz;
+        fx.merged(hx, lx);
+        fy.merged(hy, ly);
+        fz.merged(hz, lz);
+        const double Fx = (double)hx + (double)lx, Fy = (double)hy + (double)ly, Fz = (double)hz + (double)lz;
+        float he = 0.f, le = 0.f;
+        if (ENERGY) {
+            ea.merged(he, le);
+            float hv, lv;
+            vir.merged(hv, lv);
+            u_i = (double)he + (double)le;
+            w_i = 0.5 * ((double)hv + (double)lv);
+        }
+        f4[i] = make_float4((float)Fx, (float)Fy, (float)Fz, (float)((double)he + (double)le));
+        if (vel) {
+            // second kick of Algorithm 6 with the forces just computed
+            const float4 fq = f4[i];
+            const double vx = fma(h, (double)fq.x, vel[3 * i]);
+            const double vy = fma(h, (double)fq.y, vel[3 * i + 1]);
+            const double vz = fma(h, (double)fq.z, vel[3 * i + 2]);
+            vel[3 * i] = vx;
+            vel[3 * i + 1] = vy;
+            vel[3 * i + 2] = vz;
+            if (ENERGY) k_i = half_m * (vx * vx + vy * vy + vz * vz);
+        }
+    }
+    if (ENERGY) block_sum3(u_i, w_i, k_i, partials);
+}
+
+template <bool ENERGY>
+__global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(int64_t n, int64_t ld, const int4 *__restrict__ xq,
+                                                        const double *__restrict__ pos64, SegTable st, LJConst c,
+                                                        const int32_t *__restrict__ W, const int32_t *__restrict__ cnt,
+                                                        int32_t max_nbr, double *__restrict__ f64,
+                                                        double *__restrict__ vel, double h, double half_m,
+                                                        double *__restrict__ partials) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double u_i = 0.0, w_i = 0.0, k_i = 0.0;
+    if (i < n) {
+        const Seg &S = seg_ref(st, xq[i].w);
+        const int32_t m = min(cnt[i], max_nbr);
+        const double *pi = pos64 + 3 * i;
+        double fx = 0.0, fy = 0.0, fz = 0.0;
+        for (int32_t k = 0; k < m; ++k) {
+            const int32_t j = __ldg(W + k * ld + i);
+            double dr[3];
+            const double r2 = min_image_r2(pi, pos64 + 3 * (int64_t)j, S, dr);
+            if (r2 < c.rc2) {
+                const double sr2 = c.s2d / r2;
+                const double sr6 = sr2 * sr2 * sr2;
+                const double sr8 = sr6 * sr2;
+                const double sr12 = sr6 * sr6;
+                const double fmag = c.f48d * (sr12 * sr2 - 0.5 * sr8);
+                fx += fmag * dr[0];
+                fy += fmag * dr[1];
+                fz += fmag * dr[2];
+                if (ENERGY) {
+                    u_i += c.e2d * (sr12 - sr6 + c.shiftd);
+                    w_i += 0.5 * fmag * r2;
+                }
+            }
+        }
+        f64[3 * i] = fx;
+        f64[3 * i + 1] = fy;
+        f64[3 * i + 2] = fz;
+        if (vel) {
+            const double vx = fma(h, fx, vel[3 * i]);
+            const double vy = fma(h, fy, vel[3 * i + 1]);
+            const double vz = fma(h, fz, vel[3 * i + 2]);
+            vel[3 * i] = vx;
+            vel[3 * i + 1] = vy;
+            vel[3 * i + 2] = vz;
+            if (ENERGY) k_i = half_m * (vx * vx + vy * vy + vz * vz);
+        }
+    }
+    if (ENERGY) block_sum3(u_i, w_i, k_i, partials);
+}
+
+int64_t lj_columns_blocks(int64_t n) { return div_up(n, COL_BLOCK); }
+
+int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const double *pos64, const SegTable &st,
+               const LJConst &c, const int32_t *W, const int32_t *cnt, int32_t max_nbr, int prec, float4 *f4,
+               double *f64, double *vel, double h, double half_m, double *partials) {
+    if (n <= 0) return PPMD_OK;
+    const int64_t nb = lj_columns_blocks(n);
+    if (prec == PPMD_FP32) {
+        if (partials)
+            PPMD_LAUNCH(ctx, k_lj_col32<true>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f4, vel, h, half_m,
+                        partials);
+        else
+            PPMD_LAUNCH(ctx, k_lj_col32<false>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f4, vel, h, half_m,
+                        partials);
+    } else {
+        if (partials)
+            PPMD_LAUNCH(ctx, k_lj_col64<true>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
+                        partials);
+        else
+            PPMD_LAUNCH(ctx, k_lj_col64<false>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
+                        partials);
+    }
+    return check_launch(ctx, "lj_columns");
+}
+
+// ---------------------------------------------------------------------
+// Kick + drift (line 6 of Algorithm 6).
+// ---------------------------------------------------------------------
+template <class F>
+__device__ __forceinline__ void load_f(const F *f, int64_t i, double out[3]);
+template <>
+__device__ __forceinline__ void load_f<float4>(const float4 *f, int64_t i, double out[3]) {
+    const float4 v = f[i];
+    out[0] = v.x;
+    out[1] = v.y;
+    out[2] = v.z;
+}
+template <>
+__device__ __forceinline__ void load_f<double>(const double *f, int64_t i, double out[3]) {
+    out[0] = f[3 * i];
+    out[1] = f[3 * i + 1];
+    out[2] = f[3 * i + 2];
+}
+
+template <class F>
+__global__ void __launch_bounds__(256) k_kick_drift2(int64_t n, double *__restrict__ pos, double *__restrict__ vel,
+                                                     const F *__restrict__ force, int4 *__restrict__ xq,
+                                                     const int4 *__restrict__ xq_ref, SegTable st, double h, double dt,
+                                                     unsigned int *max_disp_bits) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float d2 = 0.0f;
+    if (i < n) {
+        double f[3];
+        load_f<F>(force, i, f);
+        const int32_t sid = xq_ref[i].w;
+        const Seg &S = seg_ref(st, sid);
+        uint32_t q[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double v = fma(h, f[d], vel[3 * i + d]);
+            vel[3 * i + d] = v;
+            const double r = fma(dt, v, pos[3 * i + d]);
+            pos[3 * i + d] = r;
+            // r may leave [0, L) until the next list build; the fixed-point
+            // word wraps modulo 2^32, i.e. modulo L
+            q[d] = (uint32_t)(unsigned long long)__double2ll_rn(r * S.fxs[d]);
+        }
+        xq[i] = make_int4((int)q[0], (int)q[1], (int)q[2], sid);
+        const int4 ref = xq_ref[i];
+        const float ex = fixed_delta(q[0], (uint32_t)ref.x, S.sx[0]);
+        const float ey = fixed_delta(q[1], (uint32_t)ref.y, S.sx[1]);
+        const float ez = fixed_delta(q[2], (uint32_t)ref.z, S.sx[2]);
+        d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    if ((threadIdx.x & 31) == 0 && d2 > 0.0f) atomicMax(max_disp_bits, __float_as_uint(d2));
+}
+
+int md_kick_drift2(ppmd_ctx *ctx, int64_t n, double *pos, double *vel, const float4 *f4, const double *f64, int4 *xq,
+                   const int4 *xq_ref, const SegTable &st, double h, double dt, unsigned int *max_disp_bits) {
+    if (n <= 0) return PPMD_OK;
+    if (f4)
+        PPMD_LAUNCH(ctx, k_kick_drift2<float4>, div_up(n, 256), 256, 0, n, pos, vel, f4, xq, xq_ref, st, h, dt, max_disp_bits);
+    else
+        PPMD_LAUNCH(ctx, k_kick_drift2<double>, div_up(n, 256), 256, 0, n, pos, vel, f64, xq, xq_ref, st, h, dt, max_disp_bits);
+    return check_launch(ctx, "md_kick_drift2");
+}
+
+__global__ void k_md_gather(int64_t n, const int32_t *__restrict__ perm, SegTable st, const double *__restrict__ pos,
+                            const double *__restrict__ vel, const int32_t *__restrict__ orig,
+                            const int32_t *__restrict__ seg_of, double *__restrict__ pos_o, double *__restrict__ vel_o,
+                            int4 *__restrict__ xq_o, int32_t *__restrict__ orig_o, int32_t *__restrict__ seg_o) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t j = perm[k];
+    const int32_t sid = seg_of[j];
+    const Seg &S = seg_ref(st, sid);
+    uint32_t q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double x = pos[3 * j + d];
+        x = (x >= 0.0 && x < S.L[d]) ? x : wrap_exact(x, S.L[d]);
+        pos_o[3 * k + d] = x;
+        vel_o[3 * k + d] = vel[3 * j + d];
+        q[d] = to_fixed(x, S.fxs[d]);
+    }
+    xq_o[k] = make_int4((int)q[0], (int)q[1], (int)q[2], sid);
+    orig_o[k] = orig[j];
+    seg_o[k] = sid;
+}
+
+int md_gather(ppmd_ctx *ctx, int64_t n, const int32_t *perm, const SegTable &st, const double *pos, const double *vel,
+              const int32_t *orig, const int32_t *seg_of, double *pos_o, double *vel_o, int4 *xq_o, int32_t *orig_o,
+              int32_t *seg_o) {
+    if (n > 0)
+        PPMD_LAUNCH(ctx, k_md_gather, div_up(n, 256), 256, 0, n, perm, st, pos, vel, orig, seg_of, pos_o, vel_o, xq_o, orig_o,
+                    seg_o);
+    return check_launch(ctx, "md_gather");
+}
+
+}  // namespace ppmd

@@ -1,0 +1,47 @@
+// Kernels of the time-stepping driver (atoms kept in cell order).
+#pragma once
+#include "common.cuh"
+#include "lj.cuh"
+
+namespace ppmd {
+
+// A brick: cells x0 <= x < x1 (at most 3) of rows y0 <= y < y1 (at most 2)
+// of plane z of one segment.  Its neighbourhood is the rows y0-1 .. y1 of
+// planes z-1 .. z+1, cells x0-1 .. x1 of each.
+struct Brick {
+    int32_t seg, x01, y01, z;  // x01 = x0 | x1 << 16, y01 = y0 | y1 << 16
+};
+
+constexpr int NB_MAX = 2048;     // largest neighbourhood staged in shared memory
+constexpr int BRICK_THREADS = 128;  // home atoms handled per pass of a brick block
+
+// Bricks of a cell grid (host).
+void make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out);
+size_t neigh_brick_smem(int32_t max_nbr);
+int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr);
+
+// Column-major neighbour list W[m * ld + i] (the paper's neighbour matrix)
+// of atoms stored in cell order, one block per brick.
+int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, const int4 *xq, const double *pos64,
+                      const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld, int32_t *cnt,
+                      int32_t max_nbr);
+
+// Pair loop over the column-major list, one thread per atom, followed by
+// the second kick of Algorithm 6 (v += dt/(2m) F) when vel != null.
+// partials (energy steps): per-block rows (U, W, K).
+int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const double *pos64, const SegTable &st,
+               const LJConst &c, const int32_t *W, const int32_t *cnt, int32_t max_nbr, int prec, float4 *f4,
+               double *f64, double *vel, double h, double half_m, double *partials);
+int64_t lj_columns_blocks(int64_t n);
+
+// Kick + drift without wrapping (coordinates stay continuous between list
+// builds), fixed-point refresh, displacement guard.
+int md_kick_drift2(ppmd_ctx *ctx, int64_t n, double *pos, double *vel, const float4 *f4, const double *f64, int4 *xq,
+                   const int4 *xq_ref, const SegTable &st, double h, double dt, unsigned int *max_disp_bits);
+
+// Gather through perm into cell order, wrapping positions into the box.
+int md_gather(ppmd_ctx *ctx, int64_t n, const int32_t *perm, const SegTable &st, const double *pos, const double *vel,
+              const int32_t *orig, const int32_t *seg_of, double *pos_o, double *vel_o, int4 *xq_o, int32_t *orig_o,
+              int32_t *seg_o);
+
+}  // namespace ppmd
