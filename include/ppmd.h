@@ -192,6 +192,50 @@ int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *bo
                  float *q4, float *q6, int32_t *n_nb, int8_t *label);
 
 /* ------------------------------------------------------------------ */
+/* Learned structure classifier (not in the paper): an MLP 30 -> 64 -> 64
+ * -> 4 (ReLU, softmax over 0 other, 1 fcc, 2 hcp, 3 bcc) on local-
+ * environment features, trained on labels from ppmd_cna, with exact CNA as
+ * the fallback for low-confidence atoms.  Parameters are one FP32 device
+ * vector of PPMD_MLP_NPARAM values, laid out
+ *   W1[30][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
+ * with y = x W + b.  Arithmetic: BF16 inputs, weights and activations, FP32
+ * accumulation (tensor cores).                                          */
+/* ------------------------------------------------------------------ */
+#define PPMD_MLP_NPARAM 6404
+
+/* Features of every atom from its bonds (r < r_feat, the BOA cutoff):
+ * [0] Q4, [1] Q6 (Eqs. (1)-(2)); [2..15] the 14 smallest bond lengths / r_feat,
+ * ascending (missing: 1); [16..29] histogram of the bond-angle cosines over
+ * all bond pairs, 14 bins of width 1/7 on [-1, 1] with linear weights
+ * between bin centres, divided by the number of pairs.  Outputs (device, at
+ * least one given): feat[n][30] FP32, feat_bf16[n][32] BF16 (last two 0),
+ * caller order.  Synchronises once (list capacity check). */
+int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat, float *feat,
+                  uint16_t *feat_bf16);
+/* Logits [n][4] (FP32) of the BF16 feature rows x [n][32]. */
+int ppmd_mlp_forward(ppmd_ctx *ctx, const float *params, const uint16_t *x, int64_t n, float *logits);
+/* Gradient (FP32 [PPMD_MLP_NPARAM], device) of the mean cross entropy of
+ * the batch x [batch][32] (BF16), labels y [batch] (int8 class codes), and
+ * the loss (device float, may be NULL). */
+int ppmd_mlp_grad(ppmd_ctx *ctx, const float *params, const uint16_t *x, const int8_t *y, int64_t batch, float *grad,
+                  float *loss);
+/* One AdamW update (Loshchilov & Hutter; decay on the weight matrices only)
+ * of params with moments m, v (device, PPMD_MLP_NPARAM each), step >= 1. */
+int ppmd_mlp_adamw(ppmd_ctx *ctx, float *params, float *m, float *v, const float *grad, int64_t step, float lr,
+                   float wd, float beta1, float beta2, float eps);
+/* ppmd_mlp_grad followed by ppmd_mlp_adamw with beta = (0.9, 0.999), eps = 1e-8. */
+int ppmd_mlp_train_step(ppmd_ctx *ctx, float *params, float *m, float *v, int64_t step, const uint16_t *x,
+                        const int8_t *y, int64_t batch, float lr, float wd, float *loss);
+/* Structure labels of every atom (caller order, label[n] device int8).
+ * mode 0: exact CNA (cutoff r_cna).  mode 1: features (cutoff r_feat >=
+ * r_cna) -> MLP -> class and confidence (max softmax probability, device
+ * float [n], may be NULL); atoms with confidence < threshold are labelled
+ * by exact CNA instead.  n_fallback (host, may be NULL) receives the number
+ * of atoms labelled by CNA.  Synchronises. */
+int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t n, const ppmd_box *box, double r_feat, double r_cna,
+                  const float *params, float threshold, int8_t *label, float *confidence, int64_t *n_fallback);
+
+/* ------------------------------------------------------------------ */
 /* Time stepping (Algorithm 6 driven by the list-reuse policy of Sec. 3.5,
  * the paper's IntegratorRange), for one box or a batch of independent boxes
  * (replicas) advanced together.  The integrator keeps its own copy of the

@@ -68,6 +68,12 @@ _SIGS = {
     "ppmd_boa_q46": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, _I32, _P, _P, _P]),
     "ppmd_cna": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, _I32, _P, _P]),
     "ppmd_analyze": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _D, _P, _P, _P, _P]),
+    "ppmd_features": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P]),
+    "ppmd_mlp_forward": (_I, [_P, _P, _P, _I64, _P]),
+    "ppmd_mlp_grad": (_I, [_P, _P, _P, _P, _I64, _P, _P]),
+    "ppmd_mlp_adamw": (_I, [_P, _P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
+    "ppmd_mlp_train_step": (_I, [_P, _P, _P, _P, _I64, _P, _P, _I64, C.c_float, C.c_float, _P]),
+    "ppmd_classify": (_I, [_P, _I, _P, _I64, C.POINTER(Box), _D, _D, _P, C.c_float, _P, _P, C.POINTER(_I64)]),
     "ppmd_md_create": (_I, [_P, C.POINTER(_P), _I64, _P, _P, _P, C.POINTER(MDParams)]),
     "ppmd_md_destroy": (_I, [_P]),
     "ppmd_md_set_state": (_I, [_P, _P, _P]),
@@ -260,6 +266,56 @@ def ppmd_analyze(ctx: Context, pos, box, r_boa=1.5, r_cna=None, boa=True, cna=Tr
                                 _opt(out.get("q4")), _opt(out.get("q6")), _opt(out.get("n_nb")),
                                 _opt(out.get("label"))))
     return out
+
+
+MLP_NPARAM = 6404
+
+
+def ppmd_features(ctx: Context, pos, box, r_feat=1.5, fp32=True, bf16=False):
+    """Classifier features: float32 [n, 30] and/or bfloat16 [n, 32] (caller order)."""
+    n = pos.shape[0]
+    f = torch.empty((n, 30), dtype=torch.float32, device=pos.device) if fp32 else None
+    fb = torch.empty((n, 32), dtype=torch.bfloat16, device=pos.device) if bf16 else None
+    b = _box(box)
+    ctx.check(_lib.ppmd_features(ctx.h, _ptr(pos), n, C.byref(b), float(r_feat), _opt(f), _opt(fb)))
+    return f, fb
+
+
+def ppmd_mlp_forward(ctx: Context, params, x_bf16):
+    n = x_bf16.shape[0]
+    logits = torch.empty((n, 4), dtype=torch.float32, device=x_bf16.device)
+    ctx.check(_lib.ppmd_mlp_forward(ctx.h, _ptr(params), _ptr(x_bf16), n, _ptr(logits)))
+    return logits
+
+
+def ppmd_mlp_grad(ctx: Context, params, x_bf16, y):
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=params.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    ctx.check(_lib.ppmd_mlp_grad(ctx.h, _ptr(params), _ptr(x_bf16), _ptr(y), x_bf16.shape[0], _ptr(grad), _ptr(loss)))
+    return grad, loss
+
+
+def ppmd_mlp_adamw(ctx: Context, params, m, v, grad, step, lr=1e-3, wd=0.01, beta1=0.9, beta2=0.999, eps=1e-8):
+    ctx.check(_lib.ppmd_mlp_adamw(ctx.h, _ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), lr, wd, beta1, beta2,
+                                  eps))
+
+
+def ppmd_mlp_train_step(ctx: Context, params, m, v, step, x_bf16, y, lr=1e-3, wd=0.01, loss=None):
+    ctx.check(_lib.ppmd_mlp_train_step(ctx.h, _ptr(params), _ptr(m), _ptr(v), int(step), _ptr(x_bf16), _ptr(y),
+                                       x_bf16.shape[0], lr, wd, _opt(loss)))
+
+
+def ppmd_classify(ctx: Context, pos, box, mode=1, params=None, threshold=0.9, r_feat=1.5, r_cna=1.433625,
+                  want_confidence=True):
+    """Labels int8 [n], confidence float32 [n] (mode 1), number of CNA fallbacks."""
+    n = pos.shape[0]
+    lab = torch.empty(n, dtype=torch.int8, device=pos.device)
+    conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode == 1) else None
+    nfb = _I64(0)
+    b = _box(box)
+    ctx.check(_lib.ppmd_classify(ctx.h, int(mode), _ptr(pos), n, C.byref(b), float(r_feat), float(r_cna), _opt(params),
+                                 float(threshold), _ptr(lab), _opt(conf), C.byref(nfb)))
+    return lab, conf, nfb.value
 
 
 class MD:

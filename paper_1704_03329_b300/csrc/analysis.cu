@@ -5,6 +5,7 @@
 //    per atom on 64-bit adjacency masks of the atom's bonded neighbours;
 //  - an analysis pipeline that bins and sorts the atoms by cell, builds the
 //    list and runs either analysis, returning results in caller order.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "analysis.cuh"
@@ -181,14 +182,15 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
                                                         int32_t max_nbr, double rc2, float lo, float hi,
                                                         const int32_t *__restrict__ out_idx, uint32_t *__restrict__ trip,
                                                         int8_t *__restrict__ label, int32_t *status,
-                                                        unsigned long long *needed) {
+                                                        unsigned long long *needed, const int32_t *__restrict__ which) {
     __shared__ int32_t s_j[CNA_WARPS][64];
     __shared__ int32_t s_slot[CNA_WARPS][64];
     __shared__ int4 s_x[CNA_WARPS][64];
     __shared__ unsigned long long s_A[CNA_WARPS][64];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * CNA_WARPS + w;
-    if (i >= n) return;
+    const int64_t wi = (int64_t)blockIdx.x * CNA_WARPS + w;
+    if (wi >= n) return;
+    const int64_t i = which ? (int64_t)which[wi] : wi;  // a subset of the atoms when `which` is given
     const int4 xi = xq[i];
     const Seg &S = seg_ref(st, xi.w);
     const int32_t deg = min(cnt[i], max_nbr);
@@ -299,8 +301,174 @@ int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, co
     cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
     if (n > 0)
         PPMD_LAUNCH(ctx, k_cna, div_up(n, CNA_WARPS), CNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr, r_cut * r_cut,
-                    lo, hi, out_idx, trip, label, ctx->d_status, ctx->d_needed);
+                    lo, hi, out_idx, trip, label, ctx->d_status, ctx->d_needed, nullptr);
     return check_launch(ctx, "cna");
+}
+
+int cna_subset_launch(ppmd_ctx *ctx, int64_t m, const int32_t *which, const int4 *xq, const double *pos64,
+                      const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, double r_cut,
+                      double Lmax, int8_t *label) {
+    float lo, hi;
+    cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
+    if (m > 0)
+        PPMD_LAUNCH(ctx, k_cna, div_up(m, CNA_WARPS), CNA_WARPS * 32, 0, m, xq, pos64, st, nbr, cnt, max_nbr, r_cut * r_cut,
+                    lo, hi, nullptr, nullptr, label, ctx->d_status, ctx->d_needed, which);
+    return check_launch(ctx, "cna_subset");
+}
+
+
+// ---------------------------------------------------------------------
+// Local-environment features of the learned classifier, one warp per atom.
+// With nu bonds (r < r_feat) of unit vectors u_a and lengths d_a:
+//   f[0], f[1]   Q4, Q6 (as k_boa);
+//   f[2..15]     the 14 smallest d_a / r_feat, ascending (missing: 1);
+//   f[16..29]    histogram of cos(u_a, u_b) over all pairs a < b: 14 bins of
+//                width 1/7 on [-1, 1], linear weights between bin centres
+//                (clamped at both ends), divided by the number of pairs.
+// Output: f32 [n][30] and/or bf16 [n][32] (f[30], f[31] = 0).
+// ---------------------------------------------------------------------
+constexpr int FEAT_WARPS = 4;
+
+__global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const int4 *__restrict__ xq,
+                                                              const double *__restrict__ pos64, SegTable st,
+                                                              const int32_t *__restrict__ nbr,
+                                                              const int32_t *__restrict__ cnt, int32_t max_nbr,
+                                                              double rc2, float lo, float hi, float r_feat, YlmCoef K,
+                                                              const int32_t *__restrict__ out_idx,
+                                                              float *__restrict__ f32, __nv_bfloat16 *__restrict__ fb16,
+                                                              int32_t *status, unsigned long long *needed) {
+    __shared__ float3 s_u[FEAT_WARPS][64];
+    __shared__ float s_d[FEAT_WARPS][64];
+    __shared__ float s_f[FEAT_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * FEAT_WARPS + w;
+    if (i >= n) return;
+    const int4 xi = xq[i];
+    const Seg &S = seg_ref(st, xi.w);
+    const int32_t deg = min(cnt[i], max_nbr);
+    const int32_t *row = nbr + i * (int64_t)max_nbr;
+    const unsigned lt = (1u << lane) - 1u;
+    s_f[w][lane] = (lane >= 2 && lane < 16) ? 1.0f : 0.0f;
+    int32_t nu = 0;
+    for (int32_t base = 0; base < deg; base += 32) {
+        const int32_t k = base + lane;
+        bool b = false;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        if (k < deg) {
+            const int32_t j = row[k];
+            const int4 xj = xq[j];
+            dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj.x, S.sx[0]);
+            dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj.y, S.sx[1]);
+            dz = fixed_delta((uint32_t)xi.z, (uint32_t)xj.z, S.sx[2]);
+            r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            b = r2 < lo;
+            if (!b && r2 < hi) {
+                double dr[3];
+                b = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr) < rc2;
+            }
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, b);
+        if (b) {
+            const int32_t a = nu + __popc(ball & lt);
+            if (a < 64) {
+                const float r = sqrtf(r2), ir = 1.0f / r;
+                s_u[w][a] = make_float3(dx * ir, dy * ir, dz * ir);
+                s_d[w][a] = r;
+            }
+        }
+        nu += __popc(ball);
+    }
+    if (nu > 64) {
+        if (lane == 0) {
+            latch_status(status, PPMD_ERR_CAPACITY);
+            latch_needed(needed, (unsigned long long)nu);
+        }
+        nu = 64;
+    }
+    __syncwarp();
+    // Q4, Q6: each lane its bonds, then warp sums of the moments
+    float r4[5], i4[5], r6[7], i6[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+        if (m < 5) r4[m] = i4[m] = 0.0f;
+        r6[m] = i6[m] = 0.0f;
+    }
+    for (int a = lane; a < nu; a += 32) {
+        const float3 u = s_u[w][a];
+        boa_accumulate(K, u.x, u.y, u.z, r4, i4, r6, i6);
+    }
+    float s4 = 0.0f, s6 = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (m < 5) {
+                r4[m] += __shfl_xor_sync(0xffffffffu, r4[m], o);
+                i4[m] += __shfl_xor_sync(0xffffffffu, i4[m], o);
+            }
+            r6[m] += __shfl_xor_sync(0xffffffffu, r6[m], o);
+            i6[m] += __shfl_xor_sync(0xffffffffu, i6[m], o);
+        }
+        if (m < 5) s4 = fmaf(r4[m], r4[m], fmaf(i4[m], i4[m], s4));
+        s6 = fmaf(r6[m], r6[m], fmaf(i6[m], i6[m], s6));
+    }
+    const float inv = nu > 0 ? 1.0f / (float)nu : 0.0f;
+    // sorted distances: the rank of each bond length
+    for (int a = lane; a < nu; a += 32) {
+        const float da = s_d[w][a];
+        int rank = 0;
+        for (int b = 0; b < nu; ++b) {
+            const float db = s_d[w][b];
+            rank += (db < da) || (db == da && b < a);
+        }
+        if (rank < 14) s_f[w][2 + rank] = da / r_feat;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        s_f[w][0] = sqrtf(s4) * inv;
+        s_f[w][1] = sqrtf(s6) * inv;
+    }
+    // angle histogram with tent weights
+    for (int a = lane; a < nu; a += 32) {
+        const float3 ua = s_u[w][a];
+        for (int b = a + 1; b < nu; ++b) {
+            const float3 ub = s_u[w][b];
+            float c = fmaf(ua.x, ub.x, fmaf(ua.y, ub.y, ua.z * ub.z));
+            c = fminf(1.0f, fmaxf(-1.0f, c));
+            const float x = (c + 1.0f) * 7.0f - 0.5f;
+            const float fl = floorf(x);
+            const int b0 = (int)fl;
+            const float t = x - fl;
+            if (b0 < 0) {
+                atomicAdd(&s_f[w][16], 1.0f);
+            } else if (b0 >= 13) {
+                atomicAdd(&s_f[w][16 + 13], 1.0f);
+            } else {
+                atomicAdd(&s_f[w][16 + b0], 1.0f - t);
+                atomicAdd(&s_f[w][16 + b0 + 1], t);
+            }
+        }
+    }
+    __syncwarp();
+    const int npair = nu * (nu - 1) / 2;
+    float v = s_f[w][lane];
+    if (lane >= 16 && lane < 30 && npair > 0) v /= (float)npair;
+    if (lane >= 30) v = 0.0f;
+    const int64_t o = out_idx ? out_idx[i] : i;
+    if (f32 && lane < 30) f32[o * 30 + lane] = v;
+    if (fb16) fb16[o * 32 + lane] = __float2bfloat16_rn(v);
+}
+
+int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st,
+                    const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, double r_feat, double Lmax,
+                    const int32_t *out_idx, float *f32, __nv_bfloat16 *fb16) {
+    static const YlmCoef K = make_coef();
+    float lo, hi;
+    cutoff_band(r_feat * r_feat, Lmax, &lo, &hi);
+    if (n > 0)
+        PPMD_LAUNCH(ctx, k_features, div_up(n, FEAT_WARPS), FEAT_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
+                    r_feat * r_feat, lo, hi, (float)r_feat, K, out_idx, f32, fb16, ctx->d_status, ctx->d_needed);
+    return check_launch(ctx, "features");
 }
 
 // ---------------------------------------------------------------------
@@ -414,4 +582,15 @@ extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const p
     if (want_boa) PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
     if (want_cna) PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_cna, s.Lmax, s.perm, nullptr, label));
     return PPMD_OK;
+}
+
+extern "C" int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat, float *feat,
+                             uint16_t *feat_bf16) {
+    if (!ctx || !box || n < 0 || (n > 0 && !pos) || !(r_feat > 0) || (!feat && !feat_bf16))
+        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_features: bad argument");
+    cudaSetDevice(ctx->device);
+    Snapshot s;
+    PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, 32, s));
+    return features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_feat, s.Lmax, s.perm, feat,
+                           (__nv_bfloat16 *)feat_bf16);
 }

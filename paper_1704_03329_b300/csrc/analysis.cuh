@@ -1,6 +1,8 @@
 // Structure analysis kernels (bond order parameters, common neighbour
 // analysis) and the sorted-snapshot pipeline shared with the classifier.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace ppmd {
@@ -27,4 +29,13 @@ int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, co
 int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
                const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
                int8_t *label);
+// CNA labels of the snapshot atoms listed in `which` (m of them), written
+// at label[which[k]].
+int cna_subset_launch(ppmd_ctx *ctx, int64_t m, const int32_t *which, const int4 *xq, const double *pos64,
+                      const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, double r_cut,
+                      double Lmax, int8_t *label);
+// Classifier features (30 per atom) of the snapshot atoms, written at out_idx.
+int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st,
+                    const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, double r_feat, double Lmax,
+                    const int32_t *out_idx, float *f32, __nv_bfloat16 *fb16);
 }  // namespace ppmd

@@ -1,0 +1,199 @@
+"""GPU parity of the learned classifier: features, tensor-core MLP forward,
+gradients, AdamW, training and the classification pipeline, against the
+FP64 oracle.
+
+Tolerances: features |d| <= 2e-5 (single precision; Q_l as in BOA);
+logits |d| <= 0.03 max(1, rms logit) (BF16 inputs, weights and activations,
+FP32 accumulation: 2^-9 relative per rounding through three layers);
+weight gradients per block: relative norm error <= 2e-2 and cosine >= 0.999
+(the oracle evaluated on the same BF16-rounded inputs and weights);
+AdamW in FP32 against FP64: <= 1e-5 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp as omlp
+from synth import configs
+from synth.configs import R_BOA, R_CNA
+
+pytestmark = pytest.mark.gpu
+BLOCKS = [("W1", 0, 1920, (30, 64)), ("b1", 1920, 1984, (64,)), ("W2", 1984, 6080, (64, 64)),
+          ("b2", 6080, 6144, (64,)), ("W3", 6144, 6400, (64, 4)), ("b3", 6400, 6404, (4,))]
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1704_03329_b300 import lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    return L.Context(0)
+
+
+def cu(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def pack(p):
+    return np.concatenate([p[name].reshape(-1) for name, *_ in BLOCKS])
+
+
+def unpack(v):
+    return {name: v[a:b].reshape(shape) for name, a, b, shape in BLOCKS}
+
+
+def _params(seed, bias_scale=0.1):
+    rng = np.random.default_rng(seed)
+    p = omlp.init_params(rng)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.normal(0, bias_scale, p[k].shape)
+    return p
+
+
+def _box(kind, sigma, seed=33):
+    cells = {"fcc": (10, 10, 5), "bcc": (10, 10, 5), "hcp": (10, 6, 6), "liquid": (12, 12, 12)}[kind]
+    return configs.structure_box(kind, sigma, seed, cells=cells)
+
+
+@pytest.mark.parametrize("kind", ["fcc", "bcc", "hcp", "liquid"])
+def test_features_parity(L, ctx, kind):
+    c = _box(kind, 0.05)
+    pos, box = c["pos"], c["box"]
+    offs, nb = oracle.neighbours_cells(pos, box, R_BOA)
+    fo = oracle.features(pos, box, offs, nb, R_BOA)
+    f, fb = L.ppmd_features(ctx, cu(pos), box, R_BOA, fp32=True, bf16=True)
+    f = f.cpu().numpy()
+    assert np.abs(f - fo).max() <= 2e-5
+    fb = fb.to(torch.float32).cpu().numpy()
+    assert np.abs(fb[:, :30] - f).max() <= 2 ** -8 * max(1.0, np.abs(f).max())
+    assert (fb[:, 30:] == 0).all()
+
+
+def test_mlp_forward_parity(L, ctx):
+    p = _params(1)
+    rng = np.random.default_rng(2)
+    x = rng.normal(0.3, 0.4, (1000, 30))
+    xb = np.zeros((1000, 32))
+    xb[:, :30] = x
+    x_bf = bf16_round(xb)
+    pq = {k: bf16_round(v) if k.startswith("W") else v for k, v in p.items()}
+    ref, _ = omlp.forward(pq, x_bf[:, :30])
+    logits = L.ppmd_mlp_forward(ctx, cu(pack(p), torch.float32), cu(x_bf, torch.bfloat16)).cpu().numpy()
+    scale = max(1.0, np.sqrt((ref ** 2).mean()))
+    assert np.abs(logits - ref).max() <= 0.03 * scale
+    agree = (logits.argmax(1) == ref.argmax(1)).mean()
+    assert agree >= 0.99
+
+
+def _cos(a, b):
+    return float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
+
+
+@pytest.mark.parametrize("batch", [4096, 1000])
+def test_mlp_gradients_parity(L, ctx, batch):
+    p = _params(3)
+    rng = np.random.default_rng(4)
+    xb = np.zeros((batch, 32))
+    xb[:, :30] = rng.normal(0.3, 0.4, (batch, 30))
+    y = rng.integers(0, 4, batch)
+    x_bf = bf16_round(xb)
+    pq = {k: bf16_round(v) if k.startswith("W") else v for k, v in p.items()}
+    loss_o, g_o = omlp.loss_and_grad(pq, x_bf[:, :30], y)
+    grad, loss = L.ppmd_mlp_grad(ctx, cu(pack(p), torch.float32), cu(x_bf, torch.bfloat16), cu(y, torch.int8))
+    g = unpack(grad.cpu().numpy().astype(np.float64))
+    assert abs(float(loss.cpu()) - loss_o) <= 1e-3 * loss_o
+    for name, *_ in BLOCKS:
+        a, b = g[name].reshape(-1), g_o[name].reshape(-1)
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b), name
+        assert _cos(a, b) >= 0.999, name
+
+
+def test_adamw_matches_oracle(L, ctx):
+    p = _params(5)
+    rng = np.random.default_rng(6)
+    pv = pack(p)
+    P = cu(pv, torch.float32)
+    M = torch.zeros_like(P)
+    V = torch.zeros_like(P)
+    state = omlp.adamw_init(p)
+    for step in (1, 2, 3):
+        gv = rng.normal(0, 0.05, pv.shape)
+        L.ppmd_mlp_adamw(ctx, P, M, V, cu(gv, torch.float32), step, lr=1e-3, wd=0.01)
+        omlp.adamw_step(p, unpack(gv), state, lr=1e-3, wd=0.01)
+    got = P.cpu().numpy().astype(np.float64)
+    ref = pack(p)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def _training_set(L, ctx, seed):
+    xs, ys = [], []
+    for kind in ("fcc", "bcc", "hcp", "liquid"):
+        for sigma in (0.02, 0.06, 0.1):
+            c = _box(kind, sigma, seed)
+            p = cu(c["pos"])
+            _, fb = L.ppmd_features(ctx, p, c["box"], R_BOA, fp32=False, bf16=True)
+            lab, _, _ = L.ppmd_classify(ctx, p, c["box"], mode=0, r_cna=R_CNA)
+            xs.append(fb)
+            ys.append(lab)
+    return torch.cat(xs), torch.cat(ys)
+
+
+def test_training_learns_cna_labels(L, ctx):
+    """A few hundred AdamW steps on CNA-labelled structure boxes: the loss
+    falls and held-out atoms are classified like CNA."""
+    x, y = _training_set(L, ctx, 41)
+    xt, yt = _training_set(L, ctx, 42)
+    rng = np.random.default_rng(7)
+    P = cu(pack(omlp.init_params(rng)), torch.float32)
+    M = torch.zeros_like(P)
+    V = torch.zeros_like(P)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    g = torch.Generator(device="cpu").manual_seed(0)
+    losses = []
+    B = 4096
+    for step in range(1, 401):
+        idx = torch.randint(0, x.shape[0], (B,), generator=g).cuda()
+        L.ppmd_mlp_train_step(ctx, P, M, V, step, x[idx].contiguous(), y[idx].contiguous(), lr=3e-3, wd=0.01, loss=loss)
+        if step % 50 == 0:
+            losses.append(float(loss.cpu()))
+    assert losses[-1] < 0.5 * losses[0]
+    logits = L.ppmd_mlp_forward(ctx, P, xt)
+    agree = (logits.argmax(1).to(torch.int8) == yt).float().mean().item()
+    assert agree >= 0.9, agree
+    # with the CNA fallback below confidence 0.9 the labels follow CNA closely
+    c = _box("hcp", 0.06, 43)
+    pc = cu(c["pos"])
+    exact, _, _ = L.ppmd_classify(ctx, pc, c["box"], mode=0, r_cna=R_CNA)
+    lab, conf, nfb = L.ppmd_classify(ctx, pc, c["box"], mode=1, params=P, threshold=0.9)
+    both = (lab == exact).float().mean().item()
+    assert both >= 0.95 and both >= agree, (both, nfb / len(c["pos"]))
+
+
+def test_classify_modes(L, ctx):
+    c = _box("fcc", 0.06, 44)
+    p = cu(c["pos"])
+    exact, _, nfb0 = L.ppmd_classify(ctx, p, c["box"], mode=0, r_cna=R_CNA)
+    offs, nb = oracle.neighbours_cells(c["pos"], c["box"], R_BOA)
+    lab_o = oracle.cna_label(*oracle.cna(c["pos"], c["box"], offs, nb, R_CNA)[:2])
+    assert np.array_equal(exact.cpu().numpy(), lab_o)
+    params = cu(pack(_params(8)), torch.float32)
+    # threshold above 1: every atom falls back to CNA
+    lab, conf, nfb = L.ppmd_classify(ctx, p, c["box"], mode=1, params=params, threshold=1.01)
+    assert nfb == len(c["pos"]) and np.array_equal(lab.cpu().numpy(), lab_o)
+    # threshold 0: no fallback, labels are the MLP's argmax over the features
+    lab, conf, nfb = L.ppmd_classify(ctx, p, c["box"], mode=1, params=params, threshold=0.0)
+    assert nfb == 0
+    _, fb = L.ppmd_features(ctx, p, c["box"], R_BOA, fp32=False, bf16=True)
+    logits = L.ppmd_mlp_forward(ctx, params, fb)
+    assert torch.equal(lab, logits.argmax(1).to(torch.int8))
+    pr = torch.softmax(logits, 1).max(1).values
+    assert torch.allclose(conf, pr, atol=1e-5)
