@@ -197,21 +197,30 @@ int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *bo
  * environment features, trained on labels from ppmd_cna, with exact CNA as
  * the fallback for low-confidence atoms.  Parameters are one FP32 device
  * vector of PPMD_MLP_NPARAM values, laid out
- *   W1[30][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
- * with y = x W + b.  Arithmetic: BF16 inputs, weights and activations, FP32
+ *   mu[30] | isd[30] | W1[30][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
+ * with x' = (x - mu) isd (input standardisation, set by
+ * ppmd_mlp_fit_input_norm, never trained) and y = x' W + b.  Arithmetic: BF16 inputs, weights and activations, FP32
  * accumulation (tensor cores).                                          */
 /* ------------------------------------------------------------------ */
-#define PPMD_MLP_NPARAM 6404
+#define PPMD_MLP_NPARAM 6464
 
 /* Features of every atom from its bonds (r < r_feat, the BOA cutoff):
- * [0] Q4, [1] Q6 (Eqs. (1)-(2)); [2..15] the 14 smallest bond lengths / r_feat,
- * ascending (missing: 1); [16..29] histogram of the bond-angle cosines over
- * all bond pairs, 14 bins of width 1/7 on [-1, 1] with linear weights
- * between bin centres, divided by the number of pairs.  Outputs (device, at
+ * [0] Q4, [1] Q6 (Eqs. (1)-(2)); [2..15] the 14 smallest bond lengths d,
+ * ascending, as (d - r_ref) / (r_feat - r_ref) with r_ref < r_feat a
+ * reference length (the CNA cutoff: values change sign where CNA's bond
+ * test does), missing ones 1; [16..29] a histogram of the chords
+ * |r_ij - r_ik| of the bond angles between bonded neighbours (closer than
+ * r_ref), 14 bins of width 0.05 centred on r_ref - 0.35 + 0.05 (b + 1/2),
+ * linear weights between centres, clamped at both ends, divided by 24.
+ * Outputs (device, at
  * least one given): feat[n][30] FP32, feat_bf16[n][32] BF16 (last two 0),
  * caller order.  Synchronises once (list capacity check). */
-int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat, float *feat,
-                  uint16_t *feat_bf16);
+int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat, double r_ref,
+                  float *feat, uint16_t *feat_bf16);
+/* Sets mu and isd of params to the mean and 1/standard deviation of each of
+ * the 30 features over the n rows of x [n][32] (BF16); isd = 1 for a
+ * constant feature. */
+int ppmd_mlp_fit_input_norm(ppmd_ctx *ctx, float *params, const uint16_t *x, int64_t n);
 /* Logits [n][4] (FP32) of the BF16 feature rows x [n][32]. */
 int ppmd_mlp_forward(ppmd_ctx *ctx, const float *params, const uint16_t *x, int64_t n, float *logits);
 /* Gradient (FP32 [PPMD_MLP_NPARAM], device) of the mean cross entropy of
@@ -227,8 +236,8 @@ int ppmd_mlp_adamw(ppmd_ctx *ctx, float *params, float *m, float *v, const float
 int ppmd_mlp_train_step(ppmd_ctx *ctx, float *params, float *m, float *v, int64_t step, const uint16_t *x,
                         const int8_t *y, int64_t batch, float lr, float wd, float *loss);
 /* Structure labels of every atom (caller order, label[n] device int8).
- * mode 0: exact CNA (cutoff r_cna).  mode 1: features (cutoff r_feat >=
- * r_cna) -> MLP -> class and confidence (max softmax probability, device
+ * mode 0: exact CNA (cutoff r_cna).  mode 1: features (cutoff r_feat >
+ * r_cna, reference length r_cna) -> MLP -> class and confidence (max softmax probability, device
  * float [n], may be NULL); atoms with confidence < threshold are labelled
  * by exact CNA instead.  n_fallback (host, may be NULL) receives the number
  * of atoms labelled by CNA.  Synchronises. */

@@ -56,7 +56,7 @@ def _load():
         "ora_boa_addition": (None, [i64, P, P, f64, P, P, C.c_int, P]),
         "ora_cna": (i32, [i64, P, P, f64, P, P, i32, P, P, P]),
         "ora_cna_label": (None, [i64, P, P, i32, P]),
-        "ora_features": (None, [i64, P, P, f64, P, P, P]),
+        "ora_features": (None, [i64, P, P, f64, f64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -206,14 +206,14 @@ def cna_label(nbond, trip):
     return lab
 
 
-def features(pos, box, offs, nbr, r_feat=1.5):
+def features(pos, box, offs, nbr, r_feat=1.5, r_ref=1.433625):
     """30 local-environment features per atom (see ppmd_oracle.c)."""
     pos, box = _f64(pos), _f64(box)
     n = len(pos)
     f = np.zeros((n, 30))
     offs = np.ascontiguousarray(offs, np.int64)
     nbr = np.ascontiguousarray(nbr, np.int32)
-    _load().ora_features(n, _p(pos), _p(box), float(r_feat), _p(offs), _p(nbr), _p(f))
+    _load().ora_features(n, _p(pos), _p(box), float(r_feat), float(r_ref), _p(offs), _p(nbr), _p(f))
     return f
 
 

@@ -2,8 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Network: 30 -> 64 -> 64 -> 4, ReLU after the two hidden layers, softmax
-output over the classes (0 other, 1 fcc, 2 hcp, 3 bcc).  Loss: mean cross
+Network: inputs standardised x' = (x - mu) isd (mu, isd fitted to the
+training features, not trained), then 30 -> 64 -> 64 -> 4, ReLU after the
+two hidden layers, softmax output over the classes (0 other, 1 fcc, 2 hcp,
+3 bcc).  Loss: mean cross
 entropy over the batch.  Optimiser: AdamW (Loshchilov & Hutter, decoupled
 weight decay) with beta = (0.9, 0.999), eps = 1e-8; the decay applies to the
 weight matrices only.  Initialisation: He-uniform weights
@@ -16,11 +18,11 @@ from __future__ import annotations
 import numpy as np
 
 SIZES = (30, 64, 64, 4)
-NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
+NAMES = ("mu", "isd", "W1", "b1", "W2", "b2", "W3", "b3")
 
 
 def init_params(rng: np.random.Generator):
-    p = {}
+    p = {"mu": np.zeros(SIZES[0]), "isd": np.ones(SIZES[0])}
     for k in range(3):
         fi, fo = SIZES[k], SIZES[k + 1]
         lim = np.sqrt(6.0 / fi)
@@ -29,8 +31,17 @@ def init_params(rng: np.random.Generator):
     return p
 
 
+def fit_input_norm(p, x):
+    """mu, isd = mean and 1/standard deviation of every input feature."""
+    p["mu"] = x.mean(axis=0)
+    var = x.var(axis=0)
+    p["isd"] = np.where(var > 1e-12, 1.0 / np.sqrt(np.maximum(var, 1e-300)), 1.0)
+    return p
+
+
 def forward(p, x):
-    """Returns (logits, cache)."""
+    """Returns (logits, cache); the cache holds the standardised inputs."""
+    x = (x - p["mu"]) * p["isd"]
     z1 = x @ p["W1"] + p["b1"]
     h1 = np.maximum(z1, 0.0)
     z2 = h1 @ p["W2"] + p["b2"]
@@ -61,6 +72,8 @@ def loss_and_grad(p, x, y):
     d1 = (d2 @ p["W2"].T) * (z1 > 0)
     grads["W1"] = x.T @ d1
     grads["b1"] = d1.sum(0)
+    grads["mu"] = np.zeros_like(p["mu"])  # standardisation is not trained
+    grads["isd"] = np.zeros_like(p["isd"])
     return loss, grads
 
 
@@ -73,6 +86,8 @@ def adamw_step(p, grads, state, lr=1e-3, wd=0.01, b1=0.9, b2=0.999, eps=1e-8):
     state["t"] += 1
     t = state["t"]
     for k in p:
+        if k in ("mu", "isd"):
+            continue  # fitted, not trained
         g = grads[k]
         m = state["m"][k] = b1 * state["m"][k] + (1.0 - b1) * g
         v = state["v"][k] = b2 * state["v"][k] + (1.0 - b2) * g * g

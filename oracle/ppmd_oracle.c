@@ -632,12 +632,15 @@ void ora_cna_label(int64_t n, const int32_t *nbond, const uint32_t *trip, int32_
 /* Local-environment features for the learned classifier (30 per atom):
  *   [0] Q4, [1] Q6 over neighbours within r_feat (Eqs. (1)-(2), computed by
  *       the direct route above);
- *   [2..15]  the 14 smallest neighbour distances within r_feat, ascending,
- *            divided by r_feat, missing ones set to 1;
- *   [16..29] a 14-bin histogram of cos(theta_jik) over all unordered
- *            neighbour pairs (j, k) of i, bins of width 1/7 on [-1, 1] with
- *            linear (tent) weights between adjacent bin centres, divided by
- *            the number of pairs (all zero with fewer than two neighbours).
+ *   [2..15]  the 14 smallest neighbour distances d within r_feat, ascending,
+ *            as (d - r_ref) / (r_feat - r_ref) (r_ref: a reference length
+ *            inside the shell, the CNA cutoff), missing ones set to 1;
+ *   [16..29] a 14-bin histogram of the chord |r_ij - r_ik| of every bond
+ *            angle theta_jik between two bonded neighbours j, k of i (bonded:
+ *            closer than r_ref), bins of width 0.05 centred on
+ *            r_ref - 0.35 + 0.05 (b + 1/2), linear (tent) weights between
+ *            adjacent centres, clamped at both ends, divided by 24 (the number
+ *            of such pairs a perfect fcc or hcp site has at 60 degrees).
  */
 /* ------------------------------------------------------------------ */
 
@@ -646,7 +649,7 @@ static int cmp_f64(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
-void ora_features(int64_t n, const double *pos, const double *L, double r_feat, const int64_t *offs,
+void ora_features(int64_t n, const double *pos, const double *L, double r_feat, double r_ref, const int64_t *offs,
                   const int32_t *nbr, double *feat) {
     double rc2 = r_feat * r_feat, dr[3];
     double *q4 = (double *)malloc(sizeof(double) * (size_t)n);
@@ -679,16 +682,24 @@ void ora_features(int64_t n, const double *pos, const double *L, double r_feat, 
             ++nu;
         }
         qsort(d, (size_t)nu, sizeof(double), cmp_f64);
-        for (int k = 0; k < 14; ++k) f[2 + k] = (k < nu) ? d[k] / r_feat : 1.0;
+        for (int k = 0; k < 14; ++k) f[2 + k] = (k < nu) ? (d[k] - r_ref) / (r_feat - r_ref) : 1.0;
         for (int b = 0; b < 14; ++b) f[16 + b] = 0.0;
-        int npair = 0;
-        for (int a = 0; a < nu; ++a)
-            for (int b = a + 1; b < nu; ++b) {
-                double c = u[3 * a] * u[3 * b] + u[3 * a + 1] * u[3 * b + 1] + u[3 * a + 2] * u[3 * b + 2];
-                if (c > 1.0) c = 1.0;
-                if (c < -1.0) c = -1.0;
-                /* bin centres at -1 + (b + 1/2) / 7; tent weights, clamped at the ends */
-                double x = (c + 1.0) * 7.0 - 0.5;
+        /* bonded neighbours: the vectors r_i - r_j with |r_i - r_j| < r_ref */
+        int nb_ = 0;
+        for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
+            double r2 = min_image(&pos[3 * i], &pos[3 * nbr[k]], L, dr);
+            if (!(r2 < r_ref * r_ref)) continue;
+            u[3 * nb_] = dr[0];
+            u[3 * nb_ + 1] = dr[1];
+            u[3 * nb_ + 2] = dr[2];
+            ++nb_;
+        }
+        double lo = r_ref - 0.35;
+        for (int a = 0; a < nb_; ++a)
+            for (int b = a + 1; b < nb_; ++b) {
+                double cx = u[3 * a] - u[3 * b], cy = u[3 * a + 1] - u[3 * b + 1], cz = u[3 * a + 2] - u[3 * b + 2];
+                double chord = sqrt(cx * cx + cy * cy + cz * cz);
+                double x = (chord - lo) / 0.05 - 0.5;
                 int b0 = (int)floor(x);
                 double t = x - b0;
                 if (b0 < 0) {
@@ -699,10 +710,8 @@ void ora_features(int64_t n, const double *pos, const double *L, double r_feat, 
                     f[16 + b0] += 1.0 - t;
                     f[16 + b0 + 1] += t;
                 }
-                ++npair;
             }
-        if (npair > 0)
-            for (int b = 0; b < 14; ++b) f[16 + b] /= npair;
+        for (int b = 0; b < 14; ++b) f[16 + b] /= 24.0;
     }
     free(d);
     free(u);

@@ -68,8 +68,9 @@ _SIGS = {
     "ppmd_boa_q46": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, _I32, _P, _P, _P]),
     "ppmd_cna": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, _I32, _P, _P]),
     "ppmd_analyze": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _D, _P, _P, _P, _P]),
-    "ppmd_features": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P]),
+    "ppmd_features": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _D, _P, _P]),
     "ppmd_mlp_forward": (_I, [_P, _P, _P, _I64, _P]),
+    "ppmd_mlp_fit_input_norm": (_I, [_P, _P, _P, _I64]),
     "ppmd_mlp_grad": (_I, [_P, _P, _P, _P, _I64, _P, _P]),
     "ppmd_mlp_adamw": (_I, [_P, _P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
     "ppmd_mlp_train_step": (_I, [_P, _P, _P, _P, _I64, _P, _P, _I64, C.c_float, C.c_float, _P]),
@@ -268,17 +269,21 @@ def ppmd_analyze(ctx: Context, pos, box, r_boa=1.5, r_cna=None, boa=True, cna=Tr
     return out
 
 
-MLP_NPARAM = 6404
+MLP_NPARAM = 6464
 
 
-def ppmd_features(ctx: Context, pos, box, r_feat=1.5, fp32=True, bf16=False):
+def ppmd_features(ctx: Context, pos, box, r_feat=1.5, fp32=True, bf16=False, r_ref=1.433625):
     """Classifier features: float32 [n, 30] and/or bfloat16 [n, 32] (caller order)."""
     n = pos.shape[0]
     f = torch.empty((n, 30), dtype=torch.float32, device=pos.device) if fp32 else None
     fb = torch.empty((n, 32), dtype=torch.bfloat16, device=pos.device) if bf16 else None
     b = _box(box)
-    ctx.check(_lib.ppmd_features(ctx.h, _ptr(pos), n, C.byref(b), float(r_feat), _opt(f), _opt(fb)))
+    ctx.check(_lib.ppmd_features(ctx.h, _ptr(pos), n, C.byref(b), float(r_feat), float(r_ref), _opt(f), _opt(fb)))
     return f, fb
+
+
+def ppmd_mlp_fit_input_norm(ctx: Context, params, x_bf16):
+    ctx.check(_lib.ppmd_mlp_fit_input_norm(ctx.h, _ptr(params), _ptr(x_bf16), x_bf16.shape[0]))
 
 
 def ppmd_mlp_forward(ctx: Context, params, x_bf16):

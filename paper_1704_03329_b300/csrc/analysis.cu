@@ -10,6 +10,7 @@
 
 #include "analysis.cuh"
 #include "cells.cuh"
+#include "md_kernels.cuh"
 #include "neighbours.cuh"
 
 namespace ppmd {
@@ -98,7 +99,8 @@ __device__ __forceinline__ void boa_accumulate(const YlmCoef &K, float x, float 
 // out_idx (may be null): write the results of atom i at out_idx[i].
 __global__ void __launch_bounds__(256) k_boa(int64_t n, const int4 *__restrict__ xq, const double *__restrict__ pos64,
                                              SegTable st, const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
-                                             int32_t max_nbr, double rc2, float rc2_lo, float rc2_hi, YlmCoef K,
+                                             int32_t max_nbr, int64_t si, int64_t sm, double rc2, float rc2_lo,
+                                             float rc2_hi, YlmCoef K,
                                              const int32_t *__restrict__ out_idx, float *__restrict__ q4,
                                              float *__restrict__ q6, int32_t *__restrict__ nnb) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -112,10 +114,10 @@ __global__ void __launch_bounds__(256) k_boa(int64_t n, const int4 *__restrict__
         r6[m] = i6[m] = 0.0f;
     }
     const int32_t deg = min(cnt[i], max_nbr);
-    const int32_t *row = nbr + i * (int64_t)max_nbr;
+    const int32_t *row = nbr + i * si;
     int32_t nu = 0;
     for (int32_t k = 0; k < deg; ++k) {
-        const int32_t j = row[k];
+        const int32_t j = row[k * sm];
         const int4 xj = __ldg(&xq[j]);
         float dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj.x, S.sx[0]);
         float dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj.y, S.sx[1]);
@@ -179,7 +181,8 @@ __device__ __forceinline__ int32_t cna_label_of(int nu, int c421, int c422, int 
 __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *__restrict__ xq,
                                                         const double *__restrict__ pos64, SegTable st,
                                                         const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
-                                                        int32_t max_nbr, double rc2, float lo, float hi,
+                                                        int32_t max_nbr, int64_t si, int64_t sm, double rc2, float lo,
+                                                        float hi,
                                                         const int32_t *__restrict__ out_idx, uint32_t *__restrict__ trip,
                                                         int8_t *__restrict__ label, int32_t *status,
                                                         unsigned long long *needed, const int32_t *__restrict__ which) {
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
     const int4 xi = xq[i];
     const Seg &S = seg_ref(st, xi.w);
     const int32_t deg = min(cnt[i], max_nbr);
-    const int32_t *row = nbr + i * (int64_t)max_nbr;
+    const int32_t *row = nbr + i * si;
     uint32_t *trow = trip ? trip + i * (int64_t)max_nbr : nullptr;
     const unsigned lt = (1u << lane) - 1u;
     // bonded neighbours, compacted in list order
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
         int32_t j = 0;
         int4 xj = make_int4(0, 0, 0, 0);
         if (k < deg) {
-            j = row[k];
+            j = row[k * sm];
             xj = xq[j];
             b = bonded(xi, xj, pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, rc2, lo, hi);
             if (!b && trow) trow[k] = NOT_BONDED;
@@ -283,35 +286,38 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
 }
 
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
-               const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
+               const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
                float *q6, int32_t *nnb) {
     static const YlmCoef K = make_coef();
     float lo, hi;
     cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
     if (n > 0)
-        PPMD_LAUNCH(ctx, k_boa, div_up(n, 256), 256, 0, n, xq, pos64, st, nbr, cnt, max_nbr, r_cut * r_cut, lo, hi, K, out_idx,
+        PPMD_LAUNCH(ctx, k_boa, div_up(n, 256), 256, 0, n, xq, pos64, st, nbr, cnt, max_nbr, ld ? 1 : (int64_t)max_nbr,
+                    ld ? ld : 1, r_cut * r_cut, lo, hi, K, out_idx,
                     q4, q6, nnb);
     return check_launch(ctx, "boa");
 }
 
 int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
-               const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
+               const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
                int8_t *label) {
     float lo, hi;
     cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
     if (n > 0)
-        PPMD_LAUNCH(ctx, k_cna, div_up(n, CNA_WARPS), CNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr, r_cut * r_cut,
+        PPMD_LAUNCH(ctx, k_cna, div_up(n, CNA_WARPS), CNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
+                    ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_cut * r_cut,
                     lo, hi, out_idx, trip, label, ctx->d_status, ctx->d_needed, nullptr);
     return check_launch(ctx, "cna");
 }
 
 int cna_subset_launch(ppmd_ctx *ctx, int64_t m, const int32_t *which, const int4 *xq, const double *pos64,
-                      const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, double r_cut,
+                      const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut,
                       double Lmax, int8_t *label) {
     float lo, hi;
     cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
     if (m > 0)
-        PPMD_LAUNCH(ctx, k_cna, div_up(m, CNA_WARPS), CNA_WARPS * 32, 0, m, xq, pos64, st, nbr, cnt, max_nbr, r_cut * r_cut,
+        PPMD_LAUNCH(ctx, k_cna, div_up(m, CNA_WARPS), CNA_WARPS * 32, 0, m, xq, pos64, st, nbr, cnt, max_nbr,
+                    ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_cut * r_cut,
                     lo, hi, nullptr, nullptr, label, ctx->d_status, ctx->d_needed, which);
     return check_launch(ctx, "cna_subset");
 }
@@ -321,7 +327,8 @@ int cna_subset_launch(ppmd_ctx *ctx, int64_t m, const int32_t *which, const int4
 // Local-environment features of the learned classifier, one warp per atom.
 // With nu bonds (r < r_feat) of unit vectors u_a and lengths d_a:
 //   f[0], f[1]   Q4, Q6 (as k_boa);
-//   f[2..15]     the 14 smallest d_a / r_feat, ascending (missing: 1);
+//   f[2..15]     the 14 smallest d_a, ascending, as (d_a - r_ref) / (r_feat - r_ref)
+//                (missing: 1);
 //   f[16..29]    histogram of cos(u_a, u_b) over all pairs a < b: 14 bins of
 //                width 1/7 on [-1, 1], linear weights between bin centres
 //                (clamped at both ends), divided by the number of pairs.
@@ -333,41 +340,58 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
                                                               const double *__restrict__ pos64, SegTable st,
                                                               const int32_t *__restrict__ nbr,
                                                               const int32_t *__restrict__ cnt, int32_t max_nbr,
-                                                              double rc2, float lo, float hi, float r_feat, YlmCoef K,
+                                                              int64_t si, int64_t sm, double rc2, float lo, float hi,
+                                                              double rb2, float blo, float bhi, float r_ref,
+                                                              float inv_span, YlmCoef K,
                                                               const int32_t *__restrict__ out_idx,
                                                               float *__restrict__ f32, __nv_bfloat16 *__restrict__ fb16,
                                                               int32_t *status, unsigned long long *needed) {
     __shared__ float3 s_u[FEAT_WARPS][64];
     __shared__ float s_d[FEAT_WARPS][64];
+    __shared__ float3 s_v[FEAT_WARPS][64];  // r_i - r_j of the bonded neighbours (r < r_ref)
     __shared__ float s_f[FEAT_WARPS][32];
+    __shared__ float s_red[FEAT_WARPS][32][39];  // per-lane partial sums (odd stride against bank conflicts)
+    __shared__ float s_mom[FEAT_WARPS][24];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * FEAT_WARPS + w;
     if (i >= n) return;
     const int4 xi = xq[i];
     const Seg &S = seg_ref(st, xi.w);
     const int32_t deg = min(cnt[i], max_nbr);
-    const int32_t *row = nbr + i * (int64_t)max_nbr;
+    const int32_t *row = nbr + i * si;
     const unsigned lt = (1u << lane) - 1u;
     s_f[w][lane] = (lane >= 2 && lane < 16) ? 1.0f : 0.0f;
-    int32_t nu = 0;
+    int32_t nu = 0, nbd = 0;
     for (int32_t base = 0; base < deg; base += 32) {
         const int32_t k = base + lane;
-        bool b = false;
+        bool b = false, bb = false;
         float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
         if (k < deg) {
-            const int32_t j = row[k];
+            const int32_t j = row[k * sm];
             const int4 xj = xq[j];
             dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj.x, S.sx[0]);
             dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj.y, S.sx[1]);
             dz = fixed_delta((uint32_t)xi.z, (uint32_t)xj.z, S.sx[2]);
             r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            double r2x = -1.0;  // exact r^2 when needed
             b = r2 < lo;
             if (!b && r2 < hi) {
                 double dr[3];
-                b = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr) < rc2;
+                r2x = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr);
+                b = r2x < rc2;
             }
+            bb = r2 < blo;
+            if (!bb && r2 < bhi) {
+                if (r2x < 0.0) {
+                    double dr[3];
+                    r2x = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr);
+                }
+                bb = r2x < rb2;
+            }
+            bb = bb && b;
         }
         const unsigned ball = __ballot_sync(0xffffffffu, b);
+        const unsigned bbal = __ballot_sync(0xffffffffu, bb);
         if (b) {
             const int32_t a = nu + __popc(ball & lt);
             if (a < 64) {
@@ -376,7 +400,12 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
                 s_d[w][a] = r;
             }
         }
+        if (bb) {
+            const int32_t a = nbd + __popc(bbal & lt);
+            if (a < 64) s_v[w][a] = make_float3(dx, dy, dz);
+        }
         nu += __popc(ball);
+        nbd += __popc(bbal);
     }
     if (nu > 64) {
         if (lane == 0) {
@@ -385,8 +414,10 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
         }
         nu = 64;
     }
+    nbd = min(nbd, 64);
     __syncwarp();
-    // Q4, Q6: each lane its bonds, then warp sums of the moments
+    // Q4, Q6: each lane its bonds; the 24 moment sums are reduced through
+    // shared memory (one column per lane)
     float r4[5], i4[5], r6[7], i6[7];
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
@@ -397,23 +428,50 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
         const float3 u = s_u[w][a];
         boa_accumulate(K, u.x, u.y, u.z, r4, i4, r6, i6);
     }
-    float s4 = 0.0f, s6 = 0.0f;
+    float *red = s_red[w][lane];
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            if (m < 5) {
-                r4[m] += __shfl_xor_sync(0xffffffffu, r4[m], o);
-                i4[m] += __shfl_xor_sync(0xffffffffu, i4[m], o);
-            }
-            r6[m] += __shfl_xor_sync(0xffffffffu, r6[m], o);
-            i6[m] += __shfl_xor_sync(0xffffffffu, i6[m], o);
+        if (m < 5) {
+            red[2 * m] = r4[m];
+            red[2 * m + 1] = i4[m];
         }
-        if (m < 5) s4 = fmaf(r4[m], r4[m], fmaf(i4[m], i4[m], s4));
-        s6 = fmaf(r6[m], r6[m], fmaf(i6[m], i6[m], s6));
+        red[10 + 2 * m] = r6[m];
+        red[10 + 2 * m + 1] = i6[m];
     }
-    const float inv = nu > 0 ? 1.0f / (float)nu : 0.0f;
-    // sorted distances: the rank of each bond length
+    // histogram of the chords |r_ij - r_ik| of the bond angles between
+    // bonded neighbours: the nbd (nbd-1)/2 pairs spread evenly over the
+    // lanes, tent weights accumulated in registers
+    float h[14];
+#pragma unroll
+    for (int b = 0; b < 14; ++b) h[b] = 0.0f;
+    const int npair = nbd * (nbd - 1) / 2;
+    const float hlo = r_ref - 0.35f;
+    for (int pidx = lane; pidx < npair; pidx += 32) {
+        // pair (a, b), a < b, with pidx = a (2 nbd - a - 1) / 2 + (b - a - 1)
+        const float q = (float)(2 * nbd - 1);
+        int a = (int)floorf(0.5f * (q - sqrtf(fmaxf(q * q - 8.0f * pidx, 0.0f))));
+        while (a > 0 && a * (2 * nbd - a - 1) / 2 > pidx) --a;
+        while ((a + 1) * (2 * nbd - a - 2) / 2 <= pidx) ++a;
+        const int b = pidx - a * (2 * nbd - a - 1) / 2 + a + 1;
+        const float3 va = s_v[w][a], vb = s_v[w][b];
+        const float cx = va.x - vb.x, cy = va.y - vb.y, cz = va.z - vb.z;
+        const float chord = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
+        const float x = (chord - hlo) * 20.0f - 0.5f;
+        const float fl = floorf(x);
+        const int b0 = (int)fl;
+        const float t = x - fl;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            float add = 0.0f;
+            if (b0 < 0) add = (k == 0) ? 1.0f : 0.0f;
+            else if (b0 >= 13) add = (k == 13) ? 1.0f : 0.0f;
+            else add = (k == b0) ? 1.0f - t : ((k == b0 + 1) ? t : 0.0f);
+            h[k] += add;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 14; ++k) red[24 + k] = h[k];
+    // sorted bond lengths: the rank of each
     for (int a = lane; a < nu; a += 32) {
         const float da = s_d[w][a];
         int rank = 0;
@@ -421,38 +479,31 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
             const float db = s_d[w][b];
             rank += (db < da) || (db == da && b < a);
         }
-        if (rank < 14) s_f[w][2 + rank] = da / r_feat;
+        if (rank < 14) s_f[w][2 + rank] = (da - r_ref) * inv_span;
     }
     __syncwarp();
+    // column sums: lane c < 38 sums entry c over the 32 lanes
+    float colsum = 0.0f;
+    for (int c = lane; c < 38; c += 32) {
+        float acc = 0.0f;
+        for (int l = 0; l < 32; ++l) acc += s_red[w][l][c];
+        if (c < 24) s_mom[w][c] = acc;
+        else colsum = acc;
+        if (c >= 24) s_f[w][16 + c - 24] = acc;
+    }
+    (void)colsum;
+    __syncwarp();
     if (lane == 0) {
+        const float inv = nu > 0 ? 1.0f / (float)nu : 0.0f;
+        float s4 = 0.0f, s6 = 0.0f;
+        for (int c = 0; c < 10; ++c) s4 = fmaf(s_mom[w][c], s_mom[w][c], s4);
+        for (int c = 10; c < 24; ++c) s6 = fmaf(s_mom[w][c], s_mom[w][c], s6);
         s_f[w][0] = sqrtf(s4) * inv;
         s_f[w][1] = sqrtf(s6) * inv;
     }
-    // angle histogram with tent weights
-    for (int a = lane; a < nu; a += 32) {
-        const float3 ua = s_u[w][a];
-        for (int b = a + 1; b < nu; ++b) {
-            const float3 ub = s_u[w][b];
-            float c = fmaf(ua.x, ub.x, fmaf(ua.y, ub.y, ua.z * ub.z));
-            c = fminf(1.0f, fmaxf(-1.0f, c));
-            const float x = (c + 1.0f) * 7.0f - 0.5f;
-            const float fl = floorf(x);
-            const int b0 = (int)fl;
-            const float t = x - fl;
-            if (b0 < 0) {
-                atomicAdd(&s_f[w][16], 1.0f);
-            } else if (b0 >= 13) {
-                atomicAdd(&s_f[w][16 + 13], 1.0f);
-            } else {
-                atomicAdd(&s_f[w][16 + b0], 1.0f - t);
-                atomicAdd(&s_f[w][16 + b0 + 1], t);
-            }
-        }
-    }
     __syncwarp();
-    const int npair = nu * (nu - 1) / 2;
     float v = s_f[w][lane];
-    if (lane >= 16 && lane < 30 && npair > 0) v /= (float)npair;
+    if (lane >= 16 && lane < 30) v *= 1.0f / 24.0f;
     if (lane >= 30) v = 0.0f;
     const int64_t o = out_idx ? out_idx[i] : i;
     if (f32 && lane < 30) f32[o * 30 + lane] = v;
@@ -460,14 +511,16 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
 }
 
 int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st,
-                    const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, double r_feat, double Lmax,
-                    const int32_t *out_idx, float *f32, __nv_bfloat16 *fb16) {
+                    const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_feat, double r_ref,
+                    double Lmax, const int32_t *out_idx, float *f32, __nv_bfloat16 *fb16) {
     static const YlmCoef K = make_coef();
-    float lo, hi;
+    float lo, hi, blo, bhi;
     cutoff_band(r_feat * r_feat, Lmax, &lo, &hi);
+    cutoff_band(r_ref * r_ref, Lmax, &blo, &bhi);
     if (n > 0)
         PPMD_LAUNCH(ctx, k_features, div_up(n, FEAT_WARPS), FEAT_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
-                    r_feat * r_feat, lo, hi, (float)r_feat, K, out_idx, f32, fb16, ctx->d_status, ctx->d_needed);
+                    ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_feat * r_feat, lo, hi, r_ref * r_ref, blo, bhi, (float)r_ref, (float)(1.0 / (r_feat - r_ref)), K, out_idx, f32, fb16,
+                    ctx->d_status, ctx->d_needed);
     return check_launch(ctx, "features");
 }
 
@@ -475,15 +528,12 @@ int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos6
 // Pipeline: sort by cell, list at r_list, analyses, results in caller order.
 // ---------------------------------------------------------------------
 __global__ void k_gather_pos(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ pos,
-                             const int4 *__restrict__ xq_in, double *__restrict__ pos_o, int4 *__restrict__ xq_o,
-                             const int32_t *__restrict__ cell_in, int32_t *__restrict__ cell_o) {
+                             double *__restrict__ pos_o) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t j = perm[k];
 #pragma unroll
     for (int d = 0; d < 3; ++d) pos_o[3 * k + d] = pos[3 * j + d];
-    xq_o[k] = xq_in[j];
-    cell_o[k] = cell_in[j];
 }
 
 int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int32_t max_nbr,
@@ -492,27 +542,35 @@ int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box 
     s.st.d = nullptr;
     s.st.nseg = 1;
     PPMD_TRY(make_seg(ctx, s.st.one, box->L, r_list, r_list));
+    s.st.one.atom0 = 0;
+    s.st.one.atom1 = n;
     s.Lmax = fmax(box->L[0], fmax(box->L[1], box->L[2]));
     const int64_t ncell = (int64_t)s.st.one.nc[0] * s.st.one.nc[1] * s.st.one.nc[2];
     const size_t nn = (size_t)(n > 0 ? n : 1);
-    int4 *xq0 = (int4 *)scratch(ctx, S_XQ, sizeof(int4) * nn);
     int32_t *cell0 = (int32_t *)scratch(ctx, S_CELLS0, sizeof(int32_t) * nn);
     s.cell_start = (int32_t *)scratch(ctx, S_CELLS1, sizeof(int32_t) * (size_t)(ncell + 1));
     s.perm = (int32_t *)scratch(ctx, S_CELLS2, sizeof(int32_t) * nn);
     s.pos = (double *)scratch(ctx, S_SORTPOS, sizeof(double) * 3 * nn);
     s.xq = (int4 *)scratch(ctx, S_AUX0, sizeof(int4) * nn);
-    s.cell_of = (int32_t *)scratch(ctx, S_SORTIDX, sizeof(int32_t) * nn);
-    if (!xq0 || !cell0 || !s.cell_start || !s.perm || !s.pos || !s.xq || !s.cell_of) return PPMD_ERR_NOMEM;
-    // exact cells of the caller's atoms, then sort
-    PPMD_TRY(prep_fixed(ctx, pos, n, s.st, nullptr, xq0, nullptr));
-    PPMD_TRY(bin_atoms(ctx, pos, n, s.st, nullptr, ncell, true, cell0, s.cell_start, s.perm));
-    if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos, div_up(n, 256), 256, 0, n, s.perm, pos, xq0, s.pos, s.xq, cell0, s.cell_of);
+    std::vector<Brick> bl;
+    make_bricks(std::vector<Seg>(1, s.st.one), bl);
+    Brick *bricks = (Brick *)scratch(ctx, S_SORTIDX, sizeof(Brick) * (bl.size() + 1));
+    if (!cell0 || !s.cell_start || !s.perm || !s.pos || !s.xq || !bricks) return PPMD_ERR_NOMEM;
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice,
+                                             ctx->stream), "copy"));
+    // bin (positions need not be wrapped), sort by cell, fixed point in cell order
+    PPMD_TRY(bin_atoms(ctx, pos, n, s.st, nullptr, ncell, false, cell0, s.cell_start, s.perm));
+    if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos, div_up(n, 256), 256, 0, n, s.perm, pos, s.pos);
+    PPMD_TRY(prep_fixed(ctx, s.pos, n, s.st, nullptr, s.xq, nullptr));
+    s.ld = (n + 31) / 32 * 32;
+    PPMD_TRY(neigh_brick_setup(ctx, max_nbr));
     for (int attempt = 0; attempt < 2; ++attempt) {
         s.max_nbr = max_nbr;
-        s.nbr = (int32_t *)scratch(ctx, S_NBR, sizeof(int32_t) * nn * (size_t)max_nbr);
+        s.nbr = (int32_t *)scratch(ctx, S_NBR, sizeof(int32_t) * (size_t)s.ld * (size_t)max_nbr);
         s.cnt = (int32_t *)scratch(ctx, S_NBRCNT, sizeof(int32_t) * nn);
         if (!s.nbr || !s.cnt) return PPMD_ERR_NOMEM;
-        PPMD_TRY(build_list(ctx, n, s.xq, s.pos, s.st, s.cell_of, s.cell_start, nullptr, s.nbr, s.cnt, max_nbr));
+        PPMD_TRY(build_list_bricks(ctx, (int64_t)bl.size(), bricks, s.xq, s.pos, s.st, s.cell_start, s.nbr, s.ld, s.cnt,
+                                   max_nbr));
         int64_t need = 0;
         int rc = ppmd_status(ctx, &need);
         if (rc == PPMD_ERR_CAPACITY && attempt == 0) {
@@ -549,7 +607,7 @@ extern "C" int ppmd_boa_q46(ppmd_ctx *ctx, const double *pos, int64_t n, const p
     if (!xq) return PPMD_ERR_NOMEM;
     PPMD_TRY(prep_fixed(ctx, pos, n, st, nullptr, xq, nullptr));
     double Lmax = fmax(box->L[0], fmax(box->L[1], box->L[2]));
-    return boa_launch(ctx, n, xq, pos, st, nbr, nbr_count, max_nbr, r_cut, Lmax, nullptr, q4, q6, n_nb);
+    return boa_launch(ctx, n, xq, pos, st, nbr, nbr_count, max_nbr, 0, r_cut, Lmax, nullptr, q4, q6, n_nb);
 }
 
 extern "C" int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_cut, const int32_t *nbr,
@@ -564,7 +622,7 @@ extern "C" int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_
     if (!xq) return PPMD_ERR_NOMEM;
     PPMD_TRY(prep_fixed(ctx, pos, n, st, nullptr, xq, nullptr));
     double Lmax = fmax(box->L[0], fmax(box->L[1], box->L[2]));
-    return cna_launch(ctx, n, xq, pos, st, nbr, nbr_count, max_nbr, r_cut, Lmax, nullptr, triplets, label);
+    return cna_launch(ctx, n, xq, pos, st, nbr, nbr_count, max_nbr, 0, r_cut, Lmax, nullptr, triplets, label);
 }
 
 extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
@@ -579,18 +637,18 @@ extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const p
     if (!(r_list > 0)) return PPMD_OK;
     Snapshot s;
     PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_list, 32, s));
-    if (want_boa) PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
-    if (want_cna) PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_cna, s.Lmax, s.perm, nullptr, label));
+    if (want_boa) PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
+    if (want_cna) PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, s.perm, nullptr, label));
     return PPMD_OK;
 }
 
-extern "C" int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat, float *feat,
-                             uint16_t *feat_bf16) {
-    if (!ctx || !box || n < 0 || (n > 0 && !pos) || !(r_feat > 0) || (!feat && !feat_bf16))
+extern "C" int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat,
+                             double r_ref, float *feat, uint16_t *feat_bf16) {
+    if (!ctx || !box || n < 0 || (n > 0 && !pos) || !(r_feat > 0) || !(r_ref < r_feat) || (!feat && !feat_bf16))
         return set_error(ctx, PPMD_ERR_INVALID, "ppmd_features: bad argument");
     cudaSetDevice(ctx->device);
     Snapshot s;
     PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, 32, s));
-    return features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_feat, s.Lmax, s.perm, feat,
+    return features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, r_ref, s.Lmax, s.perm, feat,
                            (__nv_bfloat16 *)feat_bf16);
 }

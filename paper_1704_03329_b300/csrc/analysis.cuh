@@ -6,7 +6,8 @@
 #include "common.cuh"
 
 namespace ppmd {
-// Atoms of one box binned and sorted by cell, with their neighbour list.
+// Atoms of one box binned and sorted by cell, with their neighbour list
+// (column-major, built by bricks).
 struct Snapshot {
     int64_t n = 0;
     SegTable st{};
@@ -17,6 +18,7 @@ struct Snapshot {
     int32_t *cell_of = nullptr, *cell_start = nullptr;
     int32_t *nbr = nullptr, *cnt = nullptr;
     int32_t max_nbr = 0;
+    int64_t ld = 0;  // column-major list: entry m of atom i at nbr[m * ld + i]
 };
 // Bin/sort the caller's atoms with cells of edge >= r_list and build the
 // list at r_list (row capacity grown once if max_nbr is too small).
@@ -24,18 +26,18 @@ struct Snapshot {
 int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int32_t max_nbr,
                     Snapshot &s);
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
-               const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
+               const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
                float *q6, int32_t *nnb);
 int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
-               const int32_t *cnt, int32_t max_nbr, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
+               const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
                int8_t *label);
 // CNA labels of the snapshot atoms listed in `which` (m of them), written
 // at label[which[k]].
 int cna_subset_launch(ppmd_ctx *ctx, int64_t m, const int32_t *which, const int4 *xq, const double *pos64,
-                      const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, double r_cut,
+                      const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut,
                       double Lmax, int8_t *label);
 // Classifier features (30 per atom) of the snapshot atoms, written at out_idx.
 int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st,
-                    const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, double r_feat, double Lmax,
+                    const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_feat, double r_ref, double Lmax,
                     const int32_t *out_idx, float *f32, __nv_bfloat16 *fb16);
 }  // namespace ppmd

@@ -56,8 +56,15 @@ void make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out) {
     for (size_t s = 0; s < segs.size(); ++s) {
         const Seg &S = segs[s];
         // the neighbourhood spans bw + 2 cells of a row and bh + 2 rows; they
-        // must be distinct cells of the periodic grid
-        const int32_t bw = std::min(3, S.nc[0] - 2), bh = std::min(2, S.nc[1] - 2);
+        // must be distinct cells of the periodic grid, and its expected size
+        // (with a margin for density fluctuations) should fit in shared memory
+        int32_t bw = std::min(3, S.nc[0] - 2), bh = std::min(2, S.nc[1] - 2);
+        const double per_cell = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
+        auto fits = [&](int32_t w, int32_t h) { return 1.5 * per_cell * 3.0 * (w + 2) * (h + 2) <= NB_MAX; };
+        while (!fits(bw, bh) && (bw > 1 || bh > 1)) {
+            if (bh > 1) bh -= 1;
+            else bw -= 1;
+        }
         for (int32_t z = 0; z < S.nc[2]; ++z)
             for (int32_t y0 = 0; y0 < S.nc[1]; y0 += bh)
                 for (int32_t x0 = 0; x0 < S.nc[0]; x0 += bw) {
@@ -148,18 +155,15 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
     const int32_t T = s_total;
     const int32_t n0 = s_home[0][bw] - s_home[0][0];
     const int32_t H = n0 + (bh > 1 ? s_home[1][bw] - s_home[1][0] : 0);
-    if (T > NB_MAX) {
-        for (int32_t h = tid; h < H; h += blockDim.x) cnt[h < n0 ? s_home[0][0] + h : s_home[1][0] + h - n0] = 0;
-        if (tid == 0) {
-            latch_status(status, PPMD_ERR_CAPACITY);
-            latch_needed(needed, (unsigned long long)T);
+    // a neighbourhood larger than the shared-memory stage is read from global
+    // memory instead (same indices, slower)
+    const bool staged = T <= NB_MAX;
+    if (staged) {
+        for (int32_t t = tid; t < T; t += blockDim.x) {
+            int r = 0;
+            while (r + 1 < nrow && s_cell[r + 1][0] <= t) ++r;
+            s_x[t] = xq[t + (t < s_sw[r] ? s_da[r] : s_db[r])];
         }
-        return;
-    }
-    for (int32_t t = tid; t < T; t += blockDim.x) {
-        int r = 0;
-        while (r + 1 < nrow && s_cell[r + 1][0] <= t) ++r;
-        s_x[t] = xq[t + (t < s_sw[r] ? s_da[r] : s_db[r])];
     }
     __syncthreads();
     const float sx = S.sx[0], sy = S.sx[1], sz = S.sx[2];
@@ -184,7 +188,9 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
                 const int32_t sw = s_sw[r], da = s_da[r], db = s_db[r];
                 for (int32_t k = a; k < b; k += 2) {
                     const bool v1 = k + 1 < b;
-                    const int4 xa = s_x[k], xb = s_x[v1 ? k + 1 : k];
+                    const int32_t kb = v1 ? k + 1 : k;
+                    const int4 xa = staged ? s_x[k] : xq[k + (k < sw ? da : db)];
+                    const int4 xb = staged ? s_x[kb] : xq[kb + (kb < sw ? da : db)];
                     const f2_t dx = mul2(pk(fdiff(xi.x, xa.x), fdiff(xi.x, xb.x)), sxx);
                     const f2_t dy_ = mul2(pk(fdiff(xi.y, xa.y), fdiff(xi.y, xb.y)), syy);
                     const f2_t dz_ = mul2(pk(fdiff(xi.z, xa.z), fdiff(xi.z, xb.z)), szz);

@@ -4,8 +4,9 @@
 // classification pipeline with exact-CNA fallback.
 //
 // Parameters are one FP32 vector (PPMD_MLP_NPARAM values):
-//   W1[30][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
-// with y = x W + b (input-major weights).  Each call packs BF16 copies of
+//   mu[30] | isd[30] | W1[30][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
+// with x' = (x - mu) isd (input standardisation, fitted to the training
+// features, not trained) and y = x' W + b (input-major weights).  Each call packs BF16 copies of
 // the weights in the operand layouts the MMAs read.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -16,7 +17,8 @@
 
 namespace ppmd {
 
-constexpr int OFF_W1 = 0, OFF_B1 = 1920, OFF_W2 = 1984, OFF_B2 = 6080, OFF_W3 = 6144, OFF_B3 = 6400, NPARAM = 6404;
+constexpr int OFF_MU = 0, OFF_ISD = 30, OFF_W1 = 60, OFF_B1 = 1980, OFF_W2 = 2044, OFF_B2 = 6140, OFF_W3 = 6204,
+              OFF_B3 = 6460, NPARAM = 6464;
 static_assert(NPARAM == PPMD_MLP_NPARAM, "parameter count");
 
 // BF16 operand images (row strides padded so that fragment loads are free of
@@ -73,10 +75,16 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 __device__ __forceinline__ uint32_t ldg32(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const unsigned int *>(p)); }
+// Two adjacent input features (columns c, c+1) standardised and repacked.
+__device__ __forceinline__ uint32_t norm2(uint32_t raw, const float *mu, const float *isd, int c) {
+    __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162 *>(&raw);
+    return pack2((__low2float(v) - mu[c]) * isd[c], (__high2float(v) - mu[c + 1]) * isd[c + 1]);
+}
 
 struct MlpSmem {
     __nv_bfloat16 img[IMG_END];
     float bias[BIAS_FLOATS];  // b1[64] | b2[64] | b3[4] + 4 zeros
+    float mu[32], isd[32];    // input standardisation (columns 30, 31: 0)
 };
 
 __device__ __forceinline__ void load_mlp_smem(MlpSmem &sm, const __nv_bfloat16 *img, const float *p) {
@@ -85,6 +93,10 @@ __device__ __forceinline__ void load_mlp_smem(MlpSmem &sm, const __nv_bfloat16 *
     for (int e = threadIdx.x; e < IMG_END / 2; e += blockDim.x) dst[e] = src[e];
     for (int e = threadIdx.x; e < BIAS_FLOATS; e += blockDim.x)
         sm.bias[e] = e < 64 ? p[OFF_B1 + e] : (e < 128 ? p[OFF_B2 + e - 64] : (e < 132 ? p[OFF_B3 + e - 128] : 0.0f));
+    for (int e = threadIdx.x; e < 32; e += blockDim.x) {
+        sm.mu[e] = e < 30 ? p[OFF_MU + e] : 0.0f;
+        sm.isd[e] = e < 30 ? p[OFF_ISD + e] : 0.0f;
+    }
     __syncthreads();
 }
 
@@ -102,10 +114,11 @@ __device__ __forceinline__ void mlp_forward_tile(const MlpSmem &sm, const __nv_b
     uint32_t a[2][4];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        a[s][0] = x0 ? ldg32(x0 + 16 * s + 2 * t) : 0u;
-        a[s][1] = x1 ? ldg32(x1 + 16 * s + 2 * t) : 0u;
-        a[s][2] = x0 ? ldg32(x0 + 16 * s + 2 * t + 8) : 0u;
-        a[s][3] = x1 ? ldg32(x1 + 16 * s + 2 * t + 8) : 0u;
+        const int c0 = 16 * s + 2 * t, c1 = c0 + 8;
+        a[s][0] = x0 ? norm2(ldg32(x0 + c0), sm.mu, sm.isd, c0) : 0u;
+        a[s][1] = x1 ? norm2(ldg32(x1 + c0), sm.mu, sm.isd, c0) : 0u;
+        a[s][2] = x0 ? norm2(ldg32(x0 + c1), sm.mu, sm.isd, c1) : 0u;
+        a[s][3] = x1 ? norm2(ldg32(x1 + c1), sm.mu, sm.isd, c1) : 0u;
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -391,12 +404,18 @@ __global__ void __launch_bounds__(128) k_mlp_wgrad(int64_t B, int64_t chunk, con
                                                    const __nv_bfloat16 *__restrict__ H2,
                                                    const __nv_bfloat16 *__restrict__ D1,
                                                    const __nv_bfloat16 *__restrict__ D2,
-                                                   const __nv_bfloat16 *__restrict__ D3, float *__restrict__ part) {
+                                                   const __nv_bfloat16 *__restrict__ D3, const float *__restrict__ p,
+                                                   float *__restrict__ part) {
     // staged rows (padded strides against bank conflicts)
     __shared__ __nv_bfloat16 sx[WG_ROWS][40], sh1[WG_ROWS][72], sh2[WG_ROWS][72], sd1[WG_ROWS][72], sd2[WG_ROWS][72],
         sd3[WG_ROWS][8];
+    __shared__ float smu[32], sisd[32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int64_t s0 = (int64_t)blockIdx.x * chunk, s1 = min(B, s0 + chunk);
+    if (threadIdx.x < 32) {
+        smu[threadIdx.x] = threadIdx.x < 30 ? p[OFF_MU + threadIdx.x] : 0.0f;
+        sisd[threadIdx.x] = threadIdx.x < 30 ? p[OFF_ISD + threadIdx.x] : 0.0f;
+    }
     float acc[16][4];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
@@ -408,7 +427,8 @@ __global__ void __launch_bounds__(128) k_mlp_wgrad(int64_t B, int64_t chunk, con
             const int64_t row = base + r;
             const bool ok = row < s1;
             // 32-bit words: x row = 16 words, 64-wide rows = 32 words, d3 row = 4 words
-            if (c < 16) *reinterpret_cast<uint32_t *>(&sx[r][2 * c]) = ok ? ldg32(x + row * 32 + 2 * c) : 0u;
+            if (c < 16)
+                *reinterpret_cast<uint32_t *>(&sx[r][2 * c]) = ok ? norm2(ldg32(x + row * 32 + 2 * c), smu, sisd, 2 * c) : 0u;
             *reinterpret_cast<uint32_t *>(&sh1[r][2 * c]) = ok ? ldg32(H1 + row * 64 + 2 * c) : 0u;
             *reinterpret_cast<uint32_t *>(&sh2[r][2 * c]) = ok ? ldg32(H2 + row * 64 + 2 * c) : 0u;
             *reinterpret_cast<uint32_t *>(&sd1[r][2 * c]) = ok ? ldg32(D1 + row * 64 + 2 * c) : 0u;
@@ -508,6 +528,7 @@ __global__ void __launch_bounds__(128) k_mlp_wgrad(int64_t B, int64_t chunk, con
         out[OFF_B2 + lane] = bsum[2];
         out[OFF_B2 + lane + 32] = bsum[3];
         if (lane < 4) out[OFF_B3 + lane] = bsum[4];
+        for (int e = lane; e < OFF_W1; e += 32) out[e] = 0.0f;  // the standardisation is not trained
     }
 }
 
@@ -525,6 +546,7 @@ __global__ void k_adamw(float *__restrict__ p, float *__restrict__ m, float *__r
                         float lr, float wd, float b1, float b2, float eps, float c1, float c2) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= NPARAM) return;
+    if (e < OFF_W1) return;  // input standardisation: fitted, not trained
     const bool weight = (e < OFF_B1) || (e >= OFF_W2 && e < OFF_B2) || (e >= OFF_W3 && e < OFF_B3);
     const float gr = g[e];
     const float mm = b1 * m[e] + (1.0f - b1) * gr;
@@ -538,11 +560,53 @@ __global__ void k_adamw(float *__restrict__ p, float *__restrict__ m, float *__r
 }
 
 __global__ void k_sum_loss(const double *part, int nblk, float *loss) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[b];
-        *loss = (float)s;
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *loss = (float)sh[0];
+}
+
+// Input standardisation from n feature rows: per feature (thread f of 32)
+// sums of x and x^2 over rows, in FP64, one partial per block.
+__global__ void k_feat_stats(int64_t n, const __nv_bfloat16 *__restrict__ x, double *__restrict__ part) {
+    __shared__ double sh[8][32][2];
+    const int f = threadIdx.x & 31, rl = threadIdx.x >> 5;
+    double s = 0.0, s2 = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * 8 + rl; r < n; r += (int64_t)gridDim.x * 8) {
+        const double v = __bfloat162float(x[r * 32 + f]);
+        s += v;
+        s2 += v * v;
+    }
+    sh[rl][f][0] = s;
+    sh[rl][f][1] = s2;
+    __syncthreads();
+    if (rl == 0) {
+        for (int q = 1; q < 8; ++q) {
+            s += sh[q][f][0];
+            s2 += sh[q][f][1];
+        }
+        part[(blockIdx.x * 32 + f) * 2] = s;
+        part[(blockIdx.x * 32 + f) * 2 + 1] = s2;
+    }
+}
+
+__global__ void k_feat_norm(const double *__restrict__ part, int nblk, int64_t n, float *__restrict__ p) {
+    const int f = threadIdx.x;
+    if (f >= 30) return;
+    double s = 0.0, s2 = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+        s += part[(b * 32 + f) * 2];
+        s2 += part[(b * 32 + f) * 2 + 1];
+    }
+    const double mu = s / (double)n, var = fmax(s2 / (double)n - mu * mu, 0.0);
+    p[OFF_MU + f] = (float)mu;
+    p[OFF_ISD + f] = var > 1e-12 ? (float)(1.0 / sqrt(var)) : 1.0f;
 }
 
 int pack_weights(ppmd_ctx *ctx, const float *params, __nv_bfloat16 **img) {
@@ -590,10 +654,22 @@ extern "C" int ppmd_mlp_grad(ppmd_ctx *ctx, const float *params, const uint16_t 
     float *wpart = (float *)(lpart + fb_grid);
     PPMD_LAUNCH(ctx, k_mlp_fwd_bwd, fb_grid, MLP_WARPS * 32, 0, batch, (const __nv_bfloat16 *)x, y, img, params, H1, H2, D1, D2,
                 D3, lpart);
-    PPMD_LAUNCH(ctx, k_mlp_wgrad, wg_grid, 128, 0, batch, chunk, (const __nv_bfloat16 *)x, H1, H2, D1, D2, D3, wpart);
+    PPMD_LAUNCH(ctx, k_mlp_wgrad, wg_grid, 128, 0, batch, chunk, (const __nv_bfloat16 *)x, H1, H2, D1, D2, D3, params,
+                wpart);
     PPMD_LAUNCH(ctx, k_sum_partials, div_up(NPARAM, 256), 256, 0, wpart, wg_grid, grad);
-    if (loss) PPMD_LAUNCH(ctx, k_sum_loss, 1, 32, 0, lpart, fb_grid, loss);
+    if (loss) PPMD_LAUNCH(ctx, k_sum_loss, 1, 256, 0, lpart, fb_grid, loss);
     return check_launch(ctx, "ppmd_mlp_grad");
+}
+
+extern "C" int ppmd_mlp_fit_input_norm(ppmd_ctx *ctx, float *params, const uint16_t *x, int64_t n) {
+    if (!ctx || !params || n < 1 || !x) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_mlp_fit_input_norm: bad argument");
+    cudaSetDevice(ctx->device);
+    const int nblk = 256;
+    double *part = (double *)scratch(ctx, S_AUX2, sizeof(double) * nblk * 64);
+    if (!part) return PPMD_ERR_NOMEM;
+    PPMD_LAUNCH(ctx, k_feat_stats, nblk, 256, 0, n, (const __nv_bfloat16 *)x, part);
+    PPMD_LAUNCH(ctx, k_feat_norm, 1, 32, 0, part, nblk, n, params);
+    return check_launch(ctx, "ppmd_mlp_fit_input_norm");
 }
 
 extern "C" int ppmd_mlp_adamw(ppmd_ctx *ctx, float *params, float *m, float *v, const float *grad, int64_t step, float lr,
@@ -648,7 +724,7 @@ extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t
     int32_t *fb = (int32_t *)scratch(ctx, S_AUX1, sizeof(int32_t) * (nn + 1));
     if (!feat || !cls || !conf_s || !fb) return PPMD_ERR_NOMEM;
     int32_t *nfb = fb + nn;
-    PPMD_TRY(features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_feat, s.Lmax, nullptr, nullptr, feat));
+    PPMD_TRY(features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, r_cna, s.Lmax, nullptr, nullptr, feat));
     __nv_bfloat16 *img;
     PPMD_TRY(pack_weights(ctx, params, &img));
     PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(nfb, 0, sizeof(int32_t), ctx->stream), "memset"));
@@ -659,7 +735,7 @@ extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t
     int32_t hfb = 0;
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(&hfb, nfb, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
-    if (hfb > 0) PPMD_TRY(cna_subset_launch(ctx, hfb, fb, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, r_cna, s.Lmax, cls));
+    if (hfb > 0) PPMD_TRY(cna_subset_launch(ctx, hfb, fb, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, cls));
     if (n > 0) PPMD_LAUNCH(ctx, k_write_labels, div_up(n, 256), 256, 0, n, s.perm, cls, conf_s, label, confidence);
     if (n_fallback) *n_fallback = hfb;
     return check_launch(ctx, "ppmd_classify");

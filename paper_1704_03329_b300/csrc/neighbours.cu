@@ -25,10 +25,14 @@ __global__ void k_prep_fixed(const double *__restrict__ pos, int64_t n, SegTable
             bad = true;
             x = 0.0;
         }
-        double xw = wrap_exact(x, S.L[d]);
+        // the fixed-point word only needs x modulo L; the exact cell (when
+        // asked for) follows the documented wrap
+        const double xw = cell_of ? wrap_exact(x, S.L[d]) : ((x >= 0.0 && x < S.L[d]) ? x : wrap_exact(x, S.L[d]));
         q[d] = to_fixed(xw, S.fxs[d]);
-        int32_t cd = (int32_t)floor(__ddiv_rn(xw, S.w[d]));
-        c[d] = cd < 0 ? 0 : (cd > S.nc[d] - 1 ? S.nc[d] - 1 : cd);
+        if (cell_of) {
+            int32_t cd = (int32_t)floor(__ddiv_rn(xw, S.w[d]));
+            c[d] = cd < 0 ? 0 : (cd > S.nc[d] - 1 ? S.nc[d] - 1 : cd);
+        }
     }
     if (bad) latch_status(status, PPMD_ERR_NONFINITE);
     xq[i] = make_int4((int)q[0], (int)q[1], (int)q[2], sid);

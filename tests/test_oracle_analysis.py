@@ -153,36 +153,54 @@ def test_cna_labels_permutation_invariant():
     assert (lab == 2).sum() > 0
 
 
+def _tent14(values, lo, width):
+    """Reference tent histogram (14 bins of `width` centred on lo + width (b + 1/2))."""
+    h = np.zeros(14)
+    for v in values:
+        x = (v - lo) / width - 0.5
+        b0 = int(np.floor(x))
+        t = x - b0
+        if b0 < 0:
+            h[0] += 1
+        elif b0 >= 13:
+            h[13] += 1
+        else:
+            h[b0] += 1 - t
+            h[b0 + 1] += t
+    return h
+
+
 def test_features_perfect_fcc_closed_form():
     pos, box = _perfect("fcc")
     offs, nbr = oracle.neighbours_brute(pos, box, 1.5)
-    f = oracle.features(pos, box, offs, nbr, 1.5)
+    f = oracle.features(pos, box, offs, nbr, 1.5, R_CNA)
     d = (4.0 / RHO) ** (1.0 / 3.0) / np.sqrt(2.0)
     expect = np.zeros(30)
     expect[0], expect[1] = 0.19094065395649334, 0.5745242597140697
-    expect[2:14] = d / 1.5
+    expect[2:14] = (d - R_CNA) / (1.5 - R_CNA)
     expect[14:16] = 1.0
-    # 66 neighbour pairs: cos = 1/2 (24), 0 (12), -1/2 (24), -1 (6); tent bins
-    expect[16 + 10] = 24 / 66
-    expect[16 + 6] = expect[16 + 7] = 6 / 66
-    expect[16 + 3] = 24 / 66
-    expect[16 + 0] = 6 / 66
+    # 66 pairs of the 12 bonded neighbours: chords d (60 deg, 24 pairs),
+    # sqrt2 d (90, 12), sqrt3 d (120, 24), 2 d (180, 6)
+    chords = [d] * 24 + [np.sqrt(2) * d] * 12 + [np.sqrt(3) * d] * 24 + [2 * d] * 6
+    expect[16:] = _tent14(chords, R_CNA - 0.35, 0.05) / 24.0
     assert np.abs(f - expect).max() < 1e-9
 
 
-def test_features_rotation_invariant_and_normalised():
+def test_features_rotation_invariant_and_counts():
     rng = np.random.default_rng(8)
     cluster = rng.normal(0, 0.6, (30, 3))
     box = np.array([40.0, 40.0, 40.0])
     a = cluster + 20.0
     b = cluster @ _rotation(9).T + 17.5
     offs, nbr = oracle.neighbours_brute(a, box, 1.5)
-    fa = oracle.features(a, box, offs, nbr)
-    fb = oracle.features(b, box, offs, nbr)
+    fa = oracle.features(a, box, offs, nbr, 1.5, R_CNA)
+    fb = oracle.features(b, box, offs, nbr, 1.5, R_CNA)
     assert np.abs(fa - fb).max() < 1e-9
-    nn = np.diff(offs)
-    has2 = nn >= 2
-    assert np.allclose(fa[has2, 16:].sum(1), 1.0)
+    # the chord histogram holds one unit per pair of bonded neighbours
+    dist = np.sqrt(((a[:, None] - a[None]) ** 2).sum(-1))
+    np.fill_diagonal(dist, np.inf)
+    nb = (dist < R_CNA).sum(1)
+    assert np.allclose(fa[:, 16:].sum(1) * 24.0, nb * (nb - 1) / 2)
     assert (np.diff(fa[:, 2:16], axis=1) >= -1e-15).all()
 
 
@@ -194,9 +212,13 @@ def test_mlp_gradient_matches_finite_differences():
             p[k] = rng.normal(0, 0.1, p[k].shape)
     x = rng.normal(0, 1, (16, 30))
     y = rng.integers(0, 4, 16)
+    p = mlp.fit_input_norm(p, rng.normal(0.2, 0.5, (64, 30)))
     loss, g = mlp.loss_and_grad(p, x, y)
     h = 1e-6
     for k in p:
+        if k in ("mu", "isd"):
+            assert (g[k] == 0).all()  # fitted, not trained
+            continue
         flat = p[k].reshape(-1)
         for idx in rng.choice(flat.size, min(6, flat.size), replace=False):
             old = flat[idx]
@@ -207,6 +229,29 @@ def test_mlp_gradient_matches_finite_differences():
             flat[idx] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - g[k].reshape(-1)[idx]) < 1e-7 * max(1.0, abs(fd)), k
+
+
+def test_mlp_input_standardisation():
+    """fit_input_norm gives the standardised training features zero mean and
+    unit variance (a constant feature passes through unscaled), and the
+    forward pass with (mu, isd) equals the unstandardised network applied to
+    (x - mu) isd."""
+    rng = np.random.default_rng(3)
+    x = rng.normal(rng.uniform(-2, 2, 30), rng.uniform(0.1, 3.0, 30), (500, 30))
+    x[:, 4] = 0.7
+    p = mlp.fit_input_norm(mlp.init_params(rng), x)
+    z = (x - p["mu"]) * p["isd"]
+    keep = np.arange(30) != 4
+    assert np.allclose(z.mean(0), 0.0, atol=1e-12)
+    assert np.allclose(z[:, keep].std(0), 1.0, rtol=1e-12)
+    assert p["isd"][4] == 1.0 and np.abs(z[:, 4]).max() < 1e-12
+    q = dict(p, mu=np.zeros(30), isd=np.ones(30))
+    assert np.allclose(mlp.forward(p, x)[0], mlp.forward(q, z)[0], rtol=1e-12, atol=1e-12)
+    # AdamW leaves the standardisation alone
+    g = {k: np.ones_like(v) for k, v in p.items()}
+    mu0 = p["mu"].copy()
+    mlp.adamw_step(p, g, mlp.adamw_init(p), lr=0.1, wd=0.5)
+    assert np.array_equal(p["mu"], mu0)
 
 
 def test_adamw_textbook_steps():
