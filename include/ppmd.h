@@ -187,7 +187,9 @@ int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, d
  * cell internally, the list is built at max(r_boa, r_cna) and the results
  * are returned in caller order.  Bond order is computed when any of q4, q6,
  * n_nb is given (cutoff r_boa), CNA labels when label is given (cutoff
- * r_cna).  Synchronises once (list capacity check). */
+ * r_cna).  Synchronises once, at the end, to check the list capacity; if
+ * the list overflowed, the whole analysis is run again with the capacity
+ * that was needed. */
 int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
                  float *q4, float *q6, int32_t *n_nb, int8_t *label);
 
@@ -199,8 +201,9 @@ int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *bo
  * vector of PPMD_MLP_NPARAM values, laid out
  *   mu[30] | isd[30] | W1[30][64] | b1[64] | W2[64][64] | b2[64] | W3[64][4] | b3[4]
  * with x' = (x - mu) isd (input standardisation, set by
- * ppmd_mlp_fit_input_norm, never trained) and y = x' W + b.  Arithmetic: BF16 inputs, weights and activations, FP32
- * accumulation (tensor cores).                                          */
+ * ppmd_mlp_fit_input_norm, never trained) and y = x' W + b.
+ * Arithmetic: BF16 inputs, weights and activations, FP32 accumulation
+ * (tensor cores).                                                       */
 /* ------------------------------------------------------------------ */
 #define PPMD_MLP_NPARAM 6464
 
@@ -214,7 +217,8 @@ int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *bo
  * linear weights between centres, clamped at both ends, divided by 24.
  * Outputs (device, at
  * least one given): feat[n][30] FP32, feat_bf16[n][32] BF16 (last two 0),
- * caller order.  Synchronises once (list capacity check). */
+ * caller order.  Synchronises once at the end (list capacity check and
+ * rerun, as ppmd_analyze). */
 int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat, double r_ref,
                   float *feat, uint16_t *feat_bf16);
 /* Sets mu and isd of params to the mean and 1/standard deviation of each of
@@ -239,8 +243,10 @@ int ppmd_mlp_train_step(ppmd_ctx *ctx, float *params, float *m, float *v, int64_
  * mode 0: exact CNA (cutoff r_cna).  mode 1: features (cutoff r_feat >
  * r_cna, reference length r_cna) -> MLP -> class and confidence (max softmax probability, device
  * float [n], may be NULL); atoms with confidence < threshold are labelled
- * by exact CNA instead.  n_fallback (host, may be NULL) receives the number
- * of atoms labelled by CNA.  Synchronises. */
+ * by exact CNA instead (the device keeps the count: no synchronisation
+ * between the MLP and CNA).  n_fallback (host, may be NULL) receives the
+ * number of atoms labelled by CNA.  Synchronises once, at the end (list
+ * capacity check and rerun, as ppmd_analyze). */
 int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t n, const ppmd_box *box, double r_feat, double r_cna,
                   const float *params, float threshold, int8_t *label, float *confidence, int64_t *n_fallback);
 

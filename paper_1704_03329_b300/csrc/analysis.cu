@@ -178,22 +178,13 @@ __device__ __forceinline__ int32_t cna_label_of(int nu, int c421, int c422, int 
     return PPMD_OTHER;
 }
 
-__global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *__restrict__ xq,
-                                                        const double *__restrict__ pos64, SegTable st,
-                                                        const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
-                                                        int32_t max_nbr, int64_t si, int64_t sm, double rc2, float lo,
-                                                        float hi,
-                                                        const int32_t *__restrict__ out_idx, uint32_t *__restrict__ trip,
-                                                        int8_t *__restrict__ label, int32_t *status,
-                                                        unsigned long long *needed, const int32_t *__restrict__ which) {
-    __shared__ int32_t s_j[CNA_WARPS][64];
-    __shared__ int32_t s_slot[CNA_WARPS][64];
-    __shared__ int4 s_x[CNA_WARPS][64];
-    __shared__ unsigned long long s_A[CNA_WARPS][64];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t wi = (int64_t)blockIdx.x * CNA_WARPS + w;
-    if (wi >= n) return;
-    const int64_t i = which ? (int64_t)which[wi] : wi;  // a subset of the atoms when `which` is given
+__device__ __forceinline__ void cna_atom(int64_t i, int w, int lane, const int4 *__restrict__ xq,
+                                         const double *__restrict__ pos64, const SegTable &st,
+                                         const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
+                                         int32_t max_nbr, int64_t si, int64_t sm, double rc2, float lo, float hi,
+                                         const int32_t *__restrict__ out_idx, uint32_t *__restrict__ trip,
+                                         int8_t *__restrict__ label, int32_t *status, unsigned long long *needed,
+                                         int32_t *s_j, int32_t *s_slot, int4 *s_x, unsigned long long *s_A) {
     const int4 xi = xq[i];
     const Seg &S = seg_ref(st, xi.w);
     const int32_t deg = min(cnt[i], max_nbr);
@@ -217,9 +208,9 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
         if (b) {
             const int32_t a = nu + __popc(ball & lt);
             if (a < 64) {
-                s_j[w][a] = j;
-                s_slot[w][a] = k;
-                s_x[w][a] = xj;
+                s_j[a] = j;
+                s_slot[a] = k;
+                s_x[a] = xj;
             }
         }
         nu += __popc(ball);
@@ -237,22 +228,22 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
     // adjacency among the bonded neighbours
     for (int a = lane; a < nu; a += 32) {
         unsigned long long m = 0ull;
-        const int4 xa = s_x[w][a];
-        const int32_t ja = s_j[w][a];
+        const int4 xa = s_x[a];
+        const int32_t ja = s_j[a];
         for (int b = 0; b < nu; ++b) {
             if (b == a) continue;
-            if (bonded(xa, s_x[w][b], pos64 + 3 * (int64_t)ja, pos64 + 3 * (int64_t)s_j[w][b], S, rc2, lo, hi))
+            if (bonded(xa, s_x[b], pos64 + 3 * (int64_t)ja, pos64 + 3 * (int64_t)s_j[b], S, rc2, lo, hi))
                 m |= 1ull << b;
         }
-        s_A[w][a] = m;
+        s_A[a] = m;
     }
     __syncwarp();
     int c421 = 0, c422 = 0, c444 = 0, c666 = 0;
     for (int a = lane; a < nu; a += 32) {
-        const unsigned long long C = s_A[w][a];
+        const unsigned long long C = s_A[a];
         const int ncn = __popcll(C);
         int twice_nb = 0;
-        for (unsigned long long r = C; r; r &= r - 1) twice_nb += __popcll(s_A[w][__ffsll((long long)r) - 1] & C);
+        for (unsigned long long r = C; r; r &= r - 1) twice_nb += __popcll(s_A[__ffsll((long long)r) - 1] & C);
         // components of the common-neighbour graph
         int best = 0;
         unsigned long long rest = C;
@@ -261,18 +252,18 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
             unsigned long long frontier = comp;
             while (frontier) {
                 unsigned long long grow = 0ull;
-                for (unsigned long long f = frontier; f; f &= f - 1) grow |= s_A[w][__ffsll((long long)f) - 1];
+                for (unsigned long long f = frontier; f; f &= f - 1) grow |= s_A[__ffsll((long long)f) - 1];
                 grow &= C & ~comp;
                 comp |= grow;
                 frontier = grow;
             }
             int twice_e = 0;
-            for (unsigned long long f = comp; f; f &= f - 1) twice_e += __popcll(s_A[w][__ffsll((long long)f) - 1] & comp);
+            for (unsigned long long f = comp; f; f &= f - 1) twice_e += __popcll(s_A[__ffsll((long long)f) - 1] & comp);
             best = max(best, twice_e >> 1);
             rest &= ~comp;
         }
         const uint32_t t = ((uint32_t)ncn << 16) | ((uint32_t)(twice_nb >> 1) << 8) | (uint32_t)best;
-        if (trow) trow[s_slot[w][a]] = t;
+        if (trow) trow[s_slot[a]] = t;
         c421 += t == ((4u << 16) | (2u << 8) | 1u);
         c422 += t == ((4u << 16) | (2u << 8) | 2u);
         c444 += t == ((4u << 16) | (4u << 8) | 4u);
@@ -283,6 +274,30 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
     c444 = __reduce_add_sync(0xffffffffu, c444);
     c666 = __reduce_add_sync(0xffffffffu, c666);
     if (lane == 0 && label) label[out_idx ? out_idx[i] : i] = (int8_t)cna_label_of(nu, c421, c422, c444, c666);
+}
+
+__global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *__restrict__ xq,
+                                                        const double *__restrict__ pos64, SegTable st,
+                                                        const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
+                                                        int32_t max_nbr, int64_t si, int64_t sm, double rc2, float lo,
+                                                        float hi,
+                                                        const int32_t *__restrict__ out_idx, uint32_t *__restrict__ trip,
+                                                        int8_t *__restrict__ label, int32_t *status,
+                                                        unsigned long long *needed, const int32_t *__restrict__ which,
+                                                        const int32_t *__restrict__ n_dev) {
+    __shared__ int32_t s_j[CNA_WARPS][64];
+    __shared__ int32_t s_slot[CNA_WARPS][64];
+    __shared__ int4 s_x[CNA_WARPS][64];
+    __shared__ unsigned long long s_A[CNA_WARPS][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // the count comes from the device when the subset was chosen there
+    const int64_t m = n_dev ? (int64_t)*n_dev : n;
+    for (int64_t wi = (int64_t)blockIdx.x * CNA_WARPS + w; wi < m; wi += (int64_t)gridDim.x * CNA_WARPS) {
+        const int64_t i = which ? (int64_t)which[wi] : wi;  // a subset of the atoms when `which` is given
+        cna_atom(i, w, lane, xq, pos64, st, nbr, cnt, max_nbr, si, sm, rc2, lo, hi, out_idx, trip, label, status, needed,
+                 s_j[w], s_slot[w], s_x[w], s_A[w]);
+        __syncwarp();
+    }
 }
 
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
@@ -306,35 +321,40 @@ int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, co
     if (n > 0)
         PPMD_LAUNCH(ctx, k_cna, div_up(n, CNA_WARPS), CNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
                     ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_cut * r_cut,
-                    lo, hi, out_idx, trip, label, ctx->d_status, ctx->d_needed, nullptr);
+                    lo, hi, out_idx, trip, label, ctx->d_status, ctx->d_needed, nullptr, nullptr);
     return check_launch(ctx, "cna");
 }
 
-int cna_subset_launch(ppmd_ctx *ctx, int64_t m, const int32_t *which, const int4 *xq, const double *pos64,
-                      const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut,
-                      double Lmax, int8_t *label) {
+int cna_subset_launch(ppmd_ctx *ctx, int64_t m_max, const int32_t *m_dev, const int32_t *which, const int4 *xq,
+                      const double *pos64, const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr,
+                      int64_t ld, double r_cut, double Lmax, int8_t *label) {
     float lo, hi;
     cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
-    if (m > 0)
-        PPMD_LAUNCH(ctx, k_cna, div_up(m, CNA_WARPS), CNA_WARPS * 32, 0, m, xq, pos64, st, nbr, cnt, max_nbr,
+    // a grid of a few blocks per SM strides over however many atoms the
+    // device chose
+    const int64_t grid = std::min<int64_t>(div_up(m_max, CNA_WARPS), 148 * 8);
+    if (m_max > 0)
+        PPMD_LAUNCH(ctx, k_cna, grid, CNA_WARPS * 32, 0, m_max, xq, pos64, st, nbr, cnt, max_nbr,
                     ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_cut * r_cut,
-                    lo, hi, nullptr, nullptr, label, ctx->d_status, ctx->d_needed, which);
+                    lo, hi, nullptr, nullptr, label, ctx->d_status, ctx->d_needed, which, m_dev);
     return check_launch(ctx, "cna_subset");
 }
 
 
 // ---------------------------------------------------------------------
-// Local-environment features of the learned classifier, one warp per atom.
-// With nu bonds (r < r_feat) of unit vectors u_a and lengths d_a:
+// Local-environment features of the learned classifier, eight lanes per
+// atom.  With nu bonds (r < r_feat) of unit vectors u_a and lengths d_a,
+// and the nbd bonded neighbours (r < r_ref) at r_i - r_j = v_a:
 //   f[0], f[1]   Q4, Q6 (as k_boa);
 //   f[2..15]     the 14 smallest d_a, ascending, as (d_a - r_ref) / (r_feat - r_ref)
 //                (missing: 1);
-//   f[16..29]    histogram of cos(u_a, u_b) over all pairs a < b: 14 bins of
-//                width 1/7 on [-1, 1], linear weights between bin centres
-//                (clamped at both ends), divided by the number of pairs.
+//   f[16..29]    histogram of the chords |v_a - v_b| over the pairs a < b of
+//                bonded neighbours: 14 bins of width 0.05 centred at
+//                r_ref - 0.35 + 0.05 (k + 1/2), linear weights between bin
+//                centres (clamped at both ends), divided by 24.
 // Output: f32 [n][30] and/or bf16 [n][32] (f[30], f[31] = 0).
 // ---------------------------------------------------------------------
-constexpr int FEAT_WARPS = 4;
+constexpr int FEAT_WARPS = 4, FEAT_G = 8, FEAT_GROUPS = FEAT_WARPS * 32 / FEAT_G, FEAT_CAP = 64;
 
 __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const int4 *__restrict__ xq,
                                                               const double *__restrict__ pos64, SegTable st,
@@ -346,24 +366,30 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
                                                               const int32_t *__restrict__ out_idx,
                                                               float *__restrict__ f32, __nv_bfloat16 *__restrict__ fb16,
                                                               int32_t *status, unsigned long long *needed) {
-    __shared__ float3 s_u[FEAT_WARPS][64];
-    __shared__ float s_d[FEAT_WARPS][64];
-    __shared__ float3 s_v[FEAT_WARPS][64];  // r_i - r_j of the bonded neighbours (r < r_ref)
-    __shared__ float s_f[FEAT_WARPS][32];
-    __shared__ float s_red[FEAT_WARPS][32][39];  // per-lane partial sums (odd stride against bank conflicts)
-    __shared__ float s_mom[FEAT_WARPS][24];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * FEAT_WARPS + w;
-    if (i >= n) return;
+    // per-group rows padded to an odd number of words, so that the four
+    // groups of a warp reading entry a of their rows hit different banks
+    __shared__ float3 s_u[FEAT_GROUPS][FEAT_CAP + 1];
+    __shared__ float s_d[FEAT_GROUPS][FEAT_CAP + 1];
+    __shared__ float3 s_v[FEAT_GROUPS][FEAT_CAP + 1];
+    __shared__ float s_h[FEAT_GROUPS][FEAT_G][15];  // private histogram of each lane
+    __shared__ float s_f[FEAT_GROUPS][32];
+    const int gl = threadIdx.x & (FEAT_G - 1), g = threadIdx.x / FEAT_G, shift = threadIdx.x & 31 & ~(FEAT_G - 1);
+    const unsigned gmask = 0xffu << shift;
+    const int64_t i = (int64_t)blockIdx.x * FEAT_GROUPS + g;
+    if (i >= n) return;  // whole groups leave together
     const int4 xi = xq[i];
     const Seg &S = seg_ref(st, xi.w);
     const int32_t deg = min(cnt[i], max_nbr);
     const int32_t *row = nbr + i * si;
-    const unsigned lt = (1u << lane) - 1u;
-    s_f[w][lane] = (lane >= 2 && lane < 16) ? 1.0f : 0.0f;
+    const unsigned lt = (1u << gl) - 1u;
+    float *hist = s_h[g][gl];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) hist[k] = 0.0f;
+#pragma unroll
+    for (int c = gl; c < 32; c += FEAT_G) s_f[g][c] = (c >= 2 && c < 16) ? 1.0f : 0.0f;
     int32_t nu = 0, nbd = 0;
-    for (int32_t base = 0; base < deg; base += 32) {
-        const int32_t k = base + lane;
+    for (int32_t base = 0; base < deg; base += FEAT_G) {
+        const int32_t k = base + gl;
         bool b = false, bb = false;
         float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
         if (k < deg) {
@@ -390,124 +416,120 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
             }
             bb = bb && b;
         }
-        const unsigned ball = __ballot_sync(0xffffffffu, b);
-        const unsigned bbal = __ballot_sync(0xffffffffu, bb);
+        const unsigned ball = __ballot_sync(gmask, b) >> shift, bbal = __ballot_sync(gmask, bb) >> shift;
         if (b) {
             const int32_t a = nu + __popc(ball & lt);
-            if (a < 64) {
+            if (a < FEAT_CAP) {
                 const float r = sqrtf(r2), ir = 1.0f / r;
-                s_u[w][a] = make_float3(dx * ir, dy * ir, dz * ir);
-                s_d[w][a] = r;
+                s_u[g][a] = make_float3(dx * ir, dy * ir, dz * ir);
+                s_d[g][a] = r;
             }
         }
         if (bb) {
             const int32_t a = nbd + __popc(bbal & lt);
-            if (a < 64) s_v[w][a] = make_float3(dx, dy, dz);
+            if (a < FEAT_CAP) s_v[g][a] = make_float3(dx, dy, dz);
         }
         nu += __popc(ball);
         nbd += __popc(bbal);
     }
-    if (nu > 64) {
-        if (lane == 0) {
+    if (nu > FEAT_CAP) {
+        if (gl == 0) {
             latch_status(status, PPMD_ERR_CAPACITY);
             latch_needed(needed, (unsigned long long)nu);
         }
-        nu = 64;
+        nu = FEAT_CAP;
     }
-    nbd = min(nbd, 64);
-    __syncwarp();
-    // Q4, Q6: each lane its bonds; the 24 moment sums are reduced through
-    // shared memory (one column per lane)
+    nbd = min(nbd, FEAT_CAP);
+    __syncwarp(gmask);
+    // Q4, Q6: each lane its bonds, moment sums reduced over the group
     float r4[5], i4[5], r6[7], i6[7];
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
         if (m < 5) r4[m] = i4[m] = 0.0f;
         r6[m] = i6[m] = 0.0f;
     }
-    for (int a = lane; a < nu; a += 32) {
-        const float3 u = s_u[w][a];
+    for (int a = gl; a < nu; a += FEAT_G) {
+        const float3 u = s_u[g][a];
         boa_accumulate(K, u.x, u.y, u.z, r4, i4, r6, i6);
     }
-    float *red = s_red[w][lane];
+    float s4 = 0.0f, s6 = 0.0f;
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
-        if (m < 5) {
-            red[2 * m] = r4[m];
-            red[2 * m + 1] = i4[m];
-        }
-        red[10 + 2 * m] = r6[m];
-        red[10 + 2 * m + 1] = i6[m];
-    }
-    // histogram of the chords |r_ij - r_ik| of the bond angles between
-    // bonded neighbours: the nbd (nbd-1)/2 pairs spread evenly over the
-    // lanes, tent weights accumulated in registers
-    float h[14];
 #pragma unroll
-    for (int b = 0; b < 14; ++b) h[b] = 0.0f;
+        for (int o = FEAT_G / 2; o > 0; o >>= 1) {
+            if (m < 5) {
+                r4[m] += __shfl_xor_sync(gmask, r4[m], o);
+                i4[m] += __shfl_xor_sync(gmask, i4[m], o);
+            }
+            r6[m] += __shfl_xor_sync(gmask, r6[m], o);
+            i6[m] += __shfl_xor_sync(gmask, i6[m], o);
+        }
+        if (m < 5) s4 = fmaf(r4[m], r4[m], fmaf(i4[m], i4[m], s4));
+        s6 = fmaf(r6[m], r6[m], fmaf(i6[m], i6[m], s6));
+    }
+    // chord histogram: the nbd (nbd - 1) / 2 pairs spread over the lanes,
+    // tent weights added to the lane's own row
     const int npair = nbd * (nbd - 1) / 2;
     const float hlo = r_ref - 0.35f;
-    for (int pidx = lane; pidx < npair; pidx += 32) {
+    for (int pidx = gl; pidx < npair; pidx += FEAT_G) {
         // pair (a, b), a < b, with pidx = a (2 nbd - a - 1) / 2 + (b - a - 1)
         const float q = (float)(2 * nbd - 1);
         int a = (int)floorf(0.5f * (q - sqrtf(fmaxf(q * q - 8.0f * pidx, 0.0f))));
         while (a > 0 && a * (2 * nbd - a - 1) / 2 > pidx) --a;
         while ((a + 1) * (2 * nbd - a - 2) / 2 <= pidx) ++a;
         const int b = pidx - a * (2 * nbd - a - 1) / 2 + a + 1;
-        const float3 va = s_v[w][a], vb = s_v[w][b];
+        const float3 va = s_v[g][a], vb = s_v[g][b];
         const float cx = va.x - vb.x, cy = va.y - vb.y, cz = va.z - vb.z;
         const float chord = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
         const float x = (chord - hlo) * 20.0f - 0.5f;
         const float fl = floorf(x);
         const int b0 = (int)fl;
-        const float t = x - fl;
-#pragma unroll
-        for (int k = 0; k < 14; ++k) {
-            float add = 0.0f;
-            if (b0 < 0) add = (k == 0) ? 1.0f : 0.0f;
-            else if (b0 >= 13) add = (k == 13) ? 1.0f : 0.0f;
-            else add = (k == b0) ? 1.0f - t : ((k == b0 + 1) ? t : 0.0f);
-            h[k] += add;
-        }
+        const bool edge = b0 < 0 || b0 >= 13;
+        const float t = edge ? 0.0f : x - fl;
+        hist[min(max(b0, 0), 13)] += 1.0f - t;
+        hist[min(max(b0 + 1, 0), 13)] += t;
     }
-#pragma unroll
-    for (int k = 0; k < 14; ++k) red[24 + k] = h[k];
     // sorted bond lengths: the rank of each
-    for (int a = lane; a < nu; a += 32) {
-        const float da = s_d[w][a];
+    for (int a = gl; a < nu; a += FEAT_G) {
+        const float da = s_d[g][a];
         int rank = 0;
         for (int b = 0; b < nu; ++b) {
-            const float db = s_d[w][b];
+            const float db = s_d[g][b];
             rank += (db < da) || (db == da && b < a);
         }
-        if (rank < 14) s_f[w][2 + rank] = (da - r_ref) * inv_span;
+        if (rank < 14) s_f[g][2 + rank] = (da - r_ref) * inv_span;
     }
-    __syncwarp();
-    // column sums: lane c < 38 sums entry c over the 32 lanes
-    float colsum = 0.0f;
-    for (int c = lane; c < 38; c += 32) {
+    __syncwarp(gmask);
+    for (int c = gl; c < 14; c += FEAT_G) {
         float acc = 0.0f;
-        for (int l = 0; l < 32; ++l) acc += s_red[w][l][c];
-        if (c < 24) s_mom[w][c] = acc;
-        else colsum = acc;
-        if (c >= 24) s_f[w][16 + c - 24] = acc;
+#pragma unroll
+        for (int l = 0; l < FEAT_G; ++l) acc += s_h[g][l][c];
+        s_f[g][16 + c] = acc * (1.0f / 24.0f);
     }
-    (void)colsum;
-    __syncwarp();
-    if (lane == 0) {
+    if (gl == 0) {
         const float inv = nu > 0 ? 1.0f / (float)nu : 0.0f;
-        float s4 = 0.0f, s6 = 0.0f;
-        for (int c = 0; c < 10; ++c) s4 = fmaf(s_mom[w][c], s_mom[w][c], s4);
-        for (int c = 10; c < 24; ++c) s6 = fmaf(s_mom[w][c], s_mom[w][c], s6);
-        s_f[w][0] = sqrtf(s4) * inv;
-        s_f[w][1] = sqrtf(s6) * inv;
+        s_f[g][0] = sqrtf(s4) * inv;
+        s_f[g][1] = sqrtf(s6) * inv;
     }
-    __syncwarp();
-    float v = s_f[w][lane];
-    if (lane >= 16 && lane < 30) v *= 1.0f / 24.0f;
-    if (lane >= 30) v = 0.0f;
+    __syncwarp(gmask);
     const int64_t o = out_idx ? out_idx[i] : i;
-    if (f32 && lane < 30) f32[o * 30 + lane] = v;
-    if (fb16) fb16[o * 32 + lane] = __float2bfloat16_rn(v);
+    const float4 v = make_float4(s_f[g][4 * gl], s_f[g][4 * gl + 1], s_f[g][4 * gl + 2], s_f[g][4 * gl + 3]);
+    if (f32) {
+        float *dst = f32 + o * 30 + 4 * gl;
+        dst[0] = v.x;
+        dst[1] = v.y;
+        if (gl < 7) {
+            dst[2] = v.z;
+            dst[3] = v.w;
+        }
+    }
+    if (fb16) {
+        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(v.x, v.y), hi2 = __floats2bfloat162_rn(v.z, v.w);
+        uint2 w2;
+        w2.x = *reinterpret_cast<const uint32_t *>(&lo2);
+        w2.y = *reinterpret_cast<const uint32_t *>(&hi2);
+        *reinterpret_cast<uint2 *>(fb16 + o * 32 + 4 * gl) = w2;
+    }
 }
 
 int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st,
@@ -518,7 +540,7 @@ int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos6
     cutoff_band(r_feat * r_feat, Lmax, &lo, &hi);
     cutoff_band(r_ref * r_ref, Lmax, &blo, &bhi);
     if (n > 0)
-        PPMD_LAUNCH(ctx, k_features, div_up(n, FEAT_WARPS), FEAT_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
+        PPMD_LAUNCH(ctx, k_features, div_up(n, FEAT_GROUPS), FEAT_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
                     ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_feat * r_feat, lo, hi, r_ref * r_ref, blo, bhi, (float)r_ref, (float)(1.0 / (r_feat - r_ref)), K, out_idx, f32, fb16,
                     ctx->d_status, ctx->d_needed);
     return check_launch(ctx, "features");
@@ -534,6 +556,16 @@ __global__ void k_gather_pos(int64_t n, const int32_t *__restrict__ perm, const 
     const int64_t j = perm[k];
 #pragma unroll
     for (int d = 0; d < 3; ++d) pos_o[3 * k + d] = pos[3 * j + d];
+}
+
+int end_pipeline(ppmd_ctx *ctx, int attempt, int32_t &max_nbr, int32_t *aux) {
+    int64_t need = 0;
+    const int rc = status_sync(ctx, &need, aux);
+    if (rc == PPMD_ERR_CAPACITY && attempt == 0 && need > max_nbr) {
+        max_nbr = (int32_t)((need + 15) / 16 * 16);
+        return PIPELINE_RETRY;
+    }
+    return rc;
 }
 
 int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int32_t max_nbr,
@@ -552,34 +584,23 @@ int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box 
     s.perm = (int32_t *)scratch(ctx, S_CELLS2, sizeof(int32_t) * nn);
     s.pos = (double *)scratch(ctx, S_SORTPOS, sizeof(double) * 3 * nn);
     s.xq = (int4 *)scratch(ctx, S_AUX0, sizeof(int4) * nn);
-    std::vector<Brick> bl;
-    make_bricks(std::vector<Seg>(1, s.st.one), bl);
-    Brick *bricks = (Brick *)scratch(ctx, S_SORTIDX, sizeof(Brick) * (bl.size() + 1));
-    if (!cell0 || !s.cell_start || !s.perm || !s.pos || !s.xq || !bricks) return PPMD_ERR_NOMEM;
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice,
-                                             ctx->stream), "copy"));
+    if (!cell0 || !s.cell_start || !s.perm || !s.pos || !s.xq) return PPMD_ERR_NOMEM;
+    // one segment: bricks are cut from the grid inside the kernel
+    s.st.one.atom1 = n;
+    const BrickShape shape = brick_shape(s.st.one);
+    const int64_t nbricks = brick_count(s.st.one, shape);
     // bin (positions need not be wrapped), sort by cell, fixed point in cell order
     PPMD_TRY(bin_atoms(ctx, pos, n, s.st, nullptr, ncell, false, cell0, s.cell_start, s.perm));
     if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos, div_up(n, 256), 256, 0, n, s.perm, pos, s.pos);
     PPMD_TRY(prep_fixed(ctx, s.pos, n, s.st, nullptr, s.xq, nullptr));
     s.ld = (n + 31) / 32 * 32;
     PPMD_TRY(neigh_brick_setup(ctx, max_nbr));
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        s.max_nbr = max_nbr;
-        s.nbr = (int32_t *)scratch(ctx, S_NBR, sizeof(int32_t) * (size_t)s.ld * (size_t)max_nbr);
-        s.cnt = (int32_t *)scratch(ctx, S_NBRCNT, sizeof(int32_t) * nn);
-        if (!s.nbr || !s.cnt) return PPMD_ERR_NOMEM;
-        PPMD_TRY(build_list_bricks(ctx, (int64_t)bl.size(), bricks, s.xq, s.pos, s.st, s.cell_start, s.nbr, s.ld, s.cnt,
-                                   max_nbr));
-        int64_t need = 0;
-        int rc = ppmd_status(ctx, &need);
-        if (rc == PPMD_ERR_CAPACITY && attempt == 0) {
-            max_nbr = (int32_t)((need + 15) / 16 * 16);
-            continue;
-        }
-        if (rc < 0) return rc;
-        break;
-    }
+    s.max_nbr = max_nbr;
+    s.nbr = (int32_t *)scratch(ctx, S_NBR, sizeof(int32_t) * (size_t)s.ld * (size_t)max_nbr);
+    s.cnt = (int32_t *)scratch(ctx, S_NBRCNT, sizeof(int32_t) * nn);
+    if (!s.nbr || !s.cnt) return PPMD_ERR_NOMEM;
+    PPMD_TRY(build_list_bricks(ctx, nbricks, nullptr, shape, s.xq, s.pos, s.st, s.cell_start, s.nbr, s.ld, s.cnt,
+                               max_nbr));
     return PPMD_OK;
 }
 
@@ -635,11 +656,17 @@ extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const p
     cudaSetDevice(ctx->device);
     double r_list = fmax(want_boa ? r_boa : 0.0, want_cna ? r_cna : 0.0);
     if (!(r_list > 0)) return PPMD_OK;
-    Snapshot s;
-    PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_list, 32, s));
-    if (want_boa) PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
-    if (want_cna) PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, s.perm, nullptr, label));
-    return PPMD_OK;
+    int32_t max_nbr = SNAPSHOT_NBR;
+    for (int attempt = 0;; ++attempt) {
+        Snapshot s;
+        PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_list, max_nbr, s));
+        if (want_boa)
+            PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
+        if (want_cna)
+            PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, s.perm, nullptr, label));
+        const int rc = end_pipeline(ctx, attempt, max_nbr);
+        if (rc != PIPELINE_RETRY) return rc;
+    }
 }
 
 extern "C" int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat,
@@ -647,8 +674,13 @@ extern "C" int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const 
     if (!ctx || !box || n < 0 || (n > 0 && !pos) || !(r_feat > 0) || !(r_ref < r_feat) || (!feat && !feat_bf16))
         return set_error(ctx, PPMD_ERR_INVALID, "ppmd_features: bad argument");
     cudaSetDevice(ctx->device);
-    Snapshot s;
-    PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, 32, s));
-    return features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, r_ref, s.Lmax, s.perm, feat,
-                           (__nv_bfloat16 *)feat_bf16);
+    int32_t max_nbr = SNAPSHOT_NBR;
+    for (int attempt = 0;; ++attempt) {
+        Snapshot s;
+        PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, max_nbr, s));
+        PPMD_TRY(features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, r_ref, s.Lmax, s.perm,
+                                 feat, (__nv_bfloat16 *)feat_bf16));
+        const int rc = end_pipeline(ctx, attempt, max_nbr);
+        if (rc != PIPELINE_RETRY) return rc;
+    }
 }

@@ -21,8 +21,15 @@ struct Snapshot {
     int64_t ld = 0;  // column-major list: entry m of atom i at nbr[m * ld + i]
 };
 // Bin/sort the caller's atoms with cells of edge >= r_list and build the
-// list at r_list (row capacity grown once if max_nbr is too small).
-// Synchronises once to check the list capacity.
+// list at r_list with max_nbr entries per atom (no synchronisation: an
+// overflow is latched in the context's status).
+constexpr int32_t SNAPSHOT_NBR = 32;  // first list capacity of the analysis pipelines
+// End of a pipeline: wait and read the status (and the aux result word).
+// Returns PIPELINE_RETRY when the list overflowed on the first attempt, with
+// max_nbr raised to what was needed (the caller runs the pipeline again),
+// else the status.
+constexpr int PIPELINE_RETRY = 1;
+int end_pipeline(ppmd_ctx *ctx, int attempt, int32_t &max_nbr, int32_t *aux = nullptr);
 int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int32_t max_nbr,
                     Snapshot &s);
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
@@ -33,7 +40,7 @@ int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, co
                int8_t *label);
 // CNA labels of the snapshot atoms listed in `which` (m of them), written
 // at label[which[k]].
-int cna_subset_launch(ppmd_ctx *ctx, int64_t m, const int32_t *which, const int4 *xq, const double *pos64,
+int cna_subset_launch(ppmd_ctx *ctx, int64_t m_max, const int32_t *m_dev, const int32_t *which, const int4 *xq, const double *pos64,
                       const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut,
                       double Lmax, int8_t *label);
 // Classifier features (30 per atom) of the snapshot atoms, written at out_idx.

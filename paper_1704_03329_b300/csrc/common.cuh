@@ -120,6 +120,9 @@ __device__ __forceinline__ const Seg &seg_ref(const SegTable &t, int32_t s) { re
 
 // Host: fill a segment for box L, cell grid for min_cell_width (0 = none).
 int make_seg(ppmd_ctx *ctx, Seg &s, const double L[3], double min_cell_width, double r_list);
+// Wait for the stream and read the latched status (as ppmd_status); with
+// aux, also the int32 result word that kernels may leave at d_status[4].
+int status_sync(ppmd_ctx *ctx, int64_t *needed, int32_t *aux);
 // FP32 decision band for a squared cutoff rc2 in a box of largest edge Lmax.
 void cutoff_band(double rc2, double Lmax, float *lo, float *hi);
 

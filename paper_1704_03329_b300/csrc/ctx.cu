@@ -256,13 +256,16 @@ extern "C" int ppmd_set_stream(ppmd_ctx *ctx, void *cuda_stream) {
     return PPMD_OK;
 }
 
-extern "C" int ppmd_status(ppmd_ctx *ctx, int64_t *needed) {
+namespace ppmd {
+int status_sync(ppmd_ctx *ctx, int64_t *needed, int32_t *aux) {
     if (!ctx) return PPMD_ERR_INVALID;
     cudaSetDevice(ctx->device);
-    int rc = cuda_check(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, 16, cudaMemcpyDeviceToHost, ctx->stream),
+    int rc = cuda_check(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, aux ? 24 : 16, cudaMemcpyDeviceToHost,
+                                             ctx->stream),
                         "status copy");
     if (rc == PPMD_OK) rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     if (rc != PPMD_OK) return rc;
+    if (aux) *aux = ctx->h_status[4];
     int32_t st = ctx->h_status[0];
     int64_t nd = (int64_t)ctx->h_needed[0];
     if (ctx->host_needed > nd) nd = ctx->host_needed;
@@ -277,6 +280,9 @@ extern "C" int ppmd_status(ppmd_ctx *ctx, int64_t *needed) {
     }
     return st;
 }
+}  // namespace ppmd
+
+extern "C" int ppmd_status(ppmd_ctx *ctx, int64_t *needed) { return status_sync(ctx, needed, nullptr); }
 
 extern "C" int ppmd_sync(ppmd_ctx *ctx) { return ppmd_status(ctx, nullptr); }
 

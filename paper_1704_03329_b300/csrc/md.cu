@@ -121,8 +121,8 @@ int rebuild(ppmd_md *m) {
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq_ref, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, m->xq, m->pos, m->st, m->cell_start, m->W, m->ld, m->cnt,
-                               m->p.max_nbr));
+    PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, BrickShape{1, 1, 1}, m->xq, m->pos, m->st, m->cell_start,
+                               m->W, m->ld, m->cnt, m->p.max_nbr));
     return PPMD_OK;
 }
 

@@ -51,25 +51,45 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+BrickShape brick_shape(const Seg &S) {
+    // the neighbourhood spans bw + 2 cells of a row, bh + 2 rows and bd + 2
+    // planes; they must be distinct cells of the periodic grid
+    const double pc = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
+    const int32_t mw = std::max(1, std::min(BW_MAX, S.nc[0] - 2)), mh = std::max(1, std::min(BH_MAX, S.nc[1] - 2)),
+                  md = std::max(1, std::min(BD_MAX, S.nc[2] - 2));
+    BrickShape best{1, 1, 1};
+    double best_home = -1.0, best_halo = 0.0;
+    for (int32_t bd = 1; bd <= md; ++bd)
+        for (int32_t bh = 1; bh <= mh; ++bh)
+            for (int32_t bw = 1; bw <= mw; ++bw) {
+                const double cells = (double)bw * bh * bd, hood = (double)(bw + 2) * (bh + 2) * (bd + 2);
+                const double home = pc * cells;
+                if (1.5 * pc * hood > NB_MAX || home > BRICK_THREADS) continue;
+                const double halo = hood / cells;
+                if (home > best_home * (1.0 + 1e-9) || (home >= best_home * (1.0 - 1e-9) && halo < best_halo)) {
+                    best = BrickShape{bw, bh, bd};
+                    best_home = home;
+                    best_halo = halo;
+                }
+            }
+    return best;
+}
+
+int64_t brick_count(const Seg &S, BrickShape b) {
+    return (int64_t)((S.nc[0] + b.bw - 1) / b.bw) * ((S.nc[1] + b.bh - 1) / b.bh) * ((S.nc[2] + b.bd - 1) / b.bd);
+}
+
 void make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out) {
     out.clear();
     for (size_t s = 0; s < segs.size(); ++s) {
         const Seg &S = segs[s];
-        // the neighbourhood spans bw + 2 cells of a row and bh + 2 rows; they
-        // must be distinct cells of the periodic grid, and its expected size
-        // (with a margin for density fluctuations) should fit in shared memory
-        int32_t bw = std::min(3, S.nc[0] - 2), bh = std::min(2, S.nc[1] - 2);
-        const double per_cell = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
-        auto fits = [&](int32_t w, int32_t h) { return 1.5 * per_cell * 3.0 * (w + 2) * (h + 2) <= NB_MAX; };
-        while (!fits(bw, bh) && (bw > 1 || bh > 1)) {
-            if (bh > 1) bh -= 1;
-            else bw -= 1;
-        }
-        for (int32_t z = 0; z < S.nc[2]; ++z)
-            for (int32_t y0 = 0; y0 < S.nc[1]; y0 += bh)
-                for (int32_t x0 = 0; x0 < S.nc[0]; x0 += bw) {
-                    const int32_t x1 = std::min(x0 + bw, S.nc[0]), y1 = std::min(y0 + bh, S.nc[1]);
-                    out.push_back(Brick{(int32_t)s, x0 | (x1 << 16), y0 | (y1 << 16), z});
+        const BrickShape b = brick_shape(S);
+        for (int32_t z0 = 0; z0 < S.nc[2]; z0 += b.bd)
+            for (int32_t y0 = 0; y0 < S.nc[1]; y0 += b.bh)
+                for (int32_t x0 = 0; x0 < S.nc[0]; x0 += b.bw) {
+                    const int32_t x1 = std::min(x0 + b.bw, S.nc[0]), y1 = std::min(y0 + b.bh, S.nc[1]),
+                                  z1 = std::min(z0 + b.bd, S.nc[2]);
+                    out.push_back(Brick{(int32_t)s, x0 | (x1 << 16), y0 | (y1 << 16), z0 | (z1 << 16)});
                 }
     }
 }
@@ -88,80 +108,113 @@ __device__ __forceinline__ float fdiff(int32_t a, int32_t b) { return __int2floa
 // two candidates per packed step; threads of the same cell read the same
 // candidate, so the shared-memory reads are broadcasts.  Hits go straight
 // to the atom's column of W.
-__global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__restrict__ bricks,
+__global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
                                                                const int4 *__restrict__ xq,
                                                                const double *__restrict__ pos64, SegTable st,
                                                                const int32_t *__restrict__ cs, int32_t *__restrict__ W,
                                                                int64_t ld, int32_t *__restrict__ cnt, int32_t max_nbr,
                                                                int32_t *status, unsigned long long *needed) {
+    constexpr int NROW = (BH_MAX + 2) * (BD_MAX + 2), NHOME = BH_MAX * BD_MAX;
     extern __shared__ __align__(16) unsigned char smem[];
     int4 *s_x = (int4 *)smem;
-    __shared__ int32_t s_cell[12][6];  // local start of the row's cells t = 0 .. bw+2
-    __shared__ int32_t s_da[12], s_db[12], s_sw[12];  // global = local + (local < sw ? da : db)
-    __shared__ int32_t s_home[2][4];   // cell starts of the home cells of each home row
+    __shared__ int32_t s_cell[NROW][BW_MAX + 3];  // start of the row's cells t = 0 .. bw+2 in the stage
+    __shared__ int32_t s_da[NROW], s_db[NROW], s_sw[NROW];  // global = local + (local < sw ? da : db)
+    __shared__ int32_t s_home[NHOME][BW_MAX + 1];  // cell starts of the home cells of each home row
+    __shared__ int32_t s_hoff[32];                 // first home index of each home row (then H)
     __shared__ int32_t s_total;
 
-    const Brick B = bricks[blockIdx.x];
+    Brick B;
+    if (bricks) {
+        B = bricks[blockIdx.x];
+    } else {
+        const Seg &S0 = seg_ref(st, 0);
+        const int32_t nbx = (S0.nc[0] + shape.bw - 1) / shape.bw, nby = (S0.nc[1] + shape.bh - 1) / shape.bh;
+        const int32_t bx = (int32_t)(blockIdx.x % nbx), by = (int32_t)((blockIdx.x / nbx) % nby),
+                      bz = (int32_t)(blockIdx.x / ((int64_t)nbx * nby));
+        const int32_t x0 = bx * shape.bw, y0 = by * shape.bh, z0 = bz * shape.bd;
+        B.seg = 0;
+        B.x01 = x0 | (min(x0 + shape.bw, S0.nc[0]) << 16);
+        B.y01 = y0 | (min(y0 + shape.bh, S0.nc[1]) << 16);
+        B.z01 = z0 | (min(z0 + shape.bd, S0.nc[2]) << 16);
+    }
     const Seg &S = seg_ref(st, B.seg);
     const int32_t nx = S.nc[0], ny = S.nc[1], nz = S.nc[2];
-    const int32_t x0 = B.x01 & 0xffff, x1 = B.x01 >> 16, y0 = B.y01 & 0xffff, y1 = B.y01 >> 16, z = B.z;
-    const int32_t bw = x1 - x0, bh = y1 - y0, nyr = bh + 2, nrow = 3 * nyr;
-    const int tid = threadIdx.x;
-    if (tid < nrow) {
-        const int32_t yy = wrapi(y0 - 1 + tid % nyr, ny), zz = wrapi(z + tid / nyr - 1, nz);
-        const int32_t rb = S.cell0 + (zz * ny + yy) * nx;
-        int32_t acc = 0;
-        for (int t = 0; t <= bw + 1; ++t) {
-            const int32_t x = wrapi(x0 - 1 + t, nx);
-            s_cell[tid][t] = acc;
-            acc += cs[rb + x + 1] - cs[rb + x];
+    const int32_t x0 = B.x01 & 0xffff, x1 = B.x01 >> 16, y0 = B.y01 & 0xffff, y1 = B.y01 >> 16;
+    const int32_t z0 = B.z01 & 0xffff, z1 = B.z01 >> 16;
+    const int32_t bw = x1 - x0, bh = y1 - y0, bd = z1 - z0, nyr = bh + 2, nrow = nyr * (bd + 2), nhome = bh * bd;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        // warp 0: the staged rows, their cell offsets and their mapping back
+        // to the sorted order
+        int32_t tot = 0, rb = 0;
+        if (tid < nrow) {
+            const int32_t yy = wrapi(y0 - 1 + tid % nyr, ny), zz = wrapi(z0 - 1 + tid / nyr, nz);
+            rb = S.cell0 + (zz * ny + yy) * nx;
+            for (int t = 0; t <= bw + 1; ++t) {
+                const int32_t x = wrapi(x0 - 1 + t, nx);
+                s_cell[tid][t] = tot;
+                tot += cs[rb + x + 1] - cs[rb + x];
+            }
+            s_cell[tid][bw + 2] = tot;
         }
-        s_cell[tid][bw + 2] = acc;
-    }
-    if (tid >= 32 && tid < 32 + bh) {
-        const int32_t r = tid - 32;
-        const int32_t rm = S.cell0 + (z * ny + y0 + r) * nx;
-        for (int t = 0; t <= bw; ++t) s_home[r][t] = cs[rm + x0 + t];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int32_t base = 0;
-        for (int r = 0; r < nrow; ++r) {
-            const int32_t yy = wrapi(y0 - 1 + r % nyr, ny), zz = wrapi(z + r / nyr - 1, nz);
-            const int32_t rb = S.cell0 + (zz * ny + yy) * nx;
-            const int32_t tot = s_cell[r][bw + 2];
-            for (int t = 0; t <= bw + 2; ++t) s_cell[r][t] += base;
+        int32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int32_t base = inc - tot;
+        if (tid < nrow) {
+            for (int t = 0; t <= bw + 2; ++t) s_cell[tid][t] += base;
             const int32_t xa = x0 - 1, xb = x1;  // inclusive cell range of the row
             if (xa < 0) {  // cell nx-1 first, then cells 0 .. xb
                 const int32_t len1 = cs[rb + nx] - cs[rb + nx - 1];
-                s_da[r] = cs[rb + nx - 1] - base;
-                s_sw[r] = base + len1;
-                s_db[r] = cs[rb] - (base + len1);
+                s_da[tid] = cs[rb + nx - 1] - base;
+                s_sw[tid] = base + len1;
+                s_db[tid] = cs[rb] - (base + len1);
             } else if (xb >= nx) {  // cells xa .. nx-1, then cell 0
                 const int32_t len1 = cs[rb + nx] - cs[rb + xa];
-                s_da[r] = cs[rb + xa] - base;
-                s_sw[r] = base + len1;
-                s_db[r] = cs[rb] - (base + len1);
+                s_da[tid] = cs[rb + xa] - base;
+                s_sw[tid] = base + len1;
+                s_db[tid] = cs[rb] - (base + len1);
             } else {
-                s_da[r] = cs[rb + xa] - base;
-                s_sw[r] = base + tot;
-                s_db[r] = s_da[r];
+                s_da[tid] = cs[rb + xa] - base;
+                s_sw[tid] = base + tot;
+                s_db[tid] = s_da[tid];
             }
-            base += tot;
         }
-        s_total = base;
+        if (tid == 31) s_total = inc;
+    } else if (tid < 64) {
+        // warp 1: the home rows (home row l is row l % bh, plane l / bh)
+        const int l = lane;
+        int32_t c = 0;
+        if (l < nhome) {
+            const int32_t rm = S.cell0 + ((z0 + l / bh) * ny + y0 + l % bh) * nx;
+            for (int t = 0; t <= bw; ++t) s_home[l][t] = cs[rm + x0 + t];
+            c = s_home[l][bw] - s_home[l][0];
+        }
+        int32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        s_hoff[l] = inc - c;  // rows past nhome hold H
     }
     __syncthreads();
     const int32_t T = s_total;
-    const int32_t n0 = s_home[0][bw] - s_home[0][0];
-    const int32_t H = n0 + (bh > 1 ? s_home[1][bw] - s_home[1][0] : 0);
+    const int32_t H = s_hoff[nhome];
     // a neighbourhood larger than the shared-memory stage is read from global
     // memory instead (same indices, slower)
     const bool staged = T <= NB_MAX;
     if (staged) {
         for (int32_t t = tid; t < T; t += blockDim.x) {
-            int r = 0;
-            while (r + 1 < nrow && s_cell[r + 1][0] <= t) ++r;
+            int r = 0, rh = nrow - 1;  // the last row starting at or before t
+            while (r < rh) {
+                const int mid = (r + rh + 1) >> 1;
+                if (s_cell[mid][0] <= t) r = mid;
+                else rh = mid - 1;
+            }
             s_x[t] = xq[t + (t < s_sw[r] ? s_da[r] : s_db[r])];
         }
     }
@@ -170,8 +223,10 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
     const f2_t sxx = pk(sx, sx), syy = pk(sy, sy), szz = pk(sz, sz);
     const float lo = S.rl2_lo, hi = S.rl2_hi;
     for (int32_t h = tid; h < H; h += blockDim.x) {
-        const int hr = h < n0 ? 0 : 1;
-        const int32_t i = h < n0 ? s_home[0][0] + h : s_home[1][0] + (h - n0);
+        int hr = 0;  // the last home row starting at or before h
+        while (hr + 1 < nhome && s_hoff[hr + 1] <= h) ++hr;
+        const int32_t i = s_home[hr][0] + (h - s_hoff[hr]);
+        const int32_t hy = hr % bh, hz = hr / bh;
         const int4 xi = xq[i];
         int t = 0;
         while (t + 1 < bw && i >= s_home[hr][t + 1]) ++t;
@@ -183,7 +238,7 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
         };
         for (int dz = 0; dz < 3; ++dz)
             for (int dy = 0; dy < 3; ++dy) {
-                const int r = dz * nyr + hr + dy;
+                const int r = (hz + dz) * nyr + hy + dy;
                 const int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
                 const int32_t sw = s_sw[r], da = s_da[r], db = s_db[r];
                 for (int32_t k = a; k < b; k += 2) {
@@ -223,11 +278,11 @@ int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr) {
                       "cudaFuncSetAttribute");
 }
 
-int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, const int4 *xq, const double *pos64,
-                      const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld, int32_t *cnt,
-                      int32_t max_nbr) {
+int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, BrickShape shape, const int4 *xq,
+                      const double *pos64, const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld,
+                      int32_t *cnt, int32_t max_nbr) {
     if (nbricks > 0)
-        PPMD_LAUNCH(ctx, k_neigh_brick, nbricks, BRICK_THREADS, neigh_brick_smem(max_nbr), bricks, xq, pos64, st,
+        PPMD_LAUNCH(ctx, k_neigh_brick, nbricks, BRICK_THREADS, neigh_brick_smem(max_nbr), bricks, shape, xq, pos64, st,
                     cell_start, W, ld, cnt, max_nbr, ctx->d_status, ctx->d_needed);
     return check_launch(ctx, "build_list_bricks");
 }

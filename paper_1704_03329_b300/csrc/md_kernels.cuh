@@ -5,26 +5,36 @@
 
 namespace ppmd {
 
-// A brick: cells x0 <= x < x1 (at most 3) of rows y0 <= y < y1 (at most 2)
-// of plane z of one segment.  Its neighbourhood is the rows y0-1 .. y1 of
-// planes z-1 .. z+1, cells x0-1 .. x1 of each.
+// A brick: the cells x0 <= x < x1, y0 <= y < y1, z0 <= z < z1 of one
+// segment (at most BW_MAX x BH_MAX x BD_MAX).  Its neighbourhood is the
+// cells x0-1 .. x1 of the rows y0-1 .. y1 of the planes z0-1 .. z1.
 struct Brick {
-    int32_t seg, x01, y01, z;  // x01 = x0 | x1 << 16, y01 = y0 | y1 << 16
+    int32_t seg, x01, y01, z01;  // x01 = x0 | x1 << 16, and so on
+};
+struct BrickShape {
+    int32_t bw, bh, bd;  // cells of a brick along x, y, z
 };
 
-constexpr int NB_MAX = 2048;     // largest neighbourhood staged in shared memory
+constexpr int NB_MAX = 2048;        // largest neighbourhood staged in shared memory
 constexpr int BRICK_THREADS = 128;  // home atoms handled per pass of a brick block
+constexpr int BW_MAX = 8, BH_MAX = 4, BD_MAX = 2;
 
-// Bricks of a cell grid (host).
+// Brick shape for a segment: the most home atoms up to one per thread whose
+// neighbourhood (with a margin for density fluctuations) fits the stage.
+BrickShape brick_shape(const Seg &S);
+// Bricks of the cell grids of several segments (host).
 void make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out);
+int64_t brick_count(const Seg &S, BrickShape b);
 size_t neigh_brick_smem(int32_t max_nbr);
 int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr);
 
 // Column-major neighbour list W[m * ld + i] (the paper's neighbour matrix)
-// of atoms stored in cell order, one block per brick.
-int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, const int4 *xq, const double *pos64,
-                      const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld, int32_t *cnt,
-                      int32_t max_nbr);
+// of atoms stored in cell order, one block per brick.  With bricks == null
+// the grid is one segment's (st.nseg == 1) cut into bricks of `shape`, in
+// x-fastest order.
+int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, BrickShape shape, const int4 *xq,
+                      const double *pos64, const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld,
+                      int32_t *cnt, int32_t max_nbr);
 
 // Pair loop over the column-major list, one thread per atom, followed by
 // the second kick of Algorithm 6 (v += dt/(2m) F) when vel != null.

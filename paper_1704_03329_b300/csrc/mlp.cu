@@ -715,28 +715,34 @@ extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t
         if (n_fallback) *n_fallback = n;
         return ppmd_analyze(ctx, pos, n, box, 0.0, r_cna, nullptr, nullptr, nullptr, label);
     }
-    Snapshot s;
-    PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, 32, s));
     const size_t nn = (size_t)(n > 0 ? n : 1);
-    __nv_bfloat16 *feat = (__nv_bfloat16 *)scratch(ctx, S_TMP0, sizeof(__nv_bfloat16) * 32 * nn);
-    int8_t *cls = (int8_t *)scratch(ctx, S_TMP1, nn + 16);
-    float *conf_s = (float *)scratch(ctx, S_TMP2, sizeof(float) * nn);
-    int32_t *fb = (int32_t *)scratch(ctx, S_AUX1, sizeof(int32_t) * (nn + 1));
-    if (!feat || !cls || !conf_s || !fb) return PPMD_ERR_NOMEM;
-    int32_t *nfb = fb + nn;
-    PPMD_TRY(features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, r_cna, s.Lmax, nullptr, nullptr, feat));
-    __nv_bfloat16 *img;
-    PPMD_TRY(pack_weights(ctx, params, &img));
-    PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(nfb, 0, sizeof(int32_t), ctx->stream), "memset"));
-    if (n > 0)
-        PPMD_LAUNCH(ctx, k_mlp_infer, mlp_grid((n + 15) / 16), MLP_WARPS * 32, 0, n, feat, img, params, nullptr, cls, conf_s,
-                    threshold, fb, nfb);
-    // exact CNA for the low-confidence atoms, written over their MLP class
-    int32_t hfb = 0;
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(&hfb, nfb, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "copy"));
-    PPMD_TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
-    if (hfb > 0) PPMD_TRY(cna_subset_launch(ctx, hfb, fb, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, cls));
-    if (n > 0) PPMD_LAUNCH(ctx, k_write_labels, div_up(n, 256), 256, 0, n, s.perm, cls, conf_s, label, confidence);
-    if (n_fallback) *n_fallback = hfb;
-    return check_launch(ctx, "ppmd_classify");
+    int32_t max_nbr = SNAPSHOT_NBR;
+    for (int attempt = 0;; ++attempt) {
+        Snapshot s;
+        PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, max_nbr, s));
+        __nv_bfloat16 *feat = (__nv_bfloat16 *)scratch(ctx, S_TMP0, sizeof(__nv_bfloat16) * 32 * nn);
+        int8_t *cls = (int8_t *)scratch(ctx, S_TMP1, nn + 16);
+        float *conf_s = (float *)scratch(ctx, S_TMP2, sizeof(float) * nn);
+        int32_t *fb = (int32_t *)scratch(ctx, S_AUX1, sizeof(int32_t) * nn);
+        if (!feat || !cls || !conf_s || !fb) return PPMD_ERR_NOMEM;
+        int32_t *nfb = ctx->d_status + 4;  // the fallback count, read back with the status
+        PPMD_TRY(features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, r_cna, s.Lmax, nullptr,
+                                 nullptr, feat));
+        __nv_bfloat16 *img;
+        PPMD_TRY(pack_weights(ctx, params, &img));
+        PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(nfb, 0, sizeof(int32_t), ctx->stream), "memset"));
+        if (n > 0)
+            PPMD_LAUNCH(ctx, k_mlp_infer, mlp_grid((n + 15) / 16), MLP_WARPS * 32, 0, n, feat, img, params, nullptr, cls,
+                        conf_s, threshold, fb, nfb);
+        // exact CNA for the low-confidence atoms (as many as the device
+        // found), written over their MLP class
+        PPMD_TRY(cna_subset_launch(ctx, n, nfb, fb, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, cls));
+        if (n > 0) PPMD_LAUNCH(ctx, k_write_labels, div_up(n, 256), 256, 0, n, s.perm, cls, conf_s, label, confidence);
+        PPMD_TRY(check_launch(ctx, "ppmd_classify"));
+        int32_t hfb = 0;
+        const int rc = end_pipeline(ctx, attempt, max_nbr, &hfb);
+        if (rc == PIPELINE_RETRY) continue;
+        if (n_fallback) *n_fallback = hfb;
+        return rc;
+    }
 }
