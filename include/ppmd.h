@@ -278,7 +278,10 @@ int ppmd_md_set_state(ppmd_md *md, const double *pos, const double *vel);
 /* Advance nsteps steps of Algorithm 6.  energies (device, may be NULL):
  * [nsteps][2] receives (kinetic, potential) energy summed over all boxes
  * on every step s with s % energy_every == 0 (other rows untouched).
- * use_graph != 0 replays CUDA graphs of whole rebuild periods. */
+ * use_graph != 0 replays CUDA graphs of whole rebuild periods.  Inside a
+ * run, the FP32 pair loop of each step but the last also applies the next
+ * step's first kick and drift (same arithmetic, so the same bits as separate
+ * kernels); a run always ends with full-step velocities. */
 int ppmd_md_run(ppmd_md *md, int32_t nsteps, double *energies, int use_graph);
 /* Copy positions, velocities and forces back in caller order (device,
  * [n][3] each; any may be NULL). */

@@ -600,7 +600,7 @@ int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box 
     s.cnt = (int32_t *)scratch(ctx, S_NBRCNT, sizeof(int32_t) * nn);
     if (!s.nbr || !s.cnt) return PPMD_ERR_NOMEM;
     PPMD_TRY(build_list_bricks(ctx, nbricks, nullptr, shape, s.xq, s.pos, s.st, s.cell_start, s.nbr, s.ld, s.cnt,
-                               max_nbr));
+                               max_nbr, brick_stage_cap(s.st.one, shape)));
     return PPMD_OK;
 }
 

@@ -29,10 +29,18 @@ struct ppmd_md {
     double *pos = nullptr, *vel = nullptr, *f64 = nullptr;
     float4 *f4 = nullptr;
     int4 *xq = nullptr, *xq_ref = nullptr;
+    // pos and xq point at buffer `cur` of two: a pair loop with the next
+    // drift fused in writes the other one.  Rebuilds and set-up return to
+    // buffer 0, so a captured rebuild period starts and ends there.
+    double *pos_buf[2] = {nullptr, nullptr};
+    int4 *xq_buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool half_kicked = false;  // positions already at step+1 (velocities at step+1/2)
     int32_t *orig = nullptr, *seg_of = nullptr, *cell_of = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
     int32_t *W = nullptr, *cnt = nullptr;  // column-major neighbour matrix W[m * ld + i]
     int64_t ld = 0;
     Brick *bricks = nullptr;
+    int32_t stage_cap = 0;  // shared-memory stage of a list-build block (atoms)
     int64_t nbricks = 0;
     // reorder temporaries
     double *pos_t = nullptr, *vel_t = nullptr;
@@ -108,6 +116,12 @@ __global__ void k_energy_row(const double *red, double *row) {
     row[1] = red[0];
 }
 
+void use_buffer(ppmd_md *m, int b) {
+    m->cur = b;
+    m->pos = m->pos_buf[b];
+    m->xq = m->xq_buf[b];
+}
+
 int rebuild(ppmd_md *m) {
     ppmd_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
@@ -115,6 +129,7 @@ int rebuild(ppmd_md *m) {
     PPMD_TRY(bin_atoms(ctx, m->pos, n, m->st, m->seg_of, m->ncell, false, m->cell_of, m->cell_start, m->cell_atoms));
     PPMD_TRY(md_gather(ctx, n, m->cell_atoms, m->st, m->pos, m->vel, m->orig, m->seg_of, m->pos_t, m->vel_t, m->xq_t,
                        m->orig_t, m->seg_t));
+    use_buffer(m, 0);
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, m->pos_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, m->vel_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
@@ -122,30 +137,49 @@ int rebuild(ppmd_md *m) {
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, BrickShape{1, 1, 1}, m->xq, m->pos, m->st, m->cell_start,
-                               m->W, m->ld, m->cnt, m->p.max_nbr));
+                               m->W, m->ld, m->cnt, m->p.max_nbr, m->stage_cap));
     return PPMD_OK;
 }
 
-// Pair loop; with kick = true also the second kick of the step; on energy
-// steps the per-block (U, W, K) sums.
-int forces(ppmd_md *m, bool energy, bool kick) {
+// Pair loop; with kick = true also the second kick of the step, with
+// drift = true (FP32) also the next step's kick and drift; on energy steps
+// the per-block (U, W, K) sums.
+int forces(ppmd_md *m, bool energy, bool kick, bool drift = false) {
     const bool f32 = m->p.prec == PPMD_FP32;
-    return lj_columns(m->ctx, m->n, m->ld, m->xq, m->pos, m->st, m->c, m->W, m->cnt, m->p.max_nbr, m->p.prec,
-                      f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, kick ? m->vel : nullptr, m->h, m->half_m,
-                      energy ? m->part_f : nullptr);
+    Drift d;
+    if (drift) {
+        d.pos_next = m->pos_buf[m->cur ^ 1];
+        d.xq_next = m->xq_buf[m->cur ^ 1];
+        d.xq_ref = m->xq_ref;
+        d.dt = m->p.dt;
+        d.max_disp_bits = m->max_disp_bits;
+    }
+    PPMD_TRY(lj_columns(m->ctx, m->n, m->ld, m->xq, m->pos, m->st, m->c, m->W, m->cnt, m->p.max_nbr, m->p.prec,
+                        f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, kick ? m->vel : nullptr, m->h, m->half_m,
+                        energy ? m->part_f : nullptr, d));
+    if (drift) {
+        use_buffer(m, m->cur ^ 1);
+        m->half_kicked = true;
+    }
+    return PPMD_OK;
 }
 
-// One step of Algorithm 6.  erow: device row receiving (KE, PE) on energy steps.
-int one_step(ppmd_md *m, int64_t s, double *erow) {
+// One step of Algorithm 6.  erow: device row receiving (KE, PE) on energy
+// steps.  The step's kick and drift are skipped when the previous pair loop
+// already made them; with fuse_next (FP32) this step's pair loop makes the
+// next step's.
+int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next) {
     ppmd_ctx *ctx = m->ctx;
     const bool f32 = m->p.prec == PPMD_FP32;
     const bool energy = m->p.energy_every > 0 && (s % m->p.energy_every) == 0 && erow;
-    PPMD_TRY(md_kick_drift2(ctx, m->n, m->pos, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->xq, m->xq_ref,
-                            m->st, m->h, m->p.dt, m->max_disp_bits));
+    if (!m->half_kicked)
+        PPMD_TRY(md_kick_drift2(ctx, m->n, m->pos, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->xq,
+                                m->xq_ref, m->st, m->h, m->p.dt, m->max_disp_bits));
+    m->half_kicked = false;
     if (m->p.rebuild_every > 0 && s % m->p.rebuild_every == 0) {
         PPMD_TRY(rebuild(m));
     }
-    PPMD_TRY(forces(m, energy, true));
+    PPMD_TRY(forces(m, energy, true, fuse_next && f32));
     if (energy) {
         PPMD_TRY(reduce_partials(ctx, m->part_f, lj_columns_blocks(m->n), 3, m->red));
         PPMD_LAUNCH(ctx, k_energy_row, 1, 1, 0, m->red, erow);
@@ -221,7 +255,8 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->d_atom_off, nbox + 1);
     if (rc == PPMD_OK)
         rc = cuda_check(ctx, cudaMemcpy(m->d_atom_off, atom_off, sizeof(int64_t) * (nbox + 1), cudaMemcpyHostToDevice), "copy");
-    if (rc == PPMD_OK) rc = md_alloc(m, &m->pos, 3 * n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->pos_buf[0], 3 * n);
+    if (rc == PPMD_OK && p.prec == PPMD_FP32) rc = md_alloc(m, &m->pos_buf[1], 3 * n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->vel, 3 * n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->pos_t, 3 * n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->vel_t, 3 * n);
@@ -229,7 +264,9 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
         if (p.prec == PPMD_FP32) rc = md_alloc(m, &m->f4, n);
         else rc = md_alloc(m, &m->f64, 3 * n);
     }
-    if (rc == PPMD_OK) rc = md_alloc(m, &m->xq, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->xq_buf[0], n);
+    if (rc == PPMD_OK && p.prec == PPMD_FP32) rc = md_alloc(m, &m->xq_buf[1], n);
+    use_buffer(m, 0);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->xq_ref, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->xq_t, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->orig, n);
@@ -244,7 +281,7 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->W, (size_t)m->ld * p.max_nbr);
     if (rc == PPMD_OK) {
         std::vector<Brick> bl;
-        make_bricks(m->segs, bl);
+        m->stage_cap = make_bricks(m->segs, bl);
         m->nbricks = (int64_t)bl.size();
         rc = md_alloc(m, &m->bricks, bl.size());
         if (rc == PPMD_OK && !bl.empty())
@@ -285,6 +322,8 @@ extern "C" int ppmd_md_set_state(ppmd_md *m, const double *pos, const double *ve
     cudaSetDevice(ctx->device);
     const int64_t n = m->n;
     cudaStream_t s = ctx->stream;
+    use_buffer(m, 0);
+    m->half_kicked = false;
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
     if (n > 0)
@@ -321,7 +360,10 @@ extern "C" int ppmd_md_run(ppmd_md *m, int32_t nsteps, double *energies, int use
                 int64_t k0 = ctx->launches;
                 cudaGraph_t g = nullptr;
                 int rc = cuda_check(ctx, cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
-                for (int32_t k = 1; rc == PPMD_OK && k <= unit; ++k) rc = one_step(m, k, m->ebuf + 2 * (k - 1));
+                // a unit starts and ends with full-step velocities; inside it
+                // each pair loop makes the next step's kick and drift
+                for (int32_t k = 1; rc == PPMD_OK && k <= unit; ++k)
+                    rc = one_step(m, k, m->ebuf + 2 * (k - 1), k < unit);
                 cudaError_t e = cudaStreamEndCapture(m->cap_stream, &g);
                 ctx->stream = user;
                 if (rc != PPMD_OK) {
@@ -350,7 +392,10 @@ extern "C" int ppmd_md_run(ppmd_md *m, int32_t nsteps, double *energies, int use
             done += unit;
         } else {
             const int64_t s = s0 + 1;
-            PPMD_TRY(one_step(m, s, energies ? energies + 2 * done : nullptr));
+            // fuse the next step's kick and drift unless this is the run's
+            // last step or the next one is a graph replay
+            const bool next_graph = graph_ok && s % unit == 0 && nsteps - (done + 1) >= unit;
+            PPMD_TRY(one_step(m, s, energies ? energies + 2 * done : nullptr, done + 1 < nsteps && !next_graph));
             if (s % P == 0) m->rebuilds += 1;
             m->step = s;
             done += 1;

@@ -79,11 +79,13 @@ int64_t brick_count(const Seg &S, BrickShape b) {
     return (int64_t)((S.nc[0] + b.bw - 1) / b.bw) * ((S.nc[1] + b.bh - 1) / b.bh) * ((S.nc[2] + b.bd - 1) / b.bd);
 }
 
-void make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out) {
+int32_t make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out) {
     out.clear();
+    int32_t cap = 64;
     for (size_t s = 0; s < segs.size(); ++s) {
         const Seg &S = segs[s];
         const BrickShape b = brick_shape(S);
+        cap = std::max(cap, brick_stage_cap(S, b));
         for (int32_t z0 = 0; z0 < S.nc[2]; z0 += b.bd)
             for (int32_t y0 = 0; y0 < S.nc[1]; y0 += b.bh)
                 for (int32_t x0 = 0; x0 < S.nc[0]; x0 += b.bw) {
@@ -92,9 +94,20 @@ void make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out) {
                     out.push_back(Brick{(int32_t)s, x0 | (x1 << 16), y0 | (y1 << 16), z0 | (z1 << 16)});
                 }
     }
+    return cap;
 }
 
 size_t neigh_brick_smem(int32_t) { return (size_t)NB_MAX * sizeof(int4); }
+
+// Staged atoms of a brick: the expected neighbourhood count with a 1.5x
+// margin (denser bricks read the global arrays instead), so that bricks of
+// sparse grids leave room for more resident blocks.
+int32_t brick_stage_cap(const Seg &S, BrickShape b) {
+    const double pc = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
+    const double need = 1.5 * pc * (b.bw + 2) * (b.bh + 2) * (b.bd + 2);
+    const int64_t cap = ((int64_t)ceil(need) + 63) / 64 * 64;
+    return (int32_t)std::max<int64_t>(64, std::min<int64_t>(NB_MAX, cap));
+}
 
 __device__ __forceinline__ int32_t wrapi(int32_t v, int32_t n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -113,7 +126,8 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
                                                                const double *__restrict__ pos64, SegTable st,
                                                                const int32_t *__restrict__ cs, int32_t *__restrict__ W,
                                                                int64_t ld, int32_t *__restrict__ cnt, int32_t max_nbr,
-                                                               int32_t *status, unsigned long long *needed) {
+                                                               int32_t stage_cap, int32_t *status,
+                                                               unsigned long long *needed) {
     constexpr int NROW = (BH_MAX + 2) * (BD_MAX + 2), NHOME = BH_MAX * BD_MAX;
     extern __shared__ __align__(16) unsigned char smem[];
     int4 *s_x = (int4 *)smem;
@@ -206,8 +220,26 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
     const int32_t H = s_hoff[nhome];
     // a neighbourhood larger than the shared-memory stage is read from global
     // memory instead (same indices, slower)
-    const bool staged = T <= NB_MAX;
+    const bool staged = T <= stage_cap;
+    // Where the neighbourhood leaves at least one cell of the periodic grid
+    // outside it in every direction, positions are staged as FP32 offsets
+    // from its centre (the signed fixed-point difference is then the
+    // periodic image seen from the brick) with the atom index in .w, so the
+    // candidate tests need no integer work.  Rounding: each offset is within
+    // 2^-23 of its value (at most 5 cells), which moves r^2 by less than
+    // 1e-5 r^2, inside the FP64 re-test band.
+    const bool fstage = staged && bw + 3 <= nx && bh + 3 <= ny && bd + 3 <= nz;
+    // the centre needs no precision: any point within a cell of it serves
+    const uint32_t refx = (uint32_t)__float2ull_rz((x0 - 1 + 0.5f * (bw + 2)) / (float)nx * 4294967296.0f);
+    const uint32_t refy = (uint32_t)__float2ull_rz((y0 - 1 + 0.5f * (bh + 2)) / (float)ny * 4294967296.0f);
+    const uint32_t refz = (uint32_t)__float2ull_rz((z0 - 1 + 0.5f * (bd + 2)) / (float)nz * 4294967296.0f);
+    const float sx = S.sx[0], sy = S.sx[1], sz = S.sx[2];
+    auto rel = [&](const int4 q, int32_t j) {
+        return make_float4((float)(int32_t)((uint32_t)q.x - refx) * sx, (float)(int32_t)((uint32_t)q.y - refy) * sy,
+                           (float)(int32_t)((uint32_t)q.z - refz) * sz, __int_as_float(j));
+    };
     if (staged) {
+        float4 *s_f = (float4 *)smem;
         for (int32_t t = tid; t < T; t += blockDim.x) {
             int r = 0, rh = nrow - 1;  // the last row starting at or before t
             while (r < rh) {
@@ -215,11 +247,12 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
                 if (s_cell[mid][0] <= t) r = mid;
                 else rh = mid - 1;
             }
-            s_x[t] = xq[t + (t < s_sw[r] ? s_da[r] : s_db[r])];
+            const int32_t j = t + (t < s_sw[r] ? s_da[r] : s_db[r]);
+            if (fstage) s_f[t] = rel(xq[j], j);
+            else s_x[t] = xq[j];
         }
     }
     __syncthreads();
-    const float sx = S.sx[0], sy = S.sx[1], sz = S.sx[2];
     const f2_t sxx = pk(sx, sx), syy = pk(sy, sy), szz = pk(sz, sz);
     const float lo = S.rl2_lo, hi = S.rl2_hi;
     for (int32_t h = tid; h < H; h += blockDim.x) {
@@ -236,6 +269,39 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
             if (count < max_nbr) col[(int64_t)count * ld] = j;
             ++count;
         };
+        if (fstage) {
+            const float4 fi = rel(xi, i);
+            const float4 *s_f = (const float4 *)smem;
+            const f2_t xii = pk(fi.x, fi.x), yii = pk(fi.y, fi.y), zii = pk(fi.z, fi.z);
+            for (int dz = 0; dz < 3; ++dz)
+                for (int dy = 0; dy < 3; ++dy) {
+                    const int r = (hz + dz) * nyr + hy + dy;
+                    const int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
+                    // four candidates per pass (two packed pairs), tested in order
+                    for (int32_t k = a; k < b; k += 4) {
+                        const int32_t e = b - 1;
+                        const float4 f0 = s_f[k], f1 = s_f[min(k + 1, e)], f2 = s_f[min(k + 2, e)],
+                                     f3 = s_f[min(k + 3, e)];
+                        const f2_t dx0 = sub2(xii, pk(f0.x, f1.x)), dx1 = sub2(xii, pk(f2.x, f3.x));
+                        const f2_t dy0 = sub2(yii, pk(f0.y, f1.y)), dy1 = sub2(yii, pk(f2.y, f3.y));
+                        const f2_t dz0 = sub2(zii, pk(f0.z, f1.z)), dz1 = sub2(zii, pk(f2.z, f3.z));
+                        float r2v[4];
+                        upk(fma2(dx0, dx0, fma2(dy0, dy0, mul2(dz0, dz0))), r2v[0], r2v[1]);
+                        upk(fma2(dx1, dx1, fma2(dy1, dy1, mul2(dz1, dz1))), r2v[2], r2v[3]);
+                        const int32_t jv[4] = {__float_as_int(f0.w), __float_as_int(f1.w), __float_as_int(f2.w),
+                                               __float_as_int(f3.w)};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (k + q < b && r2v[q] < hi && jv[q] != i) {
+                                double dr[3];
+                                if (r2v[q] < lo ||
+                                    min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jv[q], S, dr) < S.rl2)
+                                    hit(jv[q]);
+                            }
+                        }
+                    }
+                }
+        } else
         for (int dz = 0; dz < 3; ++dz)
             for (int dy = 0; dy < 3; ++dy) {
                 const int r = (hz + dz) * nyr + hy + dy;
@@ -280,10 +346,11 @@ int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr) {
 
 int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, BrickShape shape, const int4 *xq,
                       const double *pos64, const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld,
-                      int32_t *cnt, int32_t max_nbr) {
+                      int32_t *cnt, int32_t max_nbr, int32_t stage_cap) {
+    if (stage_cap <= 0 || stage_cap > NB_MAX) stage_cap = NB_MAX;
     if (nbricks > 0)
-        PPMD_LAUNCH(ctx, k_neigh_brick, nbricks, BRICK_THREADS, neigh_brick_smem(max_nbr), bricks, shape, xq, pos64, st,
-                    cell_start, W, ld, cnt, max_nbr, ctx->d_status, ctx->d_needed);
+        PPMD_LAUNCH(ctx, k_neigh_brick, nbricks, BRICK_THREADS, (size_t)stage_cap * sizeof(int4), bricks, shape, xq,
+                    pos64, st, cell_start, W, ld, cnt, max_nbr, stage_cap, ctx->d_status, ctx->d_needed);
     return check_launch(ctx, "build_list_bricks");
 }
 
@@ -336,15 +403,16 @@ __device__ __forceinline__ void block_sum3(double a, double b, double c, double 
 
 constexpr int COL_BLOCK = 256;
 
-template <bool ENERGY>
-__global__ void __launch_bounds__(COL_BLOCK) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
+template <bool ENERGY, bool DRIFT>
+__global__ void __launch_bounds__(COL_BLOCK, (ENERGY || DRIFT) ? 3 : 4) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
                                                         const double *__restrict__ pos64, SegTable st, LJConst c,
                                                         const int32_t *__restrict__ W, const int32_t *__restrict__ cnt,
                                                         int32_t max_nbr, float4 *__restrict__ f4,
                                                         double *__restrict__ vel, double h, double half_m,
-                                                        double *__restrict__ partials) {
+                                                        double *__restrict__ partials, Drift dr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double u_i = 0.0, w_i = 0.0, k_i = 0.0;
+    float d2 = 0.0f;
     if (i < n) {
         const int4 xi = xq[i];
         const Seg &S = seg_ref(st, xi.w);
@@ -430,14 +498,39 @@ __global__ void __launch_bounds__(COL_BLOCK) k_lj_col32(int64_t n, int64_t ld, c
         if (vel) {
             // second kick of Algorithm 6 with the forces just computed
             const float4 fq = f4[i];
-            const double vx = fma(h, (double)fq.x, vel[3 * i]);
-            const double vy = fma(h, (double)fq.y, vel[3 * i + 1]);
-            const double vz = fma(h, (double)fq.z, vel[3 * i + 2]);
-            vel[3 * i] = vx;
-            vel[3 * i + 1] = vy;
-            vel[3 * i + 2] = vz;
-            if (ENERGY) k_i = half_m * (vx * vx + vy * vy + vz * vz);
+            const double f[3] = {(double)fq.x, (double)fq.y, (double)fq.z};
+            double v[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v[d] = fma(h, f[d], vel[3 * i + d]);
+            if (ENERGY) k_i = half_m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            if (DRIFT) {
+                // the next step's kick and drift, in the same arithmetic as
+                // k_kick_drift2 (the atom's segment is looked up again, so
+                // that nothing of the pair loop stays live until here)
+                const int4 ref = dr.xq_ref[i];
+                const Seg &Sd = seg_ref(st, ref.w);
+                uint32_t q[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    v[d] = fma(h, f[d], v[d]);
+                    const double r = fma(dr.dt, v[d], pos64[3 * i + d]);
+                    dr.pos_next[3 * i + d] = r;
+                    q[d] = (uint32_t)(unsigned long long)__double2ll_rn(r * Sd.fxs[d]);
+                }
+                dr.xq_next[i] = make_int4((int)q[0], (int)q[1], (int)q[2], ref.w);
+                const float ex = fixed_delta(q[0], (uint32_t)ref.x, Sd.sx[0]);
+                const float ey = fixed_delta(q[1], (uint32_t)ref.y, Sd.sx[1]);
+                const float ez = fixed_delta(q[2], (uint32_t)ref.z, Sd.sx[2]);
+                d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) vel[3 * i + d] = v[d];
         }
+    }
+    if (DRIFT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+        if ((threadIdx.x & 31) == 0 && d2 > 0.0f) atomicMax(dr.max_disp_bits, __float_as_uint(d2));
     }
     if (ENERGY) block_sum3(u_i, w_i, k_i, partials);
 }
@@ -495,16 +588,16 @@ int64_t lj_columns_blocks(int64_t n) { return div_up(n, COL_BLOCK); }
 
 int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const double *pos64, const SegTable &st,
                const LJConst &c, const int32_t *W, const int32_t *cnt, int32_t max_nbr, int prec, float4 *f4,
-               double *f64, double *vel, double h, double half_m, double *partials) {
+               double *f64, double *vel, double h, double half_m, double *partials, const Drift &drift) {
     if (n <= 0) return PPMD_OK;
     const int64_t nb = lj_columns_blocks(n);
+    if (drift.pos_next && (prec != PPMD_FP32 || !vel)) return set_error(ctx, PPMD_ERR_INVALID, "lj_columns: drift needs FP32 and a kick");
     if (prec == PPMD_FP32) {
-        if (partials)
-            PPMD_LAUNCH(ctx, k_lj_col32<true>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f4, vel, h, half_m,
-                        partials);
-        else
-            PPMD_LAUNCH(ctx, k_lj_col32<false>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f4, vel, h, half_m,
-                        partials);
+        const bool e = partials != nullptr, d = drift.pos_next != nullptr;
+        auto kern = e ? (d ? k_lj_col32<true, true> : k_lj_col32<true, false>)
+                      : (d ? k_lj_col32<false, true> : k_lj_col32<false, false>);
+        PPMD_LAUNCH(ctx, kern, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f4, vel, h, half_m, partials,
+                    drift);
     } else {
         if (partials)
             PPMD_LAUNCH(ctx, k_lj_col64<true>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,

@@ -23,8 +23,11 @@ constexpr int BW_MAX = 8, BH_MAX = 4, BD_MAX = 2;
 // neighbourhood (with a margin for density fluctuations) fits the stage.
 BrickShape brick_shape(const Seg &S);
 // Bricks of the cell grids of several segments (host).
-void make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out);
+// Returns the stage capacity covering every segment.
+int32_t make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out);
 int64_t brick_count(const Seg &S, BrickShape b);
+// Shared-memory stage (atoms) of a brick of that shape.
+int32_t brick_stage_cap(const Seg &S, BrickShape b);
 size_t neigh_brick_smem(int32_t max_nbr);
 int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr);
 
@@ -34,14 +37,25 @@ int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr);
 // x-fastest order.
 int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, BrickShape shape, const int4 *xq,
                       const double *pos64, const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld,
-                      int32_t *cnt, int32_t max_nbr);
+                      int32_t *cnt, int32_t max_nbr, int32_t stage_cap);
 
 // Pair loop over the column-major list, one thread per atom, followed by
 // the second kick of Algorithm 6 (v += dt/(2m) F) when vel != null.
 // partials (energy steps): per-block rows (U, W, K).
+// The next step's first kick and drift (Algorithm 6) fused into the FP32
+// pair loop: after the second kick, v += dt/(2m) F once more and
+// x' = x + dt v is written to the other position buffers (the pair loop is
+// still reading x), with the displacement guard against xq_ref.
+struct Drift {
+    double *pos_next = nullptr;
+    int4 *xq_next = nullptr;
+    const int4 *xq_ref = nullptr;
+    double dt = 0.0;
+    unsigned int *max_disp_bits = nullptr;
+};
 int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const double *pos64, const SegTable &st,
                const LJConst &c, const int32_t *W, const int32_t *cnt, int32_t max_nbr, int prec, float4 *f4,
-               double *f64, double *vel, double h, double half_m, double *partials);
+               double *f64, double *vel, double h, double half_m, double *partials, const Drift &drift = Drift());
 int64_t lj_columns_blocks(int64_t n);
 
 // Kick + drift without wrapping (coordinates stay continuous between list

@@ -257,3 +257,32 @@ def test_md_batched_boxes_equal_single_runs(L, ctx):
         # displacement that a force error of 1e-5 rms|F| produces over 20 steps
         bound = (20 * 0.005) ** 2 * 1e-5 * np.sqrt((Fo ** 2).sum(1).mean())
         assert _pos_err(P[off[k]:off[k + 1]], po, r["box"]) <= bound
+
+
+def test_md_fused_kick_drift_is_bit_identical(L, ctx):
+    """Inside a run the FP32 pair loop also makes the next step's kick and
+    drift (the same arithmetic as the separate kernel): one run of 23 steps
+    (graph replays plus single steps, or single steps only) and 23 runs of one
+    step (no fusion) give identical bits."""
+    c = configs.lj_solid(n_cells=8)
+    n = len(c["pos"])
+
+    def state(runs, use_graph):
+        md = L.MD(ctx, [0, n], [c["box"]], r_list=c["r_list"], rebuild_every=c["rebuild_every"], max_nbr=128,
+                  prec=L.FP32, energy_every=5)
+        md.set_state(cu(c["pos"]), cu(c["vel"]))
+        en = torch.zeros((23, 2), dtype=torch.float64, device="cuda")
+        done = 0
+        for r in runs:
+            md.run(r, en[done:done + r], use_graph=use_graph)
+            done += r
+        p = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        v = torch.empty_like(p)
+        md.get_state(p, v)
+        return p.cpu().numpy(), v.cpu().numpy(), en.cpu().numpy()
+
+    ref = state([1] * 23, False)
+    for runs, g in (([23], True), ([23], False), ([7, 16], True)):
+        got = state(runs, g)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), (runs, g)
