@@ -366,12 +366,11 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
                                                               const int32_t *__restrict__ out_idx,
                                                               float *__restrict__ f32, __nv_bfloat16 *__restrict__ fb16,
                                                               int32_t *status, unsigned long long *needed) {
-    // per-group rows padded to an odd number of words, so that the four
-    // groups of a warp reading entry a of their rows hit different banks
-    __shared__ float3 s_u[FEAT_GROUPS][FEAT_CAP + 1];
-    __shared__ float s_d[FEAT_GROUPS][FEAT_CAP + 1];
-    __shared__ float3 s_v[FEAT_GROUPS][FEAT_CAP + 1];
-    __shared__ float s_h[FEAT_GROUPS][FEAT_G][15];  // private histogram of each lane
+    // (u_a, d_a) and v_a as one 16-byte entry each: the eight lanes of a
+    // group read eight entries in one conflict-free phase
+    __shared__ float4 s_ud[FEAT_GROUPS][FEAT_CAP];
+    __shared__ float4 s_v[FEAT_GROUPS][FEAT_CAP];
+    __shared__ float s_h[14][FEAT_WARPS * 32];  // private histogram of each lane, bin-major (no bank conflicts)
     __shared__ float s_f[FEAT_GROUPS][32];
     const int gl = threadIdx.x & (FEAT_G - 1), g = threadIdx.x / FEAT_G, shift = threadIdx.x & 31 & ~(FEAT_G - 1);
     const unsigned gmask = 0xffu << shift;
@@ -382,9 +381,9 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
     const int32_t deg = min(cnt[i], max_nbr);
     const int32_t *row = nbr + i * si;
     const unsigned lt = (1u << gl) - 1u;
-    float *hist = s_h[g][gl];
+    float *hist = &s_h[0][threadIdx.x];  // bin k at hist[k * FEAT_WARPS * 32]
 #pragma unroll
-    for (int k = 0; k < 14; ++k) hist[k] = 0.0f;
+    for (int k = 0; k < 14; ++k) hist[k * FEAT_WARPS * 32] = 0.0f;
 #pragma unroll
     for (int c = gl; c < 32; c += FEAT_G) s_f[g][c] = (c >= 2 && c < 16) ? 1.0f : 0.0f;
     int32_t nu = 0, nbd = 0;
@@ -421,13 +420,12 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
             const int32_t a = nu + __popc(ball & lt);
             if (a < FEAT_CAP) {
                 const float r = sqrtf(r2), ir = 1.0f / r;
-                s_u[g][a] = make_float3(dx * ir, dy * ir, dz * ir);
-                s_d[g][a] = r;
+                s_ud[g][a] = make_float4(dx * ir, dy * ir, dz * ir, r);
             }
         }
         if (bb) {
             const int32_t a = nbd + __popc(bbal & lt);
-            if (a < FEAT_CAP) s_v[g][a] = make_float3(dx, dy, dz);
+            if (a < FEAT_CAP) s_v[g][a] = make_float4(dx, dy, dz, 0.0f);
         }
         nu += __popc(ball);
         nbd += __popc(bbal);
@@ -449,7 +447,7 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
         r6[m] = i6[m] = 0.0f;
     }
     for (int a = gl; a < nu; a += FEAT_G) {
-        const float3 u = s_u[g][a];
+        const float4 u = s_ud[g][a];
         boa_accumulate(K, u.x, u.y, u.z, r4, i4, r6, i6);
     }
     float s4 = 0.0f, s6 = 0.0f;
@@ -472,13 +470,12 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
     const int npair = nbd * (nbd - 1) / 2;
     const float hlo = r_ref - 0.35f;
     for (int pidx = gl; pidx < npair; pidx += FEAT_G) {
-        // pair (a, b), a < b, with pidx = a (2 nbd - a - 1) / 2 + (b - a - 1)
-        const float q = (float)(2 * nbd - 1);
-        int a = (int)floorf(0.5f * (q - sqrtf(fmaxf(q * q - 8.0f * pidx, 0.0f))));
-        while (a > 0 && a * (2 * nbd - a - 1) / 2 > pidx) --a;
-        while ((a + 1) * (2 * nbd - a - 2) / 2 <= pidx) ++a;
-        const int b = pidx - a * (2 * nbd - a - 1) / 2 + a + 1;
-        const float3 va = s_v[g][a], vb = s_v[g][b];
+        // pair (a, b), a < b, numbered pidx = b (b - 1) / 2 + a
+        int b = (int)(0.5f * (1.0f + sqrtf(fmaf(8.0f, (float)pidx, 1.0f))));
+        if (b * (b - 1) / 2 > pidx) --b;
+        if ((b + 1) * b / 2 <= pidx) ++b;
+        const int a = pidx - b * (b - 1) / 2;
+        const float4 va = s_v[g][a], vb = s_v[g][b];
         const float cx = va.x - vb.x, cy = va.y - vb.y, cz = va.z - vb.z;
         const float chord = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
         const float x = (chord - hlo) * 20.0f - 0.5f;
@@ -486,15 +483,15 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
         const int b0 = (int)fl;
         const bool edge = b0 < 0 || b0 >= 13;
         const float t = edge ? 0.0f : x - fl;
-        hist[min(max(b0, 0), 13)] += 1.0f - t;
-        hist[min(max(b0 + 1, 0), 13)] += t;
+        hist[min(max(b0, 0), 13) * (FEAT_WARPS * 32)] += 1.0f - t;
+        hist[min(max(b0 + 1, 0), 13) * (FEAT_WARPS * 32)] += t;
     }
     // sorted bond lengths: the rank of each
     for (int a = gl; a < nu; a += FEAT_G) {
-        const float da = s_d[g][a];
+        const float da = s_ud[g][a].w;
         int rank = 0;
         for (int b = 0; b < nu; ++b) {
-            const float db = s_d[g][b];
+            const float db = s_ud[g][b].w;
             rank += (db < da) || (db == da && b < a);
         }
         if (rank < 14) s_f[g][2 + rank] = (da - r_ref) * inv_span;
@@ -503,7 +500,7 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
     for (int c = gl; c < 14; c += FEAT_G) {
         float acc = 0.0f;
 #pragma unroll
-        for (int l = 0; l < FEAT_G; ++l) acc += s_h[g][l][c];
+        for (int l = 0; l < FEAT_G; ++l) acc += s_h[c][g * FEAT_G + l];
         s_f[g][16 + c] = acc * (1.0f / 24.0f);
     }
     if (gl == 0) {
