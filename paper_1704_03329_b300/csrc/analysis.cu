@@ -498,9 +498,11 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
     }
     __syncwarp(gmask);
     for (int c = gl; c < 14; c += FEAT_G) {
+        // lanes start at different rows of the group (distinct banks); each
+        // bin is always summed in the same order
         float acc = 0.0f;
 #pragma unroll
-        for (int l = 0; l < FEAT_G; ++l) acc += s_h[c][g * FEAT_G + l];
+        for (int l = 0; l < FEAT_G; ++l) acc += s_h[c][g * FEAT_G + ((l + gl) & (FEAT_G - 1))];
         s_f[g][16 + c] = acc * (1.0f / 24.0f);
     }
     if (gl == 0) {

@@ -64,7 +64,7 @@ BrickShape brick_shape(const Seg &S) {
             for (int32_t bw = 1; bw <= mw; ++bw) {
                 const double cells = (double)bw * bh * bd, hood = (double)(bw + 2) * (bh + 2) * (bd + 2);
                 const double home = pc * cells;
-                if (1.5 * pc * hood > NB_MAX || home > BRICK_THREADS) continue;
+                if (1.5 * pc * hood + ROW_GAP * (bh + 2) * (bd + 2) > NB_MAX || home > BRICK_THREADS) continue;
                 const double halo = hood / cells;
                 if (home > best_home * (1.0 + 1e-9) || (home >= best_home * (1.0 - 1e-9) && halo < best_halo)) {
                     best = BrickShape{bw, bh, bd};
@@ -104,7 +104,7 @@ size_t neigh_brick_smem(int32_t) { return (size_t)NB_MAX * sizeof(int4); }
 // sparse grids leave room for more resident blocks.
 int32_t brick_stage_cap(const Seg &S, BrickShape b) {
     const double pc = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
-    const double need = 1.5 * pc * (b.bw + 2) * (b.bh + 2) * (b.bd + 2);
+    const double need = 1.5 * pc * (b.bw + 2) * (b.bh + 2) * (b.bd + 2) + ROW_GAP * (b.bh + 2) * (b.bd + 2);
     const int64_t cap = ((int64_t)ceil(need) + 63) / 64 * 64;
     return (int32_t)std::max<int64_t>(64, std::min<int64_t>(NB_MAX, cap));
 }
@@ -121,7 +121,7 @@ __device__ __forceinline__ float fdiff(int32_t a, int32_t b) { return __int2floa
 // two candidates per packed step; threads of the same cell read the same
 // candidate, so the shared-memory reads are broadcasts.  Hits go straight
 // to the atom's column of W.
-__global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
+__global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
                                                                const int4 *__restrict__ xq,
                                                                const double *__restrict__ pos64, SegTable st,
                                                                const int32_t *__restrict__ cs, int32_t *__restrict__ W,
@@ -171,13 +171,17 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
             }
             s_cell[tid][bw + 2] = tot;
         }
-        int32_t inc = tot;
+        // each staged row is followed by ROW_GAP slots (far-away sentinels
+        // in the FP32 stage), so that candidate reads may run past a row's
+        // end without bounds tests
+        const int32_t span = tid < nrow ? tot + ROW_GAP : 0;
+        int32_t inc = span;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int32_t v = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += v;
         }
-        const int32_t base = inc - tot;
+        const int32_t base = inc - span;
         if (tid < nrow) {
             for (int t = 0; t <= bw + 2; ++t) s_cell[tid][t] += base;
             const int32_t xa = x0 - 1, xb = x1;  // inclusive cell range of the row
@@ -247,6 +251,10 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
                 if (s_cell[mid][0] <= t) r = mid;
                 else rh = mid - 1;
             }
+            if (t >= s_cell[r][bw + 2]) {  // a row's sentinel slot
+                if (fstage) s_f[t] = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-1));
+                continue;
+            }
             const int32_t j = t + (t < s_sw[r] ? s_da[r] : s_db[r]);
             if (fstage) s_f[t] = rel(xq[j], j);
             else s_x[t] = xq[j];
@@ -277,11 +285,12 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
                 for (int dy = 0; dy < 3; ++dy) {
                     const int r = (hz + dz) * nyr + hy + dy;
                     const int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
-                    // four candidates per pass (two packed pairs), tested in order
+                    // four candidates per pass (two packed pairs), tested in
+                    // order; reads past b find either atoms of cells two or
+                    // more cells away from the home cell (farther than the
+                    // cell edge, so never a hit) or the row's sentinels
                     for (int32_t k = a; k < b; k += 4) {
-                        const int32_t e = b - 1;
-                        const float4 f0 = s_f[k], f1 = s_f[min(k + 1, e)], f2 = s_f[min(k + 2, e)],
-                                     f3 = s_f[min(k + 3, e)];
+                        const float4 f0 = s_f[k], f1 = s_f[k + 1], f2 = s_f[k + 2], f3 = s_f[k + 3];
                         const f2_t dx0 = sub2(xii, pk(f0.x, f1.x)), dx1 = sub2(xii, pk(f2.x, f3.x));
                         const f2_t dy0 = sub2(yii, pk(f0.y, f1.y)), dy1 = sub2(yii, pk(f2.y, f3.y));
                         const f2_t dz0 = sub2(zii, pk(f0.z, f1.z)), dz1 = sub2(zii, pk(f2.z, f3.z));
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_neigh_brick(const Brick *__re
                                                __float_as_int(f3.w)};
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            if (k + q < b && r2v[q] < hi && jv[q] != i) {
+                            if (r2v[q] < hi && jv[q] != i) {
                                 double dr[3];
                                 if (r2v[q] < lo ||
                                     min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jv[q], S, dr) < S.rl2)

@@ -18,6 +18,7 @@ struct BrickShape {
 constexpr int NB_MAX = 2048;        // largest neighbourhood staged in shared memory
 constexpr int BRICK_THREADS = 128;  // home atoms handled per pass of a brick block
 constexpr int BW_MAX = 8, BH_MAX = 4, BD_MAX = 2;
+constexpr int ROW_GAP = 3;  // stage slots after each row (candidates are read in fours)
 
 // Brick shape for a segment: the most home atoms up to one per thread whose
 // neighbourhood (with a margin for density fluctuations) fits the stage.
