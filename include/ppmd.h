@@ -187,9 +187,10 @@ int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, d
  * cell internally, the list is built at max(r_boa, r_cna) and the results
  * are returned in caller order.  Bond order is computed when any of q4, q6,
  * n_nb is given (cutoff r_boa), CNA labels when label is given (cutoff
- * r_cna).  Synchronises once, at the end, to check the list capacity; if
- * the list overflowed, the whole analysis is run again with the capacity
- * that was needed. */
+ * r_cna).  Asynchronous: the list capacity is set from the box density
+ * (1.6 times the mean neighbour count plus 16, at least 48); an overflow
+ * (PPMD_ERR_CAPACITY, results invalid) is reported by the next
+ * synchronising call. */
 int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
                  float *q4, float *q6, int32_t *n_nb, int8_t *label);
 
@@ -217,8 +218,9 @@ int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *bo
  * linear weights between centres, clamped at both ends, divided by 24.
  * Outputs (device, at
  * least one given): feat[n][30] FP32, feat_bf16[n][32] BF16 (last two 0),
- * caller order.  Synchronises once at the end (list capacity check and
- * rerun, as ppmd_analyze). */
+ * caller order.  Synchronises once at the end to check the list capacity
+ * (set as for ppmd_analyze); if the list overflowed, the features are
+ * computed again with the capacity that was needed. */
 int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat, double r_ref,
                   float *feat, uint16_t *feat_bf16);
 /* Sets mu and isd of params to the mean and 1/standard deviation of each of
@@ -245,8 +247,10 @@ int ppmd_mlp_train_step(ppmd_ctx *ctx, float *params, float *m, float *v, int64_
  * float [n], may be NULL); atoms with confidence < threshold are labelled
  * by exact CNA instead (the device keeps the count: no synchronisation
  * between the MLP and CNA).  n_fallback (host, may be NULL) receives the
- * number of atoms labelled by CNA.  Synchronises once, at the end (list
- * capacity check and rerun, as ppmd_analyze). */
+ * number of atoms labelled by CNA; when it is given the call synchronises
+ * once at the end (list capacity check and rerun, as ppmd_features),
+ * otherwise it is asynchronous (an overflow is reported by the next
+ * synchronising call). */
 int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t n, const ppmd_box *box, double r_feat, double r_cna,
                   const float *params, float threshold, int8_t *label, float *confidence, int64_t *n_fallback);
 

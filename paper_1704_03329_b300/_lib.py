@@ -311,16 +311,17 @@ def ppmd_mlp_train_step(ctx: Context, params, m, v, step, x_bf16, y, lr=1e-3, wd
 
 
 def ppmd_classify(ctx: Context, pos, box, mode=1, params=None, threshold=0.9, r_feat=1.5, r_cna=1.433625,
-                  want_confidence=True):
-    """Labels int8 [n], confidence float32 [n] (mode 1), number of CNA fallbacks."""
+                  want_confidence=True, count=True):
+    """Labels int8 [n], confidence float32 [n] (mode 1), number of CNA fallbacks
+    (None with count=False: the call is then asynchronous)."""
     n = pos.shape[0]
     lab = torch.empty(n, dtype=torch.int8, device=pos.device)
     conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode == 1) else None
     nfb = _I64(0)
     b = _box(box)
     ctx.check(_lib.ppmd_classify(ctx.h, int(mode), _ptr(pos), n, C.byref(b), float(r_feat), float(r_cna), _opt(params),
-                                 float(threshold), _ptr(lab), _opt(conf), C.byref(nfb)))
-    return lab, conf, nfb.value
+                                 float(threshold), _ptr(lab), _opt(conf), C.byref(nfb) if count else None))
+    return lab, conf, (nfb.value if count else None)
 
 
 class MD:

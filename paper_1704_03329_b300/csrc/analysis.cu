@@ -27,71 +27,86 @@ namespace ppmd {
 // (the Y_l^{-m} terms equal the Y_l^m ones in modulus).  sqrt(c_lm) is folded
 // into each term so that every partial sum stays of order one.
 // ---------------------------------------------------------------------
+// The polynomials sqrt(c_lm) Pr_l^m(z) have the parity of l - m, so each is
+// stored as z^((l-m) mod 2) times a polynomial in z^2 (ascending
+// coefficients), built on the host from the recurrence above in FP64.
 struct YlmCoef {
-    float pmm[7];        // (-1)^m (2m-1)!!
-    float a[7][7];       // (2l-1)/(l-m)
-    float b[7][7];       // (l+m-1)/(l-m)
-    float s4[5], s6[7];  // sqrt(c_4m), sqrt(c_6m)
+    float c4[5][3];  // l = 4: degree (4-m)/2 in z^2
+    float c6[7][4];  // l = 6: degree (6-m)/2 in z^2
 };
 
 static YlmCoef make_coef() {
     YlmCoef k;
     memset(&k, 0, sizeof(k));
-    double df = 1.0;
-    for (int m = 0; m <= 6; ++m) {
-        if (m > 0) df *= (2.0 * m - 1.0);
-        k.pmm[m] = (float)((m % 2 ? -1.0 : 1.0) * df);
-        for (int l = m + 2; l <= 6; ++l) {
-            k.a[l][m] = (float)((2.0 * l - 1.0) / (l - m));
-            k.b[l][m] = (float)((l + m - 1.0) / (l - m));
-        }
-    }
     auto fact = [](int q) {
         double f = 1.0;
         for (int i = 2; i <= q; ++i) f *= i;
         return f;
     };
-    for (int m = 0; m <= 4; ++m) k.s4[m] = (float)sqrt((m ? 2.0 : 1.0) * fact(4 - m) / fact(4 + m));
-    for (int m = 0; m <= 6; ++m) k.s6[m] = (float)sqrt((m ? 2.0 : 1.0) * fact(6 - m) / fact(6 + m));
+    for (int m = 0; m <= 6; ++m) {
+        // polynomials in z as coefficient arrays (index = power)
+        double pm2[8] = {0}, pm1[8] = {0}, pl[8] = {0};
+        double df = 1.0;
+        for (int q = 1; q <= m; ++q) df *= (2.0 * q - 1.0);
+        pm1[0] = (m % 2 ? -1.0 : 1.0) * df;  // Pr_m^m
+        auto store = [&](int l, const double *poly) {
+            if (l != 4 && l != 6) return;
+            const double sc = sqrt((m ? 2.0 : 1.0) * fact(l - m) / fact(l + m));
+            const int par = (l - m) & 1;
+            for (int e = 0; e <= (l - m) / 2; ++e) {
+                const float v = (float)(sc * poly[2 * e + par]);
+                if (l == 4) k.c4[m][e] = v;
+                else k.c6[m][e] = v;
+            }
+        };
+        store(m, pm1);
+        if (m + 1 <= 6) {
+            for (int e = 0; e < 7; ++e) pl[e + 1] = (2.0 * m + 1.0) * pm1[e];  // Pr_{m+1}^m
+            memcpy(pm2, pm1, sizeof(pm1));
+            memcpy(pm1, pl, sizeof(pl));
+            store(m + 1, pm1);
+        }
+        for (int l = m + 2; l <= 6; ++l) {
+            double nx[8] = {0};
+            for (int e = 0; e < 8; ++e) {
+                const double zt = e > 0 ? pm1[e - 1] : 0.0;
+                nx[e] = ((2.0 * l - 1.0) * zt - (l + m - 1.0) * pm2[e]) / (l - m);
+            }
+            memcpy(pm2, pm1, sizeof(pm1));
+            memcpy(pm1, nx, sizeof(nx));
+            store(l, pm1);
+        }
+    }
     return k;
 }
 
+// Adds the moments of one bond direction (x, y, z) (unit vector):
+// r_lm + i i_lm += sqrt(c_lm) Pr_l^m(z) (x + i y)^m, l = 4, 6, m = 0..l.
 __device__ __forceinline__ void boa_accumulate(const YlmCoef &K, float x, float y, float z, float (&r4)[5],
                                                float (&i4)[5], float (&r6)[7], float (&i6)[7]) {
+    const float z2 = z * z;
     float pr = 1.0f, pi = 0.0f;  // (x + i y)^m
 #pragma unroll
     for (int m = 0; m <= 6; ++m) {
         if (m > 0) {
-            const float t = pr * x - pi * y;
+            const float t = fmaf(pr, x, -pi * y);
             pi = fmaf(pr, y, pi * x);
             pr = t;
         }
-        float p2 = 0.0f, p1 = K.pmm[m], p4 = 0.0f, p6 = 0.0f;
-        if (m == 4) p4 = p1;
-        if (m == 6) p6 = p1;
-        if (m + 1 <= 6) {
-            const float p = (2.0f * m + 1.0f) * z * p1;
-            p2 = p1;
-            p1 = p;
-            if (m + 1 == 4) p4 = p1;
-            if (m + 1 == 6) p6 = p1;
-        }
-#pragma unroll
-        for (int l = m + 2; l <= 6; ++l) {
-            const float p = fmaf(K.a[l][m] * z, p1, -K.b[l][m] * p2);
-            p2 = p1;
-            p1 = p;
-            if (l == 4) p4 = p1;
-            if (l == 6) p6 = p1;
-        }
         if (m <= 4) {
-            const float w = K.s4[m] * p4;
+            float w = K.c4[m][(4 - m) / 2];
+#pragma unroll
+            for (int e = (4 - m) / 2 - 1; e >= 0; --e) w = fmaf(w, z2, K.c4[m][e]);
+            if ((4 - m) & 1) w *= z;
             r4[m] = fmaf(w, pr, r4[m]);
-            i4[m] = fmaf(w, pi, i4[m]);
+            if (m > 0) i4[m] = fmaf(w, pi, i4[m]);
         }
-        const float w6 = K.s6[m] * p6;
+        float w6 = K.c6[m][(6 - m) / 2];
+#pragma unroll
+        for (int e = (6 - m) / 2 - 1; e >= 0; --e) w6 = fmaf(w6, z2, K.c6[m][e]);
+        if ((6 - m) & 1) w6 *= z;
         r6[m] = fmaf(w6, pr, r6[m]);
-        i6[m] = fmaf(w6, pi, i6[m]);
+        if (m > 0) i6[m] = fmaf(w6, pi, i6[m]);
     }
 }
 
@@ -419,7 +434,7 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
         if (b) {
             const int32_t a = nu + __popc(ball & lt);
             if (a < FEAT_CAP) {
-                const float r = sqrtf(r2), ir = 1.0f / r;
+                const float ir = rsqrtf(r2), r = r2 * ir;  // hardware estimates (~2 ulp)
                 s_ud[g][a] = make_float4(dx * ir, dy * ir, dz * ir, r);
             }
         }
@@ -471,13 +486,15 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
     const float hlo = r_ref - 0.35f;
     for (int pidx = gl; pidx < npair; pidx += FEAT_G) {
         // pair (a, b), a < b, numbered pidx = b (b - 1) / 2 + a
-        int b = (int)(0.5f * (1.0f + sqrtf(fmaf(8.0f, (float)pidx, 1.0f))));
+        const float q8 = fmaf(8.0f, (float)pidx, 1.0f);
+        int b = (int)(0.5f * (1.0f + q8 * rsqrtf(q8)));  // an estimate, corrected below
         if (b * (b - 1) / 2 > pidx) --b;
         if ((b + 1) * b / 2 <= pidx) ++b;
         const int a = pidx - b * (b - 1) / 2;
         const float4 va = s_v[g][a], vb = s_v[g][b];
         const float cx = va.x - vb.x, cy = va.y - vb.y, cz = va.z - vb.z;
-        const float chord = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)));
+        const float c2 = fmaxf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)), 1e-30f);
+        const float chord = c2 * rsqrtf(c2);
         const float x = (chord - hlo) * 20.0f - 0.5f;
         const float fl = floorf(x);
         const int b0 = (int)fl;
@@ -555,6 +572,15 @@ __global__ void k_gather_pos(int64_t n, const int32_t *__restrict__ perm, const 
     const int64_t j = perm[k];
 #pragma unroll
     for (int d = 0; d < 3; ++d) pos_o[3 * k + d] = pos[3 * j + d];
+}
+
+int32_t snapshot_capacity(int64_t n, const ppmd_box *box, double r_list) {
+    // 1.6 times the mean count within r_list plus 16, at least 48: an overflow
+    // needs a local density far above the box's
+    const double vol = box->L[0] * box->L[1] * box->L[2];
+    const double mean = vol > 0 ? 4.18879020478639 * r_list * r_list * r_list * (double)n / vol : 0.0;
+    const int64_t cap = ((int64_t)ceil(1.6 * mean + 16.0) + 15) / 16 * 16;
+    return (int32_t)std::min<int64_t>(std::max<int64_t>(cap, 48), 1 << 20);
 }
 
 int end_pipeline(ppmd_ctx *ctx, int attempt, int32_t &max_nbr, int32_t *aux) {
@@ -655,17 +681,14 @@ extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const p
     cudaSetDevice(ctx->device);
     double r_list = fmax(want_boa ? r_boa : 0.0, want_cna ? r_cna : 0.0);
     if (!(r_list > 0)) return PPMD_OK;
-    int32_t max_nbr = SNAPSHOT_NBR;
-    for (int attempt = 0;; ++attempt) {
-        Snapshot s;
-        PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_list, max_nbr, s));
-        if (want_boa)
-            PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
-        if (want_cna)
-            PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, s.perm, nullptr, label));
-        const int rc = end_pipeline(ctx, attempt, max_nbr);
-        if (rc != PIPELINE_RETRY) return rc;
-    }
+    // asynchronous: a list overflow stays latched for the next synchronising call
+    Snapshot s;
+    PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_list, snapshot_capacity(n, box, r_list), s));
+    if (want_boa)
+        PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
+    if (want_cna)
+        PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, s.perm, nullptr, label));
+    return check_launch(ctx, "ppmd_analyze");
 }
 
 extern "C" int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat,
@@ -673,7 +696,7 @@ extern "C" int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const 
     if (!ctx || !box || n < 0 || (n > 0 && !pos) || !(r_feat > 0) || !(r_ref < r_feat) || (!feat && !feat_bf16))
         return set_error(ctx, PPMD_ERR_INVALID, "ppmd_features: bad argument");
     cudaSetDevice(ctx->device);
-    int32_t max_nbr = SNAPSHOT_NBR;
+    int32_t max_nbr = snapshot_capacity(n, box, r_feat);
     for (int attempt = 0;; ++attempt) {
         Snapshot s;
         PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, max_nbr, s));

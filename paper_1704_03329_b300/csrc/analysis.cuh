@@ -23,7 +23,8 @@ struct Snapshot {
 // Bin/sort the caller's atoms with cells of edge >= r_list and build the
 // list at r_list with max_nbr entries per atom (no synchronisation: an
 // overflow is latched in the context's status).
-constexpr int32_t SNAPSHOT_NBR = 32;  // first list capacity of the analysis pipelines
+// List capacity of the analysis pipelines for n atoms in box at r_list.
+int32_t snapshot_capacity(int64_t n, const ppmd_box *box, double r_list);
 // End of a pipeline: wait and read the status (and the aux result word).
 // Returns PIPELINE_RETRY when the list overflowed on the first attempt, with
 // max_nbr raised to what was needed (the caller runs the pipeline again),

@@ -573,16 +573,23 @@ __global__ void k_sum_loss(const double *part, int nblk, float *loss) {
 }
 
 // Input standardisation from n feature rows: per feature (thread f of 32)
-// sums of x and x^2 over rows, in FP64, one partial per block.
+// sums of x and x^2 over rows, compensated (Kahan) in FP32 per thread (FP64
+// arithmetic is slow on this part), then in FP64 across threads and blocks;
+// one partial per block.
 __global__ void k_feat_stats(int64_t n, const __nv_bfloat16 *__restrict__ x, double *__restrict__ part) {
     __shared__ double sh[8][32][2];
     const int f = threadIdx.x & 31, rl = threadIdx.x >> 5;
-    double s = 0.0, s2 = 0.0;
+    float a = 0.0f, ac = 0.0f, b = 0.0f, bc = 0.0f;  // sums and their compensations
     for (int64_t r = (int64_t)blockIdx.x * 8 + rl; r < n; r += (int64_t)gridDim.x * 8) {
-        const double v = __bfloat162float(x[r * 32 + f]);
-        s += v;
-        s2 += v * v;
+        const float v = __bfloat162float(x[r * 32 + f]);
+        const float y1 = v - ac, t1 = a + y1;
+        ac = (t1 - a) - y1;
+        a = t1;
+        const float y2 = fmaf(v, v, -bc), t2 = b + y2;
+        bc = (t2 - b) - y2;
+        b = t2;
     }
+    double s = (double)a - (double)ac, s2 = (double)b - (double)bc;
     sh[rl][f][0] = s;
     sh[rl][f][1] = s2;
     __syncthreads();
@@ -716,7 +723,7 @@ extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t
         return ppmd_analyze(ctx, pos, n, box, 0.0, r_cna, nullptr, nullptr, nullptr, label);
     }
     const size_t nn = (size_t)(n > 0 ? n : 1);
-    int32_t max_nbr = SNAPSHOT_NBR;
+    int32_t max_nbr = snapshot_capacity(n, box, r_feat);
     for (int attempt = 0;; ++attempt) {
         Snapshot s;
         PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, max_nbr, s));
@@ -739,10 +746,11 @@ extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t
         PPMD_TRY(cna_subset_launch(ctx, n, nfb, fb, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, cls));
         if (n > 0) PPMD_LAUNCH(ctx, k_write_labels, div_up(n, 256), 256, 0, n, s.perm, cls, conf_s, label, confidence);
         PPMD_TRY(check_launch(ctx, "ppmd_classify"));
+        if (!n_fallback) return PPMD_OK;  // asynchronous: an overflow stays latched
         int32_t hfb = 0;
         const int rc = end_pipeline(ctx, attempt, max_nbr, &hfb);
         if (rc == PIPELINE_RETRY) continue;
-        if (n_fallback) *n_fallback = hfb;
+        *n_fallback = hfb;
         return rc;
     }
 }

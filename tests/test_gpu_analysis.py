@@ -138,3 +138,26 @@ def test_analyze_full_size_box_sampled(L, ctx):
     assert np.abs(out["q6"].cpu().numpy()[sample] - Q6o[sample]).max() <= 1e-5
     # labels are mostly hcp at this noise level
     assert (out["label"].cpu().numpy() == 2).mean() > 0.5
+
+
+def test_analyze_overflow_is_latched_and_features_retry(L, ctx):
+    """A dense clump in a dilute box: the asynchronous pipeline's list (capacity
+    from the box density) overflows; the next synchronising call reports
+    PPMD_ERR_CAPACITY with the row length needed.  ppmd_features, which
+    synchronises, builds the list again at that length and matches the oracle."""
+    rng = np.random.default_rng(11)
+    L_box = np.array([20.0, 20.0, 20.0])
+    spread = rng.uniform(0.0, 20.0, (600, 3))
+    clump = 10.0 + rng.uniform(-0.4, 0.4, (56, 3))  # every pair closer than 1.39
+    pos = np.concatenate([spread, clump])
+    L.ppmd_analyze(ctx, cu(pos), L_box, R_BOA, R_CNA)
+    with pytest.raises(L.PPMDError) as ei:
+        ctx.sync()
+    assert ei.value.code == L.ERR_CAPACITY
+    ctx.sync()  # the report cleared the status
+    f, _ = L.ppmd_features(ctx, cu(pos), L_box, R_BOA, fp32=True, bf16=False, r_ref=R_CNA)
+    offs, nb = oracle.neighbours_cells(pos, L_box, R_BOA)
+    nbond = np.diff(offs)
+    assert 48 < nbond.max() <= 64  # over the first capacity, within the 64 bonds features take
+    fo = oracle.features(pos, L_box, offs, nb, R_BOA, R_CNA)
+    assert np.abs(f.cpu().numpy() - fo).max() <= 2e-5
