@@ -57,6 +57,7 @@ def _load():
         "ora_cna": (i32, [i64, P, P, f64, P, P, i32, P, P, P]),
         "ora_cna_label": (None, [i64, P, P, i32, P]),
         "ora_features": (None, [i64, P, P, f64, f64, P, P, P]),
+        "ora_acna": (None, [i64, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -204,6 +205,20 @@ def cna_label(nbond, trip):
     lab = np.zeros(n, np.int8)
     _load().ora_cna_label(n, _p(nbond), _p(trip), int(mb), _p(lab))
     return lab
+
+
+def acna(pos, box, offs, nbr):
+    """Adaptive CNA over a neighbour list that holds at least the 14 nearest
+    neighbours of every atom (see ppmd_oracle.c).  Returns (label int8 [n],
+    rcut [n, 2]: the fcc/hcp and bcc local cutoffs, 0 when not computed)."""
+    pos, box = _f64(pos), _f64(box)
+    n = len(pos)
+    lab = np.zeros(n, np.int8)
+    rc = np.zeros((n, 2))
+    offs = np.ascontiguousarray(offs, np.int64)
+    nbr = np.ascontiguousarray(nbr, np.int32)
+    _load().ora_acna(n, _p(pos), _p(box), _p(offs), _p(nbr), _p(lab), _p(rc))
+    return lab, rc
 
 
 def features(pos, box, offs, nbr, r_feat=1.5, r_ref=1.433625):

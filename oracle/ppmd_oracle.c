@@ -15,7 +15,9 @@
  *   - Velocity Verlet: Algorithm 6 with the access descriptors of Table 5;
  *   - bond order parameters: Eqs. (1)-(2), Algorithms 1 and 2;
  *   - common neighbour analysis: Eqs. (3)-(5), Algorithms 3-5 and the
- *     largest-cluster Algorithm 7 (appendix D).
+ *     largest-cluster Algorithm 7 (appendix D);
+ *   - adaptive CNA (the extension the CNA section cites): per-atom cutoffs
+ *     from the 12 or 14 nearest neighbours, then Eqs. (3)-(5).
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - all cutoff tests are strict (r < rc), as in the printed kernels;
@@ -717,4 +719,116 @@ void ora_features(int64_t n, const double *pos, const double *L, double r_feat, 
     free(u);
     free(q4);
     free(q6);
+}
+
+/* ------------------------------------------------------------------ */
+/* Adaptive CNA: the extension of CNA that the CNA section cites
+ * (Stukowski 2012) to remove the choice of the cutoff.  Each atom i sets its
+ * own bond cutoff from its N nearest neighbours (distances d_1 <= ... <= d_N
+ * over its list, ties by index; N = 12 for the fcc/hcp test, 14 for bcc):
+ *   fcc/hcp  r_i = f (d_1 + ... + d_12) / 12,
+ *   bcc      r_i = f (c (d_1 + ... + d_8) + d_9 + ... + d_14) / 14,
+ * with f = (1 + sqrt 2) / 2 (midway between the first and second shells of
+ * fcc in units of the nearest-neighbour distance) and c = 2 / sqrt 3 (the
+ * first bcc shell scaled to the second).  Only those N neighbours take part:
+ * all are bonded to i, and two of them are bonded when closer than r_i
+ * (strict, as everywhere).  The bond i-j then gets the CNA triplet of
+ * Eqs. (3)-(5) over the common neighbours among the N, with Algorithm 7 for
+ * the largest cluster.  fcc: 12 x (4,2,1); hcp: 6 x (4,2,1) + 6 x (4,2,2)
+ * (12-neighbour test); failing both, bcc: 8 x (6,6,6) + 6 x (4,4,4)
+ * (14-neighbour test); else other.  A test that needs more neighbours than
+ * the list holds fails.  rcut (may be NULL): [n][2], the two cutoffs, 0 when
+ * not computed (the bcc one only when the fcc/hcp test failed).
+ * ------------------------------------------------------------------ */
+typedef struct {
+    double r2;
+    int32_t j;
+} ora_nb;
+
+static int cmp_nb(const void *a, const void *b) {
+    const ora_nb *x = (const ora_nb *)a, *y = (const ora_nb *)b;
+    if (x->r2 < y->r2) return -1;
+    if (x->r2 > y->r2) return 1;
+    return (x->j > y->j) - (x->j < y->j);
+}
+
+/* Triplet of the bond between the centre and sel[a] among the N selected. */
+static uint32_t acna_triplet(const double *pos, const double *L, const int32_t *sel, int N, int a, double rc2) {
+    int32_t cn[16];
+    int ncn = 0;
+    double dr[3];
+    for (int b = 0; b < N; ++b)
+        if (b != a && min_image(&pos[3 * sel[a]], &pos[3 * sel[b]], L, dr) < rc2) cn[ncn++] = sel[b];
+    ora_edge E[16 * 15 / 2];
+    int ne = 0;
+    for (int p = 0; p < ncn; ++p)
+        for (int q = p + 1; q < ncn; ++q)
+            if (min_image(&pos[3 * cn[p]], &pos[3 * cn[q]], L, dr) < rc2) {
+                E[ne].a = cn[p];
+                E[ne].b = cn[q];
+                ++ne;
+            }
+    const int nlcb = ne > 0 ? max_cluster_size(E, ne) : 0;
+    return ((uint32_t)ncn << 16) | ((uint32_t)ne << 8) | (uint32_t)nlcb;
+}
+
+void ora_acna(int64_t n, const double *pos, const double *L, const int64_t *offs, const int32_t *nbr, int8_t *label,
+              double *rcut) {
+    const double f = (1.0 + sqrt(2.0)) * 0.5;
+    const double c = 2.0 / sqrt(3.0);
+    const uint32_t t421 = (4u << 16) | (2u << 8) | 1u, t422 = (4u << 16) | (2u << 8) | 2u;
+    const uint32_t t444 = (4u << 16) | (4u << 8) | 4u, t666 = (6u << 16) | (6u << 8) | 6u;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t deg = offs[i + 1] - offs[i];
+        ora_nb *cand = (ora_nb *)malloc(sizeof(ora_nb) * (size_t)(deg > 0 ? deg : 1));
+        double dr[3];
+        for (int64_t k = 0; k < deg; ++k) {
+            cand[k].j = nbr[offs[i] + k];
+            cand[k].r2 = min_image(&pos[3 * i], &pos[3 * cand[k].j], L, dr);
+        }
+        qsort(cand, (size_t)deg, sizeof(ora_nb), cmp_nb);
+        int8_t lab = 0;
+        double rc12 = 0.0, rc14 = 0.0;
+        int32_t sel[14];
+        if (deg >= 12) {
+            double s = 0.0;
+            for (int a = 0; a < 12; ++a) {
+                s += sqrt(cand[a].r2);
+                sel[a] = cand[a].j;
+            }
+            rc12 = f * (s / 12.0);
+            const double rc2 = rc12 * rc12;
+            int c421 = 0, c422 = 0;
+            for (int a = 0; a < 12; ++a) {
+                const uint32_t t = acna_triplet(pos, L, sel, 12, a, rc2);
+                c421 += (t == t421);
+                c422 += (t == t422);
+            }
+            if (c421 == 12) lab = 1;
+            else if (c421 == 6 && c422 == 6) lab = 2;
+        }
+        if (lab == 0 && deg >= 14) {
+            double s8 = 0.0, s6 = 0.0;
+            for (int a = 0; a < 14; ++a) {
+                if (a < 8) s8 += sqrt(cand[a].r2);
+                else s6 += sqrt(cand[a].r2);
+                sel[a] = cand[a].j;
+            }
+            rc14 = f * ((c * s8 + s6) / 14.0);
+            const double rc2 = rc14 * rc14;
+            int c444 = 0, c666 = 0;
+            for (int a = 0; a < 14; ++a) {
+                const uint32_t t = acna_triplet(pos, L, sel, 14, a, rc2);
+                c444 += (t == t444);
+                c666 += (t == t666);
+            }
+            if (c666 == 8 && c444 == 6) lab = 3;
+        }
+        label[i] = lab;
+        if (rcut) {
+            rcut[2 * i] = rc12;
+            rcut[2 * i + 1] = rc14;
+        }
+        free(cand);
+    }
 }

@@ -273,3 +273,128 @@ def test_adamw_textbook_steps():
     mh, vh = m / (1 - 0.81), v / (1 - 0.999 ** 2)
     exp2 = exp1 * (1 - 0.05) - 0.1 * mh / (np.sqrt(vh) + 1e-8)
     assert np.allclose(p["W1"], exp2, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Adaptive CNA
+# ---------------------------------------------------------------------------
+ACNA_F = (1.0 + np.sqrt(2.0)) / 2.0
+ACNA_CELLS = {"fcc": (4, 4, 4), "hcp": (5, 3, 3), "bcc": (5, 5, 5)}
+
+
+@pytest.mark.parametrize("kind,code", [("fcc", 1), ("hcp", 2), ("bcc", 3)])
+@pytest.mark.parametrize("scale", [0.8, 1.0, 1.3])
+def test_acna_perfect_lattices_at_any_density(kind, code, scale):
+    """The point of the adaptive cutoff: perfect lattices are recognised at
+    any density (a fixed-cutoff CNA at 1.433625 would not be), and the local
+    cutoff is f d_nn (fcc, hcp) or f a (bcc) in closed form."""
+    rho = 0.8442 / scale ** 3
+    lat = make_lattice(kind, ACNA_CELLS[kind], rho)
+    pos, box = lat.sites(), lat.box
+    offs, nb = oracle.neighbours_cells(pos, box, 1.8 * scale)
+    lab, rc = oracle.acna(pos, box, offs, nb)
+    assert (lab == code).all()
+    if kind == "bcc":
+        a = (2.0 / rho) ** (1.0 / 3.0)
+        assert np.allclose(rc[:, 1], ACNA_F * a, rtol=1e-12)
+    else:
+        d_nn = (np.sqrt(2.0) / rho) ** (1.0 / 3.0)
+        assert np.allclose(rc[:, 0], ACNA_F * d_nn, rtol=1e-12)
+        assert (rc[:, 1] == 0).all()
+
+
+def test_acna_scale_invariance_is_exact():
+    """Doubling every length (a power of two: every FP64 operation scales
+    exactly) leaves every label unchanged and doubles every cutoff."""
+    pos, box = _mixed_box(seed=5)
+    offs, nb = oracle.neighbours_cells(pos, box, 1.8)
+    lab, rc = oracle.acna(pos, box, offs, nb)
+    offs2, nb2 = oracle.neighbours_cells(2.0 * pos, 2.0 * box, 3.6)
+    lab2, rc2 = oracle.acna(2.0 * pos, 2.0 * box, offs2, nb2)
+    assert np.array_equal(lab, lab2)
+    assert np.array_equal(2.0 * rc, rc2)
+    assert len(set(lab.tolist())) >= 2  # the box mixes ordered and disordered environments
+
+
+def _mixed_box(seed):
+    """A small noisy box: fcc, bcc or hcp environments and disordered ones."""
+    rng = np.random.default_rng(seed)
+    lat = make_lattice("fcc", (5, 5, 5), 0.8442)
+    pos = lat.sites() + rng.normal(0.0, 0.06, (len(lat.sites()), 3))
+    # a disordered slab
+    sl = pos[:, 2] < lat.box[2] * 0.3
+    pos[sl] += rng.normal(0.0, 0.25, (sl.sum(), 3))
+    return pos - lat.box * np.floor(pos / lat.box), np.asarray(lat.box, float)
+
+
+def _acna_numpy(pos, box, offs, nb):
+    """Adaptive CNA written independently: dense adjacency matrices and
+    scipy's connected components for the largest cluster."""
+    from scipy.sparse.csgraph import connected_components
+    f, c = (1.0 + np.sqrt(2.0)) * 0.5, 2.0 / np.sqrt(3.0)
+    n = len(pos)
+    out = np.zeros(n, np.int8)
+
+    def r2(a, b):
+        t = pos[a] - pos[b]
+        t = t - box * np.rint(t / box)
+        return t[..., 0] * t[..., 0] + t[..., 1] * t[..., 1] + t[..., 2] * t[..., 2]
+
+    def signatures(sel, rc):
+        rc2 = rc * rc
+        A = r2(sel[:, None], sel[None, :]) < rc2
+        np.fill_diagonal(A, False)
+        sig = []
+        for a in range(len(sel)):
+            cn = np.flatnonzero(A[a])
+            sub = A[np.ix_(cn, cn)]
+            ne = int(sub.sum()) // 2
+            best = 0
+            if ne:
+                k, comp = connected_components(sub.astype(np.int8), directed=False)
+                for q in range(k):
+                    m = comp == q
+                    best = max(best, int(sub[np.ix_(m, m)].sum()) // 2)
+            sig.append((len(cn), ne, best))
+        return sig
+
+    for i in range(n):
+        js = nb[offs[i]:offs[i + 1]]
+        d2 = r2(np.full(len(js), i), js)
+        order = np.lexsort((js, d2))
+        js, d2 = js[order], d2[order]
+        lab = 0
+        if len(js) >= 12:
+            s = 0.0
+            for v in d2[:12]:
+                s += np.sqrt(v)
+            sig = signatures(js[:12], f * (s / 12.0))
+            if sig.count((4, 2, 1)) == 12:
+                lab = 1
+            elif sig.count((4, 2, 1)) == 6 and sig.count((4, 2, 2)) == 6:
+                lab = 2
+        if lab == 0 and len(js) >= 14:
+            s8 = s6 = 0.0
+            for k, v in enumerate(d2[:14]):
+                if k < 8:
+                    s8 += np.sqrt(v)
+                else:
+                    s6 += np.sqrt(v)
+            sig = signatures(js[:14], f * ((c * s8 + s6) / 14.0))
+            if sig.count((6, 6, 6)) == 8 and sig.count((4, 4, 4)) == 6:
+                lab = 3
+        out[i] = lab
+    return out
+
+
+@pytest.mark.parametrize("kind", ["fcc", "bcc", "hcp", "mixed"])
+def test_acna_matches_independent_numpy_version(kind):
+    if kind == "mixed":
+        pos, box = _mixed_box(seed=9)
+    else:
+        c = configs.structure_box(kind, 0.07, 8, cells={"fcc": (4, 4, 3), "bcc": (5, 5, 4), "hcp": (5, 3, 3)}[kind])
+        pos, box = c["pos"], np.asarray(c["box"], float)
+    offs, nb = oracle.neighbours_cells(pos, box, 1.8)
+    lab, _ = oracle.acna(pos, box, offs, nb)
+    assert np.array_equal(lab, _acna_numpy(pos, box, offs, nb))
+    assert (lab > 0).any()
