@@ -392,7 +392,7 @@ def test_acna_matches_independent_numpy_version(kind):
     if kind == "mixed":
         pos, box = _mixed_box(seed=9)
     else:
-        c = configs.structure_box(kind, 0.07, 8, cells={"fcc": (4, 4, 3), "bcc": (5, 5, 4), "hcp": (5, 3, 3)}[kind])
+        c = configs.structure_box(kind, 0.07, 8, cells={"fcc": (4, 4, 4), "bcc": (5, 5, 5), "hcp": (5, 3, 3)}[kind])
         pos, box = c["pos"], np.asarray(c["box"], float)
     offs, nb = oracle.neighbours_cells(pos, box, 1.8)
     lab, _ = oracle.acna(pos, box, offs, nb)
