@@ -368,14 +368,26 @@ def suite_analysis(args, L, ctx, stream):
     def cna():
         for (p, b), o in zip(dev, outs):
             L.ppmd_analyze(ctx, p, b, None, R_CNA, boa=False, cna=True, out={"label": o["label"]})
+    acna_lab = [torch.empty(p.shape[0], dtype=torch.int8, device="cuda") for p, _ in dev]
+
+    def acna():
+        for (p, b), lab in zip(dev, acna_lab):
+            lab.copy_(L.ppmd_acna(ctx, p, b, 1.8, want_rcut=False)[0])
+    acna()  # warm-up
     tb, _ = _timed(stream, boa)
     tc, _ = _timed(stream, cna)
-    frac = {k: float((torch.cat([o["label"] for o in outs]) == v).float().mean()) for k, v in
-            (("other", 0), ("fcc", 1), ("hcp", 2), ("bcc", 3))}
+    ta, _ = _timed(stream, acna)
+    ctx.sync()
+    lab_c = torch.cat([o["label"] for o in outs])
+    lab_a = torch.cat(acna_lab)
+    frac = {k: float((lab_c == v).float().mean()) for k, v in (("other", 0), ("fcc", 1), ("hcp", 2), ("bcc", 3))}
+    frac_a = {k: float((lab_a == v).float().mean()) for k, v in (("other", 0), ("fcc", 1), ("hcp", 2), ("bcc", 3))}
     res = {"workload": "structure boxes fcc, bcc, hcp, liquid-like x 512,000 atoms, noise 0.05 d_nn; "
-                       "BOA cutoff 1.5, CNA cutoff 1.433625; each timing includes cell sort and list build",
+                       "BOA cutoff 1.5, CNA cutoff 1.433625, adaptive CNA list 1.8; each timing includes "
+                       "cell sort and list build",
            "metric": "classified atoms/s", "atoms": n, "boa_atoms_per_s": n / tb, "cna_atoms_per_s": n / tc,
-           "label_fractions": frac}
+           "acna_atoms_per_s": n / ta, "label_fractions": frac, "acna_label_fractions": frac_a,
+           "acna_agreement_with_cna": float((lab_a == lab_c).float().mean())}
     if not args.no_cpu:
         import time as _t
         import oracle

@@ -194,6 +194,26 @@ int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, d
 int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
                  float *q4, float *q6, int32_t *n_nb, int8_t *label);
 
+/* Adaptive CNA (the extension of CNA that Sec. 4.2 cites, Stukowski 2012):
+ * every atom sets its own bond cutoff from its N nearest neighbours
+ * (distances d_1 <= ... <= d_N over the list at r_list, ties by index):
+ *   fcc/hcp test, N = 12:  r = f (d_1 + ... + d_12) / 12,
+ *   bcc test,     N = 14:  r = f (c (d_1 + ... + d_8) + d_9 + ... + d_14) / 14,
+ * f = (1 + sqrt 2)/2, c = 2/sqrt 3.  Only those N neighbours take part (all
+ * bonded to the atom, two of them bonded when closer than r) and each bond
+ * gets the triplet of Eqs. (3)-(5) over its common neighbours among them.
+ * Labels (caller order, label[n] device int8): 1 fcc (12 x (4,2,1)), 2 hcp
+ * (6 x (4,2,1) + 6 x (4,2,2)), else 3 bcc (8 x (6,6,6) + 6 x (4,4,4) in the
+ * 14-neighbour test), else 0.  rcut (device FP64 [n][2], may be NULL): the
+ * two cutoffs, 0 when not computed (the bcc one only after the fcc/hcp test
+ * failed).  Decisions and cutoffs equal the FP64 evaluation bit for bit.
+ * r_list must reach the 14th neighbour (e.g. 1.8 at density 0.8442); a test
+ * that needs more neighbours than the list holds fails.  At most 64 list
+ * entries per atom (more: PPMD_ERR_CAPACITY, latched).  Asynchronous, as
+ * ppmd_analyze. */
+int ppmd_acna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int8_t *label,
+              double *rcut);
+
 /* ------------------------------------------------------------------ */
 /* Learned structure classifier (not in the paper): an MLP 30 -> 64 -> 64
  * -> 4 (ReLU, softmax over 0 other, 1 fcc, 2 hcp, 3 bcc) on local-

@@ -70,6 +70,7 @@ _SIGS = {
     "ppmd_analyze": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _D, _P, _P, _P, _P]),
     "ppmd_features": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _D, _P, _P]),
     "ppmd_mlp_forward": (_I, [_P, _P, _P, _I64, _P]),
+    "ppmd_acna": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P]),
     "ppmd_mlp_fit_input_norm": (_I, [_P, _P, _P, _I64]),
     "ppmd_mlp_grad": (_I, [_P, _P, _P, _P, _I64, _P, _P]),
     "ppmd_mlp_adamw": (_I, [_P, _P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -267,6 +268,16 @@ def ppmd_analyze(ctx: Context, pos, box, r_boa=1.5, r_cna=None, boa=True, cna=Tr
                                 _opt(out.get("q4")), _opt(out.get("q6")), _opt(out.get("n_nb")),
                                 _opt(out.get("label"))))
     return out
+
+
+def ppmd_acna(ctx: Context, pos, box, r_list=1.8, want_rcut=True):
+    """Adaptive CNA labels int8 [n] and the local cutoffs float64 [n, 2] (caller order)."""
+    n = pos.shape[0]
+    lab = torch.empty(n, dtype=torch.int8, device=pos.device)
+    rc = torch.empty((n, 2), dtype=torch.float64, device=pos.device) if want_rcut else None
+    b = _box(box)
+    ctx.check(_lib.ppmd_acna(ctx.h, _ptr(pos), n, C.byref(b), float(r_list), _ptr(lab), _opt(rc)))
+    return lab, rc
 
 
 MLP_NPARAM = 6464

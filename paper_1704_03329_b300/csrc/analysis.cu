@@ -315,6 +315,232 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
     }
 }
 
+// ---------------------------------------------------------------------
+// Adaptive CNA (the extension the CNA section cites): per-atom cutoffs
+// from the 12 (fcc/hcp test) or 14 (bcc test) nearest neighbours,
+//   r_12 = f (d_1 + ... + d_12) / 12,  r_14 = f (c (d_1 + ... + d_8) + d_9 + ... + d_14) / 14,
+// f = (1 + sqrt 2)/2, c = 2/sqrt 3; only those neighbours take part, two of
+// them bonded when closer than the cutoff; CNA triplets over them.  One warp
+// per atom, up to 64 list entries (two per lane).  Every decision is the
+// FP64 one: the nearest neighbours are ranked in FP32 and the candidates
+// that could sit at the N-th place within FP32 error are ranked again by
+// their FP64 distance (ties by index); the cutoff is summed in FP64 in rank
+// order with IEEE operations; bond tests take FP32 outside a band around
+// the cutoff and FP64 inside it.
+// ---------------------------------------------------------------------
+constexpr int ACNA_WARPS = 4;
+
+__global__ void __launch_bounds__(ACNA_WARPS * 32) k_acna(int64_t n, const int4 *__restrict__ xq,
+                                                          const double *__restrict__ pos64, SegTable st,
+                                                          const int32_t *__restrict__ nbr,
+                                                          const int32_t *__restrict__ cnt, int32_t max_nbr, int64_t si,
+                                                          int64_t sm, double f, double c,
+                                                          const int32_t *__restrict__ out_idx, int8_t *__restrict__ label,
+                                                          double *__restrict__ rcut, int32_t *status,
+                                                          unsigned long long *needed) {
+    __shared__ int32_t s_j[ACNA_WARPS][16];
+    __shared__ int4 s_x[ACNA_WARPS][16];
+    __shared__ unsigned s_A[ACNA_WARPS][16];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * ACNA_WARPS + w;
+    if (i >= n) return;
+    const int4 xi = xq[i];
+    const Seg &S = seg_ref(st, xi.w);
+    const int32_t deg = min(cnt[i], max_nbr);
+    const int64_t o = out_idx ? out_idx[i] : i;
+    if (deg > 64) {
+        if (lane == 0) {
+            latch_status(status, PPMD_ERR_CAPACITY);
+            latch_needed(needed, (unsigned long long)deg);
+            label[o] = PPMD_OTHER;
+            if (rcut) rcut[2 * o] = rcut[2 * o + 1] = 0.0;
+        }
+        return;
+    }
+    const int32_t *row = nbr + i * si;
+    // candidates k = lane and lane + 32
+    int32_t jj[2];
+    int4 xj[2];
+    float r2f[2];
+    double d64[2];
+    bool have64[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int32_t k = lane + 32 * q;
+        have64[q] = false;
+        d64[q] = 0.0;
+        if (k < deg) {
+            jj[q] = row[k * sm];
+            xj[q] = xq[jj[q]];
+            const float dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj[q].x, S.sx[0]);
+            const float dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj[q].y, S.sx[1]);
+            const float dz = fixed_delta((uint32_t)xi.z, (uint32_t)xj[q].z, S.sx[2]);
+            r2f[q] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        } else {
+            jj[q] = 0x7fffffff;
+            xj[q] = make_int4(0, 0, 0, 0);
+            r2f[q] = __int_as_float(0x7f800000);  // +inf
+        }
+    }
+    // FP32 rank by (r2, index)
+    int rk[2] = {0, 0};
+    for (int src = 0; src < 32; ++src)
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2) {
+            const float r = __shfl_sync(0xffffffffu, r2f[q2], src);
+            const int32_t jv = __shfl_sync(0xffffffffu, jj[q2], src);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) rk[q] += (r < r2f[q]) || (r == r2f[q] && jv < jj[q]);
+        }
+    int8_t lab = PPMD_OTHER;
+    double rc12 = 0.0, rc14 = 0.0;
+    for (int test = 0; test < 2; ++test) {
+        const int N = test == 0 ? 12 : 14;
+        if (deg < N || (test == 1 && lab != PPMD_OTHER)) break;
+        // FP32 distance of the (N+1)-th candidate (inf when there is none)
+        float tN = __int_as_float(0x7f800000);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const unsigned b = __ballot_sync(0xffffffffu, rk[q] == N && lane + 32 * q < deg);
+            if (b) tN = __shfl_sync(0xffffffffu, r2f[q], __ffs(b) - 1);
+        }
+        // FP32 r^2 is within ~3e-7 r^2 + 1e-7 of the FP64 value: every
+        // candidate that can be among the N nearest lies below tN + band
+        const float lim = tN + (2e-6f * tN + 1e-6f);
+        bool near[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            near[q] = (lane + 32 * q < deg) && r2f[q] <= lim;
+            if (near[q] && !have64[q]) {
+                double dr[3];
+                d64[q] = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)jj[q], S, dr);
+                have64[q] = true;
+            }
+        }
+        // exact rank among the near candidates by (FP64 r^2, index)
+        int ex[2] = {0, 0};
+        for (int src = 0; src < 32; ++src)
+#pragma unroll
+            for (int q2 = 0; q2 < 2; ++q2) {
+                const bool nv = __shfl_sync(0xffffffffu, near[q2], src);
+                const double dv = __shfl_sync(0xffffffffu, d64[q2], src);
+                const int32_t jv = __shfl_sync(0xffffffffu, jj[q2], src);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) ex[q] += nv && ((dv < d64[q]) || (dv == d64[q] && jv < jj[q]));
+            }
+        bool sel[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            sel[q] = near[q] && ex[q] < N;
+            if (sel[q]) {
+                s_j[w][ex[q]] = jj[q];
+                s_x[w][ex[q]] = xj[q];
+            }
+        }
+        // the cutoff: sum of the FP64 distances in rank order
+        double s8 = 0.0, s6 = 0.0;
+        for (int r = 0; r < N; ++r) {
+            double v = 0.0;
+            int src = 0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const unsigned b = __ballot_sync(0xffffffffu, sel[q] && ex[q] == r);
+                if (b) {
+                    src = __ffs(b) - 1;
+                    v = __shfl_sync(0xffffffffu, d64[q], src);
+                }
+            }
+            const double d = __dsqrt_rn(v);
+            if (test == 0 || r < 8) s8 = __dadd_rn(s8, d);
+            else s6 = __dadd_rn(s6, d);
+        }
+        const double rc = test == 0 ? __dmul_rn(f, __ddiv_rn(s8, 12.0))
+                                    : __dmul_rn(f, __ddiv_rn(__dadd_rn(__dmul_rn(c, s8), s6), 14.0));
+        const double rc2 = __dmul_rn(rc, rc);
+        if (test == 0) rc12 = rc;
+        else rc14 = rc;
+        __syncwarp();
+        // bonds among the N selected (bit b of s_A[a]: a and b closer than rc)
+        const float rc2f = (float)rc2, bandb = 2e-6f * rc2f + 1e-6f;
+        if (lane < N) {
+            const int4 xa = s_x[w][lane];
+            const double *pa = pos64 + 3 * (int64_t)s_j[w][lane];
+            unsigned m = 0u;
+            for (int b = 0; b < N; ++b) {
+                if (b == lane) continue;
+                const int4 xb = s_x[w][b];
+                const float dx = fixed_delta((uint32_t)xa.x, (uint32_t)xb.x, S.sx[0]);
+                const float dy = fixed_delta((uint32_t)xa.y, (uint32_t)xb.y, S.sx[1]);
+                const float dz = fixed_delta((uint32_t)xa.z, (uint32_t)xb.z, S.sx[2]);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                bool bd = r2 < rc2f - bandb;
+                if (!bd && r2 <= rc2f + bandb) {
+                    double dr[3];
+                    bd = min_image_r2(pa, pos64 + 3 * (int64_t)s_j[w][b], S, dr) < rc2;
+                }
+                if (bd) m |= 1u << b;
+            }
+            s_A[w][lane] = m;
+        }
+        __syncwarp();
+        int c421 = 0, c422 = 0, c444 = 0, c666 = 0;
+        if (lane < N) {
+            const unsigned C = s_A[w][lane];
+            const int ncn = __popc(C);
+            int twice_nb = 0;
+            for (unsigned r = C; r; r &= r - 1) twice_nb += __popc(s_A[w][__ffs(r) - 1] & C);
+            int best = 0;
+            unsigned rest = C;
+            while (rest) {
+                unsigned comp = rest & (~rest + 1u), frontier = comp;
+                while (frontier) {
+                    unsigned grow = 0u;
+                    for (unsigned fr = frontier; fr; fr &= fr - 1) grow |= s_A[w][__ffs(fr) - 1];
+                    grow &= C & ~comp;
+                    comp |= grow;
+                    frontier = grow;
+                }
+                int twice_e = 0;
+                for (unsigned fr = comp; fr; fr &= fr - 1) twice_e += __popc(s_A[w][__ffs(fr) - 1] & comp);
+                best = max(best, twice_e >> 1);
+                rest &= ~comp;
+            }
+            const uint32_t t = ((uint32_t)ncn << 16) | ((uint32_t)(twice_nb >> 1) << 8) | (uint32_t)best;
+            c421 = t == ((4u << 16) | (2u << 8) | 1u);
+            c422 = t == ((4u << 16) | (2u << 8) | 2u);
+            c444 = t == ((4u << 16) | (4u << 8) | 4u);
+            c666 = t == ((6u << 16) | (6u << 8) | 6u);
+        }
+        c421 = __reduce_add_sync(0xffffffffu, c421);
+        c422 = __reduce_add_sync(0xffffffffu, c422);
+        c444 = __reduce_add_sync(0xffffffffu, c444);
+        c666 = __reduce_add_sync(0xffffffffu, c666);
+        if (test == 0) {
+            if (c421 == 12) lab = PPMD_FCC;
+            else if (c421 == 6 && c422 == 6) lab = PPMD_HCP;
+        } else if (c666 == 8 && c444 == 6) {
+            lab = PPMD_BCC;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        label[o] = lab;
+        if (rcut) {
+            rcut[2 * o] = rc12;
+            rcut[2 * o + 1] = rc14;
+        }
+    }
+}
+
+int acna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
+                const int32_t *cnt, int32_t max_nbr, int64_t ld, const int32_t *out_idx, int8_t *label, double *rcut) {
+    const double f = (1.0 + sqrt(2.0)) * 0.5, c = 2.0 / sqrt(3.0);
+    if (n > 0)
+        PPMD_LAUNCH(ctx, k_acna, div_up(n, ACNA_WARPS), ACNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
+                    ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, f, c, out_idx, label, rcut, ctx->d_status, ctx->d_needed);
+    return check_launch(ctx, "acna");
+}
+
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
                const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
                float *q6, int32_t *nnb) {
@@ -689,6 +915,18 @@ extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const p
     if (want_cna)
         PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, s.perm, nullptr, label));
     return check_launch(ctx, "ppmd_analyze");
+}
+
+extern "C" int ppmd_acna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list,
+                         int8_t *label, double *rcut) {
+    if (!ctx || !box || n < 0 || (n > 0 && (!pos || !label)) || !(r_list > 0))
+        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_acna: bad argument");
+    cudaSetDevice(ctx->device);
+    // asynchronous, as ppmd_analyze
+    Snapshot s;
+    PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_list, snapshot_capacity(n, box, r_list), s));
+    PPMD_TRY(acna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, s.perm, label, rcut));
+    return PPMD_OK;
 }
 
 extern "C" int ppmd_features(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_feat,

@@ -161,3 +161,51 @@ def test_analyze_overflow_is_latched_and_features_retry(L, ctx):
     assert 48 < nbond.max() <= 64  # over the first capacity, within the 64 bonds features take
     fo = oracle.features(pos, L_box, offs, nb, R_BOA, R_CNA)
     assert np.abs(f.cpu().numpy() - fo).max() <= 2e-5
+
+
+R_ACNA = 1.8  # reaches the 14th neighbour at density 0.8442
+
+
+@pytest.mark.parametrize("kind", ["fcc", "bcc", "hcp", "liquid"])
+@pytest.mark.parametrize("sigma", [0.02, 0.07, 0.12])
+def test_acna_bit_exact(L, ctx, kind, sigma):
+    """Adaptive CNA: labels and both FP64 local cutoffs equal the oracle's bit
+    for bit (caller order, shuffled input)."""
+    c = _box(kind, sigma, seed=34)
+    perm = np.random.default_rng(1).permutation(len(c["pos"]))
+    pos, box = c["pos"][perm], c["box"]
+    offs, nb = oracle.neighbours_cells(pos, box, R_ACNA)
+    lab_o, rc_o = oracle.acna(pos, box, offs, nb)
+    lab, rc = L.ppmd_acna(ctx, cu(pos), box, R_ACNA)
+    ctx.sync()
+    assert np.array_equal(lab.cpu().numpy(), lab_o)
+    assert np.array_equal(rc.cpu().numpy(), rc_o)
+
+
+@pytest.mark.parametrize("kind,code", [("fcc", 1), ("hcp", 2), ("bcc", 3)])
+@pytest.mark.parametrize("scale", [0.8, 1.3])
+def test_acna_perfect_lattices_scaled(L, ctx, kind, code, scale):
+    lat = make_lattice(kind, SMALL[kind], 0.8442 / scale ** 3)
+    lab, _ = L.ppmd_acna(ctx, cu(lat.sites()), lat.box, R_ACNA * scale)
+    ctx.sync()
+    assert (lab.cpu().numpy() == code).all()
+
+
+def test_acna_full_size_box_sampled(L, ctx):
+    """A 512,000-atom structure box: labels and cutoffs of a seeded sample
+    against the oracle evaluated on those atoms only."""
+    c = configs.structure_box("bcc", 0.05, seed=30)
+    pos, box = c["pos"], c["box"]
+    lab, rc = L.ppmd_acna(ctx, cu(pos), box, R_ACNA)
+    ctx.sync()
+    sample = np.sort(np.random.default_rng(3).choice(len(pos), 500, replace=False))
+    offs, nb = oracle.neighbours_cells(pos, box, R_ACNA)
+    # rows of the other atoms emptied: the oracle then only works on the sample
+    deg = np.zeros(len(pos), np.int64)
+    deg[sample] = np.diff(offs)[sample]
+    offs_s = np.concatenate([[0], np.cumsum(deg)])
+    nb_s = np.concatenate([nb[offs[i]:offs[i + 1]] for i in sample])
+    lab_o, rc_o = oracle.acna(pos, box, offs_s, nb_s)
+    assert np.array_equal(lab.cpu().numpy()[sample], lab_o[sample])
+    assert np.array_equal(rc.cpu().numpy()[sample], rc_o[sample])
+    assert (lab.cpu().numpy() == 3).mean() > 0.5
