@@ -58,6 +58,10 @@ def _load():
         "ora_cna_label": (None, [i64, P, P, i32, P]),
         "ora_features": (None, [i64, P, P, f64, f64, P, P, P]),
         "ora_acna": (None, [i64, P, P, P, P, P, P]),
+        "ora_philox4x32": (None, [P, P, P]),
+        "ora_andersen_threshold": (C.c_uint64, [f64, f64]),
+        "ora_md_run_otf": (i64, [i64, P, P, P, P, f64, f64, f64, f64, f64, i32, f64, f64, i32, P, C.c_uint64, f64,
+                                 C.c_uint64, i32, f64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -164,6 +168,41 @@ def md_run(pos, vel, box, nsteps, rc=2.5, r_list=2.5, rebuild_every=1, dt=0.005,
     md = _load().ora_md_run(n, _p(pos), _p(vel), _p(F), _p(_f64(box)), eps, sigma, rc, shift, r_list,
                             int(rebuild_every), mass, dt, int(nsteps), _p(en))
     return pos, vel, F, en[:nsteps], md
+
+
+def philox4x32(ctr, key):
+    """Philox4x32-10 of a 4-word counter and a 2-word key (uint32 arrays)."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    _load().ora_philox4x32(_p(c), _p(k), _p(out))
+    return out
+
+
+def andersen_threshold(nu, dt):
+    return int(_load().ora_andersen_threshold(float(nu), float(dt)))
+
+
+def md_run_otf(pos, vel, box, nsteps, rc=2.5, r_list=2.5, rebuild_every=1, dt=0.005, mass=1.0, eps=1.0,
+               sigma=1.0, shift=0.0, thermostat=None, boa=None):
+    """md_run with the on-the-fly analysis run's additions: thermostat =
+    (T, nu, seed) for Andersen collisions, boa = (every, r_boa) for Q4, Q5,
+    Q6.  Returns (pos, vel, F, energies, qrows [nsteps, 3] of means (0 on
+    other steps), qlast [3, n] of the last analysis step, collisions)."""
+    pos, vel = _f64(pos).copy(), _f64(vel).copy()
+    n = len(pos)
+    F = np.zeros((n, 3))
+    en = np.zeros((max(nsteps, 1), 2))
+    qrows = np.zeros((max(nsteps, 1), 3))
+    qlast = np.zeros((3, n))
+    md = np.zeros(1)
+    T, nu, seed = thermostat if thermostat else (0.0, 0.0, 0)
+    thr = andersen_threshold(nu, dt) if thermostat else 0
+    every, r_boa = boa if boa else (0, 0.0)
+    ncoll = _load().ora_md_run_otf(n, _p(pos), _p(vel), _p(F), _p(_f64(box)), eps, sigma, rc, shift, r_list,
+                                   int(rebuild_every), mass, dt, int(nsteps), _p(en), thr, float(T), int(seed),
+                                   int(every), float(r_boa), _p(qrows), _p(qlast), _p(md))
+    return pos, vel, F, en[:nsteps], qrows[:nsteps], qlast, int(ncoll)
 
 
 def boa(pos, box, offs, nbr, r_cut=1.5, l=6, method="direct"):

@@ -273,6 +273,136 @@ static int64_t build_list_cells(int64_t n, const double *pos, const double *L, d
     return tot;
 }
 
+void ora_boa_direct(int64_t n, const double *pos, const double *L, double r_cut, const int64_t *offs,
+                    const int32_t *nbr, int l, double *Q, int32_t *nnb);
+
+/* Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel random numbers:
+ * as easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplications
+ * by 0xD2511F53 and 0xCD9E8D57, the counter words permuted and mixed with
+ * the key, the key advanced by the Weyl constants 0x9E3779B9 and 0xBB67AE85
+ * before every round but the first. */
+static uint32_t mulhilo32(uint32_t a, uint32_t b, uint32_t *lo) {
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
+    *lo = (uint32_t)p;
+    return (uint32_t)(p >> 32);
+}
+
+void ora_philox4x32(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t lo0, lo1;
+        const uint32_t hi0 = mulhilo32(0xD2511F53u, c0, &lo0);
+        const uint32_t hi1 = mulhilo32(0xCD9E8D57u, c2, &lo1);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* Andersen thermostat (the on-the-fly analysis run of Sec. 5.3 couples the
+ * system to one): at the end of step s, atom id collides with the heat bath
+ * with probability p = nu dt, decided by the first word u0 of Philox at
+ * counter (id, s mod 2^32, s / 2^32, 0) and key (seed mod 2^32, seed / 2^32):
+ * u0 < thr = floor(p 2^32) (every atom when p >= 1).  Its new velocity is
+ * drawn from N(0, T/m) per component by the Box-Muller transform of the
+ * uniforms U(u) = (u + 1/2) 2^-32: (v_x, v_y) from (u1, u2), v_z from u3 and
+ * the first word of the draw at counter word 3 = 1. */
+static int andersen_draw(uint64_t seed, int64_t id, int64_t step, uint64_t thr, double sd, double v[3]) {
+    const double two_pi = 6.283185307179586, inv32 = 2.3283064365386962890625e-10;
+    uint32_t ctr[4] = {(uint32_t)id, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t u[4], w[4];
+    ora_philox4x32(ctr, key, u);
+    if ((uint64_t)u[0] >= thr) return 0;
+    ctr[3] = 1u;
+    ora_philox4x32(ctr, key, w);
+    const double U1 = ((double)u[1] + 0.5) * inv32, U2 = ((double)u[2] + 0.5) * inv32;
+    const double U3 = ((double)u[3] + 0.5) * inv32, U4 = ((double)w[0] + 0.5) * inv32;
+    const double r1 = sqrt(-2.0 * log(U1)), t1 = two_pi * U2;
+    const double r2 = sqrt(-2.0 * log(U3)), t2 = two_pi * U4;
+    v[0] = sd * (r1 * cos(t1));
+    v[1] = sd * (r1 * sin(t1));
+    v[2] = sd * (r2 * cos(t2));
+    return 1;
+}
+
+uint64_t ora_andersen_threshold(double nu, double dt) {
+    const double p = nu * dt;
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)floor(p * 4294967296.0);
+}
+
+/* Algorithm 6 as ora_md_run, with the additions of the on-the-fly analysis
+ * run (Sec. 5.3): after the kick of step s (and the energies) the Andersen
+ * thermostat (thr = 0: none; T, seed as above); then, when boa_every > 0
+ * and s % boa_every == 0, Q4, Q5, Q6 of every atom over the current list
+ * with cutoff r_boa (Eqs. (1)-(2)), their means written to
+ * qrows[3 (s - 1) .. +2] and the per-atom values of the last such step to
+ * qlast [3][n] (either may be NULL).  Returns the number of collisions. */
+int64_t ora_md_run_otf(int64_t n, double *pos, double *vel, double *F, const double *L, double eps, double sigma,
+                       double rc, double shift, double r_list, int32_t rebuild_every, double mass, double dt,
+                       int32_t nsteps, double *energies, uint64_t thr, double T, uint64_t seed, int32_t boa_every,
+                       double r_boa, double *qrows, double *qlast, double *maxdisp_out) {
+    int64_t *offs = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int32_t *nbr = NULL;
+    int64_t cap = 0, ncoll = 0;
+    double *ref = (double *)malloc(sizeof(double) * (size_t)(3 * n));
+    double *Q = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    const double sd = sqrt(T / mass);
+    double maxdisp = 0.0;
+    ora_wrap(n, pos, L);
+    build_list_cells(n, pos, L, r_list, offs, &nbr, &cap);
+    memcpy(ref, pos, sizeof(double) * (size_t)(3 * n));
+    double U;
+    ora_lj(n, pos, L, eps, sigma, rc, shift, offs, nbr, F, NULL, &U, NULL);
+    for (int32_t s = 1; s <= nsteps; ++s) {
+        ora_vv(1, n, pos, vel, F, L, mass, dt);
+        double dr[3];
+        for (int64_t i = 0; i < n; ++i) {
+            double d2 = min_image(&pos[3 * i], &ref[3 * i], L, dr);
+            if (d2 > maxdisp * maxdisp) maxdisp = sqrt(d2);
+        }
+        if (rebuild_every > 0 && s % rebuild_every == 0) {
+            build_list_cells(n, pos, L, r_list, offs, &nbr, &cap);
+            memcpy(ref, pos, sizeof(double) * (size_t)(3 * n));
+        }
+        ora_lj(n, pos, L, eps, sigma, rc, shift, offs, nbr, F, NULL, &U, NULL);
+        ora_vv(2, n, pos, vel, F, L, mass, dt);
+        if (energies) {
+            energies[2 * (s - 1)] = ora_kinetic(n, vel, mass);
+            energies[2 * (s - 1) + 1] = U;
+        }
+        if (thr > 0)
+            for (int64_t i = 0; i < n; ++i) ncoll += andersen_draw(seed, i, s, thr, sd, &vel[3 * i]);
+        if (boa_every > 0 && s % boa_every == 0) {
+            for (int l = 4; l <= 6; ++l) {
+                ora_boa_direct(n, pos, L, r_boa, offs, nbr, l, Q, NULL);
+                double sum = 0.0;
+                for (int64_t i = 0; i < n; ++i) sum += Q[i];
+                if (qrows) qrows[3 * (s - 1) + (l - 4)] = sum / (double)(n > 0 ? n : 1);
+                if (qlast) memcpy(&qlast[(l - 4) * n], Q, sizeof(double) * (size_t)n);
+            }
+        }
+    }
+    free(offs);
+    free(nbr);
+    free(ref);
+    free(Q);
+    if (maxdisp_out) *maxdisp_out = maxdisp;
+    return ncoll;
+}
+
 double ora_md_run(int64_t n, double *pos, double *vel, double *F, const double *L, double eps, double sigma,
                   double rc, double shift, double r_list, int32_t rebuild_every, double mass, double dt,
                   int32_t nsteps, double *energies) {

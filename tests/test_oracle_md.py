@@ -206,3 +206,85 @@ def test_md_rebuild_policy_matches_fresh_lists():
     b = oracle.md_run(c["pos"], c["vel"], c["box"], 20, r_list=2.5, rebuild_every=1)
     assert 0.0 < a[4] < 0.3  # largest displacement between rebuilds stayed below the skin
     assert np.abs(a[0] - b[0]).max() < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# On-the-fly analysis run: Philox, Andersen thermostat, Q4/Q5/Q6 rows
+# ---------------------------------------------------------------------------
+def test_philox4x32_known_answers():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.json")) as f:
+        kat = json.load(f)
+    for v in kat["vectors"]:
+        out = oracle.philox4x32([int(x, 16) for x in v["ctr"]], [int(x, 16) for x in v["key"]])
+        assert [f"{int(x):08x}" for x in out] == v["out"]
+
+
+def test_andersen_threshold():
+    assert oracle.andersen_threshold(0.0, 0.005) == 0
+    assert oracle.andersen_threshold(1.0, 0.005) == math.floor(0.005 * 2 ** 32)
+    assert oracle.andersen_threshold(400.0, 0.005) == 2 ** 32
+
+
+def test_otf_run_without_additions_is_the_plain_run():
+    c = configs.lj_solid(n_cells=6)
+    a = oracle.md_run(c["pos"], c["vel"], c["box"], 12, r_list=2.8, rebuild_every=10)
+    b = oracle.md_run_otf(c["pos"], c["vel"], c["box"], 12, r_list=2.8, rebuild_every=10)
+    for x, y in zip(a[:4], b[:4]):
+        assert np.array_equal(x, y)
+    assert b[6] == 0
+
+
+def _draws(seed, ids, step, T):
+    """The thermostat's velocity draw written out with the generator above and
+    numpy's transcendental functions (every atom collides)."""
+    out = np.zeros((len(ids), 3))
+    inv = 2.0 ** -32
+    for k, i in enumerate(ids):
+        c = [i & 0xffffffff, step & 0xffffffff, step >> 32, 0]
+        key = [seed & 0xffffffff, seed >> 32]
+        u = oracle.philox4x32(c, key).astype(np.float64)
+        w = oracle.philox4x32(c[:3] + [1], key).astype(np.float64)
+        r1, t1 = np.sqrt(-2.0 * np.log((u[1] + 0.5) * inv)), 2 * np.pi * (u[2] + 0.5) * inv
+        r2, t2 = np.sqrt(-2.0 * np.log((u[3] + 0.5) * inv)), 2 * np.pi * (w[0] + 0.5) * inv
+        out[k] = np.sqrt(T) * np.array([r1 * np.cos(t1), r1 * np.sin(t1), r2 * np.cos(t2)])
+    return out
+
+
+def test_andersen_every_atom_every_step():
+    """With nu dt >= 1 every atom is redrawn at the end of every step: the
+    final velocities are the last step's draws; their second moment is T."""
+    c = configs.lj_solid(n_cells=6)
+    n = len(c["pos"])
+    T, seed = 0.7, 12345678901
+    _, vel, _, _, _, _, ncoll = oracle.md_run_otf(c["pos"], c["vel"], c["box"], 3, r_list=2.8, rebuild_every=10,
+                                                  thermostat=(T, 1000.0, seed))
+    assert ncoll == 3 * n
+    assert np.allclose(vel, _draws(seed, range(n), 3, T), rtol=0, atol=1e-13)
+    assert abs((vel ** 2).mean() / T - 1.0) < 4 * np.sqrt(2.0 / (3 * n))
+
+
+def test_andersen_collision_rate():
+    c = configs.lj_solid(n_cells=6)
+    n, steps, nu, dt = len(c["pos"]), 20, 4.0, 0.005
+    ncoll = oracle.md_run_otf(c["pos"], c["vel"], c["box"], steps, r_list=2.8, rebuild_every=10,
+                              thermostat=(1.0, nu, 7))[6]
+    p = nu * dt
+    mean, sd = n * steps * p, np.sqrt(n * steps * p * (1 - p))
+    assert abs(ncoll - mean) < 5 * sd
+
+
+def test_otf_q_rows_of_a_crystal_at_rest(golden):
+    """A perfect fcc crystal with zero velocities stays put (zero forces): every
+    analysis row holds the paper's Q4, Q5, Q6 of fcc."""
+    lat = make_lattice("fcc", (6, 6, 6), 0.8442)
+    pos = lat.sites()
+    vel = np.zeros_like(pos)
+    *_, qrows, qlast, _ = oracle.md_run_otf(pos, vel, lat.box, 6, rc=2.5, r_list=2.8, rebuild_every=3,
+                                            boa=(2, 1.5))
+    tab = golden["Q_table"]["fcc"]
+    for s in (1, 3, 5):
+        assert np.allclose(qrows[s], [tab["Q4"], tab["Q5"], tab["Q6"]], atol=5e-4)
+    assert (qrows[[0, 2, 4]] == 0).all()
+    assert np.allclose(qlast.mean(1), qrows[5], rtol=1e-13, atol=1e-15)
