@@ -307,6 +307,30 @@ int ppmd_md_set_state(ppmd_md *md, const double *pos, const double *vel);
  * step's first kick and drift (same arithmetic, so the same bits as separate
  * kernels); a run always ends with full-step velocities. */
 int ppmd_md_run(ppmd_md *md, int32_t nsteps, double *energies, int use_graph);
+/* The on-the-fly analysis run of Sec. 5.3: the time-stepping loop extended
+ * by an Andersen thermostat and by the bond order parameters.
+ *
+ * Andersen thermostat (nu = 0: off): at the end of step s (after the second
+ * kick and the energies) atom id (caller index) collides with probability
+ * p = nu dt: the first word of Philox4x32-10 (Salmon et al., SC'11) at
+ * counter (id, s mod 2^32, s / 2^32, 0) and key (seed mod 2^32, seed / 2^32)
+ * is compared with floor(p 2^32) (every atom when p >= 1); a colliding atom
+ * gets velocities from N(0, T/m) by Box-Muller on U(u) = (u + 1/2) 2^-32:
+ * (v_x, v_y) = sqrt(-2 ln U1) (cos, sin)(2 pi U2), v_z = sqrt(-2 ln U3)
+ * cos(2 pi U4), U1..U3 from words 1..3, U4 from word 0 of the draw at
+ * counter word 3 = 1 (FP64).  Steps count from ppmd_md_set_state. */
+int ppmd_md_set_thermostat(ppmd_md *md, double T, double nu, uint64_t seed);
+/* Q4, Q5, Q6 (Eqs. (1)-(2)) of every atom over the integrator's own list,
+ * bonds r < r_boa (0 < r_boa <= rc), after every step s with
+ * s % every == 0 (every = 0: off), on the positions of step s. */
+int ppmd_md_set_boa(ppmd_md *md, int32_t every, double r_boa);
+/* ppmd_md_run, also writing (mean Q4, mean Q5, mean Q6) over all atoms to
+ * qrows (device [nsteps][3], may be NULL) on analysis steps.  Steps with the
+ * thermostat or an analysis are not fused with the next step's drift. */
+int ppmd_md_run_analysed(ppmd_md *md, int32_t nsteps, double *energies, double *qrows, int use_graph);
+/* Per-atom Q4, Q5, Q6 of the last analysis step (device float [n] each,
+ * caller order; any may be NULL).  PPMD_ERR_INVALID before the first. */
+int ppmd_md_get_q(ppmd_md *md, float *q4, float *q5, float *q6);
 /* Copy positions, velocities and forces back in caller order (device,
  * [n][3] each; any may be NULL). */
 int ppmd_md_get_state(ppmd_md *md, double *pos, double *vel, double *force);

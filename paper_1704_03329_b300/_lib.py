@@ -71,6 +71,10 @@ _SIGS = {
     "ppmd_features": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _D, _P, _P]),
     "ppmd_mlp_forward": (_I, [_P, _P, _P, _I64, _P]),
     "ppmd_acna": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P]),
+    "ppmd_md_set_thermostat": (_I, [_P, _D, _D, C.c_uint64]),
+    "ppmd_md_set_boa": (_I, [_P, C.c_int32, _D]),
+    "ppmd_md_run_analysed": (_I, [_P, C.c_int32, _P, _P, C.c_int]),
+    "ppmd_md_get_q": (_I, [_P, _P, _P, _P]),
     "ppmd_mlp_fit_input_norm": (_I, [_P, _P, _P, _I64]),
     "ppmd_mlp_grad": (_I, [_P, _P, _P, _P, _I64, _P, _P]),
     "ppmd_mlp_adamw": (_I, [_P, _P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
@@ -376,6 +380,21 @@ class MD:
     def run(self, nsteps, energies=None, use_graph=True):
         self.ctx.check(_lib.ppmd_md_run(self.h, int(nsteps), _ptr(energies) if energies is not None else None,
                                         1 if use_graph else 0))
+
+    def set_thermostat(self, T, nu, seed):
+        self.ctx.check(_lib.ppmd_md_set_thermostat(self.h, float(T), float(nu), int(seed)))
+
+    def set_boa(self, every, r_boa=1.5):
+        self.ctx.check(_lib.ppmd_md_set_boa(self.h, int(every), float(r_boa)))
+
+    def run_analysed(self, nsteps, energies=None, qrows=None, use_graph=True):
+        self.ctx.check(_lib.ppmd_md_run_analysed(self.h, int(nsteps), _opt(energies), _opt(qrows),
+                                                 1 if use_graph else 0))
+
+    def get_q(self):
+        q = torch.empty((3, self.n), dtype=torch.float32, device="cuda")
+        self.ctx.check(_lib.ppmd_md_get_q(self.h, _ptr(q[0]), _ptr(q[1]), _ptr(q[2])))
+        return q
 
     def get_state(self, pos=None, vel=None, force=None):
         self.ctx.check(_lib.ppmd_md_get_state(self.h, _ptr(pos) if pos is not None else None,

@@ -32,6 +32,7 @@ namespace ppmd {
 // coefficients), built on the host from the recurrence above in FP64.
 struct YlmCoef {
     float c4[5][3];  // l = 4: degree (4-m)/2 in z^2
+    float c5[6][3];  // l = 5: degree (5-m)/2 in z^2
     float c6[7][4];  // l = 6: degree (6-m)/2 in z^2
 };
 
@@ -50,12 +51,13 @@ static YlmCoef make_coef() {
         for (int q = 1; q <= m; ++q) df *= (2.0 * q - 1.0);
         pm1[0] = (m % 2 ? -1.0 : 1.0) * df;  // Pr_m^m
         auto store = [&](int l, const double *poly) {
-            if (l != 4 && l != 6) return;
+            if (l < 4) return;
             const double sc = sqrt((m ? 2.0 : 1.0) * fact(l - m) / fact(l + m));
             const int par = (l - m) & 1;
             for (int e = 0; e <= (l - m) / 2; ++e) {
                 const float v = (float)(sc * poly[2 * e + par]);
                 if (l == 4) k.c4[m][e] = v;
+                else if (l == 5) k.c5[m][e] = v;
                 else k.c6[m][e] = v;
             }
         };
@@ -81,9 +83,12 @@ static YlmCoef make_coef() {
 }
 
 // Adds the moments of one bond direction (x, y, z) (unit vector):
-// r_lm + i i_lm += sqrt(c_lm) Pr_l^m(z) (x + i y)^m, l = 4, 6, m = 0..l.
-__device__ __forceinline__ void boa_accumulate(const YlmCoef &K, float x, float y, float z, float (&r4)[5],
-                                               float (&i4)[5], float (&r6)[7], float (&i6)[7]) {
+// r_lm + i i_lm += sqrt(c_lm) Pr_l^m(z) (x + i y)^m, l = 4, 6 (and 5 with
+// Q5), m = 0..l.
+template <bool Q5>
+__device__ __forceinline__ void boa_moments(const YlmCoef &K, float x, float y, float z, float (&r4)[5],
+                                            float (&i4)[5], float (&r5)[6], float (&i5)[6], float (&r6)[7],
+                                            float (&i6)[7]) {
     const float z2 = z * z;
     float pr = 1.0f, pi = 0.0f;  // (x + i y)^m
 #pragma unroll
@@ -101,6 +106,14 @@ __device__ __forceinline__ void boa_accumulate(const YlmCoef &K, float x, float 
             r4[m] = fmaf(w, pr, r4[m]);
             if (m > 0) i4[m] = fmaf(w, pi, i4[m]);
         }
+        if (Q5 && m <= 5) {
+            float w = K.c5[m][(5 - m) / 2];
+#pragma unroll
+            for (int e = (5 - m) / 2 - 1; e >= 0; --e) w = fmaf(w, z2, K.c5[m][e]);
+            if ((5 - m) & 1) w *= z;
+            r5[m] = fmaf(w, pr, r5[m]);
+            if (m > 0) i5[m] = fmaf(w, pi, i5[m]);
+        }
         float w6 = K.c6[m][(6 - m) / 2];
 #pragma unroll
         for (int e = (6 - m) / 2 - 1; e >= 0; --e) w6 = fmaf(w6, z2, K.c6[m][e]);
@@ -108,6 +121,12 @@ __device__ __forceinline__ void boa_accumulate(const YlmCoef &K, float x, float 
         r6[m] = fmaf(w6, pr, r6[m]);
         if (m > 0) i6[m] = fmaf(w6, pi, i6[m]);
     }
+}
+
+__device__ __forceinline__ void boa_accumulate(const YlmCoef &K, float x, float y, float z, float (&r4)[5],
+                                               float (&i4)[5], float (&r6)[7], float (&i6)[7]) {
+    float r5[6], i5[6];  // unused
+    boa_moments<false>(K, x, y, z, r4, i4, r5, i5, r6, i6);
 }
 
 // One thread per atom.  Bonds: list entries with r < r_cut (exact decision).
@@ -539,6 +558,98 @@ int acna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, c
         PPMD_LAUNCH(ctx, k_acna, div_up(n, ACNA_WARPS), ACNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
                     ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, f, c, out_idx, label, rcut, ctx->d_status, ctx->d_needed);
     return check_launch(ctx, "acna");
+}
+
+// Q4, Q5, Q6 of the integrator's atoms (the on-the-fly analysis of
+// Sec. 5.3) over its column-major list W[m * ld + i], bonds r < r_cut:
+// per atom into q3 [3][n] at out_idx[i] (the caller's order) and per block
+// the three sums into partials[3 * block + l - 4] (FP64).
+constexpr int BOA_OTF_BLOCK = 256;
+
+__global__ void __launch_bounds__(BOA_OTF_BLOCK) k_boa_otf(int64_t n, const int4 *__restrict__ xq,
+                                                           const double *__restrict__ pos64, SegTable st,
+                                                           const int32_t *__restrict__ W,
+                                                           const int32_t *__restrict__ cnt, int32_t max_nbr,
+                                                           int64_t ld, double rc2, float rc2_lo, float rc2_hi,
+                                                           YlmCoef K, const int32_t *__restrict__ out_idx,
+                                                           float *__restrict__ q3, double *__restrict__ partials) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double qs[3] = {0.0, 0.0, 0.0};
+    if (i < n) {
+        const int4 xi = xq[i];
+        const Seg &S = seg_ref(st, xi.w);
+        float r4[5], i4[5], r5[6], i5[6], r6[7], i6[7];
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+            if (m < 5) r4[m] = i4[m] = 0.0f;
+            if (m < 6) r5[m] = i5[m] = 0.0f;
+            r6[m] = i6[m] = 0.0f;
+        }
+        const int32_t deg = min(cnt[i], max_nbr);
+        int32_t nu = 0;
+        for (int32_t k = 0; k < deg; ++k) {
+            const int32_t j = __ldg(W + (int64_t)k * ld + i);
+            const int4 xj = __ldg(&xq[j]);
+            const float dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj.x, S.sx[0]);
+            const float dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj.y, S.sx[1]);
+            const float dz = fixed_delta((uint32_t)xi.z, (uint32_t)xj.z, S.sx[2]);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool in = r2 < rc2_lo;
+            if (!in && r2 < rc2_hi) {
+                double dr[3];
+                in = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr) < rc2;
+            }
+            if (!in) continue;
+            const float ir = rsqrtf(r2);
+            boa_moments<true>(K, dx * ir, dy * ir, dz * ir, r4, i4, r5, i5, r6, i6);
+            ++nu;
+        }
+        float s4 = 0.0f, s5 = 0.0f, s6 = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 7; ++m) {
+            if (m < 5) s4 = fmaf(r4[m], r4[m], fmaf(i4[m], i4[m], s4));
+            if (m < 6) s5 = fmaf(r5[m], r5[m], fmaf(i5[m], i5[m], s5));
+            s6 = fmaf(r6[m], r6[m], fmaf(i6[m], i6[m], s6));
+        }
+        const float inv = nu > 0 ? 1.0f / (float)nu : 0.0f;
+        const float Q4 = sqrtf(s4) * inv, Q5 = sqrtf(s5) * inv, Q6 = sqrtf(s6) * inv;
+        const int64_t o = out_idx ? out_idx[i] : i;
+        q3[o] = Q4;
+        q3[n + o] = Q5;
+        q3[2 * n + o] = Q6;
+        qs[0] = Q4;
+        qs[1] = Q5;
+        qs[2] = Q6;
+    }
+    __shared__ double sh[3][BOA_OTF_BLOCK / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        double v = qs[l];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[l][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int q = 0; q < BOA_OTF_BLOCK / 32; ++q) v += sh[threadIdx.x][q];
+        partials[3 * blockIdx.x + threadIdx.x] = v;
+    }
+}
+
+int64_t boa_otf_blocks(int64_t n) { return div_up(n, BOA_OTF_BLOCK); }
+
+int boa_otf_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *W,
+                   const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx,
+                   float *q3, double *partials) {
+    static const YlmCoef K = make_coef();
+    float lo, hi;
+    cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
+    if (n > 0)
+        PPMD_LAUNCH(ctx, k_boa_otf, boa_otf_blocks(n), BOA_OTF_BLOCK, 0, n, xq, pos64, st, W, cnt, max_nbr, ld,
+                    r_cut * r_cut, lo, hi, K, out_idx, q3, partials);
+    return check_launch(ctx, "boa_otf");
 }
 
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,

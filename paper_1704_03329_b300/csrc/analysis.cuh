@@ -31,6 +31,11 @@ int32_t snapshot_capacity(int64_t n, const ppmd_box *box, double r_list);
 // else the status.
 constexpr int PIPELINE_RETRY = 1;
 int end_pipeline(ppmd_ctx *ctx, int attempt, int32_t &max_nbr, int32_t *aux = nullptr);
+// Q4, Q5, Q6 over the integrator's column-major list (see analysis.cu).
+int boa_otf_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *W,
+                   const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx,
+                   float *q3, double *partials);
+int64_t boa_otf_blocks(int64_t n);
 int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int32_t max_nbr,
                     Snapshot &s);
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <math.h>
 
+#include "analysis.cuh"
 #include "cells.cuh"
 #include "lj.cuh"
 #include "neighbours.cuh"
@@ -56,6 +57,15 @@ struct ppmd_md {
     cudaGraphExec_t exec = nullptr;
     int32_t graph_steps = 0;
     int64_t graph_kernels = 0;
+    // on-the-fly analysis run (Sec. 5.3): Andersen thermostat and Q4/Q5/Q6
+    uint64_t thermo_thr = 0, thermo_seed = 0;
+    double thermo_sd = 0.0, Lmax = 0.0;
+    int32_t boa_every = 0;
+    double r_boa = 0.0;
+    float *q3 = nullptr;  // [3][n] of the last analysis step, caller order
+    double *part_q = nullptr, *red_q = nullptr, *qbuf = nullptr;
+    int64_t *d_base = nullptr;  // step number before a replayed unit
+    bool have_q = false;
     std::vector<void *> allocs;
 };
 
@@ -109,6 +119,60 @@ __global__ void k_gather_i32(int64_t n, const int32_t *perm, const int32_t *in, 
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) out[k] = in[perm[k]];
 }
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+// products by 0xD2511F53 and 0xCD9E8D57 with the counter words permuted
+// and mixed with the key; the key advances by 0x9E3779B9, 0xBB67AE85 before
+// every round but the first.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// Andersen collisions at the end of step (*base + step_off) (base may be
+// null): atom i (caller index orig[i]) collides when the first Philox word
+// at counter (orig[i], step mod 2^32, step / 2^32, 0), key (seed mod 2^32,
+// seed / 2^32) is below thr; its velocity is then drawn from N(0, sd^2)
+// per component by Box-Muller on U(u) = (u + 1/2) 2^-32: (v_x, v_y) from
+// words 1, 2, v_z from word 3 and word 0 of the draw at counter word 3 = 1.
+__global__ void k_andersen(int64_t n, double *__restrict__ vel, const int32_t *__restrict__ orig, uint64_t seed,
+                           uint64_t thr, double sd, const int64_t *__restrict__ base, int64_t step_off) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t step = (base ? *base : 0) + step_off;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    uint32_t u[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
+    philox4x32_10(u, k0, k1);
+    if ((uint64_t)u[0] >= thr) return;
+    uint32_t w[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 1u};
+    philox4x32_10(w, k0, k1);
+    const double two_pi = 6.283185307179586, inv32 = 2.3283064365386962890625e-10;
+    const double U1 = __dmul_rn(__dadd_rn((double)u[1], 0.5), inv32), U2 = __dmul_rn(__dadd_rn((double)u[2], 0.5), inv32);
+    const double U3 = __dmul_rn(__dadd_rn((double)u[3], 0.5), inv32), U4 = __dmul_rn(__dadd_rn((double)w[0], 0.5), inv32);
+    const double r1 = sqrt(__dmul_rn(-2.0, log(U1))), t1 = __dmul_rn(two_pi, U2);
+    const double r2 = sqrt(__dmul_rn(-2.0, log(U3))), t2 = __dmul_rn(two_pi, U4);
+    vel[3 * i] = __dmul_rn(sd, __dmul_rn(r1, cos(t1)));
+    vel[3 * i + 1] = __dmul_rn(sd, __dmul_rn(r1, sin(t1)));
+    vel[3 * i + 2] = __dmul_rn(sd, __dmul_rn(r2, cos(t2)));
+}
+
+__global__ void k_q_row(const double *red, double n, double *row) {
+    if (threadIdx.x < 3) row[threadIdx.x] = __ddiv_rn(red[threadIdx.x], n);
+}
+
+__global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
 
 __global__ void k_energy_row(const double *red, double *row) {
     // red = (potential U, virial W, kinetic K)
@@ -165,13 +229,19 @@ int forces(ppmd_md *m, bool energy, bool kick, bool drift = false) {
 }
 
 // One step of Algorithm 6.  erow: device row receiving (KE, PE) on energy
-// steps.  The step's kick and drift are skipped when the previous pair loop
-// already made them; with fuse_next (FP32) this step's pair loop makes the
-// next step's.
-int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next) {
+// steps; qrow: (mean Q4, Q5, Q6) on analysis steps.  The step's kick and
+// drift are skipped when the previous pair loop already made them; with
+// fuse_next (FP32) this step's pair loop makes the next step's, unless the
+// thermostat or the analysis needs the step to end first.  base: device step
+// number to add to s (graph capture), else null.
+int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow = nullptr,
+             const int64_t *base = nullptr) {
     ppmd_ctx *ctx = m->ctx;
     const bool f32 = m->p.prec == PPMD_FP32;
     const bool energy = m->p.energy_every > 0 && (s % m->p.energy_every) == 0 && erow;
+    const bool thermo = m->thermo_thr > 0;
+    const bool analyse = m->boa_every > 0 && (s % m->boa_every) == 0;
+    if (thermo || analyse) fuse_next = false;
     if (!m->half_kicked)
         PPMD_TRY(md_kick_drift2(ctx, m->n, m->pos, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->xq,
                                 m->xq_ref, m->st, m->h, m->p.dt, m->max_disp_bits));
@@ -183,6 +253,16 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next) {
     if (energy) {
         PPMD_TRY(reduce_partials(ctx, m->part_f, lj_columns_blocks(m->n), 3, m->red));
         PPMD_LAUNCH(ctx, k_energy_row, 1, 1, 0, m->red, erow);
+    }
+    if (thermo && m->n > 0)
+        PPMD_LAUNCH(ctx, k_andersen, div_up(m->n, 256), 256, 0, m->n, m->vel, m->orig, m->thermo_seed, m->thermo_thr,
+                    m->thermo_sd, base, s);
+    if (analyse) {
+        PPMD_TRY(boa_otf_launch(ctx, m->n, m->xq, m->pos, m->st, m->W, m->cnt, m->p.max_nbr, m->ld, m->r_boa, m->Lmax,
+                                m->orig, m->q3, m->part_q));
+        PPMD_TRY(reduce_partials(ctx, m->part_q, boa_otf_blocks(m->n), 3, m->red_q));
+        if (qrow) PPMD_LAUNCH(ctx, k_q_row, 1, 32, 0, m->red_q, (double)(m->n > 0 ? m->n : 1), qrow);
+        m->have_q = true;
     }
     return check_launch(ctx, "one_step");
 }
@@ -239,6 +319,7 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     }
     m->ncell = cell0;
     m->skin_half = 0.5 * min_skin;
+    m->Lmax = Lmax;
     m->c = make_ljconst(p.lj, Lmax);
     const int64_t n = m->n;
     int rc = PPMD_OK;
@@ -293,6 +374,11 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->red, 4);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->ebuf, 2 * 1024);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->q3, 3 * n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->part_q, 3 * boa_otf_blocks(n) + 3);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->red_q, 3);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->qbuf, 3 * 1024);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->d_base, 1);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->max_disp_bits, 1);
     if (rc == PPMD_OK) rc = cuda_check(ctx, cudaMemset(m->max_disp_bits, 0, sizeof(unsigned int)), "memset");
     if (rc != PPMD_OK) {
@@ -338,14 +424,19 @@ extern "C" int ppmd_md_set_state(ppmd_md *m, const double *pos, const double *ve
 }
 
 extern "C" int ppmd_md_run(ppmd_md *m, int32_t nsteps, double *energies, int use_graph) {
+    return ppmd_md_run_analysed(m, nsteps, energies, nullptr, use_graph);
+}
+
+extern "C" int ppmd_md_run_analysed(ppmd_md *m, int32_t nsteps, double *energies, double *qrows, int use_graph) {
     if (!m || nsteps < 0) return PPMD_ERR_INVALID;
     ppmd_ctx *ctx = m->ctx;
     if (!m->ready) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_run: state not set");
     cudaSetDevice(ctx->device);
     const int32_t P = m->p.rebuild_every;
     const int32_t E = m->p.energy_every;
+    const int32_t B = m->boa_every;
     int32_t unit = P * std::max(1, 10 / P);
-    const bool graph_ok = use_graph && unit <= 1024 && (E == 0 || unit % E == 0);
+    const bool graph_ok = use_graph && unit <= 1024 && (E == 0 || unit % E == 0) && (B == 0 || unit % B == 0);
     int32_t done = 0;
     while (done < nsteps) {
         const int64_t s0 = m->step;
@@ -363,7 +454,7 @@ extern "C" int ppmd_md_run(ppmd_md *m, int32_t nsteps, double *energies, int use
                 // a unit starts and ends with full-step velocities; inside it
                 // each pair loop makes the next step's kick and drift
                 for (int32_t k = 1; rc == PPMD_OK && k <= unit; ++k)
-                    rc = one_step(m, k, m->ebuf + 2 * (k - 1), k < unit);
+                    rc = one_step(m, k, m->ebuf + 2 * (k - 1), k < unit, m->qbuf + 3 * (k - 1), m->d_base);
                 cudaError_t e = cudaStreamEndCapture(m->cap_stream, &g);
                 ctx->stream = user;
                 if (rc != PPMD_OK) {
@@ -378,8 +469,16 @@ extern "C" int ppmd_md_run(ppmd_md *m, int32_t nsteps, double *energies, int use
                 m->graph_kernels = ctx->launches - k0;
                 ctx->launches = k0;
             }
+            PPMD_LAUNCH(ctx, k_set_i64, 1, 1, 0, m->d_base, s0);  // step numbers of the replayed unit
             PPMD_TRY(cuda_check(ctx, cudaGraphLaunch(m->exec, ctx->stream), "graph launch"));
             ctx->launches += m->graph_kernels;
+            if (qrows && B > 0) {
+                for (int32_t k = 1; k <= unit; ++k)
+                    if ((k % B) == 0)
+                        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(qrows + 3 * (done + k - 1), m->qbuf + 3 * (k - 1),
+                                                                 3 * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream),
+                                            "copy"));
+            }
             if (energies && E > 0) {
                 for (int32_t k = 1; k <= unit; ++k)
                     if ((k % E) == 0)
@@ -395,7 +494,8 @@ extern "C" int ppmd_md_run(ppmd_md *m, int32_t nsteps, double *energies, int use
             // fuse the next step's kick and drift unless this is the run's
             // last step or the next one is a graph replay
             const bool next_graph = graph_ok && s % unit == 0 && nsteps - (done + 1) >= unit;
-            PPMD_TRY(one_step(m, s, energies ? energies + 2 * done : nullptr, done + 1 < nsteps && !next_graph));
+            PPMD_TRY(one_step(m, s, energies ? energies + 2 * done : nullptr, done + 1 < nsteps && !next_graph,
+                              qrows ? qrows + 3 * done : nullptr, nullptr));
             if (s % P == 0) m->rebuilds += 1;
             m->step = s;
             done += 1;
@@ -451,6 +551,54 @@ __global__ void k_list_stats(const int32_t *cnt, int64_t n, unsigned long long *
     }
 }
 }  // namespace
+
+namespace {
+void drop_graph(ppmd_md *m) {
+    if (m->exec) {
+        cudaStreamSynchronize(m->ctx->stream);
+        cudaGraphExecDestroy(m->exec);
+        m->exec = nullptr;
+    }
+}
+}  // namespace
+
+extern "C" int ppmd_md_set_thermostat(ppmd_md *m, double T, double nu, uint64_t seed) {
+    if (!m) return PPMD_ERR_INVALID;
+    if (!(T >= 0.0) || !(nu >= 0.0) || !isfinite(T) || !isfinite(nu))
+        return set_error(m->ctx, PPMD_ERR_INVALID, "ppmd_md_set_thermostat: bad temperature or rate");
+    cudaSetDevice(m->ctx->device);
+    drop_graph(m);
+    const double p = nu * m->p.dt;
+    m->thermo_thr = !(p > 0.0) ? 0 : (p >= 1.0 ? ((uint64_t)1 << 32) : (uint64_t)floor(p * 4294967296.0));
+    m->thermo_sd = sqrt(T / m->p.mass);
+    m->thermo_seed = seed;
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_set_boa(ppmd_md *m, int32_t every, double r_boa) {
+    if (!m) return PPMD_ERR_INVALID;
+    if (every < 0 || (every > 0 && !(r_boa > 0.0 && r_boa <= m->p.lj.rc)))
+        return set_error(m->ctx, PPMD_ERR_INVALID, "ppmd_md_set_boa: need every >= 0 and 0 < r_boa <= rc");
+    cudaSetDevice(m->ctx->device);
+    drop_graph(m);
+    m->boa_every = every;
+    m->r_boa = r_boa;
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_get_q(ppmd_md *m, float *q4, float *q5, float *q6) {
+    if (!m) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    if (!m->have_q) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_get_q: no analysis step yet");
+    cudaSetDevice(ctx->device);
+    float *out[3] = {q4, q5, q6};
+    for (int l = 0; l < 3; ++l)
+        if (out[l])
+            PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(out[l], m->q3 + (size_t)l * m->n, sizeof(float) * (size_t)m->n,
+                                                     cudaMemcpyDeviceToDevice, ctx->stream),
+                                "copy"));
+    return PPMD_OK;
+}
 
 extern "C" int ppmd_md_forces(ppmd_md *m) {
     if (!m || !m->ready) return PPMD_ERR_INVALID;

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 import oracle
-from synth import configs
+from synth import configs, make_lattice
 from synth.configs import random_box
 
 pytestmark = pytest.mark.gpu
@@ -286,3 +286,64 @@ def test_md_fused_kick_drift_is_bit_identical(L, ctx):
         got = state(runs, g)
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), (runs, g)
+
+
+def _otf_md(L, ctx, c, nsteps, use_graph, thermo, boa):
+    n = len(c["pos"])
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=c["r_list"], rebuild_every=c["rebuild_every"], max_nbr=128,
+              prec=L.FP32, energy_every=5)
+    if thermo:
+        md.set_thermostat(*thermo)
+    if boa:
+        md.set_boa(*boa)
+    md.set_state(cu(c["pos"]), cu(c["vel"]))
+    en = torch.zeros((nsteps, 2), dtype=torch.float64, device="cuda")
+    q = torch.zeros((nsteps, 3), dtype=torch.float64, device="cuda")
+    md.run_analysed(nsteps, en, q, use_graph=use_graph)
+    p = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    v = torch.empty_like(p)
+    md.get_state(p, v)
+    ql = md.get_q().cpu().numpy() if boa else None
+    return p.cpu().numpy(), v.cpu().numpy(), en.cpu().numpy(), q.cpu().numpy(), ql
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_otf_run_matches_oracle(L, ctx, use_graph):
+    """The on-the-fly analysis run: Andersen collisions (p = 0.05 per step,
+    decided by integer counters, so the same atoms collide on both sides)
+    and Q4/Q5/Q6 every second step, 20 steps of the fcc solid, against the
+    FP64 oracle with the FP32-force tolerances."""
+    c = configs.lj_solid(n_cells=8)
+    thermo, boa = (0.5, 10.0, 987654321), (2, 1.5)
+    po, vo, Fo, eno, qo, qlo, ncoll = oracle.md_run_otf(c["pos"], c["vel"], c["box"], 20, r_list=2.8,
+                                                        rebuild_every=10, thermostat=thermo, boa=boa)
+    assert ncoll > 0
+    p, v, en, q, ql = _otf_md(L, ctx, c, 20, use_graph, thermo, boa)
+    assert _pos_err(p, po, c["box"]) / c["box"][0] <= 1e-8
+    # velocity change a 1e-5 rms|F| force error makes over 20 steps (twice)
+    assert np.abs(v - vo).max() <= 2 * 20 * 0.005 * 1e-5 * np.sqrt((Fo ** 2).sum(1).mean())
+    rows = np.arange(1, 20, 2)
+    assert np.abs(q[rows] - qo[rows]).max() <= 1e-5
+    assert (q[np.arange(0, 20, 2)] == 0).all()
+    assert np.abs(ql - qlo).max() <= 1e-5
+    assert np.abs(en[4::5, 0] - eno[4::5, 0]).max() <= 1e-6 * np.abs(eno[4::5, 0]).max()
+
+
+def test_otf_graph_and_single_steps_are_bit_identical(L, ctx):
+    """Graph replays take the thermostat's step numbers from the device: the
+    same bits as single steps."""
+    c = configs.lj_solid(n_cells=8)
+    a = _otf_md(L, ctx, c, 23, True, (0.5, 10.0, 5), (1, 1.5))
+    b = _otf_md(L, ctx, c, 23, False, (0.5, 10.0, 5), (1, 1.5))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_otf_q_rows_of_a_crystal_at_rest(L, ctx, golden):
+    lat = make_lattice("fcc", (8, 8, 8), 0.8442)
+    c = {"pos": lat.sites(), "vel": np.zeros((len(lat.sites()), 3)), "box": lat.box, "r_list": 2.8,
+         "rebuild_every": 10}
+    _, _, _, q, ql = _otf_md(L, ctx, c, 10, True, None, (5, 1.5))
+    tab = golden["Q_table"]["fcc"]
+    assert np.allclose(q[[4, 9]], [tab["Q4"], tab["Q5"], tab["Q6"]], atol=5e-4)
+    assert np.allclose(ql.mean(1), q[9], atol=1e-6)
