@@ -37,7 +37,8 @@ def parse():
     ap.add_argument("--cpu-cells", type=int, default=44, help="fcc cells per edge of the CPU-baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=200)
-    ap.add_argument("--suites", default="replicas,analysis,classifier",
+    ap.add_argument("--otf-steps", type=int, default=540)
+    ap.add_argument("--suites", default="replicas,analysis,classifier,otf",
                     help="extra workloads reported beside the main line (comma list, or 'none')")
     ap.add_argument("--replica-steps", type=int, default=500)
     ap.add_argument("--epochs", type=int, default=20)
@@ -301,7 +302,8 @@ def run_ours(args):
     if world == 1:
         suites = [x for x in args.suites.split(",") if x and x != "none"]
         for name in suites:
-            fn = {"replicas": suite_replicas, "analysis": suite_analysis, "classifier": suite_classifier}[name]
+            fn = {"replicas": suite_replicas, "analysis": suite_analysis, "classifier": suite_classifier,
+                  "otf": suite_otf}[name]
             try:
                 k0 = ctx.kernel_count()
                 line[name] = fn(args, L, ctx, stream)
@@ -345,6 +347,37 @@ def suite_replicas(args, L, ctx, stream):
                         f"jittered sc, rc 2.5, list min(2.8, L/3), rebuild every 10, dt 0.005",
             "metric": "aggregate atom-steps/s", "value": n * K / t, "unit": UNIT, "steps": K, "atoms": n,
             "ms_per_step": t / K * 1e3}
+
+
+def suite_otf(args, L, ctx, stream):
+    """The on-the-fly analysis run (Sec. 5.3) at the size of its weak-scaling
+    table: 524,288 atoms, rho 0.8442, rc 3.0, list 3.3, rebuild every 18;
+    Andersen thermostat (T 0.1, nu 1) and Q4/Q5/Q6 (cutoff 1.5) on every step,
+    against the same run without them."""
+    import torch
+    from synth import configs
+    c = configs.otf_box(seed=6)
+    n = len(c["pos"])
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=3.3, rc=3.0, rebuild_every=18, max_nbr=192, prec=L.FP32,
+              energy_every=18)
+    pos, vel = torch.from_numpy(c["pos"]).cuda(), torch.from_numpy(c["vel"]).cuda()
+    K = max(18, (args.otf_steps // 18) * 18)
+    md.set_state(pos, vel)
+    md.run(18)
+    t_plain, _ = _timed(stream, lambda: md.run(K))
+    md.set_thermostat(0.1, 1.0, 20170410)
+    md.set_boa(1, 1.5)
+    q = torch.zeros((K, 3), dtype=torch.float64, device="cuda")
+    md.run_analysed(18, None, q[:18])
+    k0 = ctx.kernel_count()
+    t_otf, _ = _timed(stream, lambda: md.run_analysed(K, None, q))
+    launches = ctx.kernel_count() - k0
+    qm = q.cpu().numpy()
+    return {"workload": f"{n} atoms on a jittered simple-cubic lattice, rho 0.8442, rc 3.0, list 3.3, rebuild "
+                        "every 18, dt 0.005; Andersen T 0.1 nu 1 and Q4/Q5/Q6 (cutoff 1.5) every step",
+            "metric": "atom-steps/s with on-the-fly analysis", "value": n * K / t_otf, "unit": UNIT, "steps": K,
+            "atoms": n, "plain_atom_steps_per_s": n * K / t_plain, "analysis_overhead": t_otf / t_plain - 1.0,
+            "mean_q_first": qm[0].tolist(), "mean_q_last": qm[-1].tolist(), "gpu_launches": launches}
 
 
 def suite_analysis(args, L, ctx, stream):

@@ -564,7 +564,7 @@ int acna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, c
 // Sec. 5.3) over its column-major list W[m * ld + i], bonds r < r_cut:
 // per atom into q3 [3][n] at out_idx[i] (the caller's order) and per block
 // the three sums into partials[3 * block + l - 4] (FP64).
-constexpr int BOA_OTF_BLOCK = 256;
+constexpr int BOA_OTF_BLOCK = 128;
 
 __global__ void __launch_bounds__(BOA_OTF_BLOCK) k_boa_otf(int64_t n, const int4 *__restrict__ xq,
                                                            const double *__restrict__ pos64, SegTable st,
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(BOA_OTF_BLOCK) k_boa_otf(int64_t n, const int4
                                                            YlmCoef K, const int32_t *__restrict__ out_idx,
                                                            float *__restrict__ q3, double *__restrict__ partials) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double qs[3] = {0.0, 0.0, 0.0};
+    float qs[3] = {0.0f, 0.0f, 0.0f};
     if (i < n) {
         const int4 xi = xq[i];
         const Seg &S = seg_ref(st, xi.w);
@@ -587,22 +587,32 @@ __global__ void __launch_bounds__(BOA_OTF_BLOCK) k_boa_otf(int64_t n, const int4
         }
         const int32_t deg = min(cnt[i], max_nbr);
         int32_t nu = 0;
-        for (int32_t k = 0; k < deg; ++k) {
-            const int32_t j = __ldg(W + (int64_t)k * ld + i);
-            const int4 xj = __ldg(&xq[j]);
-            const float dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj.x, S.sx[0]);
-            const float dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj.y, S.sx[1]);
-            const float dz = fixed_delta((uint32_t)xi.z, (uint32_t)xj.z, S.sx[2]);
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            bool in = r2 < rc2_lo;
-            if (!in && r2 < rc2_hi) {
-                double dr[3];
-                in = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr) < rc2;
+        // four entries per pass: their list words and positions are loaded
+        // together, so four loads are in flight per thread
+        for (int32_t k0 = 0; k0 < deg; k0 += 4) {
+            int32_t jv[4];
+            int4 xv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) jv[q] = k0 + q < deg ? __ldg(W + (int64_t)(k0 + q) * ld + i) : (int32_t)i;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xv[q] = __ldg(&xq[jv[q]]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (k0 + q >= deg) break;
+                const float dx = fixed_delta((uint32_t)xi.x, (uint32_t)xv[q].x, S.sx[0]);
+                const float dy = fixed_delta((uint32_t)xi.y, (uint32_t)xv[q].y, S.sx[1]);
+                const float dz = fixed_delta((uint32_t)xi.z, (uint32_t)xv[q].z, S.sx[2]);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                bool in = r2 < rc2_lo;
+                if (!in && r2 < rc2_hi) {
+                    double dr[3];
+                    in = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)jv[q], S, dr) < rc2;
+                }
+                if (!in) continue;
+                const float ir = rsqrtf(r2);
+                boa_moments<true>(K, dx * ir, dy * ir, dz * ir, r4, i4, r5, i5, r6, i6);
+                ++nu;
             }
-            if (!in) continue;
-            const float ir = rsqrtf(r2);
-            boa_moments<true>(K, dx * ir, dy * ir, dz * ir, r4, i4, r5, i5, r6, i6);
-            ++nu;
         }
         float s4 = 0.0f, s5 = 0.0f, s6 = 0.0f;
 #pragma unroll
@@ -621,14 +631,16 @@ __global__ void __launch_bounds__(BOA_OTF_BLOCK) k_boa_otf(int64_t n, const int4
         qs[1] = Q5;
         qs[2] = Q6;
     }
+    // warp sums in FP32 (32 values of order one), block and grid sums in
+    // FP64 (FP64 arithmetic on every lane is slow on this part)
     __shared__ double sh[3][BOA_OTF_BLOCK / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        double v = qs[l];
+        float v = qs[l];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[l][w] = v;
+        if (lane == 0) sh[l][w] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < 3) {

@@ -66,6 +66,11 @@ struct ppmd_md {
     double *part_q = nullptr, *red_q = nullptr, *qbuf = nullptr;
     int64_t *d_base = nullptr;  // step number before a replayed unit
     bool have_q = false;
+    // short list for the analysis: pairs of W closer than r_boa + skin at
+    // the last build (they stay a superset of the bonds until the next one)
+    int32_t *W2 = nullptr, *cnt2 = nullptr;
+    int32_t max2 = 64;
+    int32_t *coll_list = nullptr, *coll_count = nullptr;  // this step's colliding atoms
     std::vector<void *> allocs;
 };
 
@@ -147,25 +152,99 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 // seed / 2^32) is below thr; its velocity is then drawn from N(0, sd^2)
 // per component by Box-Muller on U(u) = (u + 1/2) 2^-32: (v_x, v_y) from
 // words 1, 2, v_z from word 3 and word 0 of the draw at counter word 3 = 1.
-__global__ void k_andersen(int64_t n, double *__restrict__ vel, const int32_t *__restrict__ orig, uint64_t seed,
-                           uint64_t thr, double sd, const int64_t *__restrict__ base, int64_t step_off) {
+// The decision (integer work for every atom) and the draw (FP64
+// transcendentals, slow on this part) run as two kernels: the colliding
+// atoms are first collected in a list so that the draw runs on full warps.
+__global__ void k_andersen_decide(int64_t n, const int32_t *__restrict__ orig, uint64_t seed, uint64_t thr,
+                                  const int64_t *__restrict__ base, int64_t step_off, int32_t *__restrict__ list,
+                                  int32_t *__restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool hit = false;
+    if (i < n) {
+        const int64_t step = (base ? *base : 0) + step_off;
+        uint32_t u[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
+        philox4x32_10(u, (uint32_t)seed, (uint32_t)(seed >> 32));
+        hit = (uint64_t)u[0] < thr;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, hit);
+    if (!b) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(b) - 1;
+    int32_t at = 0;
+    if (lane == leader) at = atomicAdd(count, __popc(b));
+    at = __shfl_sync(0xffffffffu, at, leader);
+    if (hit) list[at + __popc(b & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+__global__ void k_andersen(const int32_t *__restrict__ list, const int32_t *__restrict__ count,
+                           double *__restrict__ vel, const int32_t *__restrict__ orig, uint64_t seed, double sd,
+                           const int64_t *__restrict__ base, int64_t step_off) {
+    const int32_t m = *count;
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const int64_t i = list[t];
+        const int64_t step = (base ? *base : 0) + step_off;
+        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+        uint32_t u[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
+        philox4x32_10(u, k0, k1);
+        uint32_t w[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 1u};
+        philox4x32_10(w, k0, k1);
+        const double two_pi = 6.283185307179586, inv32 = 2.3283064365386962890625e-10;
+        const double U1 = __dmul_rn(__dadd_rn((double)u[1], 0.5), inv32);
+        const double U2 = __dmul_rn(__dadd_rn((double)u[2], 0.5), inv32);
+        const double U3 = __dmul_rn(__dadd_rn((double)u[3], 0.5), inv32);
+        const double U4 = __dmul_rn(__dadd_rn((double)w[0], 0.5), inv32);
+        const double r1 = sqrt(__dmul_rn(-2.0, log(U1))), t1 = __dmul_rn(two_pi, U2);
+        const double r2 = sqrt(__dmul_rn(-2.0, log(U3))), t2 = __dmul_rn(two_pi, U4);
+        vel[3 * i] = __dmul_rn(sd, __dmul_rn(r1, cos(t1)));
+        vel[3 * i + 1] = __dmul_rn(sd, __dmul_rn(r1, sin(t1)));
+        vel[3 * i + 2] = __dmul_rn(sd, __dmul_rn(r2, cos(t2)));
+    }
+}
+
+// Entries of the list W (column-major) closer than r_short (FP32 test
+// with a small margin: extra entries are harmless, the analysis decides
+// exactly) into W2 (column-major, capacity max2; more: PPMD_ERR_CAPACITY).
+__global__ void k_short_list(int64_t n, const int4 *__restrict__ xq, SegTable st, const int32_t *__restrict__ W,
+                             const int32_t *__restrict__ cnt, int32_t max_nbr, int64_t ld, float r2_short,
+                             int32_t *__restrict__ W2, int32_t *__restrict__ cnt2, int32_t max2, int32_t *status,
+                             unsigned long long *needed) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int64_t step = (base ? *base : 0) + step_off;
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    uint32_t u[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
-    philox4x32_10(u, k0, k1);
-    if ((uint64_t)u[0] >= thr) return;
-    uint32_t w[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 1u};
-    philox4x32_10(w, k0, k1);
-    const double two_pi = 6.283185307179586, inv32 = 2.3283064365386962890625e-10;
-    const double U1 = __dmul_rn(__dadd_rn((double)u[1], 0.5), inv32), U2 = __dmul_rn(__dadd_rn((double)u[2], 0.5), inv32);
-    const double U3 = __dmul_rn(__dadd_rn((double)u[3], 0.5), inv32), U4 = __dmul_rn(__dadd_rn((double)w[0], 0.5), inv32);
-    const double r1 = sqrt(__dmul_rn(-2.0, log(U1))), t1 = __dmul_rn(two_pi, U2);
-    const double r2 = sqrt(__dmul_rn(-2.0, log(U3))), t2 = __dmul_rn(two_pi, U4);
-    vel[3 * i] = __dmul_rn(sd, __dmul_rn(r1, cos(t1)));
-    vel[3 * i + 1] = __dmul_rn(sd, __dmul_rn(r1, sin(t1)));
-    vel[3 * i + 2] = __dmul_rn(sd, __dmul_rn(r2, cos(t2)));
+    const int4 xi = xq[i];
+    const Seg &S = seg_ref(st, xi.w);
+    const int32_t deg = min(cnt[i], max_nbr);
+    int32_t c = 0;
+    for (int32_t k0 = 0; k0 < deg; k0 += 4) {  // four loads in flight per thread
+        int32_t jv[4];
+        int4 xv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) jv[q] = k0 + q < deg ? __ldg(W + (int64_t)(k0 + q) * ld + i) : (int32_t)i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xv[q] = __ldg(&xq[jv[q]]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (k0 + q >= deg) break;
+            const float dx = fixed_delta((uint32_t)xi.x, (uint32_t)xv[q].x, S.sx[0]);
+            const float dy = fixed_delta((uint32_t)xi.y, (uint32_t)xv[q].y, S.sx[1]);
+            const float dz = fixed_delta((uint32_t)xi.z, (uint32_t)xv[q].z, S.sx[2]);
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < r2_short) {
+                if (c < max2) W2[(int64_t)c * ld + i] = jv[q];
+                ++c;
+            }
+        }
+    }
+    cnt2[i] = c;
+    if (c > max2) {
+        latch_status(status, PPMD_ERR_CAPACITY);
+        latch_needed(needed, (unsigned long long)c);
+    }
+}
+
+int build_short_list(ppmd_md *m) {
+    if (m->boa_every <= 0 || m->n <= 0) return PPMD_OK;
+    const double rs = (m->r_boa + (m->p.r_list - m->p.lj.rc)) * (1.0 + 1e-5);
+    PPMD_LAUNCH(m->ctx, k_short_list, div_up(m->n, 256), 256, 0, m->n, m->xq, m->st, m->W, m->cnt, m->p.max_nbr,
+                m->ld, (float)(rs * rs), m->W2, m->cnt2, m->max2, m->ctx->d_status, m->ctx->d_needed);
+    return check_launch(m->ctx, "short list");
 }
 
 __global__ void k_q_row(const double *red, double n, double *row) {
@@ -202,7 +281,7 @@ int rebuild(ppmd_md *m) {
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, BrickShape{1, 1, 1}, m->xq, m->pos, m->st, m->cell_start,
                                m->W, m->ld, m->cnt, m->p.max_nbr, m->stage_cap));
-    return PPMD_OK;
+    return build_short_list(m);
 }
 
 // Pair loop; with kick = true also the second kick of the step, with
@@ -254,11 +333,15 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow =
         PPMD_TRY(reduce_partials(ctx, m->part_f, lj_columns_blocks(m->n), 3, m->red));
         PPMD_LAUNCH(ctx, k_energy_row, 1, 1, 0, m->red, erow);
     }
-    if (thermo && m->n > 0)
-        PPMD_LAUNCH(ctx, k_andersen, div_up(m->n, 256), 256, 0, m->n, m->vel, m->orig, m->thermo_seed, m->thermo_thr,
-                    m->thermo_sd, base, s);
+    if (thermo && m->n > 0) {
+        PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(m->coll_count, 0, sizeof(int32_t), ctx->stream), "memset"));
+        PPMD_LAUNCH(ctx, k_andersen_decide, div_up(m->n, 256), 256, 0, m->n, m->orig, m->thermo_seed, m->thermo_thr,
+                    base, s, m->coll_list, m->coll_count);
+        PPMD_LAUNCH(ctx, k_andersen, std::min<int64_t>(div_up(m->n, 128), 148 * 4), 128, 0, m->coll_list,
+                    m->coll_count, m->vel, m->orig, m->thermo_seed, m->thermo_sd, base, s);
+    }
     if (analyse) {
-        PPMD_TRY(boa_otf_launch(ctx, m->n, m->xq, m->pos, m->st, m->W, m->cnt, m->p.max_nbr, m->ld, m->r_boa, m->Lmax,
+        PPMD_TRY(boa_otf_launch(ctx, m->n, m->xq, m->pos, m->st, m->W2, m->cnt2, m->max2, m->ld, m->r_boa, m->Lmax,
                                 m->orig, m->q3, m->part_q));
         PPMD_TRY(reduce_partials(ctx, m->part_q, boa_otf_blocks(m->n), 3, m->red_q));
         if (qrow) PPMD_LAUNCH(ctx, k_q_row, 1, 32, 0, m->red_q, (double)(m->n > 0 ? m->n : 1), qrow);
@@ -379,6 +462,10 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->red_q, 3);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->qbuf, 3 * 1024);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->d_base, 1);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->W2, (size_t)m->ld * (size_t)m->max2);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt2, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->coll_list, n);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->coll_count, 1);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->max_disp_bits, 1);
     if (rc == PPMD_OK) rc = cuda_check(ctx, cudaMemset(m->max_disp_bits, 0, sizeof(unsigned int)), "memset");
     if (rc != PPMD_OK) {
@@ -583,7 +670,8 @@ extern "C" int ppmd_md_set_boa(ppmd_md *m, int32_t every, double r_boa) {
     drop_graph(m);
     m->boa_every = every;
     m->r_boa = r_boa;
-    return PPMD_OK;
+    // the short list of the current build (later builds make their own)
+    return m->ready ? build_short_list(m) : PPMD_OK;
 }
 
 extern "C" int ppmd_md_get_q(ppmd_md *m, float *q4, float *q5, float *q6) {

@@ -52,6 +52,23 @@ def lj_solid(seed: int = 2, n_cells: int = 63, temperature: float = 0.8, skin: f
                 steps=1000, mass=1.0, name=f"lj_solid_fcc{n_cells}^3")
 
 
+def otf_box(seed: int = 6, n: int = 524288, temperature: float = 1.0):
+    """The on-the-fly analysis workload at the size of the paper's weak-scaling
+    table for it (524,288 atoms per node, rho 0.8442, rc 3.0, list 3.3,
+    rebuild every 18): particles on a periodic cubic lattice (the first n of
+    ceil(n^(1/3))^3 simple-cubic sites, box (n/rho)^(1/3)), +-0.05 uniform
+    jitter, Maxwell-Boltzmann velocities."""
+    side = int(math.ceil(round(n ** (1.0 / 3.0), 9)))
+    box_l = (n / RHO) ** (1.0 / 3.0)
+    lat = make_lattice("sc", side, 1.0)
+    lat.edges = np.full(3, box_l / side)
+    lat.box = lat.edges * side
+    pos, box = jittered(lat, rng_stream(seed, 0), "uniform", 0.05, cutoffs=(3.0, 3.3, R_BOA), n_active=n,
+                        resample_rng=rng_stream(seed, 1))
+    vel = maxwell_boltzmann(rng_stream(seed, 2), n, temperature)
+    return dict(pos=pos, vel=vel, box=box, rc=3.0, r_list=3.3, rebuild_every=18, dt=DT, mass=1.0)
+
+
 def nn_distance(kind: str, rho: float = RHO) -> float:
     e = cell_edges(kind, rho)
     if kind == "fcc":
