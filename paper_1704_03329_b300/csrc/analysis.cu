@@ -416,75 +416,129 @@ __global__ void __launch_bounds__(ACNA_WARPS * 32) k_acna(int64_t n, const int4 
     for (int test = 0; test < 2; ++test) {
         const int N = test == 0 ? 12 : 14;
         if (deg < N || (test == 1 && lab != PPMD_OTHER)) break;
-        // FP32 distance of the (N+1)-th candidate (inf when there is none)
-        float tN = __int_as_float(0x7f800000);
+        // FP32 distances of the N-th and (N+1)-th candidates (inf when none)
+        float tN = __int_as_float(0x7f800000), tN1 = 0.0f;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const unsigned b = __ballot_sync(0xffffffffu, rk[q] == N && lane + 32 * q < deg);
+            const bool v = lane + 32 * q < deg;
+            const unsigned b = __ballot_sync(0xffffffffu, rk[q] == N && v);
             if (b) tN = __shfl_sync(0xffffffffu, r2f[q], __ffs(b) - 1);
+            const unsigned b1 = __ballot_sync(0xffffffffu, rk[q] == N - 1 && v);
+            if (b1) tN1 = __shfl_sync(0xffffffffu, r2f[q], __ffs(b1) - 1);
         }
-        // FP32 r^2 is within ~3e-7 r^2 + 1e-7 of the FP64 value: every
-        // candidate that can be among the N nearest lies below tN + band
-        const float lim = tN + (2e-6f * tN + 1e-6f);
-        bool near[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            near[q] = (lane + 32 * q < deg) && r2f[q] <= lim;
-            if (near[q] && !have64[q]) {
-                double dr[3];
-                d64[q] = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)jj[q], S, dr);
-                have64[q] = true;
-            }
-        }
-        // exact rank among the near candidates by (FP64 r^2, index)
-        int ex[2] = {0, 0};
-        for (int src = 0; src < 32; ++src)
-#pragma unroll
-            for (int q2 = 0; q2 < 2; ++q2) {
-                const bool nv = __shfl_sync(0xffffffffu, near[q2], src);
-                const double dv = __shfl_sync(0xffffffffu, d64[q2], src);
-                const int32_t jv = __shfl_sync(0xffffffffu, jj[q2], src);
-#pragma unroll
-                for (int q = 0; q < 2; ++q) ex[q] += nv && ((dv < d64[q]) || (dv == d64[q] && jv < jj[q]));
-            }
+        // FP32 r^2 is within ~3e-7 r^2 + 1e-7 of the FP64 value: with a
+        // wider gap between the N-th and the (N+1)-th the FP32 ranks select
+        // the same N atoms as the FP64 ones
+        const float tol = 2e-6f * tN + 1e-6f;
+        const bool ambiguous = deg > N && tN - tN1 <= 2.0f * tol;
         bool sel[2];
+        int ex[2];
+        if (!ambiguous) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            sel[q] = near[q] && ex[q] < N;
+            for (int q = 0; q < 2; ++q) {
+                sel[q] = lane + 32 * q < deg && rk[q] < N;
+                ex[q] = rk[q];
+            }
+        } else {
+            // every candidate that can be among the N nearest lies below
+            // tN + tol: rank those by (FP64 r^2, index)
+            const float lim = tN + tol;
+            bool near[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                near[q] = (lane + 32 * q < deg) && r2f[q] <= lim;
+                if (near[q] && !have64[q]) {
+                    double dr[3];
+                    d64[q] = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)jj[q], S, dr);
+                    have64[q] = true;
+                }
+            }
+            ex[0] = ex[1] = 0;
+            for (int src = 0; src < 32; ++src)
+#pragma unroll
+                for (int q2 = 0; q2 < 2; ++q2) {
+                    const bool nv = __shfl_sync(0xffffffffu, near[q2], src);
+                    const double dv = __shfl_sync(0xffffffffu, d64[q2], src);
+                    const int32_t jv = __shfl_sync(0xffffffffu, jj[q2], src);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) ex[q] += nv && ((dv < d64[q]) || (dv == d64[q] && jv < jj[q]));
+                }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) sel[q] = near[q] && ex[q] < N;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
             if (sel[q]) {
                 s_j[w][ex[q]] = jj[q];
                 s_x[w][ex[q]] = xj[q];
             }
-        }
-        // the cutoff: sum of the FP64 distances in rank order
-        double s8 = 0.0, s6 = 0.0;
-        for (int r = 0; r < N; ++r) {
-            double v = 0.0;
-            int src = 0;
+        // FP32 cutoff: within ~3e-6 r^2 of the FP64 one (the selected set is exact)
+        float part = 0.0f, part6 = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const unsigned b = __ballot_sync(0xffffffffu, sel[q] && ex[q] == r);
-                if (b) {
-                    src = __ffs(b) - 1;
-                    v = __shfl_sync(0xffffffffu, d64[q], src);
-                }
+        for (int q = 0; q < 2; ++q)
+            if (sel[q]) {
+                const float d = sqrtf(r2f[q]);
+                if (test == 0 || ex[q] < 8) part += d;
+                else part6 += d;
             }
-            const double d = __dsqrt_rn(v);
-            if (test == 0 || r < 8) s8 = __dadd_rn(s8, d);
-            else s6 = __dadd_rn(s6, d);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            part += __shfl_xor_sync(0xffffffffu, part, o);
+            part6 += __shfl_xor_sync(0xffffffffu, part6, o);
         }
-        const double rc = test == 0 ? __dmul_rn(f, __ddiv_rn(s8, 12.0))
-                                    : __dmul_rn(f, __ddiv_rn(__dadd_rn(__dmul_rn(c, s8), s6), 14.0));
-        const double rc2 = __dmul_rn(rc, rc);
-        if (test == 0) rc12 = rc;
-        else rc14 = rc;
+        const float rcf = test == 0 ? (float)f * (part / 12.0f) : (float)f * (((float)c * part + part6) / 14.0f);
+        float rc2f = rcf * rcf;
+        // the exact FP64 cutoff: the sum of the FP64 distances in FP64 rank
+        // order, needed for the cutoff output and for bond tests within the
+        // band (computed only then)
+        double rc2 = 0.0;
+        auto exact_cutoff = [&]() {
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (sel[q] && !have64[q]) {
+                    double dr[3];
+                    d64[q] = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)jj[q], S, dr);
+                    have64[q] = true;
+                }
+            int er[2] = {0, 0};  // FP64 rank among the selected
+            for (int src = 0; src < 32; ++src)
+#pragma unroll
+                for (int q2 = 0; q2 < 2; ++q2) {
+                    const bool sv = __shfl_sync(0xffffffffu, sel[q2], src);
+                    const double dv = __shfl_sync(0xffffffffu, d64[q2], src);
+                    const int32_t jv = __shfl_sync(0xffffffffu, jj[q2], src);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) er[q] += sv && ((dv < d64[q]) || (dv == d64[q] && jv < jj[q]));
+                }
+            double sq[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) sq[q] = sel[q] ? __dsqrt_rn(d64[q]) : 0.0;
+            double s8 = 0.0, s6 = 0.0;
+            for (int r = 0; r < N; ++r) {
+                double v = 0.0;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const unsigned bb = __ballot_sync(0xffffffffu, sel[q] && er[q] == r);
+                    if (bb) v = __shfl_sync(0xffffffffu, sq[q], __ffs(bb) - 1);
+                }
+                if (test == 0 || r < 8) s8 = __dadd_rn(s8, v);
+                else s6 = __dadd_rn(s6, v);
+            }
+            const double rc = test == 0 ? __dmul_rn(f, __ddiv_rn(s8, 12.0))
+                                        : __dmul_rn(f, __ddiv_rn(__dadd_rn(__dmul_rn(c, s8), s6), 14.0));
+            rc2 = __dmul_rn(rc, rc);
+            if (test == 0) rc12 = rc;
+            else rc14 = rc;
+        };
+        if (rcut) exact_cutoff();
         __syncwarp();
-        // bonds among the N selected (bit b of s_A[a]: a and b closer than rc)
-        const float rc2f = (float)rc2, bandb = 2e-6f * rc2f + 1e-6f;
+        // bonds among the N selected (bit b of s_A[a]: a and b closer than
+        // rc): FP32 against the FP32 cutoff outside a band that covers both
+        // errors, the FP64 test against the exact cutoff inside it
+        const float bandb = 2e-5f * rc2f + 1e-6f;
+        unsigned m = 0u, und = 0u;
         if (lane < N) {
             const int4 xa = s_x[w][lane];
-            const double *pa = pos64 + 3 * (int64_t)s_j[w][lane];
-            unsigned m = 0u;
             for (int b = 0; b < N; ++b) {
                 if (b == lane) continue;
                 const int4 xb = s_x[w][b];
@@ -492,15 +546,22 @@ __global__ void __launch_bounds__(ACNA_WARPS * 32) k_acna(int64_t n, const int4 
                 const float dy = fixed_delta((uint32_t)xa.y, (uint32_t)xb.y, S.sx[1]);
                 const float dz = fixed_delta((uint32_t)xa.z, (uint32_t)xb.z, S.sx[2]);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                bool bd = r2 < rc2f - bandb;
-                if (!bd && r2 <= rc2f + bandb) {
-                    double dr[3];
-                    bd = min_image_r2(pa, pos64 + 3 * (int64_t)s_j[w][b], S, dr) < rc2;
-                }
-                if (bd) m |= 1u << b;
+                if (r2 < rc2f - bandb) m |= 1u << b;
+                else if (r2 <= rc2f + bandb) und |= 1u << b;
             }
-            s_A[w][lane] = m;
         }
+        if (__any_sync(0xffffffffu, und != 0u)) {
+            if (!rcut) exact_cutoff();
+            if (lane < N) {
+                const double *pa = pos64 + 3 * (int64_t)s_j[w][lane];
+                for (unsigned u = und; u; u &= u - 1) {
+                    const int b = __ffs(u) - 1;
+                    double dr[3];
+                    if (min_image_r2(pa, pos64 + 3 * (int64_t)s_j[w][b], S, dr) < rc2) m |= 1u << b;
+                }
+            }
+        }
+        if (lane < N) s_A[w][lane] = m;
         __syncwarp();
         int c421 = 0, c422 = 0, c444 = 0, c666 = 0;
         if (lane < N) {
@@ -964,7 +1025,7 @@ int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box 
     const BrickShape shape = brick_shape(s.st.one);
     const int64_t nbricks = brick_count(s.st.one, shape);
     // bin (positions need not be wrapped), sort by cell, fixed point in cell order
-    PPMD_TRY(bin_atoms(ctx, pos, n, s.st, nullptr, ncell, false, cell0, s.cell_start, s.perm));
+    PPMD_TRY(bin_atoms(ctx, pos, n, s.st, nullptr, ncell, false, cell0, s.cell_start, s.perm, true));
     if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos, div_up(n, 256), 256, 0, n, s.perm, pos, s.pos);
     PPMD_TRY(prep_fixed(ctx, s.pos, n, s.st, nullptr, s.xq, nullptr));
     s.ld = (n + 31) / 32 * 32;

@@ -1,5 +1,6 @@
 // Cell binning by counting sort (Sec. 3.5): histogram -> exclusive scan ->
-// scatter -> per-cell ordering by atom index.
+// scatter -> per-cell ordering by atom index (or by x coordinate, for the
+// sorted layouts whose list build searches each row of cells by x).
 #include "cells.cuh"
 
 namespace ppmd {
@@ -46,6 +47,42 @@ __global__ void k_scatter(int64_t n, const int32_t *__restrict__ cell_of, const 
     cell_atoms[cell_start[c] + slot] = (int32_t)i;
 }
 
+// As k_scatter, also writing the sort key of each slot: the atom's x
+// coordinate wrapped into its box (FP32; monotone in the fixed-point word).
+__global__ void k_scatter_x(int64_t n, const double *__restrict__ pos, SegTable st, const int32_t *__restrict__ seg_of,
+                            const int32_t *__restrict__ cell_of, const int32_t *__restrict__ cell_start,
+                            int32_t *__restrict__ cursor, int32_t *__restrict__ cell_atoms, float *__restrict__ key) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Seg &S = seg_ref(st, seg_of ? seg_of[i] : 0);
+    double x = pos[3 * i];
+    if (!(x >= 0.0 && x < S.L[0])) x = isfinite(x) ? wrap_exact(x, S.L[0]) : 0.0;
+    int32_t c = cell_of[i];
+    int32_t slot = cell_start[c] + atomicAdd(&cursor[c], 1);
+    cell_atoms[slot] = (int32_t)i;
+    key[slot] = (float)x;
+}
+
+// Order every cell's atoms by (x, index) (insertion sort; cells are small).
+__global__ void k_sort_cells_x(int64_t ncell, const int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_atoms,
+                               float *__restrict__ key) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int32_t a = cell_start[c], b = cell_start[c + 1];
+    for (int32_t k = a + 1; k < b; ++k) {
+        const int32_t v = cell_atoms[k];
+        const float kv = key[k];
+        int32_t m = k - 1;
+        while (m >= a && (key[m] > kv || (key[m] == kv && cell_atoms[m] > v))) {
+            cell_atoms[m + 1] = cell_atoms[m];
+            key[m + 1] = key[m];
+            --m;
+        }
+        cell_atoms[m + 1] = v;
+        key[m + 1] = kv;
+    }
+}
+
 // Order every cell's atoms by index (insertion sort; cells are small).
 __global__ void k_sort_cells(int64_t ncell, const int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_atoms) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,7 +100,7 @@ __global__ void k_sort_cells(int64_t ncell, const int32_t *__restrict__ cell_sta
 }
 
 int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, const int32_t *seg_of, int64_t ncell,
-              bool exact, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms) {
+              bool exact, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms, bool order_x) {
     cudaStream_t s = ctx->stream;
     PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cell_start, 0, sizeof(int32_t) * (size_t)(ncell + 1), s), "memset"));
     if (n > 0) {
@@ -77,8 +114,16 @@ int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, c
         int32_t *cursor = (int32_t *)scratch(ctx, S_COUNT, sizeof(int32_t) * (size_t)ncell);
         if (!cursor) return PPMD_ERR_NOMEM;
         PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)ncell, s), "memset"));
-        PPMD_LAUNCH(ctx, k_scatter, div_up(n, 256), 256, 0, n, cell_of, cell_start, cursor, cell_atoms);
-        PPMD_LAUNCH(ctx, k_sort_cells, div_up(ncell, 128), 128, 0, ncell, cell_start, cell_atoms);
+        if (order_x) {
+            float *key = (float *)scratch(ctx, S_CELLKEY, sizeof(float) * (size_t)n);
+            if (!key) return PPMD_ERR_NOMEM;
+            PPMD_LAUNCH(ctx, k_scatter_x, div_up(n, 256), 256, 0, n, pos, st, seg_of, cell_of, cell_start, cursor,
+                        cell_atoms, key);
+            PPMD_LAUNCH(ctx, k_sort_cells_x, div_up(ncell, 128), 128, 0, ncell, cell_start, cell_atoms, key);
+        } else {
+            PPMD_LAUNCH(ctx, k_scatter, div_up(n, 256), 256, 0, n, cell_of, cell_start, cursor, cell_atoms);
+            PPMD_LAUNCH(ctx, k_sort_cells, div_up(ncell, 128), 128, 0, ncell, cell_start, cell_atoms);
+        }
     }
     return check_launch(ctx, "bin_atoms");
 }

@@ -11,5 +11,5 @@ namespace ppmd {
 // the box).  Writes cell_of[n], cell_start[ncell+1], cell_atoms[n] (atoms
 // of a cell in increasing index).
 int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, const int32_t *seg_of, int64_t ncell,
-              bool exact, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms);
+              bool exact, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms, bool order_x = false);
 }  // namespace ppmd

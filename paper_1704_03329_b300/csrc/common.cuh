@@ -31,6 +31,7 @@ enum ScratchSlot {
     S_TMP2,
     S_SORTPOS,  // analysis: sorted positions
     S_SORTIDX,
+    S_CELLKEY,
     S_CELLS0,
     S_CELLS1,
     S_CELLS2,

@@ -269,7 +269,8 @@ int rebuild(ppmd_md *m) {
     ppmd_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
     const int64_t n = m->n;
-    PPMD_TRY(bin_atoms(ctx, m->pos, n, m->st, m->seg_of, m->ncell, false, m->cell_of, m->cell_start, m->cell_atoms));
+    PPMD_TRY(bin_atoms(ctx, m->pos, n, m->st, m->seg_of, m->ncell, false, m->cell_of, m->cell_start, m->cell_atoms,
+                       true));
     PPMD_TRY(md_gather(ctx, n, m->cell_atoms, m->st, m->pos, m->vel, m->orig, m->seg_of, m->pos_t, m->vel_t, m->xq_t,
                        m->orig_t, m->seg_t));
     use_buffer(m, 0);

@@ -281,16 +281,28 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
             const float4 fi = rel(xi, i);
             const float4 *s_f = (const float4 *)smem;
             const f2_t xii = pk(fi.x, fi.x), yii = pk(fi.y, fi.y), zii = pk(fi.z, fi.z);
+            // atoms are ordered by x within each cell, so a row of three cells
+            // is ordered by x: only the window |dx| < r_list (widened far
+            // beyond the FP32 error of the offsets) can hold hits
+            const float rwin = sqrtf((float)S.rl2) * 1.00001f + 1e-5f, xlo = fi.x - rwin, xhi = fi.x + rwin;
             for (int dz = 0; dz < 3; ++dz)
                 for (int dy = 0; dy < 3; ++dy) {
                     const int r = (hz + dz) * nyr + hy + dy;
-                    const int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
+                    const int32_t b = s_cell[r][t + 3];
+                    int32_t a = s_cell[r][t];
+                    for (int32_t hi2 = b; a < hi2;) {  // first candidate with x >= xlo
+                        const int32_t mid = (a + hi2) >> 1;
+                        if (s_f[mid].x < xlo) a = mid + 1;
+                        else hi2 = mid;
+                    }
                     // four candidates per pass (two packed pairs), tested in
-                    // order; reads past b find either atoms of cells two or
-                    // more cells away from the home cell (farther than the
-                    // cell edge, so never a hit) or the row's sentinels
+                    // order until one starts beyond the window; reads past b
+                    // find either atoms of cells two or more cells away from
+                    // the home cell (farther than the cell edge, so never a
+                    // hit) or the row's sentinels
                     for (int32_t k = a; k < b; k += 4) {
                         const float4 f0 = s_f[k], f1 = s_f[k + 1], f2 = s_f[k + 2], f3 = s_f[k + 3];
+                        if (f0.x > xhi) break;
                         const f2_t dx0 = sub2(xii, pk(f0.x, f1.x)), dx1 = sub2(xii, pk(f2.x, f3.x));
                         const f2_t dy0 = sub2(yii, pk(f0.y, f1.y)), dy1 = sub2(yii, pk(f2.y, f3.y));
                         const f2_t dz0 = sub2(zii, pk(f0.z, f1.z)), dz1 = sub2(zii, pk(f2.z, f3.z));

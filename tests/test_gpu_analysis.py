@@ -177,8 +177,12 @@ def test_acna_bit_exact(L, ctx, kind, sigma):
     offs, nb = oracle.neighbours_cells(pos, box, R_ACNA)
     lab_o, rc_o = oracle.acna(pos, box, offs, nb)
     lab, rc = L.ppmd_acna(ctx, cu(pos), box, R_ACNA)
+    # without the cutoff output the kernel decides in FP32 where that is
+    # safe and computes the FP64 cutoff only for bonds within its band
+    lab_fast, _ = L.ppmd_acna(ctx, cu(pos), box, R_ACNA, want_rcut=False)
     ctx.sync()
     assert np.array_equal(lab.cpu().numpy(), lab_o)
+    assert np.array_equal(lab_fast.cpu().numpy(), lab_o)
     assert np.array_equal(rc.cpu().numpy(), rc_o)
 
 
@@ -197,7 +201,9 @@ def test_acna_full_size_box_sampled(L, ctx):
     c = configs.structure_box("bcc", 0.05, seed=30)
     pos, box = c["pos"], c["box"]
     lab, rc = L.ppmd_acna(ctx, cu(pos), box, R_ACNA)
+    lab_fast, _ = L.ppmd_acna(ctx, cu(pos), box, R_ACNA, want_rcut=False)
     ctx.sync()
+    assert np.array_equal(lab.cpu().numpy(), lab_fast.cpu().numpy())
     sample = np.sort(np.random.default_rng(3).choice(len(pos), 500, replace=False))
     offs, nb = oracle.neighbours_cells(pos, box, R_ACNA)
     # rows of the other atoms emptied: the oracle then only works on the sample
