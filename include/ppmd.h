@@ -285,7 +285,7 @@ typedef struct {
     double r_list;         /* list cutoff r_c + delta (Eq. (6)); per box min(r_list, box_r_list[b]) */
     double mass, dt;
     int32_t rebuild_every; /* list rebuilt when step % rebuild_every == 0 (and at set-up) */
-    int32_t max_nbr;       /* row capacity of the neighbour list */
+    int32_t max_nbr;       /* row capacity of the neighbour list (rounded up to a multiple of 4) */
     int32_t prec;          /* ppmd_prec of the pair loop */
     int32_t energy_every;  /* potential/kinetic energy recorded every k steps (0 = never) */
 } ppmd_md_params;

@@ -217,7 +217,7 @@ __global__ void k_short_list(int64_t n, const int4 *__restrict__ xq, SegTable st
         int32_t jv[4];
         int4 xv[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) jv[q] = k0 + q < deg ? __ldg(W + (int64_t)(k0 + q) * ld + i) : (int32_t)i;
+        for (int q = 0; q < 4; ++q) jv[q] = k0 + q < deg ? __ldg(W + (((int64_t)(k0 >> 2) * ld + i) << 2) + q) : (int32_t)i;
 #pragma unroll
         for (int q = 0; q < 4; ++q) xv[q] = __ldg(&xq[jv[q]]);
 #pragma unroll
@@ -281,7 +281,7 @@ int rebuild(ppmd_md *m) {
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, BrickShape{1, 1, 1}, m->xq, m->pos, m->st, m->cell_start,
-                               m->W, m->ld, m->cnt, m->p.max_nbr, m->stage_cap));
+                               m->W, m->ld, m->cnt, m->p.max_nbr, m->stage_cap, true));
     return build_short_list(m);
 }
 
@@ -371,6 +371,7 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     m->n = atom_off[nbox];
     m->nbox = nbox;
     m->p = p;
+    m->p.max_nbr = (p.max_nbr + 3) & ~3;  // the list is stored in groups of four
     m->h = p.dt / (2.0 * p.mass);
     m->half_m = 0.5 * p.mass;
     m->segs.resize(nbox);
@@ -443,7 +444,7 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_atoms, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_start, m->ncell + 1);
     m->ld = (n + 31) / 32 * 32;
-    if (rc == PPMD_OK) rc = md_alloc(m, &m->W, (size_t)m->ld * p.max_nbr);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->W, (size_t)m->ld * m->p.max_nbr);
     if (rc == PPMD_OK) {
         std::vector<Brick> bl;
         m->stage_cap = make_bricks(m->segs, bl);
@@ -452,7 +453,7 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
         if (rc == PPMD_OK && !bl.empty())
             rc = cuda_check(ctx, cudaMemcpy(m->bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice), "copy");
     }
-    if (rc == PPMD_OK) rc = neigh_brick_setup(ctx, p.max_nbr);
+    if (rc == PPMD_OK) rc = neigh_brick_setup(ctx, m->p.max_nbr);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_f, 3 * lj_columns_blocks(n) + 3);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);

@@ -121,6 +121,7 @@ __device__ __forceinline__ float fdiff(int32_t a, int32_t b) { return __int2floa
 // two candidates per packed step; threads of the same cell read the same
 // candidate, so the shared-memory reads are broadcasts.  Hits go straight
 // to the atom's column of W.
+template <bool VEC4>
 __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
                                                                const int4 *__restrict__ xq,
                                                                const double *__restrict__ pos64, SegTable st,
@@ -273,8 +274,17 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
         while (t + 1 < bw && i >= s_home[hr][t + 1]) ++t;
         int32_t count = 0;
         int32_t *col = W + i;
+        // VEC4: the row is stored as groups of four entries (one 16-byte word
+        // per group, W4[g * ld + i]), collected in a shift register
+        int4 grp = make_int4(-1, -1, -1, -1);
+        int4 *col4 = reinterpret_cast<int4 *>(W) + i;
         auto hit = [&](int32_t j) {
-            if (count < max_nbr) col[(int64_t)count * ld] = j;
+            if (VEC4) {
+                grp = make_int4(grp.y, grp.z, grp.w, j);
+                if ((count & 3) == 3 && count < max_nbr) col4[(int64_t)(count >> 2) * ld] = grp;
+            } else if (count < max_nbr) {
+                col[(int64_t)count * ld] = j;
+            }
             ++count;
         };
         if (fstage) {
@@ -351,6 +361,11 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
                     }
                 }
             }
+        if (VEC4 && (count & 3) != 0 && count < max_nbr) {
+            // the last, partial group, padded with -1
+            for (int q = count & 3; q < 4; ++q) grp = make_int4(grp.y, grp.z, grp.w, -1);
+            col4[(int64_t)(count >> 2) * ld] = grp;
+        }
         cnt[i] = count;
         if (count > max_nbr) {
             latch_status(status, PPMD_ERR_CAPACITY);
@@ -360,18 +375,26 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
 }
 
 int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr) {
-    return cuda_check(ctx, cudaFuncSetAttribute(k_neigh_brick, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)neigh_brick_smem(max_nbr)),
-                      "cudaFuncSetAttribute");
+    int rc = cuda_check(ctx, cudaFuncSetAttribute(k_neigh_brick<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)neigh_brick_smem(max_nbr)),
+                        "cudaFuncSetAttribute");
+    if (rc == PPMD_OK)
+        rc = cuda_check(ctx, cudaFuncSetAttribute(k_neigh_brick<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)neigh_brick_smem(max_nbr)),
+                        "cudaFuncSetAttribute");
+    return rc;
 }
 
 int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, BrickShape shape, const int4 *xq,
                       const double *pos64, const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld,
-                      int32_t *cnt, int32_t max_nbr, int32_t stage_cap) {
+                      int32_t *cnt, int32_t max_nbr, int32_t stage_cap, bool vec4) {
     if (stage_cap <= 0 || stage_cap > NB_MAX) stage_cap = NB_MAX;
-    if (nbricks > 0)
-        PPMD_LAUNCH(ctx, k_neigh_brick, nbricks, BRICK_THREADS, (size_t)stage_cap * sizeof(int4), bricks, shape, xq,
-                    pos64, st, cell_start, W, ld, cnt, max_nbr, stage_cap, ctx->d_status, ctx->d_needed);
+    if (vec4 && (max_nbr & 3)) return set_error(ctx, PPMD_ERR_INVALID, "grouped list needs a capacity divisible by 4");
+    if (nbricks > 0) {
+        auto kern = vec4 ? k_neigh_brick<true> : k_neigh_brick<false>;
+        PPMD_LAUNCH(ctx, kern, nbricks, BRICK_THREADS, (size_t)stage_cap * sizeof(int4), bricks, shape, xq, pos64, st,
+                    cell_start, W, ld, cnt, max_nbr, stage_cap, ctx->d_status, ctx->d_needed);
+    }
     return check_launch(ctx, "build_list_bricks");
 }
 
@@ -425,7 +448,7 @@ __device__ __forceinline__ void block_sum3(double a, double b, double c, double 
 constexpr int COL_BLOCK = 256;
 
 template <bool ENERGY, bool DRIFT>
-__global__ void __launch_bounds__(COL_BLOCK, (ENERGY || DRIFT) ? 3 : 4) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
+__global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
                                                         const double *__restrict__ pos64, SegTable st, LJConst c,
                                                         const int32_t *__restrict__ W, const int32_t *__restrict__ cnt,
                                                         int32_t max_nbr, float4 *__restrict__ f4,
@@ -449,7 +472,7 @@ __global__ void __launch_bounds__(COL_BLOCK, (ENERGY || DRIFT) ? 3 : 4) k_lj_col
             ea.init();
             vir.init();
         }
-        const int32_t *col = W + i;
+        const int4 *col4 = reinterpret_cast<const int4 *>(W) + i;  // groups of four entries
         // Two neighbours per packed step; the list entries of the next four
         // neighbours are loaded one iteration ahead of their use.
         auto step = [&](int32_t j0, int32_t j1, const int4 &a, const int4 &b) {
@@ -489,18 +512,18 @@ __global__ void __launch_bounds__(COL_BLOCK, (ENERGY || DRIFT) ? 3 : 4) k_lj_col
                 vir.add_prod(fm, r2);
             }
         };
-        auto entry = [&](int32_t k) { return k < m ? __ldg(col + (int64_t)k * ld) : -1; };
-        int32_t j0 = entry(0), j1 = entry(1), j2 = entry(2), j3 = entry(3);
+        // one 16-byte list word per four neighbours (entries past the row
+        // are -1), loaded one group ahead of its use
+        auto group = [&](int32_t k) { return k < m ? __ldg(col4 + (int64_t)(k >> 2) * ld) : make_int4(-1, -1, -1, -1); };
+        int4 g = group(0);
         for (int32_t k = 0; k < m; k += 4) {
-            const int32_t n0 = entry(k + 4), n1 = entry(k + 5), n2 = entry(k + 6), n3 = entry(k + 7);
+            const int4 nx = group(k + 4);
+            const int32_t j0 = g.x, j1 = g.y, j2 = g.z, j3 = g.w;
             const int4 a0 = __ldg(&xq[j0 >= 0 ? j0 : i]), a1 = __ldg(&xq[j1 >= 0 ? j1 : i]);
             const int4 a2 = __ldg(&xq[j2 >= 0 ? j2 : i]), a3 = __ldg(&xq[j3 >= 0 ? j3 : i]);
             step(j0, j1, a0, a1);
             step(j2, j3, a2, a3);
-            j0 = n0;
-            j1 = n1;
-            j2 = n2;
-            j3 = n3;
+            g = nx;
         }
         float hx, lx, hy, ly, hz, lz;
         fx.merged(hx, lx);
@@ -571,7 +594,7 @@ __global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(int64_t n, int64_t ld, c
         const double *pi = pos64 + 3 * i;
         double fx = 0.0, fy = 0.0, fz = 0.0;
         for (int32_t k = 0; k < m; ++k) {
-            const int32_t j = __ldg(W + k * ld + i);
+            const int32_t j = __ldg(W + (((int64_t)(k >> 2) * ld + i) << 2) + (k & 3));  // grouped by four
             double dr[3];
             const double r2 = min_image_r2(pi, pos64 + 3 * (int64_t)j, S, dr);
             if (r2 < c.rc2) {

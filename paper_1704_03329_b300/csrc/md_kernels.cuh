@@ -33,15 +33,18 @@ size_t neigh_brick_smem(int32_t max_nbr);
 int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr);
 
 // Column-major neighbour list W[m * ld + i] (the paper's neighbour matrix)
-// of atoms stored in cell order, one block per brick.  With bricks == null
+// of atoms stored in cell order, one block per brick.  With vec4 the
+// entries are grouped by four: entry m of atom i at W[((m/4) ld + i) 4 + m%4],
+// the last group padded with -1 (max_nbr must be divisible by 4).  With bricks == null
 // the grid is one segment's (st.nseg == 1) cut into bricks of `shape`, in
 // x-fastest order.
 int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, BrickShape shape, const int4 *xq,
                       const double *pos64, const SegTable &st, const int32_t *cell_start, int32_t *W, int64_t ld,
-                      int32_t *cnt, int32_t max_nbr, int32_t stage_cap);
+                      int32_t *cnt, int32_t max_nbr, int32_t stage_cap, bool vec4 = false);
 
-// Pair loop over the column-major list, one thread per atom, followed by
-// the second kick of Algorithm 6 (v += dt/(2m) F) when vel != null.
+// Pair loop over the grouped column-major list (vec4 layout above), one
+// thread per atom, followed by the second kick of Algorithm 6
+// (v += dt/(2m) F) when vel != null.
 // partials (energy steps): per-block rows (U, W, K).
 // The next step's first kick and drift (Algorithm 6) fused into the FP32
 // pair loop: after the second kick, v += dt/(2m) F once more and
