@@ -409,6 +409,13 @@ struct Kahan2 {
         cn = sub2(yv, sub2(t, s));
         s = t;
     }
+    // adds v to each stream
+    __device__ __forceinline__ void add(f2 v) {
+        const f2 yv = add2(v, cn);
+        const f2 t = add2(s, yv);
+        cn = sub2(yv, sub2(t, s));
+        s = t;
+    }
     // the two streams merged: (hi, lo) with hi + lo the sum
     __device__ __forceinline__ void merged(float &hi, float &lo) const {
         float s0, s1, c0, c1;
@@ -475,7 +482,9 @@ __global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld
         const int4 *col4 = reinterpret_cast<const int4 *>(W) + i;  // groups of four entries
         // Two neighbours per packed step; the list entries of the next four
         // neighbours are loaded one iteration ahead of their use.
-        auto step = [&](int32_t j0, int32_t j1, const int4 &a, const int4 &b) {
+        // Two neighbours per packed step: their force terms fm dr (fm = 0
+        // outside the cutoff) are returned; energy and virial are added here.
+        auto step = [&](int32_t j0, int32_t j1, const int4 &a, const int4 &b, f2 &tx, f2 &ty, f2 &tz) {
             const bool v0 = j0 >= 0, v1 = j1 >= 0;
             const f2 dx = mul2(pk(fdiff(xi.x, a.x), fdiff(xi.x, b.x)), sxx);
             const f2 dy = mul2(pk(fdiff(xi.y, a.y), fdiff(xi.y, b.y)), syy);
@@ -501,9 +510,9 @@ __global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld
             float fa, fb;
             upk(fm, fa, fb);
             fm = pk(in0 ? fa : 0.0f, in1 ? fb : 0.0f);
-            fx.add_prod(fm, dx);
-            fy.add_prod(fm, dy);
-            fz.add_prod(fm, dz);
+            tx = mul2(fm, dx);
+            ty = mul2(fm, dy);
+            tz = mul2(fm, dz);
             if (ENERGY) {
                 f2 v = mul2(e2, fma2(sr6, sub2(sr6, one), shift));
                 float va, vb;
@@ -521,8 +530,14 @@ __global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld
             const int32_t j0 = g.x, j1 = g.y, j2 = g.z, j3 = g.w;
             const int4 a0 = __ldg(&xq[j0 >= 0 ? j0 : i]), a1 = __ldg(&xq[j1 >= 0 ? j1 : i]);
             const int4 a2 = __ldg(&xq[j2 >= 0 ? j2 : i]), a3 = __ldg(&xq[j3 >= 0 ? j3 : i]);
-            step(j0, j1, a0, a1);
-            step(j2, j3, a2, a3);
+            // the four terms of each component enter the compensated sum as
+            // one plain FP32 partial (two terms per stream)
+            f2 tx0, ty0, tz0, tx1, ty1, tz1;
+            step(j0, j1, a0, a1, tx0, ty0, tz0);
+            step(j2, j3, a2, a3, tx1, ty1, tz1);
+            fx.add(add2(tx0, tx1));
+            fy.add(add2(ty0, ty1));
+            fz.add(add2(tz0, tz1));
             g = nx;
         }
         float hx, lx, hy, ly, hz, lz;
