@@ -63,24 +63,23 @@ __global__ void k_scatter_x(int64_t n, const double *__restrict__ pos, SegTable 
     key[slot] = (float)x;
 }
 
-// Order every cell's atoms by (x, index) (insertion sort; cells are small).
-__global__ void k_sort_cells_x(int64_t ncell, const int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_atoms,
-                               float *__restrict__ key) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int32_t a = cell_start[c], b = cell_start[c + 1];
-    for (int32_t k = a + 1; k < b; ++k) {
-        const int32_t v = cell_atoms[k];
-        const float kv = key[k];
-        int32_t m = k - 1;
-        while (m >= a && (key[m] > kv || (key[m] == kv && cell_atoms[m] > v))) {
-            cell_atoms[m + 1] = cell_atoms[m];
-            key[m + 1] = key[m];
-            --m;
-        }
-        cell_atoms[m + 1] = v;
-        key[m + 1] = kv;
+// Order every cell's atoms by (x, index): one thread per slot counts the
+// members of its cell that come first (cells are small) and writes its atom
+// at that rank.
+__global__ void k_rank_cells_x(int64_t n, const int32_t *__restrict__ cell_of, const int32_t *__restrict__ cell_start,
+                               const int32_t *__restrict__ tmp_atoms, const float *__restrict__ key,
+                               int32_t *__restrict__ cell_atoms) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int32_t v = tmp_atoms[s];
+    const float kv = key[s];
+    const int32_t c = cell_of[v], a = cell_start[c], b = cell_start[c + 1];
+    int32_t rank = 0;
+    for (int32_t t = a; t < b; ++t) {
+        const float kt = key[t];
+        rank += (kt < kv) || (kt == kv && tmp_atoms[t] < v);
     }
+    cell_atoms[a + rank] = v;
 }
 
 // Order every cell's atoms by index (insertion sort; cells are small).
@@ -116,10 +115,11 @@ int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, c
         PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)ncell, s), "memset"));
         if (order_x) {
             float *key = (float *)scratch(ctx, S_CELLKEY, sizeof(float) * (size_t)n);
-            if (!key) return PPMD_ERR_NOMEM;
-            PPMD_LAUNCH(ctx, k_scatter_x, div_up(n, 256), 256, 0, n, pos, st, seg_of, cell_of, cell_start, cursor,
-                        cell_atoms, key);
-            PPMD_LAUNCH(ctx, k_sort_cells_x, div_up(ncell, 128), 128, 0, ncell, cell_start, cell_atoms, key);
+            int32_t *tmp = (int32_t *)scratch(ctx, S_CELLTMP, sizeof(int32_t) * (size_t)n);
+            if (!key || !tmp) return PPMD_ERR_NOMEM;
+            PPMD_LAUNCH(ctx, k_scatter_x, div_up(n, 256), 256, 0, n, pos, st, seg_of, cell_of, cell_start, cursor, tmp,
+                        key);
+            PPMD_LAUNCH(ctx, k_rank_cells_x, div_up(n, 256), 256, 0, n, cell_of, cell_start, tmp, key, cell_atoms);
         } else {
             PPMD_LAUNCH(ctx, k_scatter, div_up(n, 256), 256, 0, n, cell_of, cell_start, cursor, cell_atoms);
             PPMD_LAUNCH(ctx, k_sort_cells, div_up(ncell, 128), 128, 0, ncell, cell_start, cell_atoms);

@@ -32,6 +32,7 @@ enum ScratchSlot {
     S_SORTPOS,  // analysis: sorted positions
     S_SORTIDX,
     S_CELLKEY,
+    S_CELLTMP,
     S_CELLS0,
     S_CELLS1,
     S_CELLS2,

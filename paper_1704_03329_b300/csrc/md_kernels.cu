@@ -452,6 +452,50 @@ __device__ __forceinline__ void block_sum3(double a, double b, double c, double 
     }
 }
 
+// As block_sum3, with the warp sums taken on FP32 pairs (hi, lo) by
+// error-free transformations (about 48 significant bits) instead of FP64
+// additions on every lane, which are slow on this part.
+__device__ __forceinline__ void pair_add(float &s, float &e, float s2, float e2) {
+    const float t = s + s2, bb = t - s, err = (s - (t - bb)) + (s2 - bb);
+    const float lo = err + (e + e2);
+    s = t + lo;
+    e = lo - (s - t);
+}
+
+__device__ __forceinline__ void block_sum3_pairs(double a, double b, double c, double *partials) {
+    __shared__ double sh[3][32];
+    float hs[3], ls[3];
+    const double v[3] = {a, b, c};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        hs[k] = (float)v[k];
+        ls[k] = (float)(v[k] - (double)hs[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hs[k], o), l2 = __shfl_xor_sync(0xffffffffu, ls[k], o);
+            pair_add(hs[k], ls[k], h2, l2);
+        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sh[k][w] = (double)hs[k] + (double)ls[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double u = 0, vv = 0, kk = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            u += sh[0][q];
+            vv += sh[1][q];
+            kk += sh[2][q];
+        }
+        partials[3 * blockIdx.x] = u;
+        partials[3 * blockIdx.x + 1] = vv;
+        partials[3 * blockIdx.x + 2] = kk;
+    }
+}
+
 constexpr int COL_BLOCK = 256;
 
 template <bool ENERGY, bool DRIFT>
@@ -591,7 +635,7 @@ __global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld
         for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
         if ((threadIdx.x & 31) == 0 && d2 > 0.0f) atomicMax(dr.max_disp_bits, __float_as_uint(d2));
     }
-    if (ENERGY) block_sum3(u_i, w_i, k_i, partials);
+    if (ENERGY) block_sum3_pairs(u_i, w_i, k_i, partials);
 }
 
 template <bool ENERGY>
