@@ -46,7 +46,8 @@ def parse():
 
 
 def dist_info():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1704_03329_b300.replicas import rank_info
+    return rank_info()
 
 
 def peaks():
@@ -175,7 +176,8 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    c = configs.lj_solid(seed=2 + rank, n_cells=args.cells)
+    from paper_1704_03329_b300.replicas import barrier as rank_barrier, max_over_ranks, rank_seed
+    c = configs.lj_solid(seed=rank_seed(2, rank), n_cells=args.cells)
     n = len(c["pos"])
     pos_h = torch.from_numpy(c["pos"]).pin_memory()
     vel_h = torch.from_numpy(c["vel"]).pin_memory()
@@ -198,10 +200,7 @@ def run_ours(args):
     ctx.sync()
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
+        rank_barrier(cuda=True)
 
     # ---- device-resident timed region -----------------------------------
     sampler = ClockSampler(local)
@@ -217,11 +216,7 @@ def run_ours(args):
     launches = ctx.kernel_count() - k0
     clocks = sampler.stop()
     info = md.info()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device="cuda")
     value = world * n * K / (ms * 1e-3)
 
     # ---- force kernel alone: average launch duration ----------------------
@@ -275,7 +270,7 @@ def run_ours(args):
     pos_out.copy_(out, non_blocking=True)
     en_h.copy_(energies, non_blocking=True)
     barrier()
-    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e = {"value": world * n * K / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": 48.0 * n / K, "d2h_bytes_per_step": (24.0 * n + 16.0 * K) / K,
            "note": "pinned host positions+velocities in, set-up (sort, list, F(r0)), K steps, positions+energies out"}
