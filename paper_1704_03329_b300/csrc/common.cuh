@@ -33,6 +33,7 @@ enum ScratchSlot {
     S_SORTIDX,
     S_CELLKEY,
     S_CELLTMP,
+    S_MLPTC,
     S_CELLS0,
     S_CELLS1,
     S_CELLS2,

@@ -14,11 +14,11 @@
 #include <algorithm>
 
 #include "analysis.cuh"
+#include "mlp_layout.cuh"
+#include "mlp_tc.cuh"
 
 namespace ppmd {
 
-constexpr int OFF_MU = 0, OFF_ISD = 30, OFF_W1 = 60, OFF_B1 = 1980, OFF_W2 = 2044, OFF_B2 = 6140, OFF_W3 = 6204,
-              OFF_B3 = 6460, NPARAM = 6464;
 static_assert(NPARAM == PPMD_MLP_NPARAM, "parameter count");
 
 // BF16 operand images (row strides padded so that fragment loads are free of
@@ -635,12 +635,7 @@ using namespace ppmd;
 extern "C" int ppmd_mlp_forward(ppmd_ctx *ctx, const float *params, const uint16_t *x, int64_t n, float *logits) {
     if (!ctx || !params || n < 0 || (n > 0 && (!x || !logits))) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_mlp_forward: bad argument");
     cudaSetDevice(ctx->device);
-    __nv_bfloat16 *img;
-    PPMD_TRY(pack_weights(ctx, params, &img));
-    if (n > 0)
-        PPMD_LAUNCH(ctx, k_mlp_infer, mlp_grid((n + 15) / 16), MLP_WARPS * 32, 0, n, (const __nv_bfloat16 *)x, img, params,
-                    logits, nullptr, nullptr, 0.0f, nullptr, nullptr);
-    return check_launch(ctx, "ppmd_mlp_forward");
+    return mlp_infer_tc(ctx, n, (const __nv_bfloat16 *)x, params, logits, nullptr, nullptr, 0.0f, nullptr, nullptr);
 }
 
 extern "C" int ppmd_mlp_grad(ppmd_ctx *ctx, const float *params, const uint16_t *x, const int8_t *y, int64_t batch,
@@ -735,12 +730,8 @@ extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t
         int32_t *nfb = ctx->d_status + 4;  // the fallback count, read back with the status
         PPMD_TRY(features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, r_cna, s.Lmax, nullptr,
                                  nullptr, feat));
-        __nv_bfloat16 *img;
-        PPMD_TRY(pack_weights(ctx, params, &img));
         PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(nfb, 0, sizeof(int32_t), ctx->stream), "memset"));
-        if (n > 0)
-            PPMD_LAUNCH(ctx, k_mlp_infer, mlp_grid((n + 15) / 16), MLP_WARPS * 32, 0, n, feat, img, params, nullptr, cls,
-                        conf_s, threshold, fb, nfb);
+        PPMD_TRY(mlp_infer_tc(ctx, n, feat, params, nullptr, cls, conf_s, threshold, fb, nfb));
         // exact CNA for the low-confidence atoms (as many as the device
         // found), written over their MLP class
         PPMD_TRY(cna_subset_launch(ctx, n, nfb, fb, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, cls));
