@@ -14,8 +14,9 @@
 //      memory as operand A of the next layer;
 //   4. after layer 3 (N padded to 16) the logits give class, confidence and
 //      the fallback list.
-// Each thread loads its feature row of the next tile while the current one
-// is processed; up to seven CTAs share an SM.
+// Two tiles are in flight per CTA (two operand slots, two accumulator
+// regions, two mbarriers): while the tensor cores work on one, the threads
+// prepare or finish the other; up to four CTAs share an SM.
 // The weights (operand B), biases and standardisation are packed once per
 // call and brought into each CTA by one bulk copy (cp.async.bulk).
 //
@@ -35,24 +36,24 @@ namespace {
 
 constexpr int TC_ROWS = 128;
 // shared-memory map (bytes from the 1024-aligned dynamic base)
-// X (A of layer 1, 128 x 32 BF16) and H (A of layers 2 and 3, 128 x 64)
-// share one region: each is written only after the tensor cores finished
+// Two tiles are in flight per CTA (slots 0 and 1).  In each slot X (A of
+// layer 1, 128 x 32 BF16) and H (A of layers 2 and 3, 128 x 64) share one
+// 16 KB region: each is written only after the tensor cores finished
 // reading the other.
-constexpr uint32_t SM_X = 0;
-constexpr uint32_t SM_H = 0;
-constexpr uint32_t SM_W1 = 16384;         // B of layer 1: 64 x 32 (n x k)
+constexpr uint32_t SM_SLOT = 16384;
+constexpr uint32_t SM_W1 = 2 * SM_SLOT;   // B of layer 1: 64 x 32 (n x k)
 constexpr uint32_t SM_W2 = SM_W1 + 4096;  // B of layer 2: 64 x 64
 constexpr uint32_t SM_W3 = SM_W2 + 8192;  // B of layer 3: 16 x 64 (n >= 4 zero)
 constexpr uint32_t SM_BIAS = SM_W3 + 2048;    // b1[64] b2[64] b3[16] (floats)
 constexpr uint32_t SM_NORM = SM_BIAS + 576;   // mu[32] isd[32]
-constexpr uint32_t SM_BAR = SM_NORM + 256;    // mbarrier (8 bytes) + tensor-memory address (4 bytes)
-constexpr uint32_t SM_USED = SM_BAR + 16;
-// Requested dynamic shared memory: at most seven CTAs per SM, so that their
-// tensor memory (64 columns each) stays within the SM's 512 columns.
-constexpr uint32_t SM_REQUEST = 32 * 1024;
+constexpr uint32_t SM_BAR = SM_NORM + 256;    // mbarriers of slots 0, 1 (8 bytes each) + tensor-memory address
+constexpr uint32_t SM_USED = SM_BAR + 32;
+// Requested dynamic shared memory: at most four CTAs per SM, so that their
+// tensor memory (128 columns each) stays within the SM's 512 columns.
+constexpr uint32_t SM_REQUEST = 48 * 1024;
 static_assert(SM_USED <= SM_REQUEST, "shared memory map");
-constexpr uint32_t TMEM_COLS = 64;  // every layer's accumulator at column 0, read before the next layer
-constexpr int TC_CTAS_PER_SM = 7;
+constexpr uint32_t TMEM_COLS = 128;  // slot s: columns 64 s .. 64 s + 63, every layer's accumulator
+constexpr int TC_CTAS_PER_SM = 4;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t core_off(int r, int k, int R) {
@@ -108,18 +109,16 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 16 consecutive FP32 columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 16 consecutive FP32 columns of this thread's lane (issued; complete
+// after tmem_wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
 }
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pk_bf16(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -136,21 +135,24 @@ __device__ __forceinline__ void st_chunk(uint8_t *smem, uint32_t off, const floa
     *reinterpret_cast<uint4 *>(smem + off) = q;
 }
 
-// Layer output of this thread's row: bias + ReLU, BF16, into operand H.
-__device__ __forceinline__ void relu_to_h(uint8_t *smem, uint32_t t_lane, const float *bias) {
+// Layer output of this thread's row: bias + ReLU, BF16, into operand H
+// (the four loads of the 64 columns complete on one wait).
+__device__ __forceinline__ void relu_to_h(uint8_t *smem, uint32_t h_base, uint32_t t_lane, const float *bias) {
+    uint32_t raw[4][16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tmem_ld16(t_lane + 16 * q, raw[q]);
+    tmem_wait();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        float v[16];
-        tmem_ld16(t_lane + 16 * q, v);
         float lo[8], hi[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            lo[c] = fmaxf(v[c] + bias[16 * q + c], 0.0f);
-            hi[c] = fmaxf(v[8 + c] + bias[16 * q + 8 + c], 0.0f);
+            lo[c] = fmaxf(__uint_as_float(raw[q][c]) + bias[16 * q + c], 0.0f);
+            hi[c] = fmaxf(__uint_as_float(raw[q][8 + c]) + bias[16 * q + 8 + c], 0.0f);
         }
         const int r = threadIdx.x;
-        st_chunk(smem, SM_H + core_off(r, 16 * q, TC_ROWS), lo);
-        st_chunk(smem, SM_H + core_off(r, 16 * q + 8, TC_ROWS), hi);
+        st_chunk(smem, h_base + core_off(r, 16 * q, TC_ROWS), lo);
+        st_chunk(smem, h_base + core_off(r, 16 * q + 8, TC_ROWS), hi);
     }
 }
 
@@ -197,21 +199,22 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_infer_tc(int64_t n, const __
     const int tid = threadIdx.x, warp = tid >> 5;
     float *bias = reinterpret_cast<float *>(smem + SM_BIAS);
     float *mu = reinterpret_cast<float *>(smem + SM_NORM), *isd = mu + 32;
-    const uint32_t bar = sb + SM_BAR;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + SM_BAR + 8);
+    const uint32_t bar0 = sb + SM_BAR, bar1 = sb + SM_BAR + 8;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + SM_BAR + 16);
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         // the packed weights, biases and standardisation: one bulk copy (TMA)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(IMG_TC_BYTES) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar0), "r"(IMG_TC_BYTES) : "memory");
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                          sb + SM_W1),
-                     "l"(img), "r"(IMG_TC_BYTES), "r"(bar)
+                     "l"(img), "r"(IMG_TC_BYTES), "r"(bar0)
                      : "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sb + SM_BAR + 8),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sb + SM_BAR + 16),
                      "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -222,13 +225,12 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_infer_tc(int64_t n, const __
     tc_fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
-    bool ok = __syncthreads_and(bar_wait(bar, 0) ? 1 : 0) != 0;  // the weights have arrived
-    uint32_t phase = 1;
+    bool ok = __syncthreads_and(bar_wait(bar0, 0) ? 1 : 0) != 0;  // the weights have arrived
+    uint32_t ph[2] = {1u, 0u};  // next phase to wait for, per slot
 
-    const uint64_t ntile = (uint64_t)((n + TC_ROWS - 1) / TC_ROWS);
-    // this thread's feature row of the next tile, loaded one tile ahead
-    auto load_row = [&](uint64_t tl, uint4 (&q4)[4]) {
-        const int64_t rr = (int64_t)tl * TC_ROWS + tid;
+    const int64_t ntile = (n + TC_ROWS - 1) / TC_ROWS;
+    auto load_row = [&](int64_t tl, uint4 (&q4)[4]) {
+        const int64_t rr = tl * TC_ROWS + tid;
         if (tl < ntile && rr < n) {
             const uint4 *src = reinterpret_cast<const uint4 *>(x + rr * 32);
 #pragma unroll
@@ -238,101 +240,105 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_infer_tc(int64_t n, const __
             for (int q = 0; q < 4; ++q) q4[q] = make_uint4(0u, 0u, 0u, 0u);
         }
     };
-    uint4 cur[4];
-    load_row(blockIdx.x, cur);
-    for (uint64_t tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
-        const int64_t r = (int64_t)tile * TC_ROWS + tid;
-        uint4 nxt[4];
-        load_row(tile + gridDim.x, nxt);
-        // 1. standardised BF16 row into operand A of layer 1
-        {
-            float xv[32];
-            {
+    // standardised BF16 row into slot s as operand A of layer 1
+    auto stage = [&](int sl, const uint4 (&q4)[4]) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 w4 = cur[q];
-                    const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t w[4] = {q4[c].x, q4[c].y, q4[c].z, q4[c].w};
+            float v[8];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162 *>(&w[h]);
-                        xv[8 * q + 2 * h] = __low2float(b2);
-                        xv[8 * q + 2 * h + 1] = __high2float(b2);
-                    }
-                }
+            for (int h = 0; h < 4; ++h) {
+                __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162 *>(&w[h]);
+                const int kk = 8 * c + 2 * h;
+                v[2 * h] = (__low2float(b2) - mu[kk]) * isd[kk];  // columns 30, 31: isd = 0
+                v[2 * h + 1] = (__high2float(b2) - mu[kk + 1]) * isd[kk + 1];
             }
+            st_chunk(smem, sl * SM_SLOT + core_off(tid, 8 * c, TC_ROWS), v);
+        }
+    };
+    // operands of slot s visible to the tensor cores, then one thread issues
+    // layer `layer` of slot s and commits it to the slot's mbarrier
+    auto issue = [&](int sl, int layer) {
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a_base = sb + sl * SM_SLOT;
+            const int nk = layer == 0 ? 2 : 4;  // K / 16
+            const int N = layer == 2 ? 16 : 64;
+            const uint32_t b_base = sb + (layer == 0 ? SM_W1 : (layer == 1 ? SM_W2 : SM_W3));
+            for (int k = 0; k < nk; ++k) {
+                const uint64_t da = smem_desc(a_base + (uint32_t)(2 * k) * (TC_ROWS / 8) * 128, (TC_ROWS / 8) * 128, 128);
+                const uint64_t db = smem_desc(b_base + (uint32_t)(2 * k) * (N / 8) * 128, (N / 8) * 128, 128);
+                mma_bf16_tc(tmem + 64u * sl, da, db, instr_desc(N), k > 0 ? 1u : 0u);
+            }
+            mma_commit(sl == 0 ? bar0 : bar1);
+        }
+    };
+    // wait for slot s (a timed-out wait ends the work on every thread together)
+    auto wait_slot = [&](int sl) {
+        ok = __syncthreads_and(ok && bar_wait(sl == 0 ? bar0 : bar1, ph[sl]) ? 1 : 0) != 0;
+        ph[sl] ^= 1u;
+        tc_fence_after();
+        return ok;
+    };
+    auto finish = [&](int sl, int64_t tl) {
+        uint32_t raw[16];
+        tmem_ld16(t_lane + 64u * sl, raw);
+        tmem_wait();
+        const int64_t r = tl * TC_ROWS + tid;
+        if (tl < ntile && r < n) {
+            float l[4], mx = -3.4e38f;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                float v[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int kk = 8 * c + k;
-                    v[k] = (xv[kk] - mu[kk]) * isd[kk];  // columns 30, 31: isd = 0
-                }
-                st_chunk(smem, SM_X + core_off(tid, 8 * c, TC_ROWS), v);
+                l[c] = __uint_as_float(raw[c]) + bias[128 + c];
+                mx = fmaxf(mx, l[c]);
             }
+            float e[4], sum = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                e[c] = expf(l[c] - mx);
+                sum += e[c];
+            }
+            int best = 0;  // the first largest logit
+#pragma unroll
+            for (int c = 1; c < 4; ++c)
+                if (l[c] > l[best]) best = c;
+            const float pb = e[best] / sum;
+            if (logits)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) logits[r * 4 + c] = l[c];
+            if (cls) cls[r] = (int8_t)best;
+            if (conf) conf[r] = pb;
+            if (fallback && pb < threshold) fallback[atomicAdd(n_fallback, 1)] = (int32_t)r;
         }
-        // layers 1..3
+    };
+    // pairs of tiles: while the tensor cores work on one slot, the threads
+    // prepare or finish the other
+    for (int64_t t0 = 2 * (int64_t)blockIdx.x; t0 < ntile && ok; t0 += 2 * (int64_t)gridDim.x) {
+        const int64_t t1 = t0 + 1;
+        uint4 q0[4], q1[4];
+        load_row(t0, q0);
+        load_row(t1, q1);
+        stage(0, q0);
+        issue(0, 0);
+        stage(1, q1);
+        issue(1, 0);
 #pragma unroll 1
-        for (int layer = 0; layer < 3 && ok; ++layer) {
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t a_base = sb + (layer == 0 ? SM_X : SM_H);
-                const int nk = layer == 0 ? 2 : 4;         // K / 16
-                const int N = layer == 2 ? 16 : 64;
-                const uint32_t b_base = sb + (layer == 0 ? SM_W1 : (layer == 1 ? SM_W2 : SM_W3));
-                const uint32_t d = tmem;
-                for (int s = 0; s < nk; ++s) {
-                    const uint64_t da = smem_desc(a_base + (uint32_t)(2 * s) * (TC_ROWS / 8) * 128, (TC_ROWS / 8) * 128, 128);
-                    const uint64_t db = smem_desc(b_base + (uint32_t)(2 * s) * (N / 8) * 128, (N / 8) * 128, 128);
-                    mma_bf16_tc(d, da, db, instr_desc(N), s > 0 ? 1u : 0u);
-                }
-                mma_commit(bar);
-            }
-            // a timed-out wait ends the loop on every thread together
-            ok = __syncthreads_and(bar_wait(bar, phase) ? 1 : 0) != 0;
-            phase ^= 1u;
-            tc_fence_after();
-            if (!ok) break;
-            if (layer < 2) {
-                relu_to_h(smem, t_lane, bias + 64 * layer);
-            } else {
-                float v[16];
-                tmem_ld16(t_lane, v);
-                if (r < n) {
-                    float l[4], mx = -3.4e38f;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        l[c] = v[c] + bias[128 + c];
-                        mx = fmaxf(mx, l[c]);
-                    }
-                    float e[4], sum = 0.0f;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        e[c] = expf(l[c] - mx);
-                        sum += e[c];
-                    }
-                    int best = 0;  // the first largest logit
-#pragma unroll
-                    for (int c = 1; c < 4; ++c)
-                        if (l[c] > l[best]) best = c;
-                    const float pb = e[best] / sum;
-                    if (logits)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) logits[r * 4 + c] = l[c];
-                    if (cls) cls[r] = (int8_t)best;
-                    if (conf) conf[r] = pb;
-                    if (fallback && pb < threshold) fallback[atomicAdd(n_fallback, 1)] = (int32_t)r;
-                }
-            }
+        for (int layer = 1; layer < 3 && ok; ++layer) {
+            if (!wait_slot(0)) break;
+            relu_to_h(smem, 0, t_lane, bias + 64 * (layer - 1));
+            issue(0, layer);
+            if (!wait_slot(1)) break;
+            relu_to_h(smem, SM_SLOT, t_lane + 64u, bias + 64 * (layer - 1));
+            issue(1, layer);
         }
+        if (ok && wait_slot(0)) finish(0, t0);
+        if (ok && wait_slot(1)) finish(1, t1);
         tc_fence_before();
-        __syncthreads();  // the next tile overwrites the operands and accumulators
+        __syncthreads();  // the next pair overwrites the operands and accumulators
         tc_fence_after();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
     }
     if (!ok && tid == 0) latch_status(status, PPMD_ERR_TIMEOUT);
     tc_fence_before();
@@ -358,7 +364,8 @@ int mlp_infer_tc(ppmd_ctx *ctx, int64_t n, const __nv_bfloat16 *x, const float *
     if (!img) return PPMD_ERR_NOMEM;
     PPMD_LAUNCH(ctx, k_pack_tc, 32, 256, 0, params, img);
     const int64_t ntile = (n + TC_ROWS - 1) / TC_ROWS;
-    const int64_t grid = ntile < 148 * TC_CTAS_PER_SM ? ntile : 148 * TC_CTAS_PER_SM;
+    const int64_t npair = (ntile + 1) / 2;
+    const int64_t grid = npair < 148 * TC_CTAS_PER_SM ? npair : 148 * TC_CTAS_PER_SM;
     PPMD_LAUNCH(ctx, k_mlp_infer_tc, grid, TC_ROWS, SM_REQUEST, n, x, img, logits, cls, conf, threshold, fallback,
                 n_fallback, ctx->d_status);
     return check_launch(ctx, "mlp_infer_tc");
