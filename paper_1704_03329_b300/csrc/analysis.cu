@@ -781,20 +781,21 @@ int cna_subset_launch(ppmd_ctx *ctx, int64_t m_max, const int32_t *m_dev, const 
 // ---------------------------------------------------------------------
 constexpr int FEAT_WARPS = 4, FEAT_G = 8, FEAT_GROUPS = FEAT_WARPS * 32 / FEAT_G, FEAT_CAP = 64;
 
-__global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const int4 *__restrict__ xq,
-                                                              const double *__restrict__ pos64, SegTable st,
-                                                              const int32_t *__restrict__ nbr,
-                                                              const int32_t *__restrict__ cnt, int32_t max_nbr,
-                                                              int64_t si, int64_t sm, double rc2, float lo, float hi,
-                                                              double rb2, float blo, float bhi, float r_ref,
-                                                              float inv_span, YlmCoef K,
-                                                              const int32_t *__restrict__ out_idx,
-                                                              float *__restrict__ f32, __nv_bfloat16 *__restrict__ fb16,
-                                                              int32_t *status, unsigned long long *needed) {
-    // (u_a, d_a) and v_a as one 16-byte entry each: the eight lanes of a
-    // group read eight entries in one conflict-free phase
-    __shared__ float4 s_ud[FEAT_GROUPS][FEAT_CAP];
-    __shared__ float4 s_v[FEAT_GROUPS][FEAT_CAP];
+__global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, const int4 *__restrict__ xq,
+                                                                 const double *__restrict__ pos64, SegTable st,
+                                                                 const int32_t *__restrict__ nbr,
+                                                                 const int32_t *__restrict__ cnt, int32_t max_nbr,
+                                                                 int64_t si, int64_t sm, double rc2, float lo, float hi,
+                                                                 double rb2, float blo, float bhi, float r_ref,
+                                                                 float inv_span, YlmCoef K,
+                                                                 const int32_t *__restrict__ out_idx,
+                                                                 float *__restrict__ f32, __nv_bfloat16 *__restrict__ fb16,
+                                                                 int32_t *status, unsigned long long *needed) {
+    // The bonds of each group as (v_a, d_a), one 16-byte entry each (the
+    // eight lanes of a group read eight entries in one conflict-free phase):
+    // the bonded neighbours (r < r_ref) from the front, the other bonds from
+    // the back.
+    __shared__ float4 s_e[FEAT_GROUPS][FEAT_CAP];
     __shared__ float s_h[14][FEAT_WARPS * 32];  // private histogram of each lane, bin-major (no bank conflicts)
     __shared__ float s_f[FEAT_GROUPS][32];
     const int gl = threadIdx.x & (FEAT_G - 1), g = threadIdx.x / FEAT_G, shift = threadIdx.x & 31 & ~(FEAT_G - 1);
@@ -811,7 +812,7 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
     for (int k = 0; k < 14; ++k) hist[k * FEAT_WARPS * 32] = 0.0f;
 #pragma unroll
     for (int c = gl; c < 32; c += FEAT_G) s_f[g][c] = (c >= 2 && c < 16) ? 1.0f : 0.0f;
-    int32_t nu = 0, nbd = 0;
+    int32_t nu = 0, nbd = 0;  // bonds, bonded neighbours among them
     for (int32_t base = 0; base < deg; base += FEAT_G) {
         const int32_t k = base + gl;
         bool b = false, bb = false;
@@ -842,15 +843,9 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
         }
         const unsigned ball = __ballot_sync(gmask, b) >> shift, bbal = __ballot_sync(gmask, bb) >> shift;
         if (b) {
-            const int32_t a = nu + __popc(ball & lt);
-            if (a < FEAT_CAP) {
-                const float ir = rsqrtf(r2), r = r2 * ir;  // hardware estimates (~2 ulp)
-                s_ud[g][a] = make_float4(dx * ir, dy * ir, dz * ir, r);
-            }
-        }
-        if (bb) {
-            const int32_t a = nbd + __popc(bbal & lt);
-            if (a < FEAT_CAP) s_v[g][a] = make_float4(dx, dy, dz, 0.0f);
+            const float ir = rsqrtf(r2), r = r2 * ir;  // hardware estimates (~2 ulp)
+            const int32_t a = bb ? nbd + __popc(bbal & lt) : FEAT_CAP - 1 - (nu - nbd) - __popc(ball & ~bbal & lt);
+            if (a >= 0 && a < FEAT_CAP) s_e[g][a] = make_float4(dx, dy, dz, r);
         }
         nu += __popc(ball);
         nbd += __popc(bbal);
@@ -860,35 +855,58 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
             latch_status(status, PPMD_ERR_CAPACITY);
             latch_needed(needed, (unsigned long long)nu);
         }
-        nu = FEAT_CAP;
+        nbd = min(nbd, FEAT_CAP);
+        nu = FEAT_CAP;  // (entries overwritten; the call reports the error)
     }
-    nbd = min(nbd, FEAT_CAP);
+    const int32_t back = FEAT_CAP - nu;  // bond number q >= nbd is at back + q
     __syncwarp(gmask);
-    // Q4, Q6: each lane its bonds, moment sums reduced over the group
+    // Q4, Q6: each lane its bonds; unit vectors from the same r^2 and
+    // reciprocal root as the stored length
     float r4[5], i4[5], r6[7], i6[7];
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
         if (m < 5) r4[m] = i4[m] = 0.0f;
         r6[m] = i6[m] = 0.0f;
     }
-    for (int a = gl; a < nu; a += FEAT_G) {
-        const float4 u = s_ud[g][a];
-        boa_accumulate(K, u.x, u.y, u.z, r4, i4, r6, i6);
+    for (int q = gl; q < nu; q += FEAT_G) {
+        const float4 e = s_e[g][q < nbd ? q : back + q];
+        const float ir = rsqrtf(fmaf(e.x, e.x, fmaf(e.y, e.y, e.z * e.z)));
+        boa_accumulate(K, e.x * ir, e.y * ir, e.z * ir, r4, i4, r6, i6);
+    }
+    // group sums of the 22 moments (the imaginary parts of m = 0 vanish):
+    // reduce-scatter over the eight lanes, lane gl ends with moments
+    // 3 gl .. 3 gl + 2 of the list r4[0..4] i4[1..4] r6[0..6] i6[1..6] 0 0
+    float v[24];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) v[m] = r4[m];
+#pragma unroll
+    for (int m = 1; m < 5; ++m) v[4 + m] = i4[m];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) v[9 + m] = r6[m];
+#pragma unroll
+    for (int m = 1; m < 7; ++m) v[15 + m] = i6[m];
+    v[22] = v[23] = 0.0f;
+#pragma unroll
+    for (int h = 12; h >= 3; h >>= 1) {
+        const bool up = (gl & (h / 3)) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const float keep = up ? v[k + h] : v[k], send = up ? v[k] : v[k + h];
+            v[k] = keep + __shfl_xor_sync(gmask, send, h / 3);
+        }
     }
     float s4 = 0.0f, s6 = 0.0f;
 #pragma unroll
-    for (int m = 0; m < 7; ++m) {
+    for (int k = 0; k < 3; ++k) {
+        const int idx = 3 * gl + k;
+        const float sq = v[k] * v[k];
+        if (idx < 9) s4 += sq;
+        else s6 += sq;
+    }
 #pragma unroll
-        for (int o = FEAT_G / 2; o > 0; o >>= 1) {
-            if (m < 5) {
-                r4[m] += __shfl_xor_sync(gmask, r4[m], o);
-                i4[m] += __shfl_xor_sync(gmask, i4[m], o);
-            }
-            r6[m] += __shfl_xor_sync(gmask, r6[m], o);
-            i6[m] += __shfl_xor_sync(gmask, i6[m], o);
-        }
-        if (m < 5) s4 = fmaf(r4[m], r4[m], fmaf(i4[m], i4[m], s4));
-        s6 = fmaf(r6[m], r6[m], fmaf(i6[m], i6[m], s6));
+    for (int o = FEAT_G / 2; o > 0; o >>= 1) {
+        s4 += __shfl_xor_sync(gmask, s4, o);
+        s6 += __shfl_xor_sync(gmask, s6, o);
     }
     // chord histogram: the nbd (nbd - 1) / 2 pairs spread over the lanes,
     // tent weights added to the lane's own row
@@ -901,7 +919,7 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
         if (b * (b - 1) / 2 > pidx) --b;
         if ((b + 1) * b / 2 <= pidx) ++b;
         const int a = pidx - b * (b - 1) / 2;
-        const float4 va = s_v[g][a], vb = s_v[g][b];
+        const float4 va = s_e[g][a], vb = s_e[g][b];
         const float cx = va.x - vb.x, cy = va.y - vb.y, cz = va.z - vb.z;
         const float c2 = fmaxf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)), 1e-30f);
         const float chord = c2 * rsqrtf(c2);
@@ -913,15 +931,21 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
         hist[min(max(b0, 0), 13) * (FEAT_WARPS * 32)] += 1.0f - t;
         hist[min(max(b0 + 1, 0), 13) * (FEAT_WARPS * 32)] += t;
     }
-    // sorted bond lengths: the rank of each
-    for (int a = gl; a < nu; a += FEAT_G) {
-        const float da = s_ud[g][a].w;
-        int rank = 0;
-        for (int b = 0; b < nu; ++b) {
-            const float db = s_ud[g][b].w;
-            rank += (db < da) || (db == da && b < a);
+    // sorted bond lengths: the rank of each (ties ordered by slot), two
+    // bonds per lane per pass over the others
+    for (int q = gl; q < nu; q += 2 * FEAT_G) {
+        const int q2 = q + FEAT_G;
+        const int a1 = q < nbd ? q : back + q, a2 = q2 < nbd ? q2 : back + q2;
+        const float d1 = s_e[g][a1].w, d2 = q2 < nu ? s_e[g][a2].w : 3.4e38f;
+        int rank1 = 0, rank2 = 0;
+        for (int c = 0; c < nu; ++c) {
+            const int sl = c < nbd ? c : back + c;
+            const float dc = s_e[g][sl].w;
+            rank1 += (dc < d1) || (dc == d1 && sl < a1);
+            rank2 += (dc < d2) || (dc == d2 && sl < a2);
         }
-        if (rank < 14) s_f[g][2 + rank] = (da - r_ref) * inv_span;
+        if (rank1 < 14) s_f[g][2 + rank1] = (d1 - r_ref) * inv_span;
+        if (q2 < nu && rank2 < 14) s_f[g][2 + rank2] = (d2 - r_ref) * inv_span;
     }
     __syncwarp(gmask);
     for (int c = gl; c < 14; c += FEAT_G) {
@@ -939,18 +963,18 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32) k_features(int64_t n, const i
     }
     __syncwarp(gmask);
     const int64_t o = out_idx ? out_idx[i] : i;
-    const float4 v = make_float4(s_f[g][4 * gl], s_f[g][4 * gl + 1], s_f[g][4 * gl + 2], s_f[g][4 * gl + 3]);
+    const float4 fv = make_float4(s_f[g][4 * gl], s_f[g][4 * gl + 1], s_f[g][4 * gl + 2], s_f[g][4 * gl + 3]);
     if (f32) {
         float *dst = f32 + o * 30 + 4 * gl;
-        dst[0] = v.x;
-        dst[1] = v.y;
+        dst[0] = fv.x;
+        dst[1] = fv.y;
         if (gl < 7) {
-            dst[2] = v.z;
-            dst[3] = v.w;
+            dst[2] = fv.z;
+            dst[3] = fv.w;
         }
     }
     if (fb16) {
-        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(v.x, v.y), hi2 = __floats2bfloat162_rn(v.z, v.w);
+        const __nv_bfloat162 lo2 = __floats2bfloat162_rn(fv.x, fv.y), hi2 = __floats2bfloat162_rn(fv.z, fv.w);
         uint2 w2;
         w2.x = *reinterpret_cast<const uint32_t *>(&lo2);
         w2.y = *reinterpret_cast<const uint32_t *>(&hi2);
