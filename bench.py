@@ -489,28 +489,38 @@ def suite_classifier(args, L, ctx, stream):
     test = configs.classifier_boxes(51)
     dev = [(torch.from_numpy(b["pos"]).cuda(), b["box"]) for b in test]
     n = sum(p.shape[0] for p, _ in dev)
-    for p, b in dev[:1]:  # warm-up
-        L.ppmd_classify(ctx, p, b, mode=1, params=P, threshold=0.9)
-        L.ppmd_classify(ctx, p, b, mode=0, r_cna=R_CNA)
-    res_m, res_c = [], []
-    nfb = 0
+    # the 32 boxes as one box set: one pipeline for all of them
+    pos_all = torch.cat([p for p, _ in dev])
+    off = np.cumsum([0] + [p.shape[0] for p, _ in dev]).tolist()
+    bxs = [b for _, b in dev]
+    for _ in range(2):  # warm-up
+        L.ppmd_classify_boxes(ctx, pos_all, off, bxs, mode=1, params=P, threshold=0.9)
+        L.ppmd_classify_boxes(ctx, pos_all, off, bxs, mode=0, r_cna=R_CNA)
+    res = {}
 
     def run_mlp():
-        # asynchronous calls (no fallback count): one synchronisation at the end
-        for p, b in dev:
-            lab, _, _ = L.ppmd_classify(ctx, p, b, mode=1, params=P, threshold=0.9, want_confidence=False, count=False)
-            res_m.append(lab)
+        # asynchronous (no fallback count): the one synchronisation is after the timed region
+        res["mlp"] = L.ppmd_classify_boxes(ctx, pos_all, off, bxs, mode=1, params=P, threshold=0.9,
+                                           want_confidence=False, count=False)[0]
 
     def run_cna():
-        for p, b in dev:
-            lab, _, _ = L.ppmd_classify(ctx, p, b, mode=0, r_cna=R_CNA)
-            res_c.append(lab)
-    t_m, _ = _timed(stream, run_mlp)
-    t_c, _ = _timed(stream, run_cna)
+        res["cna"] = L.ppmd_classify_boxes(ctx, pos_all, off, bxs, mode=0, r_cna=R_CNA)[0]
+    t_m = min(_timed(stream, run_mlp)[0] for _ in range(3))
+    t_c = min(_timed(stream, run_cna)[0] for _ in range(3))
     ctx.sync()  # reports any list overflow of the asynchronous calls
-    for p, b in dev:  # fallback count, untimed
-        nfb += L.ppmd_classify(ctx, p, b, mode=1, params=P, threshold=0.9, want_confidence=False)[2]
-    agree = float((torch.cat(res_m) == torch.cat(res_c)).float().mean())
+
+    # the same work as one call per box (context: per-call latency of the small kernels)
+    def per_box(mode):
+        for p, b in dev:
+            if mode == 1:
+                L.ppmd_classify(ctx, p, b, mode=1, params=P, threshold=0.9, want_confidence=False, count=False)
+            else:
+                L.ppmd_classify(ctx, p, b, mode=0, r_cna=R_CNA)
+    t_m1, _ = _timed(stream, lambda: per_box(1))
+    t_c1, _ = _timed(stream, lambda: per_box(0))
+    ctx.sync()
+    nfb = L.ppmd_classify_boxes(ctx, pos_all, off, bxs, mode=1, params=P, threshold=0.9, want_confidence=False)[2]
+    agree = float((res["mlp"] == res["cna"]).float().mean())
     # the MLP kernel alone on the inference features (tensor-core roofline)
     feats = [L.ppmd_features(ctx, p, b, R_BOA, fp32=False, bf16=True)[1] for p, b in dev]
     xf = torch.cat(feats)
@@ -524,11 +534,15 @@ def suite_classifier(args, L, ctx, stream):
     except Exception:
         pass
     mlp_only = torch.cat([L.ppmd_mlp_forward(ctx, P, f).argmax(1).to(torch.int8) for f in feats])
+    res_c = res["cna"]
     return {"workload": "train: 32 structure boxes (4,096,000 atoms, noise U[0.01, 0.12] d_nn, seed 50), "
                         f"{args.epochs} epochs, batch 65536, AdamW lr 1e-3 wd 0.01; infer: 4,096,000 fresh atoms (seed 51)",
             "metric": "classified atoms/s (MLP + CNA fallback vs exact CNA)", "atoms": n,
             "mlp_fallback_atoms_per_s": n / t_m, "cna_atoms_per_s": n / t_c, "speedup_vs_cna": t_c / t_m,
-            "agreement_with_cna": agree, "mlp_only_agreement": float((mlp_only == torch.cat(res_c)).float().mean()),
+            "calls": "one box-set call (ppmd_classify_boxes) for the 32 boxes, best of 3",
+            "one_call_per_box": {"mlp_fallback_atoms_per_s": n / t_m1, "cna_atoms_per_s": n / t_c1,
+                                 "speedup_vs_cna": t_c1 / t_m1},
+            "agreement_with_cna": agree, "mlp_only_agreement": float((mlp_only == res_c).float().mean()),
             "fallback_fraction": nfb / n, "train_steps": step, "train_s": t_train, "loss_per_epoch": losses,
             "mlp_kernel": {"ms": t_f * 1e3, "achieved_tflops": flops / t_f / 1e12, "peak_tflops": peak,
                            "frac": flops / t_f / 1e12 / peak, "bound": "tensor (BF16, sustained peak of measured)"}}

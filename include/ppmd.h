@@ -194,6 +194,20 @@ int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, d
 int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
                  float *q4, float *q6, int32_t *n_nb, int8_t *label);
 
+/* ppmd_analyze over nbox independent periodic boxes in one pipeline (one
+ * binning, one list build and one launch per analysis for all of them):
+ * box b (boxes[b], host array) holds atoms atom_off[b] .. atom_off[b+1]-1
+ * of pos (atom_off: host int64 array of nbox + 1 offsets, atom_off[0] = 0,
+ * non-decreasing; n = atom_off[nbox] < 2^31).  Atoms of different boxes
+ * never interact.  Outputs and their layout as ppmd_analyze over the n
+ * atoms (caller order); every box must hold at least 3 cells of edge
+ * max(r_boa, r_cna) along each axis.  List capacity: the largest over the
+ * boxes.  With nbox > 1 the box table is copied from pageable host memory,
+ * which waits for earlier work on the context stream; otherwise
+ * asynchronous, as ppmd_analyze. */
+int ppmd_analyze_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes,
+                       double r_boa, double r_cna, float *q4, float *q6, int32_t *n_nb, int8_t *label);
+
 /* Adaptive CNA (the extension of CNA that Sec. 4.2 cites, Stukowski 2012):
  * every atom sets its own bond cutoff from its N nearest neighbours
  * (distances d_1 <= ... <= d_N over the list at r_list, ties by index):
@@ -273,6 +287,12 @@ int ppmd_mlp_train_step(ppmd_ctx *ctx, float *params, float *m, float *v, int64_
  * synchronising call). */
 int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t n, const ppmd_box *box, double r_feat, double r_cna,
                   const float *params, float threshold, int8_t *label, float *confidence, int64_t *n_fallback);
+/* ppmd_classify over nbox independent boxes in one pipeline (box set as
+ * for ppmd_analyze_boxes); labels and confidences of all n = atom_off[nbox]
+ * atoms in the caller's order, n_fallback the total over the boxes. */
+int ppmd_classify_boxes(ppmd_ctx *ctx, int mode, const double *pos, int64_t nbox, const int64_t *atom_off,
+                        const ppmd_box *boxes, double r_feat, double r_cna, const float *params, float threshold,
+                        int8_t *label, float *confidence, int64_t *n_fallback);
 
 /* ------------------------------------------------------------------ */
 /* Time stepping (Algorithm 6 driven by the list-reuse policy of Sec. 3.5,

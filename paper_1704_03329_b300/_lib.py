@@ -80,6 +80,8 @@ _SIGS = {
     "ppmd_mlp_adamw": (_I, [_P, _P, _P, _P, _P, _I64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float]),
     "ppmd_mlp_train_step": (_I, [_P, _P, _P, _P, _I64, _P, _P, _I64, C.c_float, C.c_float, _P]),
     "ppmd_classify": (_I, [_P, _I, _P, _I64, C.POINTER(Box), _D, _D, _P, C.c_float, _P, _P, C.POINTER(_I64)]),
+    "ppmd_analyze_boxes": (_I, [_P, _P, _I64, _P, _P, _D, _D, _P, _P, _P, _P]),
+    "ppmd_classify_boxes": (_I, [_P, _I, _P, _I64, _P, _P, _D, _D, _P, C.c_float, _P, _P, C.POINTER(_I64)]),
     "ppmd_md_create": (_I, [_P, C.POINTER(_P), _I64, _P, _P, _P, C.POINTER(MDParams)]),
     "ppmd_md_destroy": (_I, [_P]),
     "ppmd_md_set_state": (_I, [_P, _P, _P]),
@@ -274,6 +276,38 @@ def ppmd_analyze(ctx: Context, pos, box, r_boa=1.5, r_cna=None, boa=True, cna=Tr
     return out
 
 
+def _box_set(atom_off, boxes):
+    """Host tables of a box set: int64 offsets [nbox + 1] and the boxes."""
+    nbox = len(atom_off) - 1
+    off = (C.c_int64 * (nbox + 1))(*[int(x) for x in atom_off])
+    bx = (Box * max(nbox, 1))()
+    for b in range(nbox):
+        for d in range(3):
+            bx[b].L[d] = float(boxes[b][d])
+    return nbox, off, bx
+
+
+def ppmd_analyze_boxes(ctx: Context, pos, atom_off, boxes, r_boa=1.5, r_cna=None, boa=True, cna=True, out=None):
+    """ppmd_analyze over several independent boxes (box b: atoms atom_off[b] ..
+    atom_off[b + 1] - 1 of pos) in one pipeline; same outputs over all atoms."""
+    n = pos.shape[0]
+    dev = pos.device
+    out = out or {}
+    if boa:
+        out.setdefault("q4", torch.empty(n, dtype=torch.float32, device=dev))
+        out.setdefault("q6", torch.empty(n, dtype=torch.float32, device=dev))
+        out.setdefault("n_nb", torch.empty(n, dtype=torch.int32, device=dev))
+    if cna:
+        out.setdefault("label", torch.empty(n, dtype=torch.int8, device=dev))
+    nbox, off, bx = _box_set(atom_off, boxes)
+    if off[nbox] != n:
+        raise ValueError("atom_off[-1] must equal the number of atoms")
+    ctx.check(_lib.ppmd_analyze_boxes(ctx.h, _ptr(pos), nbox, C.cast(off, _P), C.cast(bx, _P), float(r_boa or 0.0),
+                                      float(r_cna or 0.0), _opt(out.get("q4")), _opt(out.get("q6")),
+                                      _opt(out.get("n_nb")), _opt(out.get("label"))))
+    return out
+
+
 def ppmd_acna(ctx: Context, pos, box, r_list=1.8, want_rcut=True):
     """Adaptive CNA labels int8 [n] and the local cutoffs float64 [n, 2] (caller order)."""
     n = pos.shape[0]
@@ -336,6 +370,23 @@ def ppmd_classify(ctx: Context, pos, box, mode=1, params=None, threshold=0.9, r_
     b = _box(box)
     ctx.check(_lib.ppmd_classify(ctx.h, int(mode), _ptr(pos), n, C.byref(b), float(r_feat), float(r_cna), _opt(params),
                                  float(threshold), _ptr(lab), _opt(conf), C.byref(nfb) if count else None))
+    return lab, conf, (nfb.value if count else None)
+
+
+def ppmd_classify_boxes(ctx: Context, pos, atom_off, boxes, mode=1, params=None, threshold=0.9, r_feat=1.5,
+                        r_cna=1.433625, want_confidence=True, count=True):
+    """ppmd_classify over several independent boxes in one pipeline (box set as
+    ppmd_analyze_boxes); labels, confidences and the total fallback count."""
+    n = pos.shape[0]
+    lab = torch.empty(n, dtype=torch.int8, device=pos.device)
+    conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode == 1) else None
+    nfb = _I64(0)
+    nbox, off, bx = _box_set(atom_off, boxes)
+    if off[nbox] != n:
+        raise ValueError("atom_off[-1] must equal the number of atoms")
+    ctx.check(_lib.ppmd_classify_boxes(ctx.h, int(mode), _ptr(pos), nbox, C.cast(off, _P), C.cast(bx, _P), float(r_feat),
+                                       float(r_cna), _opt(params), float(threshold), _ptr(lab), _opt(conf),
+                                       C.byref(nfb) if count else None))
     return lab, conf, (nfb.value if count else None)
 
 

@@ -1063,6 +1063,94 @@ int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box 
     return PPMD_OK;
 }
 
+__global__ void k_seg_of(int64_t n, const int64_t *__restrict__ off, int32_t nbox, int32_t *__restrict__ seg_of) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = nbox - 1;  // the last box with off[b] <= i
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        seg_of[i] = lo;
+    }
+}
+
+int check_boxes(ppmd_ctx *ctx, int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes, const char *who) {
+    if (nbox < 1 || !atom_off || !boxes) return set_error(ctx, PPMD_ERR_INVALID, "%s: bad box set", who);
+    if (atom_off[0] != 0) return set_error(ctx, PPMD_ERR_INVALID, "%s: atom_off[0] must be 0", who);
+    for (int64_t b = 0; b < nbox; ++b)
+        if (atom_off[b + 1] < atom_off[b]) return set_error(ctx, PPMD_ERR_INVALID, "%s: atom_off decreases at %lld", who, (long long)b);
+    if (atom_off[nbox] >= (int64_t)1 << 31) return set_error(ctx, PPMD_ERR_INVALID, "%s: too many atoms", who);
+    return PPMD_OK;
+}
+
+int32_t snapshot_capacity_boxes(int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes, double r_list) {
+    int32_t cap = 0;
+    for (int64_t b = 0; b < nbox; ++b)
+        cap = std::max(cap, snapshot_capacity(atom_off[b + 1] - atom_off[b], &boxes[b], r_list));
+    return cap;
+}
+
+int sorted_snapshot_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const int64_t *atom_off,
+                          const ppmd_box *boxes, double r_list, int32_t max_nbr, Snapshot &s) {
+    if (nbox == 1) return sorted_snapshot(ctx, pos, atom_off[1], boxes, r_list, max_nbr, s);
+    const int64_t n = atom_off[nbox];
+    s.n = n;
+    std::vector<Seg> segs((size_t)nbox);
+    int64_t ncell = 0;
+    double Lmax = 0;
+    for (int64_t b = 0; b < nbox; ++b) {
+        Seg &S = segs[(size_t)b];
+        PPMD_TRY(make_seg(ctx, S, boxes[b].L, r_list, r_list));
+        S.cell0 = (int32_t)ncell;
+        S.atom0 = atom_off[b];
+        S.atom1 = atom_off[b + 1];
+        ncell += (int64_t)S.nc[0] * S.nc[1] * S.nc[2];
+        if (ncell >= (int64_t)1 << 31) return set_error(ctx, PPMD_ERR_BOX, "too many cells");
+        for (int d = 0; d < 3; ++d) Lmax = fmax(Lmax, boxes[b].L[d]);
+    }
+    s.Lmax = Lmax;
+    std::vector<Brick> bl;
+    const int32_t stage_cap = make_bricks(segs, bl);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    Seg *d_segs = (Seg *)scratch(ctx, S_SEGS, sizeof(Seg) * (size_t)nbox);
+    int64_t *d_off = (int64_t *)scratch(ctx, S_SEGOFF, sizeof(int64_t) * (size_t)(nbox + 1));
+    int32_t *seg_of = (int32_t *)scratch(ctx, S_SEGOF, sizeof(int32_t) * nn);
+    Brick *d_bricks = (Brick *)scratch(ctx, S_BRICKS, sizeof(Brick) * (bl.empty() ? 1 : bl.size()));
+    int32_t *cell0 = (int32_t *)scratch(ctx, S_CELLS0, sizeof(int32_t) * nn);
+    s.cell_start = (int32_t *)scratch(ctx, S_CELLS1, sizeof(int32_t) * (size_t)(ncell + 1));
+    s.perm = (int32_t *)scratch(ctx, S_CELLS2, sizeof(int32_t) * nn);
+    s.pos = (double *)scratch(ctx, S_SORTPOS, sizeof(double) * 3 * nn);
+    s.xq = (int4 *)scratch(ctx, S_AUX0, sizeof(int4) * nn);
+    if (!d_segs || !d_off || !seg_of || !d_bricks || !cell0 || !s.cell_start || !s.perm || !s.pos || !s.xq)
+        return PPMD_ERR_NOMEM;
+    // tables from pageable host memory (the copies are staged before they return)
+    cudaStream_t st = ctx->stream;
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_segs, segs.data(), sizeof(Seg) * (size_t)nbox, cudaMemcpyHostToDevice, st), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_off, atom_off, sizeof(int64_t) * (size_t)(nbox + 1), cudaMemcpyHostToDevice, st), "copy"));
+    if (!bl.empty())
+        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice, st), "copy"));
+    s.st.d = d_segs;
+    s.st.nseg = (int32_t)nbox;
+    s.st.one = segs[0];
+    if (n > 0) PPMD_LAUNCH(ctx, k_seg_of, div_up(n, 256), 256, 0, n, d_off, (int32_t)nbox, seg_of);
+    // bin and sort by cell: cells of box b follow those of box b - 1, so the
+    // sorted atoms of box b keep the positions atom_off[b] .. atom_off[b + 1]
+    // - 1 and seg_of holds for the sorted order as well
+    PPMD_TRY(bin_atoms(ctx, pos, n, s.st, seg_of, ncell, false, cell0, s.cell_start, s.perm, true));
+    if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos, div_up(n, 256), 256, 0, n, s.perm, pos, s.pos);
+    PPMD_TRY(prep_fixed(ctx, s.pos, n, s.st, seg_of, s.xq, nullptr));
+    s.ld = (n + 31) / 32 * 32;
+    PPMD_TRY(neigh_brick_setup(ctx, max_nbr));
+    s.max_nbr = max_nbr;
+    s.nbr = (int32_t *)scratch(ctx, S_NBR, sizeof(int32_t) * (size_t)s.ld * (size_t)max_nbr);
+    s.cnt = (int32_t *)scratch(ctx, S_NBRCNT, sizeof(int32_t) * nn);
+    if (!s.nbr || !s.cnt) return PPMD_ERR_NOMEM;
+    PPMD_TRY(build_list_bricks(ctx, (int64_t)bl.size(), d_bricks, BrickShape{1, 1, 1}, s.xq, s.pos, s.st, s.cell_start,
+                               s.nbr, s.ld, s.cnt, max_nbr, stage_cap));
+    return PPMD_OK;
+}
+
 }  // namespace ppmd
 
 using namespace ppmd;
@@ -1105,9 +1193,13 @@ extern "C" int ppmd_cna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_
     return cna_launch(ctx, n, xq, pos, st, nbr, nbr_count, max_nbr, 0, r_cut, Lmax, nullptr, triplets, label);
 }
 
-extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
-                            float *q4, float *q6, int32_t *n_nb, int8_t *label) {
-    if (!ctx || !box || n < 0 || (n > 0 && !pos)) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_analyze: bad argument");
+extern "C" int ppmd_analyze_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const int64_t *atom_off,
+                                  const ppmd_box *boxes, double r_boa, double r_cna, float *q4, float *q6, int32_t *n_nb,
+                                  int8_t *label) {
+    if (!ctx) return PPMD_ERR_INVALID;
+    PPMD_TRY(check_boxes(ctx, nbox, atom_off, boxes, "ppmd_analyze"));
+    const int64_t n = atom_off[nbox];
+    if (n > 0 && !pos) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_analyze: bad argument");
     const bool want_boa = q4 || q6 || n_nb;
     const bool want_cna = label != nullptr;
     if ((want_boa && !(r_boa > 0)) || (want_cna && !(r_cna > 0)))
@@ -1117,12 +1209,20 @@ extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const p
     if (!(r_list > 0)) return PPMD_OK;
     // asynchronous: a list overflow stays latched for the next synchronising call
     Snapshot s;
-    PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_list, snapshot_capacity(n, box, r_list), s));
+    PPMD_TRY(sorted_snapshot_boxes(ctx, pos, nbox, atom_off, boxes, r_list,
+                                   snapshot_capacity_boxes(nbox, atom_off, boxes, r_list), s));
     if (want_boa)
         PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_boa, s.Lmax, s.perm, q4, q6, n_nb));
     if (want_cna)
         PPMD_TRY(cna_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, s.perm, nullptr, label));
     return check_launch(ctx, "ppmd_analyze");
+}
+
+extern "C" int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_boa, double r_cna,
+                            float *q4, float *q6, int32_t *n_nb, int8_t *label) {
+    if (!ctx || !box || n < 0) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_analyze: bad argument");
+    const int64_t off[2] = {0, n};
+    return ppmd_analyze_boxes(ctx, pos, 1, off, box, r_boa, r_cna, q4, q6, n_nb, label);
 }
 
 extern "C" int ppmd_acna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list,

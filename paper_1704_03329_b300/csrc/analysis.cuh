@@ -38,6 +38,15 @@ int boa_otf_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64
 int64_t boa_otf_blocks(int64_t n);
 int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_list, int32_t max_nbr,
                     Snapshot &s);
+// The same over nbox independent boxes (box b holds the caller's atoms
+// atom_off[b] .. atom_off[b + 1] - 1; atom_off and boxes in host memory),
+// one segment per box: the atoms stay grouped by box in the sorted order.
+int sorted_snapshot_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const int64_t *atom_off,
+                          const ppmd_box *boxes, double r_list, int32_t max_nbr, Snapshot &s);
+// Largest snapshot_capacity over the boxes.
+int32_t snapshot_capacity_boxes(int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes, double r_list);
+// Checks a box set: nbox >= 1, atom_off[0] = 0, non-decreasing, total < 2^31.
+int check_boxes(ppmd_ctx *ctx, int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes, const char *who);
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
                const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
                float *q6, int32_t *nnb);

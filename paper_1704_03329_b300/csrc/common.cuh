@@ -43,6 +43,10 @@ enum ScratchSlot {
     S_AUX1,
     S_AUX2,
     S_AUX3,
+    S_SEGS,    // analysis of several boxes: segment table, atom offsets,
+    S_SEGOFF,  // segment of each atom, bricks
+    S_SEGOF,
+    S_BRICKS,
     S_NSLOTS
 };
 

@@ -706,22 +706,25 @@ __global__ void k_write_labels(int64_t n, const int32_t *__restrict__ perm, cons
 
 }  // namespace ppmd
 
-extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t n, const ppmd_box *box, double r_feat,
-                             double r_cna, const float *params, float threshold, int8_t *label, float *confidence,
-                             int64_t *n_fallback) {
-    if (!ctx || !box || n < 0 || (n > 0 && (!pos || !label)) || (mode != 0 && mode != 1) || (mode == 1 && !params) ||
-        !(r_cna > 0) || (mode == 1 && !(r_feat >= r_cna)))
+extern "C" int ppmd_classify_boxes(ppmd_ctx *ctx, int mode, const double *pos, int64_t nbox, const int64_t *atom_off,
+                                   const ppmd_box *boxes, double r_feat, double r_cna, const float *params, float threshold,
+                                   int8_t *label, float *confidence, int64_t *n_fallback) {
+    if (!ctx) return PPMD_ERR_INVALID;
+    PPMD_TRY(check_boxes(ctx, nbox, atom_off, boxes, "ppmd_classify"));
+    const int64_t n = atom_off[nbox];
+    if ((n > 0 && (!pos || !label)) || (mode != 0 && mode != 1) || (mode == 1 && !params) || !(r_cna > 0) ||
+        (mode == 1 && !(r_feat >= r_cna)))
         return set_error(ctx, PPMD_ERR_INVALID, "ppmd_classify: bad argument");
     cudaSetDevice(ctx->device);
     if (mode == 0) {
         if (n_fallback) *n_fallback = n;
-        return ppmd_analyze(ctx, pos, n, box, 0.0, r_cna, nullptr, nullptr, nullptr, label);
+        return ppmd_analyze_boxes(ctx, pos, nbox, atom_off, boxes, 0.0, r_cna, nullptr, nullptr, nullptr, label);
     }
     const size_t nn = (size_t)(n > 0 ? n : 1);
-    int32_t max_nbr = snapshot_capacity(n, box, r_feat);
+    int32_t max_nbr = snapshot_capacity_boxes(nbox, atom_off, boxes, r_feat);
     for (int attempt = 0;; ++attempt) {
         Snapshot s;
-        PPMD_TRY(sorted_snapshot(ctx, pos, n, box, r_feat, max_nbr, s));
+        PPMD_TRY(sorted_snapshot_boxes(ctx, pos, nbox, atom_off, boxes, r_feat, max_nbr, s));
         __nv_bfloat16 *feat = (__nv_bfloat16 *)scratch(ctx, S_TMP0, sizeof(__nv_bfloat16) * 32 * nn);
         int8_t *cls = (int8_t *)scratch(ctx, S_TMP1, nn + 16);
         float *conf_s = (float *)scratch(ctx, S_TMP2, sizeof(float) * nn);
@@ -744,4 +747,13 @@ extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t
         *n_fallback = hfb;
         return rc;
     }
+}
+
+extern "C" int ppmd_classify(ppmd_ctx *ctx, int mode, const double *pos, int64_t n, const ppmd_box *box, double r_feat,
+                             double r_cna, const float *params, float threshold, int8_t *label, float *confidence,
+                             int64_t *n_fallback) {
+    if (!ctx || !box || n < 0) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_classify: bad argument");
+    const int64_t off[2] = {0, n};
+    return ppmd_classify_boxes(ctx, mode, pos, 1, off, box, r_feat, r_cna, params, threshold, label, confidence,
+                               n_fallback);
 }
