@@ -241,6 +241,50 @@ def run_ours(args):
                 "kernel_ms": round(f_ms, 5), "algorithmic_bytes_per_launch": alg_bytes,
                 "pairs_listed_per_atom": round(pairs / n, 2)}
 
+    # ---- list-free pair loop (no neighbour list) on the same positions -----
+    pos_now = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    md.get_state(pos_now)
+    L.ppmd_lj_forces_cells(ctx, pos_now, box, prec=L.FP32, want_energy=False)
+    torch.cuda.synchronize()
+    RL = 10
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(RL):
+        L.ppmd_lj_forces_cells(ctx, pos_now, box, prec=L.FP32, want_energy=False)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    lf_ms = h0.elapsed_time(h1) / RL
+    list_free = {"call": "ppmd_lj_forces_cells (FP32: binning, sort by cell, 27-cell sweep; no list)",
+                 "ms_per_call": round(lf_ms, 4), "atoms_per_s": n / (lf_ms * 1e-3),
+                 "vs_list_pair_loop_ms": round(f_ms, 4), "vs_md_step_ms": round(ms / K, 4)}
+
+    # ---- half list (Newton's third law) against the full list: the granular
+    # force calls on the same positions and list cutoff --------------------
+    nc_, _, start_, atoms_ = L.ppmd_build_cells(ctx, pos_now, box, 2.8)
+    nbr_f, cnt_f = L.ppmd_build_neighbours(ctx, pos_now, box, 2.8, start_, atoms_, nc_, 128)
+    half, hcnt = L.ppmd_half_list(ctx, pos_now, box, nbr_f, cnt_f)
+
+    def time_calls(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    full_ms = time_calls(lambda: L.ppmd_lj_forces(ctx, pos_now, box, nbr_f, cnt_f, prec=L.FP32, want_energy=False))
+    half_ms = time_calls(lambda: L.ppmd_lj_forces_newton3(ctx, pos_now, box, half, hcnt, prec=L.FP32,
+                                                          want_energy=False))
+    newton3 = {"calls": "ppmd_lj_forces (full list) vs ppmd_lj_forces_newton3 (half list, atomic j updates), FP32, "
+                        "list 2.8 in caller order",
+               "full_list_ms": round(full_ms, 4), "half_list_ms": round(half_ms, 4),
+               "half_vs_full_speedup": round(full_ms / half_ms, 3),
+               "listed_pairs_per_atom": {"full": round(float(cnt_f.sum()) / n, 2),
+                                         "half": round(float(hcnt.sum()) / n, 2)}}
+    del nbr_f, cnt_f, half, hcnt, start_, atoms_
+
     # ---- plain FP64 GPU path on the same workload -------------------------
     md64 = make_md(L.FP64)
     md64.set_state(pos_d, vel_d)
@@ -291,6 +335,7 @@ def run_ours(args):
             "clocks": clocks,
             "fp64_gpu_path": {"value": value64, "unit": UNIT, "steps": K64,
                               "fp32_speedup": value / world / value64},
+            "list_free_forces": list_free, "newton3_half_list": newton3,
             "md_info": {"max_disp": info["max_disp"], "skin_warning": info["status"] == L.WARN_SKIN,
                         "total_energy_drift_per_atom": drift},
             "impl": "ours"}

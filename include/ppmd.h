@@ -144,6 +144,47 @@ int ppmd_lj_forces(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *
                    const int32_t *nbr, const int32_t *nbr_count, int32_t max_nbr, ppmd_prec prec, double *force,
                    double *e_atom, double *e_total, double *virial);
 
+/* The same forces, per-atom energies, U and W as ppmd_lj_forces, without a
+ * neighbour list: the cell structure of Sec. 3.5 is swept directly and no
+ * neighbour matrix W is built or read (the role of the layer algorithm that
+ * Sec. 3.5 cites for cell-based codes).  The call bins pos into cells of
+ * edge >= rc (at least three per axis, rc < L/2: else PPMD_ERR_BOX), sorts
+ * the atoms by cell in scratch memory, and every atom sweeps the 27 cells
+ * around its own (8 lanes per atom).  Cutoff decisions are exact (FP32 test,
+ * FP64 re-test inside the band), as in ppmd_lj_forces; prec, outputs
+ * (caller order, device memory), INC_ZERO semantics and NULL options as
+ * there.  Asynchronous. */
+int ppmd_lj_forces_cells(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, const ppmd_lj_params *lj,
+                         ppmd_prec prec, double *force, double *e_atom, double *e_total, double *virial);
+
+/* Half neighbour list (Newton's third law; Sec. 2 on write conflicts):
+ * half[i][0..half_count[i]) = the entries j of row i of the full row-major
+ * list nbr [n][max_nbr] (as ppmd_build_neighbours writes it, for the same
+ * pos and box) whose minimum-image displacement r_j - r_i, in the 32-bit
+ * fixed-point box coordinates, is positive in the order (z, y, x): the
+ * first non-zero component decides.  These integer differences are exactly
+ * antisymmetric, so every listed pair is kept by exactly one of its atoms,
+ * and rows hold about half of the full length in any atom order (a pair of
+ * coincident atoms is dropped).  half: device int32 [n][max_half]; a row
+ * with more than max_half entries latches PPMD_ERR_CAPACITY with the length
+ * needed (reported by the next synchronising call, e.g. ppmd_status).
+ * Asynchronous. */
+int ppmd_half_list(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, const int32_t *nbr,
+                   const int32_t *nbr_count, int32_t max_nbr, int32_t *half, int32_t *half_count, int32_t max_half);
+
+/* The forces, per-atom energies, U and W of ppmd_lj_forces from a half
+ * list (ppmd_half_list): each unordered pair is evaluated once, by the atom
+ * whose row holds it, and its force and half of its energy go to both
+ * atoms (the other through atomic adds).  Same arguments, outputs and exact
+ * cutoff decisions as ppmd_lj_forces.  PPMD_FP32: single-precision pair
+ * terms, each atom's own share in compensated sums and the shares from its
+ * neighbours through FP32 atomic adds, so the last bits of F and e_i vary
+ * with the order in which the GPU performs those adds; PPMD_FP64: double
+ * precision with double atomic adds.  Asynchronous. */
+int ppmd_lj_forces_newton3(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, const ppmd_lj_params *lj,
+                           const int32_t *half, const int32_t *half_count, int32_t max_half, ppmd_prec prec,
+                           double *force, double *e_atom, double *e_total, double *virial);
+
 /* Velocity Verlet particle loops, Algorithm 6 and Listings
  * "position_update" / "velocity_update":
  *   phase 1 (line 6): v += dt/(2m) F;  r += dt v;  r wrapped into the box

@@ -63,6 +63,10 @@ _SIGS = {
     "ppmd_build_neighbours": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, C.POINTER(_I32), _P, _P, _I32,
                                    C.POINTER(_I32)]),
     "ppmd_lj_forces": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _P, _P, _I32, _I, _P, _P, _P, _P]),
+    "ppmd_lj_forces_cells": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _I, _P, _P, _P, _P]),
+    "ppmd_half_list": (_I, [_P, _P, _I64, C.POINTER(Box), _P, _P, _I32, _P, _P, _I32]),
+    "ppmd_lj_forces_newton3": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _P, _P, _I32, _I, _P, _P, _P,
+                                    _P]),
     "ppmd_verlet_step": (_I, [_P, _I, _P, _P, _P, _I64, C.POINTER(Box), _D, _D]),
     "ppmd_kinetic_energy": (_I, [_P, _P, _I64, _D, _P]),
     "ppmd_boa_q46": (_I, [_P, _P, _I64, C.POINTER(Box), _D, _P, _P, _I32, _P, _P, _P]),
@@ -216,6 +220,53 @@ def ppmd_lj_forces(ctx: Context, pos, box, nbr, nbr_count, rc=2.5, eps=1.0, sigm
                                int(prec), _ptr(F), _ptr(e) if e is not None else None, _ptr(tot[0:1]),
                                C.c_void_p(tot.data_ptr() + 8))
     ctx.check(code)
+    return F, e, tot
+
+
+def ppmd_lj_forces_cells(ctx: Context, pos, box, rc=2.5, eps=1.0, sigma=1.0, shift=0.0, prec=FP32, want_energy=True):
+    """List-free pair loop (cells of edge >= rc swept directly, no neighbour
+    list): forces [n,3] f64, per-atom energies [n] f64, device scalars (U, W)."""
+    n = pos.shape[0]
+    dev = pos.device
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    e = torch.empty(n, dtype=torch.float64, device=dev) if want_energy else None
+    tot = torch.zeros(2, dtype=torch.float64, device=dev)
+    p = LJParams(eps, sigma, rc, shift)
+    b = _box(box)
+    code = _lib.ppmd_lj_forces_cells(ctx.h, _ptr(pos), n, C.byref(b), C.byref(p), int(prec), _ptr(F),
+                                     _ptr(e) if e is not None else None, _ptr(tot[0:1]), C.c_void_p(tot.data_ptr() + 8))
+    ctx.check(code)
+    return F, e, tot
+
+
+def ppmd_half_list(ctx: Context, pos, box, nbr, nbr_count, max_half=None):
+    """Half list of a full row-major list [n, max_nbr]: each pair kept by the
+    atom from which the other lies in the upper half space (z, y, x order)."""
+    n, max_nbr = nbr.shape[0], (nbr.shape[1] if nbr.dim() == 2 else 0)
+    max_half = (max_nbr + 1) // 2 + 8 if max_half is None else max_half
+    half = torch.empty((n, max_half), dtype=torch.int32, device=nbr.device)
+    hcnt = torch.empty(n, dtype=torch.int32, device=nbr.device)
+    b = _box(box)
+    ctx.check(_lib.ppmd_half_list(ctx.h, _ptr(pos), n, C.byref(b), _ptr(nbr), _ptr(nbr_count), int(max_nbr), _ptr(half),
+                                  _ptr(hcnt), int(max_half)))
+    return half, hcnt
+
+
+def ppmd_lj_forces_newton3(ctx: Context, pos, box, half, half_count, rc=2.5, eps=1.0, sigma=1.0, shift=0.0, prec=FP32,
+                           want_energy=True):
+    """Forces [n,3] f64, per-atom energies [n] f64 and device scalars (U, W)
+    from a half list (each pair once, Newton's third law)."""
+    n = pos.shape[0]
+    dev = pos.device
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    e = torch.empty(n, dtype=torch.float64, device=dev) if want_energy else None
+    tot = torch.zeros(2, dtype=torch.float64, device=dev)
+    p = LJParams(eps, sigma, rc, shift)
+    b = _box(box)
+    max_half = half.shape[1] if half.dim() == 2 else 0
+    ctx.check(_lib.ppmd_lj_forces_newton3(ctx.h, _ptr(pos), n, C.byref(b), C.byref(p), _ptr(half), _ptr(half_count),
+                                          int(max_half), int(prec), _ptr(F), _ptr(e) if e is not None else None,
+                                          _ptr(tot[0:1]), C.c_void_p(tot.data_ptr() + 8)))
     return F, e, tot
 
 

@@ -149,6 +149,100 @@ def test_lj_fp32_parity(L, ctx, case):
     assert abs(tot[0] - Uo) / len(pos) <= 1e-6 * abs(Uo) / len(pos)
 
 
+CELL_CASES = dict(CASES, three_cells=lambda: (dict(zip(("pos", "box"), random_box(300, [7.6, 8.1, 9.9], 5, cutoffs=(2.5,),
+                                                                                  margin=1e-6, min_dist=1.0))), 2.5))
+
+
+@pytest.mark.parametrize("case", list(CELL_CASES))
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_lj_cells_parity(L, ctx, case, prec):
+    """List-free pair loop: the oracle's forces, energies and totals at the
+    tolerances of the list-based loop of the same precision (three cells per
+    axis: every row of the sweep wraps)."""
+    c, r = CELL_CASES[case]()
+    pos, box = c["pos"], c["box"]
+    offs, nbr_o = oracle.neighbours_cells(pos, box, r)
+    Fo, eo, Uo, Wo = oracle.lj(pos, box, offs, nbr_o)
+    F, e, tot = L.ppmd_lj_forces_cells(ctx, cu(pos), box, prec=getattr(L, prec))
+    F, e, tot = F.cpu().numpy(), e.cpu().numpy(), tot.cpu().numpy()
+    if prec == "FP64":
+        assert force_err(F, Fo) <= 1e-12
+        assert np.abs(e - eo).max() <= 1e-12 * np.abs(eo).mean()
+        assert abs(tot[0] - Uo) <= 1e-12 * abs(Uo)
+        assert abs(tot[1] - Wo) <= 1e-12 * max(abs(Wo), 1.0)
+    else:
+        assert force_err(F, Fo) <= 1e-5
+        assert np.abs(e - eo).max() <= 1e-6 * np.abs(eo).mean()
+        assert abs(tot[0] - Uo) <= 1e-6 * abs(Uo)
+
+
+def test_lj_cells_empty_single_and_small_box(L, ctx):
+    box = [9.0, 9.0, 9.0]
+    for n in (0, 1):
+        F, e, tot = L.ppmd_lj_forces_cells(ctx, cu(np.full((n, 3), 1.0)), box, prec=L.FP32)
+        ctx.sync()
+        assert F.shape == (n, 3) and (F.cpu() == 0).all() and float(tot[0]) == 0.0
+    with pytest.raises(L.PPMDError) as ei:  # fewer than three cells of edge rc
+        L.ppmd_lj_forces_cells(ctx, cu(np.full((4, 3), 1.0)), [7.4, 9.0, 9.0], prec=L.FP32)
+    assert ei.value.code == L.ERR_BOX
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_half_list_keeps_every_pair_once(L, ctx, case):
+    """Every pair of the full list is in exactly one of its two atoms' half
+    rows, each half row is a subset of the full row, and no row is far from
+    half of the full length (the kept side is the upper half space)."""
+    c, r = CASES[case]()
+    p, nbr, cnt = _lists(L, ctx, c["pos"], c["box"], r)
+    half, hcnt = L.ppmd_half_list(ctx, p, c["box"], nbr, cnt)
+    full = rows_as_sets(nbr, cnt)
+    got = rows_as_sets(half, hcnt)
+    kept = set()
+    for i in range(len(full)):
+        assert np.isin(got[i], full[i]).all()
+        for j in got[i]:
+            key = (min(i, int(j)), max(i, int(j)))
+            assert key not in kept
+            kept.add(key)
+    assert 2 * len(kept) == int(cnt.sum())
+    hc, fc = hcnt.cpu().numpy(), cnt.cpu().numpy()
+    assert (np.abs(2 * hc - fc) <= 0.5 * fc + 8).all()
+
+
+def test_half_list_capacity_reports_needed(L, ctx):
+    c, r = CASES["fcc10_r2.8"]()
+    p, nbr, cnt = _lists(L, ctx, c["pos"], c["box"], r)
+    L.ppmd_half_list(ctx, p, c["box"], nbr, cnt, max_half=8)
+    code, needed = ctx.status()
+    assert code == L.ERR_CAPACITY and needed > 8
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_lj_newton3_parity(L, ctx, case, prec):
+    """Half-list pair loop: the oracle's forces, energies and totals at the
+    tolerances of the full-list loop of the same precision."""
+    c, r = CASES[case]()
+    pos, box = c["pos"], c["box"]
+    offs, nbr_o = oracle.neighbours_cells(pos, box, r)
+    Fo, eo, Uo, Wo = oracle.lj(pos, box, offs, nbr_o)
+    p, nbr, cnt = _lists(L, ctx, pos, box, r)
+    half, hcnt = L.ppmd_half_list(ctx, p, box, nbr, cnt)
+    F, e, tot = L.ppmd_lj_forces_newton3(ctx, p, box, half, hcnt, prec=getattr(L, prec))
+    F, e, tot = F.cpu().numpy(), e.cpu().numpy(), tot.cpu().numpy()
+    if prec == "FP64":
+        assert force_err(F, Fo) <= 1e-12
+        assert np.abs(e - eo).max() <= 1e-12 * np.abs(eo).mean()
+        assert abs(tot[0] - Uo) <= 1e-12 * abs(Uo)
+        assert abs(tot[1] - Wo) <= 1e-12 * max(abs(Wo), 1.0)
+    else:
+        assert force_err(F, Fo) <= 1e-5
+        assert np.abs(e - eo).max() <= 1e-6 * np.abs(eo).mean()
+        assert abs(tot[0] - Uo) <= 1e-6 * abs(Uo)
+    # Newton's third law: the forces sum to zero (up to the arithmetic)
+    assert np.abs(F.sum(0)).max() <= (1e-9 if prec == "FP64" else 1e-4) * np.abs(Fo).sum(0).max()
+
+
 def test_lj_empty_and_single_atom(L, ctx):
     box = [9.0, 9.0, 9.0]
     for n in (0, 1):
