@@ -190,7 +190,9 @@ __global__ void __launch_bounds__(256) k_boa(int64_t n, const int4 *__restrict__
 // found by growing each component from its lowest member.
 // Triplets: trip[i*max_nbr + m] for list slot m (0xFFFFFFFF: not bonded).
 // ---------------------------------------------------------------------
-constexpr int CNA_WARPS = 4;
+// CNA: a group of CNA_G = 16 lanes per atom (two atoms per warp: the
+// 12-14 bonds of a crystal atom fill most of a group).
+constexpr int CNA_WARPS = 4, CNA_G = 16, CNA_GROUPS = CNA_WARPS * 32 / CNA_G;
 constexpr uint32_t NOT_BONDED = 0xFFFFFFFFu;
 
 __device__ __forceinline__ bool bonded(const int4 &a, const int4 &b, const double *pa, const double *pb, const Seg &S,
@@ -212,7 +214,7 @@ __device__ __forceinline__ int32_t cna_label_of(int nu, int c421, int c422, int 
     return PPMD_OTHER;
 }
 
-__device__ __forceinline__ void cna_atom(int64_t i, int w, int lane, const int4 *__restrict__ xq,
+__device__ __forceinline__ void cna_atom(int64_t i, int lane, unsigned gmask, int shift, const int4 *__restrict__ xq,
                                          const double *__restrict__ pos64, const SegTable &st,
                                          const int32_t *__restrict__ nbr, const int32_t *__restrict__ cnt,
                                          int32_t max_nbr, int64_t si, int64_t sm, double rc2, float lo, float hi,
@@ -227,7 +229,7 @@ __device__ __forceinline__ void cna_atom(int64_t i, int w, int lane, const int4 
     const unsigned lt = (1u << lane) - 1u;
     // bonded neighbours, compacted in list order
     int32_t nu = 0;
-    for (int32_t base = 0; base < deg; base += 32) {
+    for (int32_t base = 0; base < deg; base += CNA_G) {
         const int32_t k = base + lane;
         bool b = false;
         int32_t j = 0;
@@ -238,7 +240,7 @@ __device__ __forceinline__ void cna_atom(int64_t i, int w, int lane, const int4 
             b = bonded(xi, xj, pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, rc2, lo, hi);
             if (!b && trow) trow[k] = NOT_BONDED;
         }
-        const unsigned ball = __ballot_sync(0xffffffffu, b);
+        const unsigned ball = __ballot_sync(gmask, b) >> shift;
         if (b) {
             const int32_t a = nu + __popc(ball & lt);
             if (a < 64) {
@@ -249,7 +251,7 @@ __device__ __forceinline__ void cna_atom(int64_t i, int w, int lane, const int4 
         }
         nu += __popc(ball);
     }
-    __syncwarp();
+    __syncwarp(gmask);
     if (nu > 64) {
         // more bonded neighbours than the 64-bit masks hold
         if (lane == 0) {
@@ -259,21 +261,29 @@ __device__ __forceinline__ void cna_atom(int64_t i, int w, int lane, const int4 
         }
         return;
     }
-    // adjacency among the bonded neighbours
-    for (int a = lane; a < nu; a += 32) {
+    // adjacency among the bonded neighbours, each pair tested once: lane a
+    // takes the pairs (a, a + o mod nu) for o = 1 .. nu/2 (o = nu/2 of an
+    // even nu only for a < nu/2), so every lane has about nu/2 tests
+    for (int a = lane; a < nu; a += CNA_G) s_A[a] = 0ull;
+    __syncwarp(gmask);
+    for (int a = lane; a < nu; a += CNA_G) {
         unsigned long long m = 0ull;
         const int4 xa = s_x[a];
         const int32_t ja = s_j[a];
-        for (int b = 0; b < nu; ++b) {
-            if (b == a) continue;
-            if (bonded(xa, s_x[b], pos64 + 3 * (int64_t)ja, pos64 + 3 * (int64_t)s_j[b], S, rc2, lo, hi))
+        const int half = nu >> 1;
+        const int last = ((nu & 1) == 0 && a >= half) ? half - 1 : half;
+        for (int o = 1; o <= last; ++o) {
+            const int b = a + o < nu ? a + o : a + o - nu;
+            if (bonded(xa, s_x[b], pos64 + 3 * (int64_t)ja, pos64 + 3 * (int64_t)s_j[b], S, rc2, lo, hi)) {
                 m |= 1ull << b;
+                atomicOr(&s_A[b], 1ull << a);
+            }
         }
-        s_A[a] = m;
+        atomicOr(&s_A[a], m);
     }
-    __syncwarp();
+    __syncwarp(gmask);
     int c421 = 0, c422 = 0, c444 = 0, c666 = 0;
-    for (int a = lane; a < nu; a += 32) {
+    for (int a = lane; a < nu; a += CNA_G) {
         const unsigned long long C = s_A[a];
         const int ncn = __popcll(C);
         int twice_nb = 0;
@@ -303,10 +313,10 @@ __device__ __forceinline__ void cna_atom(int64_t i, int w, int lane, const int4 
         c444 += t == ((4u << 16) | (4u << 8) | 4u);
         c666 += t == ((6u << 16) | (6u << 8) | 6u);
     }
-    c421 = __reduce_add_sync(0xffffffffu, c421);
-    c422 = __reduce_add_sync(0xffffffffu, c422);
-    c444 = __reduce_add_sync(0xffffffffu, c444);
-    c666 = __reduce_add_sync(0xffffffffu, c666);
+    c421 = __reduce_add_sync(gmask, c421);
+    c422 = __reduce_add_sync(gmask, c422);
+    c444 = __reduce_add_sync(gmask, c444);
+    c666 = __reduce_add_sync(gmask, c666);
     if (lane == 0 && label) label[out_idx ? out_idx[i] : i] = (int8_t)cna_label_of(nu, c421, c422, c444, c666);
 }
 
@@ -319,18 +329,19 @@ __global__ void __launch_bounds__(CNA_WARPS * 32) k_cna(int64_t n, const int4 *_
                                                         int8_t *__restrict__ label, int32_t *status,
                                                         unsigned long long *needed, const int32_t *__restrict__ which,
                                                         const int32_t *__restrict__ n_dev) {
-    __shared__ int32_t s_j[CNA_WARPS][64];
-    __shared__ int32_t s_slot[CNA_WARPS][64];
-    __shared__ int4 s_x[CNA_WARPS][64];
-    __shared__ unsigned long long s_A[CNA_WARPS][64];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ int32_t s_j[CNA_GROUPS][64];
+    __shared__ int32_t s_slot[CNA_GROUPS][64];
+    __shared__ int4 s_x[CNA_GROUPS][64];
+    __shared__ unsigned long long s_A[CNA_GROUPS][64];
+    const int lane = threadIdx.x & (CNA_G - 1), g = threadIdx.x / CNA_G, shift = threadIdx.x & 31 & ~(CNA_G - 1);
+    const unsigned gmask = ((1u << CNA_G) - 1u) << shift;
     // the count comes from the device when the subset was chosen there
     const int64_t m = n_dev ? (int64_t)*n_dev : n;
-    for (int64_t wi = (int64_t)blockIdx.x * CNA_WARPS + w; wi < m; wi += (int64_t)gridDim.x * CNA_WARPS) {
-        const int64_t i = which ? (int64_t)which[wi] : wi;  // a subset of the atoms when `which` is given
-        cna_atom(i, w, lane, xq, pos64, st, nbr, cnt, max_nbr, si, sm, rc2, lo, hi, out_idx, trip, label, status, needed,
-                 s_j[w], s_slot[w], s_x[w], s_A[w]);
-        __syncwarp();
+    for (int64_t gi = (int64_t)blockIdx.x * CNA_GROUPS + g; gi < m; gi += (int64_t)gridDim.x * CNA_GROUPS) {
+        const int64_t i = which ? (int64_t)which[gi] : gi;  // a subset of the atoms when `which` is given
+        cna_atom(i, lane, gmask, shift, xq, pos64, st, nbr, cnt, max_nbr, si, sm, rc2, lo, hi, out_idx, trip, label, status,
+                 needed, s_j[g], s_slot[g], s_x[g], s_A[g]);
+        __syncwarp(gmask);
     }
 }
 
@@ -744,7 +755,7 @@ int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, co
     float lo, hi;
     cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
     if (n > 0)
-        PPMD_LAUNCH(ctx, k_cna, div_up(n, CNA_WARPS), CNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
+        PPMD_LAUNCH(ctx, k_cna, div_up(n, CNA_GROUPS), CNA_WARPS * 32, 0, n, xq, pos64, st, nbr, cnt, max_nbr,
                     ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_cut * r_cut,
                     lo, hi, out_idx, trip, label, ctx->d_status, ctx->d_needed, nullptr, nullptr);
     return check_launch(ctx, "cna");
@@ -757,7 +768,7 @@ int cna_subset_launch(ppmd_ctx *ctx, int64_t m_max, const int32_t *m_dev, const 
     cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
     // a grid of a few blocks per SM strides over however many atoms the
     // device chose
-    const int64_t grid = std::min<int64_t>(div_up(m_max, CNA_WARPS), 148 * 8);
+    const int64_t grid = std::min<int64_t>(div_up(m_max, CNA_GROUPS), 148 * 8);
     if (m_max > 0)
         PPMD_LAUNCH(ctx, k_cna, grid, CNA_WARPS * 32, 0, m_max, xq, pos64, st, nbr, cnt, max_nbr,
                     ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_cut * r_cut,
