@@ -243,9 +243,9 @@ int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *bo
  * never interact.  Outputs and their layout as ppmd_analyze over the n
  * atoms (caller order); every box must hold at least 3 cells of edge
  * max(r_boa, r_cna) along each axis.  List capacity: the largest over the
- * boxes.  With nbox > 1 the box table is copied from pageable host memory,
- * which waits for earlier work on the context stream; otherwise
- * asynchronous, as ppmd_analyze. */
+ * boxes.  Asynchronous, as ppmd_analyze: with nbox > 1 the box tables go
+ * through a pinned buffer of the context (reused once the copies of the
+ * previous call have run; allocated, or grown, on first use). */
 int ppmd_analyze_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes,
                        double r_boa, double r_cna, float *q4, float *q6, int32_t *n_nb, int8_t *label);
 

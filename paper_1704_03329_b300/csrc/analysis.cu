@@ -790,7 +790,7 @@ int cna_subset_launch(ppmd_ctx *ctx, int64_t m_max, const int32_t *m_dev, const 
 //                centres (clamped at both ends), divided by 24.
 // Output: f32 [n][30] and/or bf16 [n][32] (f[30], f[31] = 0).
 // ---------------------------------------------------------------------
-constexpr int FEAT_WARPS = 4, FEAT_G = 8, FEAT_GROUPS = FEAT_WARPS * 32 / FEAT_G, FEAT_CAP = 64;
+constexpr int FEAT_WARPS = 4, FEAT_G = 8, FEAT_GROUPS = FEAT_WARPS * 32 / FEAT_G, FEAT_CAP = 64, FEAT_PF = 3;
 
 __global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, const int4 *__restrict__ xq,
                                                                  const double *__restrict__ pos64, SegTable st,
@@ -817,6 +817,7 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, cons
     const Seg &S = seg_ref(st, xi.w);
     const int32_t deg = min(cnt[i], max_nbr);
     const int32_t *row = nbr + i * si;
+    const int64_t o = out_idx ? out_idx[i] : i;
     const unsigned lt = (1u << gl) - 1u;
     float *hist = &s_h[0][threadIdx.x];  // bin k at hist[k * FEAT_WARPS * 32]
 #pragma unroll
@@ -824,42 +825,56 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, cons
 #pragma unroll
     for (int c = gl; c < 32; c += FEAT_G) s_f[g][c] = (c >= 2 && c < 16) ? 1.0f : 0.0f;
     int32_t nu = 0, nbd = 0;  // bonds, bonded neighbours among them
-    for (int32_t base = 0; base < deg; base += FEAT_G) {
-        const int32_t k = base + gl;
-        bool b = false, bb = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        if (k < deg) {
-            const int32_t j = row[k * sm];
-            const int4 xj = xq[j];
-            dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj.x, S.sx[0]);
-            dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj.y, S.sx[1]);
-            dz = fixed_delta((uint32_t)xi.z, (uint32_t)xj.z, S.sx[2]);
-            r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            double r2x = -1.0;  // exact r^2 when needed
-            b = r2 < lo;
-            if (!b && r2 < hi) {
-                double dr[3];
-                r2x = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr);
-                b = r2x < rc2;
-            }
-            bb = r2 < blo;
-            if (!bb && r2 < bhi) {
-                if (r2x < 0.0) {
+    // FEAT_PF list entries per lane in flight (one round trip for up to
+    // FEAT_G * FEAT_PF neighbours), then taken in list order
+    for (int32_t base0 = 0; base0 < deg; base0 += FEAT_G * FEAT_PF) {
+        int32_t jj[FEAT_PF];
+        int4 xx[FEAT_PF];
+#pragma unroll
+        for (int u = 0; u < FEAT_PF; ++u) {
+            const int32_t k = base0 + u * FEAT_G + gl;
+            jj[u] = k < deg ? row[k * sm] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < FEAT_PF; ++u) xx[u] = jj[u] >= 0 ? xq[jj[u]] : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < FEAT_PF; ++u) {
+            if (base0 + u * FEAT_G >= deg) break;  // (uniform over the group)
+            const int32_t j = jj[u];
+            bool b = false, bb = false;
+            float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+            if (j >= 0) {
+                const int4 xj = xx[u];
+                dx = fixed_delta((uint32_t)xi.x, (uint32_t)xj.x, S.sx[0]);
+                dy = fixed_delta((uint32_t)xi.y, (uint32_t)xj.y, S.sx[1]);
+                dz = fixed_delta((uint32_t)xi.z, (uint32_t)xj.z, S.sx[2]);
+                r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                double r2x = -1.0;  // exact r^2 when needed
+                b = r2 < lo;
+                if (!b && r2 < hi) {
                     double dr[3];
                     r2x = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr);
+                    b = r2x < rc2;
                 }
-                bb = r2x < rb2;
+                bb = r2 < blo;
+                if (!bb && r2 < bhi) {
+                    if (r2x < 0.0) {
+                        double dr[3];
+                        r2x = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr);
+                    }
+                    bb = r2x < rb2;
+                }
+                bb = bb && b;
             }
-            bb = bb && b;
+            const unsigned ball = __ballot_sync(gmask, b) >> shift, bbal = __ballot_sync(gmask, bb) >> shift;
+            if (b) {
+                const float ir = rsqrtf(r2), r = r2 * ir;  // hardware estimates (~2 ulp)
+                const int32_t a = bb ? nbd + __popc(bbal & lt) : FEAT_CAP - 1 - (nu - nbd) - __popc(ball & ~bbal & lt);
+                if (a >= 0 && a < FEAT_CAP) s_e[g][a] = make_float4(dx, dy, dz, r);
+            }
+            nu += __popc(ball);
+            nbd += __popc(bbal);
         }
-        const unsigned ball = __ballot_sync(gmask, b) >> shift, bbal = __ballot_sync(gmask, bb) >> shift;
-        if (b) {
-            const float ir = rsqrtf(r2), r = r2 * ir;  // hardware estimates (~2 ulp)
-            const int32_t a = bb ? nbd + __popc(bbal & lt) : FEAT_CAP - 1 - (nu - nbd) - __popc(ball & ~bbal & lt);
-            if (a >= 0 && a < FEAT_CAP) s_e[g][a] = make_float4(dx, dy, dz, r);
-        }
-        nu += __popc(ball);
-        nbd += __popc(bbal);
     }
     if (nu > FEAT_CAP) {
         if (gl == 0) {
@@ -923,14 +938,20 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, cons
     // tent weights added to the lane's own row
     const int npair = nbd * (nbd - 1) / 2;
     const float hlo = r_ref - 0.35f;
+    // pair (a, b), a < b, numbered pidx = b (b - 1) / 2 + a: the lane's next
+    // pair (pidx + FEAT_G) by carrying a into b
+    int pa = gl, pb = 1;
+    while (pa >= pb) {
+        pa -= pb;
+        ++pb;
+    }
     for (int pidx = gl; pidx < npair; pidx += FEAT_G) {
-        // pair (a, b), a < b, numbered pidx = b (b - 1) / 2 + a
-        const float q8 = fmaf(8.0f, (float)pidx, 1.0f);
-        int b = (int)(0.5f * (1.0f + q8 * rsqrtf(q8)));  // an estimate, corrected below
-        if (b * (b - 1) / 2 > pidx) --b;
-        if ((b + 1) * b / 2 <= pidx) ++b;
-        const int a = pidx - b * (b - 1) / 2;
-        const float4 va = s_e[g][a], vb = s_e[g][b];
+        const float4 va = s_e[g][pa], vb = s_e[g][pb];
+        pa += FEAT_G;
+        while (pa >= pb) {
+            pa -= pb;
+            ++pb;
+        }
         const float cx = va.x - vb.x, cy = va.y - vb.y, cz = va.z - vb.z;
         const float c2 = fmaxf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)), 1e-30f);
         const float chord = c2 * rsqrtf(c2);
@@ -973,7 +994,6 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, cons
         s_f[g][1] = sqrtf(s6) * inv;
     }
     __syncwarp(gmask);
-    const int64_t o = out_idx ? out_idx[i] : i;
     const float4 fv = make_float4(s_f[g][4 * gl], s_f[g][4 * gl + 1], s_f[g][4 * gl + 2], s_f[g][4 * gl + 3]);
     if (f32) {
         float *dst = f32 + o * 30 + 4 * gl;
@@ -1135,12 +1155,21 @@ int sorted_snapshot_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const 
     s.xq = (int4 *)scratch(ctx, S_AUX0, sizeof(int4) * nn);
     if (!d_segs || !d_off || !seg_of || !d_bricks || !cell0 || !s.cell_start || !s.perm || !s.pos || !s.xq)
         return PPMD_ERR_NOMEM;
-    // tables from pageable host memory (the copies are staged before they return)
+    // the three tables through the context's pinned staging buffer: the
+    // copies queue behind the stream's work instead of waiting for it
+    const size_t b_seg = sizeof(Seg) * (size_t)nbox, b_off = sizeof(int64_t) * (size_t)(nbox + 1),
+                 b_brk = sizeof(Brick) * bl.size();
+    const size_t o_off = (b_seg + 15) / 16 * 16, o_brk = o_off + (b_off + 15) / 16 * 16;
+    char *h = (char *)stage_host(ctx, o_brk + b_brk);
+    if (!h) return PPMD_ERR_NOMEM;
+    memcpy(h, segs.data(), b_seg);
+    memcpy(h + o_off, atom_off, b_off);
+    if (b_brk) memcpy(h + o_brk, bl.data(), b_brk);
     cudaStream_t st = ctx->stream;
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_segs, segs.data(), sizeof(Seg) * (size_t)nbox, cudaMemcpyHostToDevice, st), "copy"));
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_off, atom_off, sizeof(int64_t) * (size_t)(nbox + 1), cudaMemcpyHostToDevice, st), "copy"));
-    if (!bl.empty())
-        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice, st), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_segs, h, b_seg, cudaMemcpyHostToDevice, st), "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_off, h + o_off, b_off, cudaMemcpyHostToDevice, st), "copy"));
+    if (b_brk) PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(d_bricks, h + o_brk, b_brk, cudaMemcpyHostToDevice, st), "copy"));
+    PPMD_TRY(stage_done(ctx));
     s.st.d = d_segs;
     s.st.nseg = (int32_t)nbox;
     s.st.one = segs[0];

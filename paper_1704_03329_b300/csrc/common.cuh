@@ -63,6 +63,9 @@ struct ppmd_ctx {
     int64_t host_needed = 0;  // capacity asked for by a host-side check
     char err[512] = {0};
     ppmd::Scratch scratch[ppmd::S_NSLOTS];
+    void *h_stage = nullptr;           // pinned staging of host tables (stage_host)
+    size_t h_stage_bytes = 0;
+    cudaEvent_t stage_ev = nullptr;    // recorded after the last copy out of h_stage
 };
 
 namespace ppmd {
@@ -72,6 +75,12 @@ int cuda_check(ppmd_ctx *ctx, cudaError_t e, const char *what);
 // Scratch buffer of at least `bytes` (grows; contents not preserved on growth).
 void *scratch(ppmd_ctx *ctx, int slot, size_t bytes);
 int check_launch(ppmd_ctx *ctx, const char *what);
+// Pinned host buffer of at least `bytes` for tables that are then copied to
+// the device with cudaMemcpyAsync (which does not wait for the stream when
+// the source is pinned); waits until the copies of the previous use have
+// run.  After issuing the copies, call stage_done.
+void *stage_host(ppmd_ctx *ctx, size_t bytes);
+int stage_done(ppmd_ctx *ctx);
 
 #define PPMD_LAUNCH(ctx, kernel, grid, block, smem, ...)                           \
     do {                                                                           \

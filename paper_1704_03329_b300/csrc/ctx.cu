@@ -46,6 +46,30 @@ void *scratch(ppmd_ctx *ctx, int slot, size_t bytes) {
     return s.ptr;
 }
 
+void *stage_host(ppmd_ctx *ctx, size_t bytes) {
+    if (ctx->stage_ev) cudaEventSynchronize(ctx->stage_ev);
+    if (bytes == 0) bytes = 16;
+    if (ctx->h_stage_bytes >= bytes) return ctx->h_stage;
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    const size_t want = bytes + bytes / 4;
+    if (cudaMallocHost(&ctx->h_stage, want) != cudaSuccess) {
+        cudaGetLastError();
+        set_error(ctx, PPMD_ERR_NOMEM, "cudaMallocHost of %zu bytes failed", want);
+        ctx->h_stage = nullptr;
+        return nullptr;
+    }
+    ctx->h_stage_bytes = want;
+    return ctx->h_stage;
+}
+
+int stage_done(ppmd_ctx *ctx) {
+    if (!ctx->stage_ev)
+        PPMD_TRY(cuda_check(ctx, cudaEventCreateWithFlags(&ctx->stage_ev, cudaEventDisableTiming), "cudaEventCreate"));
+    return cuda_check(ctx, cudaEventRecord(ctx->stage_ev, ctx->stream), "cudaEventRecord");
+}
+
 void cutoff_band(double rc2, double Lmax, float *lo, float *hi) {
     // The single-precision r^2 from fixed-point coordinates differs from
     // the exact value by at most ~6 units of 2^-24 relative plus the
@@ -246,6 +270,8 @@ extern "C" int ppmd_destroy(ppmd_ctx *ctx) {
     for (int s = 0; s < S_NSLOTS; ++s)
         if (ctx->scratch[s].ptr) cudaFree(ctx->scratch[s].ptr);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
     delete ctx;
     return PPMD_OK;
 }
