@@ -120,39 +120,60 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t pk_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&v);
+// Two FP32 values (first in the low half) as packed BF16, rounded to
+// nearest, negatives to zero (ReLU) when RELU.
+template <bool RELU>
+__device__ __forceinline__ uint32_t pk_bf16x2(unsigned long long v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    uint32_t d;
+    if (RELU) asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    else asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
-
-// Eight BF16 values of K (one 16-byte row of a core matrix).
-__device__ __forceinline__ void st_chunk(uint8_t *smem, uint32_t off, const float (&v)[8]) {
-    uint4 q;
-    q.x = pk_bf16(v[0], v[1]);
-    q.y = pk_bf16(v[2], v[3]);
-    q.z = pk_bf16(v[4], v[5]);
-    q.w = pk_bf16(v[6], v[7]);
-    *reinterpret_cast<uint4 *>(smem + off) = q;
+__device__ __forceinline__ unsigned long long pk2(uint32_t lo, uint32_t hi) {
+    unsigned long long v;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "r"(lo), "r"(hi));
+    return v;
+}
+// packed FP32 pairs (round to nearest, as the scalar operations)
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
 // Layer output of this thread's row: bias + ReLU, BF16, into operand H
-// (the four loads of the 64 columns complete on one wait).
+// (the four loads of the 64 columns complete on one wait; bias pairs added
+// as packed FP32, ReLU folded into the BF16 conversion).
 __device__ __forceinline__ void relu_to_h(uint8_t *smem, uint32_t h_base, uint32_t t_lane, const float *bias) {
     uint32_t raw[4][16];
 #pragma unroll
     for (int q = 0; q < 4; ++q) tmem_ld16(t_lane + 16 * q, raw[q]);
     tmem_wait();
+    const ulonglong2 *b4 = reinterpret_cast<const ulonglong2 *>(bias);
+    const int r = threadIdx.x;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        float lo[8], hi[8];
+        uint32_t w[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            lo[c] = fmaxf(__uint_as_float(raw[q][c]) + bias[16 * q + c], 0.0f);
-            hi[c] = fmaxf(__uint_as_float(raw[q][8 + c]) + bias[16 * q + 8 + c], 0.0f);
+        for (int p = 0; p < 8; p += 2) {
+            const ulonglong2 bb = b4[4 * q + p / 2];  // bias of columns 16 q + 2 p .. + 3
+            w[p] = pk_bf16x2<true>(add2(pk2(raw[q][2 * p], raw[q][2 * p + 1]), bb.x));
+            w[p + 1] = pk_bf16x2<true>(add2(pk2(raw[q][2 * p + 2], raw[q][2 * p + 3]), bb.y));
         }
-        const int r = threadIdx.x;
-        st_chunk(smem, h_base + core_off(r, 16 * q, TC_ROWS), lo);
-        st_chunk(smem, h_base + core_off(r, 16 * q + 8, TC_ROWS), hi);
+        *reinterpret_cast<uint4 *>(smem + h_base + core_off(r, 16 * q, TC_ROWS)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(smem + h_base + core_off(r, 16 * q + 8, TC_ROWS)) = make_uint4(w[4], w[5], w[6], w[7]);
     }
 }
 
@@ -240,20 +261,23 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_infer_tc(int64_t n, const __
             for (int q = 0; q < 4; ++q) q4[q] = make_uint4(0u, 0u, 0u, 0u);
         }
     };
-    // standardised BF16 row into slot s as operand A of layer 1
+    // standardised BF16 row into slot s as operand A of layer 1: (x - mu) isd
+    // on packed FP32 pairs (columns 30, 31: isd = 0), rounded to BF16
+    const unsigned long long *mu2 = reinterpret_cast<const unsigned long long *>(mu);
+    const unsigned long long *isd2 = reinterpret_cast<const unsigned long long *>(isd);
     auto stage = [&](int sl, const uint4 (&q4)[4]) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const uint32_t w[4] = {q4[c].x, q4[c].y, q4[c].z, q4[c].w};
-            float v[8];
+            uint32_t o[4];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162 *>(&w[h]);
-                const int kk = 8 * c + 2 * h;
-                v[2 * h] = (__low2float(b2) - mu[kk]) * isd[kk];  // columns 30, 31: isd = 0
-                v[2 * h + 1] = (__high2float(b2) - mu[kk + 1]) * isd[kk + 1];
+                const int kk2 = 4 * c + h;  // the pair of columns 2 kk2, 2 kk2 + 1
+                const unsigned long long x2 = pk2(w[h] << 16, w[h] & 0xFFFF0000u);  // BF16 -> FP32, exact
+                o[h] = pk_bf16x2<false>(mul2(sub2(x2, mu2[kk2]), isd2[kk2]));
             }
-            st_chunk(smem, sl * SM_SLOT + core_off(tid, 8 * c, TC_ROWS), v);
+            *reinterpret_cast<uint4 *>(smem + sl * SM_SLOT + core_off(tid, 8 * c, TC_ROWS)) =
+                make_uint4(o[0], o[1], o[2], o[3]);
         }
     };
     // operands of slot s visible to the tensor cores, then one thread issues
