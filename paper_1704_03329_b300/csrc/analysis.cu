@@ -1030,13 +1030,16 @@ int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos6
 // ---------------------------------------------------------------------
 // Pipeline: sort by cell, list at r_list, analyses, results in caller order.
 // ---------------------------------------------------------------------
-__global__ void k_gather_pos(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ pos,
-                             double *__restrict__ pos_o) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Sorted copies: positions and fixed-point words of the atoms perm[k].
+__global__ void k_gather_pos_xq(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ pos,
+                                const int4 *__restrict__ xq, double *__restrict__ pos_o, int4 *__restrict__ xq_o) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int64_t j = perm[k];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) pos_o[3 * k + d] = pos[3 * j + d];
+    const int64_t o = perm[k];
+    pos_o[3 * k] = pos[3 * o];
+    pos_o[3 * k + 1] = pos[3 * o + 1];
+    pos_o[3 * k + 2] = pos[3 * o + 2];
+    xq_o[k] = xq[o];
 }
 
 int32_t snapshot_capacity(int64_t n, const ppmd_box *box, double r_list) {
@@ -1079,10 +1082,13 @@ int sorted_snapshot(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box 
     s.st.one.atom1 = n;
     const BrickShape shape = brick_shape(s.st.one);
     const int64_t nbricks = brick_count(s.st.one, shape);
-    // bin (positions need not be wrapped), sort by cell, fixed point in cell order
-    PPMD_TRY(bin_atoms(ctx, pos, n, s.st, nullptr, ncell, false, cell0, s.cell_start, s.perm, true));
-    if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos, div_up(n, 256), 256, 0, n, s.perm, pos, s.pos);
-    PPMD_TRY(prep_fixed(ctx, s.pos, n, s.st, nullptr, s.xq, nullptr));
+    // fixed point in the caller's order (positions need not be wrapped), bin
+    // and sort by cell on the fixed-point words, gather both copies
+    int4 *xq_c = (int4 *)scratch(ctx, S_XQ, sizeof(int4) * nn);
+    if (!xq_c) return PPMD_ERR_NOMEM;
+    PPMD_TRY(prep_fixed(ctx, pos, n, s.st, nullptr, xq_c, nullptr));
+    PPMD_TRY(bin_atoms_fixed(ctx, xq_c, n, s.st, ncell, cell0, s.cell_start, s.perm));
+    if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos_xq, div_up(n, 256), 256, 0, n, s.perm, pos, xq_c, s.pos, s.xq);
     s.ld = (n + 31) / 32 * 32;
     PPMD_TRY(neigh_brick_setup(ctx, max_nbr));
     s.max_nbr = max_nbr;
@@ -1174,12 +1180,15 @@ int sorted_snapshot_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const 
     s.st.nseg = (int32_t)nbox;
     s.st.one = segs[0];
     if (n > 0) PPMD_LAUNCH(ctx, k_seg_of, div_up(n, 256), 256, 0, n, d_off, (int32_t)nbox, seg_of);
-    // bin and sort by cell: cells of box b follow those of box b - 1, so the
-    // sorted atoms of box b keep the positions atom_off[b] .. atom_off[b + 1]
-    // - 1 and seg_of holds for the sorted order as well
-    PPMD_TRY(bin_atoms(ctx, pos, n, s.st, seg_of, ncell, false, cell0, s.cell_start, s.perm, true));
-    if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos, div_up(n, 256), 256, 0, n, s.perm, pos, s.pos);
-    PPMD_TRY(prep_fixed(ctx, s.pos, n, s.st, seg_of, s.xq, nullptr));
+    // fixed point in the caller's order (the segment in .w), bin and sort by
+    // cell on the fixed-point words (cells of box b follow those of box b -
+    // 1, so the sorted atoms of box b keep the positions atom_off[b] ..
+    // atom_off[b + 1] - 1), gather both copies
+    int4 *xq_c = (int4 *)scratch(ctx, S_XQ, sizeof(int4) * nn);
+    if (!xq_c) return PPMD_ERR_NOMEM;
+    PPMD_TRY(prep_fixed(ctx, pos, n, s.st, seg_of, xq_c, nullptr));
+    PPMD_TRY(bin_atoms_fixed(ctx, xq_c, n, s.st, ncell, cell0, s.cell_start, s.perm));
+    if (n > 0) PPMD_LAUNCH(ctx, k_gather_pos_xq, div_up(n, 256), 256, 0, n, s.perm, pos, xq_c, s.pos, s.xq);
     s.ld = (n + 31) / 32 * 32;
     PPMD_TRY(neigh_brick_setup(ctx, max_nbr));
     s.max_nbr = max_nbr;

@@ -65,21 +65,54 @@ __global__ void k_scatter_x(int64_t n, const double *__restrict__ pos, SegTable 
 
 // Order every cell's atoms by (x, index): one thread per slot counts the
 // members of its cell that come first (cells are small) and writes its atom
-// at that rank.
+// at that rank.  The key is the x coordinate (FP32) or its fixed-point word.
+template <class Key>
 __global__ void k_rank_cells_x(int64_t n, const int32_t *__restrict__ cell_of, const int32_t *__restrict__ cell_start,
-                               const int32_t *__restrict__ tmp_atoms, const float *__restrict__ key,
+                               const int32_t *__restrict__ tmp_atoms, const Key *__restrict__ key,
                                int32_t *__restrict__ cell_atoms) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int32_t v = tmp_atoms[s];
-    const float kv = key[s];
+    const Key kv = key[s];
     const int32_t c = cell_of[v], a = cell_start[c], b = cell_start[c + 1];
     int32_t rank = 0;
     for (int32_t t = a; t < b; ++t) {
-        const float kt = key[t];
+        const Key kt = key[t];
         rank += (kt < kv) || (kt == kv && tmp_atoms[t] < v);
     }
     cell_atoms[a + rank] = v;
+}
+
+// Cell of a fixed-point coordinate word q on a grid of nc cells: the c with
+// c 2^32 <= q nc < (c + 1) 2^32 (cells of the box's edge L / nc, in exact
+// integer arithmetic).
+__device__ __forceinline__ int32_t fixed_cell(uint32_t q, int32_t nc) {
+    return (int32_t)(((unsigned long long)q * (unsigned long long)(uint32_t)nc) >> 32);
+}
+
+__global__ void k_bin_fixed(const int4 *__restrict__ xq, int64_t n, SegTable st, int32_t *__restrict__ cell_of,
+                            int32_t *__restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 x = xq[i];
+    const Seg &S = seg_ref(st, x.w);
+    const int32_t cell = S.cell0 + (fixed_cell((uint32_t)x.z, S.nc[2]) * S.nc[1] + fixed_cell((uint32_t)x.y, S.nc[1])) *
+                                       S.nc[0] +
+                         fixed_cell((uint32_t)x.x, S.nc[0]);
+    cell_of[i] = cell;
+    atomicAdd(&count[cell], 1);
+}
+
+// As k_scatter, the sort key of each slot being the atom's fixed-point x word.
+__global__ void k_scatter_fx(int64_t n, const int4 *__restrict__ xq, const int32_t *__restrict__ cell_of,
+                             const int32_t *__restrict__ cell_start, int32_t *__restrict__ cursor,
+                             int32_t *__restrict__ cell_atoms, uint32_t *__restrict__ key) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t c = cell_of[i];
+    const int32_t slot = cell_start[c] + atomicAdd(&cursor[c], 1);
+    cell_atoms[slot] = (int32_t)i;
+    key[slot] = (uint32_t)xq[i].x;
 }
 
 // Order every cell's atoms by index (insertion sort; cells are small).
@@ -119,13 +152,31 @@ int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, c
             if (!key || !tmp) return PPMD_ERR_NOMEM;
             PPMD_LAUNCH(ctx, k_scatter_x, div_up(n, 256), 256, 0, n, pos, st, seg_of, cell_of, cell_start, cursor, tmp,
                         key);
-            PPMD_LAUNCH(ctx, k_rank_cells_x, div_up(n, 256), 256, 0, n, cell_of, cell_start, tmp, key, cell_atoms);
+            PPMD_LAUNCH(ctx, k_rank_cells_x<float>, div_up(n, 256), 256, 0, n, cell_of, cell_start, tmp, key, cell_atoms);
         } else {
             PPMD_LAUNCH(ctx, k_scatter, div_up(n, 256), 256, 0, n, cell_of, cell_start, cursor, cell_atoms);
             PPMD_LAUNCH(ctx, k_sort_cells, div_up(ncell, 128), 128, 0, ncell, cell_start, cell_atoms);
         }
     }
     return check_launch(ctx, "bin_atoms");
+}
+
+int bin_atoms_fixed(ppmd_ctx *ctx, const int4 *xq, int64_t n, const SegTable &st, int64_t ncell, int32_t *cell_of,
+                    int32_t *cell_start, int32_t *cell_atoms) {
+    cudaStream_t s = ctx->stream;
+    PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cell_start, 0, sizeof(int32_t) * (size_t)(ncell + 1), s), "memset"));
+    if (n > 0) PPMD_LAUNCH(ctx, k_bin_fixed, div_up(n, 256), 256, 0, xq, n, st, cell_of, cell_start);
+    PPMD_TRY(exclusive_scan(ctx, cell_start, cell_start, ncell));
+    if (n > 0) {
+        int32_t *cursor = (int32_t *)scratch(ctx, S_COUNT, sizeof(int32_t) * (size_t)ncell);
+        uint32_t *key = (uint32_t *)scratch(ctx, S_CELLKEY, sizeof(uint32_t) * (size_t)n);
+        int32_t *tmp = (int32_t *)scratch(ctx, S_CELLTMP, sizeof(int32_t) * (size_t)n);
+        if (!cursor || !key || !tmp) return PPMD_ERR_NOMEM;
+        PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)ncell, s), "memset"));
+        PPMD_LAUNCH(ctx, k_scatter_fx, div_up(n, 256), 256, 0, n, xq, cell_of, cell_start, cursor, tmp, key);
+        PPMD_LAUNCH(ctx, k_rank_cells_x<uint32_t>, div_up(n, 256), 256, 0, n, cell_of, cell_start, tmp, key, cell_atoms);
+    }
+    return check_launch(ctx, "bin_atoms_fixed");
 }
 
 }  // namespace ppmd

@@ -12,4 +12,10 @@ namespace ppmd {
 // of a cell in increasing index).
 int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, const int32_t *seg_of, int64_t ncell,
               bool exact, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms, bool order_x = false);
+// The same from fixed-point coordinates xq (their .w the segment): cell c
+// along an axis of nc cells holds the words q with c 2^32 <= q nc <
+// (c + 1) 2^32 (integer arithmetic), atoms of a cell ordered by (x word,
+// index).  For pipelines that convert to fixed point first.
+int bin_atoms_fixed(ppmd_ctx *ctx, const int4 *xq, int64_t n, const SegTable &st, int64_t ncell, int32_t *cell_of,
+                    int32_t *cell_start, int32_t *cell_atoms);
 }  // namespace ppmd

@@ -107,3 +107,27 @@ def test_boxes_reject_bad_offsets(L, ctx, box_set):
     with pytest.raises(L.PPMDError) as ei:
         L.ppmd_analyze_boxes(ctx, cu(pos), bad, [b["box"] for b in boxes], R_BOA, R_CNA)
     assert ei.value.code == L.ERR_INVALID
+
+
+def test_boxes_with_an_empty_box_and_all_empty(L, ctx, box_set):
+    """An empty box in the middle of the set changes nothing for the others;
+    a set of empty boxes gives empty outputs."""
+    boxes, pos, off = box_set
+    bx = [b["box"] for b in boxes]
+    off2 = off[:3] + [off[2]] + off[3:]  # an empty box after the second
+    bx2 = bx[:2] + [[9.0, 9.0, 9.0]] + bx[2:]
+    ref = L.ppmd_analyze_boxes(ctx, cu(pos), off, bx, R_BOA, R_CNA)
+    got = L.ppmd_analyze_boxes(ctx, cu(pos), off2, bx2, R_BOA, R_CNA)
+    ctx.sync()
+    for k in ("label", "q4", "q6", "n_nb"):
+        assert torch.equal(ref[k], got[k])
+    params = cu(_params(9), torch.float32)
+    l1, c1, n1 = L.ppmd_classify_boxes(ctx, cu(pos), off, bx, mode=1, params=params, threshold=0.6)
+    l2, c2, n2 = L.ppmd_classify_boxes(ctx, cu(pos), off2, bx2, mode=1, params=params, threshold=0.6)
+    assert torch.equal(l1, l2) and torch.equal(c1, c2) and n1 == n2
+    empty = cu(np.zeros((0, 3)))
+    lab, conf, nfb = L.ppmd_classify_boxes(ctx, empty, [0, 0, 0], [[9.0, 9.0, 9.0], [8.0, 8.0, 8.0]], mode=1,
+                                           params=params)
+    out = L.ppmd_analyze_boxes(ctx, empty, [0, 0], [[9.0, 9.0, 9.0]], R_BOA, R_CNA)
+    ctx.sync()
+    assert lab.numel() == 0 and nfb == 0 and out["label"].numel() == 0
