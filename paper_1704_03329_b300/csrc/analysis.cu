@@ -261,6 +261,11 @@ __device__ __forceinline__ void cna_atom(int64_t i, int lane, unsigned gmask, in
         }
         return;
     }
+    if (!trow && nu != 12 && nu != 14) {
+        // labels only: no signature with this many bonds (cna_label_of)
+        if (lane == 0 && label) label[out_idx ? out_idx[i] : i] = PPMD_OTHER;
+        return;
+    }
     // adjacency among the bonded neighbours, each pair tested once: lane a
     // takes the pairs (a, a + o mod nu) for o = 1 .. nu/2 (o = nu/2 of an
     // even nu only for a < nu/2), so every lane has about nu/2 tests
@@ -807,7 +812,7 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, cons
     // the bonded neighbours (r < r_ref) from the front, the other bonds from
     // the back.
     __shared__ float4 s_e[FEAT_GROUPS][FEAT_CAP];
-    __shared__ float s_h[14][FEAT_WARPS * 32];  // private histogram of each lane, bin-major (no bank conflicts)
+    __shared__ float s_h[15][FEAT_WARPS * 32];  // private histogram of each lane, bin-major (no bank conflicts); row 14 a guard
     __shared__ float s_f[FEAT_GROUPS][32];
     const int gl = threadIdx.x & (FEAT_G - 1), g = threadIdx.x / FEAT_G, shift = threadIdx.x & 31 & ~(FEAT_G - 1);
     const unsigned gmask = 0xffu << shift;
@@ -821,7 +826,7 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, cons
     const unsigned lt = (1u << gl) - 1u;
     float *hist = &s_h[0][threadIdx.x];  // bin k at hist[k * FEAT_WARPS * 32]
 #pragma unroll
-    for (int k = 0; k < 14; ++k) hist[k * FEAT_WARPS * 32] = 0.0f;
+    for (int k = 0; k < 15; ++k) hist[k * FEAT_WARPS * 32] = 0.0f;
 #pragma unroll
     for (int c = gl; c < 32; c += FEAT_G) s_f[g][c] = (c >= 2 && c < 16) ? 1.0f : 0.0f;
     int32_t nu = 0, nbd = 0;  // bonds, bonded neighbours among them
@@ -955,13 +960,15 @@ __global__ void __launch_bounds__(FEAT_WARPS * 32, 8) k_features(int64_t n, cons
         const float cx = va.x - vb.x, cy = va.y - vb.y, cz = va.z - vb.z;
         const float c2 = fmaxf(fmaf(cx, cx, fmaf(cy, cy, cz * cz)), 1e-30f);
         const float chord = c2 * rsqrtf(c2);
-        const float x = (chord - hlo) * 20.0f - 0.5f;
+        // position among the bin centres, clamped to [0, 13]: a chord beyond
+        // either end puts weight 1 on the end bin and 0 on its neighbour (the
+        // guard row beyond bin 13)
+        const float x = fminf(fmaxf((chord - hlo) * 20.0f - 0.5f, 0.0f), 13.0f);
         const float fl = floorf(x);
-        const int b0 = (int)fl;
-        const bool edge = b0 < 0 || b0 >= 13;
-        const float t = edge ? 0.0f : x - fl;
-        hist[min(max(b0, 0), 13) * (FEAT_WARPS * 32)] += 1.0f - t;
-        hist[min(max(b0 + 1, 0), 13) * (FEAT_WARPS * 32)] += t;
+        const float t = x - fl;
+        float *h0 = hist + (int)fl * (FEAT_WARPS * 32);
+        h0[0] += 1.0f - t;
+        h0[FEAT_WARPS * 32] += t;
     }
     // sorted bond lengths: the rank of each (ties ordered by slot), two
     // bonds per lane per pass over the others
