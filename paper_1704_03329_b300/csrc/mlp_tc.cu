@@ -377,13 +377,10 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_infer_tc(int64_t n, const __
 int mlp_infer_tc(ppmd_ctx *ctx, int64_t n, const __nv_bfloat16 *x, const float *params, float *logits, int8_t *cls,
                  float *conf, float threshold, int32_t *fallback, int32_t *n_fallback) {
     if (n <= 0) return PPMD_OK;
-    static bool attr = false;
-    if (!attr) {
-        PPMD_TRY(cuda_check(ctx, cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)SM_REQUEST),
-                            "cudaFuncSetAttribute"));
-        attr = true;
-    }
+    // (a per-device setting: set on every call, on the context's device)
+    PPMD_TRY(cuda_check(ctx, cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)SM_REQUEST),
+                        "cudaFuncSetAttribute"));
     uint8_t *img = (uint8_t *)scratch(ctx, S_MLPTC, IMG_TC_BYTES);
     if (!img) return PPMD_ERR_NOMEM;
     PPMD_LAUNCH(ctx, k_pack_tc, 32, 256, 0, params, img);
