@@ -417,16 +417,22 @@ __global__ void __launch_bounds__(ACNA_WARPS * 32) k_acna(int64_t n, const int4 
             r2f[q] = __int_as_float(0x7f800000);  // +inf
         }
     }
-    // FP32 rank by (r2, index)
+    // FP32 rank by (r2, index) among the deg candidates (slots past the row
+    // hold +inf and never come first)
     int rk[2] = {0, 0};
-    for (int src = 0; src < 32; ++src)
-#pragma unroll
-        for (int q2 = 0; q2 < 2; ++q2) {
-            const float r = __shfl_sync(0xffffffffu, r2f[q2], src);
-            const int32_t jv = __shfl_sync(0xffffffffu, jj[q2], src);
-#pragma unroll
-            for (int q = 0; q < 2; ++q) rk[q] += (r < r2f[q]) || (r == r2f[q] && jv < jj[q]);
-        }
+    const int d0 = min(deg, 32), d1 = deg - 32;  // sources in the first and second slot of each lane
+    for (int src = 0; src < d0; ++src) {
+        const float r = __shfl_sync(0xffffffffu, r2f[0], src);
+        const int32_t jv = __shfl_sync(0xffffffffu, jj[0], src);
+        rk[0] += (r < r2f[0]) || (r == r2f[0] && jv < jj[0]);
+        if (d1 > 0) rk[1] += (r < r2f[1]) || (r == r2f[1] && jv < jj[1]);
+    }
+    for (int src = 0; src < d1; ++src) {
+        const float r = __shfl_sync(0xffffffffu, r2f[1], src);
+        const int32_t jv = __shfl_sync(0xffffffffu, jj[1], src);
+        rk[0] += (r < r2f[0]) || (r == r2f[0] && jv < jj[0]);
+        rk[1] += (r < r2f[1]) || (r == r2f[1] && jv < jj[1]);
+    }
     int8_t lab = PPMD_OTHER;
     double rc12 = 0.0, rc14 = 0.0;
     for (int test = 0; test < 2; ++test) {
@@ -470,9 +476,9 @@ __global__ void __launch_bounds__(ACNA_WARPS * 32) k_acna(int64_t n, const int4 
                 }
             }
             ex[0] = ex[1] = 0;
-            for (int src = 0; src < 32; ++src)
 #pragma unroll
-                for (int q2 = 0; q2 < 2; ++q2) {
+            for (int q2 = 0; q2 < 2; ++q2)
+                for (int src = 0; src < (q2 ? d1 : d0); ++src) {
                     const bool nv = __shfl_sync(0xffffffffu, near[q2], src);
                     const double dv = __shfl_sync(0xffffffffu, d64[q2], src);
                     const int32_t jv = __shfl_sync(0xffffffffu, jj[q2], src);
@@ -517,9 +523,9 @@ __global__ void __launch_bounds__(ACNA_WARPS * 32) k_acna(int64_t n, const int4 
                     have64[q] = true;
                 }
             int er[2] = {0, 0};  // FP64 rank among the selected
-            for (int src = 0; src < 32; ++src)
 #pragma unroll
-                for (int q2 = 0; q2 < 2; ++q2) {
+            for (int q2 = 0; q2 < 2; ++q2)
+                for (int src = 0; src < (q2 ? d1 : d0); ++src) {
                     const bool sv = __shfl_sync(0xffffffffu, sel[q2], src);
                     const double dv = __shfl_sync(0xffffffffu, d64[q2], src);
                     const int32_t jv = __shfl_sync(0xffffffffu, jj[q2], src);
@@ -551,19 +557,28 @@ __global__ void __launch_bounds__(ACNA_WARPS * 32) k_acna(int64_t n, const int4 
         // bonds among the N selected (bit b of s_A[a]: a and b closer than
         // rc): FP32 against the FP32 cutoff outside a band that covers both
         // errors, the FP64 test against the exact cutoff inside it
+        // (each pair tested once, both bits set: lane a takes the pairs
+        // (a, a + o mod N), o = 1 .. N/2, o = N/2 only for a < N/2)
         const float bandb = 2e-5f * rc2f + 1e-6f;
+        if (lane < N) s_A[w][lane] = 0u;
+        __syncwarp();
         unsigned m = 0u, und = 0u;
         if (lane < N) {
             const int4 xa = s_x[w][lane];
-            for (int b = 0; b < N; ++b) {
-                if (b == lane) continue;
+            const int half = N >> 1, last = lane >= half ? half - 1 : half;  // N is even
+            for (int o = 1; o <= last; ++o) {
+                const int b = lane + o < N ? lane + o : lane + o - N;
                 const int4 xb = s_x[w][b];
                 const float dx = fixed_delta((uint32_t)xa.x, (uint32_t)xb.x, S.sx[0]);
                 const float dy = fixed_delta((uint32_t)xa.y, (uint32_t)xb.y, S.sx[1]);
                 const float dz = fixed_delta((uint32_t)xa.z, (uint32_t)xb.z, S.sx[2]);
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 < rc2f - bandb) m |= 1u << b;
-                else if (r2 <= rc2f + bandb) und |= 1u << b;
+                if (r2 < rc2f - bandb) {
+                    m |= 1u << b;
+                    atomicOr(&s_A[w][b], 1u << lane);
+                } else if (r2 <= rc2f + bandb) {
+                    und |= 1u << b;
+                }
             }
         }
         if (__any_sync(0xffffffffu, und != 0u)) {
@@ -573,11 +588,14 @@ __global__ void __launch_bounds__(ACNA_WARPS * 32) k_acna(int64_t n, const int4 
                 for (unsigned u = und; u; u &= u - 1) {
                     const int b = __ffs(u) - 1;
                     double dr[3];
-                    if (min_image_r2(pa, pos64 + 3 * (int64_t)s_j[w][b], S, dr) < rc2) m |= 1u << b;
+                    if (min_image_r2(pa, pos64 + 3 * (int64_t)s_j[w][b], S, dr) < rc2) {
+                        m |= 1u << b;
+                        atomicOr(&s_A[w][b], 1u << lane);
+                    }
                 }
             }
         }
-        if (lane < N) s_A[w][lane] = m;
+        if (lane < N) atomicOr(&s_A[w][lane], m);
         __syncwarp();
         int c421 = 0, c422 = 0, c444 = 0, c666 = 0;
         if (lane < N) {
