@@ -239,7 +239,7 @@ int ppmd_analyze(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *bo
  * binning, one list build and one launch per analysis for all of them):
  * box b (boxes[b], host array) holds atoms atom_off[b] .. atom_off[b+1]-1
  * of pos (atom_off: host int64 array of nbox + 1 offsets, atom_off[0] = 0,
- * non-decreasing; n = atom_off[nbox] < 2^31).  Atoms of different boxes
+ * non-decreasing; 1 <= nbox < 2^31; n = atom_off[nbox] < 2^31).  Atoms of different boxes
  * never interact.  Outputs and their layout as ppmd_analyze over the n
  * atoms (caller order); every box must hold at least 3 cells of edge
  * max(r_boa, r_cna) along each axis.  List capacity: the largest over the

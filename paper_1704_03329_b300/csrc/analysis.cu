@@ -1138,7 +1138,8 @@ __global__ void k_seg_of(int64_t n, const int64_t *__restrict__ off, int32_t nbo
 }
 
 int check_boxes(ppmd_ctx *ctx, int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes, const char *who) {
-    if (nbox < 1 || !atom_off || !boxes) return set_error(ctx, PPMD_ERR_INVALID, "%s: bad box set", who);
+    if (nbox < 1 || nbox >= ((int64_t)1 << 31) || !atom_off || !boxes)
+        return set_error(ctx, PPMD_ERR_INVALID, "%s: bad box set", who);
     if (atom_off[0] != 0) return set_error(ctx, PPMD_ERR_INVALID, "%s: atom_off[0] must be 0", who);
     for (int64_t b = 0; b < nbox; ++b)
         if (atom_off[b + 1] < atom_off[b]) return set_error(ctx, PPMD_ERR_INVALID, "%s: atom_off decreases at %lld", who, (long long)b);

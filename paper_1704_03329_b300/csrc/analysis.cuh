@@ -45,7 +45,7 @@ int sorted_snapshot_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const 
                           const ppmd_box *boxes, double r_list, int32_t max_nbr, Snapshot &s);
 // Largest snapshot_capacity over the boxes.
 int32_t snapshot_capacity_boxes(int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes, double r_list);
-// Checks a box set: nbox >= 1, atom_off[0] = 0, non-decreasing, total < 2^31.
+// Checks a box set: 1 <= nbox < 2^31, atom_off[0] = 0, non-decreasing, total < 2^31.
 int check_boxes(ppmd_ctx *ctx, int64_t nbox, const int64_t *atom_off, const ppmd_box *boxes, const char *who);
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
                const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
