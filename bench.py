@@ -150,17 +150,45 @@ def cpu_baseline(c_cells, steps):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, one host thread, on
+    this arm's workload.  Each step is one step of a bounded sample of it: an
+    fcc box of the same density, noise, temperature, cutoffs and list policy,
+    sized from a short calibration so that the W warm-up and K timed steps
+    take a few minutes."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    cb = cpu_baseline(args.cpu_cells, args.cpu_steps)
+    import oracle
     from synth import configs
-    n = len(configs.lj_solid(n_cells=args.cpu_cells)["pos"])
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.cpu_steps, "warmup": 0, "ms_per_step": n / cb["value"] * 1e3 if cb["value"] else None,
+    oracle.build()
+    K, W = max(1, args.steps), max(0, args.warmup)
+    cal = configs.lj_solid(n_cells=8)
+    t0 = time.perf_counter()
+    oracle.md_run(cal["pos"], cal["vel"], cal["box"], 10, r_list=2.8, rebuild_every=10)
+    rate = len(cal["pos"]) * 10 / (time.perf_counter() - t0)
+    budget = 150.0  # seconds of timed steps
+    cells = int(round((rate * budget / K / 4.0) ** (1.0 / 3.0)))
+    cells = max(6, min(args.cpu_cells, cells))  # at least three list cells per edge
+    c = configs.lj_solid(n_cells=cells)
+    n = len(c["pos"])
+    if W:
+        oracle.md_run(c["pos"], c["vel"], c["box"], W, r_list=2.8, rebuild_every=10)
+    t0 = time.perf_counter()
+    oracle.md_run(c["pos"], c["vel"], c["box"], K, r_list=2.8, rebuild_every=10)
+    dt = time.perf_counter() - t0
+    value = n * K / dt
+    sample = (f"FP64 C oracle, 1 thread: {K} steps (after {W} warm-up steps) of an fcc {cells}^3 box "
+              f"({n} atoms) with the workload's density, noise, temperature, cutoffs and list policy "
+              f"(set-up list build + rebuild every 10), {dt:.1f} s")
+    full = 4 * args.cells ** 3
+    config = dict(workload_desc(args.cells, full), pair_precision="fp64 (oracle)", cuda_graph=False,
+                  sample_atoms=n)
+    cb = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": n / value * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_desc(args.cpu_cells, n), "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": config, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 

@@ -1,6 +1,7 @@
 """The multi-rank host logic of the replica-parallel runs, with the gloo
 backend on CPU (world size 2): distinct seeds, a partition of the units, the
 maximum of the ranks' times, and the reference arm printing on rank 0 only."""
+import json
 import os
 import subprocess
 import sys
@@ -60,3 +61,19 @@ def test_reference_arm_prints_on_rank_0_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--cpu-cells", "8",
                         "--cpu-steps", "1"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_reference_arm_line_on_rank_0():
+    """Rank 0 prints one JSON line: the oracle on this arm's workload, the
+    requested steps and warm-up, with its cpu_baseline and e2e entries."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--cpu-cells", "6",
+                        "--steps", "3", "--warmup", "1"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 3 and d["warmup"] == 1 and d["value"] > 0
+    assert d["config"]["atoms"] == 4 * 63 ** 3 and d["config"]["sample_atoms"] == 4 * 6 ** 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
