@@ -131,3 +131,21 @@ def test_boxes_with_an_empty_box_and_all_empty(L, ctx, box_set):
     out = L.ppmd_analyze_boxes(ctx, empty, [0, 0], [[9.0, 9.0, 9.0]], R_BOA, R_CNA)
     ctx.sync()
     assert lab.numel() == 0 and nfb == 0 and out["label"].numel() == 0
+
+
+def test_classify_boxes_full_size_exact_mode(L, ctx):
+    """The classifier suite's inference set at full size (32 boxes, 4,096,000
+    atoms) through one box-set call in exact mode, as the bench times it:
+    every label of four of the boxes against the oracle's CNA of that box."""
+    test = configs.classifier_boxes(51)
+    pos = np.concatenate([b["pos"] for b in test])
+    off = np.cumsum([0] + [len(b["pos"]) for b in test]).tolist()
+    assert off[-1] == 4096000
+    lab, _, _ = L.ppmd_classify_boxes(ctx, cu(pos), off, [b["box"] for b in test], mode=0, r_cna=R_CNA)
+    ctx.sync()
+    lab = lab.cpu().numpy()
+    for bi in (0, 9, 18, 27):
+        b = test[bi]
+        offs, nb = oracle.neighbours_cells(b["pos"], b["box"], R_CNA)
+        lab_o = oracle.cna_label(*oracle.cna(b["pos"], b["box"], offs, nb, R_CNA)[:2])
+        assert np.array_equal(lab[off[bi]:off[bi + 1]], lab_o), bi

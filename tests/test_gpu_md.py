@@ -319,6 +319,28 @@ def test_md_fp32_solid_10_steps(L, ctx, use_graph):
     assert abs(en[9, 0] - eno[9, 0]) <= 1e-6 * abs(eno[9, 0])
 
 
+def test_md_fp32_full_size_sampled(L, ctx):
+    """The 1,000,188-atom solid in the launch configuration the bench times
+    (FP32 pair loop, graph replay, list 2.8 rebuilt every 10, 128 list
+    slots): after 10 steps, the forces of a seeded sample of 400 atoms
+    against the oracle on the same positions (the oracle's neighbour rows
+    restricted to the sample, so it only works on those atoms)."""
+    c = configs.lj_solid()
+    assert len(c["pos"]) == 1000188
+    p, v, F, en, info = _md(L, ctx, c, L.FP32, 10, True, energy_every=10)
+    assert info["steps"] == 10
+    sample = np.sort(np.random.default_rng(5).choice(len(p), 400, replace=False))
+    offs, nb = oracle.neighbours_cells(p, c["box"], 2.8)
+    deg = np.zeros(len(p), np.int64)
+    deg[sample] = np.diff(offs)[sample]
+    offs_s = np.concatenate([[0], np.cumsum(deg)])
+    nb_s = np.concatenate([nb[offs[i]:offs[i + 1]] for i in sample])
+    Fo, _, _, _ = oracle.lj(p, c["box"], offs_s, nb_s)
+    rms = np.sqrt((Fo[sample] ** 2).sum(1).mean())
+    assert np.sqrt(((F[sample] - Fo[sample]) ** 2).sum(1)).max() <= 1e-5 * rms
+    assert np.isfinite(en[9]).all()
+
+
 def test_md_fp64_solid_10_steps_is_exact(L, ctx):
     c = configs.lj_solid(n_cells=8)
     po, vo, Fo, eno, _ = oracle.md_run(c["pos"], c["vel"], c["box"], 10, r_list=2.8, rebuild_every=10)
