@@ -786,7 +786,7 @@ int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, co
 
 int cna_subset_launch(ppmd_ctx *ctx, int64_t m_max, const int32_t *m_dev, const int32_t *which, const int4 *xq,
                       const double *pos64, const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr,
-                      int64_t ld, double r_cut, double Lmax, int8_t *label) {
+                      int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, int8_t *label) {
     float lo, hi;
     cutoff_band(r_cut * r_cut, Lmax, &lo, &hi);
     // a grid of a few blocks per SM strides over however many atoms the
@@ -795,7 +795,7 @@ int cna_subset_launch(ppmd_ctx *ctx, int64_t m_max, const int32_t *m_dev, const 
     if (m_max > 0)
         PPMD_LAUNCH(ctx, k_cna, grid, CNA_WARPS * 32, 0, m_max, xq, pos64, st, nbr, cnt, max_nbr,
                     ld ? 1 : (int64_t)max_nbr, ld ? ld : 1, r_cut * r_cut,
-                    lo, hi, nullptr, nullptr, label, ctx->d_status, ctx->d_needed, which, m_dev);
+                    lo, hi, out_idx, nullptr, label, ctx->d_status, ctx->d_needed, which, m_dev);
     return check_launch(ctx, "cna_subset");
 }
 

@@ -54,10 +54,10 @@ int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, co
                const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
                int8_t *label);
 // CNA labels of the snapshot atoms listed in `which` (m of them), written
-// at label[which[k]].
+// at label[out_idx[which[k]]] (label[which[k]] when out_idx is null).
 int cna_subset_launch(ppmd_ctx *ctx, int64_t m_max, const int32_t *m_dev, const int32_t *which, const int4 *xq, const double *pos64,
                       const SegTable &st, const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut,
-                      double Lmax, int8_t *label);
+                      double Lmax, const int32_t *out_idx, int8_t *label);
 // Classifier features (30 per atom) of the snapshot atoms, written at out_idx.
 int features_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st,
                     const int32_t *nbr, const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_feat, double r_ref, double Lmax,

@@ -692,20 +692,10 @@ extern "C" int ppmd_mlp_train_step(ppmd_ctx *ctx, float *params, float *m, float
 }
 
 // ---------------------------------------------------------------------
-// Classification pipeline.
+// Classification pipeline: features, MLP class and confidence written in
+// the caller's order, exact CNA over the low-confidence atoms written over
+// their class.
 // ---------------------------------------------------------------------
-namespace ppmd {
-__global__ void k_write_labels(int64_t n, const int32_t *__restrict__ perm, const int8_t *__restrict__ cls,
-                               const float *__restrict__ conf_s, int8_t *__restrict__ label, float *__restrict__ conf) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int64_t o = perm[k];
-    label[o] = cls[k];
-    if (conf) conf[o] = conf_s[k];
-}
-
-}  // namespace ppmd
-
 extern "C" int ppmd_classify_boxes(ppmd_ctx *ctx, int mode, const double *pos, int64_t nbox, const int64_t *atom_off,
                                    const ppmd_box *boxes, double r_feat, double r_cna, const float *params, float threshold,
                                    int8_t *label, float *confidence, int64_t *n_fallback) {
@@ -726,19 +716,17 @@ extern "C" int ppmd_classify_boxes(ppmd_ctx *ctx, int mode, const double *pos, i
         Snapshot s;
         PPMD_TRY(sorted_snapshot_boxes(ctx, pos, nbox, atom_off, boxes, r_feat, max_nbr, s));
         __nv_bfloat16 *feat = (__nv_bfloat16 *)scratch(ctx, S_TMP0, sizeof(__nv_bfloat16) * 32 * nn);
-        int8_t *cls = (int8_t *)scratch(ctx, S_TMP1, nn + 16);
-        float *conf_s = (float *)scratch(ctx, S_TMP2, sizeof(float) * nn);
         int32_t *fb = (int32_t *)scratch(ctx, S_AUX1, sizeof(int32_t) * nn);
-        if (!feat || !cls || !conf_s || !fb) return PPMD_ERR_NOMEM;
+        if (!feat || !fb) return PPMD_ERR_NOMEM;
         int32_t *nfb = ctx->d_status + 4;  // the fallback count, read back with the status
         PPMD_TRY(features_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, r_cna, s.Lmax, nullptr,
                                  nullptr, feat));
-        PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(nfb, 0, sizeof(int32_t), ctx->stream), "memset"));
-        PPMD_TRY(mlp_infer_tc(ctx, n, feat, params, nullptr, cls, conf_s, threshold, fb, nfb));
+        // MLP class and confidence of every atom, in the caller's order
+        PPMD_TRY(mlp_infer_tc(ctx, n, feat, params, nullptr, label, confidence, threshold, fb, nfb, s.perm));
         // exact CNA for the low-confidence atoms (as many as the device
         // found), written over their MLP class
-        PPMD_TRY(cna_subset_launch(ctx, n, nfb, fb, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax, cls));
-        if (n > 0) PPMD_LAUNCH(ctx, k_write_labels, div_up(n, 256), 256, 0, n, s.perm, cls, conf_s, label, confidence);
+        PPMD_TRY(cna_subset_launch(ctx, n, nfb, fb, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_cna, s.Lmax,
+                                   s.perm, label));
         PPMD_TRY(check_launch(ctx, "ppmd_classify"));
         if (!n_fallback) return PPMD_OK;  // asynchronous: an overflow stays latched
         int32_t hfb = 0;

@@ -183,7 +183,8 @@ __device__ __forceinline__ void relu_to_h(uint8_t *smem, uint32_t h_base, uint32
 constexpr uint32_t IMG_TC_BYTES = SM_BAR - SM_W1;
 static_assert(IMG_TC_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
 
-__global__ void k_pack_tc(const float *__restrict__ p, uint8_t *__restrict__ img) {
+__global__ void k_pack_tc(const float *__restrict__ p, uint8_t *__restrict__ img, int32_t *n_fallback) {
+    if (n_fallback && blockIdx.x == 0 && threadIdx.x == 0) *n_fallback = 0;  // before the inference kernel runs
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 64 * 32 + 64 * 64 + 16 * 64 + 144 + 64;
          e += gridDim.x * blockDim.x) {
         if (e < 64 * 32) {
@@ -214,7 +215,8 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_infer_tc(int64_t n, const __
                                                              const uint8_t *__restrict__ img, float *__restrict__ logits,
                                                              int8_t *__restrict__ cls, float *__restrict__ conf,
                                                              float threshold, int32_t *__restrict__ fallback,
-                                                             int32_t *__restrict__ n_fallback, int32_t *status) {
+                                                             int32_t *__restrict__ n_fallback,
+                                                             const int32_t *__restrict__ out_idx, int32_t *status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(smem);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -333,8 +335,9 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_infer_tc(int64_t n, const __
             if (logits)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) logits[r * 4 + c] = l[c];
-            if (cls) cls[r] = (int8_t)best;
-            if (conf) conf[r] = pb;
+            const int64_t o = out_idx ? out_idx[r] : r;
+            if (cls) cls[o] = (int8_t)best;
+            if (conf) conf[o] = pb;
             if (fallback && pb < threshold) fallback[atomicAdd(n_fallback, 1)] = (int32_t)r;
         }
     };
@@ -375,20 +378,21 @@ __global__ void __launch_bounds__(TC_ROWS, 1) k_mlp_infer_tc(int64_t n, const __
 }  // namespace
 
 int mlp_infer_tc(ppmd_ctx *ctx, int64_t n, const __nv_bfloat16 *x, const float *params, float *logits, int8_t *cls,
-                 float *conf, float threshold, int32_t *fallback, int32_t *n_fallback) {
-    if (n <= 0) return PPMD_OK;
+                 float *conf, float threshold, int32_t *fallback, int32_t *n_fallback, const int32_t *out_idx) {
+    if (n <= 0) return n_fallback ? cuda_check(ctx, cudaMemsetAsync(n_fallback, 0, sizeof(int32_t), ctx->stream), "memset")
+                                  : PPMD_OK;
     // (a per-device setting: set on every call, on the context's device)
     PPMD_TRY(cuda_check(ctx, cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)SM_REQUEST),
                         "cudaFuncSetAttribute"));
     uint8_t *img = (uint8_t *)scratch(ctx, S_MLPTC, IMG_TC_BYTES);
     if (!img) return PPMD_ERR_NOMEM;
-    PPMD_LAUNCH(ctx, k_pack_tc, 32, 256, 0, params, img);
+    PPMD_LAUNCH(ctx, k_pack_tc, 32, 256, 0, params, img, fallback ? n_fallback : nullptr);
     const int64_t ntile = (n + TC_ROWS - 1) / TC_ROWS;
     const int64_t npair = (ntile + 1) / 2;
     const int64_t grid = npair < 148 * TC_CTAS_PER_SM ? npair : 148 * TC_CTAS_PER_SM;
     PPMD_LAUNCH(ctx, k_mlp_infer_tc, grid, TC_ROWS, SM_REQUEST, n, x, img, logits, cls, conf, threshold, fallback,
-                n_fallback, ctx->d_status);
+                n_fallback, out_idx, ctx->d_status);
     return check_launch(ctx, "mlp_infer_tc");
 }
 
