@@ -200,6 +200,58 @@ __global__ void k_andersen(const int32_t *__restrict__ list, const int32_t *__re
     }
 }
 
+// The collisions of a step whose pair loop already made the next step's
+// kick and drift: each collider gets its new velocity (the draw of
+// k_andersen), and its next kick, drift, fixed-point word and displacement
+// are made again from it in the same arithmetic as the pair loop's
+// epilogue, so the state equals that of the separate kick and drift.
+// pos: the step's positions; pos_next, xq_next: those the pair loop wrote.
+__global__ void k_andersen_fused(const int32_t *__restrict__ list, const int32_t *__restrict__ count,
+                                 double *__restrict__ vel, const int32_t *__restrict__ orig, uint64_t seed, double sd,
+                                 const int64_t *__restrict__ base, int64_t step_off, const float4 *__restrict__ f4,
+                                 const double *__restrict__ pos, double *__restrict__ pos_next,
+                                 int4 *__restrict__ xq_next, const int4 *__restrict__ xq_ref, SegTable st, double h,
+                                 double dt, unsigned int *max_disp_bits) {
+    const int32_t m = *count;
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const int64_t i = list[t];
+        const int64_t step = (base ? *base : 0) + step_off;
+        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+        uint32_t u[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
+        philox4x32_10(u, k0, k1);
+        uint32_t w[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 1u};
+        philox4x32_10(w, k0, k1);
+        const double two_pi = 6.283185307179586, inv32 = 2.3283064365386962890625e-10;
+        const double U1 = __dmul_rn(__dadd_rn((double)u[1], 0.5), inv32);
+        const double U2 = __dmul_rn(__dadd_rn((double)u[2], 0.5), inv32);
+        const double U3 = __dmul_rn(__dadd_rn((double)u[3], 0.5), inv32);
+        const double U4 = __dmul_rn(__dadd_rn((double)w[0], 0.5), inv32);
+        const double r1 = sqrt(__dmul_rn(-2.0, log(U1))), t1 = __dmul_rn(two_pi, U2);
+        const double r2 = sqrt(__dmul_rn(-2.0, log(U3))), t2 = __dmul_rn(two_pi, U4);
+        const double vn[3] = {__dmul_rn(sd, __dmul_rn(r1, cos(t1))), __dmul_rn(sd, __dmul_rn(r1, sin(t1))),
+                              __dmul_rn(sd, __dmul_rn(r2, cos(t2)))};
+        const float4 fq = f4[i];
+        const double f[3] = {(double)fq.x, (double)fq.y, (double)fq.z};
+        const int4 ref = xq_ref[i];
+        const Seg &S = seg_ref(st, ref.w);
+        uint32_t q[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double v = fma(h, f[d], vn[d]);
+            const double r = fma(dt, v, pos[3 * i + d]);
+            vel[3 * i + d] = v;
+            pos_next[3 * i + d] = r;
+            q[d] = (uint32_t)(unsigned long long)__double2ll_rn(r * S.fxs[d]);
+        }
+        xq_next[i] = make_int4((int)q[0], (int)q[1], (int)q[2], ref.w);
+        const float ex = fixed_delta(q[0], (uint32_t)ref.x, S.sx[0]);
+        const float ey = fixed_delta(q[1], (uint32_t)ref.y, S.sx[1]);
+        const float ez = fixed_delta(q[2], (uint32_t)ref.z, S.sx[2]);
+        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        if (d2 > 0.0f) atomicMax(max_disp_bits, __float_as_uint(d2));
+    }
+}
+
 // Entries of the list W (column-major) closer than r_short (FP32 test
 // with a small margin: extra entries are harmless, the analysis decides
 // exactly) into W2 (column-major, capacity max2; more: PPMD_ERR_CAPACITY).
@@ -311,9 +363,10 @@ int forces(ppmd_md *m, bool energy, bool kick, bool drift = false) {
 // One step of Algorithm 6.  erow: device row receiving (KE, PE) on energy
 // steps; qrow: (mean Q4, Q5, Q6) on analysis steps.  The step's kick and
 // drift are skipped when the previous pair loop already made them; with
-// fuse_next (FP32) this step's pair loop makes the next step's, unless the
-// thermostat or the analysis needs the step to end first.  base: device step
-// number to add to s (graph capture), else null.
+// fuse_next (FP32) this step's pair loop makes the next step's (thermostat
+// collisions then make them again for the colliders, the analysis reads the
+// step's positions from the other buffer).  base: device step number to add
+// to s (graph capture), else null.
 int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow = nullptr,
              const int64_t *base = nullptr) {
     ppmd_ctx *ctx = m->ctx;
@@ -321,7 +374,6 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow =
     const bool energy = m->p.energy_every > 0 && (s % m->p.energy_every) == 0 && erow;
     const bool thermo = m->thermo_thr > 0;
     const bool analyse = m->boa_every > 0 && (s % m->boa_every) == 0;
-    if (thermo || analyse) fuse_next = false;
     if (!m->half_kicked)
         PPMD_TRY(md_kick_drift2(ctx, m->n, m->pos, m->vel, f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, m->xq,
                                 m->xq_ref, m->st, m->h, m->p.dt, m->max_disp_bits));
@@ -329,7 +381,11 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow =
     if (m->p.rebuild_every > 0 && s % m->p.rebuild_every == 0) {
         PPMD_TRY(rebuild(m));
     }
-    PPMD_TRY(forces(m, energy, true, fuse_next && f32));
+    // with the next step's kick and drift fused in, the step's positions
+    // stay in the other buffer (prev) for the thermostat and the analysis
+    const bool fused = fuse_next && f32;
+    PPMD_TRY(forces(m, energy, true, fused));
+    const int prev = fused ? m->cur ^ 1 : m->cur;
     if (energy) {
         PPMD_TRY(reduce_partials(ctx, m->part_f, lj_columns_blocks(m->n), 3, m->red));
         PPMD_LAUNCH(ctx, k_energy_row, 1, 1, 0, m->red, erow);
@@ -338,12 +394,17 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow =
         PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(m->coll_count, 0, sizeof(int32_t), ctx->stream), "memset"));
         PPMD_LAUNCH(ctx, k_andersen_decide, div_up(m->n, 256), 256, 0, m->n, m->orig, m->thermo_seed, m->thermo_thr,
                     base, s, m->coll_list, m->coll_count);
-        PPMD_LAUNCH(ctx, k_andersen, std::min<int64_t>(div_up(m->n, 128), 148 * 4), 128, 0, m->coll_list,
-                    m->coll_count, m->vel, m->orig, m->thermo_seed, m->thermo_sd, base, s);
+        if (fused)
+            PPMD_LAUNCH(ctx, k_andersen_fused, std::min<int64_t>(div_up(m->n, 128), 148 * 4), 128, 0, m->coll_list,
+                        m->coll_count, m->vel, m->orig, m->thermo_seed, m->thermo_sd, base, s, m->f4,
+                        m->pos_buf[prev], m->pos, m->xq, m->xq_ref, m->st, m->h, m->p.dt, m->max_disp_bits);
+        else
+            PPMD_LAUNCH(ctx, k_andersen, std::min<int64_t>(div_up(m->n, 128), 148 * 4), 128, 0, m->coll_list,
+                        m->coll_count, m->vel, m->orig, m->thermo_seed, m->thermo_sd, base, s);
     }
     if (analyse) {
-        PPMD_TRY(boa_otf_launch(ctx, m->n, m->xq, m->pos, m->st, m->W2, m->cnt2, m->max2, m->ld, m->r_boa, m->Lmax,
-                                m->orig, m->q3, m->part_q));
+        PPMD_TRY(boa_otf_launch(ctx, m->n, m->xq_buf[prev], m->pos_buf[prev], m->st, m->W2, m->cnt2, m->max2, m->ld,
+                                m->r_boa, m->Lmax, m->orig, m->q3, m->part_q));
         PPMD_TRY(reduce_partials(ctx, m->part_q, boa_otf_blocks(m->n), 3, m->red_q));
         if (qrow) PPMD_LAUNCH(ctx, k_q_row, 1, 32, 0, m->red_q, (double)(m->n > 0 ? m->n : 1), qrow);
         m->have_q = true;
