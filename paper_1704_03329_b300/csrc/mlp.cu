@@ -205,48 +205,6 @@ __device__ __forceinline__ void softmax4(const float (&l)[4], float (&p)[4]) {
 
 constexpr int MLP_WARPS = 4;
 
-// Inference: logits (optional), class = argmax, confidence = max softmax
-// probability; rows with confidence < threshold are appended to `fallback`.
-__global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_infer(int64_t n, const __nv_bfloat16 *__restrict__ x,
-                                                              const __nv_bfloat16 *__restrict__ img,
-                                                              const float *__restrict__ p, float *__restrict__ logits,
-                                                              int8_t *__restrict__ cls, float *__restrict__ conf,
-                                                              float threshold, int32_t *__restrict__ fallback,
-                                                              int32_t *__restrict__ n_fallback) {
-    __shared__ MlpSmem sm;
-    load_mlp_smem(sm, img, p);
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int64_t ntile = (n + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * MLP_WARPS + (threadIdx.x >> 5); tile < ntile;
-         tile += (int64_t)gridDim.x * MLP_WARPS) {
-        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-        Fwd f;
-        mlp_forward_tile(sm, r0 < n ? x + r0 * 32 : nullptr, r1 < n ? x + r1 * 32 : nullptr, f);
-        float la[4], lb[4];
-        quad_logits(f.z3, la, lb);
-        if (t < 2) {
-            const int64_t r = t == 0 ? r0 : r1;
-            float l[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) l[c] = t == 0 ? la[c] : lb[c];
-            if (r < n) {
-                float pr[4];
-                softmax4(l, pr);
-                int best = 0;
-#pragma unroll
-                for (int c = 1; c < 4; ++c)
-                    if (pr[c] > pr[best]) best = c;
-                if (logits)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) logits[r * 4 + c] = l[c];
-                if (cls) cls[r] = (int8_t)best;
-                if (conf) conf[r] = pr[best];
-                if (fallback && pr[best] < threshold) fallback[atomicAdd(n_fallback, 1)] = (int32_t)r;
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------
 // Training: forward and back-propagation of one tile per warp.  Stores, per
 // sample, h1 = relu(z1), h2 = relu(z2), d1 = dL/dz1, d2 = dL/dz2 (bf16
