@@ -45,6 +45,15 @@ __device__ __forceinline__ f2 sub2(f2 a, f2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+// A 16-byte list word, read once per step: not kept in L1, which then holds
+// the neighbour positions the loop gathers again and again.
+__device__ __forceinline__ int4 ld_stream4(const int4 *p) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -567,7 +576,7 @@ __global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld
         };
         // one 16-byte list word per four neighbours (entries past the row
         // are -1), loaded one group ahead of its use
-        auto group = [&](int32_t k) { return k < m ? __ldg(col4 + (int64_t)(k >> 2) * ld) : make_int4(-1, -1, -1, -1); };
+        auto group = [&](int32_t k) { return k < m ? ld_stream4(col4 + (int64_t)(k >> 2) * ld) : make_int4(-1, -1, -1, -1); };
         int4 g = group(0);
         for (int32_t k = 0; k < m; k += 4) {
             const int4 nx = group(k + 4);
