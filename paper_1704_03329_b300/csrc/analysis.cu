@@ -655,6 +655,14 @@ int acna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, c
     return check_launch(ctx, "acna");
 }
 
+// A list entry, read once per analysis: not kept in L1, which then holds
+// the neighbour positions.
+__device__ __forceinline__ int32_t ld_once_i32(const int32_t *p) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 // Q4, Q5, Q6 of the integrator's atoms (the on-the-fly analysis of
 // Sec. 5.3) over its column-major list W[m * ld + i], bonds r < r_cut:
 // per atom into q3 [3][n] at out_idx[i] (the caller's order) and per block
@@ -688,7 +696,7 @@ __global__ void __launch_bounds__(BOA_OTF_BLOCK) k_boa_otf(int64_t n, const int4
             int32_t jv[4];
             int4 xv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) jv[q] = k0 + q < deg ? __ldg(W + (int64_t)(k0 + q) * ld + i) : (int32_t)i;
+            for (int q = 0; q < 4; ++q) jv[q] = k0 + q < deg ? ld_once_i32(W + (int64_t)(k0 + q) * ld + i) : (int32_t)i;
 #pragma unroll
             for (int q = 0; q < 4; ++q) xv[q] = __ldg(&xq[jv[q]]);
 #pragma unroll
