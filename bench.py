@@ -133,6 +133,20 @@ def traffic_per_atom():
     return float(d["dram_bytes_per_atom"])
 
 
+def host_cpu():
+    """The host's CPU model and logical core count (context for the oracle timings)."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"host_cpu": model, "host_cores": os.cpu_count()}
+
+
 def cpu_baseline(c_cells, steps):
     """The oracle as it stands, single thread, on a bounded sample: the full
     workload for `steps` steps (including its list builds)."""
@@ -144,7 +158,7 @@ def cpu_baseline(c_cells, steps):
     t0 = time.perf_counter()
     oracle.md_run(c["pos"], c["vel"], c["box"], steps, r_list=2.8, rebuild_every=10)
     dt = time.perf_counter() - t0
-    return {"value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {**host_cpu(), "value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"FP64 C oracle, {n} atoms x {steps} steps (set-up list build + rebuild every 10), "
                       f"{dt:.1f} s wall, 1 thread"}
 
@@ -183,7 +197,7 @@ def run_reference(args):
     full = 4 * args.cells ** 3
     config = dict(workload_desc(args.cells, full), pair_precision="fp64 (oracle)", cuda_graph=False,
                   sample_atoms=n)
-    cb = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    cb = {**host_cpu(), "value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": n / value * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
