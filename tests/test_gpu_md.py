@@ -375,6 +375,32 @@ def test_md_batched_boxes_equal_single_runs(L, ctx):
         assert _pos_err(P[off[k]:off[k + 1]], po, r["box"]) <= bound
 
 
+def test_md_replicas_full_size_sampled(L, ctx):
+    """The 256-replica workload (2,034,923 atoms) in the launch configuration
+    the bench times (one launch per kernel for all boxes, graph replay, 160
+    list slots): after 10 steps, the forces of eight seeded boxes against the
+    oracle on the same positions."""
+    reps = configs.replicas()
+    pos = np.concatenate([r["pos"] for r in reps])
+    vel = np.concatenate([r["vel"] for r in reps])
+    off = np.cumsum([0] + [len(r["pos"]) for r in reps])
+    assert len(reps) == 256 and off[-1] == 2034923
+    md = L.MD(ctx, off, [r["box"] for r in reps], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=160, prec=L.FP32,
+              box_r_list=[r["r_list"] for r in reps])
+    md.set_state(cu(pos), cu(vel))
+    md.run(10)
+    P = torch.empty((off[-1], 3), dtype=torch.float64, device="cuda")
+    F = torch.empty_like(P)
+    md.get_state(P, None, F)
+    P, F = P.cpu().numpy(), F.cpu().numpy()
+    md.close()
+    for k in np.random.default_rng(6).choice(256, 8, replace=False):
+        r, lo, hi = reps[k], off[k], off[k + 1]
+        offs, nb = oracle.neighbours_cells(P[lo:hi], r["box"], r["r_list"])
+        Fo, _, _, _ = oracle.lj(P[lo:hi], r["box"], offs, nb)
+        assert force_err(F[lo:hi], Fo) <= 1e-5, k
+
+
 def test_md_fused_kick_drift_is_bit_identical(L, ctx):
     """Inside a run the FP32 pair loop also makes the next step's kick and
     drift (the same arithmetic as the separate kernel): one run of 23 steps
