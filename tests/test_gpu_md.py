@@ -471,6 +471,31 @@ def test_otf_run_matches_oracle(L, ctx, use_graph):
     assert np.abs(en[4::5, 0] - eno[4::5, 0]).max() <= 1e-6 * np.abs(eno[4::5, 0]).max()
 
 
+def test_otf_full_size_q_against_oracle(L, ctx):
+    """The on-the-fly analysis workload at full size (524,288 atoms, r_c 3.0,
+    list 3.3, rebuild every 18, thermostat and Q4/Q5/Q6 every step) in the
+    bench's launch configuration (one 18-step graph replay): every atom's
+    Q4, Q5, Q6 of the last step against the oracle on the final positions."""
+    c = configs.otf_box()
+    n = len(c["pos"])
+    assert n == 524288
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=3.3, rc=3.0, rebuild_every=18, max_nbr=192, prec=L.FP32,
+              energy_every=18)
+    md.set_thermostat(0.1, 1.0, 20170410)
+    md.set_boa(1, 1.5)
+    md.set_state(cu(c["pos"]), cu(c["vel"]))
+    md.run_analysed(18, None, None, use_graph=True)
+    p = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    md.get_state(p)
+    q = md.get_q().cpu().numpy()
+    md.close()
+    p = p.cpu().numpy()
+    offs, nb = oracle.neighbours_cells(p, c["box"], 1.5)
+    for row, l in enumerate((4, 5, 6)):
+        Qo, _ = oracle.boa(p, c["box"], offs, nb, 1.5, l)
+        assert np.abs(q[row] - Qo).max() <= 1e-5, l
+
+
 def test_otf_graph_and_single_steps_are_bit_identical(L, ctx):
     """Graph replays take the thermostat's step numbers from the device: the
     same bits as single steps."""
