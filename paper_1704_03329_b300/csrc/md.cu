@@ -175,28 +175,39 @@ __global__ void k_andersen_decide(int64_t n, const int32_t *__restrict__ orig, u
     if (hit) list[at + __popc(b & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
+// The new velocity of a collider (atom orig_id, step): Maxwell-Boltzmann
+// components of standard deviation sd by Box-Muller in FP64 from the
+// Philox4x32-10 words of the counters (orig_id, step, 0) and (orig_id,
+// step, 1).
+__device__ __forceinline__ void andersen_draw(int32_t orig_id, int64_t step, uint64_t seed, double sd, double (&v)[3]) {
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    uint32_t u[4] = {(uint32_t)orig_id, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
+    philox4x32_10(u, k0, k1);
+    uint32_t w[4] = {(uint32_t)orig_id, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 1u};
+    philox4x32_10(w, k0, k1);
+    const double two_pi = 6.283185307179586, inv32 = 2.3283064365386962890625e-10;
+    const double U1 = __dmul_rn(__dadd_rn((double)u[1], 0.5), inv32);
+    const double U2 = __dmul_rn(__dadd_rn((double)u[2], 0.5), inv32);
+    const double U3 = __dmul_rn(__dadd_rn((double)u[3], 0.5), inv32);
+    const double U4 = __dmul_rn(__dadd_rn((double)w[0], 0.5), inv32);
+    const double r1 = sqrt(__dmul_rn(-2.0, log(U1))), t1 = __dmul_rn(two_pi, U2);
+    const double r2 = sqrt(__dmul_rn(-2.0, log(U3))), t2 = __dmul_rn(two_pi, U4);
+    v[0] = __dmul_rn(sd, __dmul_rn(r1, cos(t1)));
+    v[1] = __dmul_rn(sd, __dmul_rn(r1, sin(t1)));
+    v[2] = __dmul_rn(sd, __dmul_rn(r2, cos(t2)));
+}
+
 __global__ void k_andersen(const int32_t *__restrict__ list, const int32_t *__restrict__ count,
                            double *__restrict__ vel, const int32_t *__restrict__ orig, uint64_t seed, double sd,
                            const int64_t *__restrict__ base, int64_t step_off) {
     const int32_t m = *count;
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
         const int64_t i = list[t];
-        const int64_t step = (base ? *base : 0) + step_off;
-        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-        uint32_t u[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
-        philox4x32_10(u, k0, k1);
-        uint32_t w[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 1u};
-        philox4x32_10(w, k0, k1);
-        const double two_pi = 6.283185307179586, inv32 = 2.3283064365386962890625e-10;
-        const double U1 = __dmul_rn(__dadd_rn((double)u[1], 0.5), inv32);
-        const double U2 = __dmul_rn(__dadd_rn((double)u[2], 0.5), inv32);
-        const double U3 = __dmul_rn(__dadd_rn((double)u[3], 0.5), inv32);
-        const double U4 = __dmul_rn(__dadd_rn((double)w[0], 0.5), inv32);
-        const double r1 = sqrt(__dmul_rn(-2.0, log(U1))), t1 = __dmul_rn(two_pi, U2);
-        const double r2 = sqrt(__dmul_rn(-2.0, log(U3))), t2 = __dmul_rn(two_pi, U4);
-        vel[3 * i] = __dmul_rn(sd, __dmul_rn(r1, cos(t1)));
-        vel[3 * i + 1] = __dmul_rn(sd, __dmul_rn(r1, sin(t1)));
-        vel[3 * i + 2] = __dmul_rn(sd, __dmul_rn(r2, cos(t2)));
+        double v[3];
+        andersen_draw(orig[i], (base ? *base : 0) + step_off, seed, sd, v);
+        vel[3 * i] = v[0];
+        vel[3 * i + 1] = v[1];
+        vel[3 * i + 2] = v[2];
     }
 }
 
@@ -215,21 +226,8 @@ __global__ void k_andersen_fused(const int32_t *__restrict__ list, const int32_t
     const int32_t m = *count;
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
         const int64_t i = list[t];
-        const int64_t step = (base ? *base : 0) + step_off;
-        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-        uint32_t u[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 0u};
-        philox4x32_10(u, k0, k1);
-        uint32_t w[4] = {(uint32_t)orig[i], (uint32_t)step, (uint32_t)((uint64_t)step >> 32), 1u};
-        philox4x32_10(w, k0, k1);
-        const double two_pi = 6.283185307179586, inv32 = 2.3283064365386962890625e-10;
-        const double U1 = __dmul_rn(__dadd_rn((double)u[1], 0.5), inv32);
-        const double U2 = __dmul_rn(__dadd_rn((double)u[2], 0.5), inv32);
-        const double U3 = __dmul_rn(__dadd_rn((double)u[3], 0.5), inv32);
-        const double U4 = __dmul_rn(__dadd_rn((double)w[0], 0.5), inv32);
-        const double r1 = sqrt(__dmul_rn(-2.0, log(U1))), t1 = __dmul_rn(two_pi, U2);
-        const double r2 = sqrt(__dmul_rn(-2.0, log(U3))), t2 = __dmul_rn(two_pi, U4);
-        const double vn[3] = {__dmul_rn(sd, __dmul_rn(r1, cos(t1))), __dmul_rn(sd, __dmul_rn(r1, sin(t1))),
-                              __dmul_rn(sd, __dmul_rn(r2, cos(t2)))};
+        double vn[3];
+        andersen_draw(orig[i], (base ? *base : 0) + step_off, seed, sd, vn);
         const float4 fq = f4[i];
         const double f[3] = {(double)fq.x, (double)fq.y, (double)fq.z};
         const int4 ref = xq_ref[i];
