@@ -122,6 +122,24 @@ def test_analyze_pipeline_parity(L, ctx, kind):
     assert np.array_equal(out["label"].cpu().numpy(), lab_o)
 
 
+def test_analysis_invariant_under_translation_and_axis_rotation(L, ctx):
+    """CNA labels bit for bit and Q4/Q6 within single-precision rounding after
+    a periodic translation of every position and after a quarter turn about
+    z, (x, y) -> (-y, x) with the box's x and y edges exchanged."""
+    c = _box("hcp", 0.05)
+    pos, box = c["pos"], np.asarray(c["box"], float)
+    base = L.ppmd_analyze(ctx, cu(pos), box, R_BOA, R_CNA)
+    moved = [(pos + np.array([0.37, 1.91, 2.53]), box),
+             (np.stack([-pos[:, 1], pos[:, 0], pos[:, 2]], 1), box[[1, 0, 2]])]
+    for p2, b2 in moved:
+        out = L.ppmd_analyze(ctx, cu(p2), b2, R_BOA, R_CNA)
+        ctx.sync()
+        assert torch.equal(out["label"], base["label"])
+        assert torch.equal(out["n_nb"], base["n_nb"])
+        for k in ("q4", "q6"):
+            assert (out[k] - base[k]).abs().max().item() <= 2e-6
+
+
 def test_analyze_full_size_box_sampled(L, ctx):
     """One 512,000-atom structure box (the analysis workload size): labels and
     Q_l of a seeded sample of atoms against the oracle evaluated on those atoms."""

@@ -349,6 +349,24 @@ def test_md_fp64_solid_10_steps_is_exact(L, ctx):
     assert _pos_err(p, po, c["box"]) <= 1e-12 * c["box"][0]
 
 
+def test_md_skin_violation_is_flagged(L, ctx):
+    """Atoms moving more than half the skin between list builds: the run goes
+    on (the guard never acts) and the state reports PPMD_WARN_SKIN with the
+    largest displacement; with a wide skin and frequent builds it stays clear."""
+    c = configs.lj_small()
+    n = len(c["pos"])
+    for r_list, every, max_nbr, flagged in ((2.55, 50, 128, True), (3.5, 10, 192, False)):
+        md = L.MD(ctx, [0, n], [c["box"]], r_list=r_list, rc=2.5, rebuild_every=every, max_nbr=max_nbr, prec=L.FP32)
+        md.set_state(cu(c["pos"]), cu(c["vel"]))
+        md.run(2 * every)
+        info = md.info()
+        md.close()
+        assert info["steps"] == 2 * every
+        assert (info["status"] == L.WARN_SKIN) == flagged, (r_list, info)
+        if flagged:
+            assert info["max_disp"] > 0.5 * (r_list - 2.5)
+
+
 def test_md_momentum_conserved(L, ctx):
     c = configs.lj_solid(n_cells=8)
     p, v, F, en, info = _md(L, ctx, c, L.FP32, 50, True)
