@@ -3,8 +3,15 @@
 on the large fcc solid (1,000,188 atoms, rc = 2.5, list cutoff 2.8, list
 rebuilt every 10 steps, dt = 0.005), one B300.
 
-Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+Prints ONE JSON line (rank 0): the device-resident rate (`value`), the same
+run through the public API from pinned host buffers (`e2e`), the pair
+loop's roofline, the plain FP64 GPU path, the list-free and half-list force
+loops on the same positions, clocks, launches, the oracle on a bounded
+sample (`cpu_baseline`), and one key per suite (`--suites`: replicas,
+analysis, classifier, otf).  Under torchrun every rank runs its own box
+(replicas, weak scaling) and rank 0 prints the maximum over ranks.
+`--impl reference` times the FP64 CPU oracle on bounded samples of the same
+workload instead, honouring --steps and --warmup.
 """
 from __future__ import annotations
 
