@@ -50,6 +50,37 @@ def forward(p, x):
     return logits, (x, z1, h1, z2, h2)
 
 
+def bf16_round(a):
+    """Nearest BF16 value (round to nearest, ties to even) of each FP32
+    value of `a`, returned as float64.  BF16 keeps the sign, the 8 exponent
+    bits and the top 7 fraction bits of an IEEE single; the dropped 16 bits
+    round the kept part."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    keep_lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + keep_lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(p, x):
+    """The network with BF16 operands, as the classifier is specified (BF16
+    weights and activations, wider accumulation): the standardisation in
+    single precision, (x - mu) then * isd, each rounded to FP32; the
+    standardised inputs and both hidden activations rounded to BF16 before
+    they enter the next layer; the weight matrices rounded to BF16; biases
+    in FP32; every sum of products accumulated in FP64.  x: BF16 values
+    (float64 array).  Returns (logits, (xs, z1, h1, z2, h2))."""
+    f32 = lambda v: np.asarray(v, dtype=np.float32)
+    W1, W2, W3 = (bf16_round(p[k]) for k in ("W1", "W2", "W3"))
+    xs = bf16_round((f32(x) - f32(p["mu"])) * f32(p["isd"]))
+    z1 = xs @ W1 + f32(p["b1"]).astype(np.float64)
+    h1 = bf16_round(np.maximum(z1, 0.0))
+    z2 = h1 @ W2 + f32(p["b2"]).astype(np.float64)
+    h2 = bf16_round(np.maximum(z2, 0.0))
+    logits = h2 @ W3 + f32(p["b3"]).astype(np.float64)
+    return logits, (xs, z1, h1, z2, h2)
+
+
 def softmax(logits):
     z = logits - logits.max(axis=1, keepdims=True)
     e = np.exp(z)

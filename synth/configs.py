@@ -169,22 +169,27 @@ def random_box(n: int, box, seed: int, cutoffs=(), margin: float = 1e-6, min_dis
 CLASSIFIER_CELLS = {"fcc": (40, 40, 20), "bcc": (40, 40, 40), "hcp": (40, 20, 40), "liquid": (40, 40, 80)}
 
 
+def classifier_box(seed: int, k: int, nbox: int = 32, sigma_lo: float = 0.01, sigma_hi: float = 0.12, cells=None):
+    """Box k of classifier_boxes(seed, nbox, ...), built on its own (the noise
+    draws of boxes 0..k are repeated, so the result is the same)."""
+    g = rng_stream(seed, 99)
+    kinds = ("fcc", "bcc", "hcp", "liquid")
+    per_kind = max(1, nbox // 4)
+    for j in range(k + 1):
+        u = g.uniform()
+    kind = kinds[k % 4]
+    stratum = (k // 4) % per_kind
+    sig = sigma_lo + (sigma_hi - sigma_lo) * (stratum + u) / per_kind
+    c = (cells or CLASSIFIER_CELLS)[kind]
+    b = structure_box(kind, float(sig), seed * 1000 + k, c)
+    b["sigma_frac"] = float(sig)
+    return b
+
+
 def classifier_boxes(seed: int, nbox: int = 32, sigma_lo: float = 0.01, sigma_hi: float = 0.12, cells=None):
     """Structure boxes for the learned classifier (32 boxes of 128,000 atoms =
     4,096,000 atoms by default).  Box k is fcc, bcc, hcp or liquid-like
     (k mod 4); the noise levels of each structure are stratified over
     [sigma_lo, sigma_hi] x d_nn (one draw in each of nbox/4 equal strata), so
     that every structure is seen across the whole noise range."""
-    g = rng_stream(seed, 99)
-    kinds = ("fcc", "bcc", "hcp", "liquid")
-    per_kind = max(1, nbox // 4)
-    out = []
-    for k in range(nbox):
-        kind = kinds[k % 4]
-        stratum = (k // 4) % per_kind
-        sig = sigma_lo + (sigma_hi - sigma_lo) * (stratum + g.uniform()) / per_kind
-        c = (cells or CLASSIFIER_CELLS)[kind]
-        b = structure_box(kind, float(sig), seed * 1000 + k, c)
-        b["sigma_frac"] = float(sig)
-        out.append(b)
-    return out
+    return [classifier_box(seed, k, nbox, sigma_lo, sigma_hi, cells) for k in range(nbox)]

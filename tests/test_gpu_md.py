@@ -149,6 +149,32 @@ def test_lj_fp32_parity(L, ctx, case):
     assert abs(tot[0] - Uo) / len(pos) <= 1e-6 * abs(Uo) / len(pos)
 
 
+def test_lj_fp32_forces_with_pairs_below_sigma(L, ctx):
+    """FP32 force parity where pairs come as close as 0.7 sigma (random
+    sequential addition with a 0.7 minimum distance): forces only, through
+    the granular call and through the integrator's pair loop (set-up forces
+    of ppmd_md_set_state).  The FP32 energy bound of the other tests assumes
+    no pair below sigma: single-precision pair energies carry ~2^-19 V(r),
+    and V grows as r^-12 there."""
+    pos, box = random_box(997, [12.1, 11.3, 13.7], 7, cutoffs=(2.5, 2.8), margin=1e-6, min_dist=0.7)
+    offs, nbr_o = oracle.neighbours_cells(pos, box, 2.8)
+    dr = pos[np.repeat(np.arange(len(pos)), np.diff(offs))] - pos[nbr_o]
+    dr -= box * np.rint(dr / box)
+    assert np.sqrt((dr ** 2).sum(1)).min() < 0.8  # pairs well inside sigma
+    Fo = oracle.lj(pos, box, offs, nbr_o)[0]
+    p, nbr, cnt = _lists(L, ctx, pos, box, 2.8)
+    F = L.ppmd_lj_forces(ctx, p, box, nbr, cnt, prec=L.FP32, want_energy=False)[0].cpu().numpy()
+    assert force_err(F, Fo) <= 1e-5
+    n = len(pos)
+    md = L.MD(ctx, [0, n], [box], r_list=2.8, rebuild_every=10, max_nbr=128, prec=L.FP32)
+    md.set_state(p, cu(np.zeros((n, 3))))
+    F2 = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    md.get_state(None, None, F2)
+    ctx.sync()
+    assert force_err(F2.cpu().numpy(), Fo) <= 1e-5
+    md.close()
+
+
 CELL_CASES = dict(CASES, three_cells=lambda: (dict(zip(("pos", "box"), random_box(300, [7.6, 8.1, 9.9], 5, cutoffs=(2.5,),
                                                                                   margin=1e-6, min_dist=1.0))), 2.5))
 

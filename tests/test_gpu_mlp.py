@@ -17,6 +17,7 @@ import pytest
 import torch
 
 import oracle
+import oracle_pipeline as op
 from oracle import mlp as omlp
 from synth import configs
 from synth.configs import R_BOA, R_CNA
@@ -244,3 +245,47 @@ def test_classify_modes(L, ctx):
     assert torch.equal(lab, logits.argmax(1).to(torch.int8))
     pr = torch.softmax(logits, 1).max(1).values
     assert torch.allclose(conf, pr, atol=1e-5)
+
+
+@pytest.fixture(scope="module")
+def trained_vec():
+    """Trained-scale parameters made by the oracle alone (oracle features,
+    CNA labels, AdamW in FP64), as the library's FP32 vector."""
+    return op.train_params()
+
+
+def test_mlp_forward_every_tile_pass_trained(L, ctx, trained_vec):
+    """The tensor-core forward pass in its steady state: the grid is at most
+    148 x 4 CTAs, each taking two 128-row tiles per pass of its two-slot
+    loop, so 500,037 rows give every CTA at least three passes (mbarrier
+    phases cycled, both slots refilled, tensor memory reused) and a ragged
+    last tile.  Rows: oracle features of the four structures at three noise
+    levels, and rows drawn around them.  Every logit is compared with the
+    oracle's BF16-operand network within the row's flip tolerance, and with
+    the FP64-activation network at the forward test's tolerance; the argmax
+    must match wherever the top two logits are further apart than twice the
+    row's tolerance."""
+    n = 500037
+    assert n >= 2 * 148 * 4 * 128 * 3
+    cells = {"fcc": (20, 20, 10), "bcc": (20, 20, 20), "hcp": (20, 12, 12), "liquid": (24, 24, 24)}
+    xs, _ = op.structure_rows(63, cells=cells)
+    rng = np.random.default_rng(64)
+    extra = rng.normal(xs.mean(0), xs.std(0) + 1e-3, (n - len(xs), 30))
+    x = omlp.bf16_round(np.concatenate([xs, extra]))
+    x = x[rng.permutation(n)]
+    xb = np.zeros((n, 32))
+    xb[:, :30] = x
+    q = op.unpack(trained_vec.astype(np.float64))
+    logits = L.ppmd_mlp_forward(ctx, cu(trained_vec, torch.float32), cu(xb, torch.bfloat16)).cpu().numpy()
+    ref, fwd = omlp.forward_bf16(q, x)
+    tol = op.flip_tolerance(q, x, fwd, inputs_differ=False)
+    err = np.abs(logits - ref).max(1)
+    assert (err <= tol).all(), (float((err / tol).max()), int(np.argmax(err / tol)))
+    # the FP64-activation network at the forward test's tolerance
+    qb = dict(q, W1=omlp.bf16_round(q["W1"]), W2=omlp.bf16_round(q["W2"]), W3=omlp.bf16_round(q["W3"]))
+    ref64 = omlp.forward(qb, x)[0]
+    assert np.abs(logits - ref64).max() <= 0.03 * max(1.0, np.sqrt((ref64 ** 2).mean()))
+    srt = np.sort(ref, 1)
+    clear = srt[:, -1] - srt[:, -2] > 2.0 * tol
+    assert clear.mean() > 0.99
+    assert np.array_equal(logits.argmax(1)[clear], ref.argmax(1)[clear])
