@@ -121,7 +121,7 @@ class ClockSampler:
 
 def lj_source_sha():
     h = hashlib.sha256()
-    for name in ("md_kernels.cu", "md_kernels.cuh", "lj.cuh", "common.cuh"):
+    for name in ("slots.cu", "md_kernels.cuh", "lj.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1704_03329_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -285,13 +285,17 @@ def run_ours(args):
     f1.record(stream)
     torch.cuda.synchronize()
     f_ms = f0.elapsed_time(f1) / R
-    alg_bytes = 36.0 * n + 4.0 * pairs  # cnt + own xq + float4 force + list entries
+    # cnt + own position (fixed-point int4; the brick copies of it come from
+    # L2) + float4 force + 16-bit list entries (stage slots)
+    alg_bytes = 36.0 * n + 2.0 * pairs
     hbm, peak_kind = peaks()
     achieved = alg_bytes / (f_ms * 1e-3) / 1e9
     tpa = traffic_per_atom()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": (tpa * n if tpa is not None else None),
-                "peak_source": peak_kind, "kernel": "k_lj_col32 (integrator pair loop, FP32, timed alone via ppmd_md_forces)",
+                "peak_source": peak_kind,
+                "kernel": "k_lj_slots32 (integrator pair loop, FP32, brick-staged, timed alone via ppmd_md_forces)",
+                "bytes_per_atom": "36 + 2 x listed pairs (count 4, position 16, force 16, list entries of 2 B)",
                 "kernel_ms": round(f_ms, 5), "algorithmic_bytes_per_launch": alg_bytes,
                 "pairs_listed_per_atom": round(pairs / n, 2)}
 

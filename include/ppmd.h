@@ -317,6 +317,14 @@ int ppmd_mlp_adamw(ppmd_ctx *ctx, float *params, float *m, float *v, const float
 int ppmd_mlp_train_step(ppmd_ctx *ctx, float *params, float *m, float *v, int64_t step, const uint16_t *x,
                         const int8_t *y, int64_t batch, float lr, float wd, float *loss);
 /* Structure labels of every atom (caller order, label[n] device int8).
+ * mode 2: bond order within a tolerance (Sec. 4.1, compared with the table
+ * of Q4, Q5, Q6 of perfect lattices): Q4 and Q6 over neighbours within
+ * r_feat (Eqs. (1)-(2)); the label is the lattice whose (Q4, Q6) in that
+ * table (fcc 0.191, 0.575; hcp 0.097, 0.485; bcc 0.036, 0.511) is nearest in
+ * the (Q4, Q6) plane, fcc before hcp before bcc on ties, when that distance
+ * is below threshold (the tolerance, >= 0), else other; confidence (may be
+ * NULL) receives that distance; params and r_cna are not used; n_fallback
+ * (may be NULL) receives 0 and makes the call synchronise as in mode 1.
  * mode 0: exact CNA (cutoff r_cna).  mode 1: features (cutoff r_feat >
  * r_cna, reference length r_cna) -> MLP -> class and confidence (max softmax probability, device
  * float [n], may be NULL); atoms with confidence < threshold are labelled
@@ -346,7 +354,8 @@ typedef struct {
     double r_list;         /* list cutoff r_c + delta (Eq. (6)); per box min(r_list, box_r_list[b]) */
     double mass, dt;
     int32_t rebuild_every; /* list rebuilt when step % rebuild_every == 0 (and at set-up) */
-    int32_t max_nbr;       /* row capacity of the neighbour list (rounded up to a multiple of 4) */
+    int32_t max_nbr;       /* row capacity of the neighbour list (rounded up to a multiple of 8 for
+                              PPMD_FP32, of 4 for PPMD_FP64) */
     int32_t prec;          /* ppmd_prec of the pair loop */
     int32_t energy_every;  /* potential/kinetic energy recorded every k steps (0 = never) */
 } ppmd_md_params;
@@ -358,7 +367,18 @@ int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **md, int64_t nbox, const int64_t *ato
                    const double *box_r_list, const ppmd_md_params *params);
 int ppmd_md_destroy(ppmd_md *md);
 /* Load positions and velocities (device, [n][3], caller order), wrap, sort,
- * build the list and compute the initial forces F(r_0). */
+ * build the list and compute the initial forces F(r_0).
+ * With PPMD_FP32 the list (the paper's neighbour matrix, Sec. 3.5.1) is kept
+ * per brick of cells: the grid is cut into bricks, each brick's
+ * neighbourhood (its cells and one layer around them) is copied into shared
+ * memory by the pair loop of every step, and a list entry is the
+ * neighbour's place in that copy.  At set-up the call reads one device word
+ * (it synchronises) to check that every neighbourhood fits the copy; a
+ * larger one makes it grow the copy and build again, or fail with
+ * PPMD_ERR_CAPACITY when it would exceed what one block may hold.  A
+ * neighbourhood that outgrows the copy at a later rebuild latches
+ * PPMD_ERR_CAPACITY (its atoms get no forces), reported by the next
+ * synchronising call. */
 int ppmd_md_set_state(ppmd_md *md, const double *pos, const double *vel);
 /* Advance nsteps steps of Algorithm 6.  energies (device, may be NULL):
  * [nsteps][2] receives (kinetic, potential) energy summed over all boxes
@@ -405,6 +425,13 @@ int ppmd_md_forces(ppmd_md *md);
 /* Current neighbour list (host outputs, may be NULL): total listed pairs and
  * the largest row.  Synchronises. */
 int ppmd_md_list_stats(ppmd_md *md, int64_t *pairs, int32_t *max_row);
+/* The list of the last build (Sec. 3.5: pairs within the list cutoff r_list
+ * of Eq. (6) at that build) in the caller's order: nbr_count[i] (device
+ * int32 [n]) the number of neighbours of caller atom i, nbr (device int32
+ * [n][max_nbr], row-major) the caller indices of its first max_nbr
+ * neighbours in list order (entries past the count untouched).  Uses context
+ * scratch of 4 bytes per atom and row entry. */
+int ppmd_md_get_list(ppmd_md *md, int32_t *nbr, int32_t *nbr_count, int32_t max_nbr);
 
 /* ------------------------------------------------------------------ */
 /* Forces without any allocation.  The paper has no counterpart: this entry

@@ -271,6 +271,29 @@ def features(pos, box, offs, nbr, r_feat=1.5, r_ref=1.433625):
     return f
 
 
+# (Q4, Q6) of perfect fcc, hcp and bcc lattices as printed in the table of
+# Q4, Q5, Q6 of Sec. 4.1, with the structure codes of cna_label.
+BOA_TABLE = ((1, 0.191, 0.575), (2, 0.097, 0.485), (3, 0.036, 0.511))
+
+
+def boa_tolerance_labels(q4, q6, tol):
+    """Sec. 4.1: the local structure is that of the lattice whose Q_l agree
+    with the atom's within a tolerance.  Reading: the lattice of BOA_TABLE
+    nearest to (Q4, Q6) in the plane (the first in table order on ties),
+    when its distance is below tol; otherwise 0 (other).  Returns (labels
+    int8, that nearest distance)."""
+    q4 = np.asarray(q4, dtype=np.float64)
+    q6 = np.asarray(q6, dtype=np.float64)
+    best = np.full(q4.shape, np.inf)
+    lab = np.zeros(q4.shape, np.int8)
+    for code, r4, r6 in BOA_TABLE:
+        d = np.sqrt((q4 - r4) ** 2 + (q6 - r6) ** 2)
+        closer = d < best
+        best = np.where(closer, d, best)
+        lab = np.where(closer, np.int8(code), lab)
+    return np.where(best < tol, lab, np.int8(0)).astype(np.int8), best
+
+
 def triplet(ncn, nb, nlcb):
     return (ncn << 16) | (nb << 8) | nlcb
 

@@ -94,6 +94,7 @@ _SIGS = {
     "ppmd_md_info": (_I, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_D)]),
     "ppmd_md_forces": (_I, [_P]),
     "ppmd_md_list_stats": (_I, [_P, C.POINTER(_I64), C.POINTER(_I32)]),
+    "ppmd_md_get_list": (_I, [_P, _P, _P, _I32]),
     "ppmd_lj_forces_noalloc": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _P, _P, _I32, _I, _P, _P, _P,
                                     _P]),
 }
@@ -412,11 +413,12 @@ def ppmd_mlp_train_step(ctx: Context, params, m, v, step, x_bf16, y, lr=1e-3, wd
 
 def ppmd_classify(ctx: Context, pos, box, mode=1, params=None, threshold=0.9, r_feat=1.5, r_cna=1.433625,
                   want_confidence=True, count=True):
-    """Labels int8 [n], confidence float32 [n] (mode 1), number of CNA fallbacks
-    (None with count=False: the call is then asynchronous)."""
+    """Labels int8 [n], confidence float32 [n] (mode 1; mode 2: the distance to
+    the nearest table (Q4, Q6), with threshold the tolerance), number of CNA
+    fallbacks (None with count=False: the call is then asynchronous)."""
     n = pos.shape[0]
     lab = torch.empty(n, dtype=torch.int8, device=pos.device)
-    conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode == 1) else None
+    conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode in (1, 2)) else None
     nfb = _I64(0)
     b = _box(box)
     ctx.check(_lib.ppmd_classify(ctx.h, int(mode), _ptr(pos), n, C.byref(b), float(r_feat), float(r_cna), _opt(params),
@@ -430,7 +432,7 @@ def ppmd_classify_boxes(ctx: Context, pos, atom_off, boxes, mode=1, params=None,
     ppmd_analyze_boxes); labels, confidences and the total fallback count."""
     n = pos.shape[0]
     lab = torch.empty(n, dtype=torch.int8, device=pos.device)
-    conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode == 1) else None
+    conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode in (1, 2)) else None
     nfb = _I64(0)
     nbox, off, bx = _box_set(atom_off, boxes)
     if off[nbox] != n:
@@ -510,6 +512,14 @@ class MD:
         pairs, mx = _I64(), _I32()
         self.ctx.check(_lib.ppmd_md_list_stats(self.h, C.byref(pairs), C.byref(mx)))
         return pairs.value, mx.value
+
+    def get_list(self, max_nbr=None):
+        """The last build's list in caller order: (nbr [n, max_nbr] int32 caller indices, count [n])."""
+        max_nbr = self.params.max_nbr if max_nbr is None else max_nbr
+        nbr = torch.full((self.n, max_nbr), -1, dtype=torch.int32, device="cuda")
+        cnt = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        self.ctx.check(_lib.ppmd_md_get_list(self.h, _ptr(nbr), _ptr(cnt), int(max_nbr)))
+        return nbr, cnt
 
     def info(self):
         s, r, d = _I64(), _I64(), _D()

@@ -780,6 +780,41 @@ int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, co
     return check_launch(ctx, "boa");
 }
 
+// Structure by bond order within a tolerance (Sec. 4.1: Q_l compared with
+// the perfect-lattice values of the table of Q4, Q5, Q6, "within some
+// tolerance"): the lattice whose (Q4, Q6) of that table is nearest in the
+// plane, in the order fcc, hcp, bcc on ties, if its distance is below tol;
+// else other.  dist (may be null): that smallest distance.
+__global__ void k_boa_tolerance(int64_t n, const float *__restrict__ q4, const float *__restrict__ q6, float tol,
+                                int8_t *__restrict__ label, float *__restrict__ dist) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // (Q4, Q6) of perfect fcc, hcp and bcc as the table prints them
+    const float ref4[3] = {0.191f, 0.097f, 0.036f}, ref6[3] = {0.575f, 0.485f, 0.511f};
+    const int8_t code[3] = {1, 2, 3};
+    const float a = q4[i], b = q6[i];
+    float best = 3.4e38f;
+    int8_t lab = 0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const float d4 = a - ref4[s], d6 = b - ref6[s];
+        const float d2 = fmaf(d4, d4, d6 * d6);
+        if (d2 < best) {
+            best = d2;
+            lab = code[s];
+        }
+    }
+    const float d = sqrtf(best);
+    label[i] = d < tol ? lab : (int8_t)0;
+    if (dist) dist[i] = d;
+}
+
+int boa_tolerance_launch(ppmd_ctx *ctx, int64_t n, const float *q4, const float *q6, float tol, int8_t *label,
+                         float *dist) {
+    if (n > 0) PPMD_LAUNCH(ctx, k_boa_tolerance, div_up(n, 256), 256, 0, n, q4, q6, tol, label, dist);
+    return check_launch(ctx, "boa_tolerance");
+}
+
 int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
                const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
                int8_t *label) {

@@ -50,6 +50,10 @@ int check_boxes(ppmd_ctx *ctx, int64_t nbox, const int64_t *atom_off, const ppmd
 int boa_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
                const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, float *q4,
                float *q6, int32_t *nnb);
+// Labels from (Q4, Q6) by the nearest perfect-lattice value within tol
+// (k_boa_tolerance in analysis.cu); dist (may be null) the nearest distance.
+int boa_tolerance_launch(ppmd_ctx *ctx, int64_t n, const float *q4, const float *q6, float tol, int8_t *label,
+                         float *dist);
 int cna_launch(ppmd_ctx *ctx, int64_t n, const int4 *xq, const double *pos64, const SegTable &st, const int32_t *nbr,
                const int32_t *cnt, int32_t max_nbr, int64_t ld, double r_cut, double Lmax, const int32_t *out_idx, uint32_t *trip,
                int8_t *label);

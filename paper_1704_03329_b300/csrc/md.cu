@@ -40,6 +40,11 @@ struct ppmd_md {
     int32_t *orig = nullptr, *seg_of = nullptr, *cell_of = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
     int32_t *W = nullptr, *cnt = nullptr;  // column-major neighbour matrix W[m * ld + i]
     int64_t ld = 0;
+    // FP32 runs keep the list as brick-stage slots (slots.cu) instead of W;
+    // on-the-fly analysis and the FP64 path use W
+    bool slots = false;
+    uint16_t *W16 = nullptr;
+    int32_t *stage_need = nullptr;  // largest neighbourhood met by a slot-list build
     Brick *bricks = nullptr;
     int32_t stage_cap = 0;  // shared-memory stage of a list-build block (atoms)
     int64_t nbricks = 0;
@@ -75,6 +80,8 @@ struct ppmd_md {
 };
 
 namespace {
+
+int64_t force_blocks(const ppmd_md *m) { return m->slots ? m->nbricks : lj_columns_blocks(m->n); }
 
 template <class T>
 int md_alloc(ppmd_md *m, T **p, size_t count) {
@@ -330,6 +337,9 @@ int rebuild(ppmd_md *m) {
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq_ref, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    if (m->slots)
+        return build_slot_list(ctx, m->nbricks, m->bricks, m->xq, m->pos, m->st, m->cell_start, m->W16, m->ld, m->cnt,
+                               m->p.max_nbr, m->stage_cap, m->stage_need, m->n);
     PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, BrickShape{1, 1, 1}, m->xq, m->pos, m->st, m->cell_start,
                                m->W, m->ld, m->cnt, m->p.max_nbr, m->stage_cap, true));
     return build_short_list(m);
@@ -348,9 +358,14 @@ int forces(ppmd_md *m, bool energy, bool kick, bool drift = false) {
         d.dt = m->p.dt;
         d.max_disp_bits = m->max_disp_bits;
     }
-    PPMD_TRY(lj_columns(m->ctx, m->n, m->ld, m->xq, m->pos, m->st, m->c, m->W, m->cnt, m->p.max_nbr, m->p.prec,
-                        f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, kick ? m->vel : nullptr, m->h, m->half_m,
-                        energy ? m->part_f : nullptr, d));
+    if (m->slots)
+        PPMD_TRY(lj_slots(m->ctx, m->nbricks, m->bricks, m->xq, m->pos, m->st, m->cell_start, m->c, m->W16, m->ld, m->cnt,
+                          m->p.max_nbr, m->stage_cap, m->f4, kick ? m->vel : nullptr, m->h, m->half_m,
+                          energy ? m->part_f : nullptr, d, m->n));
+    else
+        PPMD_TRY(lj_columns(m->ctx, m->n, m->ld, m->xq, m->pos, m->st, m->c, m->W, m->cnt, m->p.max_nbr, m->p.prec,
+                            f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, kick ? m->vel : nullptr, m->h, m->half_m,
+                            energy ? m->part_f : nullptr, d));
     if (drift) {
         use_buffer(m, m->cur ^ 1);
         m->half_kicked = true;
@@ -385,7 +400,7 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow =
     PPMD_TRY(forces(m, energy, true, fused));
     const int prev = fused ? m->cur ^ 1 : m->cur;
     if (energy) {
-        PPMD_TRY(reduce_partials(ctx, m->part_f, lj_columns_blocks(m->n), 3, m->red));
+        PPMD_TRY(reduce_partials(ctx, m->part_f, force_blocks(m), 3, m->red));
         PPMD_LAUNCH(ctx, k_energy_row, 1, 1, 0, m->red, erow);
     }
     if (thermo && m->n > 0) {
@@ -430,7 +445,9 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     m->n = atom_off[nbox];
     m->nbox = nbox;
     m->p = p;
-    m->p.max_nbr = (p.max_nbr + 3) & ~3;  // the list is stored in groups of four
+    m->slots = p.prec == PPMD_FP32;
+    // the list is stored in groups of four atom indices, or eight slots
+    m->p.max_nbr = m->slots ? (p.max_nbr + 7) & ~7 : (p.max_nbr + 3) & ~3;
     m->h = p.dt / (2.0 * p.mass);
     m->half_m = 0.5 * p.mass;
     m->segs.resize(nbox);
@@ -503,7 +520,12 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_atoms, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_start, m->ncell + 1);
     m->ld = (n + 31) / 32 * 32;
-    if (rc == PPMD_OK) rc = md_alloc(m, &m->W, (size_t)m->ld * m->p.max_nbr);
+    if (rc == PPMD_OK) {
+        if (m->slots) rc = md_alloc(m, &m->W16, (size_t)m->ld * m->p.max_nbr);
+        else rc = md_alloc(m, &m->W, (size_t)m->ld * m->p.max_nbr);
+    }
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->stage_need, 1);
+    if (rc == PPMD_OK) rc = cuda_check(ctx, cudaMemset(m->stage_need, 0, sizeof(int32_t)), "memset");
     if (rc == PPMD_OK) {
         std::vector<Brick> bl;
         m->stage_cap = make_bricks(m->segs, bl);
@@ -513,8 +535,9 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
             rc = cuda_check(ctx, cudaMemcpy(m->bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice), "copy");
     }
     if (rc == PPMD_OK) rc = neigh_brick_setup(ctx, m->p.max_nbr);
+    if (rc == PPMD_OK && m->slots) rc = slots_setup(ctx, m->stage_cap, m->p.max_nbr);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt, n);
-    if (rc == PPMD_OK) rc = md_alloc(m, &m->part_f, 3 * lj_columns_blocks(n) + 3);
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->part_f, 3 * std::max<int64_t>(lj_columns_blocks(n), m->nbricks) + 3);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->red, 4);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->ebuf, 2 * 1024);
@@ -550,6 +573,40 @@ extern "C" int ppmd_md_destroy(ppmd_md *m) {
     return PPMD_OK;
 }
 
+namespace {
+void drop_graph(ppmd_md *m);
+
+// After the set-up list build: if a brick's neighbourhood did not fit the
+// shared-memory stage, grow the stage (up to what a block may use) and build
+// again.  This reads one device word (a synchronisation, at set-up only).
+int fit_stage(ppmd_md *m) {
+    ppmd_ctx *ctx = m->ctx;
+    int32_t need = 0, st = 0;
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(&need, m->stage_need, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
+                        "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(&st, ctx->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
+                        "copy"));
+    PPMD_TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
+    if (need <= m->stage_cap) return PPMD_OK;
+    const int32_t cap = (int32_t)(((int64_t)need * 5 / 4 + 63) / 64 * 64);
+    if (slot_list_smem(cap, m->p.max_nbr) > 200 * 1024 || cap >= 65535)
+        return set_error(ctx, PPMD_ERR_CAPACITY, "a brick neighbourhood of %d atoms exceeds the shared-memory stage", need);
+    if (st == PPMD_ERR_CAPACITY) {
+        // the overflow latched by the first build; the build below latches
+        // again if a row still overflows the list capacity
+        int32_t zero = 0;
+        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(ctx->d_status, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream),
+                            "copy"));
+    }
+    drop_graph(m);
+    m->stage_cap = cap;
+    PPMD_TRY(slots_setup(ctx, m->stage_cap, m->p.max_nbr));
+    use_buffer(m, 0);
+    return build_slot_list(ctx, m->nbricks, m->bricks, m->xq, m->pos, m->st, m->cell_start, m->W16, m->ld, m->cnt,
+                           m->p.max_nbr, m->stage_cap, m->stage_need, m->n);
+}
+}  // namespace
+
 extern "C" int ppmd_md_set_state(ppmd_md *m, const double *pos, const double *vel) {
     if (!m || (m->n > 0 && (!pos || !vel))) return PPMD_ERR_INVALID;
     ppmd_ctx *ctx = m->ctx;
@@ -564,6 +621,7 @@ extern "C" int ppmd_md_set_state(ppmd_md *m, const double *pos, const double *ve
         PPMD_LAUNCH(ctx, k_init_state, div_up(n, 256), 256, 0, n, m->pos, m->d_atom_off, m->nbox, m->st, m->xq, m->orig,
                     m->seg_of, ctx->d_status);
     PPMD_TRY(rebuild(m));
+    if (m->slots) PPMD_TRY(fit_stage(m));
     PPMD_TRY(forces(m, false, false));
     m->step = 0;
     m->rebuilds = 1;
@@ -683,6 +741,41 @@ extern "C" int ppmd_md_info(ppmd_md *m, int64_t *steps, int64_t *rebuilds, doubl
 }
 
 namespace {
+// Row orig[k] of out (caller order) gets the caller indices of sorted atom
+// k's neighbours, from the grouped column-major atom-index list W.
+__global__ void k_list_out(int64_t n, const int32_t *__restrict__ orig, const int32_t *__restrict__ W,
+                           const int32_t *__restrict__ cnt, int32_t max_nbr, int64_t ld, int32_t *__restrict__ out,
+                           int32_t *__restrict__ out_cnt, int32_t max_out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t o = orig[k];
+    const int32_t c = cnt[k];
+    out_cnt[o] = c;
+    const int32_t m = min(min(c, max_nbr), max_out);
+    for (int32_t e = 0; e < m; ++e) out[o * max_out + e] = orig[W[(((int64_t)(e >> 2) * ld + k) << 2) + (e & 3)]];
+}
+}  // namespace
+
+extern "C" int ppmd_md_get_list(ppmd_md *m, int32_t *nbr, int32_t *nbr_count, int32_t max_nbr) {
+    if (!m || !m->ready || max_nbr < 0 || (m->n > 0 && (!nbr_count || (max_nbr > 0 && !nbr))))
+        return m ? set_error(m->ctx, PPMD_ERR_INVALID, "ppmd_md_get_list: bad argument") : PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    cudaSetDevice(ctx->device);
+    if (m->n == 0) return PPMD_OK;
+    const int32_t *W = m->W;
+    if (m->slots) {
+        int32_t *w = (int32_t *)scratch(ctx, S_TMP2, sizeof(int32_t) * (size_t)m->ld * (size_t)m->p.max_nbr);
+        if (!w) return PPMD_ERR_NOMEM;
+        PPMD_TRY(slots_to_atoms(ctx, m->nbricks, m->bricks, m->st, m->cell_start, m->W16, m->ld, m->cnt, m->p.max_nbr,
+                                m->stage_cap, w, m->n));
+        W = w;
+    }
+    PPMD_LAUNCH(ctx, k_list_out, div_up(m->n, 256), 256, 0, m->n, m->orig, W, m->cnt, m->p.max_nbr, m->ld, nbr,
+                nbr_count, max_nbr);
+    return check_launch(ctx, "ppmd_md_get_list");
+}
+
+namespace {
 __global__ void k_list_stats(const int32_t *cnt, int64_t n, unsigned long long *out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t v = i < n ? cnt[i] : 0;
@@ -729,6 +822,15 @@ extern "C" int ppmd_md_set_boa(ppmd_md *m, int32_t every, double r_boa) {
         return set_error(m->ctx, PPMD_ERR_INVALID, "ppmd_md_set_boa: need every >= 0 and 0 < r_boa <= rc");
     cudaSetDevice(m->ctx->device);
     drop_graph(m);
+    if (every > 0 && m->slots) {
+        // the analysis reads the atom-index list W: convert the current slot
+        // list (same entries, same order) and build W from now on
+        if (!m->W) PPMD_TRY(md_alloc(m, &m->W, (size_t)m->ld * m->p.max_nbr));
+        if (m->ready)
+            PPMD_TRY(slots_to_atoms(m->ctx, m->nbricks, m->bricks, m->st, m->cell_start, m->W16, m->ld, m->cnt,
+                                    m->p.max_nbr, m->stage_cap, m->W, m->n));
+        m->slots = false;
+    }
     m->boa_every = every;
     m->r_boa = r_boa;
     // the short list of the current build (later builds make their own)

@@ -62,6 +62,35 @@ int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const doubl
                double *f64, double *vel, double h, double half_m, double *partials, const Drift &drift = Drift());
 int64_t lj_columns_blocks(int64_t n);
 
+// Brick-staged FP32 path (slots.cu).  A list entry is the neighbour's slot
+// (16 bits) in its brick's staged neighbourhood: the cells of the brick's
+// neighbourhood row by row, each row the cells x0-1 .. x1 of one (y, z) row
+// of the sorted atoms, rows back to back; slot T (the neighbourhood's size)
+// is a sentinel far from every home atom and pads the last group of eight.
+// Entry m of atom i: W16[((m / 8) ld + i) 8 + m % 8]; max_nbr divisible by 8.
+constexpr int SLOT_THREADS = 128;
+size_t slot_list_smem(int32_t stage_cap, int32_t max_nbr);
+size_t slot_pair_smem(int32_t stage_cap);
+int slots_setup(ppmd_ctx *ctx, int32_t stage_cap, int32_t max_nbr);
+// List build over the bricks; a neighbourhood larger than stage_cap leaves
+// its home atoms without entries, raises *stage_need to its size and latches
+// PPMD_ERR_CAPACITY.
+int build_slot_list(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, const int4 *xq, const double *pos64,
+                    const SegTable &st, const int32_t *cell_start, uint16_t *W16, int64_t ld, int32_t *cnt,
+                    int32_t max_nbr, int32_t stage_cap, int32_t *stage_need, int64_t n_atoms);
+// Pair loop of the slot lists (one block per brick, its neighbourhood copied
+// into shared memory by bulk asynchronous copies); kick, drift and partials
+// as lj_columns (partials: one row per brick).
+int lj_slots(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, const int4 *xq, const double *pos64,
+             const SegTable &st, const int32_t *cell_start, const LJConst &c, const uint16_t *W16, int64_t ld,
+             const int32_t *cnt, int32_t max_nbr, int32_t stage_cap, float4 *f4, double *vel, double h,
+             double half_m, double *partials, const Drift &drift, int64_t n_atoms);
+// The slot lists as the grouped column-major atom-index list of
+// build_list_bricks (vec4 layout), same entries in the same order.
+int slots_to_atoms(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, const SegTable &st, const int32_t *cell_start,
+                   const uint16_t *W16, int64_t ld, const int32_t *cnt, int32_t max_nbr, int32_t stage_cap, int32_t *W,
+                   int64_t n_atoms);
+
 // Kick + drift without wrapping (coordinates stay continuous between list
 // builds), fixed-point refresh, displacement guard.
 int md_kick_drift2(ppmd_ctx *ctx, int64_t n, double *pos, double *vel, const float4 *f4, const double *f64, int4 *xq,

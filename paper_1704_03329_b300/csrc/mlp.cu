@@ -660,8 +660,9 @@ extern "C" int ppmd_classify_boxes(ppmd_ctx *ctx, int mode, const double *pos, i
     if (!ctx) return PPMD_ERR_INVALID;
     PPMD_TRY(check_boxes(ctx, nbox, atom_off, boxes, "ppmd_classify"));
     const int64_t n = atom_off[nbox];
-    if ((n > 0 && (!pos || !label)) || (mode != 0 && mode != 1) || (mode == 1 && !params) || !(r_cna > 0) ||
-        (mode == 1 && !(r_feat >= r_cna)))
+    if ((n > 0 && (!pos || !label)) || mode < 0 || mode > 2 || (mode == 1 && !params) ||
+        (mode != 2 && !(r_cna > 0)) || (mode == 1 && !(r_feat >= r_cna)) || (mode == 2 && !(r_feat > 0)) ||
+        (mode == 2 && !(threshold >= 0.0f)))
         return set_error(ctx, PPMD_ERR_INVALID, "ppmd_classify: bad argument");
     cudaSetDevice(ctx->device);
     if (mode == 0) {
@@ -669,6 +670,24 @@ extern "C" int ppmd_classify_boxes(ppmd_ctx *ctx, int mode, const double *pos, i
         return ppmd_analyze_boxes(ctx, pos, nbox, atom_off, boxes, 0.0, r_cna, nullptr, nullptr, nullptr, label);
     }
     const size_t nn = (size_t)(n > 0 ? n : 1);
+    if (mode == 2) {
+        // bond order within a tolerance: Q4, Q6 over r_feat, nearest table value
+        float *q = (float *)scratch(ctx, S_TMP0, sizeof(float) * 2 * nn);
+        if (!q) return PPMD_ERR_NOMEM;
+        int32_t max_nbr = snapshot_capacity_boxes(nbox, atom_off, boxes, r_feat);
+        for (int attempt = 0;; ++attempt) {
+            Snapshot s;
+            PPMD_TRY(sorted_snapshot_boxes(ctx, pos, nbox, atom_off, boxes, r_feat, max_nbr, s));
+            PPMD_TRY(boa_launch(ctx, n, s.xq, s.pos, s.st, s.nbr, s.cnt, s.max_nbr, s.ld, r_feat, s.Lmax, s.perm, q, q + nn,
+                                nullptr));
+            PPMD_TRY(boa_tolerance_launch(ctx, n, q, q + nn, threshold, label, confidence));
+            if (!n_fallback) return check_launch(ctx, "ppmd_classify");
+            const int rc = end_pipeline(ctx, attempt, max_nbr);
+            if (rc == PIPELINE_RETRY) continue;
+            *n_fallback = 0;
+            return rc;
+        }
+    }
     int32_t max_nbr = snapshot_capacity_boxes(nbox, atom_off, boxes, r_feat);
     for (int attempt = 0;; ++attempt) {
         Snapshot s;

@@ -1,0 +1,110 @@
+"""The paper's structure test by bond order (Sec. 4.1: Q4 and Q6 compared
+with the perfect-lattice table within a tolerance; ppmd_classify mode 2)
+against the oracle, and what the learned classifier gains over it.
+
+Parity: the nearest-point distance within 2e-5 of the oracle's (Q_l in
+single precision, |dQ| <= 1e-5 each), and the labels equal wherever the
+oracle's decision has a margin above that (distance to the tolerance, and
+gap between the nearest and the second-nearest table point).
+
+Gain: on held-out structure boxes of the four kinds at three noise levels,
+labelled by exact CNA (the judge of the classifier's error), the MLP with
+its CNA fallback must agree with CNA more often than bond order by
+tolerance does with its best tolerance (chosen on the training boxes).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import configs
+from synth.configs import R_BOA, R_CNA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1704_03329_b300 import lib
+    return lib
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    return L.Context(0)
+
+
+def cu(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+CELLS = {"fcc": (10, 10, 5), "bcc": (10, 10, 5), "hcp": (10, 6, 6), "liquid": (12, 12, 12)}
+
+
+@pytest.mark.parametrize("kind", ["fcc", "bcc", "hcp", "liquid"])
+@pytest.mark.parametrize("tol", [0.03, 0.08])
+def test_boa_tolerance_matches_oracle(L, ctx, kind, tol):
+    c = configs.structure_box(kind, 0.05, 35, cells=CELLS[kind])
+    pos, box = c["pos"], c["box"]
+    lab, dist, nfb = L.ppmd_classify(ctx, cu(pos), box, mode=2, threshold=tol, r_feat=R_BOA)
+    lab, dist = lab.cpu().numpy(), dist.cpu().numpy()
+    offs, nb = oracle.neighbours_cells(pos, box, R_BOA)
+    q4, _ = oracle.boa(pos, box, offs, nb, R_BOA, 4)
+    q6, _ = oracle.boa(pos, box, offs, nb, R_BOA, 6)
+    lab_o, d_o = oracle.boa_tolerance_labels(q4, q6, tol)
+    assert nfb == 0
+    assert np.abs(dist - d_o).max() <= 2e-5
+    d_all = np.sort(np.stack([np.hypot(q4 - r4, q6 - r6) for _, r4, r6 in oracle.BOA_TABLE], 1), 1)
+    margin = np.minimum(np.abs(d_o - tol), d_all[:, 1] - d_all[:, 0])
+    sure = margin > 3e-5
+    assert sure.mean() > 0.99
+    assert np.array_equal(lab[sure], lab_o[sure])
+
+
+def _set(L, ctx, seed, sigmas=(0.02, 0.06, 0.1)):
+    """Structure boxes of the four kinds at several noise levels: device
+    positions, boxes, BF16 features and exact CNA labels."""
+    out = []
+    for kind in ("fcc", "bcc", "hcp", "liquid"):
+        for s in sigmas:
+            c = configs.structure_box(kind, s, seed, cells=CELLS[kind])
+            p = cu(c["pos"])
+            _, fb = L.ppmd_features(ctx, p, c["box"], R_BOA, fp32=False, bf16=True)
+            lab, _, _ = L.ppmd_classify(ctx, p, c["box"], mode=0, r_cna=R_CNA)
+            out.append((p, c["box"], fb, lab))
+    return out
+
+
+def _agree(L, ctx, boxes, **kw):
+    hit = tot = 0
+    for p, box, _, cna in boxes:
+        lab = L.ppmd_classify(ctx, p, box, **kw)[0]
+        hit += int((lab == cna).sum())
+        tot += lab.numel()
+    return hit / tot
+
+
+def test_learned_classifier_gains_over_bond_order_tolerance(L, ctx):
+    from oracle import mlp as omlp
+    train = _set(L, ctx, 51)
+    held = _set(L, ctx, 52)
+    # the paper's method at its best tolerance on the training boxes
+    grid = [0.02, 0.04, 0.06, 0.08, 0.1, 0.12, 0.15, 0.2]
+    best_tol = max(grid, key=lambda t: _agree(L, ctx, train, mode=2, threshold=t, r_feat=R_BOA))
+    a_boa = _agree(L, ctx, held, mode=2, threshold=best_tol, r_feat=R_BOA)
+    # the network, trained on the GPU on the same boxes' CNA labels
+    x = torch.cat([b[2] for b in train])
+    y = torch.cat([b[3] for b in train])
+    rng = np.random.default_rng(8)
+    P = cu(np.concatenate([omlp.init_params(rng)[k].reshape(-1) for k in omlp.NAMES]), torch.float32)
+    L.ppmd_mlp_fit_input_norm(ctx, P, x)
+    M, V = torch.zeros_like(P), torch.zeros_like(P)
+    g = torch.Generator(device="cpu").manual_seed(1)
+    for step in range(1, 601):
+        idx = torch.randint(0, x.shape[0], (4096,), generator=g).cuda()
+        L.ppmd_mlp_train_step(ctx, P, M, V, step, x[idx].contiguous(), y[idx].contiguous(), lr=3e-3, wd=0.01)
+    a_mlp = _agree(L, ctx, held, mode=1, params=P, threshold=0.0, r_cna=R_CNA)
+    a_fb = _agree(L, ctx, held, mode=1, params=P, threshold=0.9, r_cna=R_CNA)
+    print(f"agreement with CNA: bond order (tol {best_tol}) {a_boa:.4f}, MLP {a_mlp:.4f}, MLP + CNA fallback {a_fb:.4f}")
+    assert a_fb > a_boa and a_mlp > a_boa
+    assert a_fb >= 0.98

@@ -31,6 +31,49 @@ def test_perfect_lattice_Q_matches_paper_table(kind, golden):
         assert np.abs(Q - ref[key]).max() <= 0.0006, (kind, l, Q[0])
 
 
+def test_boa_tolerance_table_is_the_papers(golden):
+    codes = {1: "fcc", 2: "hcp", 3: "bcc"}
+    for code, q4, q6 in oracle.BOA_TABLE:
+        ref = golden["Q_table"][codes[code]]
+        assert (q4, q6) == (ref["Q4"], ref["Q6"])
+
+
+@pytest.mark.parametrize("kind,code", [("fcc", 1), ("hcp", 2), ("bcc", 3)])
+def test_boa_tolerance_labels_perfect_lattices(kind, code):
+    """Sec. 4.1: Q_l of a perfect lattice (computed by the oracle from its
+    positions) lies within the paper's three printed digits of the table,
+    so a tight tolerance labels every atom with its own lattice and no
+    other."""
+    pos, box = _perfect(kind)
+    offs, nbr = oracle.neighbours_brute(pos, box, 1.5)
+    q4, _ = oracle.boa(pos, box, offs, nbr, 1.5, 4)
+    q6, _ = oracle.boa(pos, box, offs, nbr, 1.5, 6)
+    lab, d = oracle.boa_tolerance_labels(q4, q6, 0.002)
+    assert (lab == code).all() and d.max() < 0.001
+    # half the distance to the nearest other lattice's point still labels it;
+    # a tolerance below the three-digit rounding leaves it "other"
+    assert (oracle.boa_tolerance_labels(q4, q6, 0.04)[0] == code).all()
+    assert (oracle.boa_tolerance_labels(q4, q6, 1e-6)[0] == 0).all()
+
+
+def test_boa_tolerance_rule_edges():
+    """Strict tolerance, nearest point wins, table order on an exact tie,
+    far points are other."""
+    fcc, hcp = np.array([0.191, 0.575]), np.array([0.097, 0.485])
+    mid = 0.5 * (fcc + hcp)  # equidistant from fcc and hcp, farther from bcc
+    d_mid = np.linalg.norm(mid - fcc)
+    lab, d = oracle.boa_tolerance_labels([mid[0]], [mid[1]], 1.0)
+    assert lab[0] == 1 and abs(d[0] - d_mid) < 1e-15
+    lab, _ = oracle.boa_tolerance_labels([0.191, 0.191], [0.575 + 0.05, 0.575 + 0.05], 0.05)
+    assert (lab == 0).all()  # a distance equal to the tolerance is not within it
+    lab, _ = oracle.boa_tolerance_labels([0.191], [0.575 + 0.0499], 0.05)
+    assert lab[0] == 1
+    lab, _ = oracle.boa_tolerance_labels([0.0, 0.5], [0.0, 0.1], 0.3)
+    assert (lab == 0).all()
+    lab, _ = oracle.boa_tolerance_labels([0.04, 0.1], [0.51, 0.49], 0.02)
+    assert list(lab) == [3, 2]
+
+
 @pytest.mark.parametrize("seed", [1, 2])
 def test_Q_direct_equals_addition_theorem(seed):
     """Two independent routes to Q_l: sums of Y_l^m (Eq. (2)) and the Legendre
