@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=200)
     ap.add_argument("--otf-steps", type=int, default=540)
-    ap.add_argument("--suites", default="replicas,analysis,classifier,otf",
+    ap.add_argument("--precision-steps", type=int, default=1000)
+    ap.add_argument("--suites", default="replicas,analysis,classifier,otf,precision",
                     help="extra workloads reported beside the main line (comma list, or 'none')")
     ap.add_argument("--replica-steps", type=int, default=500)
     ap.add_argument("--epochs", type=int, default=20)
@@ -121,7 +122,7 @@ class ClockSampler:
 
 def lj_source_sha():
     h = hashlib.sha256()
-    for name in ("slots.cu", "md_kernels.cuh", "lj.cuh", "common.cuh"):
+    for name in ("md_kernels.cu", "md_kernels.cuh", "lj.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1704_03329_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -155,19 +156,31 @@ def host_cpu():
 
 
 def cpu_baseline(c_cells, steps):
-    """The oracle as it stands, single thread, on a bounded sample: the full
-    workload for `steps` steps (including its list builds)."""
+    """The oracle as it stands on a bounded sample (the full workload's
+    density, noise, temperature, cutoffs and list policy for `steps` steps,
+    including its list builds): one thread, and its per-atom loops on every
+    host core (OpenMP; the same results)."""
     import oracle
     from synth import configs
     c = configs.lj_solid(n_cells=c_cells)
     n = len(c["pos"])
     oracle.build()
-    t0 = time.perf_counter()
-    oracle.md_run(c["pos"], c["vel"], c["box"], steps, r_list=2.8, rebuild_every=10)
-    dt = time.perf_counter() - t0
-    return {**host_cpu(), "value": n * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 C oracle, {n} atoms x {steps} steps (set-up list build + rebuild every 10), "
-                      f"{dt:.1f} s wall, 1 thread"}
+
+    def timed(threads):
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        oracle.md_run(c["pos"], c["vel"], c["box"], steps, r_list=2.8, rebuild_every=10)
+        dt = time.perf_counter() - t0
+        oracle.set_threads(1)
+        return dt
+    dt1 = timed(1)
+    cores = os.cpu_count() or 1
+    dtn = timed(cores)
+    sample = f"FP64 C oracle, {n} atoms x {steps} steps (set-up list build + rebuild every 10)"
+    return {**host_cpu(), "value": n * steps / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample}, {dt1:.1f} s wall, 1 thread",
+            "all_cores": {"value": n * steps / dtn, "unit": UNIT, "cores": cores,
+                          "sample": f"{sample}, {dtn:.1f} s wall, {cores} threads (OpenMP over atoms)"}}
 
 
 def run_reference(args):
@@ -238,6 +251,9 @@ def run_ours(args):
         return L.MD(ctx, [0, n], [box], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=prec, energy_every=10)
 
     md = make_md(L.FP32)
+    # event-record nodes around every pair loop of the captured graphs: the
+    # dominant kernel's duration, measured inside the timed region
+    md.time_pair_loops(True)
     pos_d = pos_h.cuda()
     vel_d = vel_h.cuda()
     md.set_state(pos_d, vel_d)
@@ -273,8 +289,34 @@ def run_ours(args):
     ms = max_over_ranks(ms, device="cuda")
     value = world * n * K / (ms * 1e-3)
 
-    # ---- force kernel alone: average launch duration ----------------------
+    # ---- the dominant kernel: the fused pair loop (pair loop, second kick,
+    # next step's kick and drift; nine of the ten steps of a unit), its
+    # average duration over the last replayed unit of the timed region -----
     pairs, max_row = md.list_stats()
+    t_fused, n_fused, t_other, n_other = md.pair_loop_times()
+    t_fused = max_over_ranks(t_fused, device="cuda")
+    # per atom: count 4 + own position 16 + list 4 per listed pair + float4
+    # force 16 (the pair loop) + velocities in and out 48, positions in 24
+    # and out 24, fixed-point word out 16 and reference word in 16 (the
+    # integration)
+    fused_bytes = (36.0 + 128.0) * n + 4.0 * pairs
+    hbm, peak_kind = peaks()
+    achieved = fused_bytes / (t_fused * 1e-3) / 1e9
+    tpa = traffic_per_atom()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": (tpa * n if tpa is not None else None),
+                "peak_source": peak_kind,
+                "kernel": "k_lj_col32<false, true> (integrator pair loop with the second kick and the next step's "
+                          "kick and drift fused in; FP32 pairs, FP64 integration)",
+                "kernel_ms": round(t_fused, 5), "launches_timed": n_fused,
+                "timing": "CUDA events recorded as graph nodes around each pair-loop launch, last replayed unit of "
+                          "the timed region",
+                "bytes_per_atom": "164 + 4 x listed pairs (count 4, position 16, list 4/pair, force 16; velocities "
+                                  "48, positions 48, fixed-point words 32)",
+                "algorithmic_bytes_per_launch": fused_bytes, "pairs_listed_per_atom": round(pairs / n, 2),
+                "other_pair_loop_ms": round(t_other, 5)}
+
+    # ---- the pair loop alone (ppmd_md_forces): average launch duration ------
     R = 50
     md.forces()
     torch.cuda.synchronize()
@@ -285,19 +327,20 @@ def run_ours(args):
     f1.record(stream)
     torch.cuda.synchronize()
     f_ms = f0.elapsed_time(f1) / R
-    # cnt + own position (fixed-point int4; the brick copies of it come from
-    # L2) + float4 force + 16-bit list entries (stage slots)
-    alg_bytes = 36.0 * n + 2.0 * pairs
-    hbm, peak_kind = peaks()
-    achieved = alg_bytes / (f_ms * 1e-3) / 1e9
-    tpa = traffic_per_atom()
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": (tpa * n if tpa is not None else None),
-                "peak_source": peak_kind,
-                "kernel": "k_lj_slots32 (integrator pair loop, FP32, brick-staged, timed alone via ppmd_md_forces)",
-                "bytes_per_atom": "36 + 2 x listed pairs (count 4, position 16, force 16, list entries of 2 B)",
-                "kernel_ms": round(f_ms, 5), "algorithmic_bytes_per_launch": alg_bytes,
-                "pairs_listed_per_atom": round(pairs / n, 2)}
+    alone_bytes = 36.0 * n + 4.0 * pairs  # cnt + own position + float4 force + list entries
+    pair_loop_alone = {"kernel": "k_lj_col32<false, false> (pair loop alone, timed through ppmd_md_forces)",
+                       "ms": round(f_ms, 5), "algorithmic_bytes": alone_bytes,
+                       "achieved_gbs": round(alone_bytes / (f_ms * 1e-3) / 1e9, 1),
+                       "frac": round(alone_bytes / (f_ms * 1e-3) / 1e9 / hbm, 4)}
+
+    # ---- the list-age check over the same trajectory (warm-up + timed
+    # steps; the check changes no state) -------------------------------------
+    md_c = make_md(L.FP32)
+    md_c.set_check(True)
+    md_c.set_state(pos_d, vel_d)
+    md_c.run(W_run + K)
+    missed = md_c.missed_pairs()
+    md_c.close()
 
     # ---- list-free pair loop (no neighbour list) on the same positions -----
     pos_now = torch.empty((n, 3), dtype=torch.float64, device="cuda")
@@ -398,15 +441,19 @@ def run_ours(args):
             "clocks": clocks,
             "fp64_gpu_path": {"value": value64, "unit": UNIT, "steps": K64,
                               "fp32_speedup": value / world / value64},
-            "list_free_forces": list_free, "newton3_half_list": newton3,
+            "list_free_forces": list_free, "newton3_half_list": newton3, "pair_loop_alone": pair_loop_alone,
             "md_info": {"max_disp": info["max_disp"], "skin_warning": info["status"] == L.WARN_SKIN,
-                        "total_energy_drift_per_atom": drift},
+                        "total_energy_drift_per_atom": drift,
+                        "missed_pairs": missed,
+                        "missed_pairs_note": f"pairs within rc at the {(W_run + K) // 10} rebuilds of the warm-up "
+                                             "and timed steps that the previous list lacked (same trajectory, "
+                                             "list-age check on)"},
             "impl": "ours"}
     if world == 1:
         suites = [x for x in args.suites.split(",") if x and x != "none"]
         for name in suites:
             fn = {"replicas": suite_replicas, "analysis": suite_analysis, "classifier": suite_classifier,
-                  "otf": suite_otf}[name]
+                  "otf": suite_otf, "precision": suite_precision}[name]
             try:
                 k0 = ctx.kernel_count()
                 line[name] = fn(args, L, ctx, stream)
@@ -450,6 +497,52 @@ def suite_replicas(args, L, ctx, stream):
                         f"jittered sc, rc 2.5, list min(2.8, L/3), rebuild every 10, dt 0.005",
             "metric": "aggregate atom-steps/s", "value": n * K / t, "unit": UNIT, "steps": K, "atoms": n,
             "ms_per_step": t / K * 1e3}
+
+
+def suite_precision(args, L, ctx, stream):
+    """The large solid as its workload specifies it: 1000 steps of the
+    1,000,188-atom fcc solid from the same state, FP32 pairs with FP64
+    integration and all-FP64: total energy per atom every 10 steps, its drift
+    in each precision, the FP32-FP64 position divergence, and the list-age
+    check (pairs missed by the skin 0.3 / rebuild 10 policy) over the FP32
+    run."""
+    import numpy as np
+    import torch
+    from synth import configs
+    c = configs.lj_solid(n_cells=args.cells)
+    n = len(c["pos"])
+    K = max(10, (args.precision_steps // 10) * 10)
+    pos, vel = torch.from_numpy(c["pos"]).cuda(), torch.from_numpy(c["vel"]).cuda()
+    out = {}
+    for name, prec in (("fp32", L.FP32), ("fp64", L.FP64)):
+        md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=prec,
+                  energy_every=10)
+        if prec == L.FP32:
+            md.set_check(True)
+        md.set_state(pos, vel)
+        en = torch.zeros((K, 2), dtype=torch.float64, device="cuda")
+        t, _ = _timed(stream, lambda: md.run(K, en))
+        p = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        md.get_state(p)
+        e = en.cpu().numpy()[9::10].sum(1) / n  # (KE + PE) per atom, every 10 steps
+        out[name] = {"pos": p.cpu().numpy(), "etot": e, "s": t,
+                     "missed": md.missed_pairs() if prec == L.FP32 else None}
+        md.close()
+    d = out["fp32"]["pos"] - out["fp64"]["pos"]
+    d -= c["box"] * np.rint(d / c["box"])
+    dn = np.sqrt((d * d).sum(1))
+    res = {"workload": f"LJ fcc solid {args.cells}^3 cells ({n} atoms), rho 0.8442, rc 2.5, list 2.8 rebuilt every "
+                       f"10, dt 0.005, T 0.8, {K} steps from the same state in both precisions",
+           "steps": K, "atoms": n}
+    for name in ("fp32", "fp64"):
+        e = out[name]["etot"]
+        res[name] = {"atom_steps_per_s": n * K / out[name]["s"], "total_energy_per_atom_first": float(e[0]),
+                     "total_energy_per_atom_last": float(e[-1]), "drift_per_atom": float(e[-1] - e[0]),
+                     "max_excursion_per_atom": float(np.abs(e - e[0]).max())}
+    res["position_divergence"] = {"max": float(dn.max()), "rms": float(np.sqrt((dn ** 2).mean())),
+                                  "unit": "sigma", "note": "FP32-pair run minus all-FP64 run after the last step"}
+    res["missed_pairs_fp32"] = out["fp32"]["missed"]
+    return res
 
 
 def suite_otf(args, L, ctx, stream):
@@ -643,6 +736,34 @@ def suite_classifier(args, L, ctx, stream):
         pass
     mlp_only = torch.cat([L.ppmd_mlp_forward(ctx, P, f).argmax(1).to(torch.int8) for f in feats])
     res_c = res["cna"]
+    # the method without the learned part (Sec. 4.1): Q4, Q6 against the
+    # perfect-lattice table within a tolerance, the tolerance chosen on the
+    # training boxes (its best agreement with CNA there)
+    pos_tr = torch.cat([torch.from_numpy(b["pos"]) for b in train]).cuda()
+    off_tr = np.cumsum([0] + [len(b["pos"]) for b in train]).tolist()
+    bx_tr = [b["box"] for b in train]
+    grid = [0.02, 0.04, 0.06, 0.08, 0.1, 0.12, 0.15, 0.2]
+    agree_tr = {}
+    for tol in grid:
+        lab_t = L.ppmd_classify_boxes(ctx, pos_tr, off_tr, bx_tr, mode=2, threshold=tol, r_feat=R_BOA,
+                                      want_confidence=False, count=False)[0]
+        agree_tr[tol] = float((lab_t == y).float().mean())
+    best_tol = max(grid, key=lambda t: agree_tr[t])
+    del pos_tr
+    res_b = {}
+
+    def run_boa():
+        res_b["lab"] = L.ppmd_classify_boxes(ctx, pos_all, off, bxs, mode=2, threshold=best_tol, r_feat=R_BOA,
+                                             want_confidence=False, count=False)[0]
+
+    def run_mlp_only():
+        res_b["mlp"] = L.ppmd_classify_boxes(ctx, pos_all, off, bxs, mode=1, params=P, threshold=0.0,
+                                             want_confidence=False, count=False)[0]
+    run_boa()
+    run_mlp_only()
+    t_b = min(_timed(stream, run_boa)[0] for _ in range(3))
+    t_mo = min(_timed(stream, run_mlp_only)[0] for _ in range(3))
+    ctx.sync()
     return {"workload": "train: 32 structure boxes (4,096,000 atoms, noise U[0.01, 0.12] d_nn, seed 50), "
                         f"{args.epochs} epochs, batch 65536, AdamW lr 1e-3 wd 0.01; infer: 4,096,000 fresh atoms (seed 51)",
             "metric": "classified atoms/s (MLP + CNA fallback vs exact CNA)", "atoms": n,
@@ -651,6 +772,16 @@ def suite_classifier(args, L, ctx, stream):
             "one_call_per_box": {"mlp_fallback_atoms_per_s": n / t_m1, "cna_atoms_per_s": n / t_c1,
                                  "speedup_vs_cna": t_c1 / t_m1},
             "agreement_with_cna": agree, "mlp_only_agreement": float((mlp_only == res_c).float().mean()),
+            "methods": {"note": "agreement with exact CNA and classified atoms/s of one box-set call each, on the "
+                                "4,096,000 inference atoms",
+                        "boa_tolerance": {"tolerance": best_tol, "agreement_with_cna":
+                                          float((res_b["lab"] == res_c).float().mean()), "atoms_per_s": n / t_b,
+                                          "tolerance_chosen_on": "training boxes",
+                                          "training_agreement": agree_tr},
+                        "mlp_only": {"agreement_with_cna": float((res_b["mlp"] == res_c).float().mean()),
+                                     "atoms_per_s": n / t_mo},
+                        "mlp_fallback": {"agreement_with_cna": agree, "atoms_per_s": n / t_m},
+                        "cna": {"agreement_with_cna": 1.0, "atoms_per_s": n / t_c}},
             "fallback_fraction": nfb / n, "train_steps": step, "train_s": t_train, "loss_per_epoch": losses,
             "mlp_kernel": {"ms": t_f * 1e3, "achieved_tflops": flops / t_f / 1e12, "peak_tflops": peak,
                            "frac": flops / t_f / 1e12 / peak, "bound": "tensor (BF16, sustained peak of measured)"}}

@@ -368,11 +368,12 @@ int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **md, int64_t nbox, const int64_t *ato
 int ppmd_md_destroy(ppmd_md *md);
 /* Load positions and velocities (device, [n][3], caller order), wrap, sort,
  * build the list and compute the initial forces F(r_0).
- * With PPMD_FP32 the list (the paper's neighbour matrix, Sec. 3.5.1) is kept
- * per brick of cells: the grid is cut into bricks, each brick's
- * neighbourhood (its cells and one layer around them) is copied into shared
- * memory by the pair loop of every step, and a list entry is the
- * neighbour's place in that copy.  At set-up the call reads one device word
+ * With the PPMD_PAIR_BRICKS mechanism (ppmd_md_set_pair_loop) the list (the
+ * paper's neighbour matrix, Sec. 3.5.1) is kept per brick of cells: the
+ * grid is cut into bricks, each brick's neighbourhood (its cells and one
+ * layer around them) is copied into shared memory by the pair loop of every
+ * step, and a list entry is the neighbour's place in that copy.  At set-up
+ * the call then reads one device word
  * (it synchronises) to check that every neighbourhood fits the copy; a
  * larger one makes it grow the copy and build again, or fail with
  * PPMD_ERR_CAPACITY when it would exceed what one block may hold.  A
@@ -409,6 +410,43 @@ int ppmd_md_set_boa(ppmd_md *md, int32_t every, double r_boa);
  * qrows (device [nsteps][3], may be NULL) on analysis steps.  Steps with the
  * thermostat or an analysis are not fused with the next step's drift. */
 int ppmd_md_run_analysed(ppmd_md *md, int32_t nsteps, double *energies, double *qrows, int use_graph);
+/* Pair-loop mechanism of the integrator (Sec. 3.4: different pair-looping
+ * mechanisms give the same result at different cost), chosen before
+ * ppmd_md_set_state (PPMD_ERR_INVALID after it):
+ *   PPMD_PAIR_COLUMNS (default): the neighbour matrix W of Sec. 3.5.1 as
+ *     atom indices, column-major in groups of four, one thread per atom
+ *     gathering its neighbours' positions from global memory;
+ *   PPMD_PAIR_BRICKS (PPMD_FP32, no on-the-fly analysis): the grid cut into
+ *     bricks of cells; each brick's neighbourhood is copied into shared
+ *     memory by bulk asynchronous copies in every pair loop and W holds each
+ *     neighbour's 16-bit place in that copy (see ppmd_md_set_state).
+ * Both give the same forces bit for bit (same pairs in the same order). */
+#define PPMD_PAIR_COLUMNS 0
+#define PPMD_PAIR_BRICKS 1
+int ppmd_md_set_pair_loop(ppmd_md *md, int mechanism);
+/* List-age check (Sec. 3.5, Eq. (6): a list built with the extended cutoff
+ * r_list = r_c + delta holds every pair that can come within r_c before the
+ * next build only while no atom moves more than delta / 2).  With on != 0
+ * every later rebuild counts the pairs that are within r_c at that rebuild
+ * but were at least r_list apart at the previous build, i.e. missing from
+ * the list the pair loop used until then (FP32 tests, FP64 near both
+ * cutoffs, positions to the fixed-point quantum L 2^-32).  It changes no
+ * state: a checked run gives the same trajectory bit for bit.  Pairs that
+ * came within r_c and left again between two builds are not seen, so the
+ * count is a lower bound on the pairs the list missed.  The count restarts
+ * at ppmd_md_set_state; ppmd_md_missed_pairs (host int64) reads it
+ * (synchronises).  Uses 16 extra bytes of device memory per atom. */
+int ppmd_md_set_check(ppmd_md *md, int on);
+int ppmd_md_missed_pairs(ppmd_md *md, int64_t *missed);
+/* Measurement aid: with on != 0, the CUDA graphs of later runs record a CUDA
+ * event before and after every pair-loop launch (event-record graph nodes,
+ * on the integrator's stream); ppmd_md_pair_loop_times then returns the
+ * average duration (ms) of the pair loops of the last replayed graph, those
+ * that also made the next step's kick and drift (fused, FP32) and the
+ * others, with their counts (host outputs, any may be NULL).  Synchronises.
+ * PPMD_ERR_INVALID when no timed graph has run. */
+int ppmd_md_time_pair_loops(ppmd_md *md, int on);
+int ppmd_md_pair_loop_times(ppmd_md *md, double *ms_fused, int32_t *n_fused, double *ms_other, int32_t *n_other);
 /* Per-atom Q4, Q5, Q6 of the last analysis step (device float [n] each,
  * caller order; any may be NULL).  PPMD_ERR_INVALID before the first. */
 int ppmd_md_get_q(ppmd_md *md, float *q4, float *q5, float *q6);

@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+                               "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -44,6 +44,7 @@ def _load():
     P = C.c_void_p
     sig = {
         "ora_wrap": (None, [i64, P, P]),
+        "ora_set_threads": (None, [C.c_int]),
         "ora_cell_grid": (None, [P, f64, P]),
         "ora_cells": (None, [i64, P, P, P, P, P, P]),
         "ora_neigh_brute": (i64, [i64, P, P, f64, P, P]),
@@ -77,6 +78,12 @@ def _p(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(k: int) -> None:
+    """Threads of the integrator's per-atom loops (neighbour search, pair
+    loop, particle loops; 1 by default).  Results do not depend on it."""
+    _load().ora_set_threads(int(k))
 
 
 def wrap(pos, box):

@@ -40,6 +40,12 @@
 
 #define ORA_PI 3.14159265358979323846
 
+/* Threads of the per-atom loops of the integrator (neighbour search, pair
+ * loop, particle loops): 1 by default.  Every reduction over atoms is taken
+ * afterwards in atom order, so the results do not depend on the count.   */
+static int ora_nthreads = 1;
+void ora_set_threads(int k) { ora_nthreads = k > 0 ? k : 1; }
+
 /* ------------------------------------------------------------------ */
 /* Periodic domain (Sec. 3.5)                                          */
 /* ------------------------------------------------------------------ */
@@ -136,36 +142,57 @@ int64_t ora_neigh_brute(int64_t n, const double *pos, const double *L, double r,
 }
 
 /* Cell-based loop of Sec. 3.5: the 27 cells around the cell of i.  Needs at
- * least three cells per edge so that the 27 cells are distinct. */
+ * least three cells per edge so that the 27 cells are distinct.
+ * Row of atom i: the number of its neighbours, written (sorted) to out when
+ * out is not NULL. */
+static int64_t neigh_cells_row(int64_t i, const double *pos, const double *L, double r2, const int32_t *nc,
+                               const int32_t *cell_of, const int32_t *cell_start, const int32_t *cell_atoms,
+                               int32_t *out) {
+    double dr[3];
+    int64_t cnt = 0;
+    int32_t c = cell_of[i];
+    int32_t cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
+    for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                int32_t x = (cx + ox + nc[0]) % nc[0];
+                int32_t y = (cy + oy + nc[1]) % nc[1];
+                int32_t z = (cz + oz + nc[2]) % nc[2];
+                int32_t cc = (z * nc[1] + y) * nc[0] + x;
+                for (int32_t k = cell_start[cc]; k < cell_start[cc + 1]; ++k) {
+                    int32_t j = cell_atoms[k];
+                    if (j == i) continue;
+                    if (min_image(&pos[3 * i], &pos[3 * j], L, dr) < r2) {
+                        if (out) out[cnt] = j;
+                        ++cnt;
+                    }
+                }
+            }
+    if (out) qsort(out, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    return cnt;
+}
+
+/* All rows: the counts first, their running sum as the row offsets, then
+ * the rows (each atom's row depends on that atom alone). */
 int64_t ora_neigh_cells(int64_t n, const double *pos, const double *L, double r, const int32_t *nc,
                         const int32_t *cell_of, const int32_t *cell_start, const int32_t *cell_atoms,
                         int64_t *offs, int32_t *nbr) {
-    double r2 = r * r, dr[3];
+    double r2 = r * r;
+    int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for num_threads(ora_nthreads) schedule(static)
+    for (int64_t i = 0; i < n; ++i) cnt[i] = neigh_cells_row(i, pos, L, r2, nc, cell_of, cell_start, cell_atoms, NULL);
     int64_t tot = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (offs) offs[i] = tot;
-        int64_t row0 = tot;
-        int32_t c = cell_of[i];
-        int32_t cx = c % nc[0], cy = (c / nc[0]) % nc[1], cz = c / (nc[0] * nc[1]);
-        for (int oz = -1; oz <= 1; ++oz)
-            for (int oy = -1; oy <= 1; ++oy)
-                for (int ox = -1; ox <= 1; ++ox) {
-                    int32_t x = (cx + ox + nc[0]) % nc[0];
-                    int32_t y = (cy + oy + nc[1]) % nc[1];
-                    int32_t z = (cz + oz + nc[2]) % nc[2];
-                    int32_t cc = (z * nc[1] + y) * nc[0] + x;
-                    for (int32_t k = cell_start[cc]; k < cell_start[cc + 1]; ++k) {
-                        int32_t j = cell_atoms[k];
-                        if (j == i) continue;
-                        if (min_image(&pos[3 * i], &pos[3 * j], L, dr) < r2) {
-                            if (nbr) nbr[tot] = j;
-                            ++tot;
-                        }
-                    }
-                }
-        if (nbr) qsort(&nbr[row0], (size_t)(tot - row0), sizeof(int32_t), cmp_i32);
+        tot += cnt[i];
     }
     if (offs) offs[n] = tot;
+    if (nbr && offs) {
+#pragma omp parallel for num_threads(ora_nthreads) schedule(static)
+        for (int64_t i = 0; i < n; ++i)
+            neigh_cells_row(i, pos, L, r2, nc, cell_of, cell_start, cell_atoms, nbr + offs[i]);
+    }
+    free(cnt);
     return tot;
 }
 
@@ -179,10 +206,13 @@ int64_t ora_neigh_cells(int64_t n, const double *pos, const double *L, double r,
 
 void ora_lj(int64_t n, const double *pos, const double *L, double eps, double sigma, double rc, double shift,
             const int64_t *offs, const int32_t *nbr, double *F, double *e_atom, double *U, double *W) {
-    double rc2 = rc * rc, s2 = sigma * sigma, dr[3];
-    double usum = 0.0, wsum = 0.0;
+    double rc2 = rc * rc, s2 = sigma * sigma;
+    /* per-atom energy and virial terms, summed over the atoms in atom order below */
+    double *ew = (double *)malloc(sizeof(double) * (size_t)(2 * (n > 0 ? n : 1)));
+#pragma omp parallel for num_threads(ora_nthreads) schedule(static)
     for (int64_t i = 0; i < n; ++i) {
-        double fx = 0.0, fy = 0.0, fz = 0.0, ei = 0.0;
+        double dr[3];
+        double fx = 0.0, fy = 0.0, fz = 0.0, ei = 0.0, wsum = 0.0;
         for (int64_t k = offs[i]; k < offs[i + 1]; ++k) {
             int32_t j = nbr[k];
             double r2 = min_image(&pos[3 * i], &pos[3 * j], L, dr);
@@ -203,10 +233,17 @@ void ora_lj(int64_t n, const double *pos, const double *L, double eps, double si
         F[3 * i + 1] = fy;
         F[3 * i + 2] = fz;
         if (e_atom) e_atom[i] = ei;
-        usum += ei;
+        ew[2 * i] = ei;
+        ew[2 * i + 1] = wsum;
     }
+    double usum = 0.0, wtot = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        usum += ew[2 * i];
+        wtot += ew[2 * i + 1];
+    }
+    free(ew);
     if (U) *U = usum;
-    if (W) *W = wsum;
+    if (W) *W = wtot;
 }
 
 /* ------------------------------------------------------------------ */
@@ -368,11 +405,14 @@ int64_t ora_md_run_otf(int64_t n, double *pos, double *vel, double *F, const dou
     ora_lj(n, pos, L, eps, sigma, rc, shift, offs, nbr, F, NULL, &U, NULL);
     for (int32_t s = 1; s <= nsteps; ++s) {
         ora_vv(1, n, pos, vel, F, L, mass, dt);
-        double dr[3];
+        double md2 = maxdisp * maxdisp;
+#pragma omp parallel for num_threads(ora_nthreads) schedule(static) reduction(max : md2)
         for (int64_t i = 0; i < n; ++i) {
+            double dr[3];
             double d2 = min_image(&pos[3 * i], &ref[3 * i], L, dr);
-            if (d2 > maxdisp * maxdisp) maxdisp = sqrt(d2);
+            if (d2 > md2) md2 = d2;
         }
+        maxdisp = sqrt(md2);
         if (rebuild_every > 0 && s % rebuild_every == 0) {
             build_list_cells(n, pos, L, r_list, offs, &nbr, &cap);
             memcpy(ref, pos, sizeof(double) * (size_t)(3 * n));
@@ -418,11 +458,14 @@ double ora_md_run(int64_t n, double *pos, double *vel, double *F, const double *
     ora_lj(n, pos, L, eps, sigma, rc, shift, offs, nbr, F, NULL, &U, NULL);
     for (int32_t s = 1; s <= nsteps; ++s) {
         ora_vv(1, n, pos, vel, F, L, mass, dt);
-        double dr[3];
+        double md2 = maxdisp * maxdisp;
+#pragma omp parallel for num_threads(ora_nthreads) schedule(static) reduction(max : md2)
         for (int64_t i = 0; i < n; ++i) {
+            double dr[3];
             double d2 = min_image(&pos[3 * i], &ref[3 * i], L, dr);
-            if (d2 > maxdisp * maxdisp) maxdisp = sqrt(d2);
+            if (d2 > md2) md2 = d2;
         }
+        maxdisp = sqrt(md2);
         if (rebuild_every > 0 && s % rebuild_every == 0) {
             build_list_cells(n, pos, L, r_list, offs, &nbr, &cap);
             memcpy(ref, pos, sizeof(double) * (size_t)(3 * n));

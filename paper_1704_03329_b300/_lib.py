@@ -24,6 +24,7 @@ _lib = C.CDLL(LIB_PATH)
 OK, ERR_INVALID, ERR_BOX, ERR_CAPACITY, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6, -7
 WARN_SKIN = 1
 FP64, FP32 = 0, 1
+PAIR_COLUMNS, PAIR_BRICKS = 0, 1
 OTHER, FCC, HCP, BCC = 0, 1, 2, 3
 _NAMES = {0: "PPMD_OK", -1: "PPMD_ERR_INVALID", -2: "PPMD_ERR_BOX", -3: "PPMD_ERR_CAPACITY",
           -4: "PPMD_ERR_NONFINITE", -5: "PPMD_ERR_CUDA", -6: "PPMD_ERR_TIMEOUT", -7: "PPMD_ERR_NOMEM",
@@ -95,6 +96,11 @@ _SIGS = {
     "ppmd_md_forces": (_I, [_P]),
     "ppmd_md_list_stats": (_I, [_P, C.POINTER(_I64), C.POINTER(_I32)]),
     "ppmd_md_get_list": (_I, [_P, _P, _P, _I32]),
+    "ppmd_md_set_pair_loop": (_I, [_P, _I]),
+    "ppmd_md_set_check": (_I, [_P, _I]),
+    "ppmd_md_missed_pairs": (_I, [_P, C.POINTER(_I64)]),
+    "ppmd_md_time_pair_loops": (_I, [_P, _I]),
+    "ppmd_md_pair_loop_times": (_I, [_P, C.POINTER(_D), C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
     "ppmd_lj_forces_noalloc": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _P, _P, _I32, _I, _P, _P, _P,
                                     _P]),
 }
@@ -512,6 +518,28 @@ class MD:
         pairs, mx = _I64(), _I32()
         self.ctx.check(_lib.ppmd_md_list_stats(self.h, C.byref(pairs), C.byref(mx)))
         return pairs.value, mx.value
+
+    def set_pair_loop(self, mechanism):
+        """PAIR_COLUMNS (default) or PAIR_BRICKS; before set_state."""
+        self.ctx.check(_lib.ppmd_md_set_pair_loop(self.h, int(mechanism)))
+
+    def set_check(self, on=True):
+        """Count, at every later rebuild, pairs within rc that the previous list lacked."""
+        self.ctx.check(_lib.ppmd_md_set_check(self.h, 1 if on else 0))
+
+    def missed_pairs(self):
+        v = _I64()
+        self.ctx.check(_lib.ppmd_md_missed_pairs(self.h, C.byref(v)))
+        return v.value
+
+    def time_pair_loops(self, on=True):
+        self.ctx.check(_lib.ppmd_md_time_pair_loops(self.h, 1 if on else 0))
+
+    def pair_loop_times(self):
+        """(ms per fused pair loop, count, ms per other pair loop, count) of the last replayed graph."""
+        a, na, b, nb = _D(), _I32(), _D(), _I32()
+        self.ctx.check(_lib.ppmd_md_pair_loop_times(self.h, C.byref(a), C.byref(na), C.byref(b), C.byref(nb)))
+        return a.value, na.value, b.value, nb.value
 
     def get_list(self, max_nbr=None):
         """The last build's list in caller order: (nbr [n, max_nbr] int32 caller indices, count [n])."""

@@ -44,6 +44,14 @@ struct ppmd_md {
     // on-the-fly analysis and the FP64 path use W
     bool slots = false;
     uint16_t *W16 = nullptr;
+    // optional CUDA events around the pair loops of a captured unit (their
+    // durations in the last replay): begin/end of the launch of step k at
+    // ev[2 (k - 1)], ev[2 (k - 1) + 1]; ev_fused[k - 1]: that launch also
+    // made the next step's kick and drift
+    bool time_pair = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<char> ev_fused;
+    int32_t ev_steps = 0;
     int32_t *stage_need = nullptr;  // largest neighbourhood met by a slot-list build
     Brick *bricks = nullptr;
     int32_t stage_cap = 0;  // shared-memory stage of a list-build block (atoms)
@@ -55,6 +63,11 @@ struct ppmd_md {
     // reductions
     double *part_f = nullptr, *part_k = nullptr, *red = nullptr, *ebuf = nullptr;
     unsigned int *max_disp_bits = nullptr;
+    // missed-pair check at every rebuild (optional): the reference words of
+    // the previous build gathered into the new order, and the running count
+    bool check = false, have_ref = false;
+    int4 *xq_old = nullptr;
+    unsigned long long *missed = nullptr;
     int64_t step = 0, rebuilds = 0;
     bool ready = false;
     // graphs
@@ -322,6 +335,63 @@ void use_buffer(ppmd_md *m, int b) {
     m->xq = m->xq_buf[b];
 }
 
+// Pairs of the new list (built from the current positions) that are now
+// closer than r_c although they were at least r_list apart at the previous
+// build, i.e. missing from the list the pair loop used since then.  xq: the
+// current words, xq_old: the previous build's words in the same (new)
+// order.  FP32 tests on the fixed-point differences, FP64 inside the bands
+// of both cutoffs (exact up to the fixed-point quantum, L 2^-32).
+__global__ void k_missed_pairs(int64_t n, int64_t ld, const int4 *__restrict__ xq, const int4 *__restrict__ xq_old,
+                               const double *__restrict__ pos64, SegTable st, const int32_t *__restrict__ W,
+                               const int32_t *__restrict__ cnt, int32_t max_nbr, double rc2, float rc2_lo, float rc2_hi,
+                               unsigned long long *missed) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c = 0;
+    if (i < n) {
+        const int4 a = xq[i], ao = xq_old[i];
+        const Seg &S = seg_ref(st, a.w);
+        const int32_t m = min(cnt[i], max_nbr);
+        for (int32_t k = 0; k < m; ++k) {
+            const int32_t j = W[(((int64_t)(k >> 2) * ld + i) << 2) + (k & 3)];
+            const int4 b = xq[j];
+            const float dx = fixed_delta((uint32_t)a.x, (uint32_t)b.x, S.sx[0]);
+            const float dy = fixed_delta((uint32_t)a.y, (uint32_t)b.y, S.sx[1]);
+            const float dz = fixed_delta((uint32_t)a.z, (uint32_t)b.z, S.sx[2]);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool inside = r2 < rc2_lo;
+            if (!inside && r2 < rc2_hi) {
+                double dr[3];
+                inside = min_image_r2(pos64 + 3 * i, pos64 + 3 * (int64_t)j, S, dr) < rc2;
+            }
+            if (!inside) continue;
+            const int4 bo = xq_old[j];
+            const int32_t q[3] = {(int32_t)((uint32_t)ao.x - (uint32_t)bo.x), (int32_t)((uint32_t)ao.y - (uint32_t)bo.y),
+                                  (int32_t)((uint32_t)ao.z - (uint32_t)bo.z)};
+            const float fo = fmaf((float)q[0] * S.sx[0], (float)q[0] * S.sx[0],
+                                  fmaf((float)q[1] * S.sx[1], (float)q[1] * S.sx[1], (float)q[2] * S.sx[2] * (float)q[2] * S.sx[2]));
+            bool was_listed = fo < S.rl2_lo;
+            if (!was_listed && fo < S.rl2_hi) {
+                double r2o = 0.0;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const double x = (double)q[d] * (S.L[d] * 2.3283064365386962890625e-10);
+                    r2o += x * x;
+                }
+                was_listed = r2o < S.rl2;
+            }
+            if (!was_listed) ++c;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(missed, c);
+}
+
+__global__ void k_gather_xq(int64_t n, const int32_t *__restrict__ perm, const int4 *__restrict__ in, int4 *__restrict__ out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = in[perm[k]];
+}
+
 int rebuild(ppmd_md *m) {
     ppmd_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
@@ -330,6 +400,8 @@ int rebuild(ppmd_md *m) {
                        true));
     PPMD_TRY(md_gather(ctx, n, m->cell_atoms, m->st, m->pos, m->vel, m->orig, m->seg_of, m->pos_t, m->vel_t, m->xq_t,
                        m->orig_t, m->seg_t));
+    const bool check = m->check && m->have_ref && n > 0;
+    if (check) PPMD_LAUNCH(ctx, k_gather_xq, div_up(n, 256), 256, 0, n, m->cell_atoms, m->xq_ref, m->xq_old);
     use_buffer(m, 0);
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, m->pos_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, m->vel_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
@@ -337,12 +409,21 @@ int rebuild(ppmd_md *m) {
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq_ref, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    if (m->slots)
-        return build_slot_list(ctx, m->nbricks, m->bricks, m->xq, m->pos, m->st, m->cell_start, m->W16, m->ld, m->cnt,
-                               m->p.max_nbr, m->stage_cap, m->stage_need, m->n);
-    PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, BrickShape{1, 1, 1}, m->xq, m->pos, m->st, m->cell_start,
-                               m->W, m->ld, m->cnt, m->p.max_nbr, m->stage_cap, true));
-    return build_short_list(m);
+    m->have_ref = true;
+    if (m->slots) {
+        PPMD_TRY(build_slot_list(ctx, m->nbricks, m->bricks, m->xq, m->pos, m->st, m->cell_start, m->W16, m->ld, m->cnt,
+                                 m->p.max_nbr, m->stage_cap, m->stage_need, m->n));
+        if (check)
+            PPMD_TRY(slots_to_atoms(ctx, m->nbricks, m->bricks, m->st, m->cell_start, m->W16, m->ld, m->cnt,
+                                    m->p.max_nbr, m->stage_cap, m->W, m->n));
+    } else {
+        PPMD_TRY(build_list_bricks(ctx, m->nbricks, m->bricks, BrickShape{1, 1, 1}, m->xq, m->pos, m->st, m->cell_start,
+                                   m->W, m->ld, m->cnt, m->p.max_nbr, m->stage_cap, true));
+    }
+    if (check)
+        PPMD_LAUNCH(ctx, k_missed_pairs, div_up(n, 256), 256, 0, n, m->ld, m->xq, m->xq_old, m->pos, m->st, m->W, m->cnt,
+                    m->p.max_nbr, m->c.rc2, m->c.rc2_lo, m->c.rc2_hi, m->missed);
+    return m->slots ? check_launch(ctx, "rebuild") : build_short_list(m);
 }
 
 // Pair loop; with kick = true also the second kick of the step, with
@@ -397,7 +478,13 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow =
     // with the next step's kick and drift fused in, the step's positions
     // stay in the other buffer (prev) for the thermostat and the analysis
     const bool fused = fuse_next && f32;
+    const bool timed = m->time_pair && base && s >= 1 && 2 * s <= (int64_t)m->ev.size();
+    if (timed) PPMD_TRY(cuda_check(ctx, cudaEventRecord(m->ev[2 * (s - 1)], ctx->stream), "event"));
     PPMD_TRY(forces(m, energy, true, fused));
+    if (timed) {
+        PPMD_TRY(cuda_check(ctx, cudaEventRecord(m->ev[2 * (s - 1) + 1], ctx->stream), "event"));
+        m->ev_fused[s - 1] = fused ? 1 : 0;
+    }
     const int prev = fused ? m->cur ^ 1 : m->cur;
     if (energy) {
         PPMD_TRY(reduce_partials(ctx, m->part_f, force_blocks(m), 3, m->red));
@@ -445,9 +532,9 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     m->n = atom_off[nbox];
     m->nbox = nbox;
     m->p = p;
-    m->slots = p.prec == PPMD_FP32;
-    // the list is stored in groups of four atom indices, or eight slots
-    m->p.max_nbr = m->slots ? (p.max_nbr + 7) & ~7 : (p.max_nbr + 3) & ~3;
+    // the atom-index list is stored in groups of four; FP32 rows are rounded
+    // to eight so that the brick-staged mechanism can use the same capacity
+    m->p.max_nbr = p.prec == PPMD_FP32 ? (p.max_nbr + 7) & ~7 : (p.max_nbr + 3) & ~3;
     m->h = p.dt / (2.0 * p.mass);
     m->half_m = 0.5 * p.mass;
     m->segs.resize(nbox);
@@ -520,10 +607,7 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_atoms, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cell_start, m->ncell + 1);
     m->ld = (n + 31) / 32 * 32;
-    if (rc == PPMD_OK) {
-        if (m->slots) rc = md_alloc(m, &m->W16, (size_t)m->ld * m->p.max_nbr);
-        else rc = md_alloc(m, &m->W, (size_t)m->ld * m->p.max_nbr);
-    }
+    if (rc == PPMD_OK) rc = md_alloc(m, &m->W, (size_t)m->ld * m->p.max_nbr);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->stage_need, 1);
     if (rc == PPMD_OK) rc = cuda_check(ctx, cudaMemset(m->stage_need, 0, sizeof(int32_t)), "memset");
     if (rc == PPMD_OK) {
@@ -535,7 +619,6 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
             rc = cuda_check(ctx, cudaMemcpy(m->bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice), "copy");
     }
     if (rc == PPMD_OK) rc = neigh_brick_setup(ctx, m->p.max_nbr);
-    if (rc == PPMD_OK && m->slots) rc = slots_setup(ctx, m->stage_cap, m->p.max_nbr);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt, n);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_f, 3 * std::max<int64_t>(lj_columns_blocks(n), m->nbricks) + 3);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);
@@ -568,6 +651,7 @@ extern "C" int ppmd_md_destroy(ppmd_md *m) {
     }
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
     for (void *q : m->allocs) cudaFree(q);
     delete m;
     return PPMD_OK;
@@ -620,6 +704,8 @@ extern "C" int ppmd_md_set_state(ppmd_md *m, const double *pos, const double *ve
     if (n > 0)
         PPMD_LAUNCH(ctx, k_init_state, div_up(n, 256), 256, 0, n, m->pos, m->d_atom_off, m->nbox, m->st, m->xq, m->orig,
                     m->seg_of, ctx->d_status);
+    m->have_ref = false;  // the first build of a state has no previous list
+    if (m->missed) PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(m->missed, 0, sizeof(unsigned long long), s), "memset"));
     PPMD_TRY(rebuild(m));
     if (m->slots) PPMD_TRY(fit_stage(m));
     PPMD_TRY(forces(m, false, false));
@@ -835,6 +921,92 @@ extern "C" int ppmd_md_set_boa(ppmd_md *m, int32_t every, double r_boa) {
     m->r_boa = r_boa;
     // the short list of the current build (later builds make their own)
     return m->ready ? build_short_list(m) : PPMD_OK;
+}
+
+extern "C" int ppmd_md_set_pair_loop(ppmd_md *m, int mechanism) {
+    if (!m) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    if (mechanism != PPMD_PAIR_COLUMNS && mechanism != PPMD_PAIR_BRICKS)
+        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_set_pair_loop: unknown mechanism %d", mechanism);
+    if (m->ready) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_set_pair_loop: call it before ppmd_md_set_state");
+    if (mechanism == PPMD_PAIR_BRICKS && (m->p.prec != PPMD_FP32 || m->boa_every > 0))
+        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_set_pair_loop: bricks need FP32 and no on-the-fly analysis");
+    cudaSetDevice(ctx->device);
+    drop_graph(m);
+    if (mechanism == PPMD_PAIR_BRICKS) {
+        if (!m->W16) PPMD_TRY(md_alloc(m, &m->W16, (size_t)m->ld * m->p.max_nbr));
+        PPMD_TRY(slots_setup(ctx, m->stage_cap, m->p.max_nbr));
+    }
+    m->slots = mechanism == PPMD_PAIR_BRICKS;
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_set_check(ppmd_md *m, int on) {
+    if (!m) return PPMD_ERR_INVALID;
+    cudaSetDevice(m->ctx->device);
+    drop_graph(m);
+    if (on && !m->xq_old) {
+        PPMD_TRY(md_alloc(m, &m->xq_old, (size_t)m->n));
+        PPMD_TRY(md_alloc(m, &m->missed, 1));
+        PPMD_TRY(cuda_check(m->ctx, cudaMemset(m->missed, 0, sizeof(unsigned long long)), "memset"));
+    }
+    m->check = on != 0;
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_missed_pairs(ppmd_md *m, int64_t *missed) {
+    if (!m || !missed) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    *missed = 0;
+    if (!m->missed) return PPMD_OK;
+    cudaSetDevice(ctx->device);
+    unsigned long long h = 0;
+    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(&h, m->missed, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "copy"));
+    const int rc = ppmd_sync(ctx);
+    *missed = (int64_t)h;
+    return rc;
+}
+
+extern "C" int ppmd_md_time_pair_loops(ppmd_md *m, int on) {
+    if (!m) return PPMD_ERR_INVALID;
+    cudaSetDevice(m->ctx->device);
+    drop_graph(m);
+    m->time_pair = on != 0;
+    if (m->time_pair && m->ev.empty()) {
+        const int32_t P = m->p.rebuild_every, unit = P * std::max(1, 10 / P);
+        m->ev.resize(2 * (size_t)std::min(unit, 1024));
+        m->ev_fused.assign(m->ev.size() / 2, 0);
+        for (cudaEvent_t &e : m->ev) PPMD_TRY(cuda_check(m->ctx, cudaEventCreate(&e), "event"));
+    }
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_pair_loop_times(ppmd_md *m, double *ms_fused, int32_t *n_fused, double *ms_other,
+                                       int32_t *n_other) {
+    if (!m) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    if (!m->time_pair || !m->exec)
+        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_pair_loop_times: no timed graph replay yet");
+    cudaSetDevice(ctx->device);
+    PPMD_TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));
+    double sf = 0, so = 0;
+    int32_t nf = 0, no = 0;
+    for (int32_t k = 0; k < m->graph_steps && 2 * k + 1 < (int32_t)m->ev.size(); ++k) {
+        float t = 0.0f;
+        PPMD_TRY(cuda_check(ctx, cudaEventElapsedTime(&t, m->ev[2 * k], m->ev[2 * k + 1]), "event time"));
+        if (m->ev_fused[k]) {
+            sf += t;
+            ++nf;
+        } else {
+            so += t;
+            ++no;
+        }
+    }
+    if (ms_fused) *ms_fused = nf ? sf / nf : 0.0;
+    if (n_fused) *n_fused = nf;
+    if (ms_other) *ms_other = no ? so / no : 0.0;
+    if (n_other) *n_other = no;
+    return PPMD_OK;
 }
 
 extern "C" int ppmd_md_get_q(ppmd_md *m, float *q4, float *q5, float *q6) {

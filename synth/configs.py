@@ -7,7 +7,7 @@ Workloads (LJ units, sigma = epsilon = m = 1, density 0.8442 unless stated):
   lj_small    1000 atoms, sc 10^3, uniform noise +-0.05, T = 1.0, rc = 2.5
   lj_solid    fcc 63^3 cells = 1,000,188 atoms, Gaussian noise 0.02, T = 0.8,
               rc = 2.5, list cutoff 2.8, list rebuilt every 10 steps
-  structure   four 512,000-atom periodic boxes (fcc, bcc, hcp, liquid-like)
+  structure   four 512,000-atom periodic boxes (fcc, bcc, hcp, LJ liquid)
               per noise level sigma in {0.02, 0.05, 0.1} x nearest-neighbour distance
   replicas    256 independent boxes, N log-uniform in [500, 32000],
               density U[0.7, 1.0], T U[0.7, 1.5], jittered sc
@@ -16,6 +16,7 @@ Workloads (LJ units, sigma = epsilon = m = 1, density 0.8442 unless stated):
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -80,24 +81,82 @@ def nn_distance(kind: str, rho: float = RHO) -> float:
     raise ValueError(kind)
 
 
-# Cell counts giving 512,000 atoms for each structure box.
+# Cell counts giving 512,000 atoms for each structure box (for the liquid:
+# simple-cubic sites, i.e. atoms per edge).
 STRUCTURE_CELLS = {"fcc": (80, 80, 20), "bcc": (80, 80, 40), "hcp": (80, 40, 40), "liquid": (80, 80, 80)}
-# Liquid-like box: a simple-cubic lattice with large Gaussian displacements
-# (0.15 per component).  It stands in for an equilibrated LJ liquid snapshot,
-# which would have to be produced by the method under test.
-LIQUID_NOISE = 0.15
+
+# LJ liquid snapshots (density 0.8442, T = 1.5 after 2000 steps), written by
+# the oracle's integrator (oracle/make_liquid.py) and stored with the
+# package: periodic cubes of side^3 atoms, tiled here into larger boxes.
+_DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+_LIQUID_CACHE = {}
+
+
+def liquid_snapshot(side: int, variant: int):
+    """(positions float64 [side^3, 3], box[3]) of snapshot `variant` of a
+    cube of side^3 atoms."""
+    key = (side, variant)
+    if key not in _LIQUID_CACHE:
+        with np.load(os.path.join(_DATA, f"liquid_sc{side}_v{variant}.npz")) as z:
+            _LIQUID_CACHE[key] = (z["pos"].astype(np.float64), np.asarray(z["box"], dtype=np.float64))
+    pos, box = _LIQUID_CACHE[key]
+    return pos.copy(), box.copy()
+
+
+def _away_from_cutoffs(pos, box, cutoffs, rng, margin=1e-6, step=1e-4, max_rounds=50):
+    """Moves, by seeded uniform steps of at most `step` per component, every
+    atom in a pair whose minimum-image distance lies within `margin` of a
+    cutoff, until none is left (pairs found with a periodic k-d tree)."""
+    from scipy.spatial import cKDTree
+    pos = wrap(pos, box)
+    for _ in range(max_rounds):
+        pairs = cKDTree(pos, boxsize=box).query_pairs(max(cutoffs) + margin, output_type="ndarray")
+        if len(pairs) == 0:
+            return pos
+        d = pos[pairs[:, 0]] - pos[pairs[:, 1]]
+        d -= box * np.rint(d / box)
+        r = np.sqrt((d * d).sum(1))
+        bad = np.zeros(len(r), dtype=bool)
+        for c in cutoffs:
+            bad |= np.abs(r - c) < margin
+        if not bad.any():
+            return pos
+        idx = np.unique(pairs[bad].ravel())
+        pos[idx] = wrap(pos[idx] + rng.uniform(-step, step, (len(idx), 3)), box)
+    raise RuntimeError("could not move all pairs away from the cutoffs")
+
+
+def liquid_box(cells, seed: int, cutoffs=()):
+    """An LJ liquid box of cells[0] x cells[1] x cells[2] atoms: copies of a
+    snapshot cube (side 40 when every count is a multiple of 40, else side
+    12), the snapshot chosen by the seed (side 40: (seed // 1000) % 2, so
+    the classifier's training set, seed 50, and its inference set, seed 51,
+    see different liquids; side 12: seed % 4), moved off the cutoffs."""
+    side = 40 if all(c % 40 == 0 for c in cells) else 12
+    if any(c % side for c in cells):
+        raise ValueError(f"liquid box of {cells} atoms per edge is not a tiling of a {side}^3 snapshot")
+    variant = (seed // 1000) % 2 if side == 40 else seed % 4
+    base, edge = liquid_snapshot(side, variant)
+    if cutoffs:
+        base = _away_from_cutoffs(base, edge, cutoffs, rng_stream(seed, 7))
+    reps = [c // side for c in cells]
+    shifts = np.stack(np.meshgrid(*[np.arange(r) for r in reps], indexing="ij"), -1).reshape(-1, 3) * edge
+    pos = (shifts[:, None, :] + base[None, :, :]).reshape(-1, 3)
+    return np.ascontiguousarray(pos), edge * np.asarray(reps, dtype=np.float64)
 
 
 def structure_box(kind: str, sigma_frac: float, seed: int, cells=None):
-    """One structure-analysis box.  `kind` in fcc, bcc, hcp, liquid."""
+    """One structure-analysis box.  `kind` in fcc, bcc, hcp, liquid.  The
+    crystals carry Gaussian noise of sigma_frac times their nearest-neighbour
+    distance; the liquid is an equilibrated LJ liquid (liquid_box; its
+    disorder is thermal, sigma_frac does not apply)."""
     cells = cells if cells is not None else STRUCTURE_CELLS[kind]
-    stream0 = {"fcc": 0, "bcc": 2, "hcp": 4, "liquid": 6}[kind]
     if kind == "liquid":
-        lat = make_lattice("sc", cells, RHO)
-        amp = LIQUID_NOISE
-    else:
-        lat = make_lattice(kind, cells, RHO)
-        amp = sigma_frac * nn_distance(kind)
+        pos, box = liquid_box(cells, seed, cutoffs=(R_BOA, R_CNA))
+        return dict(pos=pos, box=box, kind=kind, sigma=0.0)
+    stream0 = {"fcc": 0, "bcc": 2, "hcp": 4}[kind]
+    lat = make_lattice(kind, cells, RHO)
+    amp = sigma_frac * nn_distance(kind)
     pos, box = jittered(lat, rng_stream(seed, stream0), "gauss", amp, cutoffs=(R_BOA, R_CNA),
                         resample_rng=rng_stream(seed, stream0 + 1))
     return dict(pos=pos, box=box, kind=kind, sigma=amp)

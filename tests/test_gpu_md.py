@@ -558,3 +558,50 @@ def test_otf_q_rows_of_a_crystal_at_rest(L, ctx, golden):
     tab = golden["Q_table"]["fcc"]
     assert np.allclose(q[[4, 9]], [tab["Q4"], tab["Q5"], tab["Q6"]], atol=5e-4)
     assert np.allclose(ql.mean(1), q[9], atol=1e-6)
+
+
+def _oracle_missed(p_old, p_new, box, rc, r_list):
+    """Pairs within rc at p_new that were at least r_list apart at p_old."""
+    offs, nb = oracle.neighbours_cells(p_new, box, rc)
+    i = np.repeat(np.arange(len(p_new)), np.diff(offs))
+    d = p_old[i] - p_old[nb]
+    d -= box * np.rint(d / box)
+    return int((np.sqrt((d ** 2).sum(1)) >= r_list).sum())
+
+
+def test_md_missed_pairs_count_matches_oracle(L, ctx):
+    """A thin skin (list 2.55, rebuilt every 50 steps) on the small sc box:
+    the list-age check counts, at the rebuilds of steps 50 and 100, the
+    pairs within rc that were beyond the list cutoff at the previous build
+    (FP64 run, so the GPU and oracle trajectories agree to ~1e-12)."""
+    c = configs.lj_small()
+    n = len(c["pos"])
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=2.55, rc=2.5, rebuild_every=50, max_nbr=128, prec=L.FP64)
+    md.set_check(True)
+    md.set_state(cu(c["pos"]), cu(c["vel"]))
+    md.run(100)
+    got = md.missed_pairs()
+    md.close()
+    box = c["box"]
+    p0 = oracle.wrap(c["pos"], box)
+    p50, v50, _, _, _ = oracle.md_run(c["pos"], c["vel"], box, 50, r_list=2.55, rebuild_every=50)
+    p100, _, _, _, _ = oracle.md_run(p50, v50, box, 50, r_list=2.55, rebuild_every=50)
+    want = _oracle_missed(p0, p50, box, 2.5, 2.55) + _oracle_missed(p50, p100, box, 2.5, 2.55)
+    assert want > 0 and got == want, (got, want)
+
+
+def test_md_check_leaves_the_trajectory_unchanged(L, ctx):
+    c = configs.lj_solid(n_cells=8)
+    n = len(c["pos"])
+    out = []
+    for check in (False, True):
+        md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP32)
+        md.set_check(check)
+        md.set_state(cu(c["pos"]), cu(c["vel"]))
+        md.run(30)
+        p = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        md.get_state(p)
+        out.append((p.cpu().numpy(), md.missed_pairs()))
+        md.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == 0  # no count without the check

@@ -1,6 +1,7 @@
-"""GPU tests of the brick-staged FP32 integrator path (lists of stage slots,
-pair loop reading its neighbours from shared memory), against the oracle
-and against the atom-index path it replaces.
+"""GPU tests of the brick-staged FP32 pair-loop mechanism of the integrator
+(PPMD_PAIR_BRICKS: lists of stage slots, pair loop reading its neighbours
+from shared memory), against the oracle and against the default
+atom-index mechanism.
 
 - the list of every build holds exactly the oracle's neighbour sets (bit
   for bit), in the same order as the atom-index list of the FP64 path;
@@ -72,9 +73,11 @@ CASES = {
 }
 
 
-def _make(L, ctx, pos, box, r_list, every, prec):
+def _make(L, ctx, pos, box, r_list, every, prec, bricks=True):
     n = len(pos)
     md = L.MD(ctx, [0, n], [box], r_list=r_list, rc=2.5, rebuild_every=every, max_nbr=128, prec=prec)
+    if bricks and prec == L.FP32:
+        md.set_pair_loop(L.PAIR_BRICKS)
     md.set_state(cu(pos), cu(np.zeros((n, 3))))
     return md
 
@@ -115,9 +118,7 @@ def test_slot_list_order_equals_atom_index_list(L, ctx, case):
 def _run(L, ctx, c, slots, nsteps, use_graph=True):
     n = len(c["pos"])
     md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP32)
-    if not slots:  # the analysis switches the integrator to atom-index lists for good
-        md.set_boa(1, 1.5)
-        md.set_boa(0, 1.5)
+    md.set_pair_loop(L.PAIR_BRICKS if slots else L.PAIR_COLUMNS)
     md.set_state(cu(c["pos"]), cu(c["vel"]))
     md.run(nsteps, use_graph=use_graph)
     out = [torch.empty((n, 3), dtype=torch.float64, device="cuda") for _ in range(3)]
@@ -147,6 +148,7 @@ def test_set_boa_mid_period_converts_the_list(L, ctx):
     po, vo, Fo, eno, qo, qlo, _ = oracle.md_run_otf(c["pos"], c["vel"], c["box"], 15, r_list=2.8, rebuild_every=10,
                                                     boa=(1, 1.5))
     md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP32)
+    md.set_pair_loop(L.PAIR_BRICKS)
     md.set_state(cu(c["pos"]), cu(c["vel"]))
     md.run(5)
     md.set_boa(1, 1.5)
@@ -161,3 +163,34 @@ def test_set_boa_mid_period_converts_the_list(L, ctx):
     assert np.abs(d).max() <= 1e-8 * c["box"][0]
     assert np.abs(q.cpu().numpy() - qo[5:15]).max() <= 1e-5
     assert np.abs(ql - qlo).max() <= 1e-5
+
+
+def test_pair_loop_mechanism_is_chosen_before_set_state(L, ctx):
+    c = configs.lj_solid(n_cells=6)
+    n = len(c["pos"])
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP64)
+    with pytest.raises(L.PPMDError):  # bricks need FP32
+        md.set_pair_loop(L.PAIR_BRICKS)
+    md.close()
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP32)
+    md.set_state(cu(c["pos"]), cu(c["vel"]))
+    with pytest.raises(L.PPMDError):
+        md.set_pair_loop(L.PAIR_BRICKS)
+    md.close()
+
+
+def test_pair_loop_event_times(L, ctx):
+    """The measurement aid: event-record nodes around the pair loops of a
+    replayed graph give positive durations: per 10-step unit, nine pair
+    loops fused with the next step's kick and drift and one other (the
+    unit's last step, here also the energy step)."""
+    c = configs.lj_solid(n_cells=10)
+    n = len(c["pos"])
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP32,
+              energy_every=10)
+    md.time_pair_loops(True)
+    md.set_state(cu(c["pos"]), cu(c["vel"]))
+    md.run(20)
+    tf, nf, to, no = md.pair_loop_times()
+    assert nf == 9 and no == 1 and tf > 0 and to > 0, (tf, nf, to, no)
+    md.close()

@@ -288,3 +288,20 @@ def test_otf_q_rows_of_a_crystal_at_rest(golden):
         assert np.allclose(qrows[s], [tab["Q4"], tab["Q5"], tab["Q6"]], atol=5e-4)
     assert (qrows[[0, 2, 4]] == 0).all()
     assert np.allclose(qlast.mean(1), qrows[5], rtol=1e-13, atol=1e-15)
+
+
+def test_md_run_same_on_any_thread_count():
+    """The oracle's per-atom loops on several threads (the all-core CPU
+    baseline) give the one-thread run bit for bit: every reduction over atoms
+    is taken in atom order."""
+    c = configs.lj_solid(n_cells=7)
+    runs = []
+    for k in (1, 3):
+        oracle.set_threads(k)
+        try:
+            runs.append(oracle.md_run(c["pos"], c["vel"], c["box"], 12, r_list=2.8, rebuild_every=10))
+        finally:
+            oracle.set_threads(1)
+    for a, b in zip(runs[0][:4], runs[1][:4]):
+        assert np.array_equal(a, b)
+    assert runs[0][4] == runs[1][4]

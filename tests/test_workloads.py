@@ -40,3 +40,30 @@ def test_structure_box_size_and_determinism():
     b = configs.lj_solid(n_cells=6)
     c = configs.lj_solid(n_cells=6)
     assert np.array_equal(b["pos"], c["pos"]) and np.array_equal(b["vel"], c["vel"])
+
+
+def test_liquid_boxes_are_tiled_equilibrated_snapshots():
+    """The liquid boxes: copies of an LJ liquid snapshot (the oracle's run at
+    density 0.8442, T 1.5; oracle/make_liquid.py) at the boxes' sizes, at the
+    workload density, with no pair within 1e-6 of the analysis cutoffs; the
+    classifier's training and inference sets see different snapshots."""
+    from synth.configs import R_BOA, R_CNA
+    a = configs.structure_box("liquid", 0.05, seed=30)
+    assert len(a["pos"]) == 512000
+    assert np.isclose(len(a["pos"]) / np.prod(a["box"]), 0.8442, rtol=1e-12)
+    tr = configs.structure_box("liquid", 0.05, seed=50003, cells=configs.CLASSIFIER_CELLS["liquid"])
+    te = configs.structure_box("liquid", 0.05, seed=51003, cells=configs.CLASSIFIER_CELLS["liquid"])
+    assert len(tr["pos"]) == len(te["pos"]) == 128000
+    assert not np.array_equal(tr["pos"], te["pos"])
+    s = configs.structure_box("liquid", 0.0, seed=41, cells=(12, 12, 12))
+    assert len(s["pos"]) == 1728
+    from synth.lattices import min_pair_margin
+    assert min_pair_margin(s["pos"], s["box"], (R_BOA, R_CNA)) >= 1e-6
+    # a liquid: no long-range order, so no lattice site holds an atom for
+    # long; the nearest-neighbour distances spread well beyond a crystal's
+    d = s["pos"][:, None, :] - s["pos"][None, :, :]
+    d -= s["box"] * np.rint(d / s["box"])
+    r = np.sqrt((d ** 2).sum(-1))
+    np.fill_diagonal(r, np.inf)
+    nn = r.min(1)
+    assert nn.std() > 0.03 and 0.85 < nn.mean() < 1.15
