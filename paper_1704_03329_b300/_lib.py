@@ -475,7 +475,10 @@ class MD:
 
     def close(self):
         if getattr(self, "h", None):
-            _lib.ppmd_md_destroy(self.h)
+            # a context destroyed first (objects collected together at exit)
+            # has taken the device state with it: nothing left to release
+            if getattr(self.ctx, "h", None):
+                _lib.ppmd_md_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -19,6 +19,7 @@ int set_error(ppmd_ctx *ctx, int code, const char *fmt, ...) {
 
 int cuda_check(ppmd_ctx *ctx, cudaError_t e, const char *what) {
     if (e == cudaSuccess) return PPMD_OK;
+    cudaGetLastError();  // reported here: not again by the next unrelated check
     return set_error(ctx, PPMD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 

@@ -479,10 +479,14 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow =
     // stay in the other buffer (prev) for the thermostat and the analysis
     const bool fused = fuse_next && f32;
     const bool timed = m->time_pair && base && s >= 1 && 2 * s <= (int64_t)m->ev.size();
-    if (timed) PPMD_TRY(cuda_check(ctx, cudaEventRecord(m->ev[2 * (s - 1)], ctx->stream), "event"));
+    // during stream capture, only an external record becomes an event-record node
+    if (timed)
+        PPMD_TRY(cuda_check(ctx, cudaEventRecordWithFlags(m->ev[2 * (s - 1)], ctx->stream, cudaEventRecordExternal),
+                            "event"));
     PPMD_TRY(forces(m, energy, true, fused));
     if (timed) {
-        PPMD_TRY(cuda_check(ctx, cudaEventRecord(m->ev[2 * (s - 1) + 1], ctx->stream), "event"));
+        PPMD_TRY(cuda_check(ctx, cudaEventRecordWithFlags(m->ev[2 * (s - 1) + 1], ctx->stream, cudaEventRecordExternal),
+                            "event"));
         m->ev_fused[s - 1] = fused ? 1 : 0;
     }
     const int prev = fused ? m->cur ^ 1 : m->cur;

@@ -123,29 +123,47 @@ __device__ __forceinline__ int32_t wrapi(int32_t v, int32_t n) { return v < 0 ? 
 // Signed minimum-image difference of two fixed-point words, as a float.
 __device__ __forceinline__ float fdiff(int32_t a, int32_t b) { return __int2float_rn((int32_t)((uint32_t)a - (uint32_t)b)); }
 
-// One block per brick.  The neighbourhood's fixed-point positions are staged
-// in shared memory (rows of consecutive cells are contiguous in the sorted
-// order, up to the periodic wrap in x).  Each thread owns one home atom and
-// sweeps its 27 cells (three cells in each of nine staged rows), testing
-// two candidates per packed step; threads of the same cell read the same
-// candidate, so the shared-memory reads are broadcasts.  Hits go straight
-// to the atom's column of W.
+// List build (Sec. 3.5: the 27 cells around each atom's cell), one block per
+// brick of cells.  The brick's neighbourhood (its cells and one cell more on
+// every side) is staged in shared memory as (bh + 2)(bd + 2) x-rows of
+// bw + 2 consecutive cells: a row of the sorted order is contiguous up to the periodic wrap in
+// x, so each staged row maps back to the sorted order by one or two offsets.
+// Each home atom's candidates are the nine rows around its cell, three cells
+// of each; the output order is, per atom, the nine rows in order and in each
+// row the candidates in stage order (in the sorted order, x-ordered within a
+// cell).
+// A warp takes a cluster of up to CL atoms of one home cell (consecutive,
+// so ordered by x) and walks the candidates of the cluster's window in each
+// row (the union of its atoms' x-windows) 32 at a time, one per lane; each
+// candidate is tested against every atom of the cluster (two atoms per
+// packed instruction), and each atom's hits are compacted with one ballot,
+// in stage order.  A candidate load and its bookkeeping serve CL atoms.
+constexpr int CL = 8;
+constexpr int MAX_CLUSTERS = 256;
+
 template <bool VEC4>
-__global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
-                                                               const int4 *__restrict__ xq,
-                                                               const double *__restrict__ pos64, SegTable st,
-                                                               const int32_t *__restrict__ cs, int32_t *__restrict__ W,
-                                                               int64_t ld, int32_t *__restrict__ cnt, int32_t max_nbr,
-                                                               int32_t stage_cap, int32_t *status,
-                                                               unsigned long long *needed) {
+__device__ __forceinline__ void put_entry(int32_t *W, int64_t ld, int64_t i, int32_t e, int32_t j) {
+    if (VEC4) W[(((int64_t)(e >> 2) * ld + i) << 2) + (e & 3)] = j;
+    else W[(int64_t)e * ld + i] = j;
+}
+
+template <bool VEC4>
+__global__ void __launch_bounds__(BRICK_THREADS, 4) k_neigh_cluster(const Brick *__restrict__ bricks, BrickShape shape,
+                                                                const int4 *__restrict__ xq,
+                                                                const double *__restrict__ pos64, SegTable st,
+                                                                const int32_t *__restrict__ cs, int32_t *__restrict__ W,
+                                                                int64_t ld, int32_t *__restrict__ cnt, int32_t max_nbr,
+                                                                int32_t stage_cap, int32_t *status,
+                                                                unsigned long long *needed) {
     constexpr int NROW = (BH_MAX + 2) * (BD_MAX + 2), NHOME = BH_MAX * BD_MAX;
     extern __shared__ __align__(16) unsigned char smem[];
     int4 *s_x = (int4 *)smem;
-    __shared__ int32_t s_cell[NROW][BW_MAX + 3];  // start of the row's cells t = 0 .. bw+2 in the stage
-    __shared__ int32_t s_da[NROW], s_db[NROW], s_sw[NROW];  // global = local + (local < sw ? da : db)
-    __shared__ int32_t s_home[NHOME][BW_MAX + 1];  // cell starts of the home cells of each home row
-    __shared__ int32_t s_hoff[32];                 // first home index of each home row (then H)
-    __shared__ int32_t s_total;
+    __shared__ int32_t s_cell[NROW][BW_MAX + 3];
+    __shared__ int32_t s_da[NROW], s_db[NROW], s_sw[NROW];
+    __shared__ int32_t s_home[NHOME][BW_MAX + 1];
+    __shared__ int32_t s_hoff[32];
+    __shared__ int32_t s_total, s_ncl;
+    __shared__ int2 s_cl[MAX_CLUSTERS];  // (first atom (sorted index), size | home row << 8 | home cell << 16)
 
     Brick B;
     if (bricks) {
@@ -166,7 +184,7 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
     const int32_t x0 = B.x01 & 0xffff, x1 = B.x01 >> 16, y0 = B.y01 & 0xffff, y1 = B.y01 >> 16;
     const int32_t z0 = B.z01 & 0xffff, z1 = B.z01 >> 16;
     const int32_t bw = x1 - x0, bh = y1 - y0, bd = z1 - z0, nyr = bh + 2, nrow = nyr * (bd + 2), nhome = bh * bd;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 32) {
         // warp 0: the staged rows, their cell offsets and their mapping back
         // to the sorted order
@@ -181,9 +199,8 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
             }
             s_cell[tid][bw + 2] = tot;
         }
-        // each staged row is followed by ROW_GAP slots (far-away sentinels
-        // in the FP32 stage), so that candidate reads may run past a row's
-        // end without bounds tests
+        // each staged row is followed by ROW_GAP far-away sentinels, so that
+        // candidate reads may run past a row's end without bounds tests
         const int32_t span = tid < nrow ? tot + ROW_GAP : 0;
         int32_t inc = span;
 #pragma unroll
@@ -194,13 +211,13 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
         const int32_t base = inc - span;
         if (tid < nrow) {
             for (int t = 0; t <= bw + 2; ++t) s_cell[tid][t] += base;
-            const int32_t xa = x0 - 1, xb = x1;  // inclusive cell range of the row
-            if (xa < 0) {  // cell nx-1 first, then cells 0 .. xb
+            const int32_t xa = x0 - 1, xb = x1;
+            if (xa < 0) {
                 const int32_t len1 = cs[rb + nx] - cs[rb + nx - 1];
                 s_da[tid] = cs[rb + nx - 1] - base;
                 s_sw[tid] = base + len1;
                 s_db[tid] = cs[rb] - (base + len1);
-            } else if (xb >= nx) {  // cells xa .. nx-1, then cell 0
+            } else if (xb >= nx) {
                 const int32_t len1 = cs[rb + nx] - cs[rb + xa];
                 s_da[tid] = cs[rb + xa] - base;
                 s_sw[tid] = base + len1;
@@ -213,7 +230,7 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
         }
         if (tid == 31) s_total = inc;
     } else if (tid < 64) {
-        // warp 1: the home rows (home row l is row l % bh, plane l / bh)
+        // warp 1: the home rows, then (lane 0) the clusters
         const int l = lane;
         int32_t c = 0;
         if (l < nhome) {
@@ -227,170 +244,196 @@ __global__ void __launch_bounds__(BRICK_THREADS, 7) k_neigh_brick(const Brick *_
             const int32_t v = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += v;
         }
-        s_hoff[l] = inc - c;  // rows past nhome hold H
+        s_hoff[l] = inc - c;
+        __syncwarp();
+        if (l == 0) {
+            int32_t k = 0;
+            for (int hr = 0; hr < nhome; ++hr)
+                for (int t = 0; t < bw; ++t)
+                    for (int32_t a = s_home[hr][t]; a < s_home[hr][t + 1]; a += CL) {
+                        const int32_t sz = min(CL, s_home[hr][t + 1] - a);
+                        if (k < MAX_CLUSTERS) s_cl[k] = make_int2(a, sz | (hr << 8) | (t << 16));
+                        ++k;
+                    }
+            s_ncl = k;
+        }
     }
     __syncthreads();
-    const int32_t T = s_total;
-    const int32_t H = s_hoff[nhome];
+    const int32_t T = s_total, ncl = s_ncl;
+    if (ncl > MAX_CLUSTERS) {  // more home atoms than the cluster table holds (a brick far denser than planned)
+        if (tid == 0) {
+            latch_status(status, PPMD_ERR_CAPACITY);
+            latch_needed(needed, (unsigned long long)max_nbr + 1);
+        }
+        for (int hr = 0; hr < nhome; ++hr)
+            for (int32_t a = s_home[hr][0] + tid; a < s_home[hr][bw]; a += blockDim.x) cnt[a] = 0;
+        return;
+    }
     // a neighbourhood larger than the shared-memory stage is read from global
     // memory instead (same indices, slower)
     const bool staged = T <= stage_cap;
     // Where the neighbourhood leaves at least one cell of the periodic grid
     // outside it in every direction, positions are staged as FP32 offsets
     // from its centre (the signed fixed-point difference is then the
-    // periodic image seen from the brick) with the atom index in .w, so the
-    // candidate tests need no integer work.  Rounding: each offset is within
-    // 2^-23 of its value (at most 5 cells), which moves r^2 by less than
-    // 1e-5 r^2, inside the FP64 re-test band.
+    // periodic image seen from the brick), so the candidate tests need no
+    // integer work.  Rounding: each offset is within 2^-23 of its value (at
+    // most 5 cells), which moves r^2 by less than 1e-5 r^2, inside the FP64
+    // re-test band.  The centre needs no precision.
     const bool fstage = staged && bw + 3 <= nx && bh + 3 <= ny && bd + 3 <= nz;
-    // the centre needs no precision: any point within a cell of it serves
     const uint32_t refx = (uint32_t)__float2ull_rz((x0 - 1 + 0.5f * (bw + 2)) / (float)nx * 4294967296.0f);
     const uint32_t refy = (uint32_t)__float2ull_rz((y0 - 1 + 0.5f * (bh + 2)) / (float)ny * 4294967296.0f);
     const uint32_t refz = (uint32_t)__float2ull_rz((z0 - 1 + 0.5f * (bd + 2)) / (float)nz * 4294967296.0f);
-    const float sx = S.sx[0], sy = S.sx[1], sz = S.sx[2];
-    auto rel = [&](const int4 q, int32_t j) {
+    const float sx = S.sx[0], sy = S.sx[1], sz_ = S.sx[2];
+    auto rel = [&](const int4 q) {
         return make_float4((float)(int32_t)((uint32_t)q.x - refx) * sx, (float)(int32_t)((uint32_t)q.y - refy) * sy,
-                           (float)(int32_t)((uint32_t)q.z - refz) * sz, __int_as_float(j));
+                           (float)(int32_t)((uint32_t)q.z - refz) * sz_, 0.0f);
     };
+    float4 *s_f = (float4 *)smem;
     if (staged) {
-        float4 *s_f = (float4 *)smem;
         for (int32_t t = tid; t < T; t += blockDim.x) {
-            int r = 0, rh = nrow - 1;  // the last row starting at or before t
+            int r = 0, rh = nrow - 1;
             while (r < rh) {
                 const int mid = (r + rh + 1) >> 1;
                 if (s_cell[mid][0] <= t) r = mid;
                 else rh = mid - 1;
             }
-            if (t >= s_cell[r][bw + 2]) {  // a row's sentinel slot
-                if (fstage) s_f[t] = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-1));
+            if (t >= s_cell[r][bw + 2]) {
+                if (fstage) s_f[t] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
                 continue;
             }
-            const int32_t j = t + (t < s_sw[r] ? s_da[r] : s_db[r]);
-            if (fstage) s_f[t] = rel(xq[j], j);
-            else s_x[t] = xq[j];
+            const int4 q = xq[t + (t < s_sw[r] ? s_da[r] : s_db[r])];
+            if (fstage) s_f[t] = rel(q);
+            else s_x[t] = q;
         }
     }
     __syncthreads();
-    const f2_t sxx = pk(sx, sx), syy = pk(sy, sy), szz = pk(sz, sz);
     const float lo = S.rl2_lo, hi = S.rl2_hi;
-    for (int32_t h = tid; h < H; h += blockDim.x) {
-        int hr = 0;  // the last home row starting at or before h
-        while (hr + 1 < nhome && s_hoff[hr + 1] <= h) ++hr;
-        const int32_t i = s_home[hr][0] + (h - s_hoff[hr]);
+    const float rwin = sqrtf((float)S.rl2) * 1.00001f + 1e-5f;
+    const unsigned lt = (1u << lane) - 1u;
+    // position of candidate slot k (stage, or the sorted arrays when the
+    // neighbourhood was too large to stage), as an offset usable against the
+    // cluster's atoms: FP32 offsets from the centre, or fixed-point words
+    auto cand_f = [&](int32_t k) { return s_f[k]; };
+    auto cand_q = [&](int32_t k, int r) {
+        return staged ? s_x[k] : xq[k + (k < s_sw[r] ? s_da[r] : s_db[r])];
+    };
+    for (int32_t cl = warp; cl < ncl; cl += BRICK_THREADS / 32) {
+        const int2 ce = s_cl[cl];
+        const int32_t i0 = ce.x, nat = ce.y & 0xff, hr = (ce.y >> 8) & 0xff, t = ce.y >> 16;
         const int32_t hy = hr % bh, hz = hr / bh;
-        const int4 xi = xq[i];
-        int t = 0;
-        while (t + 1 < bw && i >= s_home[hr][t + 1]) ++t;
-        int32_t count = 0;
-        int32_t *col = W + i;
-        // VEC4: the row is stored as groups of four entries (one 16-byte word
-        // per group, W4[g * ld + i]), collected in a shift register
-        int4 grp = make_int4(-1, -1, -1, -1);
-        int4 *col4 = reinterpret_cast<int4 *>(W) + i;
-        auto hit = [&](int32_t j) {
-            if (VEC4) {
-                grp = make_int4(grp.y, grp.z, grp.w, j);
-                if ((count & 3) == 3 && count < max_nbr) col4[(int64_t)(count >> 2) * ld] = grp;
-            } else if (count < max_nbr) {
-                col[(int64_t)count * ld] = j;
-            }
-            ++count;
-        };
-        if (fstage) {
-            const float4 fi = rel(xi, i);
-            const float4 *s_f = (const float4 *)smem;
-            const f2_t xii = pk(fi.x, fi.x), yii = pk(fi.y, fi.y), zii = pk(fi.z, fi.z);
-            // atoms are ordered by x within each cell, so a row of three cells
-            // is ordered by x: only the window |dx| < r_list (widened far
-            // beyond the FP32 error of the offsets) can hold hits
-            const float rwin = sqrtf((float)S.rl2) * 1.00001f + 1e-5f, xlo = fi.x - rwin, xhi = fi.x + rwin;
-            for (int dz = 0; dz < 3; ++dz)
-                for (int dy = 0; dy < 3; ++dy) {
-                    const int r = (hz + dz) * nyr + hy + dy;
-                    const int32_t b = s_cell[r][t + 3];
-                    int32_t a = s_cell[r][t];
-                    for (int32_t hi2 = b; a < hi2;) {  // first candidate with x >= xlo
-                        const int32_t mid = (a + hi2) >> 1;
-                        if (s_f[mid].x < xlo) a = mid + 1;
-                        else hi2 = mid;
-                    }
-                    // four candidates per pass (two packed pairs), tested in
-                    // order until one starts beyond the window; reads past b
-                    // find either atoms of cells two or more cells away from
-                    // the home cell (farther than the cell edge, so never a
-                    // hit) or the row's sentinels
-                    for (int32_t k = a; k < b; k += 4) {
-                        const float4 f0 = s_f[k], f1 = s_f[k + 1], f2 = s_f[k + 2], f3 = s_f[k + 3];
-                        if (f0.x > xhi) break;
-                        const f2_t dx0 = sub2(xii, pk(f0.x, f1.x)), dx1 = sub2(xii, pk(f2.x, f3.x));
-                        const f2_t dy0 = sub2(yii, pk(f0.y, f1.y)), dy1 = sub2(yii, pk(f2.y, f3.y));
-                        const f2_t dz0 = sub2(zii, pk(f0.z, f1.z)), dz1 = sub2(zii, pk(f2.z, f3.z));
-                        float r2v[4];
-                        upk(fma2(dx0, dx0, fma2(dy0, dy0, mul2(dz0, dz0))), r2v[0], r2v[1]);
-                        upk(fma2(dx1, dx1, fma2(dy1, dy1, mul2(dz1, dz1))), r2v[2], r2v[3]);
-                        const int32_t jv[4] = {__float_as_int(f0.w), __float_as_int(f1.w), __float_as_int(f2.w),
-                                               __float_as_int(f3.w)};
+        const int32_t rself = (hz + 1) * nyr + hy + 1;
+        const int32_t self0 = s_cell[rself][t + 1] + (i0 - s_home[hr][t]);
+        // the cluster's atoms in registers (atoms past nat: far away, never hit)
+        float ax[CL], ay[CL], az[CL];
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            if (r2v[q] < hi && jv[q] != i) {
-                                double dr[3];
-                                if (r2v[q] < lo ||
-                                    min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jv[q], S, dr) < S.rl2)
-                                    hit(jv[q]);
-                            }
+        for (int a = 0; a < CL; ++a) {
+            const float4 f = (fstage && a < nat) ? s_f[self0 + a] : make_float4(3e18f, 3e18f, 3e18f, 0.0f);
+            ax[a] = f.x;
+            ay[a] = f.y;
+            az[a] = f.z;
+        }
+        float xmax = ax[0];
+#pragma unroll
+        for (int a = 1; a < CL; ++a)
+            if (a < nat) xmax = fmaxf(xmax, ax[a]);
+        const float xlo = fstage ? ax[0] - rwin : 0.0f, xhi = fstage ? xmax + rwin : 0.0f;
+        // the nine row windows: lane q finds row q's lower end, lane 16 + q its upper end
+        int32_t wend = 0;
+        {
+            const int q = lane & 15;
+            if (q < 9) {
+                const int r = (hz + q / 3) * nyr + hy + q % 3;
+                int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
+                if (fstage) {
+                    if (lane < 16) {
+                        while (a < b) {
+                            const int32_t mid = (a + b) >> 1;
+                            if (s_f[mid].x < xlo) a = mid + 1;
+                            else b = mid;
+                        }
+                    } else {
+                        while (a < b) {
+                            const int32_t mid = (a + b) >> 1;
+                            if (s_f[mid].x <= xhi) a = mid + 1;
+                            else b = mid;
                         }
                     }
                 }
-        } else
-        for (int dz = 0; dz < 3; ++dz)
-            for (int dy = 0; dy < 3; ++dy) {
-                const int r = (hz + dz) * nyr + hy + dy;
-                const int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
-                const int32_t sw = s_sw[r], da = s_da[r], db = s_db[r];
-                for (int32_t k = a; k < b; k += 2) {
-                    const bool v1 = k + 1 < b;
-                    const int32_t kb = v1 ? k + 1 : k;
-                    const int4 xa = staged ? s_x[k] : xq[k + (k < sw ? da : db)];
-                    const int4 xb = staged ? s_x[kb] : xq[kb + (kb < sw ? da : db)];
-                    const f2_t dx = mul2(pk(fdiff(xi.x, xa.x), fdiff(xi.x, xb.x)), sxx);
-                    const f2_t dy_ = mul2(pk(fdiff(xi.y, xa.y), fdiff(xi.y, xb.y)), syy);
-                    const f2_t dz_ = mul2(pk(fdiff(xi.z, xa.z), fdiff(xi.z, xb.z)), szz);
-                    const f2_t r2 = fma2(dx, dx, fma2(dy_, dy_, mul2(dz_, dz_)));
-                    float ra, rb2;
-                    upk(r2, ra, rb2);
-                    const int32_t ja = k + (k < sw ? da : db);
-                    const int32_t jb = k + 1 + (k + 1 < sw ? da : db);
-                    if (ra < hi && ja != i) {
-                        double dr[3];
-                        if (ra < lo || min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)ja, S, dr) < S.rl2) hit(ja);
+                wend = lane < 16 ? a : (fstage ? a : b);
+            }
+        }
+        int32_t count[CL];
+#pragma unroll
+        for (int a = 0; a < CL; ++a) count[a] = 0;
+        for (int q = 0; q < 9; ++q) {
+            const int32_t wa = __shfl_sync(0xffffffffu, wend, q), wb = __shfl_sync(0xffffffffu, wend, 16 + q);
+            const int r = (hz + q / 3) * nyr + hy + q % 3;
+            const int32_t sw = s_sw[r], da = s_da[r], db = s_db[r];
+            for (int32_t k0 = wa; k0 < wb; k0 += 32) {
+                const int32_t k = k0 + lane;
+                const bool valid = k < wb;
+                const int32_t kk = valid ? k : wa;
+                const int32_t j = kk + (kk < sw ? da : db);
+                float r2[CL];
+                if (fstage) {
+                    const float4 f = cand_f(kk);
+                    const f2 xx = pk(f.x, f.x), yy = pk(f.y, f.y), zz = pk(f.z, f.z);
+#pragma unroll
+                    for (int a = 0; a < CL; a += 2) {
+                        const f2 dx = sub2(pk(ax[a], ax[a + 1]), xx), dy = sub2(pk(ay[a], ay[a + 1]), yy),
+                                 dz = sub2(pk(az[a], az[a + 1]), zz);
+                        upk(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), r2[a], r2[a + 1]);
                     }
-                    if (v1 && rb2 < hi && jb != i) {
+                } else {
+                    // small grids (the neighbourhood wraps onto itself):
+                    // fixed-point differences, the cluster's words re-read
+                    const int4 qc = cand_q(kk, r);
+#pragma unroll
+                    for (int a = 0; a < CL; ++a) {
+                        const int4 qa = xq[i0 + min(a, nat - 1)];
+                        const float dx = fdiff(qa.x, qc.x) * sx, dy = fdiff(qa.y, qc.y) * sy, dz = fdiff(qa.z, qc.z) * sz_;
+                        r2[a] = a < nat ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : 3e38f;
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < CL; ++a) {
+                    bool hit = valid && r2[a] < hi && kk != self0 + a;
+                    if (hit && !(r2[a] < lo)) {
                         double dr[3];
-                        if (rb2 < lo || min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jb, S, dr) < S.rl2) hit(jb);
+                        hit = min_image_r2(pos64 + 3 * (int64_t)(i0 + a), pos64 + 3 * (int64_t)j, S, dr) < S.rl2;
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (m) {
+                        const int32_t e = count[a] + __popc(m & lt);
+                        if (hit && e < max_nbr) put_entry<VEC4>(W, ld, i0 + a, e, j);
+                        count[a] += __popc(m);
                     }
                 }
             }
-        if (VEC4 && (count & 3) != 0 && count < max_nbr) {
-            // the last, partial group, padded with -1
-            for (int q = count & 3; q < 4; ++q) grp = make_int4(grp.y, grp.z, grp.w, -1);
-            col4[(int64_t)(count >> 2) * ld] = grp;
         }
-        cnt[i] = count;
-        if (count > max_nbr) {
-            latch_status(status, PPMD_ERR_CAPACITY);
-            latch_needed(needed, (unsigned long long)count);
+        // counts, capacity and (grouped layout) the last group's padding
+#pragma unroll
+        for (int a = 0; a < CL; ++a) {
+            if (a < nat && lane == a) {
+                cnt[i0 + a] = count[a];
+                if (count[a] > max_nbr) {
+                    latch_status(status, PPMD_ERR_CAPACITY);
+                    latch_needed(needed, (unsigned long long)count[a]);
+                }
+                if (VEC4)
+                    for (int32_t e = count[a]; e < ((count[a] + 3) & ~3) && e < max_nbr; ++e) put_entry<VEC4>(W, ld, i0 + a, e, -1);
+            }
         }
     }
 }
 
 int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr) {
-    int rc = cuda_check(ctx, cudaFuncSetAttribute(k_neigh_brick<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)neigh_brick_smem(max_nbr)),
-                        "cudaFuncSetAttribute");
-    if (rc == PPMD_OK)
-        rc = cuda_check(ctx, cudaFuncSetAttribute(k_neigh_brick<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)neigh_brick_smem(max_nbr)),
-                        "cudaFuncSetAttribute");
+    int rc = PPMD_OK;
+    for (const void *f : {(const void *)k_neigh_cluster<false>, (const void *)k_neigh_cluster<true>})
+        if (rc == PPMD_OK)
+            rc = cuda_check(ctx, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)neigh_brick_smem(max_nbr)),
+                            "cudaFuncSetAttribute");
     return rc;
 }
 
@@ -400,7 +443,7 @@ int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, Brick
     if (stage_cap <= 0 || stage_cap > NB_MAX) stage_cap = NB_MAX;
     if (vec4 && (max_nbr & 3)) return set_error(ctx, PPMD_ERR_INVALID, "grouped list needs a capacity divisible by 4");
     if (nbricks > 0) {
-        auto kern = vec4 ? k_neigh_brick<true> : k_neigh_brick<false>;
+        auto kern = vec4 ? k_neigh_cluster<true> : k_neigh_cluster<false>;
         PPMD_LAUNCH(ctx, kern, nbricks, BRICK_THREADS, (size_t)stage_cap * sizeof(int4), bricks, shape, xq, pos64, st,
                     cell_start, W, ld, cnt, max_nbr, stage_cap, ctx->d_status, ctx->d_needed);
     }

@@ -83,10 +83,12 @@ def _make(L, ctx, pos, box, r_list, every, prec, bricks=True):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-def test_slot_list_sets_and_forces(L, ctx, case):
+@pytest.mark.parametrize("bricks", [True, False])
+def test_slot_list_sets_and_forces(L, ctx, case, bricks):
+    """Both mechanisms' list builds hold exactly the oracle's sets."""
     c, r_list, every = CASES[case]()
     pos, box = oracle.wrap(c["pos"], c["box"]), np.asarray(c["box"], float)
-    md = _make(L, ctx, pos, box, r_list, every, L.FP32)
+    md = _make(L, ctx, pos, box, r_list, every, L.FP32, bricks=bricks)
     nbr, cnt = md.get_list()
     F = torch.empty((len(pos), 3), dtype=torch.float64, device="cuda")
     md.get_state(None, None, F)
