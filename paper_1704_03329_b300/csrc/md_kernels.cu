@@ -73,7 +73,7 @@ BrickShape brick_shape(const Seg &S) {
             for (int32_t bw = 1; bw <= mw; ++bw) {
                 const double cells = (double)bw * bh * bd, hood = (double)(bw + 2) * (bh + 2) * (bd + 2);
                 const double home = pc * cells;
-                if (1.5 * pc * hood + ROW_GAP * (bh + 2) * (bd + 2) > NB_MAX || home > BRICK_THREADS) continue;
+                if (1.5 * pc * hood + (ROW_GAP + 1) * (bh + 2) * (bd + 2) > NB_MAX || home > BRICK_THREADS) continue;
                 const double halo = hood / cells;
                 if (home > best_home * (1.0 + 1e-9) || (home >= best_home * (1.0 - 1e-9) && halo < best_halo)) {
                     best = BrickShape{bw, bh, bd};
@@ -113,7 +113,7 @@ size_t neigh_brick_smem(int32_t) { return (size_t)NB_MAX * sizeof(int4); }
 // sparse grids leave room for more resident blocks.
 int32_t brick_stage_cap(const Seg &S, BrickShape b) {
     const double pc = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
-    const double need = 1.5 * pc * (b.bw + 2) * (b.bh + 2) * (b.bd + 2) + ROW_GAP * (b.bh + 2) * (b.bd + 2);
+    const double need = 1.5 * pc * (b.bw + 2) * (b.bh + 2) * (b.bd + 2) + (ROW_GAP + 1) * (b.bh + 2) * (b.bd + 2);
     const int64_t cap = ((int64_t)ceil(need) + 63) / 64 * 64;
     return (int32_t)std::max<int64_t>(64, std::min<int64_t>(NB_MAX, cap));
 }
@@ -126,20 +126,38 @@ __device__ __forceinline__ float fdiff(int32_t a, int32_t b) { return __int2floa
 // List build (Sec. 3.5: the 27 cells around each atom's cell), one block per
 // brick of cells.  The brick's neighbourhood (its cells and one cell more on
 // every side) is staged in shared memory as (bh + 2)(bd + 2) x-rows of
-// bw + 2 consecutive cells: a row of the sorted order is contiguous up to the periodic wrap in
-// x, so each staged row maps back to the sorted order by one or two offsets.
-// Each home atom's candidates are the nine rows around its cell, three cells
-// of each; the output order is, per atom, the nine rows in order and in each
-// row the candidates in stage order (in the sorted order, x-ordered within a
-// cell).
-// A warp takes a cluster of up to CL atoms of one home cell (consecutive,
-// so ordered by x) and walks the candidates of the cluster's window in each
-// row (the union of its atoms' x-windows) 32 at a time, one per lane; each
-// candidate is tested against every atom of the cluster (two atoms per
-// packed instruction), and each atom's hits are compacted with one ballot,
-// in stage order.  A candidate load and its bookkeeping serve CL atoms.
-constexpr int CL = 8;
-constexpr int MAX_CLUSTERS = 256;
+// bw + 2 consecutive cells: a row of the sorted order is contiguous up to the
+// periodic wrap in x, so each staged row maps back to the sorted order by one
+// or two offsets.  Each home atom's candidates are the nine rows around its
+// cell, three cells of each; the output order is, per atom, the nine rows in
+// order and in each row the candidates in stage order (the sorted order,
+// x-ordered within a cell).
+//
+// Atoms are ordered by x within each cell, so the three cells of a row are
+// ordered by x and only the window |dx| < r_list of a row can hold hits.  A
+// thread owns one home atom; the 32 home atoms of a warp are consecutive in
+// one x-row of home cells, so their windows have nearly the same length.  The
+// warp walks row q of all its atoms together, four candidates per step (two
+// packed pairs), for the longest window of the warp.  Hits go to a ring of
+// RING entries per thread in shared memory and are written out in groups of
+// four (one 16-byte store per group in the grouped layout) whenever a ring of
+// the warp fills up: no per-hit branch.
+constexpr int RING = 16;
+
+// The FP32 stage holds slots in pairs: float4 s & ~1 is (x, x', y, y') and
+// float4 s | 1 is (z, z', j, j') of slots s & ~1 and (s & ~1) + 1 (j: the
+// atom's sorted index), so two candidates arrive as packed pairs.
+__device__ __forceinline__ void pair_put(float4 *P, int32_t s, float x, float y, float z, int32_t j) {
+    float *a = reinterpret_cast<float *>(P + (s & ~1)), *b = reinterpret_cast<float *>(P + (s | 1));
+    const int h = s & 1;
+    a[h] = x;
+    a[2 + h] = y;
+    b[h] = z;
+    b[2 + h] = __int_as_float(j);
+}
+__device__ __forceinline__ float pair_x(const float4 *P, int32_t s) {
+    return reinterpret_cast<const float *>(P + (s & ~1))[s & 1];
+}
 
 template <bool VEC4>
 __device__ __forceinline__ void put_entry(int32_t *W, int64_t ld, int64_t i, int32_t e, int32_t j) {
@@ -148,22 +166,23 @@ __device__ __forceinline__ void put_entry(int32_t *W, int64_t ld, int64_t i, int
 }
 
 template <bool VEC4>
-__global__ void __launch_bounds__(BRICK_THREADS, 4) k_neigh_cluster(const Brick *__restrict__ bricks, BrickShape shape,
-                                                                const int4 *__restrict__ xq,
-                                                                const double *__restrict__ pos64, SegTable st,
-                                                                const int32_t *__restrict__ cs, int32_t *__restrict__ W,
-                                                                int64_t ld, int32_t *__restrict__ cnt, int32_t max_nbr,
-                                                                int32_t stage_cap, int32_t *status,
-                                                                unsigned long long *needed) {
+__global__ void __launch_bounds__(BRICK_THREADS, 5) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
+                                                              const int4 *__restrict__ xq,
+                                                              const double *__restrict__ pos64, SegTable st,
+                                                              const int32_t *__restrict__ cs, int32_t *__restrict__ W,
+                                                              int64_t ld, int32_t *__restrict__ cnt, int32_t max_nbr,
+                                                              int32_t stage_cap, int32_t *status,
+                                                              unsigned long long *needed) {
     constexpr int NROW = (BH_MAX + 2) * (BD_MAX + 2), NHOME = BH_MAX * BD_MAX;
     extern __shared__ __align__(16) unsigned char smem[];
     int4 *s_x = (int4 *)smem;
-    __shared__ int32_t s_cell[NROW][BW_MAX + 3];
-    __shared__ int32_t s_da[NROW], s_db[NROW], s_sw[NROW];
-    __shared__ int32_t s_home[NHOME][BW_MAX + 1];
-    __shared__ int32_t s_hoff[32];
-    __shared__ int32_t s_total, s_ncl;
-    __shared__ int2 s_cl[MAX_CLUSTERS];  // (first atom (sorted index), size | home row << 8 | home cell << 16)
+    float4 *P = (float4 *)smem;
+    __shared__ int32_t s_cell[NROW][BW_MAX + 3];  // start of the row's cells t = 0 .. bw+2 in the stage
+    __shared__ int32_t s_da[NROW], s_db[NROW], s_sw[NROW];  // global = local + (local < sw ? da : db)
+    __shared__ int32_t s_home[NHOME][BW_MAX + 1];  // cell starts of the home cells of each home row
+    __shared__ int32_t s_hoff[32];                 // first home index of each home row (then H)
+    __shared__ int32_t s_total;
+    __shared__ int32_t s_ring[RING * BRICK_THREADS];  // entry e of thread t at [e * BRICK_THREADS + t]
 
     Brick B;
     if (bricks) {
@@ -184,7 +203,7 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_neigh_cluster(const Brick 
     const int32_t x0 = B.x01 & 0xffff, x1 = B.x01 >> 16, y0 = B.y01 & 0xffff, y1 = B.y01 >> 16;
     const int32_t z0 = B.z01 & 0xffff, z1 = B.z01 >> 16;
     const int32_t bw = x1 - x0, bh = y1 - y0, bd = z1 - z0, nyr = bh + 2, nrow = nyr * (bd + 2), nhome = bh * bd;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
         // warp 0: the staged rows, their cell offsets and their mapping back
         // to the sorted order
@@ -199,9 +218,10 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_neigh_cluster(const Brick 
             }
             s_cell[tid][bw + 2] = tot;
         }
-        // each staged row is followed by ROW_GAP far-away sentinels, so that
-        // candidate reads may run past a row's end without bounds tests
-        const int32_t span = tid < nrow ? tot + ROW_GAP : 0;
+        // each staged row is followed by at least ROW_GAP far-away sentinels
+        // (candidate reads may run past a row's end without bounds tests) and
+        // starts on an even slot (a pair)
+        const int32_t span = tid < nrow ? (tot + ROW_GAP + 1) & ~1 : 0;
         int32_t inc = span;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -211,13 +231,13 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_neigh_cluster(const Brick 
         const int32_t base = inc - span;
         if (tid < nrow) {
             for (int t = 0; t <= bw + 2; ++t) s_cell[tid][t] += base;
-            const int32_t xa = x0 - 1, xb = x1;
-            if (xa < 0) {
+            const int32_t xa = x0 - 1, xb = x1;  // inclusive cell range of the row
+            if (xa < 0) {  // cell nx-1 first, then cells 0 .. xb
                 const int32_t len1 = cs[rb + nx] - cs[rb + nx - 1];
                 s_da[tid] = cs[rb + nx - 1] - base;
                 s_sw[tid] = base + len1;
                 s_db[tid] = cs[rb] - (base + len1);
-            } else if (xb >= nx) {
+            } else if (xb >= nx) {  // cells xa .. nx-1, then cell 0
                 const int32_t len1 = cs[rb + nx] - cs[rb + xa];
                 s_da[tid] = cs[rb + xa] - base;
                 s_sw[tid] = base + len1;
@@ -230,7 +250,7 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_neigh_cluster(const Brick 
         }
         if (tid == 31) s_total = inc;
     } else if (tid < 64) {
-        // warp 1: the home rows, then (lane 0) the clusters
+        // warp 1: the home rows (home row l is row l % bh, plane l / bh)
         const int l = lane;
         int32_t c = 0;
         if (l < nhome) {
@@ -244,31 +264,11 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_neigh_cluster(const Brick 
             const int32_t v = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += v;
         }
-        s_hoff[l] = inc - c;
-        __syncwarp();
-        if (l == 0) {
-            int32_t k = 0;
-            for (int hr = 0; hr < nhome; ++hr)
-                for (int t = 0; t < bw; ++t)
-                    for (int32_t a = s_home[hr][t]; a < s_home[hr][t + 1]; a += CL) {
-                        const int32_t sz = min(CL, s_home[hr][t + 1] - a);
-                        if (k < MAX_CLUSTERS) s_cl[k] = make_int2(a, sz | (hr << 8) | (t << 16));
-                        ++k;
-                    }
-            s_ncl = k;
-        }
+        s_hoff[l] = inc - c;  // rows past nhome hold H
     }
     __syncthreads();
-    const int32_t T = s_total, ncl = s_ncl;
-    if (ncl > MAX_CLUSTERS) {  // more home atoms than the cluster table holds (a brick far denser than planned)
-        if (tid == 0) {
-            latch_status(status, PPMD_ERR_CAPACITY);
-            latch_needed(needed, (unsigned long long)max_nbr + 1);
-        }
-        for (int hr = 0; hr < nhome; ++hr)
-            for (int32_t a = s_home[hr][0] + tid; a < s_home[hr][bw]; a += blockDim.x) cnt[a] = 0;
-        return;
-    }
+    const int32_t T = s_total;
+    const int32_t H = s_hoff[nhome];
     // a neighbourhood larger than the shared-memory stage is read from global
     // memory instead (same indices, slower)
     const bool staged = T <= stage_cap;
@@ -283,153 +283,222 @@ __global__ void __launch_bounds__(BRICK_THREADS, 4) k_neigh_cluster(const Brick 
     const uint32_t refx = (uint32_t)__float2ull_rz((x0 - 1 + 0.5f * (bw + 2)) / (float)nx * 4294967296.0f);
     const uint32_t refy = (uint32_t)__float2ull_rz((y0 - 1 + 0.5f * (bh + 2)) / (float)ny * 4294967296.0f);
     const uint32_t refz = (uint32_t)__float2ull_rz((z0 - 1 + 0.5f * (bd + 2)) / (float)nz * 4294967296.0f);
-    const float sx = S.sx[0], sy = S.sx[1], sz_ = S.sx[2];
-    auto rel = [&](const int4 q) {
-        return make_float4((float)(int32_t)((uint32_t)q.x - refx) * sx, (float)(int32_t)((uint32_t)q.y - refy) * sy,
-                           (float)(int32_t)((uint32_t)q.z - refz) * sz_, 0.0f);
-    };
-    float4 *s_f = (float4 *)smem;
+    const float sx = S.sx[0], sy = S.sx[1], sz = S.sx[2];
     if (staged) {
         for (int32_t t = tid; t < T; t += blockDim.x) {
-            int r = 0, rh = nrow - 1;
+            int r = 0, rh = nrow - 1;  // the last row starting at or before t
             while (r < rh) {
                 const int mid = (r + rh + 1) >> 1;
                 if (s_cell[mid][0] <= t) r = mid;
                 else rh = mid - 1;
             }
-            if (t >= s_cell[r][bw + 2]) {
-                if (fstage) s_f[t] = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+            if (t >= s_cell[r][bw + 2]) {  // a row's sentinel slot
+                if (fstage) pair_put(P, t, 1e18f, 1e18f, 1e18f, -1);
                 continue;
             }
-            const int4 q = xq[t + (t < s_sw[r] ? s_da[r] : s_db[r])];
-            if (fstage) s_f[t] = rel(q);
-            else s_x[t] = q;
+            const int32_t j = t + (t < s_sw[r] ? s_da[r] : s_db[r]);
+            const int4 q = xq[j];
+            if (fstage)
+                pair_put(P, t, (float)(int32_t)((uint32_t)q.x - refx) * sx, (float)(int32_t)((uint32_t)q.y - refy) * sy,
+                         (float)(int32_t)((uint32_t)q.z - refz) * sz, j);
+            else
+                s_x[t] = q;
         }
     }
     __syncthreads();
     const float lo = S.rl2_lo, hi = S.rl2_hi;
-    const float rwin = sqrtf((float)S.rl2) * 1.00001f + 1e-5f;
-    const unsigned lt = (1u << lane) - 1u;
-    // position of candidate slot k (stage, or the sorted arrays when the
-    // neighbourhood was too large to stage), as an offset usable against the
-    // cluster's atoms: FP32 offsets from the centre, or fixed-point words
-    auto cand_f = [&](int32_t k) { return s_f[k]; };
-    auto cand_q = [&](int32_t k, int r) {
-        return staged ? s_x[k] : xq[k + (k < s_sw[r] ? s_da[r] : s_db[r])];
-    };
-    for (int32_t cl = warp; cl < ncl; cl += BRICK_THREADS / 32) {
-        const int2 ce = s_cl[cl];
-        const int32_t i0 = ce.x, nat = ce.y & 0xff, hr = (ce.y >> 8) & 0xff, t = ce.y >> 16;
-        const int32_t hy = hr % bh, hz = hr / bh;
-        const int32_t rself = (hz + 1) * nyr + hy + 1;
-        const int32_t self0 = s_cell[rself][t + 1] + (i0 - s_home[hr][t]);
-        // the cluster's atoms in registers (atoms past nat: far away, never hit)
-        float ax[CL], ay[CL], az[CL];
+    if (fstage) {
+        const float rwin = sqrtf((float)S.rl2) * 1.00001f + 1e-5f;
+        const ulonglong2 *P2 = reinterpret_cast<const ulonglong2 *>(P);
+        int32_t *const ring = s_ring + tid;
+        const int32_t Hw = (H + 31) & ~31;  // whole warps walk the rows together
+        for (int32_t h = tid; h < Hw; h += blockDim.x) {
+            const bool act = h < H;
+            const int32_t hh = act ? h : H - 1;  // idle lanes shadow the last home atom
+            int hr = 0;  // the last home row starting at or before hh
+            while (hr + 1 < nhome && s_hoff[hr + 1] <= hh) ++hr;
+            const int32_t i = s_home[hr][0] + (hh - s_hoff[hr]);
+            const int32_t hy = hr % bh, hz = hr / bh;
+            int t = 0;
+            while (t + 1 < bw && i >= s_home[hr][t + 1]) ++t;
+            const int32_t sself = s_cell[(hz + 1) * nyr + hy + 1][t + 1] + (i - s_home[hr][t]);
+            float xi, yi, zi;
+            {
+                const float4 a = P[sself & ~1], b = P[sself | 1];
+                const bool odd = sself & 1;
+                xi = odd ? a.y : a.x;
+                yi = odd ? a.w : a.z;
+                zi = odd ? b.y : b.x;
+            }
+            const f2 xii = pk(xi, xi), yii = pk(yi, yi), zii = pk(zi, zi);
+            const float xlo = xi - rwin, xhi = xi + rwin;
+            int32_t *wp = ring;  // next free ring entry
+            int32_t nout = 0;    // entries written out
+            // writes out the ring's complete groups of four (all, padded
+            // with -1, when last); warp-wide
+            auto flush = [&](bool last) {
+                const int32_t n = (int32_t)(wp - ring) / BRICK_THREADS;
+                const int32_t g = last ? (n + 3) >> 2 : n >> 2;
+                const int32_t gmax = __reduce_max_sync(0xffffffffu, g);
+                for (int32_t x = 0; x < gmax; ++x) {
+                    if (x >= g) continue;
+                    int32_t v[4];
 #pragma unroll
-        for (int a = 0; a < CL; ++a) {
-            const float4 f = (fstage && a < nat) ? s_f[self0 + a] : make_float4(3e18f, 3e18f, 3e18f, 0.0f);
-            ax[a] = f.x;
-            ay[a] = f.y;
-            az[a] = f.z;
-        }
-        float xmax = ax[0];
-#pragma unroll
-        for (int a = 1; a < CL; ++a)
-            if (a < nat) xmax = fmaxf(xmax, ax[a]);
-        const float xlo = fstage ? ax[0] - rwin : 0.0f, xhi = fstage ? xmax + rwin : 0.0f;
-        // the nine row windows: lane q finds row q's lower end, lane 16 + q its upper end
-        int32_t wend = 0;
-        {
-            const int q = lane & 15;
-            if (q < 9) {
-                const int r = (hz + q / 3) * nyr + hy + q % 3;
-                int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
-                if (fstage) {
-                    if (lane < 16) {
-                        while (a < b) {
-                            const int32_t mid = (a + b) >> 1;
-                            if (s_f[mid].x < xlo) a = mid + 1;
-                            else b = mid;
-                        }
+                    for (int q = 0; q < 4; ++q) v[q] = 4 * x + q < n ? ring[(4 * x + q) * BRICK_THREADS] : -1;
+                    const int32_t e = nout + 4 * x;
+                    if (!act || e >= max_nbr) continue;
+                    if (VEC4) {
+                        reinterpret_cast<int4 *>(W)[(int64_t)(e >> 2) * ld + i] = make_int4(v[0], v[1], v[2], v[3]);
                     } else {
-                        while (a < b) {
-                            const int32_t mid = (a + b) >> 1;
-                            if (s_f[mid].x <= xhi) a = mid + 1;
-                            else b = mid;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (4 * x + q < n && e + q < max_nbr) W[(int64_t)(e + q) * ld + i] = v[q];
+                    }
+                }
+                if (last) {
+                    nout += n;
+                } else {
+                    const int32_t rest = n - 4 * g;  // 0 .. 3 entries move to the front
+                    for (int q = 0; q < rest; ++q) ring[q * BRICK_THREADS] = ring[(4 * g + q) * BRICK_THREADS];
+                    wp = ring + rest * BRICK_THREADS;
+                    nout += 4 * g;
+                }
+            };
+            for (int q = 0; q < 9; ++q) {
+                const int r = (hz + q / 3) * nyr + hy + q % 3;
+                int32_t a = s_cell[r][t], e = s_cell[r][t + 3];
+                {  // the window: first candidate with x >= xlo, first with x > xhi
+                    int32_t u = a, v = e;
+                    while (u < v) {
+                        const int32_t mid = (u + v) >> 1;
+                        if (pair_x(P, mid) < xlo) u = mid + 1;
+                        else v = mid;
+                    }
+                    a = u;
+                    v = e;
+                    while (u < v) {
+                        const int32_t mid = (u + v) >> 1;
+                        if (pair_x(P, mid) <= xhi) u = mid + 1;
+                        else v = mid;
+                    }
+                    e = u;
+                }
+                a &= ~1;  // rows start on even slots: a stays in the row
+                if (!act) e = a;
+                const int32_t nstep = __reduce_max_sync(0xffffffffu, (e - a + 3) >> 2);
+                for (int32_t s = 0; s < nstep; ++s) {
+                    const int32_t k = a + 4 * s;
+                    const bool ok = k < e;
+                    // Reads run at most three slots past the window: candidates
+                    // with x beyond the window (never within r_list), atoms two
+                    // cells away, or the row's sentinels.
+                    const int32_t kk = ok ? k : a;
+                    const ulonglong2 A = P2[kk], Bv = P2[kk + 1], C = P2[kk + 2], D = P2[kk + 3];
+                    float r2[4];
+                    {
+                        const f2 dx = sub2(xii, A.x), dy = sub2(yii, A.y), dz = sub2(zii, Bv.x);
+                        upk(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), r2[0], r2[1]);
+                        const f2 ex = sub2(xii, C.x), ey = sub2(yii, C.y), ez = sub2(zii, D.x);
+                        upk(fma2(ex, ex, fma2(ey, ey, mul2(ez, ez))), r2[2], r2[3]);
+                    }
+                    const int32_t jv[4] = {(int32_t)(uint32_t)Bv.y, (int32_t)(uint32_t)(Bv.y >> 32),
+                                           (int32_t)(uint32_t)D.y, (int32_t)(uint32_t)(D.y >> 32)};
+                    bool hit[4], band = false;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const bool other = ok & (k + c != sself);  // not the atom itself
+                        hit[c] = other & (r2[c] < lo);
+                        band |= other & (r2[c] < hi) & !hit[c];
+                    }
+                    if (band) {
+                        // rare: within the FP32 decision band of r_list (FP64
+                        // decides)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if (!hit[c] && r2[c] < hi && ok && k + c != sself) {
+                                double dr[3];
+                                hit[c] = min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jv[c], S, dr) < S.rl2;
+                            }
                         }
                     }
-                }
-                wend = lane < 16 ? a : (fstage ? a : b);
-            }
-        }
-        int32_t count[CL];
 #pragma unroll
-        for (int a = 0; a < CL; ++a) count[a] = 0;
-        for (int q = 0; q < 9; ++q) {
-            const int32_t wa = __shfl_sync(0xffffffffu, wend, q), wb = __shfl_sync(0xffffffffu, wend, 16 + q);
-            const int r = (hz + q / 3) * nyr + hy + q % 3;
-            const int32_t sw = s_sw[r], da = s_da[r], db = s_db[r];
-            for (int32_t k0 = wa; k0 < wb; k0 += 32) {
-                const int32_t k = k0 + lane;
-                const bool valid = k < wb;
-                const int32_t kk = valid ? k : wa;
-                const int32_t j = kk + (kk < sw ? da : db);
-                float r2[CL];
-                if (fstage) {
-                    const float4 f = cand_f(kk);
-                    const f2 xx = pk(f.x, f.x), yy = pk(f.y, f.y), zz = pk(f.z, f.z);
-#pragma unroll
-                    for (int a = 0; a < CL; a += 2) {
-                        const f2 dx = sub2(pk(ax[a], ax[a + 1]), xx), dy = sub2(pk(ay[a], ay[a + 1]), yy),
-                                 dz = sub2(pk(az[a], az[a + 1]), zz);
-                        upk(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), r2[a], r2[a + 1]);
+                    for (int c = 0; c < 4; ++c) {
+                        *wp = jv[c];
+                        if (hit[c]) wp += BRICK_THREADS;
                     }
-                } else {
-                    // small grids (the neighbourhood wraps onto itself):
-                    // fixed-point differences, the cluster's words re-read
-                    const int4 qc = cand_q(kk, r);
-#pragma unroll
-                    for (int a = 0; a < CL; ++a) {
-                        const int4 qa = xq[i0 + min(a, nat - 1)];
-                        const float dx = fdiff(qa.x, qc.x) * sx, dy = fdiff(qa.y, qc.y) * sy, dz = fdiff(qa.z, qc.z) * sz_;
-                        r2[a] = a < nat ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : 3e38f;
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < CL; ++a) {
-                    bool hit = valid && r2[a] < hi && kk != self0 + a;
-                    if (hit && !(r2[a] < lo)) {
-                        double dr[3];
-                        hit = min_image_r2(pos64 + 3 * (int64_t)(i0 + a), pos64 + 3 * (int64_t)j, S, dr) < S.rl2;
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (m) {
-                        const int32_t e = count[a] + __popc(m & lt);
-                        if (hit && e < max_nbr) put_entry<VEC4>(W, ld, i0 + a, e, j);
-                        count[a] += __popc(m);
-                    }
+                    if (__any_sync(0xffffffffu, wp >= ring + (RING - 4) * BRICK_THREADS)) flush(false);
                 }
             }
-        }
-        // counts, capacity and (grouped layout) the last group's padding
-#pragma unroll
-        for (int a = 0; a < CL; ++a) {
-            if (a < nat && lane == a) {
-                cnt[i0 + a] = count[a];
-                if (count[a] > max_nbr) {
+            flush(true);
+            if (act) {
+                cnt[i] = nout;
+                if (nout > max_nbr) {
                     latch_status(status, PPMD_ERR_CAPACITY);
-                    latch_needed(needed, (unsigned long long)count[a]);
+                    latch_needed(needed, (unsigned long long)nout);
                 }
-                if (VEC4)
-                    for (int32_t e = count[a]; e < ((count[a] + 3) & ~3) && e < max_nbr; ++e) put_entry<VEC4>(W, ld, i0 + a, e, -1);
             }
+        }
+        return;
+    }
+    // Small grids (the neighbourhood wraps onto itself) and neighbourhoods
+    // too large to stage: a thread per home atom, fixed-point differences,
+    // hits stored as they are found (same order).
+    const f2 sxx = pk(sx, sx), syy = pk(sy, sy), szz = pk(sz, sz);
+    for (int32_t h = tid; h < H; h += blockDim.x) {
+        int hr = 0;
+        while (hr + 1 < nhome && s_hoff[hr + 1] <= h) ++hr;
+        const int32_t i = s_home[hr][0] + (h - s_hoff[hr]);
+        const int32_t hy = hr % bh, hz = hr / bh;
+        const int4 xi = xq[i];
+        int t = 0;
+        while (t + 1 < bw && i >= s_home[hr][t + 1]) ++t;
+        int32_t count = 0;
+        auto hit = [&](int32_t j) {
+            if (count < max_nbr) put_entry<VEC4>(W, ld, i, count, j);
+            ++count;
+        };
+        for (int dz = 0; dz < 3; ++dz)
+            for (int dy = 0; dy < 3; ++dy) {
+                const int r = (hz + dz) * nyr + hy + dy;
+                const int32_t a = s_cell[r][t], b = s_cell[r][t + 3];
+                const int32_t sw = s_sw[r], da = s_da[r], db = s_db[r];
+                for (int32_t k = a; k < b; k += 2) {
+                    const bool v1 = k + 1 < b;
+                    const int32_t kb = v1 ? k + 1 : k;
+                    const int4 xa = staged ? s_x[k] : xq[k + (k < sw ? da : db)];
+                    const int4 xb = staged ? s_x[kb] : xq[kb + (kb < sw ? da : db)];
+                    const f2 dx = mul2(pk(fdiff(xi.x, xa.x), fdiff(xi.x, xb.x)), sxx);
+                    const f2 dy_ = mul2(pk(fdiff(xi.y, xa.y), fdiff(xi.y, xb.y)), syy);
+                    const f2 dz_ = mul2(pk(fdiff(xi.z, xa.z), fdiff(xi.z, xb.z)), szz);
+                    const f2 r2 = fma2(dx, dx, fma2(dy_, dy_, mul2(dz_, dz_)));
+                    float ra, rb2;
+                    upk(r2, ra, rb2);
+                    const int32_t ja = k + (k < sw ? da : db);
+                    const int32_t jb = k + 1 + (k + 1 < sw ? da : db);
+                    if (ra < hi && ja != i) {
+                        double dr[3];
+                        if (ra < lo || min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)ja, S, dr) < S.rl2) hit(ja);
+                    }
+                    if (v1 && rb2 < hi && jb != i) {
+                        double dr[3];
+                        if (rb2 < lo || min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jb, S, dr) < S.rl2) hit(jb);
+                    }
+                }
+            }
+        // the last, partial group, padded with -1
+        if (VEC4)
+            for (int32_t e = count; e < ((count + 3) & ~3) && e < max_nbr; ++e) put_entry<VEC4>(W, ld, i, e, -1);
+        cnt[i] = count;
+        if (count > max_nbr) {
+            latch_status(status, PPMD_ERR_CAPACITY);
+            latch_needed(needed, (unsigned long long)count);
         }
     }
 }
 
 int neigh_brick_setup(ppmd_ctx *ctx, int32_t max_nbr) {
     int rc = PPMD_OK;
-    for (const void *f : {(const void *)k_neigh_cluster<false>, (const void *)k_neigh_cluster<true>})
+    for (const void *f : {(const void *)k_neigh_brick<false>, (const void *)k_neigh_brick<true>})
         if (rc == PPMD_OK)
             rc = cuda_check(ctx, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)neigh_brick_smem(max_nbr)),
@@ -443,7 +512,7 @@ int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, Brick
     if (stage_cap <= 0 || stage_cap > NB_MAX) stage_cap = NB_MAX;
     if (vec4 && (max_nbr & 3)) return set_error(ctx, PPMD_ERR_INVALID, "grouped list needs a capacity divisible by 4");
     if (nbricks > 0) {
-        auto kern = vec4 ? k_neigh_cluster<true> : k_neigh_cluster<false>;
+        auto kern = vec4 ? k_neigh_brick<true> : k_neigh_brick<false>;
         PPMD_LAUNCH(ctx, kern, nbricks, BRICK_THREADS, (size_t)stage_cap * sizeof(int4), bricks, shape, xq, pos64, st,
                     cell_start, W, ld, cnt, max_nbr, stage_cap, ctx->d_status, ctx->d_needed);
     }

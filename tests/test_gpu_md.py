@@ -393,6 +393,29 @@ def test_md_skin_violation_is_flagged(L, ctx):
             assert info["max_disp"] > 0.5 * (r_list - 2.5)
 
 
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_md_list_capacity_overflow_reports_exact_need(L, ctx, prec):
+    """A list capacity below the true neighbour count (LJ liquid, ragged
+    counts): the integrator's list build latches PPMD_ERR_CAPACITY and
+    reports the largest count exactly (the oracle's); with that capacity the
+    build is clean."""
+    c = configs.structure_box("liquid", 0.0, 3, cells=(40, 40, 40))
+    pos, box = oracle.wrap(c["pos"], c["box"]), np.asarray(c["box"], float)
+    offs, _ = oracle.neighbours_cells(pos, box, 2.8)
+    need = int(np.diff(offs).max())
+    n = len(pos)
+    for max_nbr, fits in ((40, False), (need, True)):
+        ctx.status()  # clear
+        md = L.MD(ctx, [0, n], [box], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=max_nbr, prec=getattr(L, prec))
+        md.set_state(cu(pos), cu(np.zeros((n, 3))))
+        code, needed = ctx.status()  # synchronises and consumes the status
+        md.close()
+        if fits:
+            assert code == 0, (code, needed)
+        else:
+            assert code == L.ERR_CAPACITY and needed == need, (code, needed, need)
+
+
 def test_md_momentum_conserved(L, ctx):
     c = configs.lj_solid(n_cells=8)
     p, v, F, en, info = _md(L, ctx, c, L.FP32, 50, True)
