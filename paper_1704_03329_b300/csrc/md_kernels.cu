@@ -1,9 +1,9 @@
 // Kernels of the time-stepping driver.  Atoms are stored in cell order, so
 // the atoms of consecutive cells of a row are contiguous.
-//  - List build: one block per brick (up to three cells of a row) stages the
-//    positions of the brick's neighbourhood in shared memory; each home atom
-//    is tested against its 27 cells by a warp (ballot compaction); the rows
-//    are written out as the paper's column-major neighbour matrix W[m][i].
+//  - List build: one block per brick of cells stages the positions of the
+//    brick's neighbourhood in shared memory; each home atom tests the
+//    x-window of each of its nine rows of three cells; the rows are written
+//    out as the paper's column-major neighbour matrix W[m][i].
 //  - Pair loop: one thread per atom walks its column of W; the
 //    single-precision arithmetic runs on packed pairs (f32x2: two neighbours
 //    per instruction) with compensated sums, and the second kick of
@@ -11,40 +11,10 @@
 #include <algorithm>
 
 #include "md_kernels.cuh"
+#include "pair32.cuh"
 
 namespace ppmd {
 
-// ---------------------------------------------------------------------
-// Packed single-precision pairs (two neighbours per instruction).
-// ---------------------------------------------------------------------
-typedef unsigned long long f2;
-typedef f2 f2_t;
-__device__ __forceinline__ f2 pk(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 // A 16-byte list word, read once per step: not kept in L1, which then holds
 // the neighbour positions the loop gathers again and again.
 __device__ __forceinline__ int4 ld_stream4(const int4 *p) {
@@ -53,11 +23,6 @@ __device__ __forceinline__ int4 ld_stream4(const int4 *p) {
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "l"(p));
     return v;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
 }
 
 BrickShape brick_shape(const Seg &S) {
@@ -120,8 +85,6 @@ int32_t brick_stage_cap(const Seg &S, BrickShape b) {
 
 __device__ __forceinline__ int32_t wrapi(int32_t v, int32_t n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Signed minimum-image difference of two fixed-point words, as a float.
-__device__ __forceinline__ float fdiff(int32_t a, int32_t b) { return __int2float_rn((int32_t)((uint32_t)a - (uint32_t)b)); }
 
 // List build (Sec. 3.5: the 27 cells around each atom's cell), one block per
 // brick of cells.  The brick's neighbourhood (its cells and one cell more on
@@ -518,35 +481,6 @@ int build_list_bricks(ppmd_ctx *ctx, int64_t nbricks, const Brick *bricks, Brick
     }
     return check_launch(ctx, "build_list_bricks");
 }
-
-// Compensated sum of two interleaved streams: value = s - c, kept as cn = -c.
-struct Kahan2 {
-    f2 s, cn;
-    __device__ __forceinline__ void init() { s = cn = 0ull; }
-    // adds a * b to each stream
-    __device__ __forceinline__ void add_prod(f2 a, f2 b) {
-        const f2 yv = fma2(a, b, cn);
-        const f2 t = add2(s, yv);
-        cn = sub2(yv, sub2(t, s));
-        s = t;
-    }
-    // adds v to each stream
-    __device__ __forceinline__ void add(f2 v) {
-        const f2 yv = add2(v, cn);
-        const f2 t = add2(s, yv);
-        cn = sub2(yv, sub2(t, s));
-        s = t;
-    }
-    // the two streams merged: (hi, lo) with hi + lo the sum
-    __device__ __forceinline__ void merged(float &hi, float &lo) const {
-        float s0, s1, c0, c1;
-        upk(s, s0, s1);
-        upk(cn, c0, c1);
-        hi = s0;
-        lo = c0;
-        two_sum_merge(hi, lo, s1, c1);
-    }
-};
 
 __device__ __forceinline__ void block_sum3(double a, double b, double c, double *partials) {
     __shared__ double sh[3][32];

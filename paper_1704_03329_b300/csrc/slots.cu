@@ -20,6 +20,7 @@
 // the column-major loop in md_kernels.cu, entry for entry in the same order,
 // so the two paths give the same forces bit for bit.
 #include "md_kernels.cuh"
+#include "pair32.cuh"
 
 namespace ppmd {
 
@@ -235,7 +236,6 @@ __device__ __forceinline__ int32_t home_slot(const Lay &L, const BrickDims &d, c
     return L.cell(r, a.t + 1) + (a.i - L.home(a.hr, a.t));
 }
 
-__device__ __forceinline__ float fdiff(int32_t a, int32_t b) { return __int2float_rn((int32_t)((uint32_t)a - (uint32_t)b)); }
 
 // ---------------------------------------------------------------------
 // List build.
@@ -396,70 +396,11 @@ __global__ void __launch_bounds__(SLOT_THREADS) k_slot_list(const Brick *__restr
 // ---------------------------------------------------------------------
 // Pair loop.
 // ---------------------------------------------------------------------
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 pk(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 __device__ __forceinline__ uint4 ld_stream16(const uint4 *p) {
     uint4 v;
     asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
     return v;
 }
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-// Compensated sum of two interleaved streams (as in the column-major loop).
-struct Kahan2 {
-    f2 s, cn;
-    __device__ __forceinline__ void init() { s = cn = 0ull; }
-    __device__ __forceinline__ void add_prod(f2 a, f2 b) {
-        const f2 yv = fma2(a, b, cn);
-        const f2 t = add2(s, yv);
-        cn = sub2(yv, sub2(t, s));
-        s = t;
-    }
-    __device__ __forceinline__ void add(f2 v) {
-        const f2 yv = add2(v, cn);
-        const f2 t = add2(s, yv);
-        cn = sub2(yv, sub2(t, s));
-        s = t;
-    }
-    __device__ __forceinline__ void merged(float &hi, float &lo) const {
-        float s0, s1, c0, c1;
-        upk(s, s0, s1);
-        upk(cn, c0, c1);
-        hi = s0;
-        lo = c0;
-        two_sum_merge(hi, lo, s1, c1);
-    }
-};
-
 __device__ __forceinline__ void pair_add(float &s, float &e, float s2, float e2) {
     const float t = s + s2, bb = t - s, err = (s - (t - bb)) + (s2 - bb);
     const float lo = err + (e + e2);
