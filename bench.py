@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--suites", default="replicas,analysis,classifier,otf,precision",
                     help="extra workloads reported beside the main line (comma list, or 'none')")
     ap.add_argument("--replica-steps", type=int, default=500)
+    ap.add_argument("--shape-cache", default=None, help="launch-shape cache file of the replica suite (default: none)")
     ap.add_argument("--epochs", type=int, default=20)
     return ap.parse_args()
 
@@ -487,16 +488,32 @@ def suite_replicas(args, L, ctx, stream):
     n = int(off[-1])
     md = L.MD(ctx, off, [r["box"] for r in reps], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=160, prec=L.FP32,
               box_r_list=[r["r_list"] for r in reps])
-    md.set_state(pos, vel)
-    md.run(50)
     K = max(10, (args.replica_steps // 10) * 10)
-    t, _ = _timed(stream, lambda: md.run(K))
-    ctx.sync()
+
+    def timed_run():
+        md.set_state(pos, vel)
+        md.run(50)
+        k0 = ctx.kernel_count()
+        t, _ = _timed(stream, lambda: md.run(K))
+        ctx.sync()
+        return t, ctx.kernel_count() - k0
+    t0, _ = timed_run()  # the default launch shape
+    # the launch shapes timed once for this workload (pair-loop block size,
+    # persistent grid, list-build brick size); the same trajectory bit for bit
+    tune = md.tune(steps=50, cache=args.shape_cache)
+    t, launches = timed_run()
     md.close()
     return {"workload": f"256 LJ replicas, N log-uniform [500, 32000] (total {n}), rho U[0.7, 1.0], T U[0.7, 1.5], "
                         f"jittered sc, rc 2.5, list min(2.8, L/3), rebuild every 10, dt 0.005",
             "metric": "aggregate atom-steps/s", "value": n * K / t, "unit": UNIT, "steps": K, "atoms": n,
-            "ms_per_step": t / K * 1e3}
+            "ms_per_step": t / K * 1e3, "gpu_launches_timed": launches,
+            "launch_shape": {"chosen": {k: tune[k] for k in ("shape", "block", "per_sm", "brick_home")},
+                             "timed": tune["timed"], "cache": args.shape_cache,
+                             "ms_per_step_by_shape": [round(x, 5) for x in tune["ms_per_step"]],
+                             "shapes": "k: (block, persistent blocks per SM (0: one thread per atom), brick atoms) = "
+                                       "0 (256,0,128) 1 (128,0,128) 2 (256,3,128) 3 (128,6,128) "
+                                       "4 (256,0,64) 5 (128,0,64) 6 (256,3,64) 7 (128,6,64)"},
+            "default_shape_value": n * K / t0}
 
 
 def suite_precision(args, L, ctx, stream):

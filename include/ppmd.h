@@ -424,6 +424,40 @@ int ppmd_md_run_analysed(ppmd_md *md, int32_t nsteps, double *energies, double *
 #define PPMD_PAIR_COLUMNS 0
 #define PPMD_PAIR_BRICKS 1
 int ppmd_md_set_pair_loop(ppmd_md *md, int mechanism);
+/* Launch shapes of the atom-index mechanism (PPMD_PAIR_COLUMNS, PPMD_FP32):
+ * shape k of PPMD_MD_SHAPES sets the pair loop's threads per block (128 or
+ * 256), whether it runs one thread per atom or as a persistent grid (a few
+ * blocks per SM, each walking its share of the atoms), and the list build's
+ * brick size (up to 128 or 64 expected atoms per brick):
+ *   k  block  blocks per SM  brick atoms      k  block  blocks per SM  brick atoms
+ *   0  256    one per atom   128              4  256    one per atom   64
+ *   1  128    one per atom   128              5  128    one per atom   64
+ *   2  256    3 (persistent) 128              6  256    3 (persistent) 64
+ *   3  128    6 (persistent) 128              7  128    6 (persistent) 64
+ * Every shape gives the same list (same pairs in the same order) and the
+ * same positions, velocities and forces bit for bit; only the grouping of
+ * the energy and virial sums follows the shape (last bits of the totals).
+ * Shape 0 is the default.  ppmd_md_set_shape may be called at any time
+ * (PPMD_ERR_INVALID for k != 0 with PPMD_FP64 or PPMD_PAIR_BRICKS);
+ * ppmd_md_get_shape reads the shape and its three parameters (any output
+ * may be NULL).
+ * ppmd_md_tune (after ppmd_md_set_state): with cache_path (a text file, may
+ * be NULL) holding an entry for this workload (atoms, boxes, cells,
+ * cutoffs, list capacity and policy, device name and SM count), applies
+ * the cached shape without timing anything; otherwise runs each shape from
+ * the present state for `steps` steps (rounded up to whole graph units,
+ * after one unit of warm-up), keeps the fastest, starts again from the
+ * present state (as ppmd_md_set_state: the step counters restart at 0) and
+ * appends the entry "key TAB shape TAB ms_per_step" to cache_path.
+ * shape (host, may be NULL) receives the choice; ms_per_step (host, may be
+ * NULL, PPMD_MD_SHAPES doubles) the measured time per step of each shape
+ * (-1 where nothing was timed); timed (host, may be NULL) 1 if shapes were
+ * timed, 0 if the cache (or a PPMD_FP64 / PPMD_PAIR_BRICKS run, which has
+ * one shape) decided.  Uses 48 bytes of device memory per atom once. */
+#define PPMD_MD_SHAPES 8
+int ppmd_md_set_shape(ppmd_md *md, int32_t shape);
+int ppmd_md_get_shape(ppmd_md *md, int32_t *shape, int32_t *block, int32_t *per_sm, int32_t *brick_home);
+int ppmd_md_tune(ppmd_md *md, int32_t steps, const char *cache_path, int32_t *shape, double *ms_per_step, int *timed);
 /* List-age check (Sec. 3.5, Eq. (6): a list built with the extended cutoff
  * r_list = r_c + delta holds every pair that can come within r_c before the
  * next build only while no atom moves more than delta / 2).  With on != 0

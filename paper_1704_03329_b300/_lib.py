@@ -25,6 +25,7 @@ OK, ERR_INVALID, ERR_BOX, ERR_CAPACITY, ERR_NONFINITE, ERR_CUDA, ERR_TIMEOUT, ER
 WARN_SKIN = 1
 FP64, FP32 = 0, 1
 PAIR_COLUMNS, PAIR_BRICKS = 0, 1
+MD_SHAPES = 8  # launch shapes of ppmd_md_set_shape / ppmd_md_tune
 OTHER, FCC, HCP, BCC = 0, 1, 2, 3
 _NAMES = {0: "PPMD_OK", -1: "PPMD_ERR_INVALID", -2: "PPMD_ERR_BOX", -3: "PPMD_ERR_CAPACITY",
           -4: "PPMD_ERR_NONFINITE", -5: "PPMD_ERR_CUDA", -6: "PPMD_ERR_TIMEOUT", -7: "PPMD_ERR_NOMEM",
@@ -101,6 +102,9 @@ _SIGS = {
     "ppmd_md_missed_pairs": (_I, [_P, C.POINTER(_I64)]),
     "ppmd_md_time_pair_loops": (_I, [_P, _I]),
     "ppmd_md_pair_loop_times": (_I, [_P, C.POINTER(_D), C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I32)]),
+    "ppmd_md_set_shape": (_I, [_P, _I32]),
+    "ppmd_md_get_shape": (_I, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
+    "ppmd_md_tune": (_I, [_P, _I32, C.c_char_p, C.POINTER(_I32), C.POINTER(_D), C.POINTER(_I)]),
     "ppmd_lj_forces_noalloc": (_I, [_P, _P, _I64, C.POINTER(Box), C.POINTER(LJParams), _P, _P, _I32, _I, _P, _P, _P,
                                     _P]),
 }
@@ -525,6 +529,30 @@ class MD:
     def set_pair_loop(self, mechanism):
         """PAIR_COLUMNS (default) or PAIR_BRICKS; before set_state."""
         self.ctx.check(_lib.ppmd_md_set_pair_loop(self.h, int(mechanism)))
+
+    def set_shape(self, shape):
+        """Launch shape k of MD_SHAPES (FP32 atom-index pair loop; 0 is the default)."""
+        self.ctx.check(_lib.ppmd_md_set_shape(self.h, int(shape)))
+
+    def get_shape(self):
+        """dict(shape, block, per_sm, brick_home) of the present launch shape."""
+        v = [_I32() for _ in range(4)]
+        self.ctx.check(_lib.ppmd_md_get_shape(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(("shape", "block", "per_sm", "brick_home"), (x.value for x in v)))
+
+    def tune(self, steps=20, cache=None):
+        """Time every launch shape for `steps` steps from the present state
+        (or take the cached choice for this workload) and keep the fastest;
+        the state starts again as after set_state.  Returns dict(shape,
+        timed, ms_per_step: list (-1 where not timed), and the shape's
+        parameters)."""
+        shape, timed = _I32(), _I()
+        ms = (_D * MD_SHAPES)()
+        path = None if cache is None else os.fsencode(cache)
+        self.ctx.check(_lib.ppmd_md_tune(self.h, int(steps), path, C.byref(shape), ms, C.byref(timed)))
+        out = self.get_shape()
+        out.update(timed=bool(timed.value), ms_per_step=[float(x) for x in ms])
+        return out
 
     def set_check(self, on=True):
         """Count, at every later rebuild, pairs within rc that the previous list lacked."""

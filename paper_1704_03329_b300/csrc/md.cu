@@ -6,6 +6,9 @@
 // graphs.
 #include <algorithm>
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string>
 
 #include "analysis.cuh"
 #include "cells.cuh"
@@ -55,7 +58,13 @@ struct ppmd_md {
     int32_t *stage_need = nullptr;  // largest neighbourhood met by a slot-list build
     Brick *bricks = nullptr;
     int32_t stage_cap = 0;  // shared-memory stage of a list-build block (atoms)
-    int64_t nbricks = 0;
+    int64_t nbricks = 0, bricks_alloc = 0;
+    // launch shapes (ppmd_md_set_shape / ppmd_md_tune): the FP32 pair loop's
+    // and the expected home atoms of a list-build brick
+    ColShape col;
+    int32_t brick_home = BRICK_THREADS;
+    int32_t shape = 0;
+    double *tune_buf = nullptr;  // the state (caller order) while shapes are timed
     // reorder temporaries
     double *pos_t = nullptr, *vel_t = nullptr;
     int4 *xq_t = nullptr;
@@ -94,7 +103,9 @@ struct ppmd_md {
 
 namespace {
 
-int64_t force_blocks(const ppmd_md *m) { return m->slots ? m->nbricks : lj_columns_blocks(m->n); }
+int64_t force_blocks(const ppmd_md *m) {
+    return m->slots ? m->nbricks : lj_columns_blocks(m->n, m->p.prec == PPMD_FP32 ? m->col : ColShape());
+}
 
 template <class T>
 int md_alloc(ppmd_md *m, T **p, size_t count) {
@@ -446,7 +457,7 @@ int forces(ppmd_md *m, bool energy, bool kick, bool drift = false) {
     else
         PPMD_TRY(lj_columns(m->ctx, m->n, m->ld, m->xq, m->pos, m->st, m->c, m->W, m->cnt, m->p.max_nbr, m->p.prec,
                             f32 ? m->f4 : nullptr, f32 ? nullptr : m->f64, kick ? m->vel : nullptr, m->h, m->half_m,
-                            energy ? m->part_f : nullptr, d));
+                            energy ? m->part_f : nullptr, d, f32 ? m->col : ColShape()));
     if (drift) {
         use_buffer(m, m->cur ^ 1);
         m->half_kicked = true;
@@ -617,14 +628,16 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) {
         std::vector<Brick> bl;
         m->stage_cap = make_bricks(m->segs, bl);
-        m->nbricks = (int64_t)bl.size();
+        m->nbricks = m->bricks_alloc = (int64_t)bl.size();
         rc = md_alloc(m, &m->bricks, bl.size());
         if (rc == PPMD_OK && !bl.empty())
             rc = cuda_check(ctx, cudaMemcpy(m->bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice), "copy");
     }
     if (rc == PPMD_OK) rc = neigh_brick_setup(ctx, m->p.max_nbr);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt, n);
-    if (rc == PPMD_OK) rc = md_alloc(m, &m->part_f, 3 * std::max<int64_t>(lj_columns_blocks(n), m->nbricks) + 3);
+    // partial rows: the most blocks of any pair-loop shape or brick table
+    if (rc == PPMD_OK)
+        rc = md_alloc(m, &m->part_f, 3 * std::max<int64_t>(lj_columns_blocks(n, ColShape{128, 0}), m->nbricks) + 3);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->red, 4);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->ebuf, 2 * 1024);
@@ -933,8 +946,9 @@ extern "C" int ppmd_md_set_pair_loop(ppmd_md *m, int mechanism) {
     if (mechanism != PPMD_PAIR_COLUMNS && mechanism != PPMD_PAIR_BRICKS)
         return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_set_pair_loop: unknown mechanism %d", mechanism);
     if (m->ready) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_set_pair_loop: call it before ppmd_md_set_state");
-    if (mechanism == PPMD_PAIR_BRICKS && (m->p.prec != PPMD_FP32 || m->boa_every > 0))
-        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_set_pair_loop: bricks need FP32 and no on-the-fly analysis");
+    if (mechanism == PPMD_PAIR_BRICKS && (m->p.prec != PPMD_FP32 || m->boa_every > 0 || m->shape != 0))
+        return set_error(ctx, PPMD_ERR_INVALID,
+                         "ppmd_md_set_pair_loop: bricks need FP32, no on-the-fly analysis and the default shape");
     cudaSetDevice(ctx->device);
     drop_graph(m);
     if (mechanism == PPMD_PAIR_BRICKS) {
@@ -1047,4 +1061,157 @@ extern "C" int ppmd_md_list_stats(ppmd_md *m, int64_t *pairs, int32_t *max_row) 
     if (pairs) *pairs = (int64_t)h[0];
     if (max_row) *max_row = (int32_t)h[1];
     return rc;
+}
+
+// ---------------------------------------------------------------------
+// Launch shapes and their tuning.
+// ---------------------------------------------------------------------
+namespace {
+
+// Candidates: (FP32 pair-loop threads per block, persistent blocks per SM
+// (0: one thread per atom), expected home atoms of a list-build brick).
+struct ShapeCand {
+    int32_t block, per_sm, home;
+};
+constexpr ShapeCand SHAPES[PPMD_MD_SHAPES] = {{256, 0, 128}, {128, 0, 128}, {256, 3, 128}, {128, 6, 128},
+                                              {256, 0, 64},  {128, 0, 64},  {256, 3, 64},  {128, 6, 64}};
+
+int apply_shape(ppmd_md *m, int32_t k) {
+    ppmd_ctx *ctx = m->ctx;
+    const ShapeCand &c = SHAPES[k];
+    int sms = 0;
+    PPMD_TRY(cuda_check(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "attribute"));
+    drop_graph(m);
+    m->col.block = c.block;
+    m->col.grid_cap = c.per_sm > 0 ? (int64_t)c.per_sm * sms : 0;
+    if (c.home != m->brick_home) {
+        std::vector<Brick> bl;
+        const int32_t cap = make_bricks(m->segs, bl, c.home);
+        if ((int64_t)bl.size() > m->bricks_alloc) {
+            PPMD_TRY(md_alloc(m, &m->bricks, bl.size()));  // (the smaller table stays allocated until destroy)
+            m->bricks_alloc = (int64_t)bl.size();
+        }
+        if (!bl.empty())
+            PPMD_TRY(cuda_check(ctx, cudaMemcpy(m->bricks, bl.data(), sizeof(Brick) * bl.size(), cudaMemcpyHostToDevice),
+                                "copy"));
+        m->nbricks = (int64_t)bl.size();
+        m->stage_cap = cap;
+        m->brick_home = c.home;
+    }
+    m->shape = k;
+    return PPMD_OK;
+}
+
+// The workload's shape as a cache key: atoms, boxes, cells, cutoffs, list
+// policy and the device.
+std::string shape_key(const ppmd_md *m) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, m->ctx->device);
+    char buf[512];
+    snprintf(buf, sizeof(buf), "n=%lld;boxes=%lld;cells=%lld;r_list=%.9g;rc=%.9g;max_nbr=%d;every=%d;dev=%s;sms=%d",
+             (long long)m->n, (long long)m->nbox, (long long)m->ncell, m->p.r_list, m->p.lj.rc, m->p.max_nbr,
+             m->p.rebuild_every, prop.name, prop.multiProcessorCount);
+    for (char *c = buf; *c; ++c)
+        if (*c == '\t' || *c == '\n') *c = ' ';
+    return buf;
+}
+
+}  // namespace
+
+extern "C" int ppmd_md_set_shape(ppmd_md *m, int32_t shape) {
+    if (!m) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    if (shape < 0 || shape >= PPMD_MD_SHAPES) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_set_shape: shape %d", shape);
+    if (shape != 0 && (m->p.prec != PPMD_FP32 || m->slots))
+        return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_set_shape: shapes are for the FP32 atom-index pair loop");
+    cudaSetDevice(ctx->device);
+    return apply_shape(m, shape);
+}
+
+extern "C" int ppmd_md_get_shape(ppmd_md *m, int32_t *shape, int32_t *block, int32_t *per_sm, int32_t *brick_home) {
+    if (!m) return PPMD_ERR_INVALID;
+    const ShapeCand &c = SHAPES[m->shape];
+    if (shape) *shape = m->shape;
+    if (block) *block = c.block;
+    if (per_sm) *per_sm = c.per_sm;
+    if (brick_home) *brick_home = c.home;
+    return PPMD_OK;
+}
+
+extern "C" int ppmd_md_tune(ppmd_md *m, int32_t steps, const char *cache_path, int32_t *shape, double *ms_per_step,
+                            int *timed) {
+    if (!m || steps < 1) return PPMD_ERR_INVALID;
+    ppmd_ctx *ctx = m->ctx;
+    if (!m->ready) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_tune: state not set");
+    cudaSetDevice(ctx->device);
+    if (timed) *timed = 0;
+    if (ms_per_step)
+        for (int k = 0; k < PPMD_MD_SHAPES; ++k) ms_per_step[k] = -1.0;
+    if (m->p.prec != PPMD_FP32 || m->slots) {  // nothing to choose
+        if (shape) *shape = m->shape;
+        return PPMD_OK;
+    }
+    const std::string key = shape_key(m);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        int32_t found = -1;
+        if (f) {
+            char line[1024];
+            while (fgets(line, sizeof(line), f)) {
+                char *tab = strchr(line, '\t');
+                if (!tab) continue;
+                *tab = 0;
+                if (key == line) {
+                    const int32_t k = (int32_t)strtol(tab + 1, nullptr, 10);
+                    if (k >= 0 && k < PPMD_MD_SHAPES) found = k;  // the last entry of the key counts
+                }
+            }
+            fclose(f);
+        }
+        if (found >= 0) {
+            PPMD_TRY(apply_shape(m, found));
+            if (shape) *shape = found;
+            return PPMD_OK;
+        }
+    }
+    // time every candidate from the present state, then start again from it
+    const int64_t n = m->n;
+    if (!m->tune_buf) PPMD_TRY(md_alloc(m, &m->tune_buf, 6 * (size_t)std::max<int64_t>(n, 1)));
+    double *tp = m->tune_buf, *tv = m->tune_buf + 3 * n;
+    PPMD_TRY(ppmd_md_get_state(m, tp, tv, nullptr));
+    const int32_t P = m->p.rebuild_every, unit = P * std::max(1, 10 / P);
+    const int32_t timed_steps = (steps + unit - 1) / unit * unit;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PPMD_TRY(cuda_check(ctx, cudaEventCreate(&e0), "event"));
+    int rc = cuda_check(ctx, cudaEventCreate(&e1), "event");
+    double t[PPMD_MD_SHAPES];
+    int32_t best = 0;
+    for (int32_t k = 0; rc == PPMD_OK && k < PPMD_MD_SHAPES; ++k) {
+        rc = apply_shape(m, k);
+        if (rc == PPMD_OK) rc = ppmd_md_set_state(m, tp, tv);
+        if (rc == PPMD_OK) rc = ppmd_md_run(m, unit, nullptr, 1);  // warm-up, graph capture
+        if (rc == PPMD_OK) rc = cuda_check(ctx, cudaEventRecord(e0, ctx->stream), "event");
+        if (rc == PPMD_OK) rc = ppmd_md_run(m, timed_steps, nullptr, 1);
+        if (rc == PPMD_OK) rc = cuda_check(ctx, cudaEventRecord(e1, ctx->stream), "event");
+        if (rc == PPMD_OK) rc = cuda_check(ctx, cudaEventSynchronize(e1), "event");
+        float ms = 0.0f;
+        if (rc == PPMD_OK) rc = cuda_check(ctx, cudaEventElapsedTime(&ms, e0, e1), "event time");
+        t[k] = ms / timed_steps;
+        if (ms_per_step) ms_per_step[k] = t[k];
+        if (rc == PPMD_OK && t[k] < t[best]) best = k;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != PPMD_OK) return rc;
+    PPMD_TRY(apply_shape(m, best));
+    PPMD_TRY(ppmd_md_set_state(m, tp, tv));
+    if (shape) *shape = best;
+    if (timed) *timed = 1;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (!f) return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_tune: cannot write %s", cache_path);
+        fprintf(f, "%s\t%d\t%.6f\n", key.c_str(), best, t[best]);
+        fclose(f);
+    }
+    return PPMD_OK;
 }

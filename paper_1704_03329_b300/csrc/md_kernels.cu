@@ -25,7 +25,7 @@ __device__ __forceinline__ int4 ld_stream4(const int4 *p) {
     return v;
 }
 
-BrickShape brick_shape(const Seg &S) {
+BrickShape brick_shape(const Seg &S, int32_t home_max) {
     // the neighbourhood spans bw + 2 cells of a row, bh + 2 rows and bd + 2
     // planes; they must be distinct cells of the periodic grid
     const double pc = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
@@ -38,7 +38,7 @@ BrickShape brick_shape(const Seg &S) {
             for (int32_t bw = 1; bw <= mw; ++bw) {
                 const double cells = (double)bw * bh * bd, hood = (double)(bw + 2) * (bh + 2) * (bd + 2);
                 const double home = pc * cells;
-                if (1.5 * pc * hood + (ROW_GAP + 1) * (bh + 2) * (bd + 2) > NB_MAX || home > BRICK_THREADS) continue;
+                if (1.5 * pc * hood + (ROW_GAP + 1) * (bh + 2) * (bd + 2) > NB_MAX || home > home_max) continue;
                 const double halo = hood / cells;
                 if (home > best_home * (1.0 + 1e-9) || (home >= best_home * (1.0 - 1e-9) && halo < best_halo)) {
                     best = BrickShape{bw, bh, bd};
@@ -53,12 +53,13 @@ int64_t brick_count(const Seg &S, BrickShape b) {
     return (int64_t)((S.nc[0] + b.bw - 1) / b.bw) * ((S.nc[1] + b.bh - 1) / b.bh) * ((S.nc[2] + b.bd - 1) / b.bd);
 }
 
-int32_t make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out) {
+int32_t make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out, int32_t home_max) {
+    home_max = std::max(1, std::min(home_max, BRICK_THREADS));
     out.clear();
     int32_t cap = 64;
     for (size_t s = 0; s < segs.size(); ++s) {
         const Seg &S = segs[s];
-        const BrickShape b = brick_shape(S);
+        const BrickShape b = brick_shape(S, home_max);
         cap = std::max(cap, brick_stage_cap(S, b));
         for (int32_t z0 = 0; z0 < S.nc[2]; z0 += b.bd)
             for (int32_t y0 = 0; y0 < S.nc[1]; y0 += b.bh)
@@ -553,16 +554,20 @@ __device__ __forceinline__ void block_sum3_pairs(double a, double b, double c, d
 
 constexpr int COL_BLOCK = 256;
 
-template <bool ENERGY, bool DRIFT>
-__global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
+// One thread per atom; a launch with fewer blocks than atoms / BLOCK (a
+// persistent grid) walks the atoms block by block (grid stride), each
+// thread summing the energy and the largest displacement over its atoms.
+template <bool ENERGY, bool DRIFT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
                                                         const double *__restrict__ pos64, SegTable st, LJConst c,
                                                         const int32_t *__restrict__ W, const int32_t *__restrict__ cnt,
                                                         int32_t max_nbr, float4 *__restrict__ f4,
                                                         double *__restrict__ vel, double h, double half_m,
                                                         double *__restrict__ partials, Drift dr) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double u_i = 0.0, w_i = 0.0, k_i = 0.0;
     float d2 = 0.0f;
+    for (int64_t i0 = (int64_t)blockIdx.x * BLOCK; i0 < n; i0 += (int64_t)gridDim.x * BLOCK) {
+    const int64_t i = i0 + threadIdx.x;
     if (i < n) {
         const int4 xi = xq[i];
         const Seg &S = seg_ref(st, xi.w);
@@ -649,8 +654,8 @@ __global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld
             ea.merged(he, le);
             float hv, lv;
             vir.merged(hv, lv);
-            u_i = (double)he + (double)le;
-            w_i = 0.5 * ((double)hv + (double)lv);
+            u_i += (double)he + (double)le;
+            w_i += 0.5 * ((double)hv + (double)lv);
         }
         f4[i] = make_float4((float)Fx, (float)Fy, (float)Fz, (float)((double)he + (double)le));
         if (vel) {
@@ -660,7 +665,7 @@ __global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld
             double v[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) v[d] = fma(h, f[d], vel[3 * i + d]);
-            if (ENERGY) k_i = half_m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            if (ENERGY) k_i += half_m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
             if (DRIFT) {
                 // the next step's kick and drift, in the same arithmetic as
                 // k_kick_drift2 (the atom's segment is looked up again, so
@@ -679,11 +684,12 @@ __global__ void __launch_bounds__(COL_BLOCK, 3) k_lj_col32(int64_t n, int64_t ld
                 const float ex = fixed_delta(q[0], (uint32_t)ref.x, Sd.sx[0]);
                 const float ey = fixed_delta(q[1], (uint32_t)ref.y, Sd.sx[1]);
                 const float ez = fixed_delta(q[2], (uint32_t)ref.z, Sd.sx[2]);
-                d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                d2 = fmaxf(d2, fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
             }
 #pragma unroll
             for (int d = 0; d < 3; ++d) vel[3 * i + d] = v[d];
         }
+    }
     }
     if (DRIFT) {
 #pragma unroll
@@ -742,21 +748,34 @@ __global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(int64_t n, int64_t ld, c
     if (ENERGY) block_sum3(u_i, w_i, k_i, partials);
 }
 
-int64_t lj_columns_blocks(int64_t n) { return div_up(n, COL_BLOCK); }
+int64_t lj_columns_blocks(int64_t n, const ColShape &shape) {
+    const int64_t nb = div_up(n, shape.block);
+    return shape.grid_cap > 0 ? std::min<int64_t>(nb, shape.grid_cap) : nb;
+}
 
 int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const double *pos64, const SegTable &st,
                const LJConst &c, const int32_t *W, const int32_t *cnt, int32_t max_nbr, int prec, float4 *f4,
-               double *f64, double *vel, double h, double half_m, double *partials, const Drift &drift) {
+               double *f64, double *vel, double h, double half_m, double *partials, const Drift &drift,
+               const ColShape &shape) {
     if (n <= 0) return PPMD_OK;
-    const int64_t nb = lj_columns_blocks(n);
     if (drift.pos_next && (prec != PPMD_FP32 || !vel)) return set_error(ctx, PPMD_ERR_INVALID, "lj_columns: drift needs FP32 and a kick");
     if (prec == PPMD_FP32) {
+        if (shape.block != 128 && shape.block != 256) return set_error(ctx, PPMD_ERR_INVALID, "lj_columns: block %d", shape.block);
+        const int64_t nb = lj_columns_blocks(n, shape);
         const bool e = partials != nullptr, d = drift.pos_next != nullptr;
-        auto kern = e ? (d ? k_lj_col32<true, true> : k_lj_col32<true, false>)
-                      : (d ? k_lj_col32<false, true> : k_lj_col32<false, false>);
-        PPMD_LAUNCH(ctx, kern, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f4, vel, h, half_m, partials,
-                    drift);
+        if (shape.block == 256) {
+            auto kern = e ? (d ? k_lj_col32<true, true, 256> : k_lj_col32<true, false, 256>)
+                          : (d ? k_lj_col32<false, true, 256> : k_lj_col32<false, false, 256>);
+            PPMD_LAUNCH(ctx, kern, nb, 256, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f4, vel, h, half_m, partials,
+                        drift);
+        } else {
+            auto kern = e ? (d ? k_lj_col32<true, true, 128> : k_lj_col32<true, false, 128>)
+                          : (d ? k_lj_col32<false, true, 128> : k_lj_col32<false, false, 128>);
+            PPMD_LAUNCH(ctx, kern, nb, 128, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f4, vel, h, half_m, partials,
+                        drift);
+        }
     } else {
+        const int64_t nb = div_up(n, COL_BLOCK);
         if (partials)
             PPMD_LAUNCH(ctx, k_lj_col64<true>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
                         partials);

@@ -22,10 +22,11 @@ constexpr int ROW_GAP = 3;  // stage slots after each row (candidates are read i
 
 // Brick shape for a segment: the most home atoms up to one per thread whose
 // neighbourhood (with a margin for density fluctuations) fits the stage.
-BrickShape brick_shape(const Seg &S);
+// home_max (at most BRICK_THREADS) bounds the expected home atoms of a brick.
+BrickShape brick_shape(const Seg &S, int32_t home_max = BRICK_THREADS);
 // Bricks of the cell grids of several segments (host).
 // Returns the stage capacity covering every segment.
-int32_t make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out);
+int32_t make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out, int32_t home_max = BRICK_THREADS);
 int64_t brick_count(const Seg &S, BrickShape b);
 // Shared-memory stage (atoms) of a brick of that shape.
 int32_t brick_stage_cap(const Seg &S, BrickShape b);
@@ -57,10 +58,22 @@ struct Drift {
     double dt = 0.0;
     unsigned int *max_disp_bits = nullptr;
 };
+// Launch shape of the FP32 pair loop: threads per block (128 or 256) and,
+// with grid_cap > 0, at most grid_cap blocks, each walking its share of the
+// atoms (a persistent grid); else one thread per atom.  The per-atom
+// arithmetic, and so the trajectory, is the same for every shape; the
+// per-block energy sums (partials) follow the shape.  The FP64 loop always
+// takes the default.
+struct ColShape {
+    int32_t block = 256;
+    int64_t grid_cap = 0;
+};
 int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const double *pos64, const SegTable &st,
                const LJConst &c, const int32_t *W, const int32_t *cnt, int32_t max_nbr, int prec, float4 *f4,
-               double *f64, double *vel, double h, double half_m, double *partials, const Drift &drift = Drift());
-int64_t lj_columns_blocks(int64_t n);
+               double *f64, double *vel, double h, double half_m, double *partials, const Drift &drift = Drift(),
+               const ColShape &shape = ColShape());
+// blocks (and partial rows) of a launch of that shape
+int64_t lj_columns_blocks(int64_t n, const ColShape &shape = ColShape());
 
 // Brick-staged FP32 path (slots.cu).  A list entry is the neighbour's slot
 // (16 bits) in its brick's staged neighbourhood: the cells of the brick's
