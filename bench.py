@@ -123,7 +123,7 @@ class ClockSampler:
 
 def lj_source_sha():
     h = hashlib.sha256()
-    for name in ("md_kernels.cu", "md_kernels.cuh", "lj.cuh", "common.cuh"):
+    for name in ("md_kernels.cu", "md_kernels.cuh", "pair32.cuh", "lj.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1704_03329_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -521,7 +521,10 @@ int ppmd_md_get_list(ppmd_md *md, int32_t *nbr, int32_t *nbr_count, int32_t max_
  *    PPMD_ERR_CAPACITY at once (with a message on stderr), nothing launched.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the process: a
+ *    device reset (cudaDeviceReset, which destroys the primary context and
+ *    the module) invalidates it, so no call may follow a reset of that
+ *    device.
  *  - All calls share the one array, which keeps the last call's contents:
  *    calls whose work overlaps on the GPU (different streams, or different
  *    host threads without ordering) race and give wrong results.

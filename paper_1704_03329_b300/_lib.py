@@ -598,7 +598,22 @@ def ppmd_lj_forces_noalloc(pos, box, nbr, nbr_count, force, e_atom, totals, rc=2
     C status code."""
     if stream is None:
         stream = torch.cuda.current_stream()
-    n = pos.shape[0] if n is None else n
+    # n differs from the arrays' length only to exercise the size limit (the
+    # call refuses it before reading anything)
+    if n is None or n <= NOALLOC_MAX_ATOMS:
+        n = pos.shape[0]
+        if pos.dtype != torch.float64 or tuple(pos.shape) != (n, 3) or not pos.is_contiguous():
+            raise ValueError("pos: contiguous float64 [n][3]")
+        if force.dtype != torch.float64 or tuple(force.shape) != (n, 3) or not force.is_contiguous():
+            raise ValueError("force: contiguous float64 [n][3]")
+        if nbr.dtype != torch.int32 or nbr.dim() != 2 or nbr.shape[0] != n or not nbr.is_contiguous():
+            raise ValueError("nbr: contiguous int32 [n][max_nbr]")
+        if nbr_count.dtype != torch.int32 or tuple(nbr_count.shape) != (n,):
+            raise ValueError("nbr_count: int32 [n]")
+        if e_atom is not None and (e_atom.dtype != torch.float64 or tuple(e_atom.shape) != (n,)):
+            raise ValueError("e_atom: float64 [n]")
+        if totals is not None and (totals.dtype != torch.float64 or totals.numel() < 2):
+            raise ValueError("totals: float64 [2]")
     p = LJParams(eps, sigma, rc, shift)
     b = _box(box)
     max_nbr = nbr.shape[1] if nbr.dim() == 2 else 0
