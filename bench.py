@@ -628,7 +628,8 @@ def suite_analysis(args, L, ctx, stream):
     lab_a = torch.cat(acna_lab)
     frac = {k: float((lab_c == v).float().mean()) for k, v in (("other", 0), ("fcc", 1), ("hcp", 2), ("bcc", 3))}
     frac_a = {k: float((lab_a == v).float().mean()) for k, v in (("other", 0), ("fcc", 1), ("hcp", 2), ("bcc", 3))}
-    res = {"workload": "structure boxes fcc, bcc, hcp, liquid-like x 512,000 atoms, noise 0.05 d_nn; "
+    res = {"workload": "structure boxes of 512,000 atoms: fcc, bcc, hcp with noise 0.05 d_nn and an LJ liquid "
+                       "(rho 0.8442, T 1.5 snapshot tiled); "
                        "BOA cutoff 1.5, CNA cutoff 1.433625, adaptive CNA list 1.8; each timing includes "
                        "cell sort and list build",
            "metric": "classified atoms/s", "atoms": n, "boa_atoms_per_s": n / tb, "cna_atoms_per_s": n / tc,
