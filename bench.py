@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=200)
     ap.add_argument("--otf-steps", type=int, default=540)
     ap.add_argument("--precision-steps", type=int, default=1000)
-    ap.add_argument("--suites", default="replicas,analysis,classifier,otf,precision",
+    ap.add_argument("--suites", default="small,replicas,analysis,classifier,otf,precision",
                     help="extra workloads reported beside the main line (comma list, or 'none')")
     ap.add_argument("--replica-steps", type=int, default=500)
     ap.add_argument("--shape-cache", default=None, help="launch-shape cache file of the replica suite (default: none)")
@@ -453,8 +453,8 @@ def run_ours(args):
     if world == 1:
         suites = [x for x in args.suites.split(",") if x and x != "none"]
         for name in suites:
-            fn = {"replicas": suite_replicas, "analysis": suite_analysis, "classifier": suite_classifier,
-                  "otf": suite_otf, "precision": suite_precision}[name]
+            fn = {"small": suite_small, "replicas": suite_replicas, "analysis": suite_analysis,
+                  "classifier": suite_classifier, "otf": suite_otf, "precision": suite_precision}[name]
             try:
                 k0 = ctx.kernel_count()
                 line[name] = fn(args, L, ctx, stream)
@@ -560,6 +560,50 @@ def suite_precision(args, L, ctx, stream):
                                   "unit": "sigma", "note": "FP32-pair run minus all-FP64 run after the last step"}
     res["missed_pairs_fp32"] = out["fp32"]["missed"]
     return res
+
+
+def suite_small(args, L, ctx, stream):
+    """The small plain-method workload: 1000 atoms (sc 10^3, +-0.05 jitter,
+    T 1.0), all FP64, the list at r_c = 2.5 rebuilt every step, 100 steps
+    replayed from captured graphs.  Latency-bound (a handful of kernels of a
+    few microseconds per step); reported for completeness, with the oracle
+    timed on the same 100 steps on one host thread."""
+    import time
+    import numpy as np
+    import torch
+    from synth import configs
+    c = configs.lj_small()
+    n = len(c["pos"])
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=c["r_list"], rc=c["rc"], rebuild_every=c["rebuild_every"], max_nbr=64,
+              prec=L.FP64, energy_every=10)
+    pos, vel = torch.from_numpy(c["pos"]).cuda(), torch.from_numpy(c["vel"]).cuda()
+    md.set_state(pos, vel)
+    md.run(20)
+    K = c["steps"]
+    ts = []
+    launches = 0
+    for _ in range(5):
+        md.set_state(pos, vel)
+        md.run(10)
+        k0 = ctx.kernel_count()
+        t, _ = _timed(stream, lambda: md.run(K))
+        launches = ctx.kernel_count() - k0
+        ts.append(t)
+    ctx.sync()
+    md.close()
+    t = float(np.median(ts))
+    out = {"workload": "LJ sc 10^3 (1000 atoms), rho 0.8442, rc 2.5, list at rc rebuilt every step, dt 0.005, "
+                       "T 1.0, FP64, 100 steps (graph replays of 10-step units), median of 5 runs",
+           "metric": "atom-steps/s", "value": n * K / t, "unit": UNIT, "atoms": n, "steps": K,
+           "us_per_step": t / K * 1e6, "gpu_launches_timed": launches, "bound": "launch and latency"}
+    if not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.md_run(c["pos"], c["vel"], c["box"], K, rc=c["rc"], r_list=c["r_list"], rebuild_every=c["rebuild_every"])
+        tc = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n * K / tc, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "FP64 C oracle, the same 1000 atoms x 100 steps, 1 thread"}
+    return out
 
 
 def suite_otf(args, L, ctx, stream):
