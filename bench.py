@@ -574,7 +574,7 @@ def suite_small(args, L, ctx, stream):
     from synth import configs
     c = configs.lj_small()
     n = len(c["pos"])
-    md = L.MD(ctx, [0, n], [c["box"]], r_list=c["r_list"], rc=c["rc"], rebuild_every=c["rebuild_every"], max_nbr=64,
+    md = L.MD(ctx, [0, n], [c["box"]], r_list=c["r_list"], rc=c["rc"], rebuild_every=c["rebuild_every"], max_nbr=96,
               prec=L.FP64, energy_every=10)
     pos, vel = torch.from_numpy(c["pos"]).cuda(), torch.from_numpy(c["vel"]).cuda()
     md.set_state(pos, vel)

@@ -104,7 +104,8 @@ struct ppmd_md {
 namespace {
 
 int64_t force_blocks(const ppmd_md *m) {
-    return m->slots ? m->nbricks : lj_columns_blocks(m->n, m->p.prec == PPMD_FP32 ? m->col : ColShape());
+    if (m->slots) return m->nbricks;
+    return m->p.prec == PPMD_FP32 ? lj_columns_blocks(m->n, m->col) : div_up(m->n, lj_col64_block(m->n));
 }
 
 template <class T>
@@ -637,7 +638,7 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt, n);
     // partial rows: the most blocks of any pair-loop shape or brick table
     if (rc == PPMD_OK)
-        rc = md_alloc(m, &m->part_f, 3 * std::max<int64_t>(lj_columns_blocks(n, ColShape{128, 0}), m->nbricks) + 3);
+        rc = md_alloc(m, &m->part_f, 3 * std::max<int64_t>(div_up(n, 64), m->nbricks) + 3);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->red, 4);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->ebuf, 2 * 1024);

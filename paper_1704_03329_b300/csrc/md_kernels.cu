@@ -748,6 +748,11 @@ __global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(int64_t n, int64_t ld, c
     if (ENERGY) block_sum3(u_i, w_i, k_i, partials);
 }
 
+// FP64 runs at a small fraction of the FP32 rate on this part: a system too
+// small to give every SM a 256-thread block takes 64-thread blocks, so
+// that its atoms spread over four times as many SMs.
+int lj_col64_block(int64_t n) { return n < (int64_t)148 * COL_BLOCK ? 64 : COL_BLOCK; }
+
 int64_t lj_columns_blocks(int64_t n, const ColShape &shape) {
     const int64_t nb = div_up(n, shape.block);
     return shape.grid_cap > 0 ? std::min<int64_t>(nb, shape.grid_cap) : nb;
@@ -775,12 +780,13 @@ int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const doubl
                         drift);
         }
     } else {
-        const int64_t nb = div_up(n, COL_BLOCK);
+        const int block = lj_col64_block(n);
+        const int64_t nb = div_up(n, block);
         if (partials)
-            PPMD_LAUNCH(ctx, k_lj_col64<true>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
+            PPMD_LAUNCH(ctx, k_lj_col64<true>, nb, block, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
                         partials);
         else
-            PPMD_LAUNCH(ctx, k_lj_col64<false>, nb, COL_BLOCK, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
+            PPMD_LAUNCH(ctx, k_lj_col64<false>, nb, block, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
                         partials);
     }
     return check_launch(ctx, "lj_columns");

@@ -62,8 +62,8 @@ struct Drift {
 // with grid_cap > 0, at most grid_cap blocks, each walking its share of the
 // atoms (a persistent grid); else one thread per atom.  The per-atom
 // arithmetic, and so the trajectory, is the same for every shape; the
-// per-block energy sums (partials) follow the shape.  The FP64 loop always
-// takes the default.
+// per-block energy sums (partials) follow the shape.  The FP64 loop takes
+// lj_col64_block threads per block.
 struct ColShape {
     int32_t block = 256;
     int64_t grid_cap = 0;
@@ -74,6 +74,8 @@ int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const doubl
                const ColShape &shape = ColShape());
 // blocks (and partial rows) of a launch of that shape
 int64_t lj_columns_blocks(int64_t n, const ColShape &shape = ColShape());
+// threads per block of the FP64 loop for n atoms (64 or 256)
+int lj_col64_block(int64_t n);
 
 // Brick-staged FP32 path (slots.cu).  A list entry is the neighbour's slot
 // (16 bits) in its brick's staged neighbourhood: the cells of the brick's
