@@ -8,7 +8,7 @@ oracle's decision has a margin above that (distance to the tolerance, and
 gap between the nearest and the second-nearest table point).
 
 Gain: on held-out structure boxes of the four kinds at three noise levels,
-labelled by exact CNA (the judge of the classifier's error), the MLP with
+labelled by exact CNA (the reference the classifier is scored against), the MLP with
 its CNA fallback must agree with CNA more often than bond order by
 tolerance does with its best tolerance (chosen on the training boxes).
 """
