@@ -4,7 +4,8 @@ tuning (ppmd_md_tune) on batched replicas.
 - every shape (pair-loop block size, one thread per atom or a persistent
   grid, list-build brick size) gives the default shape's list, positions,
   velocities and forces bit for bit over 23 steps (graph replays and single
-  steps), and the run matches the oracle's forces;
+  steps), and the run matches the oracle's forces; the energies agree to
+  rounding (the per-block sums are grouped by the shape);
 - tuning times the shapes, keeps one, restarts from the state it was given
   (the tuned run equals an untuned run bit for bit), writes the cache, and a
   second tuning of the same workload reads the cache without timing; another
@@ -84,6 +85,25 @@ def test_every_shape_gives_the_same_trajectory(L, ctx, reps):
         Fo = oracle.lj(P[lo:hi], r["box"], offs, nb)[0]
         rms = np.sqrt((Fo ** 2).sum(1).mean())
         assert np.sqrt(((F[lo:hi] - Fo) ** 2).sum(1)).max() / rms <= 1e-5, k
+
+
+def test_energies_agree_across_shapes(L, ctx, reps):
+    """Kinetic and potential energy of every 10th step: the shapes group the
+    per-block sums differently, so the totals agree to rounding (relative
+    1e-12), not bit for bit."""
+    out = []
+    for k in (0, 1, 2, 3):
+        md, off = _md(L, ctx, reps)
+        md.set_shape(k)
+        md.set_state(*_state(reps))
+        e = torch.zeros((30, 2), dtype=torch.float64, device="cuda")
+        md.run(30, e)
+        md.close()
+        out.append(e.cpu().numpy())
+    rows = np.arange(9, 30, 10)  # the energy steps
+    for e in out[1:]:
+        assert np.abs(e[rows] - out[0][rows]).max() <= 1e-12 * np.abs(out[0][rows]).max()
+    assert np.abs(out[0][rows]).min() > 0
 
 
 def test_tune_restarts_from_the_state_and_caches(L, ctx, reps, tmp_path):
