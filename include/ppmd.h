@@ -430,10 +430,10 @@ int ppmd_md_set_pair_loop(ppmd_md *md, int mechanism);
  * blocks per SM, each walking its share of the atoms), and the list build's
  * brick size (up to 128 or 64 expected atoms per brick):
  *   k  block  blocks per SM  brick atoms      k  block  blocks per SM  brick atoms
- *   0  256    one per atom   128              4  256    one per atom   64
- *   1  128    one per atom   128              5  128    one per atom   64
- *   2  256    3 (persistent) 128              6  256    3 (persistent) 64
- *   3  128    6 (persistent) 128              7  128    6 (persistent) 64
+ *   0  128    one per atom   128              4  128    one per atom   64
+ *   1  256    one per atom   128              5  256    one per atom   64
+ *   2  128    7 (persistent) 128              6  128    7 (persistent) 64
+ *   3  256    3 (persistent) 128              7  256    3 (persistent) 64
  * Every shape gives the same list (same pairs in the same order) and the
  * same positions, velocities and forces bit for bit; only the grouping of
  * the energy and virial sums follows the shape (last bits of the totals).

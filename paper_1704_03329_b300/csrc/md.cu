@@ -1074,8 +1074,8 @@ namespace {
 struct ShapeCand {
     int32_t block, per_sm, home;
 };
-constexpr ShapeCand SHAPES[PPMD_MD_SHAPES] = {{256, 0, 128}, {128, 0, 128}, {256, 3, 128}, {128, 6, 128},
-                                              {256, 0, 64},  {128, 0, 64},  {256, 3, 64},  {128, 6, 64}};
+constexpr ShapeCand SHAPES[PPMD_MD_SHAPES] = {{128, 0, 128}, {256, 0, 128}, {128, 7, 128}, {256, 3, 128},
+                                              {128, 0, 64},  {256, 0, 64},  {128, 7, 64},  {256, 3, 64}};
 
 int apply_shape(ppmd_md *m, int32_t k) {
     ppmd_ctx *ctx = m->ctx;
@@ -1104,17 +1104,22 @@ int apply_shape(ppmd_md *m, int32_t k) {
 }
 
 // The workload's shape as a cache key: atoms, boxes, cells, cutoffs, list
-// policy and the device.
+// policy, the device and the candidate table (an entry written for another
+// table never matches).
 std::string shape_key(const ppmd_md *m) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, m->ctx->device);
+    std::string table;
+    for (const ShapeCand &c : SHAPES)
+        table += std::to_string(c.block) + "/" + std::to_string(c.per_sm) + "/" + std::to_string(c.home) + ",";
     char buf[512];
-    snprintf(buf, sizeof(buf), "n=%lld;boxes=%lld;cells=%lld;r_list=%.9g;rc=%.9g;max_nbr=%d;every=%d;dev=%s;sms=%d",
+    snprintf(buf, sizeof(buf), "n=%lld;boxes=%lld;cells=%lld;r_list=%.9g;rc=%.9g;max_nbr=%d;every=%d;dev=%s;sms=%d;shapes=",
              (long long)m->n, (long long)m->nbox, (long long)m->ncell, m->p.r_list, m->p.lj.rc, m->p.max_nbr,
              m->p.rebuild_every, prop.name, prop.multiProcessorCount);
-    for (char *c = buf; *c; ++c)
-        if (*c == '\t' || *c == '\n') *c = ' ';
-    return buf;
+    std::string key = buf + table;
+    for (char &c : key)
+        if (c == '\t' || c == '\n') c = ' ';
+    return key;
 }
 
 }  // namespace

@@ -129,6 +129,11 @@ __device__ __forceinline__ void put_entry(int32_t *W, int64_t ld, int64_t i, int
     else W[(int64_t)e * ld + i] = j;
 }
 
+template <bool B>
+struct Flag {
+    static constexpr bool value = B;
+};
+
 template <bool VEC4>
 __global__ void __launch_bounds__(BRICK_THREADS, 5) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
                                                               const int4 *__restrict__ xq,
@@ -272,6 +277,7 @@ __global__ void __launch_bounds__(BRICK_THREADS, 5) k_neigh_brick(const Brick *_
     __syncthreads();
     const float lo = S.rl2_lo, hi = S.rl2_hi;
     if (fstage) {
+        const f2 lolo = pk(lo, lo), hihi = pk(hi, hi);
         const float rwin = sqrtf((float)S.rl2) * 1.00001f + 1e-5f;
         const ulonglong2 *P2 = reinterpret_cast<const ulonglong2 *>(P);
         int32_t *const ring = s_ring + tid;
@@ -350,48 +356,66 @@ __global__ void __launch_bounds__(BRICK_THREADS, 5) k_neigh_brick(const Brick *_
                 a &= ~1;  // rows start on even slots: a stays in the row
                 if (!act) e = a;
                 const int32_t nstep = __reduce_max_sync(0xffffffffu, (e - a + 3) >> 2);
-                for (int32_t s = 0; s < nstep; ++s) {
-                    const int32_t k = a + 4 * s;
-                    const bool ok = k < e;
-                    // Reads run at most three slots past the window: candidates
-                    // with x beyond the window (never within r_list), atoms two
-                    // cells away, or the row's sentinels.
-                    const int32_t kk = ok ? k : a;
-                    const ulonglong2 A = P2[kk], Bv = P2[kk + 1], C = P2[kk + 2], D = P2[kk + 3];
-                    float r2[4];
-                    {
-                        const f2 dx = sub2(xii, A.x), dy = sub2(yii, A.y), dz = sub2(zii, Bv.x);
-                        upk(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), r2[0], r2[1]);
-                        const f2 ex = sub2(xii, C.x), ey = sub2(yii, C.y), ez = sub2(zii, D.x);
-                        upk(fma2(ex, ex, fma2(ey, ey, mul2(ez, ez))), r2[2], r2[3]);
-                    }
-                    const int32_t jv[4] = {(int32_t)(uint32_t)Bv.y, (int32_t)(uint32_t)(Bv.y >> 32),
-                                           (int32_t)(uint32_t)D.y, (int32_t)(uint32_t)(D.y >> 32)};
-                    bool hit[4], band = false;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const bool other = ok & (k + c != sself);  // not the atom itself
-                        hit[c] = other & (r2[c] < lo);
-                        band |= other & (r2[c] < hi) & !hit[c];
-                    }
-                    if (band) {
-                        // rare: within the FP32 decision band of r_list (FP64
-                        // decides)
+                const int32_t rs = (s_cell[r][bw + 2] + 1) & ~1;  // four of the row's sentinels
+                // center: true for the row of the atom's own cell, the only
+                // one that holds the atom itself (excluded by its stage slot)
+                auto walk = [&](auto center) {
+                    for (int32_t s = 0; s < nstep; ++s) {
+                        const int32_t k = a + 4 * s;
+                        // Reads run at most three slots past the window:
+                        // candidates with x beyond the window (never within
+                        // r_list), atoms two cells away, or the row's
+                        // sentinels; a lane past its window reads sentinels.
+                        const int32_t kk = k < e ? k : rs;
+                        const ulonglong2 A = P2[kk], Bv = P2[kk + 1], C = P2[kk + 2], D = P2[kk + 3];
+                        // sign bits of r^2 - lo (a hit) and of r^2 - hi (below
+                        // the band's top): the sign of a rounded difference is
+                        // exact
+                        uint32_t l[4], h[4];
+                        {
+                            const f2 dx = sub2(xii, A.x), dy = sub2(yii, A.y), dz = sub2(zii, Bv.x);
+                            const f2 r2a = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+                            const f2 ex = sub2(xii, C.x), ey = sub2(yii, C.y), ez = sub2(zii, D.x);
+                            const f2 r2b = fma2(ex, ex, fma2(ey, ey, mul2(ez, ez)));
+                            float t0, t1;
+                            upk(sub2(r2a, lolo), t0, t1);
+                            l[0] = __float_as_uint(t0), l[1] = __float_as_uint(t1);
+                            upk(sub2(r2b, lolo), t0, t1);
+                            l[2] = __float_as_uint(t0), l[3] = __float_as_uint(t1);
+                            upk(sub2(r2a, hihi), t0, t1);
+                            h[0] = __float_as_uint(t0), h[1] = __float_as_uint(t1);
+                            upk(sub2(r2b, hihi), t0, t1);
+                            h[2] = __float_as_uint(t0), h[3] = __float_as_uint(t1);
+                        }
+                        const int32_t jv[4] = {(int32_t)(uint32_t)Bv.y, (int32_t)(uint32_t)(Bv.y >> 32),
+                                               (int32_t)(uint32_t)D.y, (int32_t)(uint32_t)(D.y >> 32)};
+                        uint32_t hit[4];
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
-                            if (!hit[c] && r2[c] < hi && ok && k + c != sself) {
-                                double dr[3];
-                                hit[c] = min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jv[c], S, dr) < S.rl2;
+                            hit[c] = l[c] >> 31;
+                            if (decltype(center)::value) hit[c] &= (uint32_t)(kk + c != sself);
+                        }
+                        if (((h[0] & ~l[0]) | (h[1] & ~l[1]) | (h[2] & ~l[2]) | (h[3] & ~l[3])) >> 31) {
+                            // rare: within the FP32 decision band of r_list
+                            // (FP64 decides; never the atom itself, r^2 = 0)
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                if ((h[c] & ~l[c]) >> 31) {
+                                    double dr[3];
+                                    hit[c] = min_image_r2(pos64 + 3 * (int64_t)i, pos64 + 3 * (int64_t)jv[c], S, dr) < S.rl2;
+                                }
                             }
                         }
-                    }
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        *wp = jv[c];
-                        if (hit[c]) wp += BRICK_THREADS;
+                        for (int c = 0; c < 4; ++c) {
+                            *wp = jv[c];
+                            wp += hit[c] * BRICK_THREADS;
+                        }
+                        if (__any_sync(0xffffffffu, wp >= ring + (RING - 4) * BRICK_THREADS)) flush(false);
                     }
-                    if (__any_sync(0xffffffffu, wp >= ring + (RING - 4) * BRICK_THREADS)) flush(false);
-                }
+                };
+                if (q == 4) walk(Flag<true>());
+                else walk(Flag<false>());
             }
             flush(true);
             if (act) {
@@ -557,8 +581,11 @@ constexpr int COL_BLOCK = 256;
 // One thread per atom; a launch with fewer blocks than atoms / BLOCK (a
 // persistent grid) walks the atoms block by block (grid stride), each
 // thread summing the energy and the largest displacement over its atoms.
+// Registers: 896 threads per SM (72 registers, seven 128-thread blocks) for
+// the steps without energies, 768 (80) for the energy steps, whose sums
+// would spill at 72.
 template <bool ENERGY, bool DRIFT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
+__global__ void __launch_bounds__(BLOCK, (ENERGY ? 768 : 896) / BLOCK) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
                                                         const double *__restrict__ pos64, SegTable st, LJConst c,
                                                         const int32_t *__restrict__ W, const int32_t *__restrict__ cnt,
                                                         int32_t max_nbr, float4 *__restrict__ f4,

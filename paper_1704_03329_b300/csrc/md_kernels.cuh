@@ -18,7 +18,7 @@ struct BrickShape {
 constexpr int NB_MAX = 2048;        // largest neighbourhood staged in shared memory
 constexpr int BRICK_THREADS = 128;  // home atoms handled per pass of a brick block
 constexpr int BW_MAX = 8, BH_MAX = 4, BD_MAX = 2;
-constexpr int ROW_GAP = 3;  // stage slots after each row (candidates are read in fours)
+constexpr int ROW_GAP = 4;  // stage slots after each row (candidates are read in fours from even slots)
 
 // Brick shape for a segment: the most home atoms up to one per thread whose
 // neighbourhood (with a margin for density fluctuations) fits the stage.
@@ -65,7 +65,7 @@ struct Drift {
 // per-block energy sums (partials) follow the shape.  The FP64 loop takes
 // lj_col64_block threads per block.
 struct ColShape {
-    int32_t block = 256;
+    int32_t block = 128;
     int64_t grid_cap = 0;
 };
 int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const double *pos64, const SegTable &st,

@@ -70,7 +70,7 @@ def _run(L, ctx, reps, shape, steps=23):
 
 def test_every_shape_gives_the_same_trajectory(L, ctx, reps):
     ref, info0 = _run(L, ctx, reps, 0)
-    assert info0 == dict(shape=0, block=256, per_sm=0, brick_home=128)
+    assert info0 == dict(shape=0, block=128, per_sm=0, brick_home=128)
     for k in range(1, L.MD_SHAPES):
         got, info = _run(L, ctx, reps, k)
         assert info["shape"] == k
