@@ -511,8 +511,8 @@ def suite_replicas(args, L, ctx, stream):
                              "timed": tune["timed"], "cache": args.shape_cache,
                              "ms_per_step_by_shape": [round(x, 5) for x in tune["ms_per_step"]],
                              "shapes": "k: (block, persistent blocks per SM (0: one thread per atom), brick atoms) = "
-                                       "0 (128,0,128) 1 (256,0,128) 2 (128,7,128) 3 (256,3,128) "
-                                       "4 (128,0,64) 5 (256,0,64) 6 (128,7,64) 7 (256,3,64)"},
+                                       "0 (128,0,128) 1 (256,0,128) 2 (128,8,128) 3 (256,4,128) "
+                                       "4 (128,0,64) 5 (256,0,64) 6 (128,8,64) 7 (256,4,64)"},
             "default_shape_value": n * K / t0}
 
 

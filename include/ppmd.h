@@ -432,8 +432,8 @@ int ppmd_md_set_pair_loop(ppmd_md *md, int mechanism);
  *   k  block  blocks per SM  brick atoms      k  block  blocks per SM  brick atoms
  *   0  128    one per atom   128              4  128    one per atom   64
  *   1  256    one per atom   128              5  256    one per atom   64
- *   2  128    7 (persistent) 128              6  128    7 (persistent) 64
- *   3  256    3 (persistent) 128              7  256    3 (persistent) 64
+ *   2  128    8 (persistent) 128              6  128    8 (persistent) 64
+ *   3  256    4 (persistent) 128              7  256    4 (persistent) 64
  * Every shape gives the same list (same pairs in the same order) and the
  * same positions, velocities and forces bit for bit; only the grouping of
  * the energy and virial sums follows the shape (last bits of the totals).

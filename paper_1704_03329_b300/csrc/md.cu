@@ -1074,8 +1074,8 @@ namespace {
 struct ShapeCand {
     int32_t block, per_sm, home;
 };
-constexpr ShapeCand SHAPES[PPMD_MD_SHAPES] = {{128, 0, 128}, {256, 0, 128}, {128, 7, 128}, {256, 3, 128},
-                                              {128, 0, 64},  {256, 0, 64},  {128, 7, 64},  {256, 3, 64}};
+constexpr ShapeCand SHAPES[PPMD_MD_SHAPES] = {{128, 0, 128}, {256, 0, 128}, {128, 8, 128}, {256, 4, 128},
+                                              {128, 0, 64},  {256, 0, 64},  {128, 8, 64},  {256, 4, 64}};
 
 int apply_shape(ppmd_md *m, int32_t k) {
     ppmd_ctx *ctx = m->ctx;

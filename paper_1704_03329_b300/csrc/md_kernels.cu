@@ -581,11 +581,11 @@ constexpr int COL_BLOCK = 256;
 // One thread per atom; a launch with fewer blocks than atoms / BLOCK (a
 // persistent grid) walks the atoms block by block (grid stride), each
 // thread summing the energy and the largest displacement over its atoms.
-// Registers: 896 threads per SM (72 registers, seven 128-thread blocks) for
-// the steps without energies, 768 (80) for the energy steps, whose sums
-// would spill at 72.
+// Registers: 1024 threads per SM (64 registers; a few words of the
+// epilogue spill, which measured faster than 72 registers at 896 threads)
+// for the steps without energies, 768 (80) for the energy steps.
 template <bool ENERGY, bool DRIFT, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (ENERGY ? 768 : 896) / BLOCK) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
+__global__ void __launch_bounds__(BLOCK, (ENERGY ? 768 : 1024) / BLOCK) k_lj_col32(int64_t n, int64_t ld, const int4 *__restrict__ xq,
                                                         const double *__restrict__ pos64, SegTable st, LJConst c,
                                                         const int32_t *__restrict__ W, const int32_t *__restrict__ cnt,
                                                         int32_t max_nbr, float4 *__restrict__ f4,
@@ -675,7 +675,12 @@ __global__ void __launch_bounds__(BLOCK, (ENERGY ? 768 : 896) / BLOCK) k_lj_col3
         fx.merged(hx, lx);
         fy.merged(hy, ly);
         fz.merged(hz, lz);
-        const double Fx = (double)hx + (double)lx, Fy = (double)hy + (double)ly, Fz = (double)hz + (double)lz;
+        // The force word is hx + lx rounded once to FP32.  The FP32 sum gives
+        // the same float as the FP64 sum rounded to FP32: rounding a sum of
+        // two floats first to 53 bits and then to 24 equals rounding it to 24
+        // bits directly, since 53 >= 2 x 24 + 2 (double rounding is then
+        // innocuous), so no FP64 operation is needed here.
+        const float Fx = hx + lx, Fy = hy + ly, Fz = hz + lz;
         float he = 0.f, le = 0.f;
         if (ENERGY) {
             ea.merged(he, le);
@@ -684,7 +689,7 @@ __global__ void __launch_bounds__(BLOCK, (ENERGY ? 768 : 896) / BLOCK) k_lj_col3
             u_i += (double)he + (double)le;
             w_i += 0.5 * ((double)hv + (double)lv);
         }
-        f4[i] = make_float4((float)Fx, (float)Fy, (float)Fz, (float)((double)he + (double)le));
+        f4[i] = make_float4(Fx, Fy, Fz, he + le);
         if (vel) {
             // second kick of Algorithm 6 with the forces just computed
             const float4 fq = f4[i];

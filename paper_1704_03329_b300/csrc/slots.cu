@@ -603,7 +603,9 @@ __global__ void __launch_bounds__(SLOT_THREADS, 6) k_lj_slots32(const Brick *__r
         fx.merged(hx, lx);
         fy.merged(hy, ly);
         fz.merged(hz, lz);
-        const double Fx = (double)hx + (double)lx, Fy = (double)hy + (double)ly, Fz = (double)hz + (double)lz;
+        // hx + lx rounded once to FP32 (the same float as through FP64: the
+        // double rounding of a sum of two floats is innocuous at 53 bits)
+        const float Fx = hx + lx, Fy = hy + ly, Fz = hz + lz;
         float he = 0.f, le = 0.f;
         if (ENERGY) {
             ea.merged(he, le);
@@ -612,10 +614,10 @@ __global__ void __launch_bounds__(SLOT_THREADS, 6) k_lj_slots32(const Brick *__r
             u_sum += (double)he + (double)le;
             w_sum += 0.5 * ((double)hv + (double)lv);
         }
-        f4[i] = make_float4((float)Fx, (float)Fy, (float)Fz, (float)((double)he + (double)le));
+        f4[i] = make_float4(Fx, Fy, Fz, he + le);
         if (vel) {
             // second kick of Algorithm 6 with the forces just computed
-            const float4 fq = make_float4((float)Fx, (float)Fy, (float)Fz, 0.0f);
+            const float4 fq = make_float4(Fx, Fy, Fz, 0.0f);
             const double f[3] = {(double)fq.x, (double)fq.y, (double)fq.z};
             double v[3];
 #pragma unroll
