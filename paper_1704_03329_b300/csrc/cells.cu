@@ -161,6 +161,88 @@ int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, c
     return check_launch(ctx, "bin_atoms");
 }
 
+// Words of a cell fraction (2^-32 of a cell edge) within which a word is
+// taken to lie on a cell face.
+constexpr uint32_t FACE_MARGIN = 1u << 22;
+
+// The cells of k_bin<false> (FP64 positions, reciprocal of the cell edge)
+// found from the fixed-point words instead.  The word of an axis is the
+// position to within a quantum L 2^-32 (nc units of the cell fraction), and
+// the FP64 product x / w is exact to 2^-52 relative, so away from a cell face
+// (FACE_MARGIN >> nc) the cell c = floor(q nc / 2^32) is the FP64 formula's
+// cell; within the margin (about one atom in 500 per axis) and for
+// non-finite positions the FP64 formula itself decides.  Integer work for
+// almost every atom: FP64 runs at a small fraction of the integer rate here.
+__global__ void k_bin_xq(const int4 *__restrict__ xq, const double *__restrict__ pos, int64_t n, SegTable st,
+                         const int32_t *__restrict__ seg_of, int32_t *__restrict__ cell_of, int32_t *__restrict__ count,
+                         int32_t *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 q = xq[i];
+    const Seg &S = seg_ref(st, seg_of ? seg_of[i] : 0);
+    const uint32_t qw[3] = {(uint32_t)q.x, (uint32_t)q.y, (uint32_t)q.z};
+    int32_t c[3];
+    bool bad = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double x = pos[3 * i + d];
+        const bool finite = ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;  // exponent not all ones
+        const unsigned long long prod = (unsigned long long)qw[d] * (unsigned long long)(uint32_t)S.nc[d];
+        const uint32_t frac = (uint32_t)prod;
+        int32_t cd = (int32_t)(prod >> 32);
+        if (!finite || frac < FACE_MARGIN || frac > 0xffffffffu - FACE_MARGIN) {
+            if (!finite) {
+                bad = true;
+                x = 0.0;
+            }
+            cd = (int32_t)floor(x * S.inv_w[d]);
+            if (x < 0.0 || x >= S.L[d]) cd = (int32_t)floor(wrap_exact(x, S.L[d]) * S.inv_w[d]);
+            cd = cd < 0 ? 0 : (cd > S.nc[d] - 1 ? S.nc[d] - 1 : cd);
+        }
+        c[d] = cd;
+    }
+    if (bad) latch_status(status, PPMD_ERR_NONFINITE);
+    const int32_t cell = S.cell0 + (c[2] * S.nc[1] + c[1]) * S.nc[0] + c[0];
+    cell_of[i] = cell;
+    atomicAdd(&count[cell], 1);
+}
+
+// As k_scatter, the sort key of each slot being the atom's x word relative
+// to the centre of its cell (signed: monotone in x across the cell even
+// where the cell touches the periodic face at x = 0).
+__global__ void k_scatter_xq(int64_t n, const int4 *__restrict__ xq, SegTable st, const int32_t *__restrict__ seg_of,
+                             const int32_t *__restrict__ cell_of, const int32_t *__restrict__ cell_start,
+                             int32_t *__restrict__ cursor, int32_t *__restrict__ cell_atoms, int32_t *__restrict__ key) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Seg &S = seg_ref(st, seg_of ? seg_of[i] : 0);
+    const int32_t c = cell_of[i];
+    const int32_t cx = (c - S.cell0) % S.nc[0];
+    const uint32_t mid = (uint32_t)((((unsigned long long)(2 * cx + 1)) << 31) / (unsigned long long)(uint32_t)S.nc[0]);
+    const int32_t slot = cell_start[c] + atomicAdd(&cursor[c], 1);
+    cell_atoms[slot] = (int32_t)i;
+    key[slot] = (int32_t)((uint32_t)xq[i].x - mid);
+}
+
+int bin_atoms_md(ppmd_ctx *ctx, const int4 *xq, const double *pos, int64_t n, const SegTable &st, const int32_t *seg_of,
+                 int64_t ncell, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms) {
+    cudaStream_t s = ctx->stream;
+    PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cell_start, 0, sizeof(int32_t) * (size_t)(ncell + 1), s), "memset"));
+    if (n > 0)
+        PPMD_LAUNCH(ctx, k_bin_xq, div_up(n, 256), 256, 0, xq, pos, n, st, seg_of, cell_of, cell_start, ctx->d_status);
+    PPMD_TRY(exclusive_scan(ctx, cell_start, cell_start, ncell));
+    if (n > 0) {
+        int32_t *cursor = (int32_t *)scratch(ctx, S_COUNT, sizeof(int32_t) * (size_t)ncell);
+        int32_t *key = (int32_t *)scratch(ctx, S_CELLKEY, sizeof(int32_t) * (size_t)n);
+        int32_t *tmp = (int32_t *)scratch(ctx, S_CELLTMP, sizeof(int32_t) * (size_t)n);
+        if (!cursor || !key || !tmp) return PPMD_ERR_NOMEM;
+        PPMD_TRY(cuda_check(ctx, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)ncell, s), "memset"));
+        PPMD_LAUNCH(ctx, k_scatter_xq, div_up(n, 256), 256, 0, n, xq, st, seg_of, cell_of, cell_start, cursor, tmp, key);
+        PPMD_LAUNCH(ctx, k_rank_cells_x<int32_t>, div_up(n, 256), 256, 0, n, cell_of, cell_start, tmp, key, cell_atoms);
+    }
+    return check_launch(ctx, "bin_atoms_md");
+}
+
 int bin_atoms_fixed(ppmd_ctx *ctx, const int4 *xq, int64_t n, const SegTable &st, int64_t ncell, int32_t *cell_of,
                     int32_t *cell_start, int32_t *cell_atoms) {
     cudaStream_t s = ctx->stream;

@@ -18,4 +18,10 @@ int bin_atoms(ppmd_ctx *ctx, const double *pos, int64_t n, const SegTable &st, c
 // index).  For pipelines that convert to fixed point first.
 int bin_atoms_fixed(ppmd_ctx *ctx, const int4 *xq, int64_t n, const SegTable &st, int64_t ncell, int32_t *cell_of,
                     int32_t *cell_start, int32_t *cell_atoms);
+// The integrator's binning: the cells of bin_atoms(exact = false) for FP64
+// positions pos whose fixed-point words xq (modulo 2^32) are current, found
+// by integer arithmetic except within a hair of a cell face; atoms of a cell
+// ordered by (x word relative to the cell centre, index).
+int bin_atoms_md(ppmd_ctx *ctx, const int4 *xq, const double *pos, int64_t n, const SegTable &st, const int32_t *seg_of,
+                 int64_t ncell, int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms);
 }  // namespace ppmd

@@ -408,17 +408,28 @@ int rebuild(ppmd_md *m) {
     ppmd_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
     const int64_t n = m->n;
-    PPMD_TRY(bin_atoms(ctx, m->pos, n, m->st, m->seg_of, m->ncell, false, m->cell_of, m->cell_start, m->cell_atoms,
-                       true));
-    PPMD_TRY(md_gather(ctx, n, m->cell_atoms, m->st, m->pos, m->vel, m->orig, m->seg_of, m->pos_t, m->vel_t, m->xq_t,
-                       m->orig_t, m->seg_t));
+    // the fixed-point words are current here (set-up, the kick and drift,
+    // or a pair loop with the drift fused in made them)
+    PPMD_TRY(bin_atoms_md(ctx, m->xq, m->pos, n, m->st, m->seg_of, m->ncell, m->cell_of, m->cell_start, m->cell_atoms));
     const bool check = m->check && m->have_ref && n > 0;
+    // the previous build's words in the new order, before they are replaced
     if (check) PPMD_LAUNCH(ctx, k_gather_xq, div_up(n, 256), 256, 0, n, m->cell_atoms, m->xq_ref, m->xq_old);
+    // The sorted state goes to buffer 0.  With the positions in buffer 1
+    // (the fused steps of a rebuild period of even length flip the buffers an
+    // odd number of times; a captured period finds the same buffer at every
+    // replay) the gather writes buffer 0 directly, otherwise through the
+    // temporaries.
+    const bool direct = m->cur == 1;
+    PPMD_TRY(md_gather(ctx, n, m->cell_atoms, m->st, m->pos, m->vel, m->orig, m->seg_of, m->xq,
+                       direct ? m->pos_buf[0] : m->pos_t, m->vel_t, direct ? m->xq_buf[0] : m->xq_t, m->xq_ref,
+                       m->orig_t, m->seg_t));
     use_buffer(m, 0);
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, m->pos_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    if (!direct) {
+        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, m->pos_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s),
+                            "copy"));
+        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    }
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, m->vel_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq_ref, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     m->have_ref = true;

@@ -74,12 +74,13 @@ int32_t make_bricks(const std::vector<Seg> &segs, std::vector<Brick> &out, int32
 
 size_t neigh_brick_smem(int32_t) { return (size_t)NB_MAX * sizeof(int4); }
 
-// Staged atoms of a brick: the expected neighbourhood count with a 1.5x
-// margin (denser bricks read the global arrays instead), so that bricks of
-// sparse grids leave room for more resident blocks.
+// Staged atoms of a brick: the expected neighbourhood count with a 1.25x
+// margin (for a neighbourhood of ~1200 atoms, a Poisson count would exceed
+// it only ~9 standard deviations above its mean; denser bricks read the
+// global arrays instead), so that six list-build blocks share an SM.
 int32_t brick_stage_cap(const Seg &S, BrickShape b) {
     const double pc = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
-    const double need = 1.5 * pc * (b.bw + 2) * (b.bh + 2) * (b.bd + 2) + (ROW_GAP + 1) * (b.bh + 2) * (b.bd + 2);
+    const double need = 1.25 * pc * (b.bw + 2) * (b.bh + 2) * (b.bd + 2) + (ROW_GAP + 1) * (b.bh + 2) * (b.bd + 2);
     const int64_t cap = ((int64_t)ceil(need) + 63) / 64 * 64;
     return (int32_t)std::max<int64_t>(64, std::min<int64_t>(NB_MAX, cap));
 }
@@ -135,7 +136,7 @@ struct Flag {
 };
 
 template <bool VEC4>
-__global__ void __launch_bounds__(BRICK_THREADS, 5) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
+__global__ void __launch_bounds__(BRICK_THREADS, 6) k_neigh_brick(const Brick *__restrict__ bricks, BrickShape shape,
                                                               const int4 *__restrict__ xq,
                                                               const double *__restrict__ pos64, SegTable st,
                                                               const int32_t *__restrict__ cs, int32_t *__restrict__ W,
@@ -888,35 +889,49 @@ int md_kick_drift2(ppmd_ctx *ctx, int64_t n, double *pos, double *vel, const flo
     return check_launch(ctx, "md_kick_drift2");
 }
 
+// With xq (the current fixed-point words, modulo 2^32 already those of the
+// wrapped positions to within a quantum) the words are gathered; without,
+// they are made from the wrapped positions.  The in-box test runs on the
+// FP64 bit patterns (for x >= 0 their order is that of the values; -0.0
+// counts as inside, as in the comparison x >= 0.0), so an atom that stays
+// in the box takes no FP64 operation.
 __global__ void k_md_gather(int64_t n, const int32_t *__restrict__ perm, SegTable st, const double *__restrict__ pos,
                             const double *__restrict__ vel, const int32_t *__restrict__ orig,
-                            const int32_t *__restrict__ seg_of, double *__restrict__ pos_o, double *__restrict__ vel_o,
-                            int4 *__restrict__ xq_o, int32_t *__restrict__ orig_o, int32_t *__restrict__ seg_o) {
+                            const int32_t *__restrict__ seg_of, const int4 *__restrict__ xq, double *__restrict__ pos_o,
+                            double *__restrict__ vel_o, int4 *__restrict__ xq_o, int4 *__restrict__ xq_o2,
+                            int32_t *__restrict__ orig_o, int32_t *__restrict__ seg_o) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t j = perm[k];
     const int32_t sid = seg_of[j];
     const Seg &S = seg_ref(st, sid);
     uint32_t q[3];
+    int4 qj = make_int4(0, 0, 0, 0);
+    if (xq) qj = xq[j];
+    const uint32_t qin[3] = {(uint32_t)qj.x, (uint32_t)qj.y, (uint32_t)qj.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         double x = pos[3 * j + d];
-        x = (x >= 0.0 && x < S.L[d]) ? x : wrap_exact(x, S.L[d]);
+        const long long b = __double_as_longlong(x);
+        const bool inside = b >= 0 ? b < __double_as_longlong(S.L[d]) : b == (long long)0x8000000000000000ull;
+        if (!inside) x = wrap_exact(x, S.L[d]);
         pos_o[3 * k + d] = x;
         vel_o[3 * k + d] = vel[3 * j + d];
-        q[d] = to_fixed(x, S.fxs[d]);
+        q[d] = xq ? qin[d] : to_fixed(x, S.fxs[d]);
     }
-    xq_o[k] = make_int4((int)q[0], (int)q[1], (int)q[2], sid);
+    const int4 w = make_int4((int)q[0], (int)q[1], (int)q[2], sid);
+    xq_o[k] = w;
+    if (xq_o2) xq_o2[k] = w;
     orig_o[k] = orig[j];
     seg_o[k] = sid;
 }
 
 int md_gather(ppmd_ctx *ctx, int64_t n, const int32_t *perm, const SegTable &st, const double *pos, const double *vel,
-              const int32_t *orig, const int32_t *seg_of, double *pos_o, double *vel_o, int4 *xq_o, int32_t *orig_o,
-              int32_t *seg_o) {
+              const int32_t *orig, const int32_t *seg_of, const int4 *xq, double *pos_o, double *vel_o, int4 *xq_o,
+              int4 *xq_o2, int32_t *orig_o, int32_t *seg_o) {
     if (n > 0)
-        PPMD_LAUNCH(ctx, k_md_gather, div_up(n, 256), 256, 0, n, perm, st, pos, vel, orig, seg_of, pos_o, vel_o, xq_o, orig_o,
-                    seg_o);
+        PPMD_LAUNCH(ctx, k_md_gather, div_up(n, 256), 256, 0, n, perm, st, pos, vel, orig, seg_of, xq, pos_o, vel_o, xq_o,
+                    xq_o2, orig_o, seg_o);
     return check_launch(ctx, "md_gather");
 }
 

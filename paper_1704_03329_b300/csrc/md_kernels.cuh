@@ -112,8 +112,10 @@ int md_kick_drift2(ppmd_ctx *ctx, int64_t n, double *pos, double *vel, const flo
                    const int4 *xq_ref, const SegTable &st, double h, double dt, unsigned int *max_disp_bits);
 
 // Gather through perm into cell order, wrapping positions into the box.
+// With xq the fixed-point words are gathered (else made from the wrapped
+// positions); xq_o2 (may be null) receives a second copy of them.
 int md_gather(ppmd_ctx *ctx, int64_t n, const int32_t *perm, const SegTable &st, const double *pos, const double *vel,
-              const int32_t *orig, const int32_t *seg_of, double *pos_o, double *vel_o, int4 *xq_o, int32_t *orig_o,
-              int32_t *seg_o);
+              const int32_t *orig, const int32_t *seg_of, const int4 *xq, double *pos_o, double *vel_o, int4 *xq_o,
+              int4 *xq_o2, int32_t *orig_o, int32_t *seg_o);
 
 }  // namespace ppmd
