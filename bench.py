@@ -122,9 +122,20 @@ class ClockSampler:
 
 
 def lj_source_sha():
+    """Hash of the FP32 pair loop's source: the kernel and its helpers in
+    md_kernels.cu (from the block sums to the FP64 loop), its launch in
+    lj_columns, and the headers it includes."""
     h = hashlib.sha256()
-    for name in ("md_kernels.cu", "md_kernels.cuh", "pair32.cuh", "lj.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_1704_03329_b300", "csrc", name), "rb") as f:
+    csrc = os.path.join(ROOT, "paper_1704_03329_b300", "csrc")
+    with open(os.path.join(csrc, "md_kernels.cu")) as f:
+        src = f.read()
+    a = src.index("__device__ __forceinline__ void block_sum3(")
+    b = src.index("__global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(")
+    c = src.index("int lj_columns(")
+    h.update(src[a:b].encode())
+    h.update(src[c:src.index("\n}\n", c)].encode())
+    for name in ("md_kernels.cuh", "pair32.cuh", "lj.cuh", "common.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
