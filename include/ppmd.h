@@ -187,8 +187,8 @@ int ppmd_lj_forces_newton3(ppmd_ctx *ctx, const double *pos, int64_t n, const pp
 
 /* Velocity Verlet particle loops, Algorithm 6 and Listings
  * "position_update" / "velocity_update":
- *   phase 1 (line 6): v += dt/(2m) F;  r += dt v;  r wrapped into the box
- *   phase 2 (line 8): v += dt/(2m) F
+ *   phase 1 (first half kick, drift): v += dt/(2m) F;  r += dt v;  r wrapped
+ *   phase 2 (second half kick, after the forces): v += dt/(2m) F
  * pos and vel are updated in place (pos is not touched in phase 2). */
 int ppmd_verlet_step(ppmd_ctx *ctx, int phase, double *pos, double *vel, const double *force, int64_t n,
                      const ppmd_box *box, double mass, double dt);
@@ -491,8 +491,8 @@ int ppmd_md_get_state(ppmd_md *md, double *pos, double *vel, double *force);
  * largest displacement since a rebuild seen so far.  Synchronises; returns
  * PPMD_WARN_SKIN when that displacement exceeded half the list skin. */
 int ppmd_md_info(ppmd_md *md, int64_t *steps, int64_t *rebuilds, double *max_disp);
-/* Recompute the forces of the current state (the pair loop alone, line 7 of
- * Algorithm 6), e.g. to time it; the state is otherwise unchanged. */
+/* Recompute the forces of the current state (the pair loop alone, the force
+ * step of Algorithm 6), e.g. to time it; the state is otherwise unchanged. */
 int ppmd_md_forces(ppmd_md *md);
 /* Current neighbour list (host outputs, may be NULL): total listed pairs and
  * the largest row.  Synchronises. */

@@ -248,8 +248,8 @@ void ora_lj(int64_t n, const double *pos, const double *L, double eps, double si
 
 /* ------------------------------------------------------------------ */
 /* Velocity Verlet, Algorithm 6.
- *   phase 1 (line 6): v += dt/(2m) F ; r += dt v ; then wrap r into the box
- *   phase 2 (line 8): v += dt/(2m) F                                    */
+ *   phase 1 (first half kick, drift): v += dt/(2m) F ; r += dt v ; then wrap
+ *   phase 2 (second half kick, after the forces): v += dt/(2m) F        */
 /* ------------------------------------------------------------------ */
 
 void ora_vv(int phase, int64_t n, double *pos, double *vel, const double *F, const double *L, double mass,

@@ -826,7 +826,7 @@ int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const doubl
 }
 
 // ---------------------------------------------------------------------
-// Kick + drift (line 6 of Algorithm 6).
+// Kick + drift (the first half kick and the drift of Algorithm 6).
 // ---------------------------------------------------------------------
 template <class F>
 __device__ __forceinline__ void load_f(const F *f, int64_t i, double out[3]);
