@@ -472,13 +472,16 @@ int ppmd_md_tune(ppmd_md *md, int32_t steps, const char *cache_path, int32_t *sh
  * (synchronises).  Uses 16 extra bytes of device memory per atom. */
 int ppmd_md_set_check(ppmd_md *md, int on);
 int ppmd_md_missed_pairs(ppmd_md *md, int64_t *missed);
-/* Measurement aid: with on != 0, the CUDA graphs of later runs record a CUDA
- * event before and after every pair-loop launch (event-record graph nodes,
- * on the integrator's stream); ppmd_md_pair_loop_times then returns the
- * average duration (ms) of the pair loops of the last replayed graph, those
+/* Measurement aid: with on != 0, the last whole graph unit of each later run
+ * replays a second graph that records a CUDA event before and after every
+ * pair-loop launch (event-record graph nodes, on the integrator's stream;
+ * the other units replay the graph without them, so the events cost the
+ * run one unit's worth of nodes); ppmd_md_pair_loop_times then returns the
+ * average duration (ms) of the pair loops of the last timed unit, those
  * that also made the next step's kick and drift (fused, FP32) and the
  * others, with their counts (host outputs, any may be NULL).  Synchronises.
- * PPMD_ERR_INVALID when no timed graph has run. */
+ * PPMD_ERR_INVALID when no timed unit has run.  A run of several units
+ * captures both graphs on first use. */
 int ppmd_md_time_pair_loops(ppmd_md *md, int on);
 int ppmd_md_pair_loop_times(ppmd_md *md, double *ms_fused, int32_t *n_fused, double *ms_other, int32_t *n_other);
 /* Per-atom Q4, Q5, Q6 of the last analysis step (device float [n] each,

@@ -52,6 +52,7 @@ struct ppmd_md {
     // ev[2 (k - 1)], ev[2 (k - 1) + 1]; ev_fused[k - 1]: that launch also
     // made the next step's kick and drift
     bool time_pair = false;
+    bool rec_events = false;  // capturing the graph with the events
     std::vector<cudaEvent_t> ev;
     std::vector<char> ev_fused;
     int32_t ev_steps = 0;
@@ -81,9 +82,12 @@ struct ppmd_md {
     bool ready = false;
     // graphs
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    // exec: the unit's graph; exec_ev: the same with the pair-loop events
+    // (replayed only as the last unit of a run, so that the event-record
+    // nodes leave the other replays undisturbed)
+    cudaGraphExec_t exec = nullptr, exec_ev = nullptr;
     int32_t graph_steps = 0;
-    int64_t graph_kernels = 0;
+    int64_t graph_kernels = 0, graph_kernels_ev = 0;
     // on-the-fly analysis run (Sec. 5.3): Andersen thermostat and Q4/Q5/Q6
     uint64_t thermo_thr = 0, thermo_seed = 0;
     double thermo_sd = 0.0, Lmax = 0.0;
@@ -501,7 +505,7 @@ int one_step(ppmd_md *m, int64_t s, double *erow, bool fuse_next, double *qrow =
     // with the next step's kick and drift fused in, the step's positions
     // stay in the other buffer (prev) for the thermostat and the analysis
     const bool fused = fuse_next && f32;
-    const bool timed = m->time_pair && base && s >= 1 && 2 * s <= (int64_t)m->ev.size();
+    const bool timed = m->rec_events && base && s >= 1 && 2 * s <= (int64_t)m->ev.size();
     // during stream capture, only an external record becomes an event-record node
     if (timed)
         PPMD_TRY(cuda_check(ctx, cudaEventRecordWithFlags(m->ev[2 * (s - 1)], ctx->stream, cudaEventRecordExternal),
@@ -679,6 +683,7 @@ extern "C" int ppmd_md_destroy(ppmd_md *m) {
         cudaStreamSynchronize(m->ctx->stream);
     }
     if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->exec_ev) cudaGraphExecDestroy(m->exec_ev);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
     for (void *q : m->allocs) cudaFree(q);
@@ -762,7 +767,12 @@ extern "C" int ppmd_md_run_analysed(ppmd_md *m, int32_t nsteps, double *energies
     while (done < nsteps) {
         const int64_t s0 = m->step;
         if (graph_ok && s0 % unit == 0 && nsteps - done >= unit) {
-            if (!m->exec) {
+            // with pair-loop timing on, the run's last whole unit replays the
+            // graph that records the events
+            const bool with_ev = m->time_pair && nsteps - done < 2 * unit;
+            cudaGraphExec_t &exec = with_ev ? m->exec_ev : m->exec;
+            int64_t &graph_kernels = with_ev ? m->graph_kernels_ev : m->graph_kernels;
+            if (!exec) {
                 // capture one unit of whole rebuild periods on a private stream
                 if (!m->cap_stream)
                     PPMD_TRY(cuda_check(ctx, cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking), "stream"));
@@ -774,8 +784,10 @@ extern "C" int ppmd_md_run_analysed(ppmd_md *m, int32_t nsteps, double *energies
                 int rc = cuda_check(ctx, cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal), "capture");
                 // a unit starts and ends with full-step velocities; inside it
                 // each pair loop makes the next step's kick and drift
+                m->rec_events = with_ev;
                 for (int32_t k = 1; rc == PPMD_OK && k <= unit; ++k)
                     rc = one_step(m, k, m->ebuf + 2 * (k - 1), k < unit, m->qbuf + 3 * (k - 1), m->d_base);
+                m->rec_events = false;
                 cudaError_t e = cudaStreamEndCapture(m->cap_stream, &g);
                 ctx->stream = user;
                 if (rc != PPMD_OK) {
@@ -783,16 +795,16 @@ extern "C" int ppmd_md_run_analysed(ppmd_md *m, int32_t nsteps, double *energies
                     return rc;
                 }
                 PPMD_TRY(cuda_check(ctx, e, "end capture"));
-                e = cudaGraphInstantiate(&m->exec, g, 0);
+                e = cudaGraphInstantiate(&exec, g, 0);
                 cudaGraphDestroy(g);
                 PPMD_TRY(cuda_check(ctx, e, "graph instantiate"));
                 m->graph_steps = unit;
-                m->graph_kernels = ctx->launches - k0;
+                graph_kernels = ctx->launches - k0;
                 ctx->launches = k0;
             }
             PPMD_LAUNCH(ctx, k_set_i64, 1, 1, 0, m->d_base, s0);  // step numbers of the replayed unit
-            PPMD_TRY(cuda_check(ctx, cudaGraphLaunch(m->exec, ctx->stream), "graph launch"));
-            ctx->launches += m->graph_kernels;
+            PPMD_TRY(cuda_check(ctx, cudaGraphLaunch(exec, ctx->stream), "graph launch"));
+            ctx->launches += graph_kernels;
             if (qrows && B > 0) {
                 for (int32_t k = 1; k <= unit; ++k)
                     if ((k % B) == 0)
@@ -910,10 +922,12 @@ __global__ void k_list_stats(const int32_t *cnt, int64_t n, unsigned long long *
 
 namespace {
 void drop_graph(ppmd_md *m) {
-    if (m->exec) {
-        cudaStreamSynchronize(m->ctx->stream);
-        cudaGraphExecDestroy(m->exec);
-        m->exec = nullptr;
+    for (cudaGraphExec_t *x : {&m->exec, &m->exec_ev}) {
+        if (*x) {
+            cudaStreamSynchronize(m->ctx->stream);
+            cudaGraphExecDestroy(*x);
+            *x = nullptr;
+        }
     }
 }
 }  // namespace
@@ -1015,7 +1029,7 @@ extern "C" int ppmd_md_pair_loop_times(ppmd_md *m, double *ms_fused, int32_t *n_
                                        int32_t *n_other) {
     if (!m) return PPMD_ERR_INVALID;
     ppmd_ctx *ctx = m->ctx;
-    if (!m->time_pair || !m->exec)
+    if (!m->time_pair || !m->exec_ev)
         return set_error(ctx, PPMD_ERR_INVALID, "ppmd_md_pair_loop_times: no timed graph replay yet");
     cudaSetDevice(ctx->device);
     PPMD_TRY(cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sync"));

@@ -182,17 +182,29 @@ def test_pair_loop_mechanism_is_chosen_before_set_state(L, ctx):
 
 
 def test_pair_loop_event_times(L, ctx):
-    """The measurement aid: event-record nodes around the pair loops of a
-    replayed graph give positive durations: per 10-step unit, nine pair
-    loops fused with the next step's kick and drift and one other (the
-    unit's last step, here also the energy step)."""
+    """The measurement aid: event-record nodes around the pair loops of the
+    run's last replayed unit give positive durations: per 10-step unit, nine
+    pair loops fused with the next step's kick and drift and one other (the
+    unit's last step, here also the energy step).  The graph with the events
+    and the one without give the same trajectory bit for bit."""
     c = configs.lj_solid(n_cells=10)
     n = len(c["pos"])
-    md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP32,
-              energy_every=10)
-    md.time_pair_loops(True)
-    md.set_state(cu(c["pos"]), cu(c["vel"]))
-    md.run(20)
-    tf, nf, to, no = md.pair_loop_times()
+
+    def run(timed, steps):
+        md = L.MD(ctx, [0, n], [c["box"]], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP32,
+                  energy_every=10)
+        if timed:
+            md.time_pair_loops(True)
+        md.set_state(cu(c["pos"]), cu(c["vel"]))
+        md.run(steps)
+        times = md.pair_loop_times() if timed else None
+        out = [torch.empty((n, 3), dtype=torch.float64, device="cuda") for _ in range(3)]
+        md.get_state(*out)
+        md.close()
+        return times, [x.cpu().numpy() for x in out]
+
+    (tf, nf, to, no), timed = run(True, 30)
     assert nf == 9 and no == 1 and tf > 0 and to > 0, (tf, nf, to, no)
-    md.close()
+    _, plain = run(False, 30)
+    for a, b in zip(timed, plain):
+        assert np.array_equal(a, b)
