@@ -628,3 +628,37 @@ def test_md_check_leaves_the_trajectory_unchanged(L, ctx):
         md.close()
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == 0  # no count without the check
+
+
+def test_md_lists_with_atoms_on_cell_faces(L, ctx):
+    """Atoms on the faces of the list cells: a simple-cubic lattice of
+    spacing half the cell edge (every coordinate an exact binary fraction,
+    pairs at exactly r_list), some atoms moved 2^-40 off a face, some just
+    below the box face.  The integrator's lists at set-up and at the rebuild
+    after 10 steps (the lattice at rest stays on the faces) are the oracle's
+    sets; pairs at exactly r_list are not listed (strict cutoff)."""
+    a, m = 1.375, 12
+    edge = a * m  # 16.5: six cells of 2.75 = r_list
+    g = np.arange(m) * a
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(5)
+    k = rng.choice(len(pos), 200, replace=False)
+    pos[k[:100], 0] += np.where(rng.random(100) < 0.5, 1.0, -1.0) * 2.0 ** -40
+    pos[k[100:150], 1] -= 2.0 ** -40
+    pos[pos < 0] += edge  # just below the box face
+    box = np.array([edge] * 3)
+    n = len(pos)
+    md = L.MD(ctx, [0, n], [box], r_list=2.75, rc=2.5, rebuild_every=10, max_nbr=128, prec=L.FP32)
+    md.set_state(cu(pos), cu(np.zeros_like(pos)))
+    for steps in (0, 10):
+        md.run(steps)
+        p = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        md.get_state(p)
+        P = p.cpu().numpy()
+        nbr, cnt = md.get_list()
+        offs, nb = oracle.neighbours_brute(P, box, 2.75)
+        assert np.array_equal(cnt.cpu().numpy(), np.diff(offs)), steps
+        got = rows_as_sets(nbr, cnt)
+        for i in range(n):
+            assert np.array_equal(got[i], nb[offs[i]:offs[i + 1]]), (steps, i)
+    md.close()
