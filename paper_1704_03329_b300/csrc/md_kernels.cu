@@ -103,7 +103,9 @@ __device__ __forceinline__ int32_t wrapi(int32_t v, int32_t n) { return v < 0 ? 
 // thread owns one home atom; the 32 home atoms of a warp are consecutive in
 // one x-row of home cells, so their windows have nearly the same length.  The
 // warp walks row q of all its atoms together, four candidates per step (two
-// packed pairs), for the longest window of the warp.  Hits go to a ring of
+// packed pairs), for the longest window of the warp (a lane past its own
+// window reads the row's sentinels).  A candidate's tests are the sign bits
+// of two packed differences, r^2 - lo and r^2 - hi.  Hits go to a ring of
 // RING entries per thread in shared memory and are written out in groups of
 // four (one 16-byte store per group in the grouped layout) whenever a ring of
 // the warp fills up: no per-hit branch.
