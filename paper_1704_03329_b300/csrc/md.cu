@@ -428,14 +428,20 @@ int rebuild(ppmd_md *m) {
                        direct ? m->pos_buf[0] : m->pos_t, m->vel_t, direct ? m->xq_buf[0] : m->xq_t, m->xq_ref,
                        m->orig_t, m->seg_t));
     use_buffer(m, 0);
-    if (!direct) {
-        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, m->pos_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s),
+    if (n > 0) {
+        if (!direct) {
+            PPMD_TRY(cuda_check(
+                ctx, cudaMemcpyAsync(m->pos, m->pos_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+            PPMD_TRY(
+                cuda_check(ctx, cudaMemcpyAsync(m->xq, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+        }
+        PPMD_TRY(
+            cuda_check(ctx, cudaMemcpyAsync(m->vel, m->vel_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+        PPMD_TRY(
+            cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
+        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s),
                             "copy"));
-        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->xq, m->xq_t, sizeof(int4) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     }
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, m->vel_t, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->orig, m->orig_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->seg_of, m->seg_t, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s), "copy"));
     m->have_ref = true;
     if (m->slots) {
         PPMD_TRY(build_slot_list(ctx, m->nbricks, m->bricks, m->xq, m->pos, m->st, m->cell_start, m->W16, m->ld, m->cnt,
@@ -733,8 +739,10 @@ extern "C" int ppmd_md_set_state(ppmd_md *m, const double *pos, const double *ve
     cudaStream_t s = ctx->stream;
     use_buffer(m, 0);
     m->half_kicked = false;
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
-    PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    if (n > 0) {
+        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->pos, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+        PPMD_TRY(cuda_check(ctx, cudaMemcpyAsync(m->vel, vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s), "copy"));
+    }
     if (n > 0)
         PPMD_LAUNCH(ctx, k_init_state, div_up(n, 256), 256, 0, n, m->pos, m->d_atom_off, m->nbox, m->st, m->xq, m->orig,
                     m->seg_of, ctx->d_status);
@@ -897,8 +905,9 @@ extern "C" int ppmd_md_get_list(ppmd_md *m, int32_t *nbr, int32_t *nbr_count, in
                                 m->stage_cap, w, m->n));
         W = w;
     }
-    PPMD_LAUNCH(ctx, k_list_out, div_up(m->n, 256), 256, 0, m->n, m->orig, W, m->cnt, m->p.max_nbr, m->ld, nbr,
-                nbr_count, max_nbr);
+    if (m->n > 0)
+        PPMD_LAUNCH(ctx, k_list_out, div_up(m->n, 256), 256, 0, m->n, m->orig, W, m->cnt, m->p.max_nbr, m->ld, nbr,
+                    nbr_count, max_nbr);
     return check_launch(ctx, "ppmd_md_get_list");
 }
 

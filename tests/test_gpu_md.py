@@ -662,3 +662,49 @@ def test_md_lists_with_atoms_on_cell_faces(L, ctx):
         for i in range(n):
             assert np.array_equal(got[i], nb[offs[i]:offs[i + 1]]), (steps, i)
     md.close()
+
+
+def test_md_without_atoms(L, ctx):
+    """A system of no atoms: set-up, graph units and single steps, energy
+    rows, state and list reads all succeed; the energies are zero."""
+    box = np.array([9.0, 9.5, 10.0])
+    md = L.MD(ctx, [0, 0], [box], r_list=2.8, rc=2.5, rebuild_every=10, max_nbr=64, prec=L.FP32, energy_every=10)
+    md.set_state(cu(np.zeros((0, 3))), cu(np.zeros((0, 3))))
+    en = torch.ones((23, 2), dtype=torch.float64, device="cuda")
+    md.run(23, en)
+    p = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    md.get_state(p, p, p)
+    nbr, cnt = md.get_list()
+    info = md.info()
+    md.close()
+    assert nbr.shape[0] == 0 and cnt.shape[0] == 0 and info["steps"] == 23
+    e = en.cpu().numpy()
+    assert (e[[9, 19]] == 0).all()
+
+
+def test_md_empty_box_among_replicas(L, ctx):
+    """An empty box between replicas changes nothing: positions and
+    velocities of the others are those of the run without it, bit for bit."""
+    reps = configs.replicas(seed=4, nrep=3, n_min=600, n_max=3000)
+    pos = np.concatenate([r["pos"] for r in reps])
+    vel = np.concatenate([r["vel"] for r in reps])
+    sizes = [len(r["pos"]) for r in reps]
+    out = []
+    for with_empty in (False, True):
+        boxes = [r["box"] for r in reps]
+        rl = [r["r_list"] for r in reps]
+        sz = list(sizes)
+        if with_empty:
+            boxes.insert(1, np.array([9.0, 9.0, 9.0]))
+            rl.insert(1, 2.8)
+            sz.insert(1, 0)
+        off = np.cumsum([0] + sz)
+        md = L.MD(ctx, off, boxes, r_list=2.8, rebuild_every=10, max_nbr=128, prec=L.FP32, box_r_list=rl)
+        md.set_state(cu(pos), cu(vel))
+        md.run(23)
+        P = torch.empty((off[-1], 3), dtype=torch.float64, device="cuda")
+        V = torch.empty_like(P)
+        md.get_state(P, V)
+        md.close()
+        out.append((P.cpu().numpy(), V.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
