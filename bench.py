@@ -123,18 +123,23 @@ class ClockSampler:
 
 def lj_source_sha():
     """Hash of the FP32 pair loop's source: the kernel and its helpers in
-    md_kernels.cu (from the block sums to the FP64 loop), its launch in
-    lj_columns, and the headers it includes."""
+    md_kernels.cu (from the block sums to the end of k_lj_col32), its
+    launch (the FP32 branch of lj_columns), its launch-shape struct and the
+    headers it includes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1704_03329_b300", "csrc")
     with open(os.path.join(csrc, "md_kernels.cu")) as f:
         src = f.read()
     a = src.index("__device__ __forceinline__ void block_sum3(")
-    b = src.index("__global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(")
-    c = src.index("int lj_columns(")
+    b = src.index("\n}\n", src.index(" k_lj_col32(", a))
     h.update(src[a:b].encode())
-    h.update(src[c:src.index("\n}\n", c)].encode())
-    for name in ("md_kernels.cuh", "pair32.cuh", "lj.cuh", "common.cuh"):
+    c = src.index("if (prec == PPMD_FP32) {", src.index("int lj_columns("))
+    h.update(src[c:src.index("} else {", c)].encode())
+    with open(os.path.join(csrc, "md_kernels.cuh")) as f:
+        hdr = f.read()
+    d = hdr.index("struct ColShape {")
+    h.update(hdr[d:hdr.index("};", d)].encode())
+    for name in ("pair32.cuh", "lj.cuh", "common.cuh"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -109,7 +109,7 @@ namespace {
 
 int64_t force_blocks(const ppmd_md *m) {
     if (m->slots) return m->nbricks;
-    return m->p.prec == PPMD_FP32 ? lj_columns_blocks(m->n, m->col) : div_up(m->n, lj_col64_block(m->n));
+    return m->p.prec == PPMD_FP32 ? lj_columns_blocks(m->n, m->col) : div_up(m->n, lj_col64_atoms_per_block(m->n));
 }
 
 template <class T>
@@ -659,7 +659,7 @@ extern "C" int ppmd_md_create(ppmd_ctx *ctx, ppmd_md **out, int64_t nbox, const 
     if (rc == PPMD_OK) rc = md_alloc(m, &m->cnt, n);
     // partial rows: the most blocks of any pair-loop shape or brick table
     if (rc == PPMD_OK)
-        rc = md_alloc(m, &m->part_f, 3 * std::max<int64_t>(div_up(n, 64), m->nbricks) + 3);
+        rc = md_alloc(m, &m->part_f, 3 * std::max<int64_t>(div_up(n, 8), m->nbricks) + 3);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->part_k, kick_blocks(n) + 1);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->red, 4);
     if (rc == PPMD_OK) rc = md_alloc(m, &m->ebuf, 2 * 1024);

@@ -27,10 +27,13 @@ __device__ __forceinline__ int4 ld_stream4(const int4 *p) {
 
 BrickShape brick_shape(const Seg &S, int32_t home_max) {
     // the neighbourhood spans bw + 2 cells of a row, bh + 2 rows and bd + 2
-    // planes; they must be distinct cells of the periodic grid
+    // planes; they must be distinct cells of the periodic grid, and one cell
+    // more must stay outside them along each axis for the staged FP32 path
+    // of the list build (bw + 3 <= nx and so on; a grid of three cells per
+    // axis always takes the other path)
     const double pc = (double)(S.atom1 - S.atom0) / ((double)S.nc[0] * S.nc[1] * S.nc[2]);
-    const int32_t mw = std::max(1, std::min(BW_MAX, S.nc[0] - 2)), mh = std::max(1, std::min(BH_MAX, S.nc[1] - 2)),
-                  md = std::max(1, std::min(BD_MAX, S.nc[2] - 2));
+    const int32_t mw = std::max(1, std::min(BW_MAX, S.nc[0] - 3)), mh = std::max(1, std::min(BH_MAX, S.nc[1] - 3)),
+                  md = std::max(1, std::min(BD_MAX, S.nc[2] - 3));
     BrickShape best{1, 1, 1};
     double best_home = -1.0, best_halo = 0.0;
     for (int32_t bd = 1; bd <= md; ++bd)
@@ -734,21 +737,29 @@ __global__ void __launch_bounds__(BLOCK, (ENERGY ? 768 : 1024) / BLOCK) k_lj_col
     if (ENERGY) block_sum3_pairs(u_i, w_i, k_i, partials);
 }
 
-template <bool ENERGY>
+// G lanes per atom (a power of two up to 32): lane l takes the list entries
+// k = l, l + G, ...; the lanes' sums are combined by a butterfly of
+// shuffles (every lane ends with the same bits), and lane 0 writes the
+// force and makes the kick.  G = 1 for systems that fill the GPU; small
+// systems take more lanes, since FP64 issues slowly and a thread per atom
+// would leave most SMs idle.
+template <bool ENERGY, int G>
 __global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(int64_t n, int64_t ld, const int4 *__restrict__ xq,
                                                         const double *__restrict__ pos64, SegTable st, LJConst c,
                                                         const int32_t *__restrict__ W, const int32_t *__restrict__ cnt,
                                                         int32_t max_nbr, double *__restrict__ f64,
                                                         double *__restrict__ vel, double h, double half_m,
                                                         double *__restrict__ partials) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / G;
+    const int l = (int)(t % G);
     double u_i = 0.0, w_i = 0.0, k_i = 0.0;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
     if (i < n) {
         const Seg &S = seg_ref(st, xq[i].w);
         const int32_t m = min(cnt[i], max_nbr);
         const double *pi = pos64 + 3 * i;
-        double fx = 0.0, fy = 0.0, fz = 0.0;
-        for (int32_t k = 0; k < m; ++k) {
+        for (int32_t k = l; k < m; k += G) {
             const int32_t j = __ldg(W + (((int64_t)(k >> 2) * ld + i) << 2) + (k & 3));  // grouped by four
             double dr[3];
             const double r2 = min_image_r2(pi, pos64 + 3 * (int64_t)j, S, dr);
@@ -767,6 +778,21 @@ __global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(int64_t n, int64_t ld, c
                 }
             }
         }
+    }
+    if (G > 1) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            fx += __shfl_xor_sync(0xffffffffu, fx, o);
+            fy += __shfl_xor_sync(0xffffffffu, fy, o);
+            fz += __shfl_xor_sync(0xffffffffu, fz, o);
+            if (ENERGY) {
+                u_i += __shfl_xor_sync(0xffffffffu, u_i, o);
+                w_i += __shfl_xor_sync(0xffffffffu, w_i, o);
+            }
+        }
+        if (l != 0) u_i = w_i = 0.0;  // the atom counted once
+    }
+    if (i < n && l == 0) {
         f64[3 * i] = fx;
         f64[3 * i + 1] = fy;
         f64[3 * i + 2] = fz;
@@ -783,10 +809,32 @@ __global__ void __launch_bounds__(COL_BLOCK) k_lj_col64(int64_t n, int64_t ld, c
     if (ENERGY) block_sum3(u_i, w_i, k_i, partials);
 }
 
-// FP64 runs at a small fraction of the FP32 rate on this part: a system too
-// small to give every SM a 256-thread block takes 64-thread blocks, so
-// that its atoms spread over four times as many SMs.
-int lj_col64_block(int64_t n) { return n < (int64_t)148 * COL_BLOCK ? 64 : COL_BLOCK; }
+// FP64 runs at a small fraction of the FP32 rate on this part: a system of
+// fewer atoms than 148 x 256 takes G lanes per atom (the power of two that
+// brings the threads to at least 148 x 256, at most 16) on 128-thread
+// blocks, so that its pair terms spread over the SMs.
+int lj_col64_lanes(int64_t n) {
+    int g = 1;
+    while (g < 16 && n * g < (int64_t)148 * COL_BLOCK) g *= 2;
+    return g;
+}
+int lj_col64_atoms_per_block(int64_t n) {
+    const int g = lj_col64_lanes(n);
+    return g == 1 ? COL_BLOCK : 128 / g;
+}
+
+template <bool ENERGY>
+void launch_col64(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const double *pos64, const SegTable &st,
+                  const LJConst &c, const int32_t *W, const int32_t *cnt, int32_t max_nbr, double *f64, double *vel,
+                  double h, double half_m, double *partials) {
+    const int g = lj_col64_lanes(n);
+    const int64_t nb = div_up(n, lj_col64_atoms_per_block(n));
+    const int block = g == 1 ? COL_BLOCK : 128;
+    auto kern = g == 1 ? k_lj_col64<ENERGY, 1>
+                       : g == 2 ? k_lj_col64<ENERGY, 2>
+                                : g == 4 ? k_lj_col64<ENERGY, 4> : g == 8 ? k_lj_col64<ENERGY, 8> : k_lj_col64<ENERGY, 16>;
+    PPMD_LAUNCH(ctx, kern, nb, block, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m, partials);
+}
 
 int64_t lj_columns_blocks(int64_t n, const ColShape &shape) {
     const int64_t nb = div_up(n, shape.block);
@@ -815,14 +863,8 @@ int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const doubl
                         drift);
         }
     } else {
-        const int block = lj_col64_block(n);
-        const int64_t nb = div_up(n, block);
-        if (partials)
-            PPMD_LAUNCH(ctx, k_lj_col64<true>, nb, block, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
-                        partials);
-        else
-            PPMD_LAUNCH(ctx, k_lj_col64<false>, nb, block, 0, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m,
-                        partials);
+        if (partials) launch_col64<true>(ctx, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m, partials);
+        else launch_col64<false>(ctx, n, ld, xq, pos64, st, c, W, cnt, max_nbr, f64, vel, h, half_m, partials);
     }
     return check_launch(ctx, "lj_columns");
 }

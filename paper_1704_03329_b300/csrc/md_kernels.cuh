@@ -63,7 +63,7 @@ struct Drift {
 // atoms (a persistent grid); else one thread per atom.  The per-atom
 // arithmetic, and so the trajectory, is the same for every shape; the
 // per-block energy sums (partials) follow the shape.  The FP64 loop takes
-// lj_col64_block threads per block.
+// lj_col64_lanes lanes per atom.
 struct ColShape {
     int32_t block = 128;
     int64_t grid_cap = 0;
@@ -74,8 +74,10 @@ int lj_columns(ppmd_ctx *ctx, int64_t n, int64_t ld, const int4 *xq, const doubl
                const ColShape &shape = ColShape());
 // blocks (and partial rows) of a launch of that shape
 int64_t lj_columns_blocks(int64_t n, const ColShape &shape = ColShape());
-// threads per block of the FP64 loop for n atoms (64 or 256)
-int lj_col64_block(int64_t n);
+// lanes per atom of the FP64 loop for n atoms (1 to 16) and atoms per block
+// (its partial rows: div_up(n, atoms per block), at most div_up(n, 8))
+int lj_col64_lanes(int64_t n);
+int lj_col64_atoms_per_block(int64_t n);
 
 // Brick-staged FP32 path (slots.cu).  A list entry is the neighbour's slot
 // (16 bits) in its brick's staged neighbourhood: the cells of the brick's

@@ -247,7 +247,13 @@ def test_half_list_capacity_reports_needed(L, ctx):
 @pytest.mark.parametrize("prec", ["FP32", "FP64"])
 def test_lj_newton3_parity(L, ctx, case, prec):
     """Half-list pair loop: the oracle's forces, energies and totals at the
-    tolerances of the full-list loop of the same precision."""
+    tolerances of the full-list loop of the same precision, except the FP32
+    per-atom energies: the partner halves arrive by FP32 atomics, without
+    compensation and in any order, so an atom's energy can carry up to
+    (partner terms) x 2^-24 x sum_j |V_ij| / 2 on top of the compensated own
+    sum's error; on these cases that worst case is 1.5-2.0e-6 of the mean
+    per-atom energy (at most 30 partner terms), so the bound is 3e-6 of it
+    (1e-6 for the own sums plus 2e-6)."""
     c, r = CASES[case]()
     pos, box = c["pos"], c["box"]
     offs, nbr_o = oracle.neighbours_cells(pos, box, r)
@@ -263,7 +269,7 @@ def test_lj_newton3_parity(L, ctx, case, prec):
         assert abs(tot[1] - Wo) <= 1e-12 * max(abs(Wo), 1.0)
     else:
         assert force_err(F, Fo) <= 1e-5
-        assert np.abs(e - eo).max() <= 1e-6 * np.abs(eo).mean()
+        assert np.abs(e - eo).max() <= 3e-6 * np.abs(eo).mean()
         assert abs(tot[0] - Uo) <= 1e-6 * abs(Uo)
     # Newton's third law: the forces sum to zero (up to the arithmetic)
     assert np.abs(F.sum(0)).max() <= (1e-9 if prec == "FP64" else 1e-4) * np.abs(Fo).sum(0).max()
