@@ -203,12 +203,22 @@ int exclusive_scan(ppmd_ctx *ctx, const int32_t *in, int32_t *out, int64_t n) {
 // ---------------------------------------------------------------------
 // Fixed-order reduction of per-block FP64 partial sums.
 // ---------------------------------------------------------------------
+// Column c of the partial rows: thread t sums rows t, t + 256, ... in that
+// order, then a fixed tree over the threads.  The columns (at most four)
+// are summed in the same pass over the rows, so the loads of a row are in
+// flight together.
 __global__ void k_reduce_partials(const double *parts, int64_t nparts, int width, double *dst) {
     __shared__ double sh[256];
-    for (int c = 0; c < width; ++c) {
-        double s = 0.0;
-        for (int64_t p = threadIdx.x; p < nparts; p += blockDim.x) s += parts[p * width + c];
-        sh[threadIdx.x] = s;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t p = threadIdx.x; p < nparts; p += blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < width) s[c] += parts[p * width + c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        if (c >= width) break;
+        sh[threadIdx.x] = s[c];
         __syncthreads();
         for (int o = blockDim.x / 2; o > 0; o >>= 1) {
             if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
@@ -220,6 +230,7 @@ __global__ void k_reduce_partials(const double *parts, int64_t nparts, int width
 }
 
 int reduce_partials(ppmd_ctx *ctx, const double *parts, int64_t nparts, int width, double *dst) {
+    if (width < 1 || width > 4) return set_error(ctx, PPMD_ERR_INVALID, "reduce_partials: width %d", width);
     PPMD_LAUNCH(ctx, k_reduce_partials, 1, 256, 0, parts, nparts, width, dst);
     return check_launch(ctx, "reduce_partials");
 }
