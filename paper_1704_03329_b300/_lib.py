@@ -128,6 +128,42 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _need(t, name, dtype, shape=None, numel=None, optional=False):
+    """Check a tensor argument against what the C call reads or writes
+    through its pointer, before any pointer is taken: the element type, the
+    shape (None entries: any extent) or at least `numel` elements, and a
+    contiguous layout (_ptr then requires CUDA memory).  A mismatch raises
+    ValueError rather than letting a kernel run past the end of the buffer."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{name}: a tensor is required")
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if shape is not None:
+        if t.dim() != len(shape) or any(s is not None and t.shape[k] != s for k, s in enumerate(shape)):
+            want = "[" + ", ".join("*" if s is None else str(s) for s in shape) + "]"
+            raise ValueError(f"{name}: expected shape {want}, got {list(t.shape)}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: expected at least {numel} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+
+
+def _positions(t, name="pos"):
+    """A float64 [n][3] position or velocity array; returns n."""
+    _need(t, name, torch.float64, (None, 3))
+    return t.shape[0]
+
+
+def _rows(nbr, name, n):
+    """An int32 neighbour table [n][max_nbr]; returns max_nbr."""
+    _need(nbr, name, torch.int32, (n, None))
+    return nbr.shape[1]
+
+
 def _box(L):
     b = Box()
     for d in range(3):
@@ -183,7 +219,7 @@ class Context:
 
 def ppmd_build_cells(ctx: Context, pos, box, min_cell_width, cell_capacity=None):
     """Cell list; returns (ncell[3] list, cell_of, cell_start, cell_atoms) as int32 CUDA tensors."""
-    n = pos.shape[0]
+    n = _positions(pos)
     dev = pos.device
     ncell = [max(1, int(float(box[d]) // float(min_cell_width))) for d in range(3)]
     cap = cell_capacity if cell_capacity is not None else ncell[0] * ncell[1] * ncell[2] + 1
@@ -201,7 +237,10 @@ def ppmd_build_cells(ctx: Context, pos, box, min_cell_width, cell_capacity=None)
 
 def ppmd_build_neighbours(ctx: Context, pos, box, r_list, cell_start, cell_atoms, ncell, max_nbr, want_needed=False):
     """Neighbour list rows nbr[n, max_nbr] (int32) and counts nbr_count[n]."""
-    n = pos.shape[0]
+    n = _positions(pos)
+    ncell = [int(x) for x in ncell]
+    _need(cell_start, "cell_start", torch.int32, numel=ncell[0] * ncell[1] * ncell[2] + 1)
+    _need(cell_atoms, "cell_atoms", torch.int32, (n,))
     nbr = torch.empty((n, max_nbr), dtype=torch.int32, device=pos.device)
     cnt = torch.empty(n, dtype=torch.int32, device=pos.device)
     nc = (_I32 * 3)(*[int(x) for x in ncell])
@@ -219,14 +258,15 @@ def ppmd_build_neighbours(ctx: Context, pos, box, r_list, cell_start, cell_atoms
 def ppmd_lj_forces(ctx: Context, pos, box, nbr, nbr_count, rc=2.5, eps=1.0, sigma=1.0, shift=0.0, prec=FP32,
                    want_energy=True):
     """Forces [n,3] f64, per-atom energies [n] f64, and device scalars (U, W)."""
-    n = pos.shape[0]
+    n = _positions(pos)
+    max_nbr = _rows(nbr, "nbr", n)
+    _need(nbr_count, "nbr_count", torch.int32, (n,))
     dev = pos.device
     F = torch.empty((n, 3), dtype=torch.float64, device=dev)
     e = torch.empty(n, dtype=torch.float64, device=dev) if want_energy else None
     tot = torch.zeros(2, dtype=torch.float64, device=dev)
     p = LJParams(eps, sigma, rc, shift)
     b = _box(box)
-    max_nbr = nbr.shape[1] if nbr.dim() == 2 else 0
     code = _lib.ppmd_lj_forces(ctx.h, _ptr(pos), n, C.byref(b), C.byref(p), _ptr(nbr), _ptr(nbr_count), int(max_nbr),
                                int(prec), _ptr(F), _ptr(e) if e is not None else None, _ptr(tot[0:1]),
                                C.c_void_p(tot.data_ptr() + 8))
@@ -237,7 +277,7 @@ def ppmd_lj_forces(ctx: Context, pos, box, nbr, nbr_count, rc=2.5, eps=1.0, sigm
 def ppmd_lj_forces_cells(ctx: Context, pos, box, rc=2.5, eps=1.0, sigma=1.0, shift=0.0, prec=FP32, want_energy=True):
     """List-free pair loop (cells of edge >= rc swept directly, no neighbour
     list): forces [n,3] f64, per-atom energies [n] f64, device scalars (U, W)."""
-    n = pos.shape[0]
+    n = _positions(pos)
     dev = pos.device
     F = torch.empty((n, 3), dtype=torch.float64, device=dev)
     e = torch.empty(n, dtype=torch.float64, device=dev) if want_energy else None
@@ -253,7 +293,9 @@ def ppmd_lj_forces_cells(ctx: Context, pos, box, rc=2.5, eps=1.0, sigma=1.0, shi
 def ppmd_half_list(ctx: Context, pos, box, nbr, nbr_count, max_half=None):
     """Half list of a full row-major list [n, max_nbr]: each pair kept by the
     atom from which the other lies in the upper half space (z, y, x order)."""
-    n, max_nbr = nbr.shape[0], (nbr.shape[1] if nbr.dim() == 2 else 0)
+    n = _positions(pos)
+    max_nbr = _rows(nbr, "nbr", n)
+    _need(nbr_count, "nbr_count", torch.int32, (n,))
     max_half = (max_nbr + 1) // 2 + 8 if max_half is None else max_half
     half = torch.empty((n, max_half), dtype=torch.int32, device=nbr.device)
     hcnt = torch.empty(n, dtype=torch.int32, device=nbr.device)
@@ -267,7 +309,9 @@ def ppmd_lj_forces_newton3(ctx: Context, pos, box, half, half_count, rc=2.5, eps
                            want_energy=True):
     """Forces [n,3] f64, per-atom energies [n] f64 and device scalars (U, W)
     from a half list (each pair once, Newton's third law)."""
-    n = pos.shape[0]
+    n = _positions(pos)
+    _rows(half, "half", n)
+    _need(half_count, "half_count", torch.int32, (n,))
     dev = pos.device
     F = torch.empty((n, 3), dtype=torch.float64, device=dev)
     e = torch.empty(n, dtype=torch.float64, device=dev) if want_energy else None
@@ -282,12 +326,16 @@ def ppmd_lj_forces_newton3(ctx: Context, pos, box, half, half_count, rc=2.5, eps
 
 
 def ppmd_verlet_step(ctx: Context, phase, pos, vel, force, box, mass=1.0, dt=0.005):
+    n = _positions(vel, "vel")
+    _need(pos, "pos", torch.float64, (n, 3))
+    _need(force, "force", torch.float64, (n, 3))
     b = _box(box)
     ctx.check(_lib.ppmd_verlet_step(ctx.h, int(phase), _ptr(pos), _ptr(vel), _ptr(force), vel.shape[0], C.byref(b),
                                     float(mass), float(dt)))
 
 
 def ppmd_kinetic_energy(ctx: Context, vel, mass=1.0):
+    _positions(vel, "vel")
     ke = torch.zeros(1, dtype=torch.float64, device=vel.device)
     ctx.check(_lib.ppmd_kinetic_energy(ctx.h, _ptr(vel), vel.shape[0], float(mass), _ptr(ke)))
     return ke
@@ -299,7 +347,9 @@ def _opt(t):
 
 def ppmd_boa_q46(ctx: Context, pos, box, r_cut, nbr, nbr_count):
     """Q4, Q6 (float32 [n]) and bonded-neighbour counts (int32 [n])."""
-    n = pos.shape[0]
+    n = _positions(pos)
+    _rows(nbr, "nbr", n)
+    _need(nbr_count, "nbr_count", torch.int32, (n,))
     q4 = torch.empty(n, dtype=torch.float32, device=pos.device)
     q6 = torch.empty(n, dtype=torch.float32, device=pos.device)
     nnb = torch.empty(n, dtype=torch.int32, device=pos.device)
@@ -311,7 +361,9 @@ def ppmd_boa_q46(ctx: Context, pos, box, r_cut, nbr, nbr_count):
 
 def ppmd_cna(ctx: Context, pos, box, r_cut, nbr, nbr_count, want_triplets=True):
     """CNA triplets (uint32 as int32 [n, max_nbr]) and labels (int8 [n])."""
-    n = pos.shape[0]
+    n = _positions(pos)
+    _rows(nbr, "nbr", n)
+    _need(nbr_count, "nbr_count", torch.int32, (n,))
     trip = torch.empty(nbr.shape, dtype=torch.int32, device=pos.device) if want_triplets else None
     lab = torch.empty(n, dtype=torch.int8, device=pos.device)
     b = _box(box)
@@ -322,19 +374,28 @@ def ppmd_cna(ctx: Context, pos, box, r_cut, nbr, nbr_count, want_triplets=True):
 
 def ppmd_analyze(ctx: Context, pos, box, r_boa=1.5, r_cna=None, boa=True, cna=True, out=None):
     """Pipeline from positions; returns dict with q4, q6, n_nb and/or label."""
-    n = pos.shape[0]
-    dev = pos.device
-    out = out or {}
-    if boa:
-        out.setdefault("q4", torch.empty(n, dtype=torch.float32, device=dev))
-        out.setdefault("q6", torch.empty(n, dtype=torch.float32, device=dev))
-        out.setdefault("n_nb", torch.empty(n, dtype=torch.int32, device=dev))
-    if cna:
-        out.setdefault("label", torch.empty(n, dtype=torch.int8, device=dev))
+    n = _positions(pos)
+    out = _analysis_outputs(out, n, pos.device, boa, cna)
     b = _box(box)
     ctx.check(_lib.ppmd_analyze(ctx.h, _ptr(pos), n, C.byref(b), float(r_boa or 0.0), float(r_cna or 0.0),
                                 _opt(out.get("q4")), _opt(out.get("q6")), _opt(out.get("n_nb")),
                                 _opt(out.get("label"))))
+    return out
+
+
+_OUT_TYPES = {"q4": torch.float32, "q6": torch.float32, "n_nb": torch.int32, "label": torch.int8}
+
+
+def _analysis_outputs(out, n, dev, boa, cna):
+    """The output dict of ppmd_analyze(_boxes): the caller's tensors (checked:
+    one element per atom of the right type) and new ones for the rest."""
+    out = out or {}
+    for k, t in out.items():
+        if k not in _OUT_TYPES:
+            raise ValueError(f"out: unknown key {k!r} (expected q4, q6, n_nb, label)")
+        _need(t, f"out[{k!r}]", _OUT_TYPES[k], (n,))
+    for k in (("q4", "q6", "n_nb") if boa else ()) + (("label",) if cna else ()):
+        out.setdefault(k, torch.empty(n, dtype=_OUT_TYPES[k], device=dev))
     return out
 
 
@@ -352,15 +413,8 @@ def _box_set(atom_off, boxes):
 def ppmd_analyze_boxes(ctx: Context, pos, atom_off, boxes, r_boa=1.5, r_cna=None, boa=True, cna=True, out=None):
     """ppmd_analyze over several independent boxes (box b: atoms atom_off[b] ..
     atom_off[b + 1] - 1 of pos) in one pipeline; same outputs over all atoms."""
-    n = pos.shape[0]
-    dev = pos.device
-    out = out or {}
-    if boa:
-        out.setdefault("q4", torch.empty(n, dtype=torch.float32, device=dev))
-        out.setdefault("q6", torch.empty(n, dtype=torch.float32, device=dev))
-        out.setdefault("n_nb", torch.empty(n, dtype=torch.int32, device=dev))
-    if cna:
-        out.setdefault("label", torch.empty(n, dtype=torch.int8, device=dev))
+    n = _positions(pos)
+    out = _analysis_outputs(out, n, pos.device, boa, cna)
     nbox, off, bx = _box_set(atom_off, boxes)
     if off[nbox] != n:
         raise ValueError("atom_off[-1] must equal the number of atoms")
@@ -372,7 +426,7 @@ def ppmd_analyze_boxes(ctx: Context, pos, atom_off, boxes, r_boa=1.5, r_cna=None
 
 def ppmd_acna(ctx: Context, pos, box, r_list=1.8, want_rcut=True):
     """Adaptive CNA labels int8 [n] and the local cutoffs float64 [n, 2] (caller order)."""
-    n = pos.shape[0]
+    n = _positions(pos)
     lab = torch.empty(n, dtype=torch.int8, device=pos.device)
     rc = torch.empty((n, 2), dtype=torch.float64, device=pos.device) if want_rcut else None
     b = _box(box)
@@ -385,7 +439,7 @@ MLP_NPARAM = 6464
 
 def ppmd_features(ctx: Context, pos, box, r_feat=1.5, fp32=True, bf16=False, r_ref=1.433625):
     """Classifier features: float32 [n, 30] and/or bfloat16 [n, 32] (caller order)."""
-    n = pos.shape[0]
+    n = _positions(pos)
     f = torch.empty((n, 30), dtype=torch.float32, device=pos.device) if fp32 else None
     fb = torch.empty((n, 32), dtype=torch.bfloat16, device=pos.device) if bf16 else None
     b = _box(box)
@@ -393,18 +447,33 @@ def ppmd_features(ctx: Context, pos, box, r_feat=1.5, fp32=True, bf16=False, r_r
     return f, fb
 
 
+def _mlp_params(t, name="params"):
+    _need(t, name, torch.float32, (MLP_NPARAM,))
+
+
+def _mlp_rows(x):
+    """BF16 feature rows [n][32] (30 used); returns n."""
+    _need(x, "x_bf16", torch.bfloat16, (None, 32))
+    return x.shape[0]
+
+
 def ppmd_mlp_fit_input_norm(ctx: Context, params, x_bf16):
+    _mlp_params(params)
+    _mlp_rows(x_bf16)
     ctx.check(_lib.ppmd_mlp_fit_input_norm(ctx.h, _ptr(params), _ptr(x_bf16), x_bf16.shape[0]))
 
 
 def ppmd_mlp_forward(ctx: Context, params, x_bf16):
-    n = x_bf16.shape[0]
+    _mlp_params(params)
+    n = _mlp_rows(x_bf16)
     logits = torch.empty((n, 4), dtype=torch.float32, device=x_bf16.device)
     ctx.check(_lib.ppmd_mlp_forward(ctx.h, _ptr(params), _ptr(x_bf16), n, _ptr(logits)))
     return logits
 
 
 def ppmd_mlp_grad(ctx: Context, params, x_bf16, y):
+    _mlp_params(params)
+    _need(y, "y", torch.int8, (_mlp_rows(x_bf16),))
     grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=params.device)
     loss = torch.empty(1, dtype=torch.float32, device=params.device)
     ctx.check(_lib.ppmd_mlp_grad(ctx.h, _ptr(params), _ptr(x_bf16), _ptr(y), x_bf16.shape[0], _ptr(grad), _ptr(loss)))
@@ -412,11 +481,17 @@ def ppmd_mlp_grad(ctx: Context, params, x_bf16, y):
 
 
 def ppmd_mlp_adamw(ctx: Context, params, m, v, grad, step, lr=1e-3, wd=0.01, beta1=0.9, beta2=0.999, eps=1e-8):
+    for t, name in ((params, "params"), (m, "m"), (v, "v"), (grad, "grad")):
+        _mlp_params(t, name)
     ctx.check(_lib.ppmd_mlp_adamw(ctx.h, _ptr(params), _ptr(m), _ptr(v), _ptr(grad), int(step), lr, wd, beta1, beta2,
                                   eps))
 
 
 def ppmd_mlp_train_step(ctx: Context, params, m, v, step, x_bf16, y, lr=1e-3, wd=0.01, loss=None):
+    for t, name in ((params, "params"), (m, "m"), (v, "v")):
+        _mlp_params(t, name)
+    _need(y, "y", torch.int8, (_mlp_rows(x_bf16),))
+    _need(loss, "loss", torch.float32, numel=1, optional=True)
     ctx.check(_lib.ppmd_mlp_train_step(ctx.h, _ptr(params), _ptr(m), _ptr(v), int(step), _ptr(x_bf16), _ptr(y),
                                        x_bf16.shape[0], lr, wd, _opt(loss)))
 
@@ -426,7 +501,8 @@ def ppmd_classify(ctx: Context, pos, box, mode=1, params=None, threshold=0.9, r_
     """Labels int8 [n], confidence float32 [n] (mode 1; mode 2: the distance to
     the nearest table (Q4, Q6), with threshold the tolerance), number of CNA
     fallbacks (None with count=False: the call is then asynchronous)."""
-    n = pos.shape[0]
+    n = _positions(pos)
+    _need(params, "params", torch.float32, (MLP_NPARAM,), optional=mode != 1)
     lab = torch.empty(n, dtype=torch.int8, device=pos.device)
     conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode in (1, 2)) else None
     nfb = _I64(0)
@@ -440,7 +516,8 @@ def ppmd_classify_boxes(ctx: Context, pos, atom_off, boxes, mode=1, params=None,
                         r_cna=1.433625, want_confidence=True, count=True):
     """ppmd_classify over several independent boxes in one pipeline (box set as
     ppmd_analyze_boxes); labels, confidences and the total fallback count."""
-    n = pos.shape[0]
+    n = _positions(pos)
+    _need(params, "params", torch.float32, (MLP_NPARAM,), optional=mode != 1)
     lab = torch.empty(n, dtype=torch.int8, device=pos.device)
     conf = torch.empty(n, dtype=torch.float32, device=pos.device) if (want_confidence and mode in (1, 2)) else None
     nfb = _I64(0)
@@ -492,9 +569,12 @@ class MD:
             pass
 
     def set_state(self, pos, vel):
+        _need(pos, "pos", torch.float64, (self.n, 3))
+        _need(vel, "vel", torch.float64, (self.n, 3))
         self.ctx.check(_lib.ppmd_md_set_state(self.h, _ptr(pos), _ptr(vel)))
 
     def run(self, nsteps, energies=None, use_graph=True):
+        _need(energies, "energies", torch.float64, numel=2 * int(nsteps), optional=True)
         self.ctx.check(_lib.ppmd_md_run(self.h, int(nsteps), _ptr(energies) if energies is not None else None,
                                         1 if use_graph else 0))
 
@@ -505,6 +585,8 @@ class MD:
         self.ctx.check(_lib.ppmd_md_set_boa(self.h, int(every), float(r_boa)))
 
     def run_analysed(self, nsteps, energies=None, qrows=None, use_graph=True):
+        _need(energies, "energies", torch.float64, numel=2 * int(nsteps), optional=True)
+        _need(qrows, "qrows", torch.float64, numel=3 * int(nsteps), optional=True)
         self.ctx.check(_lib.ppmd_md_run_analysed(self.h, int(nsteps), _opt(energies), _opt(qrows),
                                                  1 if use_graph else 0))
 
@@ -514,6 +596,8 @@ class MD:
         return q
 
     def get_state(self, pos=None, vel=None, force=None):
+        for t, name in ((pos, "pos"), (vel, "vel"), (force, "force")):
+            _need(t, name, torch.float64, (self.n, 3), optional=True)
         self.ctx.check(_lib.ppmd_md_get_state(self.h, _ptr(pos) if pos is not None else None,
                                               _ptr(vel) if vel is not None else None,
                                               _ptr(force) if force is not None else None))
