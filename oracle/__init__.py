@@ -24,13 +24,18 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lib = None
 
 
+def compile_source(src: str, out: str) -> None:
+    """gcc -O2 with FP contraction off: the one way every build of the oracle's C source is made."""
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+                           "-fno-fast-math", "-fopenmp", "-o", out, src, "-lm"])
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP contraction off) if it is missing or stale."""
+    """Compile the oracle if it is missing or stale."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
-                               "-fno-fast-math", "-fopenmp", "-o", tmp, _SRC, "-lm"])
+        compile_source(_SRC, tmp)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -39,7 +44,10 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    lib = C.CDLL(build())
+    # PPMD_ORACLE_LIB names another build of ppmd_oracle.c: the tests that
+    # plant a mistake in a copy of the oracle's source (test_oracle_mutants)
+    # run the pins against that copy's build through it
+    lib = C.CDLL(os.environ.get("PPMD_ORACLE_LIB") or build())
     i64, i32, f64 = C.c_int64, C.c_int32, C.c_double
     P = C.c_void_p
     sig = {

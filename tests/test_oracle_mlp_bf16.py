@@ -7,6 +7,9 @@ classifier parity tests use (CPU only).
   partial sum is representable in BF16 (small dyadic weights and inputs), so
   it computes the same network with nothing dropped or transposed; and it
   differs from it by rounding only on general inputs;
+- the rounding points: every activation entering a product is a BF16 value
+  (torch's conversion leaves it unchanged) and each hidden layer is its
+  ReLU pre-activation rounded once;
 - the tolerance: an emulation of the library's arithmetic (the same BF16
   rounding points, sums accumulated in FP32 instead of FP64) stays within
   flip_tolerance on every row of oracle features of the four structures,
@@ -69,6 +72,30 @@ def test_forward_bf16_differs_by_rounding_only():
     d = np.abs(a - b)
     scale = np.sqrt((b ** 2).mean())
     assert 0 < d.max() <= 0.03 * scale  # three BF16 roundings of ~2^-9 each
+
+
+def test_forward_bf16_operands_are_bf16_values():
+    """Every activation that enters a product -- the standardised inputs and
+    both hidden layers -- is a BF16 value (torch's FP32 -> BF16 conversion
+    leaves it unchanged), and each hidden layer is its ReLU pre-activation
+    rounded once: within half a BF16 step (2^-8 relative: eight significant
+    bits) of it."""
+    p = op.unpack(op.train_params().astype(np.float64))
+    rng = np.random.default_rng(5)
+    x = omlp.bf16_round(rng.normal(0.3, 0.4, (5000, 30)))
+    _, (xs, z1, h1, z2, h2) = omlp.forward_bf16(p, x)
+
+    def is_bf16(a):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+        return np.array_equal(t.to(torch.bfloat16).to(torch.float64).numpy(), a)
+
+    for a in (xs, h1, h2):
+        assert is_bf16(a)
+    for z, h in ((z1, h1), (z2, h2)):
+        r = np.maximum(z, 0.0)
+        assert not is_bf16(r)  # the pre-activations are wider: the rounding is a real step
+        assert np.all(np.abs(h - r) <= 2.0 ** -8 * r)
+        assert (h > 0).any()
 
 
 def _emulate_fp32(q, x):

@@ -1,0 +1,245 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's source -- a flipped
+sign, a dropped factor, a wrong exponent, index or bound, a transposed
+operand, a skipped step -- and runs the pins named beside it against that
+copy in a child pytest: for the C source (MUTANTS) a build made with the
+oracle's own compiler flags, loaded through PPMD_ORACLE_LIB; for the NumPy
+network (MLP_MUTANTS) the copy imported as `oracle.mlp` before the pins are
+collected.  A case passes when at least one of its pins fails, so every
+entry records which pin stands guard over which part of the oracle.  The
+CUDA library is not involved.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ppmd_oracle.c")
+MD = "tests/test_oracle_md.py::"
+AN = "tests/test_oracle_analysis.py::"
+BF = "tests/test_oracle_mlp_bf16.py::"
+MLP_SRC = os.path.join(ROOT, "oracle", "mlp.py")
+
+# name: (text of the oracle, the mistake, which occurrence (0 = first), pins)
+MUTANTS = {
+    # periodic domain and cells (Sec. 3.5)
+    "wrap_by_rint": ("double y = x - L * floor(x / L);", "double y = x - L * rint(x / L);", 0,
+                     [MD + "test_vv_wraps_into_box"]),
+    "min_image_by_floor": ("t = t - L[d] * rint(t / L[d]);", "t = t - L[d] * floor(t / L[d]);", 0,
+                           [MD + "test_lattice_energy_closed_form"]),
+    "cell_index_transposed": ("cell_of[i] = (cz * nc[1] + cy) * nc[0] + cx;",
+                              "cell_of[i] = (cx * nc[1] + cy) * nc[0] + cz;", 0,
+                              [MD + "test_cells_contain_their_atoms"]),
+    "stencil_misses_a_layer": ("for (int ox = -1; ox <= 1; ++ox)", "for (int ox = -1; ox <= 0; ++ox)", 0,
+                               [MD + "test_neighbour_list_cells_equal_brute_force"]),
+    # Lennard-Jones pair loop, Eqs. (7)-(8)
+    "force_sign_x": ("fx += fmag * dr[0];", "fx -= fmag * dr[0];", 0,
+                     [MD + "test_force_is_minus_energy_gradient"]),
+    "force_exponent_12": ("double sr14 = sr12 * sr2;", "double sr14 = sr12;", 0,
+                          [MD + "test_force_is_minus_energy_gradient"]),
+    "force_prefactor_24": ("double fmag = 48.0 * eps / s2", "double fmag = 24.0 * eps / s2", 0,
+                           [MD + "test_force_is_minus_energy_gradient"]),
+    "energy_not_halved": ("ei += 0.5 * 4.0 * eps", "ei += 4.0 * eps", 0,
+                          [MD + "test_lattice_energy_closed_form"]),
+    "shift_sign": ("(sr12 - sr6 + shift)", "(sr12 - sr6 - shift)", 0,
+                   [MD + "test_lattice_energy_closed_form"]),
+    "virial_not_halved": ("wsum += 0.5 * fmag * r2;", "wsum += fmag * r2;", 0,
+                          [MD + "test_virial_is_volume_derivative"]),
+    # Velocity Verlet, Algorithm 6
+    "kick_full_step": ("double h = dt / (2.0 * mass);", "double h = dt / mass;", 0,
+                       [MD + "test_vv_constant_force_closed_form"]),
+    "drift_half_step": ("pos[3 * i + d] + dt * vel[3 * i + d]", "pos[3 * i + d] + h * vel[3 * i + d]", 0,
+                        [MD + "test_vv_constant_force_closed_form"]),
+    "kinetic_not_halved": ("k += 0.5 * mass *", "k += mass *", 0,
+                           [MD + "test_vv_energy_error_is_second_order"]),
+    "list_never_rebuilt": ("if (rebuild_every > 0 && s % rebuild_every == 0) {",
+                           "if (rebuild_every < 0 && s % rebuild_every == 0) {", 1,
+                           [MD + "test_md_rebuild_policy_matches_fresh_lists"]),
+    # bond order, Eqs. (1)-(2)
+    "legendre_recurrence_index": ("- (ll + m - 1.0) * pmm) / (ll - m);", "- (ll + m) * pmm) / (ll - m);", 0,
+                                  [AN + "test_perfect_lattice_Q_matches_paper_table"]),
+    "ylm_norm_2pi": ("(2.0 * l + 1.0) / (4.0 * ORA_PI)", "(2.0 * l + 1.0) / (2.0 * ORA_PI)", 0,
+                     [AN + "test_perfect_lattice_Q_matches_paper_table"]),
+    "q_prefactor_2l": ("sqrt(4.0 * ORA_PI / (2.0 * l + 1.0) * s)", "sqrt(4.0 * ORA_PI / (2.0 * l) * s)", 0,
+                       [AN + "test_perfect_lattice_Q_matches_paper_table"]),
+    "bonnet_sign": ("(2.0 * k + 1.0) * x * p1 - k * p0", "(2.0 * k + 1.0) * x * p1 + k * p0", 0,
+                    [AN + "test_Q_direct_equals_addition_theorem"]),
+    "ylm_azimuth_without_m": ("yi = p * sin(am * phi);", "yi = p * sin(phi);", 0,
+                              [AN + "test_Q_direct_equals_addition_theorem"]),
+    # common neighbour analysis, Eqs. (3)-(5), Algorithms 3-5 and 7
+    "cna_common_not_tested": ("if (in_set(&direct[eoff[j]], nu_nb[j], v)) C[nc++] = v;",
+                              "if (v != j) C[nc++] = v;", 0,
+                              [AN + "test_perfect_lattice_cna_signatures"]),
+    "cna_bonds_not_deduplicated": ("if (!dup) {", "if (1) {", 0,
+                                   [AN + "test_perfect_lattice_cna_signatures"]),
+    "cluster_sum_not_max": ("if (S > smax) smax = S;", "smax += S;", 0,
+                            [AN + "test_perfect_lattice_cna_signatures"]),
+    "cluster_counts_first_edge_only": ("S += 1;", "S = 1;", 0,
+                                       [AN + "test_perfect_lattice_cna_signatures"]),
+    "label_hcp_as_bcc": ("c422 == 6) lab = 2;", "c422 == 6) lab = 3;", 0,
+                         [AN + "test_perfect_lattice_cna_signatures"]),
+    # features of the learned classifier
+    "feature_distance_scale": ("(d[k] - r_ref) / (r_feat - r_ref)", "(d[k] - r_ref) / r_feat", 0,
+                               [AN + "test_features_perfect_fcc_closed_form"]),
+    "feature_tent_weights_swapped": ("f[16 + b0] += 1.0 - t;", "f[16 + b0] += t;", 0,
+                                     [AN + "test_features_perfect_fcc_closed_form"]),
+    "feature_histogram_norm": ("f[16 + b] /= 24.0;", "f[16 + b] /= 12.0;", 0,
+                               [AN + "test_features_perfect_fcc_closed_form"]),
+    # Philox4x32-10 and the Andersen thermostat (Sec. 5.3)
+    "philox_multiplier": ("mulhilo32(0xCD9E8D57u, c2, &lo1)", "mulhilo32(0xCD9E8D59u, c2, &lo1)", 0,
+                          [MD + "test_philox4x32_known_answers"]),
+    "philox_weyl_constant": ("k1 += 0xBB67AE85u;", "k1 += 0x9E3779B9u;", 0,
+                             [MD + "test_philox4x32_known_answers"]),
+    "philox_nine_rounds": ("for (int r = 0; r < 10; ++r) {", "for (int r = 0; r < 9; ++r) {", 0,
+                           [MD + "test_philox4x32_known_answers"]),
+    "andersen_threshold_rounded_up": ("return (uint64_t)floor(p * 4294967296.0);",
+                                      "return (uint64_t)ceil(p * 4294967296.0);", 0,
+                                      [MD + "test_andersen_threshold"]),
+    "box_muller_cos_twice": ("v[1] = sd * (r1 * sin(t1));", "v[1] = sd * (r1 * cos(t1));", 0,
+                             [MD + "test_andersen_every_atom_every_step"]),
+    # adaptive CNA (Stukowski 2012, cited in Sec. 4.2)
+    "acna_factor": ("const double f = (1.0 + sqrt(2.0)) * 0.5;", "const double f = (1.0 + sqrt(3.0)) * 0.5;", 0,
+                    [AN + "test_acna_perfect_lattices_at_any_density"]),
+    "acna_bcc_weight_on_second_shell": ("rc14 = f * ((c * s8 + s6) / 14.0);", "rc14 = f * ((s8 + c * s6) / 14.0);",
+                                        0, [AN + "test_acna_perfect_lattices_at_any_density"]),
+}
+
+# the classifier's network, forward and backward passes, AdamW (oracle/mlp.py)
+MLP_MUTANTS = {
+    "relu_mask_of_the_wrong_layer": ('d2 = (g3 @ p["W3"].T) * (z2 > 0)', 'd2 = (g3 @ p["W3"].T) * (z1 > 0)', 0,
+                                     [AN + "test_mlp_gradient_matches_finite_differences"]),
+    "backprop_weight_not_transposed": ('d1 = (d2 @ p["W2"].T)', 'd1 = (d2 @ p["W2"])', 0,
+                                       [AN + "test_mlp_gradient_matches_finite_differences"]),
+    "softmax_gradient_onehot_added": ("g3[np.arange(n), y] -= 1.0", "g3[np.arange(n), y] += 1.0", 0,
+                                      [AN + "test_mlp_gradient_matches_finite_differences"]),
+    "gradient_not_averaged": ("g3 /= n", "g3 /= 1", 0, [AN + "test_mlp_gradient_matches_finite_differences"]),
+    "second_relu_dropped": ("h2 = np.maximum(z2, 0.0)", "h2 = z2", 0,
+                            [AN + "test_mlp_gradient_matches_finite_differences"]),
+    "standardisation_by_variance": ("1.0 / np.sqrt(np.maximum(var, 1e-300))", "1.0 / np.maximum(var, 1e-300)", 0,
+                                    [AN + "test_mlp_input_standardisation"]),
+    "adamw_no_bias_correction": ("mh = m / (1.0 - b1 ** t)", "mh = m", 0, [AN + "test_adamw_textbook_steps"]),
+    "adamw_eps_inside_sqrt": ("np.sqrt(vh) + eps", "np.sqrt(vh + eps)", 0, [AN + "test_adamw_textbook_steps"]),
+    "adamw_decay_not_decoupled": ("p[k] = p[k] - lr * wd * p[k]", "g = g + wd * p[k]", 0,
+                                  [AN + "test_adamw_textbook_steps"]),
+    "bf16_ties_away_from_even": ("r = ((u + 0x7FFF + keep_lsb) >> 16) << 16", "r = ((u + 0x8000) >> 16) << 16", 0,
+                                 [BF + "test_bf16_round_matches_torch"]),
+    "bf16_hidden_layer_unrounded": ("h1 = bf16_round(np.maximum(z1, 0.0))", "h1 = np.maximum(z1, 0.0)", 0,
+                                    [BF + "test_forward_bf16_operands_are_bf16_values"]),
+    "bf16_standardisation_reordered": ('(f32(x) - f32(p["mu"])) * f32(p["isd"])',
+                                       'f32(x) * f32(p["isd"]) - f32(p["mu"])', 0,
+                                       [BF + "test_forward_bf16_is_the_network_on_exact_operands",
+                                        BF + "test_forward_bf16_differs_by_rounding_only"]),
+}
+
+# the child process for a NumPy mutant: the copy becomes oracle.mlp before
+# pytest imports any test module
+_MLP_BOOT = """import importlib.util, sys
+sys.path.insert(0, {root!r})
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.mlp", {path!r})
+m = importlib.util.module_from_spec(spec)
+sys.modules["oracle.mlp"] = m
+spec.loader.exec_module(m)
+oracle.mlp = m
+import pytest
+sys.exit(pytest.main({args!r}))
+"""
+
+
+def plant(src, old, new, occurrence):
+    """The source with the given occurrence of `old` replaced by `new`."""
+    at = -1
+    for _ in range(occurrence + 1):
+        at = src.find(old, at + 1)
+        assert at >= 0, f"{old!r}: occurrence {occurrence} not in the oracle's source"
+    return src[:at] + new + src[at + len(old):]
+
+
+def run_pins(pins, lib=None, mlp=None):
+    """Run the pins against the oracle build `lib` and/or the network source
+    `mlp` (None: the repository's own); (pytest's exit code, the tail of its
+    output)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    if lib:
+        env["PPMD_ORACLE_LIB"] = lib
+    args = ["-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu", *pins]
+    if mlp:
+        cmd = [sys.executable, "-c", _MLP_BOOT.format(root=ROOT, path=mlp, args=args)]
+    else:
+        cmd = [sys.executable, "-m", "pytest", *args]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, (r.stdout + r.stderr)[-1500:]
+
+
+def _mutant(kind, name, tmp):
+    sys.path.insert(0, ROOT)
+    import oracle
+    if kind == "c":
+        old, new, occurrence, pins = MUTANTS[name]
+        src = os.path.join(tmp, f"{name}.c")
+        with open(SRC) as f, open(src, "w") as g:
+            g.write(plant(f.read(), old, new, occurrence))
+        lib = os.path.join(tmp, f"{name}.so")
+        oracle.compile_source(src, lib)
+        return run_pins(pins, lib=lib)
+    old, new, occurrence, pins = MLP_MUTANTS[name]
+    path = os.path.join(tmp, f"{name}.py")
+    with open(MLP_SRC) as f, open(path, "w") as g:
+        g.write(plant(f.read(), old, new, occurrence))
+    return run_pins(pins, mlp=path)
+
+
+@pytest.fixture(scope="module")
+def results():
+    """Every mutant made and its pins run, several at a time."""
+    with tempfile.TemporaryDirectory() as tmp:
+        with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            futs = {("c", k): ex.submit(_mutant, "c", k, tmp) for k in MUTANTS}
+            futs.update({("py", k): ex.submit(_mutant, "py", k, tmp) for k in MLP_MUTANTS})
+            yield {key: f.result() for key, f in futs.items()}
+
+
+@pytest.mark.parametrize("table,path", [(MUTANTS, SRC), (MLP_MUTANTS, MLP_SRC)], ids=["c", "mlp"])
+def test_every_mistake_is_planted_where_named(table, path):
+    """Each mistake changes the source at the named place."""
+    with open(path) as f:
+        src = f.read()
+    for name, (old, new, occurrence, pins) in table.items():
+        assert old != new and pins, name
+        assert src.count(old) >= occurrence + 1, name
+        assert plant(src, old, new, occurrence) != src, name
+
+
+def test_unchanged_sources_pass_the_pins():
+    """The same two routes with nothing planted: the pins pass on a fresh
+    build of the oracle's own C source and on a copy of its network."""
+    import oracle
+    c_pins = sorted({p for *_, ps in MUTANTS.values() for p in ps})
+    py_pins = sorted({p for *_, ps in MLP_MUTANTS.values() for p in ps})
+    with tempfile.TemporaryDirectory() as tmp:
+        lib = os.path.join(tmp, "unchanged.so")
+        oracle.compile_source(SRC, lib)
+        code, out = run_pins(c_pins, lib=lib)
+        assert code == 0, out
+        path = os.path.join(tmp, "unchanged_mlp.py")
+        with open(MLP_SRC) as f, open(path, "w") as g:
+            g.write(f.read())
+        code, out = run_pins(py_pins, mlp=path)
+        assert code == 0, out
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_the_mistake(results, name):
+    code, out = results[("c", name)]
+    assert code == 1, f"{name}: the pins {MUTANTS[name][3]} did not fail (pytest exit {code}):\n{out}"
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
+def test_pins_catch_the_network_mistake(results, name):
+    code, out = results[("py", name)]
+    assert code == 1, f"{name}: the pins {MLP_MUTANTS[name][3]} did not fail (pytest exit {code}):\n{out}"
