@@ -56,16 +56,38 @@ def test_boa_tolerance_labels_perfect_lattices(kind, code):
     assert (oracle.boa_tolerance_labels(q4, q6, 1e-6)[0] == 0).all()
 
 
+def _exact_ties(a, b):
+    """Points near the midpoint of table points a and b whose two distances,
+    evaluated in double precision as the rule evaluates them, are equal bit
+    for bit (the midpoint itself is not: its two distances differ in the
+    last place)."""
+    k = np.arange(-64, 65)
+    m4, m6 = 0.5 * (a[0] + b[0]), 0.5 * (a[1] + b[1])
+    q4, q6 = np.broadcast_arrays(m4 + k[:, None] * np.spacing(m4), m6 + k[None, :] * np.spacing(m6))
+    da = np.sqrt((q4 - a[0]) ** 2 + (q6 - a[1]) ** 2)
+    db = np.sqrt((q4 - b[0]) ** 2 + (q6 - b[1]) ** 2)
+    tie = da == db
+    return q4[tie], q6[tie]
+
+
 def test_boa_tolerance_rule_edges():
     """Strict tolerance, nearest point wins, table order on an exact tie,
     far points are other."""
-    fcc, hcp = np.array([0.191, 0.575]), np.array([0.097, 0.485])
-    mid = 0.5 * (fcc + hcp)  # equidistant from fcc and hcp, farther from bcc
-    d_mid = np.linalg.norm(mid - fcc)
-    lab, d = oracle.boa_tolerance_labels([mid[0]], [mid[1]], 1.0)
-    assert lab[0] == 1 and abs(d[0] - d_mid) < 1e-15
-    lab, _ = oracle.boa_tolerance_labels([0.191, 0.191], [0.575 + 0.05, 0.575 + 0.05], 0.05)
-    assert (lab == 0).all()  # a distance equal to the tolerance is not within it
+    fcc, hcp, bcc = (0.191, 0.575), (0.097, 0.485), (0.036, 0.511)
+    # exact ties: the earlier lattice of the table wins
+    for (a, code), b in (((fcc, 1), hcp), ((hcp, 2), bcc)):
+        q4, q6 = _exact_ties(a, b)
+        assert len(q4) > 0
+        lab, _ = oracle.boa_tolerance_labels(q4, q6, 1.0)
+        assert (lab == code).all()
+    # the distance equal to the tolerance, bit for bit: q6 - 0.575 is exact
+    # (the operands are within a factor two of each other), and the square
+    # root of a rounded square gives back the number in binary64
+    q6 = 0.575 + 0.05
+    tol = q6 - 0.575
+    lab, d = oracle.boa_tolerance_labels([0.191], [q6], tol)
+    assert d[0] == tol and lab[0] == 0  # a distance equal to the tolerance is not within it
+    assert oracle.boa_tolerance_labels([0.191], [q6], np.nextafter(tol, 1.0))[0][0] == 1
     lab, _ = oracle.boa_tolerance_labels([0.191], [0.575 + 0.0499], 0.05)
     assert lab[0] == 1
     lab, _ = oracle.boa_tolerance_labels([0.0, 0.5], [0.0, 0.1], 0.3)

@@ -5,12 +5,14 @@ sign, a dropped factor, a wrong exponent, index or bound, a transposed
 operand, a skipped step -- and runs the pins named beside it against that
 copy in a child pytest: for the C source (MUTANTS) a build made with the
 oracle's own compiler flags, loaded through PPMD_ORACLE_LIB; for the NumPy
-network (MLP_MUTANTS) the copy imported as `oracle.mlp` before the pins are
-collected.  A case passes when at least one of its pins fails, so every
+network (MLP_MUTANTS) the copy imported as `oracle.mlp`, and for the
+package's own Python (PKG_MUTANTS) a copy of the package imported as
+`oracle`, before the pins are collected.  A case passes when at least one of its pins fails, so every
 entry records which pin stands guard over which part of the oracle.  The
 CUDA library is not involved.
 """
 import os
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -24,6 +26,7 @@ MD = "tests/test_oracle_md.py::"
 AN = "tests/test_oracle_analysis.py::"
 BF = "tests/test_oracle_mlp_bf16.py::"
 MLP_SRC = os.path.join(ROOT, "oracle", "mlp.py")
+PKG_SRC = os.path.join(ROOT, "oracle", "__init__.py")
 
 # name: (text of the oracle, the mistake, which occurrence (0 = first), pins)
 MUTANTS = {
@@ -136,16 +139,36 @@ MLP_MUTANTS = {
                                         BF + "test_forward_bf16_differs_by_rounding_only"]),
 }
 
-# the child process for a NumPy mutant: the copy becomes oracle.mlp before
-# pytest imports any test module
-_MLP_BOOT = """import importlib.util, sys
+# the Python side of the oracle package (oracle/__init__.py): the bond-order
+# tolerance rule of Sec. 4.1 and its table
+PKG_MUTANTS = {
+    "tolerance_edge_inclusive": ("np.where(best < tol, lab, np.int8(0))", "np.where(best <= tol, lab, np.int8(0))",
+                                 0, [AN + "test_boa_tolerance_rule_edges"]),
+    "tolerance_tie_to_the_later_lattice": ("closer = d < best", "closer = d <= best", 0,
+                                           [AN + "test_boa_tolerance_rule_edges"]),
+    "tolerance_table_hcp_q6": ("(2, 0.097, 0.485)", "(2, 0.097, 0.511)", 0,
+                               [AN + "test_boa_tolerance_table_is_the_papers"]),
+    "tolerance_distance_squared": ("d = np.sqrt((q4 - r4) ** 2 + (q6 - r6) ** 2)", "d = (q4 - r4) ** 2 + (q6 - r6) ** 2",
+                                   0, [AN + "test_boa_tolerance_labels_perfect_lattices"]),
+}
+
+# the child process for a Python mutant: the copy is imported under the
+# oracle's module name before pytest imports any test module.  `path` is
+# oracle/mlp.py's copy, or the directory holding a copy of the package.
+_PY_BOOT = """import importlib.util, os, sys
 sys.path.insert(0, {root!r})
-import oracle
-spec = importlib.util.spec_from_file_location("oracle.mlp", {path!r})
-m = importlib.util.module_from_spec(spec)
-sys.modules["oracle.mlp"] = m
-spec.loader.exec_module(m)
-oracle.mlp = m
+path = {path!r}
+if os.path.isdir(path):
+    sys.path.insert(0, path)
+    import oracle
+    assert os.path.dirname(oracle.__file__) == os.path.join(path, "oracle")
+else:
+    import oracle
+    spec = importlib.util.spec_from_file_location("oracle.mlp", path)
+    m = importlib.util.module_from_spec(spec)
+    sys.modules["oracle.mlp"] = m
+    spec.loader.exec_module(m)
+    oracle.mlp = m
 import pytest
 sys.exit(pytest.main({args!r}))
 """
@@ -160,16 +183,16 @@ def plant(src, old, new, occurrence):
     return src[:at] + new + src[at + len(old):]
 
 
-def run_pins(pins, lib=None, mlp=None):
-    """Run the pins against the oracle build `lib` and/or the network source
-    `mlp` (None: the repository's own); (pytest's exit code, the tail of its
-    output)."""
+def run_pins(pins, lib=None, py=None):
+    """Run the pins against the oracle build `lib`, or the Python copy `py`
+    (see _PY_BOOT; None: the repository's own); (pytest's exit code, the
+    tail of its output)."""
     env = dict(os.environ, OMP_NUM_THREADS="1")
     if lib:
         env["PPMD_ORACLE_LIB"] = lib
     args = ["-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu", *pins]
-    if mlp:
-        cmd = [sys.executable, "-c", _MLP_BOOT.format(root=ROOT, path=mlp, args=args)]
+    if py:
+        cmd = [sys.executable, "-c", _PY_BOOT.format(root=ROOT, path=py, args=args)]
     else:
         cmd = [sys.executable, "-m", "pytest", *args]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
@@ -187,11 +210,29 @@ def _mutant(kind, name, tmp):
         lib = os.path.join(tmp, f"{name}.so")
         oracle.compile_source(src, lib)
         return run_pins(pins, lib=lib)
-    old, new, occurrence, pins = MLP_MUTANTS[name]
-    path = os.path.join(tmp, f"{name}.py")
-    with open(MLP_SRC) as f, open(path, "w") as g:
-        g.write(plant(f.read(), old, new, occurrence))
-    return run_pins(pins, mlp=path)
+    if kind == "py":
+        old, new, occurrence, pins = MLP_MUTANTS[name]
+        path = os.path.join(tmp, f"{name}.py")
+        with open(MLP_SRC) as f, open(path, "w") as g:
+            g.write(plant(f.read(), old, new, occurrence))
+        return run_pins(pins, py=path)
+    old, new, occurrence, pins = PKG_MUTANTS[name]
+    top = copy_package(os.path.join(tmp, name))
+    init = os.path.join(top, "oracle", "__init__.py")
+    with open(init) as f:
+        src = plant(f.read(), old, new, occurrence)
+    with open(init, "w") as g:
+        g.write(src)
+    return run_pins(pins, py=top)
+
+
+def copy_package(top):
+    """A copy of the oracle package's sources under top/oracle; returns top."""
+    os.makedirs(os.path.join(top, "oracle"))
+    for f in os.listdir(os.path.dirname(SRC)):
+        if f.endswith((".py", ".c")):
+            shutil.copy(os.path.join(os.path.dirname(SRC), f), os.path.join(top, "oracle", f))
+    return top
 
 
 @pytest.fixture(scope="module")
@@ -201,10 +242,12 @@ def results():
         with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
             futs = {("c", k): ex.submit(_mutant, "c", k, tmp) for k in MUTANTS}
             futs.update({("py", k): ex.submit(_mutant, "py", k, tmp) for k in MLP_MUTANTS})
+            futs.update({("pkg", k): ex.submit(_mutant, "pkg", k, tmp) for k in PKG_MUTANTS})
             yield {key: f.result() for key, f in futs.items()}
 
 
-@pytest.mark.parametrize("table,path", [(MUTANTS, SRC), (MLP_MUTANTS, MLP_SRC)], ids=["c", "mlp"])
+@pytest.mark.parametrize("table,path", [(MUTANTS, SRC), (MLP_MUTANTS, MLP_SRC), (PKG_MUTANTS, PKG_SRC)],
+                         ids=["c", "mlp", "package"])
 def test_every_mistake_is_planted_where_named(table, path):
     """Each mistake changes the source at the named place."""
     with open(path) as f:
@@ -216,11 +259,13 @@ def test_every_mistake_is_planted_where_named(table, path):
 
 
 def test_unchanged_sources_pass_the_pins():
-    """The same two routes with nothing planted: the pins pass on a fresh
-    build of the oracle's own C source and on a copy of its network."""
+    """The same three routes with nothing planted: the pins pass on a fresh
+    build of the oracle's own C source, on a copy of its network and on a
+    copy of the package."""
     import oracle
     c_pins = sorted({p for *_, ps in MUTANTS.values() for p in ps})
     py_pins = sorted({p for *_, ps in MLP_MUTANTS.values() for p in ps})
+    pkg_pins = sorted({p for *_, ps in PKG_MUTANTS.values() for p in ps})
     with tempfile.TemporaryDirectory() as tmp:
         lib = os.path.join(tmp, "unchanged.so")
         oracle.compile_source(SRC, lib)
@@ -229,7 +274,9 @@ def test_unchanged_sources_pass_the_pins():
         path = os.path.join(tmp, "unchanged_mlp.py")
         with open(MLP_SRC) as f, open(path, "w") as g:
             g.write(f.read())
-        code, out = run_pins(py_pins, mlp=path)
+        code, out = run_pins(py_pins, py=path)
+        assert code == 0, out
+        code, out = run_pins(pkg_pins, py=copy_package(os.path.join(tmp, "unchanged_package")))
         assert code == 0, out
 
 
@@ -243,3 +290,9 @@ def test_pins_catch_the_mistake(results, name):
 def test_pins_catch_the_network_mistake(results, name):
     code, out = results[("py", name)]
     assert code == 1, f"{name}: the pins {MLP_MUTANTS[name][3]} did not fail (pytest exit {code}):\n{out}"
+
+
+@pytest.mark.parametrize("name", sorted(PKG_MUTANTS))
+def test_pins_catch_the_package_mistake(results, name):
+    code, out = results[("pkg", name)]
+    assert code == 1, f"{name}: the pins {PKG_MUTANTS[name][3]} did not fail (pytest exit {code}):\n{out}"
