@@ -128,8 +128,3 @@ def adamw_step(p, grads, state, lr=1e-3, wd=0.01, b1=0.9, b2=0.999, eps=1e-8):
             p[k] = p[k] - lr * wd * p[k]
         p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
     return p
-
-
-def predict(p, x):
-    prob = softmax(forward(p, x)[0])
-    return prob.argmax(1), prob.max(1)

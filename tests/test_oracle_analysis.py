@@ -251,6 +251,27 @@ def test_features_perfect_fcc_closed_form():
     assert np.abs(f - expect).max() < 1e-9
 
 
+def test_features_shell_between_the_cutoffs():
+    """fcc stretched so that its first shell (12 neighbours at d) lies between
+    the bond length r_ref and the feature cutoff 1.5: Q4 and Q6 (taken over
+    every neighbour within 1.5) are fcc's, the 12 distances are listed and
+    the two missing ones are 1, and no pair is bonded, so the chord
+    histogram is empty.  Q over the bonded neighbours only, or bonds taken
+    at the feature cutoff, change these values."""
+    d = 1.46
+    assert R_CNA < d < 1.5
+    a = d * np.sqrt(2.0)
+    lat = make_lattice("fcc", (4, 4, 4), 4.0 / a ** 3)
+    pos = lat.sites()
+    offs, nbr = oracle.neighbours_brute(pos, lat.box, 1.5)
+    f = oracle.features(pos, lat.box, offs, nbr, 1.5, R_CNA)
+    expect = np.zeros(30)
+    expect[0], expect[1] = 0.19094065395649334, 0.5745242597140697
+    expect[2:14] = (d - R_CNA) / (1.5 - R_CNA)
+    expect[14:16] = 1.0
+    assert np.abs(f - expect).max() < 1e-9
+
+
 def test_features_rotation_invariant_and_counts():
     rng = np.random.default_rng(8)
     cluster = rng.normal(0, 0.6, (30, 3))

@@ -167,6 +167,33 @@ def test_vv_wraps_into_box():
     assert ((p1 >= 0) & (p1 < box)).all()
 
 
+def test_wrap_maps_into_the_half_open_box():
+    """x - L floor(x / L) can round to L itself (a coordinate a hair below 0,
+    a multiple of L); every wrapped coordinate lies in [0, L)."""
+    box = np.array([5.0, 7.0, 3.0])
+    pos = np.array([[-1e-18, -0.0, 3.0], [10.0, -7.0, -1e-300], [-5.0, 14.0, 2.9999999999999996]])
+    w = oracle.wrap(pos, box)
+    assert ((w >= 0) & (w < box)).all()
+    assert (w[:2] == 0).all() and w[2, 0] == 0 and w[2, 1] == 0 and w[2, 2] == pos[2, 2]
+
+
+def test_md_max_displacement_since_rebuild():
+    """The skin guard of Sec. 3.5 (the largest displacement since the list was
+    built, against half the skin of Eq. (6)), in free flight: atoms 3.2 apart
+    never come within rc, feel no force and keep their velocities, so after
+    25 steps with a rebuild every 10 the largest displacement since a
+    rebuild is that of the fastest atom over 10 steps."""
+    k = np.arange(3)
+    pos = 3.2 * np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3) + 0.1
+    box = np.full(3, 9.6)
+    vel = np.random.default_rng(8).uniform(-1.0, 1.0, pos.shape)
+    dt = 0.005
+    _, v, F, _, md = oracle.md_run(pos, vel, box, 25, rc=2.5, r_list=2.8, rebuild_every=10, dt=dt)
+    assert (F == 0).all() and np.array_equal(v, vel)
+    expect = 10 * dt * np.sqrt((vel ** 2).sum(1)).max()
+    assert abs(md - expect) < 1e-12
+
+
 def _cold_crystal(dt, nsteps):
     lat = make_lattice("fcc", 4, RHO)
     pos = lat.sites() + rng_stream(5, 0).normal(0, 0.005, (lat.nsite, 3))

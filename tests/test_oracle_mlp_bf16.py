@@ -9,7 +9,8 @@ classifier parity tests use (CPU only).
   differs from it by rounding only on general inputs;
 - the rounding points: every activation entering a product is a BF16 value
   (torch's conversion leaves it unchanged) and each hidden layer is its
-  ReLU pre-activation rounded once;
+  ReLU pre-activation rounded once; weights moved by less than a quarter
+  BF16 step leave the logits unchanged;
 - the tolerance: an emulation of the library's arithmetic (the same BF16
   rounding points, sums accumulated in FP32 instead of FP64) stays within
   flip_tolerance on every row of oracle features of the four structures,
@@ -96,6 +97,23 @@ def test_forward_bf16_operands_are_bf16_values():
         assert not is_bf16(r)  # the pre-activations are wider: the rounding is a real step
         assert np.all(np.abs(h - r) <= 2.0 ** -8 * r)
         assert (h > 0).any()
+
+
+def test_forward_bf16_weights_enter_as_bf16():
+    """The weight matrices enter as BF16 values: moving every weight by less
+    than a quarter of its BF16 step (so that it rounds to the same BF16
+    value) leaves the logits unchanged bit for bit."""
+    p = op.unpack(op.train_params().astype(np.float64))
+    rng = np.random.default_rng(6)
+    x = omlp.bf16_round(rng.normal(0.3, 0.4, (2000, 30)))
+    ref = omlp.forward_bf16(p, x)[0]
+    for k in ("W1", "W2", "W3"):
+        w = torch.from_numpy(p[k].astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+        step = op.bf16_step(w)
+        moved = w + rng.uniform(-0.24, 0.24, w.shape) * step
+        assert not np.array_equal(moved, w)
+        q = dict(p, **{k: moved})
+        assert np.array_equal(omlp.forward_bf16(q, x)[0], ref), k
 
 
 def _emulate_fp32(q, x):

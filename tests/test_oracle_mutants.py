@@ -110,6 +110,53 @@ MUTANTS = {
                     [AN + "test_acna_perfect_lattices_at_any_density"]),
     "acna_bcc_weight_on_second_shell": ("rc14 = f * ((c * s8 + s6) / 14.0);", "rc14 = f * ((s8 + c * s6) / 14.0);",
                                         0, [AN + "test_acna_perfect_lattices_at_any_density"]),
+    # more of the same regions, each with the pin that catches it
+    "brute_force_lists_the_atom_itself": ("if (j == i) continue;", "if (0) continue;", 0,
+                                          [MD + "test_neighbour_list_cells_equal_brute_force"]),
+    "cell_prefix_sum_one_short": ("for (int64_t c = 0; c < ncell; ++c) cell_start[c + 1] += cell_start[c];",
+                                  "for (int64_t c = 0; c + 1 < ncell; ++c) cell_start[c + 1] += cell_start[c];", 0,
+                                  [MD + "test_lattice_energy_closed_form"]),
+    "wrap_upper_edge_kept": ("if (y >= L) y = 0.0;", "if (y > L) y = 0.0;", 0,
+                             [MD + "test_wrap_maps_into_the_half_open_box"]),
+    "force_cutoff_ignored": ("            if (!(r2 < rc2)) continue;\n            double sr2", "            double sr2", 0,
+                             [MD + "test_newton_third_law_and_energy_sum"]),
+    "second_kick_also_drifts": ("if (phase == 1) pos[3 * i + d]", "if (phase >= 1) pos[3 * i + d]", 0,
+                                [MD + "test_vv_constant_force_closed_form"]),
+    "potential_energy_halved": ("energies[2 * (s - 1) + 1] = U;", "energies[2 * (s - 1) + 1] = 0.5 * U;", 1,
+                                [MD + "test_vv_energy_error_is_second_order"]),
+    "skin_guard_not_a_maximum": ("if (d2 > md2) md2 = d2;", "md2 = d2;", 1,
+                                 [MD + "test_md_max_displacement_since_rebuild"]),
+    "skin_guard_reference_kept": ("memcpy(ref, pos, sizeof(double) * (size_t)(3 * n));\n        }", "}", 1,
+                                  [MD + "test_md_max_displacement_since_rebuild"]),
+    "ylm_factorials_swapped": ("factorial(l - am) / factorial(l + am)", "factorial(l + am) / factorial(l - am)", 0,
+                               [MD + "test_otf_q_rows_of_a_crystal_at_rest"]),
+    "q_rows_mean_over_n_minus_1": ("sum / (double)(n > 0 ? n : 1)", "sum / (double)(n > 1 ? n - 1 : 1)", 0,
+                                   [MD + "test_otf_q_rows_of_a_crystal_at_rest"]),
+    "q_rows_one_step_early": ("if (boa_every > 0 && s % boa_every == 0) {",
+                              "if (boa_every > 0 && (s - 1) % boa_every == 0) {", 0,
+                              [MD + "test_otf_q_rows_of_a_crystal_at_rest"]),
+    "andersen_second_draw_counter": ("ctr[3] = 1u;", "ctr[3] = 2u;", 0, [MD + "test_andersen_every_atom_every_step"]),
+    "andersen_counter_words_swapped": ("uint32_t ctr[4] = {(uint32_t)id, (uint32_t)step,",
+                                       "uint32_t ctr[4] = {(uint32_t)step, (uint32_t)id,", 0,
+                                       [MD + "test_andersen_every_atom_every_step"]),
+    "cna_bonds_capped_at_12": ("nbond[i] = ni;", "nbond[i] = ni < 12 ? ni : 12;", 0,
+                               [AN + "test_perfect_lattice_cna_signatures"]),
+    "bcc_signature_counts_swapped": ("nb == 14 && c666 == 8 && c444 == 6) lab = 3;",
+                                     "nb == 14 && c666 == 6 && c444 == 8) lab = 3;", 0,
+                                     [AN + "test_perfect_lattice_cna_signatures"]),
+    "feature_q_at_the_bond_length": ("ora_boa_direct(n, pos, L, r_feat, offs, nbr, 4, q4, NULL);",
+                                     "ora_boa_direct(n, pos, L, r_ref, offs, nbr, 4, q4, NULL);", 0,
+                                     [AN + "test_features_shell_between_the_cutoffs"]),
+    "feature_bonds_at_the_feature_cutoff": ("if (!(r2 < r_ref * r_ref)) continue;", "if (!(r2 < rc2)) continue;", 0,
+                                            [AN + "test_features_shell_between_the_cutoffs"]),
+    "feature_distances_unsorted": ("qsort(d, (size_t)nu, sizeof(double), cmp_f64);", ";", 0,
+                                   [AN + "test_features_rotation_invariant_and_counts"]),
+    "feature_missing_distance_zero": ("(k < nu) ? (d[k] - r_ref) / (r_feat - r_ref) : 1.0;",
+                                      "(k < nu) ? (d[k] - r_ref) / (r_feat - r_ref) : 0.0;", 0,
+                                      [AN + "test_features_perfect_fcc_closed_form"]),
+    "acna_skips_the_nearest": ("for (int a = 0; a < 12; ++a) {\n                s += sqrt(cand[a].r2);",
+                               "for (int a = 1; a < 13; ++a) {\n                s += sqrt(cand[a].r2);", 0,
+                               [AN + "test_acna_perfect_lattices_at_any_density"]),
 }
 
 # the classifier's network, forward and backward passes, AdamW (oracle/mlp.py)
@@ -137,6 +184,18 @@ MLP_MUTANTS = {
                                        'f32(x) * f32(p["isd"]) - f32(p["mu"])', 0,
                                        [BF + "test_forward_bf16_is_the_network_on_exact_operands",
                                         BF + "test_forward_bf16_differs_by_rounding_only"]),
+    "loss_summed_not_averaged": ("loss = -np.mean(np.log(prob[np.arange(n), y]))",
+                                 "loss = -np.sum(np.log(prob[np.arange(n), y]))", 0,
+                                 [AN + "test_mlp_gradient_matches_finite_differences"]),
+    "adamw_second_moment_unsquared": ("(1.0 - b2) * g * g", "(1.0 - b2) * g", 0, [AN + "test_adamw_textbook_steps"]),
+    "constant_feature_scaled_to_zero": ("1.0 / np.sqrt(np.maximum(var, 1e-300)), 1.0)",
+                                        "1.0 / np.sqrt(np.maximum(var, 1e-300)), 0.0)", 0,
+                                        [AN + "test_mlp_input_standardisation"]),
+    "bf16_bias_rounded": ('z1 = xs @ W1 + f32(p["b1"]).astype(np.float64)', 'z1 = xs @ W1 + bf16_round(p["b1"])', 0,
+                          [BF + "test_tolerance_covers_fp32_accumulation"]),
+    "bf16_last_weights_unrounded": ('W1, W2, W3 = (bf16_round(p[k]) for k in ("W1", "W2", "W3"))',
+                                    'W1, W2, W3 = bf16_round(p["W1"]), bf16_round(p["W2"]), p["W3"]', 0,
+                                    [BF + "test_forward_bf16_weights_enter_as_bf16"]),
 }
 
 # the Python side of the oracle package (oracle/__init__.py): the bond-order
