@@ -340,6 +340,18 @@ def test_mlp_input_standardisation():
     assert np.array_equal(p["mu"], mu0)
 
 
+def test_softmax_of_large_logits():
+    """Softmax is unchanged by a common shift of the logits, and stays finite
+    for logits far beyond exp's range (the largest logit is taken out
+    first)."""
+    rng = np.random.default_rng(4)
+    z = rng.normal(0, 3, (100, 4))
+    assert np.allclose(mlp.softmax(z), mlp.softmax(z + 700.0), rtol=1e-12, atol=0)
+    p = mlp.softmax(np.array([[1000.0, 0.0, -1000.0, 999.0]]))
+    assert np.isfinite(p).all() and abs(p.sum() - 1.0) < 1e-15
+    assert np.allclose(p, [[1 / (1 + np.exp(-1.0)), 0.0, 0.0, np.exp(-1.0) / (1 + np.exp(-1.0))]], rtol=1e-14)
+
+
 def test_adamw_textbook_steps():
     """Three parameters, two steps, against values worked out by hand from the
     AdamW update (bias-corrected moments, decoupled decay on weights)."""

@@ -77,6 +77,10 @@ def test_neighbour_list_cells_equal_brute_force(seed):
 def test_cells_contain_their_atoms():
     c = configs.lj_solid(n_cells=6)
     pos, box = c["pos"], c["box"]
+    # and atoms a hair below each box face, whose x / w can round up to n
+    edge = np.array([np.nextafter(box, 0.0), [np.nextafter(box[0], 0.0), 0.0, 0.0],
+                     [0.0, np.nextafter(box[1], 0.0), 0.0], [0.0, 0.0, np.nextafter(box[2], 0.0)]])
+    pos = np.concatenate([pos, edge])
     nc, cell_of, start, atoms = oracle.cells(pos, box, 2.8)
     assert (nc == np.floor(box / 2.8)).all()
     w = box / nc
@@ -84,6 +88,7 @@ def test_cells_contain_their_atoms():
     cy, cx = np.divmod(rem, nc[0])
     cc = np.stack([cx, cy, cz], 1)
     assert (cc * w <= pos + 1e-12).all() and (pos < (cc + 1) * w + 1e-12).all()
+    assert (cc[-4:] == np.array([nc - 1, [nc[0] - 1, 0, 0], [0, nc[1] - 1, 0], [0, 0, nc[2] - 1]])).all()
     assert start[0] == 0 and start[-1] == len(pos) and (np.diff(start) >= 0).all()
     for c_ in range(len(start) - 1):
         members = atoms[start[c_]:start[c_ + 1]]
@@ -144,6 +149,23 @@ def test_shift_changes_energy_not_force():
     assert np.allclose(e1 - e0, np.diff(offs) * 0.5, rtol=0, atol=1e-12)
 
 
+def test_cells_of_atoms_below_the_box_face():
+    """For these edges (14.0 and neighbours, cells of 2.8) the largest double
+    below L divided by the cell width rounds to n itself: such an atom
+    belongs to the last cell, n - 1."""
+    box = np.array([14.0, 14.004, 14.008])
+    nc = oracle.cell_grid(box, 2.8)
+    below = np.nextafter(box, 0.0)
+    assert (np.floor(below / (box / nc)) == nc).all()  # the rounding the clamp is for
+    pos = np.array([[1.0, 1.0, 1.0], below, [below[0], 0.0, 7.0], [7.0, below[1], 0.0], [0.0, 7.0, below[2]]])
+    _, cell_of, start, atoms = oracle.cells(pos, box, 2.8)
+    cz, rem = np.divmod(cell_of, nc[0] * nc[1])
+    cy, cx = np.divmod(rem, nc[0])
+    assert [cx[1], cy[1], cz[1]] == list(nc - 1)
+    assert cx[2] == nc[0] - 1 and cy[3] == nc[1] - 1 and cz[4] == nc[2] - 1
+    assert start[-1] == len(pos) and sorted(atoms) == list(range(len(pos)))
+
+
 def test_vv_constant_force_closed_form():
     """One step of Algorithm 6 under a constant force reproduces the exact
     kinematics r + v dt + F dt^2 / (2m) and v + F dt / m."""
@@ -194,18 +216,21 @@ def test_md_max_displacement_since_rebuild():
     assert abs(md - expect) < 1e-12
 
 
-def _cold_crystal(dt, nsteps):
+def _cold_crystal(dt, nsteps, mass=1.0):
     lat = make_lattice("fcc", 4, RHO)
     pos = lat.sites() + rng_stream(5, 0).normal(0, 0.005, (lat.nsite, 3))
-    vel = maxwell_boltzmann(rng_stream(5, 1), lat.nsite, 0.01)
-    return oracle.md_run(pos, vel, lat.box, nsteps, rc=2.5, r_list=2.5, rebuild_every=1, dt=dt)
+    vel = maxwell_boltzmann(rng_stream(5, 1), lat.nsite, 0.01 / mass)
+    return oracle.md_run(pos, vel, lat.box, nsteps, rc=2.5, r_list=2.5, rebuild_every=1, dt=dt, mass=mass)
 
 
-def test_vv_energy_error_is_second_order():
+@pytest.mark.parametrize("mass", [1.0, 2.0])
+def test_vv_energy_error_is_second_order(mass):
     """Velocity Verlet conserves energy up to O(dt^2): halving dt quarters the
-    energy fluctuation (cold fcc crystal: no pair crosses the cutoff)."""
-    _, v_a, _, en_a, _ = _cold_crystal(0.005, 200)
-    _, v_b, _, en_b, _ = _cold_crystal(0.0025, 400)
+    energy fluctuation (cold fcc crystal: no pair crosses the cutoff).  With
+    mass 2 the recorded kinetic energy must carry the mass for the total to
+    be conserved."""
+    _, v_a, _, en_a, _ = _cold_crystal(0.005, 200, mass)
+    _, v_b, _, en_b, _ = _cold_crystal(0.0025, 400, mass)
     ea = en_a.sum(1)
     eb = en_b.sum(1)
     fa = ea.max() - ea.min()
@@ -292,6 +317,20 @@ def test_andersen_every_atom_every_step():
     assert abs((vel ** 2).mean() / T - 1.0) < 4 * np.sqrt(2.0 / (3 * n))
 
 
+def test_andersen_draws_have_variance_t_over_m():
+    """Every atom redrawn from the heat bath at mass 2 (equipartition): each
+    velocity component has mean 0 and variance T/m."""
+    c = configs.lj_solid(n_cells=6)
+    n = len(c["pos"])
+    T, m = 0.7, 2.0
+    _, vel, _, _, _, _, ncoll = oracle.md_run_otf(c["pos"], c["vel"], c["box"], 2, r_list=2.8, rebuild_every=10,
+                                                  mass=m, thermostat=(T, 1000.0, 99))
+    assert ncoll == 2 * n
+    k = 3 * n
+    assert abs(vel.mean()) < 4 * np.sqrt(T / m / k)
+    assert abs((vel ** 2).mean() / (T / m) - 1.0) < 4 * np.sqrt(2.0 / k)
+
+
 def test_andersen_collision_rate():
     c = configs.lj_solid(n_cells=6)
     n, steps, nu, dt = len(c["pos"]), 20, 4.0, 0.005
@@ -315,6 +354,20 @@ def test_otf_q_rows_of_a_crystal_at_rest(golden):
         assert np.allclose(qrows[s], [tab["Q4"], tab["Q5"], tab["Q6"]], atol=5e-4)
     assert (qrows[[0, 2, 4]] == 0).all()
     assert np.allclose(qlast.mean(1), qrows[5], rtol=1e-13, atol=1e-15)
+
+
+def test_otf_q_rows_of_hcp_at_rest(golden):
+    """hcp at rest (every site is a mirror of itself across the basal plane
+    and has a threefold axis along c, so it feels no force): the analysis
+    rows hold the paper's Q4, Q5, Q6 of hcp, whose Q5 is not zero."""
+    lat = make_lattice("hcp", (6, 4, 4), 0.8442)
+    pos = lat.sites()
+    *_, qrows, qlast, _ = oracle.md_run_otf(pos, np.zeros_like(pos), lat.box, 4, rc=2.5, r_list=2.8,
+                                            rebuild_every=2, boa=(1, 1.5))
+    tab = golden["Q_table"]["hcp"]
+    assert tab["Q5"] > 0.2
+    for s in range(4):
+        assert np.allclose(qrows[s], [tab["Q4"], tab["Q5"], tab["Q6"]], atol=5e-4)
 
 
 def test_md_run_same_on_any_thread_count():

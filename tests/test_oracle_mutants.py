@@ -157,6 +157,54 @@ MUTANTS = {
     "acna_skips_the_nearest": ("for (int a = 0; a < 12; ++a) {\n                s += sqrt(cand[a].r2);",
                                "for (int a = 1; a < 13; ++a) {\n                s += sqrt(cand[a].r2);", 0,
                                [AN + "test_acna_perfect_lattices_at_any_density"]),
+    "addition_route_self_pairs_dropped": ("for (int b = 0; b < nu; ++b) {\n                double c = u[3 * a]",
+                                          "for (int b = 0; b < nu; ++b) if (b != a) {\n                double c = u[3 * a]",
+                                          0, [AN + "test_Q_direct_equals_addition_theorem"]),
+    "addition_route_divides_by_nu_squared": ("Q[i] = sqrt(s) / nu;", "Q[i] = sqrt(s) / ((double)nu * nu);", 0,
+                                             [AN + "test_Q_direct_equals_addition_theorem"]),
+    "q5_skipped_in_the_run": ("for (int l = 4; l <= 6; ++l) {", "for (int l = 4; l <= 6; l += 1 + (l == 4)) {", 0,
+                              [MD + "test_otf_q_rows_of_hcp_at_rest"]),
+    "stencil_wraps_by_n_plus_1": ("int32_t x = (cx + ox + nc[0]) % nc[0];", "int32_t x = (cx + ox + nc[0]) % (nc[0] + 1);",
+                                  0, [MD + "test_lattice_energy_closed_form"]),
+    "energy_attractive_term_sign": ("ei += 0.5 * 4.0 * eps * (sr12 - sr6 + shift);",
+                                    "ei += 0.5 * 4.0 * eps * (sr12 + sr6 + shift);", 0,
+                                    [MD + "test_lattice_energy_closed_form"]),
+    "kinetic_without_mass": ("k += 0.5 * mass *", "k += 0.5 *", 0, [MD + "test_vv_energy_error_is_second_order"]),
+    "rebuild_at_the_force_cutoff": ("build_list_cells(n, pos, L, r_list, offs, &nbr, &cap);\n            memcpy",
+                                    "build_list_cells(n, pos, L, rc, offs, &nbr, &cap);\n            memcpy", 1,
+                                    [MD + "test_md_rebuild_policy_matches_fresh_lists"]),
+    "philox_output_words_swapped": ("out[1] = c1;\n    out[2] = c2;", "out[1] = c2;\n    out[2] = c1;", 0,
+                                    [MD + "test_philox4x32_known_answers"]),
+    "philox_low_and_high_halves": ("c1 = lo1;", "c1 = hi1;", 0, [MD + "test_philox4x32_known_answers"]),
+    "thermostat_before_the_second_kick": (
+        "ora_vv(2, n, pos, vel, F, L, mass, dt);\n        if (energies) {\n            energies[2 * (s - 1)] = "
+        "ora_kinetic(n, vel, mass);\n            energies[2 * (s - 1) + 1] = U;\n        }\n        if (thr > 0)\n"
+        "            for (int64_t i = 0; i < n; ++i) ncoll += andersen_draw(seed, i, s, thr, sd, &vel[3 * i]);",
+        "if (thr > 0)\n            for (int64_t i = 0; i < n; ++i) ncoll += andersen_draw(seed, i, s, thr, sd, "
+        "&vel[3 * i]);\n        ora_vv(2, n, pos, vel, F, L, mass, dt);\n        if (energies) {\n            "
+        "energies[2 * (s - 1)] = ora_kinetic(n, vel, mass);\n            energies[2 * (s - 1) + 1] = U;\n        }",
+        0, [MD + "test_andersen_every_atom_every_step"]),
+    "andersen_spread_without_mass": ("const double sd = sqrt(T / mass);", "const double sd = sqrt(T);", 0,
+                                     [MD + "test_andersen_draws_have_variance_t_over_m"]),
+    "box_muller_radius_not_rooted": ("const double r1 = sqrt(-2.0 * log(U1)), t1 = two_pi * U2;",
+                                     "const double r1 = -2.0 * log(U1), t1 = two_pi * U2;", 0,
+                                     [MD + "test_andersen_every_atom_every_step"]),
+    "uniform_without_the_half": ("const double U1 = ((double)u[1] + 0.5) * inv32", "const double U1 = ((double)u[1]) * inv32",
+                                 0, [MD + "test_andersen_every_atom_every_step"]),
+    "cluster_neighbour_not_queued": ("if (!seen) Q[qn++] = w;", "if (0) Q[qn++] = w;", 0,
+                                     [AN + "test_perfect_lattice_cna_signatures"]),
+    "acna_triplet_counts_the_bond_partner": (
+        "if (b != a && min_image(&pos[3 * sel[a]], &pos[3 * sel[b]], L, dr) < rc2) cn[ncn++] = sel[b];",
+        "if (min_image(&pos[3 * sel[a]], &pos[3 * sel[b]], L, dr) < rc2) cn[ncn++] = sel[b];", 0,
+        [AN + "test_acna_perfect_lattices_at_any_density"]),
+    "acna_bcc_test_overrides_fcc": ("if (lab == 0 && deg >= 14) {", "if (deg >= 14) {", 0,
+                                    [AN + "test_acna_perfect_lattices_at_any_density"]),
+    "chord_from_the_sum_of_bonds": (
+        "double cx = u[3 * a] - u[3 * b], cy = u[3 * a + 1] - u[3 * b + 1], cz = u[3 * a + 2] - u[3 * b + 2];",
+        "double cx = u[3 * a] + u[3 * b], cy = u[3 * a + 1] + u[3 * b + 1], cz = u[3 * a + 2] + u[3 * b + 2];", 0,
+        [AN + "test_features_perfect_fcc_closed_form"]),
+    "histogram_low_edge_shifted": ("double lo = r_ref - 0.35;", "double lo = r_ref - 0.30;", 0,
+                                   [AN + "test_features_perfect_fcc_closed_form"]),
 }
 
 # the classifier's network, forward and backward passes, AdamW (oracle/mlp.py)
@@ -196,6 +244,20 @@ MLP_MUTANTS = {
     "bf16_last_weights_unrounded": ('W1, W2, W3 = (bf16_round(p[k]) for k in ("W1", "W2", "W3"))',
                                     'W1, W2, W3 = bf16_round(p["W1"]), bf16_round(p["W2"]), p["W3"]', 0,
                                     [BF + "test_forward_bf16_weights_enter_as_bf16"]),
+    "softmax_shifted_by_the_minimum": ("z = logits - logits.max(axis=1, keepdims=True)",
+                                       "z = logits - logits.min(axis=1, keepdims=True)", 0,
+                                       [AN + "test_softmax_of_large_logits"]),
+    "adamw_decay_without_lr": ("p[k] = p[k] - lr * wd * p[k]", "p[k] = p[k] - wd * p[k]", 0,
+                               [AN + "test_adamw_textbook_steps"]),
+    "adamw_second_moment_corrected_by_b1": ("vh = v / (1.0 - b2 ** t)", "vh = v / (1.0 - b1 ** t)", 0,
+                                            [AN + "test_adamw_textbook_steps"]),
+    "bias_gradient_from_the_wrong_layer": ('grads["b2"] = d2.sum(0)', 'grads["b2"] = d1.sum(0)', 0,
+                                           [AN + "test_mlp_gradient_matches_finite_differences"]),
+    "bf16_round_truncates": ("r = ((u + 0x7FFF + keep_lsb) >> 16) << 16", "r = (u >> 16) << 16", 0,
+                             [BF + "test_bf16_round_matches_torch"]),
+    "bf16_standardised_inputs_unrounded": ('xs = bf16_round((f32(x) - f32(p["mu"])) * f32(p["isd"]))',
+                                           'xs = (f32(x) - f32(p["mu"])) * f32(p["isd"])', 0,
+                                           [BF + "test_forward_bf16_operands_are_bf16_values"]),
 }
 
 # the Python side of the oracle package (oracle/__init__.py): the bond-order
@@ -298,7 +360,7 @@ def copy_package(top):
 def results():
     """Every mutant made and its pins run, several at a time."""
     with tempfile.TemporaryDirectory() as tmp:
-        with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
             futs = {("c", k): ex.submit(_mutant, "c", k, tmp) for k in MUTANTS}
             futs.update({("py", k): ex.submit(_mutant, "py", k, tmp) for k in MLP_MUTANTS})
             futs.update({("pkg", k): ex.submit(_mutant, "pkg", k, tmp) for k in PKG_MUTANTS})
