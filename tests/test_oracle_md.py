@@ -139,6 +139,22 @@ def test_newton_third_law_and_energy_sum():
     assert np.abs(F - F2).max() < 1e-12 * rmsF
 
 
+def test_lj_scales_with_epsilon_and_sigma():
+    """Eqs. (7)-(8) in reduced units: stretching every length (positions,
+    box, cutoff) by sigma and every energy by epsilon leaves the reduced
+    problem unchanged, so the per-atom energies, U and W scale by epsilon
+    and the forces by epsilon / sigma (the paper's 1/4 shift included)."""
+    c = configs.lj_solid(n_cells=6)
+    pos, box = c["pos"], c["box"]
+    offs, nb = oracle.neighbours_cells(pos, box, 2.8)
+    F1, e1, U1, W1 = oracle.lj(pos, box, offs, nb, rc=2.5, eps=1.0, sigma=1.0, shift=0.25)
+    eps, sigma = 1.7, 1.3
+    F, e, U, W = oracle.lj(pos * sigma, box * sigma, offs, nb, rc=2.5 * sigma, eps=eps, sigma=sigma, shift=0.25)
+    assert np.allclose(e, eps * e1, rtol=1e-12, atol=1e-12 * np.abs(e1).max())
+    assert abs(U - eps * U1) <= 1e-12 * abs(U1) and abs(W - eps * W1) <= 1e-12 * abs(W1)
+    assert np.allclose(F, eps / sigma * F1, rtol=0, atol=1e-12 * np.abs(F1).max())
+
+
 def test_shift_changes_energy_not_force():
     c = configs.lj_small()
     offs, nbr = oracle.neighbours_cells(c["pos"], c["box"], 2.5)

@@ -49,6 +49,12 @@ MUTANTS = {
                            [MD + "test_force_is_minus_energy_gradient"]),
     "energy_not_halved": ("ei += 0.5 * 4.0 * eps", "ei += 4.0 * eps", 0,
                           [MD + "test_lattice_energy_closed_form"]),
+    "sigma_left_out_of_the_ratio": ("double sr2 = s2 / r2;", "double sr2 = 1.0 / r2;", 0,
+                                    [MD + "test_lj_scales_with_epsilon_and_sigma"]),
+    "force_prefactor_without_sigma": ("double fmag = 48.0 * eps / s2", "double fmag = 48.0 * eps", 0,
+                                      [MD + "test_lj_scales_with_epsilon_and_sigma"]),
+    "energy_without_epsilon": ("ei += 0.5 * 4.0 * eps * (", "ei += 0.5 * 4.0 * (", 0,
+                               [MD + "test_lj_scales_with_epsilon_and_sigma"]),
     "shift_sign": ("(sr12 - sr6 + shift)", "(sr12 - sr6 - shift)", 0,
                    [MD + "test_lattice_energy_closed_form"]),
     "virial_not_halved": ("wsum += 0.5 * fmag * r2;", "wsum += fmag * r2;", 0,
