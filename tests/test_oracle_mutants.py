@@ -327,7 +327,6 @@ def run_pins(pins, lib=None, py=None):
 
 
 def _mutant(kind, name, tmp):
-    sys.path.insert(0, ROOT)
     import oracle
     if kind == "c":
         old, new, occurrence, pins = MUTANTS[name]
