@@ -624,7 +624,7 @@ def suite_small(args, L, ctx, stream):
 
 
 def suite_otf(args, L, ctx, stream):
-    """The on-the-fly analysis run (Sec. 5.3) at the size of its weak-scaling
+    """The on-the-fly analysis run (Sec. 5.2) at the size of its weak-scaling
     table: 524,288 atoms, rho 0.8442, rc 3.0, list 3.3, rebuild every 18;
     Andersen thermostat (T 0.1, nu 1) and Q4/Q5/Q6 (cutoff 1.5) on every step,
     against the same run without them."""

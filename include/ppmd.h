@@ -72,11 +72,11 @@ typedef struct {
  * coordinates, integration and global reductions stay in double. */
 typedef enum { PPMD_FP64 = 0, PPMD_FP32 = 1 } ppmd_prec;
 
-/* Truncated Lennard-Jones, Eq. (7) and Eq. (8):
+/* Truncated Lennard-Jones, Eq. (9) and Eq. (12):
  *   V(r) = 4 eps ((sigma/r)^12 - (sigma/r)^6 + shift)   for r < rc, else 0
  *   F_i  = sum_j 48 eps / sigma^2 (r_i - r_j) ((sigma/r)^14 - (sigma/r)^8 / 2)
  * shift = 0 gives the truncated, unshifted potential; shift = 0.25 is the
- * form printed as Eq. (7).  Forces do not depend on shift. */
+ * form printed as Eq. (9).  Forces do not depend on shift. */
 typedef struct {
     double eps, sigma, rc, shift;
 } ppmd_lj_params;
@@ -118,7 +118,7 @@ int ppmd_build_cells(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box
                      int32_t *cell_of, int32_t *cell_start, int32_t *cell_atoms, int32_t ncell_out[3],
                      int64_t cell_capacity);
 
-/* Neighbour list, Sec. 3.5 and Eq. (6): for every atom i all j != i with
+/* Neighbour list, Sec. 3.5 and Eq. (3): for every atom i all j != i with
  * |r_i - r_j| < r_list (minimum image), found through the 27 cells around
  * the cell of i.  This is the paper's neighbour matrix W (W_{m,i} = m-th
  * neighbour of i), stored transposed as nbr[i * max_nbr + m] so that the
@@ -133,7 +133,7 @@ int ppmd_build_neighbours(ppmd_ctx *ctx, const double *pos, int64_t n, const ppm
                           const int32_t *cell_start, const int32_t *cell_atoms, const int32_t ncell[3],
                           int32_t *nbr, int32_t *nbr_count, int32_t max_nbr, int32_t *needed_max_nbr);
 
-/* Lennard-Jones pair loop over a neighbour list (Eqs. (7)-(8), Listing
+/* Lennard-Jones pair loop over a neighbour list (Eqs. (9) and (12), Listing
  * "LJ-kernel"): every listed ordered pair (i, j) with r < rc adds its force
  * to i only (Sec. 2, no Newton's-third-law symmetry).  force[n][3] has
  * INC_ZERO semantics (set, not accumulated).  e_atom[n] (device, may be
@@ -200,7 +200,7 @@ int ppmd_kinetic_energy(ppmd_ctx *ctx, const double *vel, int64_t n, double mass
 /* Structure analysis (Sec. 4).                                          */
 /* ------------------------------------------------------------------ */
 
-/* Bond order parameters, Eqs. (1)-(2) with Algorithms 1 and 2: for every
+/* Bond order parameters, Eqs. (4)-(5) with Algorithms 1 and 2: for every
  * atom i, nu_i = number of list neighbours j with |r_i - r_j| < r_cut and
  *   Q_l(i) = sqrt(4 pi / (2l+1) sum_{m=-l..l} |q_lm(i)|^2),
  *   q_lm(i) = (1/nu_i) sum_j Y_l^m(r_ij / |r_ij|),
@@ -211,7 +211,7 @@ int ppmd_kinetic_energy(ppmd_ctx *ctx, const double *vel, int64_t n, double mass
 int ppmd_boa_q46(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, double r_cut, const int32_t *nbr,
                  const int32_t *nbr_count, int32_t max_nbr, float *q4, float *q6, int32_t *n_nb);
 
-/* Common neighbour analysis, Eqs. (3)-(5) with Algorithms 3, 4, 5 and 7:
+/* Common neighbour analysis, Eqs. (6)-(8) with Algorithms 3, 4, 5 and 7:
  * atoms closer than r_cut are bonded; for each bonded pair (i, j) the
  * common neighbours C = N(i) n N(j), the bonds E among them and the
  * number of bonds in the largest connected part of (C, E) give the triplet
@@ -256,7 +256,7 @@ int ppmd_analyze_boxes(ppmd_ctx *ctx, const double *pos, int64_t nbox, const int
  *   bcc test,     N = 14:  r = f (c (d_1 + ... + d_8) + d_9 + ... + d_14) / 14,
  * f = (1 + sqrt 2)/2, c = 2/sqrt 3.  Only those N neighbours take part (all
  * bonded to the atom, two of them bonded when closer than r) and each bond
- * gets the triplet of Eqs. (3)-(5) over its common neighbours among them.
+ * gets the triplet of Eqs. (6)-(8) over its common neighbours among them.
  * Labels (caller order, label[n] device int8): 1 fcc (12 x (4,2,1)), 2 hcp
  * (6 x (4,2,1) + 6 x (4,2,2)), else 3 bcc (8 x (6,6,6) + 6 x (4,4,4) in the
  * 14-neighbour test), else 0.  rcut (device FP64 [n][2], may be NULL): the
@@ -284,7 +284,7 @@ int ppmd_acna(ppmd_ctx *ctx, const double *pos, int64_t n, const ppmd_box *box, 
 #define PPMD_MLP_NPARAM 6464
 
 /* Features of every atom from its bonds (r < r_feat, the BOA cutoff):
- * [0] Q4, [1] Q6 (Eqs. (1)-(2)); [2..15] the 14 smallest bond lengths d,
+ * [0] Q4, [1] Q6 (Eqs. (4)-(5)); [2..15] the 14 smallest bond lengths d,
  * ascending, as (d - r_ref) / (r_feat - r_ref) with r_ref < r_feat a
  * reference length (the CNA cutoff: values change sign where CNA's bond
  * test does), missing ones 1; [16..29] a histogram of the chords
@@ -319,7 +319,7 @@ int ppmd_mlp_train_step(ppmd_ctx *ctx, float *params, float *m, float *v, int64_
 /* Structure labels of every atom (caller order, label[n] device int8).
  * mode 2: bond order within a tolerance (Sec. 4.1, compared with the table
  * of Q4, Q5, Q6 of perfect lattices): Q4 and Q6 over neighbours within
- * r_feat (Eqs. (1)-(2)); the label is the lattice whose (Q4, Q6) in that
+ * r_feat (Eqs. (4)-(5)); the label is the lattice whose (Q4, Q6) in that
  * table (fcc 0.191, 0.575; hcp 0.097, 0.485; bcc 0.036, 0.511) is nearest in
  * the (Q4, Q6) plane, fcc before hcp before bcc on ties, when that distance
  * is below threshold (the tolerance, >= 0), else other; confidence (may be
@@ -351,7 +351,7 @@ int ppmd_classify_boxes(ppmd_ctx *ctx, int mode, const double *pos, int64_t nbox
 /* ------------------------------------------------------------------ */
 typedef struct {
     ppmd_lj_params lj;
-    double r_list;         /* list cutoff r_c + delta (Eq. (6)); per box min(r_list, box_r_list[b]) */
+    double r_list;         /* list cutoff r_c + delta (Eq. (3)); per box min(r_list, box_r_list[b]) */
     double mass, dt;
     int32_t rebuild_every; /* list rebuilt when step % rebuild_every == 0 (and at set-up) */
     int32_t max_nbr;       /* row capacity of the neighbour list (rounded up to a multiple of 8 for
@@ -389,7 +389,7 @@ int ppmd_md_set_state(ppmd_md *md, const double *pos, const double *vel);
  * step's first kick and drift (same arithmetic, so the same bits as separate
  * kernels); a run always ends with full-step velocities. */
 int ppmd_md_run(ppmd_md *md, int32_t nsteps, double *energies, int use_graph);
-/* The on-the-fly analysis run of Sec. 5.3: the time-stepping loop extended
+/* The on-the-fly analysis run of Sec. 5.2: the time-stepping loop extended
  * by an Andersen thermostat and by the bond order parameters.
  *
  * Andersen thermostat (nu = 0: off): at the end of step s (after the second
@@ -402,7 +402,7 @@ int ppmd_md_run(ppmd_md *md, int32_t nsteps, double *energies, int use_graph);
  * cos(2 pi U4), U1..U3 from words 1..3, U4 from word 0 of the draw at
  * counter word 3 = 1 (FP64).  Steps count from ppmd_md_set_state. */
 int ppmd_md_set_thermostat(ppmd_md *md, double T, double nu, uint64_t seed);
-/* Q4, Q5, Q6 (Eqs. (1)-(2)) of every atom over the integrator's own list,
+/* Q4, Q5, Q6 (Eqs. (4)-(5)) of every atom over the integrator's own list,
  * bonds r < r_boa (0 < r_boa <= rc), after every step s with
  * s % every == 0 (every = 0: off), on the positions of step s. */
 int ppmd_md_set_boa(ppmd_md *md, int32_t every, double r_boa);
@@ -458,7 +458,7 @@ int ppmd_md_set_pair_loop(ppmd_md *md, int mechanism);
 int ppmd_md_set_shape(ppmd_md *md, int32_t shape);
 int ppmd_md_get_shape(ppmd_md *md, int32_t *shape, int32_t *block, int32_t *per_sm, int32_t *brick_home);
 int ppmd_md_tune(ppmd_md *md, int32_t steps, const char *cache_path, int32_t *shape, double *ms_per_step, int *timed);
-/* List-age check (Sec. 3.5, Eq. (6): a list built with the extended cutoff
+/* List-age check (Sec. 3.5, Eq. (3): a list built with the extended cutoff
  * r_list = r_c + delta holds every pair that can come within r_c before the
  * next build only while no atom moves more than delta / 2).  With on != 0
  * every later rebuild counts the pairs that are within r_c at that rebuild
@@ -501,7 +501,7 @@ int ppmd_md_forces(ppmd_md *md);
  * the largest row.  Synchronises. */
 int ppmd_md_list_stats(ppmd_md *md, int64_t *pairs, int32_t *max_row);
 /* The list of the last build (Sec. 3.5: pairs within the list cutoff r_list
- * of Eq. (6) at that build) in the caller's order: nbr_count[i] (device
+ * of Eq. (3) at that build) in the caller's order: nbr_count[i] (device
  * int32 [n]) the number of neighbours of caller atom i, nbr (device int32
  * [n][max_nbr], row-major) the caller indices of its first max_nbr
  * neighbours in list order (entries past the count untouched).  Uses context

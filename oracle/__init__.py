@@ -147,7 +147,7 @@ def neighbours_cells(pos, box, r, cell_r=None):
 
 
 def lj(pos, box, offs, nbr, rc=2.5, eps=1.0, sigma=1.0, shift=0.0):
-    """Forces, per-atom energies, total energy U and virial W (Eqs. (7)-(8))."""
+    """Forces, per-atom energies, total energy U and virial W (Eqs. (9) and (12))."""
     pos, box = _f64(pos), _f64(box)
     n = len(pos)
     F = np.zeros((n, 3))
@@ -221,7 +221,7 @@ def md_run_otf(pos, vel, box, nsteps, rc=2.5, r_list=2.5, rebuild_every=1, dt=0.
 
 
 def boa(pos, box, offs, nbr, r_cut=1.5, l=6, method="direct"):
-    """Q_l per atom (Eqs. (1)-(2)); method 'direct' (Y_lm sums) or 'addition' (Legendre)."""
+    """Q_l per atom (Eqs. (4)-(5)); method 'direct' (Y_lm sums) or 'addition' (Legendre)."""
     pos, box = _f64(pos), _f64(box)
     n = len(pos)
     Q = np.zeros(n)

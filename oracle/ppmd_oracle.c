@@ -9,21 +9,21 @@
  * shares no code, header, table or helper with the CUDA library.
  *
  * Every routine is a direct transcription of a definition in the paper:
- *   - periodic domain, cell list and neighbour list: Sec. 3.5 and Eq. (6)
+ *   - periodic domain, cell list and neighbour list: Sec. 3.5 and Eq. (3)
  *     (extended cutoff), with the O(N^2) loop of Sec. 3.4 as brute force;
- *   - Lennard-Jones potential and force: Eq. (7) and Eq. (8) (appendix A.1);
+ *   - Lennard-Jones potential and force: Eq. (9) and Eq. (12) (appendix A.1);
  *   - Velocity Verlet: Algorithm 6 with the access descriptors of Table 5;
- *   - bond order parameters: Eqs. (1)-(2), Algorithms 1 and 2;
- *   - common neighbour analysis: Eqs. (3)-(5), Algorithms 3-5 and the
+ *   - bond order parameters: Eqs. (4)-(5), Algorithms 1 and 2;
+ *   - common neighbour analysis: Eqs. (6)-(8), Algorithms 3-5 and the
  *     largest-cluster Algorithm 7 (appendix D);
  *   - adaptive CNA (the extension the CNA section cites): per-atom cutoffs
- *     from the 12 or 14 nearest neighbours, then Eqs. (3)-(5).
+ *     from the 12 or 14 nearest neighbours, then Eqs. (6)-(8).
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - all cutoff tests are strict (r < rc), as in the printed kernels;
  *   - the pair energy is V(r) = 4 eps ((s/r)^12 - (s/r)^6 + shift) with
- *     shift = 0 (truncated, unshifted) by default and 1/4 for Eq. (7);
- *   - the force follows Eq. (8) (repulsive at short range);
+ *     shift = 0 (truncated, unshifted) by default and 1/4 for Eq. (9);
+ *   - the force follows Eq. (12) (repulsive at short range);
  *   - every ordered pair (i,j) is visited and only i is written (Sec. 2,
  *     "Comment on Newton's third law"), so the per-atom energy takes half of
  *     each pair term and the total energy is U = 1/2 sum_{i != j} V(r_ij);
@@ -197,7 +197,7 @@ int64_t ora_neigh_cells(int64_t n, const double *pos, const double *L, double r,
 }
 
 /* ------------------------------------------------------------------ */
-/* Lennard-Jones pair loop: Eq. (7) potential, Eq. (8) force.
+/* Lennard-Jones pair loop: Eq. (9) potential, Eq. (12) force.
  * For every ordered pair (i,j) in the list with r^2 < rc^2:
  *   F_i += 48 eps / sigma^2 * dr * ((sigma/r)^14 - 1/2 (sigma/r)^8)
  *   e_i += 1/2 * 4 eps ((sigma/r)^12 - (sigma/r)^6 + shift)
@@ -270,7 +270,7 @@ double ora_kinetic(int64_t n, const double *vel, double mass) {
 }
 
 /* Full time-stepping loop (Algorithm 6 driven by the list-reuse policy of
- * Sec. 3.5 / Eq. (6)): the list with cutoff r_list is built from the
+ * Sec. 3.5 / Eq. (3)): the list with cutoff r_list is built from the
  * initial positions, F(r_0) is computed once, and for s = 1..nsteps:
  * kick+drift, rebuild the list if s % rebuild_every == 0, forces, kick.
  * energies (if not NULL) receives [KE, PE] after every step (2*nsteps).
@@ -346,7 +346,7 @@ void ora_philox4x32(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
     out[3] = c3;
 }
 
-/* Andersen thermostat (the on-the-fly analysis run of Sec. 5.3 couples the
+/* Andersen thermostat (the on-the-fly analysis run of Sec. 5.2 couples the
  * system to one): at the end of step s, atom id collides with the heat bath
  * with probability p = nu dt, decided by the first word u0 of Philox at
  * counter (id, s mod 2^32, s / 2^32, 0) and key (seed mod 2^32, seed / 2^32):
@@ -381,10 +381,10 @@ uint64_t ora_andersen_threshold(double nu, double dt) {
 }
 
 /* Algorithm 6 as ora_md_run, with the additions of the on-the-fly analysis
- * run (Sec. 5.3): after the kick of step s (and the energies) the Andersen
+ * run (Sec. 5.2): after the kick of step s (and the energies) the Andersen
  * thermostat (thr = 0: none; T, seed as above); then, when boa_every > 0
  * and s % boa_every == 0, Q4, Q5, Q6 of every atom over the current list
- * with cutoff r_boa (Eqs. (1)-(2)), their means written to
+ * with cutoff r_boa (Eqs. (4)-(5)), their means written to
  * qrows[3 (s - 1) .. +2] and the per-atom values of the last such step to
  * qlast [3][n] (either may be NULL).  Returns the number of collisions. */
 int64_t ora_md_run_otf(int64_t n, double *pos, double *vel, double *F, const double *L, double eps, double sigma,
@@ -484,7 +484,7 @@ double ora_md_run(int64_t n, double *pos, double *vel, double *F, const double *
 }
 
 /* ------------------------------------------------------------------ */
-/* Bond order analysis, Eqs. (1)-(2), Algorithms 1-2.
+/* Bond order analysis, Eqs. (4)-(5), Algorithms 1-2.
  * Two independent evaluations of Q_l for l = 4 and l = 6:
  *  (a) direct: q~_lm = sum_j Y_l^m(r^_ij) with orthonormal spherical
  *      harmonics built from the associated Legendre three-term recurrence
@@ -627,7 +627,7 @@ void ora_boa_addition(int64_t n, const double *pos, const double *L, double r_cu
 }
 
 /* ------------------------------------------------------------------ */
-/* Common neighbour analysis, Eqs. (3)-(5), Algorithms 3, 4, 5 and 7.
+/* Common neighbour analysis, Eqs. (6)-(8), Algorithms 3, 4, 5 and 7.
  * Bonded: |r_i - r_j| < r_cut.  For every atom i the bond array E^(i)
  * (pairs of global ids) is filled by loop I (direct bonds (i, j)) and loop
  * II (indirect bonds (j, w) of every bonded j, w != i); loop III then forms
@@ -805,7 +805,7 @@ void ora_cna_label(int64_t n, const int32_t *nbond, const uint32_t *trip, int32_
 
 /* ------------------------------------------------------------------ */
 /* Local-environment features for the learned classifier (30 per atom):
- *   [0] Q4, [1] Q6 over neighbours within r_feat (Eqs. (1)-(2), computed by
+ *   [0] Q4, [1] Q6 over neighbours within r_feat (Eqs. (4)-(5), computed by
  *       the direct route above);
  *   [2..15]  the 14 smallest neighbour distances d within r_feat, ascending,
  *            as (d - r_ref) / (r_feat - r_ref) (r_ref: a reference length
@@ -906,7 +906,7 @@ void ora_features(int64_t n, const double *pos, const double *L, double r_feat, 
  * first bcc shell scaled to the second).  Only those N neighbours take part:
  * all are bonded to i, and two of them are bonded when closer than r_i
  * (strict, as everywhere).  The bond i-j then gets the CNA triplet of
- * Eqs. (3)-(5) over the common neighbours among the N, with Algorithm 7 for
+ * Eqs. (6)-(8) over the common neighbours among the N, with Algorithm 7 for
  * the largest cluster.  fcc: 12 x (4,2,1); hcp: 6 x (4,2,1) + 6 x (4,2,2)
  * (12-neighbour test); failing both, bcc: 8 x (6,6,6) + 6 x (4,4,4)
  * (14-neighbour test); else other.  A test that needs more neighbours than

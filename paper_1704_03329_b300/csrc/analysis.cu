@@ -1,7 +1,7 @@
 // Structure analysis over a neighbour list:
-//  - bond order parameters Q4, Q6 (Eqs. (1)-(2), Algorithms 1-2), one thread
+//  - bond order parameters Q4, Q6 (Eqs. (4)-(5), Algorithms 1-2), one thread
 //    per atom accumulating the spherical-harmonic moments of its bonds;
-//  - common neighbour analysis (Eqs. (3)-(5), Algorithms 3-5 and 7), one warp
+//  - common neighbour analysis (Eqs. (6)-(8), Algorithms 3-5 and 7), one warp
 //    per atom on 64-bit adjacency masks of the atom's bonded neighbours;
 //  - an analysis pipeline that bins and sorts the atoms by cell, builds the
 //    list and runs either analysis, returning results in caller order.
@@ -664,7 +664,7 @@ __device__ __forceinline__ int32_t ld_once_i32(const int32_t *p) {
 }
 
 // Q4, Q5, Q6 of the integrator's atoms (the on-the-fly analysis of
-// Sec. 5.3) over its column-major list W[m * ld + i], bonds r < r_cut:
+// Sec. 5.2) over its column-major list W[m * ld + i], bonds r < r_cut:
 // per atom into q3 [3][n] at out_idx[i] (the caller's order) and per block
 // the three sums into partials[3 * block + l - 4] (FP64).
 constexpr int BOA_OTF_BLOCK = 128;

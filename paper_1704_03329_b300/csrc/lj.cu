@@ -1,4 +1,4 @@
-// Lennard-Jones pair loop over a neighbour list (Eqs. (7)-(8), Listing
+// Lennard-Jones pair loop over a neighbour list (Eqs. (9) and (12), Listing
 // "LJ-kernel"): every ordered pair (i, j) writes to i only (Sec. 2).  A group
 // of G lanes handles one atom, each lane a strided share of its neighbours;
 // the G partial sums are merged with warp shuffles.

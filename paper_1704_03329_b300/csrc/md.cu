@@ -1,5 +1,5 @@
 // Time stepping: Algorithm 6 with the list-reuse policy of Sec. 3.5 and
-// Eq. (6) (the paper's IntegratorRange), for one box or a batch of
+// Eq. (3) (the paper's IntegratorRange), for one box or a batch of
 // independent boxes.  Particles are kept in device memory sorted by cell;
 // every list rebuild re-sorts them (the periodic reordering the paper's
 // conclusions call for), and whole rebuild periods are replayed as CUDA
@@ -88,7 +88,7 @@ struct ppmd_md {
     cudaGraphExec_t exec = nullptr, exec_ev = nullptr;
     int32_t graph_steps = 0;
     int64_t graph_kernels = 0, graph_kernels_ev = 0;
-    // on-the-fly analysis run (Sec. 5.3): Andersen thermostat and Q4/Q5/Q6
+    // on-the-fly analysis run (Sec. 5.2): Andersen thermostat and Q4/Q5/Q6
     uint64_t thermo_thr = 0, thermo_seed = 0;
     double thermo_sd = 0.0, Lmax = 0.0;
     int32_t boa_every = 0;

@@ -1,4 +1,4 @@
-// Neighbour-list build (Sec. 3.5, Eq. (6)): one warp per atom sweeps the 27
+// Neighbour-list build (Sec. 3.5, Eq. (3)): one warp per atom sweeps the 27
 // cells around its cell, tests every candidate in single precision from
 // fixed-point coordinates, re-tests pairs near the cutoff in double
 // precision, and compacts the hits with a warp ballot into the atom's row.

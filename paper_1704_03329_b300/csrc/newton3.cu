@@ -6,7 +6,7 @@
 // pays for it with one atomic update of the other atom per interacting pair
 // (the write conflicts the paper's design avoids).
 //
-// FP32 path: the pair terms of Eqs. (7)-(8) in single precision; each
+// FP32 path: the pair terms of Eqs. (9) and (12) in single precision; each
 // atom's own share in compensated (Kahan) sums, the shares received from
 // other atoms through float4 atomic adds (x, y, z, energy) into an FP32
 // buffer, so the order of those additions, and with it the last bits of

@@ -1,7 +1,7 @@
 // Brick-staged integrator path (FP32 pair arithmetic).
 //
 // The paper's neighbour matrix W (Sec. 3.5.1) holds, for each atom, the
-// atoms within the extended cutoff of Eq. (6).  Here the atoms are sorted by
+// atoms within the extended cutoff of Eq. (3).  Here the atoms are sorted by
 // cell and the grid is cut into bricks of cells; the neighbourhood of a
 // brick (its cells and one layer of cells around it) is a fixed list of
 // contiguous runs of the sorted atoms between two list builds.  A list entry

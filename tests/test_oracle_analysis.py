@@ -98,7 +98,7 @@ def test_boa_tolerance_rule_edges():
 
 @pytest.mark.parametrize("seed", [1, 2])
 def test_Q_direct_equals_addition_theorem(seed):
-    """Two independent routes to Q_l: sums of Y_l^m (Eq. (2)) and the Legendre
+    """Two independent routes to Q_l: sums of Y_l^m (Eq. (5)) and the Legendre
     addition theorem."""
     pos, box = random_box(150, [6.0, 6.0, 6.0], seed, cutoffs=(1.5,), margin=1e-6, min_dist=0.8)
     offs, nbr = oracle.neighbours_brute(pos, box, 1.5)

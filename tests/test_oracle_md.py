@@ -97,7 +97,7 @@ def test_cells_contain_their_atoms():
 
 @pytest.mark.parametrize("seed", [21, 22])
 def test_force_is_minus_energy_gradient(seed):
-    """F = -grad U (Eq. (8) from Eq. (7)) by central differences of the total energy;
+    """F = -grad U (Eq. (12) from Eq. (9)) by central differences of the total energy;
     pins the force's sign, exponents and prefactor."""
     pos, box = _tiny_box(seed)
     offs, nbr = oracle.neighbours_brute(pos, box, 2.5)
@@ -140,7 +140,7 @@ def test_newton_third_law_and_energy_sum():
 
 
 def test_lj_scales_with_epsilon_and_sigma():
-    """Eqs. (7)-(8) in reduced units: stretching every length (positions,
+    """Eqs. (9) and (12) in reduced units: stretching every length (positions,
     box, cutoff) by sigma and every energy by epsilon leaves the reduced
     problem unchanged, so the per-atom energies, U and W scale by epsilon
     and the forces by epsilon / sigma (the paper's 1/4 shift included)."""
@@ -217,7 +217,7 @@ def test_wrap_maps_into_the_half_open_box():
 
 def test_md_max_displacement_since_rebuild():
     """The skin guard of Sec. 3.5 (the largest displacement since the list was
-    built, against half the skin of Eq. (6)), in free flight: atoms 3.2 apart
+    built, against half the skin of Eq. (3)), in free flight: atoms 3.2 apart
     never come within rc, feel no force and keep their velocities, so after
     25 steps with a rebuild every 10 the largest displacement since a
     rebuild is that of the fastest atom over 10 steps."""

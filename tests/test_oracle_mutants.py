@@ -40,7 +40,7 @@ MUTANTS = {
                               [MD + "test_cells_contain_their_atoms"]),
     "stencil_misses_a_layer": ("for (int ox = -1; ox <= 1; ++ox)", "for (int ox = -1; ox <= 0; ++ox)", 0,
                                [MD + "test_neighbour_list_cells_equal_brute_force"]),
-    # Lennard-Jones pair loop, Eqs. (7)-(8)
+    # Lennard-Jones pair loop, Eqs. (9) and (12)
     "force_sign_x": ("fx += fmag * dr[0];", "fx -= fmag * dr[0];", 0,
                      [MD + "test_force_is_minus_energy_gradient"]),
     "force_exponent_12": ("double sr14 = sr12 * sr2;", "double sr14 = sr12;", 0,
@@ -69,7 +69,7 @@ MUTANTS = {
     "list_never_rebuilt": ("if (rebuild_every > 0 && s % rebuild_every == 0) {",
                            "if (rebuild_every < 0 && s % rebuild_every == 0) {", 1,
                            [MD + "test_md_rebuild_policy_matches_fresh_lists"]),
-    # bond order, Eqs. (1)-(2)
+    # bond order, Eqs. (4)-(5)
     "legendre_recurrence_index": ("- (ll + m - 1.0) * pmm) / (ll - m);", "- (ll + m) * pmm) / (ll - m);", 0,
                                   [AN + "test_perfect_lattice_Q_matches_paper_table"]),
     "ylm_norm_2pi": ("(2.0 * l + 1.0) / (4.0 * ORA_PI)", "(2.0 * l + 1.0) / (2.0 * ORA_PI)", 0,
@@ -80,7 +80,7 @@ MUTANTS = {
                     [AN + "test_Q_direct_equals_addition_theorem"]),
     "ylm_azimuth_without_m": ("yi = p * sin(am * phi);", "yi = p * sin(phi);", 0,
                               [AN + "test_Q_direct_equals_addition_theorem"]),
-    # common neighbour analysis, Eqs. (3)-(5), Algorithms 3-5 and 7
+    # common neighbour analysis, Eqs. (6)-(8), Algorithms 3-5 and 7
     "cna_common_not_tested": ("if (in_set(&direct[eoff[j]], nu_nb[j], v)) C[nc++] = v;",
                               "if (v != j) C[nc++] = v;", 0,
                               [AN + "test_perfect_lattice_cna_signatures"]),
@@ -99,7 +99,7 @@ MUTANTS = {
                                      [AN + "test_features_perfect_fcc_closed_form"]),
     "feature_histogram_norm": ("f[16 + b] /= 24.0;", "f[16 + b] /= 12.0;", 0,
                                [AN + "test_features_perfect_fcc_closed_form"]),
-    # Philox4x32-10 and the Andersen thermostat (Sec. 5.3)
+    # Philox4x32-10 and the Andersen thermostat (Sec. 5.2)
     "philox_multiplier": ("mulhilo32(0xCD9E8D57u, c2, &lo1)", "mulhilo32(0xCD9E8D59u, c2, &lo1)", 0,
                           [MD + "test_philox4x32_known_answers"]),
     "philox_weyl_constant": ("k1 += 0xBB67AE85u;", "k1 += 0x9E3779B9u;", 0,
