@@ -116,3 +116,24 @@ def test_integrator_state_and_energy_rows(L):
     _raises(lambda: md.run(10, f64(9, 2)), "energies", "20")
     _raises(lambda: md.run_analysed(10, None, f64(10, 2)), "qrows", "30")
     _raises(lambda: md.run(10, f64(10, 2)), "CUDA")
+
+
+def test_allocation_free_forces_check_their_arrays(L):
+    """ppmd_lj_forces_noalloc takes every array from the caller: positions
+    float64 [n][3], forces of the same shape, an int32 list of n rows and
+    counts; an n above the static limit is the one override it accepts
+    (refused by the library before anything runs)."""
+    pos, F = f64(6, 3), f64(6, 3)
+    nbr, cnt = i32(6, 8), i32(6)
+    st = SimpleNamespace(cuda_stream=0)  # no call gets as far as the stream
+
+    def call(*a, **kw):
+        return lambda: L.ppmd_lj_forces_noalloc(*a, stream=st, **kw)
+    _raises(call(pos.float(), BOX, nbr, cnt, F, None, None), "pos")
+    _raises(call(pos, BOX, nbr, cnt, f64(5, 3), None, None), "force")
+    _raises(call(pos, BOX, i32(5, 8), cnt, F, None, None), "nbr")
+    _raises(call(pos, BOX, nbr, i32(5), F, None, None), "nbr_count")
+    _raises(call(pos, BOX, nbr, cnt, F, f64(5), None), "e_atom")
+    _raises(call(pos, BOX, nbr, cnt, F, None, f64(1)), "totals")
+    # an n at or below the limit is taken from the arrays, never from the caller
+    _raises(call(pos, BOX, nbr, cnt, F.float(), None, None, n=3), "force")
