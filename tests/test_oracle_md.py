@@ -74,6 +74,26 @@ def test_neighbour_list_cells_equal_brute_force(seed):
         assert all((j, i) in pairs for (i, j) in pairs)
 
 
+@pytest.mark.parametrize("seed", [14, 15])
+def test_cells_and_lists_on_an_uneven_grid(seed):
+    """A box of 3 x 4 x 5 (r 2.8) and 3 x 4 x 6 (r 2.5) cells: every cell
+    index, its decoding and the stencil's wrap use the edge's own count
+    (on an n x n x n grid the axes could be swapped unseen)."""
+    box = np.array([9.0, 12.0, 15.3])
+    pos, box = random_box(320, box, seed, cutoffs=(2.5, 2.8), margin=1e-3, min_dist=0.85)
+    for r, grid in ((2.8, [3, 4, 5]), (2.5, [3, 4, 6])):
+        nc, cell_of, start, atoms = oracle.cells(pos, box, r)
+        assert list(nc) == grid
+        w = box / nc
+        cz, rem = np.divmod(cell_of, nc[0] * nc[1])
+        cy, cx = np.divmod(rem, nc[0])
+        cc = np.stack([cx, cy, cz], 1)
+        assert (cc * w <= pos + 1e-12).all() and (pos < (cc + 1) * w + 1e-12).all()
+        o1, n1 = oracle.neighbours_brute(pos, box, r)
+        o2, n2 = oracle.neighbours_cells(pos, box, r)
+        assert np.array_equal(o1, o2) and np.array_equal(n1, n2)
+
+
 def test_cells_contain_their_atoms():
     c = configs.lj_solid(n_cells=6)
     pos, box = c["pos"], c["box"]

@@ -40,6 +40,15 @@ MUTANTS = {
                               [MD + "test_cells_contain_their_atoms"]),
     "stencil_misses_a_layer": ("for (int ox = -1; ox <= 1; ++ox)", "for (int ox = -1; ox <= 0; ++ox)", 0,
                                [MD + "test_neighbour_list_cells_equal_brute_force"]),
+    "stencil_y_wraps_by_nx": ("int32_t y = (cy + oy + nc[1]) % nc[1];", "int32_t y = (cy + oy + nc[1]) % nc[0];", 0,
+                              [MD + "test_cells_and_lists_on_an_uneven_grid"]),
+    "cell_decoded_with_nx_for_y": ("cy = (c / nc[0]) % nc[1]", "cy = (c / nc[0]) % nc[0]", 0,
+                                   [MD + "test_cells_and_lists_on_an_uneven_grid"]),
+    "cell_index_with_nx_twice": ("cell_of[i] = (cz * nc[1] + cy) * nc[0] + cx;",
+                                 "cell_of[i] = (cz * nc[0] + cy) * nc[0] + cx;", 0,
+                                 [MD + "test_cells_and_lists_on_an_uneven_grid"]),
+    "cell_count_rounded": ("nc[d] = (int32_t)floor(L[d] / r);", "nc[d] = (int32_t)rint(L[d] / r);", 0,
+                           [MD + "test_neighbour_list_cells_equal_brute_force"]),
     # Lennard-Jones pair loop, Eqs. (9) and (12)
     "force_sign_x": ("fx += fmag * dr[0];", "fx -= fmag * dr[0];", 0,
                      [MD + "test_force_is_minus_energy_gradient"]),
