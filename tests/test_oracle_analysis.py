@@ -206,6 +206,41 @@ def test_cna_matches_brute_force(seed):
     assert len(set(ref.values())) >= 5 and any(v[2] < v[1] for v in ref.values())
 
 
+def test_cna_label_rule_needs_the_exact_signature():
+    """Sec. 4.2's signatures, exactly: fcc 12 bonds all (4,2,1); hcp 12 bonds,
+    six (4,2,1) and six (4,2,2); bcc 14 bonds, eight (6,6,6) and six
+    (4,4,4).  Any other count or mix is other."""
+    t421, t422 = oracle.triplet(4, 2, 1), oracle.triplet(4, 2, 2)
+    t444, t666, t311 = oracle.triplet(4, 4, 4), oracle.triplet(6, 6, 6), oracle.triplet(3, 1, 1)
+    rows = [
+        (12, [t421] * 12, 1), (12, [t421] * 6 + [t422] * 6, 2), (14, [t666] * 8 + [t444] * 6, 3),
+        (12, [t421] * 11 + [t311], 0), (12, [t421] * 10 + [t422] * 2, 0), (12, [t421] * 7 + [t422] * 5, 0),
+        (12, [t421] * 5 + [t422] * 7, 0), (12, [t422] * 12, 0), (13, [t421] * 13, 0), (11, [t421] * 11, 0),
+        (14, [t666] * 7 + [t444] * 7, 0), (14, [t666] * 9 + [t444] * 5, 0), (13, [t666] * 8 + [t444] * 5, 0),
+        (15, [t666] * 8 + [t444] * 7, 0), (14, [t421] * 14, 0), (0, [], 0),
+    ]
+    mb = 16
+    nbond = np.array([r[0] for r in rows], np.int32)
+    trip = np.full((len(rows), mb), 0xFFFFFFFF, np.uint32)
+    for k, (nb, ts, _) in enumerate(rows):
+        trip[k, :len(ts)] = ts
+    assert oracle.cna_label(nbond, trip).tolist() == [r[2] for r in rows]
+
+
+def test_bond_order_of_an_atom_without_bonds_is_zero():
+    """Atoms 3 apart have no neighbour within the bond-order cutoff: nu = 0
+    and, by the convention of Eqs. (4)-(5), Q_l = 0 for every l."""
+    k = np.arange(4)
+    pos = 3.0 * np.stack(np.meshgrid(k, k, k, indexing="ij"), -1).reshape(-1, 3)
+    box = np.full(3, 12.0)
+    offs, nbr = oracle.neighbours_brute(pos, box, 3.5)
+    assert (np.diff(offs) > 0).all()  # listed neighbours, none of them bonded
+    for l in (4, 5, 6):
+        Q, nnb = oracle.boa(pos, box, offs, nbr, 1.5, l)
+        assert (nnb == 0).all() and (Q == 0).all()
+        assert (oracle.boa(pos, box, offs, nbr, 1.5, l, method="addition") == 0).all()
+
+
 def test_cna_labels_permutation_invariant():
     c = configs.structure_box("hcp", 0.05, seed=9, cells=(6, 3, 3))
     pos, box = c["pos"], c["box"]
@@ -335,9 +370,9 @@ def test_mlp_input_standardisation():
     assert np.allclose(mlp.forward(p, x)[0], mlp.forward(q, z)[0], rtol=1e-12, atol=1e-12)
     # AdamW leaves the standardisation alone
     g = {k: np.ones_like(v) for k, v in p.items()}
-    mu0 = p["mu"].copy()
+    mu0, isd0 = p["mu"].copy(), p["isd"].copy()
     mlp.adamw_step(p, g, mlp.adamw_init(p), lr=0.1, wd=0.5)
-    assert np.array_equal(p["mu"], mu0)
+    assert np.array_equal(p["mu"], mu0) and np.array_equal(p["isd"], isd0)
 
 
 def test_softmax_of_large_logits():

@@ -92,6 +92,10 @@ def test_cells_and_lists_on_an_uneven_grid(seed):
         o1, n1 = oracle.neighbours_brute(pos, box, r)
         o2, n2 = oracle.neighbours_cells(pos, box, r)
         assert np.array_equal(o1, o2) and np.array_equal(n1, n2)
+        # periodic images of the positions (whole box lengths added or taken
+        # away) fall in the same cells: coordinates are wrapped first
+        shift = np.random.default_rng(seed).integers(-2, 3, pos.shape) * box
+        assert np.array_equal(oracle.cells(pos + shift, box, r)[1], cell_of)
 
 
 def test_cells_contain_their_atoms():
@@ -250,6 +254,10 @@ def test_md_max_displacement_since_rebuild():
     assert (F == 0).all() and np.array_equal(v, vel)
     expect = 10 * dt * np.sqrt((vel ** 2).sum(1)).max()
     assert abs(md - expect) < 1e-12
+    # a rebuild at steps 4, 8, ... (not one step early or late): 6 steps with
+    # a rebuild every 4 leave 4 steps as the longest flight since a build
+    md = oracle.md_run(pos, vel, box, 6, rc=2.5, r_list=2.8, rebuild_every=4, dt=dt)[4]
+    assert abs(md - 4 * dt * np.sqrt((vel ** 2).sum(1)).max()) < 1e-12
 
 
 def _cold_crystal(dt, nsteps, mass=1.0):

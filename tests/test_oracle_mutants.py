@@ -220,6 +220,35 @@ MUTANTS = {
         [AN + "test_features_perfect_fcc_closed_form"]),
     "histogram_low_edge_shifted": ("double lo = r_ref - 0.35;", "double lo = r_ref - 0.30;", 0,
                                    [AN + "test_features_perfect_fcc_closed_form"]),
+    "fcc_label_with_10_of_12": ("if (nb == 12 && c421 == 12) lab = 1;", "if (nb == 12 && c421 >= 10) lab = 1;", 0,
+                                [AN + "test_cna_label_rule_needs_the_exact_signature"]),
+    "hcp_label_from_any_mix": ("else if (nb == 12 && c421 == 6 && c422 == 6) lab = 2;",
+                               "else if (nb == 12 && c421 + c422 == 12) lab = 2;", 0,
+                               [AN + "test_cna_label_rule_needs_the_exact_signature"]),
+    "bcc_label_loosened": ("else if (nb == 14 && c666 == 8 && c444 == 6) lab = 3;",
+                           "else if (nb >= 13 && c666 >= 7 && c444 >= 6) lab = 3;", 0,
+                           [AN + "test_cna_label_rule_needs_the_exact_signature"]),
+    "rebuild_one_step_early": ("if (rebuild_every > 0 && s % rebuild_every == 0) {",
+                               "if (rebuild_every > 0 && (s + 1) % rebuild_every == 0) {", 1,
+                               [MD + "test_md_max_displacement_since_rebuild"]),
+    "q_of_a_lone_atom_one": ("        if (nu == 0) {\n            Q[i] = 0.0;\n            continue;\n        }\n"
+                             "        double s = 0.0;\n        for (int m",
+                             "        if (nu == 0) {\n            Q[i] = 1.0;\n            continue;\n        }\n"
+                             "        double s = 0.0;\n        for (int m", 0,
+                             [AN + "test_bond_order_of_an_atom_without_bonds_is_zero"]),
+    "cells_of_unwrapped_coordinates": ("double xw = wrap1(x, L);", "double xw = x;", 0,
+                                       [MD + "test_cells_and_lists_on_an_uneven_grid"]),
+    "min_image_y_counted_twice": ("return dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2];",
+                                  "return dr[0] * dr[0] + dr[1] * dr[1] + dr[1] * dr[1];", 0,
+                                  [MD + "test_lattice_energy_closed_form"]),
+    "kinetic_y_counted_twice": ("vel[3 * i + 2] * vel[3 * i + 2]);", "vel[3 * i + 1] * vel[3 * i + 1]);", 0,
+                                [MD + "test_vv_energy_error_is_second_order"]),
+    "histogram_centres_unshifted": ("double x = (chord - lo) / 0.05 - 0.5;", "double x = (chord - lo) / 0.05;", 0,
+                                    [AN + "test_features_perfect_fcc_closed_form"]),
+    "acna_bcc_scale_inverted": ("const double c = 2.0 / sqrt(3.0);", "const double c = sqrt(3.0) / 2.0;", 0,
+                                [AN + "test_acna_perfect_lattices_at_any_density"]),
+    "thirteen_distance_features": ("for (int k = 0; k < 14; ++k) f[2 + k] =", "for (int k = 0; k < 13; ++k) f[2 + k] =", 0,
+                                   [AN + "test_features_perfect_fcc_closed_form"]),
 }
 
 # the classifier's network, forward and backward passes, AdamW (oracle/mlp.py)
@@ -270,6 +299,9 @@ MLP_MUTANTS = {
                                            [AN + "test_mlp_gradient_matches_finite_differences"]),
     "bf16_round_truncates": ("r = ((u + 0x7FFF + keep_lsb) >> 16) << 16", "r = (u >> 16) << 16", 0,
                              [BF + "test_bf16_round_matches_torch"]),
+    "adamw_trains_the_scales": ('        if k in ("mu", "isd"):\n            continue  # fitted, not trained',
+                                '        if k in ("mu",):\n            continue  # fitted, not trained', 0,
+                                [AN + "test_mlp_input_standardisation"]),
     "bf16_standardised_inputs_unrounded": ('xs = bf16_round((f32(x) - f32(p["mu"])) * f32(p["isd"]))',
                                            'xs = (f32(x) - f32(p["mu"])) * f32(p["isd"])', 0,
                                            [BF + "test_forward_bf16_operands_are_bf16_values"]),
