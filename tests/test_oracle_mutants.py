@@ -5,9 +5,11 @@ sign, a dropped factor, a wrong exponent, index or bound, a transposed
 operand, a skipped step -- and runs the pins named beside it against that
 copy in a child pytest: for the C source (MUTANTS) a build made with the
 oracle's own compiler flags, loaded through PPMD_ORACLE_LIB; for the NumPy
-network (MLP_MUTANTS) the copy imported as `oracle.mlp`, and for the
+network (MLP_MUTANTS) the copy imported as `oracle.mlp`, for the
 package's own Python (PKG_MUTANTS) a copy of the package imported as
-`oracle`, before the pins are collected.  A case passes when at least one of its pins fails, so every
+`oracle`, and for the classifier parity tests' comparison helpers
+(PIPE_MUTANTS) a copy imported as `oracle_pipeline`, before the pins are
+collected.  A case passes when at least one of its pins fails, so every
 entry records which pin stands guard over which part of the oracle.  The
 CUDA library is not involved.
 """
@@ -320,9 +322,32 @@ PKG_MUTANTS = {
                                    0, [AN + "test_boa_tolerance_labels_perfect_lattices"]),
 }
 
+# the classifier parity tests' comparison helpers (tests/oracle_pipeline.py):
+# the logit tolerance of a row and the labels admissible within it
+PIPE_SRC = os.path.join(ROOT, "tests", "oracle_pipeline.py")
+OP = "tests/test_oracle_pipeline_cpu.py::"
+PIPE_MUTANTS = {
+    "input_step_budget_x10": ("        tol *= 2.0", "        tol *= 20.0", 0,
+                              [BF + "test_tolerance_covers_one_feature_step"]),
+    "hidden_layer_step_dropped": ("    tol += (bf16_step(h1)[:, :, None] * np.abs(K1)).max(axis=(1, 2))\n", "", 0,
+                                  [BF + "test_tolerance_covers_fp32_accumulation"]),
+    "bf16_step_four_times_too_large": ("return np.where(a > 0, 2.0 ** (e - 7), 0.0)",
+                                       "return np.where(a > 0, 2.0 ** (e - 5), 0.0)", 0,
+                                       [BF + "test_tolerance_covers_one_feature_step"]),
+    "leading_window_x10": ("cand = logits >= (top - 2.0 * tol)[:, None]", "cand = logits >= (top - 20.0 * tol)[:, None]",
+                           0, [OP + "test_hand_worked_rows"]),
+    "probability_move_x10": ("dp = 3.0 * pmax * (1.0 - pmax) * tol + 1e-6", "dp = 30.0 * pmax * (1.0 - pmax) * tol + 1e-6",
+                             0, [OP + "test_hand_worked_rows"]),
+    "cna_label_always_admissible": ("can_fall = pmax - dp < threshold", "can_fall = pmax - dp < 2.0", 0,
+                                    [OP + "test_no_tolerance_admits_the_rule_alone"]),
+    "every_class_admissible": ("ok[can_keep] = cand[can_keep]", "ok[can_keep] = True", 0,
+                               [OP + "test_no_tolerance_admits_the_rule_alone"]),
+}
+
 # the child process for a Python mutant: the copy is imported under the
-# oracle's module name before pytest imports any test module.  `path` is
-# oracle/mlp.py's copy, or the directory holding a copy of the package.
+# module's own name before pytest imports any test module.  `path` is
+# oracle/mlp.py's copy, tests/oracle_pipeline.py's (saved under that file
+# name), or the directory holding a copy of the package.
 _PY_BOOT = """import importlib.util, os, sys
 sys.path.insert(0, {root!r})
 path = {path!r}
@@ -330,6 +355,12 @@ if os.path.isdir(path):
     sys.path.insert(0, path)
     import oracle
     assert os.path.dirname(oracle.__file__) == os.path.join(path, "oracle")
+elif path.endswith("oracle_pipeline.py"):
+    sys.path.insert(0, os.path.join({root!r}, "tests"))
+    spec = importlib.util.spec_from_file_location("oracle_pipeline", path)
+    m = importlib.util.module_from_spec(spec)
+    sys.modules["oracle_pipeline"] = m
+    spec.loader.exec_module(m)
 else:
     import oracle
     spec = importlib.util.spec_from_file_location("oracle.mlp", path)
@@ -355,7 +386,7 @@ def run_pins(pins, lib=None, py=None):
     """Run the pins against the oracle build `lib`, or the Python copy `py`
     (see _PY_BOOT; None: the repository's own); (pytest's exit code, the
     tail of its output)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     if lib:
         env["PPMD_ORACLE_LIB"] = lib
     args = ["-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu", *pins]
@@ -381,6 +412,13 @@ def _mutant(kind, name, tmp):
         old, new, occurrence, pins = MLP_MUTANTS[name]
         path = os.path.join(tmp, f"{name}.py")
         with open(MLP_SRC) as f, open(path, "w") as g:
+            g.write(plant(f.read(), old, new, occurrence))
+        return run_pins(pins, py=path)
+    if kind == "pipe":
+        old, new, occurrence, pins = PIPE_MUTANTS[name]
+        os.makedirs(os.path.join(tmp, name))
+        path = os.path.join(tmp, name, "oracle_pipeline.py")
+        with open(PIPE_SRC) as f, open(path, "w") as g:
             g.write(plant(f.read(), old, new, occurrence))
         return run_pins(pins, py=path)
     old, new, occurrence, pins = PKG_MUTANTS[name]
@@ -410,11 +448,12 @@ def results():
             futs = {("c", k): ex.submit(_mutant, "c", k, tmp) for k in MUTANTS}
             futs.update({("py", k): ex.submit(_mutant, "py", k, tmp) for k in MLP_MUTANTS})
             futs.update({("pkg", k): ex.submit(_mutant, "pkg", k, tmp) for k in PKG_MUTANTS})
+            futs.update({("pipe", k): ex.submit(_mutant, "pipe", k, tmp) for k in PIPE_MUTANTS})
             yield {key: f.result() for key, f in futs.items()}
 
 
-@pytest.mark.parametrize("table,path", [(MUTANTS, SRC), (MLP_MUTANTS, MLP_SRC), (PKG_MUTANTS, PKG_SRC)],
-                         ids=["c", "mlp", "package"])
+@pytest.mark.parametrize("table,path", [(MUTANTS, SRC), (MLP_MUTANTS, MLP_SRC), (PKG_MUTANTS, PKG_SRC),
+                                        (PIPE_MUTANTS, PIPE_SRC)], ids=["c", "mlp", "package", "pipeline"])
 def test_every_mistake_is_planted_where_named(table, path):
     """Each mistake changes the source at the named place."""
     with open(path) as f:
@@ -426,13 +465,14 @@ def test_every_mistake_is_planted_where_named(table, path):
 
 
 def test_unchanged_sources_pass_the_pins():
-    """The same three routes with nothing planted: the pins pass on a fresh
-    build of the oracle's own C source, on a copy of its network and on a
-    copy of the package."""
+    """The same four routes with nothing planted: the pins pass on a fresh
+    build of the oracle's own C source, on copies of its network and of the
+    package, and on a copy of the comparison helpers."""
     import oracle
     c_pins = sorted({p for *_, ps in MUTANTS.values() for p in ps})
     py_pins = sorted({p for *_, ps in MLP_MUTANTS.values() for p in ps})
     pkg_pins = sorted({p for *_, ps in PKG_MUTANTS.values() for p in ps})
+    pipe_pins = sorted({p for *_, ps in PIPE_MUTANTS.values() for p in ps})
     with tempfile.TemporaryDirectory() as tmp:
         lib = os.path.join(tmp, "unchanged.so")
         oracle.compile_source(SRC, lib)
@@ -444,6 +484,12 @@ def test_unchanged_sources_pass_the_pins():
         code, out = run_pins(py_pins, py=path)
         assert code == 0, out
         code, out = run_pins(pkg_pins, py=copy_package(os.path.join(tmp, "unchanged_package")))
+        assert code == 0, out
+        os.makedirs(os.path.join(tmp, "unchanged_pipeline"))
+        path = os.path.join(tmp, "unchanged_pipeline", "oracle_pipeline.py")
+        with open(PIPE_SRC) as f, open(path, "w") as g:
+            g.write(f.read())
+        code, out = run_pins(pipe_pins, py=path)
         assert code == 0, out
 
 
@@ -463,3 +509,9 @@ def test_pins_catch_the_network_mistake(results, name):
 def test_pins_catch_the_package_mistake(results, name):
     code, out = results[("pkg", name)]
     assert code == 1, f"{name}: the pins {PKG_MUTANTS[name][3]} did not fail (pytest exit {code}):\n{out}"
+
+
+@pytest.mark.parametrize("name", sorted(PIPE_MUTANTS))
+def test_pins_catch_the_comparison_mistake(results, name):
+    code, out = results[("pipe", name)]
+    assert code == 1, f"{name}: the pins {PIPE_MUTANTS[name][3]} did not fail (pytest exit {code}):\n{out}"
